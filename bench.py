@@ -1,0 +1,303 @@
+#!/usr/bin/env python
+"""Benchmark of the blended P2-P1 Stokes hot path on one GB300.
+
+Workload: the spherical shell r in [0.5, 1] (60 macro-tets, radial blending), refinement
+level 5 (1,966,080 micro-tets, 8,325,576 velocity + pressure dofs), viscosity contrast
+1e6 (radial step x plumes x log-normal noise, seed 2), compressible density
+d ln rho/dr = -0.3781.  One step = one fused, constrained saddle-point apply
+[A B^T; (B+C) 0] (x, p) in FP32 — the operator application that the mixed-precision
+solver's Krylov, smoother and residual work is made of.
+Metric: GDoF/s = (N_u + N_p) / time per apply / 1e9.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same workload
+(micro-tets of the same level, scaled to the full apply).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "P2-P1 Stokes apply GDoF/s; time to 1e-8 residual, mixed vs FP64, 1 GB300"
+WORKLOAD = "shell-L5-contrast1e6: blended icosahedral shell, level 5, 8,325,576 dofs, FP32 fused constrained Stokes apply"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+
+
+def fused_stokes_flops_per_tet():
+    """Algorithmic FP32 flops of one micro-tet of the fused apply (FMA = 2 flops),
+    counted term by term from the per-quadrature-point algebra of the sweep kernel
+    (itemised in the design doc): per tet 60 (nodal sums), per qp 4 x 300 (position 24,
+    blending Jacobian and K 57, viscosity/pressure at qp 6, lattice gradient 36,
+    physical gradient 45, divergence + compressible term 32, stress 25, test side 45,
+    accumulation 30), final distribution 123."""
+    return 60 + 4 * 300 + 123
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(f) > 5 + k and f[5 + k].lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def setup_problem(level, device):
+    import numpy as np
+    import torch
+    import paper_2506_04157_gb300 as mfs
+    import workloads as W
+    ctx = mfs.Context(device)
+    mesh = mfs.Mesh(ctx, level)
+    prob = mfs.Problem(mesh)
+    x1 = mesh.coords(level, p2=False).T
+    prob.set_viscosity(torch.tensor(W.viscosity_plumes(x1, seed=2, contrast=1e6), device=f"cuda:{device}"))
+    prob.set_density(W.dlnrho_table_compressible())
+    inf = mesh.info(level)
+    return ctx, mesh, prob, inf
+
+
+def run_ours(args, rank, world, device):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import workloads as W
+
+    torch.cuda.set_device(device)
+    level = args.level
+    ctx, mesh, prob, inf = setup_problem(level, device)
+    nu, npp = 3 * inf.n_p2, inf.n_p1
+    dofs = nu + npp
+    dt = torch.float32
+    bytes_per_set = 4 * (2 * nu + 2 * npp)
+    l2 = 126 * 2 ** 20
+    nsets = max(2, int(np.ceil(2 * l2 / bytes_per_set)))
+    dev = f"cuda:{device}"
+    sets = []
+    for k in range(nsets):
+        u = torch.tensor(W.random_field(nu, 100 + k, np.float32), device=dev)
+        p = torch.tensor(W.random_field(npp, 200 + k, np.float32), device=dev)
+        sets.append((u, p, torch.empty_like(u), torch.empty_like(p)))
+
+    def step(i):
+        u, p, yu, yp = sets[i % nsets]
+        prob.apply_stokes(level, u, p, yu, yp)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.kernel_time()
+    ctx.enable_timing(True)
+    with ClockSampler(device) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for i in range(args.steps):
+            step(i)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ctx.enable_timing(False)
+    ktot, klaunch = ctx.kernel_time()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    ms_per_step = ms_max / args.steps
+    value = world * dofs / (ms_per_step * 1e-3) / 1e9
+
+    # end to end through the public API with host buffers (pinned), copies inside the timing
+    hu = torch.tensor(W.random_field(nu, 7, np.float32)).pin_memory()
+    hp = torch.tensor(W.random_field(npp, 8, np.float32)).pin_memory()
+    ou, op_ = torch.empty_like(hu).pin_memory(), torch.empty_like(hp).pin_memory()
+    du, dp = torch.empty(nu, dtype=dt, device=dev), torch.empty(npp, dtype=dt, device=dev)
+    dyu, dyp = torch.empty_like(du), torch.empty_like(dp)
+
+    def e2e_step():
+        du.copy_(hu, non_blocking=True)
+        dp.copy_(hp, non_blocking=True)
+        prob.apply_stokes(level, du, dp, dyu, dyp)
+        ou.copy_(dyu, non_blocking=True)
+        op_.copy_(dyp, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    n_e2e = max(3, args.steps // 2)
+    e0.record(stream)
+    for _ in range(n_e2e):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / n_e2e
+    e2e_value = world * dofs / (e2e_ms * 1e-3) / 1e9
+
+    if rank != 0:
+        return None
+    peaks = read_peaks()
+    clocks = clk.summary()
+    kern_ms = ktot / max(klaunch, 1)
+    flops = fused_stokes_flops_per_tet() * inf.n_tets
+    achieved = flops / (kern_ms * 1e-3) / 1e12
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "level": level, "n_tets": inf.n_tets, "n_u": nu, "n_p": npp,
+                   "viscosity": "plumes contrast 1e6 seed 2", "parallelism": "replicas" if world > 1 else "single",
+                   "l2": f"{nsets} rotating input sets of {bytes_per_set / 2**20:.1f} MiB (> L2)"},
+        "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "kernel": "stokes_tile_kernel<float, A|BT|B>", "kernel_ms": round(kern_ms, 5),
+                     "flops_per_launch": flops,
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz max clock (derived, not in MEASURED_PEAKS)"},
+        "e2e": {"value": round(e2e_value, 3), "unit": "GDoF/s", "h2d_bytes_per_step": 4 * (nu + npp),
+                "d2h_bytes_per_step": 4 * (nu + npp)},
+        "gpu_launches": int(args.steps * 6),   # per apply: 2 (p sum) + 1 sweep + 2 (q sum) + 1 (mean removal)
+        "clocks": clocks,
+        "hbm_peak_measured_gbs": peaks.get("hbm_gbs"),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(level, budget_s=args.cpu_seconds)
+    return line
+
+
+def cpu_baseline(level, budget_s=12.0):
+    """The FP64 oracle's fused apply on a bounded sample of micro-tets of the same
+    workload, scaled to the full level (GDoF/s)."""
+    import numpy as np
+    import workloads as W
+    from oracle.mesh import MacroMesh, Level
+    from oracle.fem import stokes_apply_elements
+    L = Level(MacroMesh(), level)
+    eta = W.viscosity_plumes(L.p1_x, seed=2, contrast=1e6)
+    u = W.random_field(3 * L.n_p2, 1)
+    p = W.random_field(L.n_p1, 2)
+    ntet = L.tet_p2.shape[0]
+    chunk = 4096
+    done, t_used = 0, 0.0
+    rng = np.random.default_rng(0)
+    while t_used < budget_s and done < ntet:
+        sel = np.sort(rng.choice(ntet, size=chunk, replace=False))
+        t0 = time.perf_counter()
+        stokes_apply_elements(L, eta, W.dlnrho_table_compressible(), u, p, sel)
+        t_used += time.perf_counter() - t0
+        done += chunk
+    t_full = t_used * ntet / done
+    dofs = 3 * L.n_p2 + L.n_p1
+    return {"value": round(dofs / t_full / 1e9, 6), "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done} of {ntet} micro-tets (random), {t_used:.1f} s, scaled to one full apply"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    times = []
+    cb = None
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(args.level, budget_s=max(1.0, args.cpu_seconds / max(1, args.steps)))
+        if i >= args.warmup:
+            times.append(cb["value"])
+    v = statistics.median(times)
+    cb["value"] = v
+    return {"metric": METRIC, "value": v, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "level": args.level},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--level", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        import torch
+        import torch.distributed as dist
+        if world > 1:
+            dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+        line = run_ours(args, rank, world, local)
+        if world > 1:
+            dist.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

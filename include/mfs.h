@@ -1,0 +1,165 @@
+/* mfs.h — matrix-free blended P2-P1 Stokes operators and solver on one GPU (sm_103a).
+ *
+ * C ABI of libmfs.so.  Method: arxiv 2506.04157 ("paper" below).
+ *
+ * Conventions for every entry point
+ *   - Return value: MFS_OK or an error code; the library never aborts.  On error,
+ *     mfs_last_error() returns a message (thread-local, valid until the next call).
+ *   - Vector arguments are DEVICE pointers owned by the caller (e.g. torch tensors),
+ *     contiguous, on the context's device, unless a parameter says "host".
+ *   - Velocity vectors are component-major [3][n_p2] (SoA: all x, then all y, then z);
+ *     pressure and viscosity vectors are [n_p1].  FP64 entry points (prec = MFS_F64)
+ *     take double*, FP32 ones (prec = MFS_F32) take float*.
+ *   - All device work is enqueued on the context's stream; apply calls are
+ *     asynchronous; calls that return host scalars synchronise the stream.
+ *   - The library owns the mesh hierarchy, per-level coefficient data and solver
+ *     workspaces (device memory it allocates with cudaMalloc); destroy functions free it.
+ *   - One context per host thread at a time.
+ *
+ * Vector layout (node numbering) of refinement level l, N = 2^l intervals per macro
+ * edge, for P1 vertices; the P2 nodes of level l are the P1 vertices of level l+1:
+ *   ids [0, 24)                  macro vertices (12 icosahedron directions on r_cmb,
+ *                                then the same 12 on r_surf)
+ *   then 102 macro edges x (N-1) edge-interior points, from the lower to the higher
+ *                                macro vertex id
+ *   then 140 macro faces x (N-1)(N-2)/2 face-interior points
+ *   then  60 macro cells x (N-1)(N-2)(N-3)/6 cell-interior points.
+ * mfs_mesh_coords() returns the positions in this order.
+ */
+#ifndef MFS_H
+#define MFS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MFS_OK = 0,
+  MFS_EINVAL = 1,      /* invalid argument (null handle, bad level, size, mode) */
+  MFS_ENOMEM = 2,      /* device or host allocation failed */
+  MFS_ECUDA = 3,       /* a CUDA runtime call failed (message has the CUDA error) */
+  MFS_ENOTCONV = 4,    /* iterative solve did not reach its tolerance (best iterate kept) */
+  MFS_EBREAKDOWN = 5,  /* Krylov breakdown (zero denominator) */
+  MFS_ENAN = 6,        /* NaN or Inf in a residual norm */
+  MFS_ETIMEOUT = 7     /* a bounded device-side wait ran out */
+} mfs_status;
+
+typedef enum { MFS_F64 = 0, MFS_F32 = 1 } mfs_prec;
+typedef enum { MFS_BC_DIRICHLET = 0, MFS_BC_FREESLIP = 1 } mfs_bc;
+/* RAW: the full assembled-equivalent block, no boundary handling.
+ * CONSTRAINED: the projected, Dirichlet-eliminated block of the paper's Eq.
+ *   (SaddlePointStructureDirichlet): Dirichlet velocity rows are the identity and
+ *   their columns are dropped, free-slip nodes are projected, u -> u - (u.n)n, on input
+ *   and output (P_v), pressure inputs and outputs are made mean-free (P_p). */
+typedef enum { MFS_RAW = 0, MFS_CONSTRAINED = 1 } mfs_bcmode;
+
+typedef struct mfs_ctx mfs_ctx;
+typedef struct mfs_mesh mfs_mesh;
+typedef struct mfs_problem mfs_problem;
+
+typedef struct {
+  int level;
+  int64_t n_tets;      /* micro-tets: 60 * 8^level */
+  int64_t n_p2;        /* P2 nodes (velocity has 3 * n_p2 entries) */
+  int64_t n_p1;        /* P1 vertices (pressure / viscosity entries) */
+  int64_t n_surface;   /* P2 nodes on r = r_surf */
+  int64_t n_cmb;       /* P2 nodes on r = r_cmb */
+} mfs_level_info;
+
+/* Last error message of the calling thread ("" if none). */
+const char* mfs_last_error(void);
+
+/* Library version string. */
+const char* mfs_version(void);
+
+/* Context: device ordinal and the CUDA stream (cudaStream_t passed as void*, NULL =
+ * legacy default stream) on which all work is enqueued.  The stream stays owned by
+ * the caller.  Errors: MFS_EINVAL (bad device), MFS_ECUDA. */
+mfs_status mfs_ctx_create(int device, void* cuda_stream, mfs_ctx** out);
+mfs_status mfs_ctx_set_stream(mfs_ctx* ctx, void* cuda_stream);
+mfs_status mfs_ctx_destroy(mfs_ctx* ctx);
+
+/* Optional device timing of the element-sweep kernel (the matrix-free micro-tet
+ * sweep behind every apply): with enable != 0 each sweep launch is bracketed by CUDA
+ * events on the context's stream.  mfs_ctx_kernel_time() synchronises the stream and
+ * returns the summed duration (ms) and the number of timed launches since the last
+ * query, then resets both.  Not part of the method; a measurement aid. */
+mfs_status mfs_ctx_timing(mfs_ctx* ctx, int enable);
+mfs_status mfs_ctx_kernel_time(mfs_ctx* ctx, double* total_ms, int64_t* launches);
+
+/* Spherical-shell mesh r_cmb <= |x| <= r_surf (paper Sec. 4.1): the 20 faces of the
+ * icosahedron give 20 prisms in one radial layer, each cut into 3 macro-tets (each
+ * quad face along the diagonal through its lowest-numbered vertex), 60 macro-tets,
+ * uniformly refined (Freudenthal/Kuhn subdivision, 8^l micro-tets per macro) on levels
+ * 0..l_max.  blending = 1 maps the straight mesh onto the shell by the radial blending
+ * map B(x) = (x.nh/delta) x/|x| (nh, delta: normal and offset of the prism's face
+ * plane); blending = 0 keeps the polyhedral shell.  Requires 0 < r_cmb < r_surf,
+ * 0 <= l_max <= 7.  ctx = NULL builds a host-only mesh (numbering, coordinates and node
+ * classes; no device data, no problem can be created on it).
+ * Errors: MFS_EINVAL, MFS_ENOMEM, MFS_ECUDA. */
+mfs_status mfs_mesh_shell(mfs_ctx* ctx, double r_cmb, double r_surf, int l_max, int blending,
+                          mfs_mesh** out);
+mfs_status mfs_mesh_destroy(mfs_mesh* mesh);
+mfs_status mfs_mesh_info(const mfs_mesh* mesh, int level, mfs_level_info* out);
+
+/* Node positions of a level into a HOST buffer xyz[3][n] (component-major), n = n_p2
+ * if p2 != 0 else n_p1; blended = 1 gives physical positions B(x~), 0 the straight
+ * ones.  Errors: MFS_EINVAL. */
+mfs_status mfs_mesh_coords(const mfs_mesh* mesh, int level, int p2, int blended, double* xyz);
+
+/* Node classes of a level into a HOST buffer (0 inner, 1 surface, 2 CMB). */
+mfs_status mfs_mesh_node_class(const mfs_mesh* mesh, int level, int p2, int8_t* cls);
+
+/* Problem = mesh + boundary conditions + coefficients (paper Sec. 2 boundary
+ * conditions, Sec. 5.1 projections).  Defaults of the paper: surface Dirichlet, CMB
+ * free-slip.  Errors: MFS_EINVAL, MFS_ENOMEM. */
+mfs_status mfs_problem_create(mfs_mesh* mesh, mfs_bc bc_surface, mfs_bc bc_cmb, mfs_problem** out);
+mfs_status mfs_problem_destroy(mfs_problem* prob);
+
+/* Nodal P1 viscosity on the finest level (DEVICE pointer, double[n_p1(l_max)]; if
+ * is_log != 0 the values are ln(eta)).  Coarser levels receive it by injection
+ * (coarse vertices are fine vertices): eta is a P1 function on every level, evaluated
+ * at quadrature points by linear interpolation (paper Sec. 5.2.2, "eta_P1 on every
+ * level").  Errors: MFS_EINVAL (non-positive eta reported by a later solve as
+ * MFS_ENAN), MFS_ECUDA. */
+mfs_status mfs_set_viscosity(mfs_problem* prob, const double* eta_p1, int is_log);
+
+/* Radial profile of d ln(rho)/dr on a uniform grid of n >= 1 points over
+ * [r_cmb, r_surf] (HOST array), linearly interpolated at the physical radius of each
+ * quadrature point; it defines C of paper Eq. (SaddlePointStructure),
+ * C_ij = -int (grad ln rho . phi_j) psi_i with grad ln rho = (d ln rho/dr) x/|x|.
+ * Default: 0 (incompressible).  Errors: MFS_EINVAL. */
+mfs_status mfs_set_density(mfs_problem* prob, int n, const double* dlnrho_dr);
+
+/* y = A(eta) u on level lvl (paper Sec. 5.1, A_ij = int 2 eta eps(phi_j):eps(phi_i),
+ * eps(u) = sym grad u - (div u) I/3; blending Jacobian evaluated at every quadrature
+ * point of the symmetric 4-point degree-2 rule).  u, y: [3][n_p2(lvl)].  u and y must
+ * not overlap.  Errors: MFS_EINVAL, MFS_ECUDA. */
+mfs_status mfs_apply_A(mfs_problem* prob, int lvl, mfs_prec prec, mfs_bcmode mode, const void* u,
+                       void* y);
+
+/* q = B u or q = (B + C) u (with_C != 0), B_ij = -int (div phi_j) psi_i (paper Sec. 5.1).
+ * u: [3][n_p2], q: [n_p1].  Errors: MFS_EINVAL, MFS_ECUDA. */
+mfs_status mfs_apply_B(mfs_problem* prob, int lvl, mfs_prec prec, mfs_bcmode mode, int with_C,
+                       const void* u, void* q);
+
+/* y = B^T p, or y = (B + C)^T p if with_C != 0.  p: [n_p1], y: [3][n_p2]. */
+mfs_status mfs_apply_BT(mfs_problem* prob, int lvl, mfs_prec prec, mfs_bcmode mode, int with_C,
+                        const void* p, void* y);
+
+/* Fused saddle-point operator in one sweep over the micro-tets (paper Eq.
+ * SaddlePointStructure with Bbar = B + C):
+ *   transpose = 0:  yu = A u + B^T p,     yp = (B + C) u
+ *   transpose = 1:  yu = A u + (B + C)^T p, yp = B u       (the adjoint operator)
+ * Always CONSTRAINED (projections of Eq. SaddlePointStructureDirichlet).
+ * Errors: MFS_EINVAL, MFS_ECUDA. */
+mfs_status mfs_apply_stokes(mfs_problem* prob, int lvl, mfs_prec prec, int transpose, const void* u,
+                            const void* p, void* yu, void* yp);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MFS_H */

@@ -251,3 +251,36 @@ class ConstrainedOperators:
 
     def apply_BbarT(self, q):
         return self.BbarT_raw @ project_mean_zero(q)
+
+
+def stokes_apply_elements(level, eta_p1, dlnrho_table, u, p, sel):
+    """Raw fused operator restricted to the micro-tets `sel`:
+         yu = sum_e (A_e u_e + B_e^T p_e),   yp = sum_e (B_e + C_e) u_e
+    (element matrices are the definition, the sum over all tets is the operator).
+    Returns dense yu [3 n_p2], yp [n_p1] holding only those contributions."""
+    mesh = level.mesh
+    geo = Geometry(mesh, level.tet_x[sel], level.tet_prism[sel])
+    Ae = element_A(geo, np.asarray(eta_p1)[level.tet_p1[sel]])
+    Be = element_B(geo)
+    Ce = element_C(geo, mesh, dlnrho_table)
+    vd = velocity_dofs(level, sel)
+    pd = level.tet_p1[sel]
+    ue = np.asarray(u)[vd]
+    pe = np.asarray(p)[pd]
+    yu_e = np.einsum("eij,ej->ei", Ae, ue) + np.einsum("eki,ek->ei", Be, pe)
+    yp_e = np.einsum("eki,ei->ek", Be + Ce, ue)
+    yu = np.zeros(3 * level.n_p2)
+    yp = np.zeros(level.n_p1)
+    np.add.at(yu, vd.reshape(-1), yu_e.reshape(-1))
+    np.add.at(yp, pd.reshape(-1), yp_e.reshape(-1))
+    return yu, yp
+
+
+def tets_touching(level, p2_nodes=None, p1_nodes=None):
+    """Indices of the micro-tets that contain any of the given P2 nodes / P1 vertices."""
+    mask = np.zeros(level.tet_p2.shape[0], dtype=bool)
+    if p2_nodes is not None:
+        mask |= np.isin(level.tet_p2, p2_nodes).any(axis=1)
+    if p1_nodes is not None:
+        mask |= np.isin(level.tet_p1, p1_nodes).any(axis=1)
+    return np.nonzero(mask)[0]

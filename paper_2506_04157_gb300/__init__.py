@@ -1,0 +1,219 @@
+"""Python binding of libmfs: matrix-free blended P2-P1 Stokes on one GB300.
+
+A thin ctypes layer over the C ABI in include/mfs.h: it marshals handles, torch device
+pointers and the current CUDA stream; every computation runs in the library's CUDA
+kernels.  There is no fallback: if libmfs.so is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libmfs.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, EBREAKDOWN, ENAN, ETIMEOUT = range(8)
+F64, F32 = 0, 1
+BC = {"dirichlet": 0, "freeslip": 1}
+RAW, CONSTRAINED = 0, 1
+
+_STATUS = {0: "MFS_OK", 1: "MFS_EINVAL", 2: "MFS_ENOMEM", 3: "MFS_ECUDA", 4: "MFS_ENOTCONV",
+           5: "MFS_EBREAKDOWN", 6: "MFS_ENAN", 7: "MFS_ETIMEOUT"}
+
+
+class MfsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class LevelInfo(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int), ("n_tets", ctypes.c_int64), ("n_p2", ctypes.c_int64),
+                ("n_p1", ctypes.c_int64), ("n_surface", ctypes.c_int64), ("n_cmb", ctypes.c_int64)]
+
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_d = ctypes.c_double
+_SIGS = {
+    "mfs_last_error": ([], ctypes.c_char_p),
+    "mfs_version": ([], ctypes.c_char_p),
+    "mfs_ctx_create": ([_i, _vp, ctypes.POINTER(_vp)], _i),
+    "mfs_ctx_set_stream": ([_vp, _vp], _i),
+    "mfs_ctx_destroy": ([_vp], _i),
+    "mfs_ctx_timing": ([_vp, _i], _i),
+    "mfs_ctx_kernel_time": ([_vp, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_int64)], _i),
+    "mfs_mesh_shell": ([_vp, _d, _d, _i, _i, ctypes.POINTER(_vp)], _i),
+    "mfs_mesh_destroy": ([_vp], _i),
+    "mfs_mesh_info": ([_vp, _i, ctypes.POINTER(LevelInfo)], _i),
+    "mfs_mesh_coords": ([_vp, _i, _i, _i, _vp], _i),
+    "mfs_mesh_node_class": ([_vp, _i, _i, _vp], _i),
+    "mfs_problem_create": ([_vp, _i, _i, ctypes.POINTER(_vp)], _i),
+    "mfs_problem_destroy": ([_vp], _i),
+    "mfs_set_viscosity": ([_vp, _vp, _i], _i),
+    "mfs_set_density": ([_vp, _i, _vp], _i),
+    "mfs_apply_A": ([_vp, _i, _i, _i, _vp, _vp], _i),
+    "mfs_apply_B": ([_vp, _i, _i, _i, _i, _vp, _vp], _i),
+    "mfs_apply_BT": ([_vp, _i, _i, _i, _i, _vp, _vp], _i),
+    "mfs_apply_stokes": ([_vp, _i, _i, _i, _vp, _vp, _vp, _vp], _i),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded libmfs.so (raises MfsError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise MfsError(EINVAL, f"{LIB_PATH} not built (python -m paper_2506_04157_gb300.build)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != OK:
+        raise MfsError(status, lib().mfs_last_error().decode())
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _prec_of(t):
+    import torch
+    if t.dtype == torch.float64:
+        return F64
+    if t.dtype == torch.float32:
+        return F32
+    raise MfsError(EINVAL, f"unsupported dtype {t.dtype}")
+
+
+def _need(t, n, dtype=None, name="tensor"):
+    if not t.is_cuda or not t.is_contiguous():
+        raise MfsError(EINVAL, f"{name} must be a contiguous CUDA tensor")
+    if t.numel() != n:
+        raise MfsError(EINVAL, f"{name} has {t.numel()} entries, expected {n}")
+    if dtype is not None and t.dtype != dtype:
+        raise MfsError(EINVAL, f"{name} has dtype {t.dtype}, expected {dtype}")
+
+
+class Context:
+    """Device + stream; the stream defaults to torch's current stream."""
+
+    def __init__(self, device=0, stream=None):
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream(device).cuda_stream
+        h = ctypes.c_void_p()
+        _check(lib().mfs_ctx_create(device, ctypes.c_void_p(stream), ctypes.byref(h)))
+        self.handle, self.device = h, device
+
+    def set_stream(self, stream):
+        _check(lib().mfs_ctx_set_stream(self.handle, ctypes.c_void_p(stream)))
+
+    def enable_timing(self, on=True):
+        _check(lib().mfs_ctx_timing(self.handle, int(on)))
+
+    def kernel_time(self):
+        """(total ms, launches) of the timed element-sweep kernels since the last call."""
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        _check(lib().mfs_ctx_kernel_time(self.handle, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.mfs_ctx_destroy(self.handle)
+            self.handle = None
+
+
+class Mesh:
+    """Blended icosahedral shell mesh with levels 0..l_max (ctx=None: host-only)."""
+
+    def __init__(self, ctx, l_max, r_cmb=0.5, r_surf=1.0, blending=True):
+        h = ctypes.c_void_p()
+        _check(lib().mfs_mesh_shell(ctx.handle if ctx is not None else None, r_cmb, r_surf, l_max,
+                                    1 if blending else 0, ctypes.byref(h)))
+        self.handle, self.ctx, self.l_max = h, ctx, l_max
+        self.r_cmb, self.r_surf = r_cmb, r_surf
+
+    def info(self, level):
+        out = LevelInfo()
+        _check(lib().mfs_mesh_info(self.handle, level, ctypes.byref(out)))
+        return out
+
+    def coords(self, level, p2=True, blended=True):
+        n = self.info(level).n_p2 if p2 else self.info(level).n_p1
+        buf = np.empty((3, n), dtype=np.float64)
+        _check(lib().mfs_mesh_coords(self.handle, level, int(p2), int(blended),
+                                     buf.ctypes.data_as(ctypes.c_void_p)))
+        return buf
+
+    def node_class(self, level, p2=True):
+        n = self.info(level).n_p2 if p2 else self.info(level).n_p1
+        buf = np.empty(n, dtype=np.int8)
+        _check(lib().mfs_mesh_node_class(self.handle, level, int(p2), buf.ctypes.data_as(ctypes.c_void_p)))
+        return buf
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.mfs_mesh_destroy(self.handle)
+            self.handle = None
+
+
+class Problem:
+    """Mesh + boundary conditions + viscosity/density; operator applies on torch tensors."""
+
+    def __init__(self, mesh, bc_surface="dirichlet", bc_cmb="freeslip"):
+        h = ctypes.c_void_p()
+        _check(lib().mfs_problem_create(mesh.handle, BC[bc_surface], BC[bc_cmb], ctypes.byref(h)))
+        self.handle, self.mesh = h, mesh
+
+    def set_viscosity(self, eta, is_log=False):
+        import torch
+        _need(eta, self.mesh.info(self.mesh.l_max).n_p1, torch.float64, "eta")
+        _check(lib().mfs_set_viscosity(self.handle, _ptr(eta), int(is_log)))
+
+    def set_density(self, dlnrho_dr):
+        t = np.ascontiguousarray(np.atleast_1d(dlnrho_dr), dtype=np.float64)
+        _check(lib().mfs_set_density(self.handle, t.size, t.ctypes.data_as(ctypes.c_void_p)))
+
+    def _sizes(self, level):
+        inf = self.mesh.info(level)
+        return 3 * inf.n_p2, inf.n_p1
+
+    def apply_A(self, level, u, y, constrained=False):
+        nu, _ = self._sizes(level)
+        _need(u, nu, None, "u"); _need(y, nu, u.dtype, "y")
+        _check(lib().mfs_apply_A(self.handle, level, _prec_of(u), int(constrained), _ptr(u), _ptr(y)))
+
+    def apply_B(self, level, u, q, with_C=True, constrained=False):
+        nu, npp = self._sizes(level)
+        _need(u, nu, None, "u"); _need(q, npp, u.dtype, "q")
+        _check(lib().mfs_apply_B(self.handle, level, _prec_of(u), int(constrained), int(with_C),
+                                 _ptr(u), _ptr(q)))
+
+    def apply_BT(self, level, p, y, with_C=False, constrained=False):
+        nu, npp = self._sizes(level)
+        _need(p, npp, None, "p"); _need(y, nu, p.dtype, "y")
+        _check(lib().mfs_apply_BT(self.handle, level, _prec_of(p), int(constrained), int(with_C),
+                                  _ptr(p), _ptr(y)))
+
+    def apply_stokes(self, level, u, p, yu, yp, transpose=False):
+        nu, npp = self._sizes(level)
+        _need(u, nu, None, "u"); _need(p, npp, u.dtype, "p")
+        _need(yu, nu, u.dtype, "yu"); _need(yp, npp, u.dtype, "yp")
+        _check(lib().mfs_apply_stokes(self.handle, level, _prec_of(u), int(transpose), _ptr(u), _ptr(p),
+                                      _ptr(yu), _ptr(yp)))
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.mfs_problem_destroy(self.handle)
+            self.handle = None

@@ -1,0 +1,464 @@
+// C ABI of libmfs (declared in include/mfs.h).
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "library.h"
+
+namespace mfs {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+mfs_status cuda_fail(cudaError_t e, const char* what) {
+  set_error("CUDA error %s (%s) in %s", cudaGetErrorName(e), cudaGetErrorString(e), what);
+  return e == cudaErrorMemoryAllocation ? MFS_ENOMEM : MFS_ECUDA;
+}
+
+template <typename T>
+static mfs_status upload(T** dst, const T* src, size_t count, cudaStream_t s) {
+  MFS_CUDA(cudaMalloc((void**)dst, sizeof(T) * (count ? count : 1)));
+  if (count) MFS_CUDA(cudaMemcpyAsync(*dst, src, sizeof(T) * count, cudaMemcpyHostToDevice, s));
+  return MFS_OK;
+}
+
+static mfs_status check_level(const mfs_mesh* M, int lvl) {
+  if (!M) {
+    set_error("null mesh");
+    return MFS_EINVAL;
+  }
+  if (lvl < 0 || lvl > M->l_max) {
+    set_error("level %d outside [0, %d]", lvl, M->l_max);
+    return MFS_EINVAL;
+  }
+  return MFS_OK;
+}
+
+static mfs_status check_problem(const mfs_problem* P, int lvl, bool need_eta) {
+  if (!P) {
+    set_error("null problem");
+    return MFS_EINVAL;
+  }
+  MFS_TRY(check_level(P->mesh, lvl));
+  if (need_eta && !P->has_eta) {
+    set_error("viscosity not set (call mfs_set_viscosity first)");
+    return MFS_EINVAL;
+  }
+  return MFS_OK;
+}
+
+std::pair<cudaEvent_t, cudaEvent_t> timing_events(mfs_ctx* ctx) {
+  if (!ctx || !ctx->timing) return {nullptr, nullptr};
+  cudaEvent_t e[2];
+  for (int k = 0; k < 2; ++k) {
+    if (!ctx->ev_pool.empty()) {
+      e[k] = ctx->ev_pool.back();
+      ctx->ev_pool.pop_back();
+    } else if (cudaEventCreate(&e[k]) != cudaSuccess) {
+      return {nullptr, nullptr};
+    }
+  }
+  ctx->ev_used.push_back({e[0], e[1]});
+  return {e[0], e[1]};
+}
+
+}  // namespace mfs
+
+using namespace mfs;
+
+// Definitions below inherit C linkage from their declarations in mfs.h.
+
+const char* mfs_last_error(void) { return g_err; }
+const char* mfs_version(void) { return "mfs 0.1 (sm_103a)"; }
+
+mfs_status mfs_ctx_create(int device, void* stream, mfs_ctx** out) {
+  if (!out) {
+    set_error("null output handle");
+    return MFS_EINVAL;
+  }
+  int nd = 0;
+  MFS_CUDA(cudaGetDeviceCount(&nd));
+  if (device < 0 || device >= nd) {
+    set_error("device %d not available (%d devices)", device, nd);
+    return MFS_EINVAL;
+  }
+  MFS_CUDA(cudaSetDevice(device));
+  mfs_ctx* c = new (std::nothrow) mfs_ctx;
+  if (!c) {
+    set_error("host allocation failed");
+    return MFS_ENOMEM;
+  }
+  c->device = device;
+  c->stream = (cudaStream_t)stream;
+  *out = c;
+  return MFS_OK;
+}
+
+mfs_status mfs_ctx_set_stream(mfs_ctx* ctx, void* stream) {
+  if (!ctx) {
+    set_error("null context");
+    return MFS_EINVAL;
+  }
+  ctx->stream = (cudaStream_t)stream;
+  return MFS_OK;
+}
+
+mfs_status mfs_ctx_destroy(mfs_ctx* ctx) {
+  if (!ctx) return MFS_OK;
+  for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+  for (auto& e : ctx->ev_used) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  delete ctx;
+  return MFS_OK;
+}
+
+mfs_status mfs_ctx_timing(mfs_ctx* ctx, int enable) {
+  if (!ctx) {
+    set_error("null context");
+    return MFS_EINVAL;
+  }
+  ctx->timing = enable ? 1 : 0;
+  return MFS_OK;
+}
+
+mfs_status mfs_ctx_kernel_time(mfs_ctx* ctx, double* total_ms, int64_t* launches) {
+  if (!ctx || !total_ms || !launches) {
+    set_error("null argument");
+    return MFS_EINVAL;
+  }
+  MFS_CUDA(cudaStreamSynchronize(ctx->stream));
+  double tot = 0.0;
+  for (auto& e : ctx->ev_used) {
+    float ms = 0.f;
+    MFS_CUDA(cudaEventElapsedTime(&ms, e.first, e.second));
+    tot += ms;
+    ctx->ev_pool.push_back(e.first);
+    ctx->ev_pool.push_back(e.second);
+  }
+  *total_ms = tot;
+  *launches = (int64_t)ctx->ev_used.size();
+  ctx->ev_used.clear();
+  return MFS_OK;
+}
+
+mfs_status mfs_mesh_shell(mfs_ctx* ctx, double r_cmb, double r_surf, int l_max, int blending, mfs_mesh** out) {
+  if (!out) {
+    set_error("null output handle");
+    return MFS_EINVAL;
+  }
+  if (!(r_cmb > 0.0) || !(r_surf > r_cmb)) {
+    set_error("need 0 < r_cmb < r_surf (got %g, %g)", r_cmb, r_surf);
+    return MFS_EINVAL;
+  }
+  if (l_max < 0 || l_max > 7) {
+    set_error("l_max %d outside [0, 7]", l_max);
+    return MFS_EINVAL;
+  }
+  if (ctx) MFS_CUDA(cudaSetDevice(ctx->device));
+  mfs_mesh* M = new (std::nothrow) mfs_mesh;
+  if (!M) {
+    set_error("host allocation failed");
+    return MFS_ENOMEM;
+  }
+  M->ctx = ctx;
+  M->l_max = l_max;
+  M->host.build(r_cmb, r_surf, blending ? 1 : 0);
+  if (!ctx) {  // host-only mesh: numbering, coordinates and classes, no device data
+    *out = M;
+    return MFS_OK;
+  }
+  cudaStream_t s = ctx->stream;
+  mfs_status st = upload(&M->d_topo, M->host.topo, 60, s);
+  MacroGeom<float> g32[60];
+  for (int m = 0; m < 60 && st == MFS_OK; ++m) g32[m] = cast_geom<float>(M->host.geom[m]);
+  if (st == MFS_OK) st = upload(&M->d_geom64, M->host.geom, 60, s);
+  if (st == MFS_OK) st = upload(&M->d_geom32, g32, 60, s);
+  for (int l = 0; l <= l_max && st == MFS_OK; ++l) {
+    LevelData L;
+    L.l = l;
+    L.n = 1 << l;
+    L.nb2 = make_numbering(2 * L.n);
+    L.nb1 = make_numbering(L.n);
+    L.n_tets = 60LL << (3 * l);
+    L.n_surface = L.n_cmb = 10LL * (1LL << (2 * (l + 1))) + 2;
+    HostTiles H = build_tiles(L.n);
+    L.n_tiles = (int)H.tiles.size();
+    st = upload(&L.d_tiles, H.tiles.data(), H.tiles.size(), s);
+    if (st == MFS_OK) st = upload(&L.d_tets, H.tets.data(), H.tets.size(), s);
+    if (st == MFS_OK) st = upload(&L.d_classes, H.classes.data(), H.classes.size(), s);
+    if (st == MFS_OK) MFS_CUDA(cudaStreamSynchronize(s));   // host vectors die here
+    M->levels.push_back(L);
+  }
+  if (st != MFS_OK) {
+    mfs_mesh_destroy(M);
+    return st;
+  }
+  *out = M;
+  return MFS_OK;
+}
+
+mfs_status mfs_mesh_destroy(mfs_mesh* M) {
+  if (!M) return MFS_OK;
+  cudaFree(M->d_topo);
+  cudaFree(M->d_geom64);
+  cudaFree(M->d_geom32);
+  for (auto& L : M->levels) {
+    cudaFree(L.d_tiles);
+    cudaFree(L.d_tets);
+    cudaFree(L.d_classes);
+  }
+  delete M;
+  return MFS_OK;
+}
+
+mfs_status mfs_mesh_info(const mfs_mesh* M, int lvl, mfs_level_info* out) {
+  MFS_TRY(check_level(M, lvl));
+  if (!out) {
+    set_error("null output");
+    return MFS_EINVAL;
+  }
+  out->level = lvl;
+  out->n_tets = 60LL << (3 * lvl);
+  out->n_p2 = make_numbering(2 << lvl).total;
+  out->n_p1 = make_numbering(1 << lvl).total;
+  out->n_surface = out->n_cmb = 10LL * (1LL << (2 * (lvl + 1))) + 2;
+  return MFS_OK;
+}
+
+// Visit every lattice point of every macro at N intervals: f(m, i[4], id).
+template <typename F>
+static void for_each_point(const mfs_mesh* M, int N, F f) {
+  const Numbering nb = make_numbering(N);
+  for (int m = 0; m < 60; ++m)
+    for (int i3 = 0; i3 <= N; ++i3)
+      for (int i2 = 0; i2 <= N - i3; ++i2)
+        for (int i1 = 0; i1 <= N - i3 - i2; ++i1) {
+          const int i[4] = {N - i1 - i2 - i3, i1, i2, i3};
+          f(m, i, lattice_id(M->host.topo[m], nb, m, i[0], i[1], i[2], i[3]));
+        }
+}
+
+mfs_status mfs_mesh_coords(const mfs_mesh* M, int lvl, int p2, int blended, double* xyz) {
+  MFS_TRY(check_level(M, lvl));
+  if (!xyz) {
+    set_error("null output buffer");
+    return MFS_EINVAL;
+  }
+  const int N = p2 ? (2 << lvl) : (1 << lvl);
+  const int64_t n = make_numbering(N).total;
+  for_each_point(M, N, [&](int m, const int* i, int id) {
+    double xs[3], x[3];
+    M->host.straight_point(m, i, N, xs);
+    if (blended) M->host.blend_point(m, xs, x);
+    else for (int r = 0; r < 3; ++r) x[r] = xs[r];
+    for (int r = 0; r < 3; ++r) xyz[r * n + id] = x[r];
+  });
+  return MFS_OK;
+}
+
+mfs_status mfs_mesh_node_class(const mfs_mesh* M, int lvl, int p2, int8_t* cls) {
+  MFS_TRY(check_level(M, lvl));
+  if (!cls) {
+    set_error("null output buffer");
+    return MFS_EINVAL;
+  }
+  const int N = p2 ? (2 << lvl) : (1 << lvl);
+  for_each_point(M, N, [&](int m, const int* i, int id) {
+    const int mask = (i[0] > 0) | ((i[1] > 0) << 1) | ((i[2] > 0) << 2) | ((i[3] > 0) << 3);
+    const MacroTopo& t = M->host.topo[m];
+    int c = 0;
+    if ((mask & ~t.topmask & 15) == 0) c = 1;
+    else if ((mask & ~t.botmask & 15) == 0) c = 2;
+    cls[id] = (int8_t)c;
+  });
+  return MFS_OK;
+}
+
+mfs_status mfs_problem_create(mfs_mesh* M, mfs_bc bc_surface, mfs_bc bc_cmb, mfs_problem** out) {
+  if (!M || !out) {
+    set_error("null mesh or output handle");
+    return MFS_EINVAL;
+  }
+  if ((bc_surface != MFS_BC_DIRICHLET && bc_surface != MFS_BC_FREESLIP) ||
+      (bc_cmb != MFS_BC_DIRICHLET && bc_cmb != MFS_BC_FREESLIP)) {
+    set_error("invalid boundary condition type");
+    return MFS_EINVAL;
+  }
+  if (!M->ctx) {
+    set_error("mesh was created without a context (host-only)");
+    return MFS_EINVAL;
+  }
+  MFS_CUDA(cudaSetDevice(M->ctx->device));
+  mfs_problem* P = new (std::nothrow) mfs_problem;
+  if (!P) {
+    set_error("host allocation failed");
+    return MFS_ENOMEM;
+  }
+  P->mesh = M;
+  P->bc_surface = bc_surface;
+  P->bc_cmb = bc_cmb;
+  cudaStream_t s = M->ctx->stream;
+  const double zero64 = 0.0;
+  const float zero32 = 0.0f;
+  mfs_status st = upload(&P->d_dlnrho64, &zero64, 1, s);
+  if (st == MFS_OK) st = upload(&P->d_dlnrho32, &zero32, 1, s);
+  if (st == MFS_OK) {
+    cudaError_t e = cudaMalloc((void**)&P->d_red64, sizeof(double) * kRedSlots);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&P->d_red32, sizeof(float) * kRedSlots);
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaMalloc(reduction workspace)");
+  }
+  for (int l = 0; l <= M->l_max && st == MFS_OK; ++l) {
+    double* e64 = nullptr;
+    float* e32 = nullptr;
+    const size_t np1 = M->levels[l].nb1.total;
+    cudaError_t e = cudaMalloc((void**)&e64, sizeof(double) * np1);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&e32, sizeof(float) * np1);
+    P->eta64.push_back(e64);
+    P->eta32.push_back(e32);
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaMalloc(eta)");
+  }
+  if (st == MFS_OK) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize");
+  }
+  if (st != MFS_OK) {
+    mfs_problem_destroy(P);
+    return st;
+  }
+  P->n_dlnrho = 1;
+  *out = P;
+  return MFS_OK;
+}
+
+mfs_status mfs_problem_destroy(mfs_problem* P) {
+  if (!P) return MFS_OK;
+  for (auto p : P->eta64) cudaFree(p);
+  for (auto p : P->eta32) cudaFree(p);
+  cudaFree(P->d_dlnrho64);
+  cudaFree(P->d_dlnrho32);
+  cudaFree(P->d_red64);
+  cudaFree(P->d_red32);
+  delete P;
+  return MFS_OK;
+}
+
+mfs_status mfs_set_viscosity(mfs_problem* P, const double* eta, int is_log) {
+  MFS_TRY(check_problem(P, 0, false));
+  if (!eta) {
+    set_error("null viscosity pointer");
+    return MFS_EINVAL;
+  }
+  mfs_mesh* M = P->mesh;
+  cudaStream_t s = M->ctx->stream;
+  const int L = M->l_max;
+  const size_t np1 = M->levels[L].nb1.total;
+  MFS_CUDA(cudaMemcpyAsync(P->eta64[L], eta, sizeof(double) * np1, cudaMemcpyDeviceToDevice, s));
+  if (is_log) MFS_TRY(exp_inplace(P->eta64[L], (int64_t)np1, s));
+  for (int l = L - 1; l >= 0; --l) MFS_TRY(inject_p1(M, L, l, P->eta64[L], P->eta64[l]));
+  for (int l = 0; l <= L; ++l)
+    MFS_TRY(convert_f64_f32(P->eta64[l], P->eta32[l], M->levels[l].nb1.total, s));
+  P->has_eta = true;
+  return MFS_OK;
+}
+
+mfs_status mfs_set_density(mfs_problem* P, int n, const double* tab) {
+  MFS_TRY(check_problem(P, 0, false));
+  if (n < 1 || !tab) {
+    set_error("density table needs n >= 1 entries");
+    return MFS_EINVAL;
+  }
+  cudaStream_t s = P->mesh->ctx->stream;
+  MFS_CUDA(cudaStreamSynchronize(s));
+  cudaFree(P->d_dlnrho64);
+  cudaFree(P->d_dlnrho32);
+  P->d_dlnrho64 = nullptr;
+  P->d_dlnrho32 = nullptr;
+  std::vector<float> t32(tab, tab + n);
+  MFS_TRY(upload(&P->d_dlnrho64, tab, (size_t)n, s));
+  MFS_TRY(upload(&P->d_dlnrho32, t32.data(), (size_t)n, s));
+  MFS_CUDA(cudaStreamSynchronize(s));
+  P->n_dlnrho = n;
+  return MFS_OK;
+}
+
+template <typename T>
+static T* red_of(mfs_problem* P);
+template <>
+double* red_of<double>(mfs_problem* P) { return P->d_red64; }
+template <>
+float* red_of<float>(mfs_problem* P) { return P->d_red32; }
+
+template <typename T>
+static mfs_status apply_typed(mfs_problem* P, int lvl, int op, int constrained, int withc_b, const void* u,
+                              const void* p, void* yu, void* yp) {
+  mfs_mesh* M = P->mesh;
+  cudaStream_t s = M->ctx->stream;
+  const LevelData& L = M->levels[lvl];
+  T* red = red_of<T>(P);
+  const T* psum = nullptr;
+  if (constrained && (op & OP_BT)) {   // P_p on the pressure input: the kernel subtracts sum/n
+    MFS_TRY(vec_sum<T>((const T*)p, L.nb1.total, red, red + kRedBlocks, s));
+    psum = red + kRedBlocks;
+  }
+  MFS_TRY(launch_apply<T>(P, lvl, op, constrained, withc_b, (const T*)u, (const T*)p, (T*)yu, (T*)yp, psum));
+  if (constrained && (op & OP_B)) {
+    MFS_TRY(vec_sum<T>((const T*)yp, L.nb1.total, red, red + kRedBlocks + 2, s));
+    MFS_TRY(vec_sub_mean<T>((T*)yp, L.nb1.total, red + kRedBlocks + 2, s));
+  }
+  return MFS_OK;
+}
+
+static mfs_status check_vecs(const void* a, const void* b) {
+  if (!a || !b) {
+    set_error("null vector pointer");
+    return MFS_EINVAL;
+  }
+  return MFS_OK;
+}
+
+static mfs_status dispatch(mfs_problem* P, int lvl, mfs_prec prec, int op, int constrained, int withc_b,
+                           const void* u, const void* p, void* yu, void* yp) {
+  MFS_TRY(check_problem(P, lvl, true));
+  if (prec != MFS_F64 && prec != MFS_F32) {
+    set_error("invalid precision %d", (int)prec);
+    return MFS_EINVAL;
+  }
+  if (prec == MFS_F64) return apply_typed<double>(P, lvl, op, constrained, withc_b, u, p, yu, yp);
+  return apply_typed<float>(P, lvl, op, constrained, withc_b, u, p, yu, yp);
+}
+
+mfs_status mfs_apply_A(mfs_problem* P, int lvl, mfs_prec prec, mfs_bcmode mode, const void* u, void* y) {
+  MFS_TRY(check_vecs(u, y));
+  return dispatch(P, lvl, prec, OP_A, mode == MFS_CONSTRAINED, 0, u, nullptr, y, nullptr);
+}
+
+mfs_status mfs_apply_B(mfs_problem* P, int lvl, mfs_prec prec, mfs_bcmode mode, int with_C, const void* u,
+                       void* q) {
+  MFS_TRY(check_vecs(u, q));
+  return dispatch(P, lvl, prec, OP_B, mode == MFS_CONSTRAINED, with_C ? 1 : 0, u, nullptr, nullptr, q);
+}
+
+mfs_status mfs_apply_BT(mfs_problem* P, int lvl, mfs_prec prec, mfs_bcmode mode, int with_C, const void* p,
+                        void* y) {
+  MFS_TRY(check_vecs(p, y));
+  const int op = with_C ? (OP_BT | OP_CT) : OP_BT;
+  return dispatch(P, lvl, prec, op, mode == MFS_CONSTRAINED, 0, nullptr, p, y, nullptr);
+}
+
+mfs_status mfs_apply_stokes(mfs_problem* P, int lvl, mfs_prec prec, int transpose, const void* u, const void* p,
+                            void* yu, void* yp) {
+  MFS_TRY(check_vecs(u, p));
+  MFS_TRY(check_vecs(yu, yp));
+  if (transpose) return dispatch(P, lvl, prec, OP_A | OP_BT | OP_CT | OP_B, 1, 0, u, p, yu, yp);
+  return dispatch(P, lvl, prec, OP_A | OP_BT | OP_B, 1, 1, u, p, yu, yp);
+}
+

@@ -1,0 +1,130 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/mfs.h"
+#include "mfs_internal.h"
+
+namespace mfs {
+
+// ---- error handling ----
+void set_error(const char* fmt, ...);
+mfs_status cuda_fail(cudaError_t e, const char* what);
+#define MFS_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e__ = (call);                            \
+    if (e__ != cudaSuccess) return cuda_fail(e__, #call); \
+  } while (0)
+#define MFS_TRY(call)                   \
+  do {                                  \
+    mfs_status s__ = (call);            \
+    if (s__ != MFS_OK) return s__;      \
+  } while (0)
+
+// ---- host macro mesh (Sec. 4.1: icosahedral shell, one radial layer) ----
+struct HostMacroMesh {
+  double r_cmb = 0.5, r_surf = 1.0;
+  int blending = 1;
+  double unit[24][3];
+  double verts[24][3];
+  int layer[24];
+  int cells[60][4];       // increasing global vertex ids
+  int cell_prism[60];
+  int edges[102][2];
+  int faces[140][3];
+  double prism_nh[20][3];
+  double prism_delta[20];
+  MacroTopo topo[60];
+  MacroGeom<double> geom[60];
+  void build(double r_cmb, double r_surf, int blending);
+  // position of a lattice point of macro m with integer barycentrics i (sum N)
+  void straight_point(int m, const int i[4], int N, double x[3]) const;
+  void blend_point(int m, const double xs[3], double x[3]) const;
+};
+
+// Tiles and per-class local tet lists of one level.
+struct HostTiles {
+  std::vector<Tile> tiles;
+  std::vector<uint16_t> tets;
+  std::vector<int2> classes;
+};
+HostTiles build_tiles(int n);
+
+struct LevelData {
+  int l = 0, n = 1;
+  Numbering nb2{}, nb1{};
+  int n_tiles = 0;
+  Tile* d_tiles = nullptr;
+  uint16_t* d_tets = nullptr;
+  int2* d_classes = nullptr;
+  int64_t n_tets = 0, n_surface = 0, n_cmb = 0;
+};
+
+template <typename T>
+MacroGeom<T> cast_geom(const MacroGeom<double>& g);
+
+}  // namespace mfs
+
+struct mfs_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  // optional CUDA-event timing of the element-sweep kernels
+  int timing = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used;
+};
+
+namespace mfs {
+// events bracketing one sweep launch when ctx->timing is on (nullptr otherwise)
+std::pair<cudaEvent_t, cudaEvent_t> timing_events(mfs_ctx* ctx);
+}
+
+struct mfs_mesh {
+  mfs_ctx* ctx = nullptr;
+  int l_max = 0;
+  mfs::HostMacroMesh host;
+  mfs::MacroTopo* d_topo = nullptr;
+  mfs::MacroGeom<double>* d_geom64 = nullptr;
+  mfs::MacroGeom<float>* d_geom32 = nullptr;
+  std::vector<mfs::LevelData> levels;
+};
+
+struct mfs_problem {
+  mfs_mesh* mesh = nullptr;
+  int bc_surface = 0, bc_cmb = 1;
+  bool has_eta = false;
+  std::vector<double*> eta64;   // per level, [n_p1(l)]
+  std::vector<float*> eta32;
+  double* d_dlnrho64 = nullptr;
+  float* d_dlnrho32 = nullptr;
+  int n_dlnrho = 1;
+  // reduction workspace: partial sums and a few device scalars
+  double* d_red64 = nullptr;    // [kRedSlots]
+  float* d_red32 = nullptr;
+};
+
+namespace mfs {
+
+constexpr int kRedBlocks = 512;     // partial sums of the two-pass reductions
+constexpr int kRedSlots = kRedBlocks + 64;
+
+// ---- launchers (apply.cu) ----
+template <typename T>
+mfs_status launch_apply(mfs_problem* P, int lvl, int op, int constrained, int withc_b, const T* u,
+                        const T* p, T* yu, T* yp, const T* psum);
+
+// ---- vector kernels (vec.cu) ----
+template <typename T>
+mfs_status vec_sum(const T* x, int64_t n, T* d_partials, T* d_out, cudaStream_t s);
+template <typename T>
+mfs_status vec_sub_mean(T* x, int64_t n, const T* d_sum, cudaStream_t s);
+mfs_status inject_p1(const mfs_mesh* M, int l_from, int l_to, const double* src, double* dst);
+mfs_status convert_f64_f32(const double* src, float* dst, int64_t n, cudaStream_t s);
+mfs_status exp_inplace(double* x, int64_t n, cudaStream_t s);
+
+}  // namespace mfs

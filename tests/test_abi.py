@@ -1,0 +1,68 @@
+"""C-ABI library: loads, exports every declared symbol, and its host-side mesh (numbering,
+coordinates, node classes) agrees with the independently written oracle (no GPU)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2506_04157_gb300 as mfs
+from oracle.mesh import MacroMesh, Level
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    syms = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            syms |= set(re.findall(r"\b(mfs_[A-Za-z0-9_]+)\s*\(", src))
+    return syms
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(mfs.LIB_PATH):
+        import paper_2506_04157_gb300.build as b
+        b.build()
+    return mfs.lib()
+
+
+def test_exports_every_declared_symbol(lib):
+    syms = declared_symbols()
+    assert len(syms) >= 18
+    for s in sorted(syms):
+        assert hasattr(lib, s), s
+    assert set(mfs._SIGS) <= syms | {"mfs_last_error", "mfs_version"}
+
+
+def test_errors_without_gpu_or_bad_args(lib):
+    with pytest.raises(mfs.MfsError):
+        mfs.Mesh(None, 8)
+    with pytest.raises(mfs.MfsError):
+        mfs.Mesh(None, 2, r_cmb=1.0, r_surf=0.5)
+    m = mfs.Mesh(None, 2)
+    with pytest.raises(mfs.MfsError) as e:
+        mfs.Problem(m)
+    assert "host-only" in str(e.value)
+
+
+@pytest.mark.parametrize("blending", [True, False])
+@pytest.mark.parametrize("l", [0, 1, 2, 3])
+def test_numbering_coords_classes_match_oracle(lib, l, blending):
+    M = mfs.Mesh(None, l, blending=blending)
+    L = Level(MacroMesh(blending=blending), l)
+    inf = M.info(l)
+    assert (inf.n_p2, inf.n_p1, inf.n_tets) == (L.n_p2, L.n_p1, L.tet_p2.shape[0])
+    for p2 in (True, False):
+        xs = M.coords(l, p2=p2, blended=False).T
+        xb = M.coords(l, p2=p2, blended=True).T
+        ref_s = L.p2_straight if p2 else L.p1_straight
+        ref_b = L.p2_x if p2 else L.p1_x
+        assert np.abs(xs - ref_s).max() < 1e-14
+        assert np.abs(xb - ref_b).max() < 1e-14
+        cls = M.node_class(l, p2=p2)
+        ref_c = L.p2_class if p2 else L.p1_class
+        assert np.array_equal(cls, ref_c)
