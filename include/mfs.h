@@ -159,6 +159,25 @@ mfs_status mfs_apply_BT(mfs_problem* prob, int lvl, mfs_prec prec, mfs_bcmode mo
 mfs_status mfs_apply_stokes(mfs_problem* prob, int lvl, mfs_prec prec, int transpose, const void* u,
                             const void* p, void* yu, void* yp);
 
+/* Allocation-free variant of mfs_apply_B (no counterpart in the paper).
+ *
+ * For callers that cannot call cudaMalloc while they apply the operator: for example code
+ * running under an external memory manager that owns every device allocation, or a
+ * real-time loop in which a device allocation would synchronise the device.  Same
+ * arguments, result and errors as mfs_apply_B; the caller passes u and q as before.  In
+ * MFS_CONSTRAINED mode the mean removal (P_p) sums q in a fixed, library-owned static
+ * device array of 8,448 bytes (1,024 partial sums) instead of the problem's workspace, so
+ * the call allocates nothing (no cudaMalloc/cudaFree, no allocating library routine).
+ * Limit: levels with at most 4,194,304 pressure entries (levels 0-6); larger levels return
+ * MFS_EINVAL with a message giving the limit.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream capture.  Every GPU
+ * that loads the library holds the array until the process exits; all calls share it and
+ * it keeps the last call's contents, so calls that overlap on the GPU (for example on two
+ * streams) race and must be serialised by the caller. */
+mfs_status mfs_apply_B_noalloc(mfs_problem* prob, int lvl, mfs_prec prec, mfs_bcmode mode, int with_C,
+                               const void* u, void* q);
+
 #ifdef __cplusplus
 }
 #endif

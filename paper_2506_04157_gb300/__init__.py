@@ -58,6 +58,7 @@ _SIGS = {
     "mfs_apply_B": ([_vp, _i, _i, _i, _i, _vp, _vp], _i),
     "mfs_apply_BT": ([_vp, _i, _i, _i, _i, _vp, _vp], _i),
     "mfs_apply_stokes": ([_vp, _i, _i, _i, _vp, _vp, _vp, _vp], _i),
+    "mfs_apply_B_noalloc": ([_vp, _i, _i, _i, _i, _vp, _vp], _i),
 }
 
 _lib = None
@@ -199,6 +200,14 @@ class Problem:
         _need(u, nu, None, "u"); _need(q, npp, u.dtype, "q")
         _check(lib().mfs_apply_B(self.handle, level, _prec_of(u), int(constrained), int(with_C),
                                  _ptr(u), _ptr(q)))
+
+    def apply_B_noalloc(self, level, u, q, with_C=True, constrained=False):
+        """mfs_apply_B without device allocation: the mean-removal scratch lives in a
+        fixed static device array (for callers that cannot call cudaMalloc)."""
+        nu, npp = self._sizes(level)
+        _need(u, nu, None, "u"); _need(q, npp, u.dtype, "q")
+        _check(lib().mfs_apply_B_noalloc(self.handle, level, _prec_of(u), int(constrained), int(with_C),
+                                         _ptr(u), _ptr(q)))
 
     def apply_BT(self, level, p, y, with_C=False, constrained=False):
         nu, npp = self._sizes(level)
