@@ -11,7 +11,7 @@ from concurrent.futures import ThreadPoolExecutor
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "lib")
-SOURCES = ["capi.cpp", "mesh_host.cpp", "apply.cu", "vec.cu", "noalloc.cu"]
+SOURCES = ["capi.cpp", "mesh_host.cpp", "apply_f32.cu", "apply_f64.cu", "tables.cu", "vec.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(HERE, "..", "include")]
@@ -24,9 +24,9 @@ def nvcc():
     raise RuntimeError("nvcc not found")
 
 
-def _compile(src, objdir, verbose):
+def _compile(src, objdir, verbose, defines=()):
     obj = os.path.join(objdir, os.path.basename(src) + ".o")
-    cmd = [nvcc(), *ARCH, *FLAGS]
+    cmd = [nvcc(), *ARCH, *FLAGS, *[f"-D{d}" for d in defines]]
     if src.endswith(".cpp"):
         cmd += ["-x", "cu"]
     cmd += ["-c", os.path.join(CSRC, src), "-o", obj]
@@ -38,16 +38,18 @@ def _compile(src, objdir, verbose):
     return obj, r.stderr
 
 
-def build(verbose=False):
-    """Compile every translation unit and link lib/libmfs.so; returns its path."""
-    objdir = os.path.join(OUT, "obj")
+def build(verbose=False, out_dir=OUT, defines=()):
+    """Compile every translation unit and link <out_dir>/libmfs.so; returns its path.
+    `defines` are extra preprocessor definitions (tuning knobs such as
+    MFS_SWEEP_MINBLOCKS)."""
+    objdir = os.path.join(out_dir, "obj")
     os.makedirs(objdir, exist_ok=True)
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        res = list(ex.map(lambda s: _compile(s, objdir, verbose), SOURCES))
+        res = list(ex.map(lambda s: _compile(s, objdir, verbose, defines), SOURCES))
     if verbose:
         for _, log in res:
             sys.stderr.write(log)
-    so = os.path.join(OUT, "libmfs.so")
+    so = os.path.join(out_dir, "libmfs.so")
     tmp = so + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *[o for o, _ in res]]
     r = subprocess.run(cmd, capture_output=True, text=True)

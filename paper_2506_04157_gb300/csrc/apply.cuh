@@ -5,10 +5,15 @@
 // Work decomposition: one CTA per tile of TT^3 lattice cubes of one macro-tet
 // (Freudenthal cubes (a,b,c) with n > a >= b >= c >= 0).  The CTA stages the tile's
 // (2TT+1)^3 block of P2 nodes and (TT+1)^3 block of P1 vertices in shared memory
-// (coalesced along the macro lattice rows), one thread per micro-tet computes the
-// element contribution at the 4 quadrature points with the blending Jacobian evaluated
-// at each of them, accumulates into shared memory, and the block is added to the global
-// result with one atomic add per node and component.
+// (global ids from a per-tile table built once per level), one thread per micro-tet
+// computes the element contribution at the 4 quadrature points with the blending
+// Jacobian evaluated at each of them, accumulates into shared memory, and the block is
+// added to the global result with one atomic add per node and component.
+//
+// Shared-memory layout: nodes are split into the 8 parity classes of their local fine
+// coordinates (A&1, B&1, C&1), each a 5x5x5 sub-block.  The threads of a warp process
+// the same Freudenthal type in different cubes, so "node k of my tet" lies in one parity
+// class at sub-index i + 5j + 25k + const: at most 2-way bank conflicts.
 //
 // Per-quadrature-point algebra (all derived from Sec. 4.1's pulled-back integrals):
 //  * straight position x~ = v0 + Jm xi / n, xi the lattice coordinate of the point;
@@ -26,6 +31,11 @@
 
 namespace mfs {
 
+#ifndef MFS_SWEEP_MINBLOCKS
+#define MFS_SWEEP_MINBLOCKS 4   // resident CTAs per SM the register allocation targets
+#endif
+constexpr int kSweepThreads = 192;
+constexpr int kSub = 125;   // 5x5x5 parity sub-block
 
 template <typename T>
 struct ApplyParams {
@@ -37,17 +47,16 @@ struct ApplyParams {
   const T* dlnrho;   // radial table of d ln rho / dr (n_dlnrho entries)
   const T* psum;     // device scalar: sum of p; p - psum/n_p1 is used (P_p), or nullptr
   const MacroGeom<T>* geom;
-  const MacroTopo* topo;
   const Tile* tiles;
   const uint16_t* tets;   // packed local tets (perm<<12 | k<<8 | j<<4 | i)
   const int2* classes;    // (offset, count) into tets per tile class
-  Numbering nb2, nb1;
+  const int* ids2;        // [60*tiles][NSLOT2]: global P2 id | geometric class << 29, or -1
+  const int* ids1;        // [60*tiles][NSLOT1]: global P1 id, or -1
+  int n_p2, n_p1;
   int n;                  // cubes per macro edge
   int n_dlnrho;
-  T r_cmb, r_surf;
-  int blending;
+  T r_cmb, inv_dr;        // table grid: s = (r - r_cmb) * inv_dr * (n_dlnrho - 1)
   int constrained;
-  int withc_b;            // OP_B computes (B + C) u
   int bc_surface, bc_cmb;
 };
 
@@ -55,12 +64,12 @@ struct ApplyParams {
 #define MFS_QA 0.58541019662496845446
 #define MFS_QB 0.13819660112501051518
 
-__device__ __forceinline__ constexpr int edge_of(int a, int b) {
+__host__ __device__ __forceinline__ constexpr int edge_of(int a, int b) {
   return (a < b ? a : b) == 0 ? (a > b ? a : b) - 1
                               : ((a < b ? a : b) == 1 ? (a > b ? a : b) + 1 : 5);
 }
 // node (0..9) carrying u_{a,q}: the vertex a itself if a == q, else the edge (a,q)
-__device__ __forceinline__ constexpr int wnode(int a, int q) { return a == q ? a : 4 + edge_of(a, q); }
+__host__ __device__ __forceinline__ constexpr int wnode(int a, int q) { return a == q ? a : 4 + edge_of(a, q); }
 
 template <typename T>
 __device__ __forceinline__ T rsqrt_t(T x);
@@ -68,42 +77,88 @@ template <>
 __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
 template <>
 __device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
-
 template <typename T>
-__device__ __forceinline__ T interp_table(const T* tab, int nt, T r, T r0, T r1) {
-  if (nt <= 1) return tab[0];
-  T s = (r - r0) / (r1 - r0) * T(nt - 1);
-  s = s < T(0) ? T(0) : (s > T(nt - 1) ? T(nt - 1) : s);
-  int i = (int)s;
-  i = i > nt - 2 ? nt - 2 : i;
-  const T f = s - T(i);
-  return (T(1) - f) * tab[i] + f * tab[i + 1];
+__device__ __forceinline__ T rcp_t(T x);
+template <>
+__device__ __forceinline__ float rcp_t<float>(float x) { return __frcp_rn(x); }
+template <>
+__device__ __forceinline__ double rcp_t<double>(double x) { return 1.0 / x; }
+
+// offset inside a 5x5x5 parity sub-block of a 3-bit corner mask (x = bit 0)
+__host__ __device__ __forceinline__ constexpr int sub_off(int m) {
+  return (m & 1) + 5 * ((m >> 1) & 1) + 25 * ((m >> 2) & 1);
 }
 
+// local fine coordinates (0..2TT) of a P2 slot; returns false for padding slots
+__host__ __device__ __forceinline__ bool slot_coords(int s, int& dA, int& dB, int& dC) {
+  const int cls = s / kSub, sub = s - cls * kSub;
+  dA = 2 * (sub % 5) + (cls & 1);
+  dB = 2 * ((sub / 5) % 5) + ((cls >> 1) & 1);
+  dC = 2 * (sub / 25) + (cls >> 2);
+  return dA <= 2 * TT && dB <= 2 * TT && dC <= 2 * TT;
+}
+
+template <typename T>
+__device__ __forceinline__ T dlnrho_at(const ApplyParams<T>& P, T r) {
+  if (P.n_dlnrho <= 1) return P.dlnrho[0];
+  const T top = T(P.n_dlnrho - 1);
+  T s = (r - P.r_cmb) * P.inv_dr * top;
+  s = s < T(0) ? T(0) : (s > top ? top : s);
+  int i = (int)s;
+  i = i > P.n_dlnrho - 2 ? P.n_dlnrho - 2 : i;
+  const T f = s - T(i);
+  return (T(1) - f) * P.dlnrho[i] + f * P.dlnrho[i + 1];
+}
+
+// outward radial unit vector at a lattice point (Kuhn coordinates A,B,C of N)
+template <typename T>
+__device__ __forceinline__ void lattice_normal(const MacroGeom<T>& G, int A, int B, int C, int N, T nrm[3]) {
+  const T inv = T(1) / T(N);
+  const T xa = T(A) * inv, xb = T(B) * inv, xc = T(C) * inv;
+  T x[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) x[r] = G.v0[r] + G.Jm[3 * r] * xa + G.Jm[3 * r + 1] * xb + G.Jm[3 * r + 2] * xc;
+  const T ri = rsqrt_t<T>(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  nrm[0] = x[0] * ri;
+  nrm[1] = x[1] * ri;
+  nrm[2] = x[2] * ri;
+}
+
+// bytes of dynamic shared memory of one sweep CTA
 template <typename T, int OP>
-__global__ void __launch_bounds__(256) stokes_tile_kernel(const ApplyParams<T> P) {
+constexpr size_t sweep_smem_bytes() {
+  return sizeof(T) * ((((OP & (OP_A | OP_B)) != 0) ? 3 * NSLOT2 : 0) + (((OP & (OP_A | OP_BT)) != 0) ? 3 * NSLOT2 : 0) +
+                      NSLOT1 + (((OP & OP_BT) != 0) ? NSLOT1 : 0) + (((OP & OP_B) != 0) ? NSLOT1 : 0)) +
+         sizeof(int) * (NSLOT2 + NSLOT1);
+}
+
+template <typename T, int OP, bool BLEND>
+__global__ void __launch_bounds__(kSweepThreads, MFS_SWEEP_MINBLOCKS) stokes_tile_kernel(const ApplyParams<T> P) {
   constexpr bool HAS_U = (OP & (OP_A | OP_B)) != 0;
   constexpr bool HAS_P = (OP & OP_BT) != 0;
   constexpr bool OUT_U = (OP & (OP_A | OP_BT)) != 0;
   constexpr bool OUT_P = (OP & OP_B) != 0;
   constexpr bool HAS_CT = (OP & OP_CT) != 0;
+  constexpr bool HAS_BC = (OP & OP_BC) != 0;
 
-  __shared__ T us[HAS_U ? 3 * NSLOT2 : 1];
-  __shared__ T ys[OUT_U ? 3 * NSLOT2 : 1];
-  __shared__ int gid2[NSLOT2];
-  __shared__ int8_t cls2[NSLOT2];
-  __shared__ T eta_s[NSLOT1];
-  __shared__ T p_s[HAS_P ? NSLOT1 : 1];
-  __shared__ T yp_s[OUT_P ? NSLOT1 : 1];
-  __shared__ int gid1[NSLOT1];
+  // dynamic shared memory, layout of sweep_smem_bytes(): us, ys, eta_s, p_s, yp_s, gid2, gid1
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* us = reinterpret_cast<T*>(smem_raw);
+  T* ys = us + (HAS_U ? 3 * NSLOT2 : 0);
+  T* eta_s = ys + (OUT_U ? 3 * NSLOT2 : 0);
+  T* p_s = eta_s + NSLOT1;
+  T* yp_s = p_s + (HAS_P ? NSLOT1 : 0);
+  int* gid2 = reinterpret_cast<int*>(yp_s + (OUT_P ? NSLOT1 : 0));
+  int* gid1 = gid2 + NSLOT2;
   __shared__ T cM[9], cJn[9], cv0[3], cnh[3];
 
   const int m = blockIdx.y;
-  const Tile tile = P.tiles[blockIdx.x];
-  const MacroTopo topo = P.topo[m];
+  const int tidx = blockIdx.x;
+  const size_t tile_lin = (size_t)m * gridDim.x + tidx;
+  const Tile tile = P.tiles[tidx];
   const MacroGeom<T>& G = P.geom[m];
   const int a0 = tile.ta * TT, b0 = tile.tb * TT, c0 = tile.tc * TT;
-  const int N = P.nb2.N, n = P.n;
+  const int n = P.n, N = 2 * n;
   const int tid = threadIdx.x;
 
   if (tid < 9) {
@@ -116,40 +171,49 @@ __global__ void __launch_bounds__(256) stokes_tile_kernel(const ApplyParams<T> P
   }
 
   // ---- stage the P2 node block (u, with the input-side projections) ----
-  for (int s = tid; s < NSLOT2; s += blockDim.x) {
-    const int dA = s % NB2, dB = (s / NB2) % NB2, dC = s / (NB2 * NB2);
-    const int A = 2 * a0 + dA, B = 2 * b0 + dB, C = 2 * c0 + dC;
-    int id = -1, cl = NODE_FREE;
-    T v0 = 0, v1 = 0, v2 = 0;
-    if (A <= N && A >= B && B >= C) {
-      const int i0 = N - A, i1 = A - B, i2 = B - C, i3 = C;
-      id = lattice_id(topo, P.nb2, m, i0, i1, i2, i3);
-      const int mask = (i0 > 0) | ((i1 > 0) << 1) | ((i2 > 0) << 2) | ((i3 > 0) << 3);
-      if (P.constrained) cl = node_class(topo, mask, P.bc_surface, P.bc_cmb);
-      if (HAS_U) {
-        const int nn = P.nb2.total;
-        v0 = P.u[id];
-        v1 = P.u[nn + id];
-        v2 = P.u[2 * nn + id];
-        if (cl == NODE_DIRICHLET) {
-          v0 = v1 = v2 = T(0);
-        } else if (cl == NODE_FREESLIP) {
-          const T xa = T(A) / T(N), xb = T(B) / T(N), xc = T(C) / T(N);
-          T x[3];
+  // All table entries of this thread first, then all node values: independent loads in flight.
+  constexpr int kG = (NSLOT2 + kSweepThreads - 1) / kSweepThreads;
+  const int* tab2 = P.ids2 + tile_lin * NSLOT2;
+  int codes[kG];
 #pragma unroll
-          for (int r = 0; r < 3; ++r)
-            x[r] = G.v0[r] + G.Jm[3 * r] * xa + G.Jm[3 * r + 1] * xb + G.Jm[3 * r + 2] * xc;
-          const T ri = rsqrt_t<T>(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
-          const T nx = x[0] * ri, ny = x[1] * ri, nz = x[2] * ri;
-          const T un = v0 * nx + v1 * ny + v2 * nz;
-          v0 -= un * nx;
-          v1 -= un * ny;
-          v2 -= un * nz;
-        }
+  for (int k = 0; k < kG; ++k) {
+    const int s = tid + k * kSweepThreads;
+    codes[k] = s < NSLOT2 ? __ldg(tab2 + s) : -1;
+  }
+  T uv[kG][3];
+#pragma unroll
+  for (int k = 0; k < kG; ++k) {
+    uv[k][0] = uv[k][1] = uv[k][2] = T(0);
+    if (HAS_U && codes[k] >= 0) {
+      const int id = codes[k] & 0x1fffffff;
+      uv[k][0] = __ldg(P.u + id);
+      uv[k][1] = __ldg(P.u + P.n_p2 + id);
+      uv[k][2] = __ldg(P.u + 2 * P.n_p2 + id);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kG; ++k) {
+    const int s = tid + k * kSweepThreads;
+    if (s >= NSLOT2) break;
+    const int code = codes[k];
+    gid2[s] = code;
+    T v0 = uv[k][0], v1 = uv[k][1], v2 = uv[k][2];
+    if (HAS_U && code >= 0 && P.constrained && (code >> 29) != 0) {
+      const int gc = code >> 29;     // 1 surface, 2 CMB
+      const int bc = gc == 1 ? P.bc_surface : P.bc_cmb;
+      if (bc == BC_DIRICHLET) {
+        v0 = v1 = v2 = T(0);
+      } else {
+        int dA, dB, dC;
+        slot_coords(s, dA, dB, dC);
+        T nr[3];
+        lattice_normal<T>(G, 2 * a0 + dA, 2 * b0 + dB, 2 * c0 + dC, N, nr);
+        const T un = v0 * nr[0] + v1 * nr[1] + v2 * nr[2];
+        v0 -= un * nr[0];
+        v1 -= un * nr[1];
+        v2 -= un * nr[2];
       }
     }
-    gid2[s] = id;
-    cls2[s] = (int8_t)cl;
     if (HAS_U) {
       us[s] = v0;
       us[NSLOT2 + s] = v1;
@@ -162,21 +226,21 @@ __global__ void __launch_bounds__(256) stokes_tile_kernel(const ApplyParams<T> P
     }
   }
   // ---- stage the P1 vertex block (eta, p) ----
-  const T pm = (HAS_P && P.psum) ? *P.psum / T(P.nb1.total) : T(0);
-  for (int s = tid; s < NSLOT1; s += blockDim.x) {
-    const int da = s % NB1, db = (s / NB1) % NB1, dc = s / (NB1 * NB1);
-    const int a = a0 + da, b = b0 + db, c = c0 + dc;
-    int id = -1;
+  const int* tab1 = P.ids1 + tile_lin * NSLOT1;
+  const T pm = (HAS_P && P.psum) ? *P.psum / T(P.n_p1) : T(0);
+  for (int s = tid; s < NSLOT1; s += kSweepThreads) {
+    const int id = tab1[s];
     T e = T(1), pv = T(0);
-    if (a <= n && a >= b && b >= c) {
-      id = lattice_id(topo, P.nb1, m, n - a, a - b, b - c, c);
+    if (id >= 0) {
       e = P.eta[id];
       if (HAS_P) pv = P.p[id] - pm;
     }
-    gid1[s] = id;
     eta_s[s] = e;
     if (HAS_P) p_s[s] = pv;
-    if (OUT_P) yp_s[s] = T(0);
+    if (OUT_P) {
+      yp_s[s] = T(0);
+      gid1[s] = id;
+    }
   }
   __syncthreads();
 
@@ -185,81 +249,67 @@ __global__ void __launch_bounds__(256) stokes_tile_kernel(const ApplyParams<T> P
   const T dq = T(4) * (QA - QB);           // 4(alpha - beta)
   const T bq1 = T(4) * QB - T(1);          // 4 beta - 1
   const T b4 = T(4) * QB;                  // 4 beta
+  // P2 basis values at the qps: vertex beta(2beta-1) (alpha(2alpha-1) at its own qp),
+  // edge 4 beta^2 (4 alpha beta at the qps of its two vertices)
+  const T fvb = QB * (T(2) * QB - T(1)), fva = QA * (T(2) * QA - T(1));
+  const T feo = T(4) * QB * QB, fei = T(4) * QA * QB;
   const T C0 = G.absdet / (T(24) * T(n) * T(n) * T(n));
   const T dinv = T(1) / G.delta;
-  const T delta = G.delta;
   const int2 cinfo = P.classes[tile.cls];
 
-  for (int t = tid; t < cinfo.y; t += blockDim.x) {
+  for (int t = tid; t < cinfo.y; t += kSweepThreads) {
     const int code = P.tets[cinfo.x + t];
     const int ci = code & 15, cj = (code >> 4) & 15, ck = (code >> 8) & 15, pmu = code >> 12;
     const int p0 = (0x221100 >> (4 * pmu)) & 3;
     const int p1 = (0x102021 >> (4 * pmu)) & 3;
     const int p2 = (0x010212 >> (4 * pmu)) & 3;
-    // shared-memory slots of the 10 P2 nodes and 4 P1 vertices
-    const int w2p0 = p0 == 0 ? 1 : (p0 == 1 ? NB2 : NB2 * NB2);
-    const int w2p1 = p1 == 0 ? 1 : (p1 == 1 ? NB2 : NB2 * NB2);
-    const int w1p0 = p0 == 0 ? 1 : (p0 == 1 ? NB1 : NB1 * NB1);
-    const int w1p1 = p1 == 0 ? 1 : (p1 == 1 ? NB1 : NB1 * NB1);
-    int o2[4], o1[4];
-    o2[0] = 0;
-    o2[1] = w2p0;
-    o2[2] = w2p0 + w2p1;
-    o2[3] = 1 + NB2 + NB2 * NB2;
-    o1[0] = 0;
-    o1[1] = w1p0;
-    o1[2] = w1p0 + w1p1;
-    o1[3] = 1 + NB1 + NB1 * NB1;
-    const int base2 = (2 * ck * NB2 + 2 * cj) * NB2 + 2 * ci;
-    const int base1 = (ck * NB1 + cj) * NB1 + ci;
+    // corner masks of the Freudenthal path 0, e_p0, e_p0+e_p1, (1,1,1)
+    const int S1 = 1 << p0, S2 = S1 | (1 << p1);
+    const int base = ci + 5 * cj + 25 * ck;
     int slot[10];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) slot[a] = base2 + 2 * o2[a];
-    slot[4] = base2 + o2[0] + o2[1];
-    slot[5] = base2 + o2[0] + o2[2];
-    slot[6] = base2 + o2[0] + o2[3];
-    slot[7] = base2 + o2[1] + o2[2];
-    slot[8] = base2 + o2[1] + o2[3];
-    slot[9] = base2 + o2[2] + o2[3];
+    slot[0] = base;
+    slot[1] = base + sub_off(S1);
+    slot[2] = base + sub_off(S2);
+    slot[3] = base + sub_off(7);
+    slot[4] = S1 * kSub + base;                           // edge 01
+    slot[5] = S2 * kSub + base;                           // edge 02
+    slot[6] = 7 * kSub + base;                            // edge 03
+    slot[7] = (S1 ^ S2) * kSub + base + sub_off(S1);      // edge 12
+    slot[8] = (S1 ^ 7) * kSub + base + sub_off(S1);       // edge 13
+    slot[9] = (S2 ^ 7) * kSub + base + sub_off(S2);       // edge 23
 
     T eta_v[4], p_v[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-      eta_v[a] = eta_s[base1 + o1[a]];
-      if (HAS_P) p_v[a] = p_s[base1 + o1[a]];
+      eta_v[a] = eta_s[slot[a]];          // P1 block uses the same sub-block indexing
+      if (HAS_P) p_v[a] = p_s[slot[a]];
     }
     const T eta_sum = eta_v[0] + eta_v[1] + eta_v[2] + eta_v[3];
     T p_sum = T(0);
     if (HAS_P) p_sum = p_v[0] + p_v[1] + p_v[2] + p_v[3];
 
-    // nodal values and the qp-independent parts of the barycentric gradient
-    T uu[10][3];
-    T baseg[4][3];
+    // qp-independent parts: dbase_j = base_{j+1} - base_j, base_a = (4b-1) u_a + 4b sum_b u_ab,
+    // and U0 = fvb sum u_v + feo sum u_e for the P2 value at the qps
+    T dbase[3][3], U0[3];
     if (HAS_U) {
 #pragma unroll
-      for (int a = 0; a < 10; ++a)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) uu[a][c] = us[c * NSLOT2 + slot[a]];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          T sa = T(0);
-#pragma unroll
-          for (int b = 0; b < 4; ++b)
-            if (b != a) sa += uu[4 + edge_of(a, b)][c];
-          baseg[a][c] = bq1 * uu[a][c] + b4 * sa;
-        }
+      for (int c = 0; c < 3; ++c) {
+        const T* uc = us + c * NSLOT2;
+        const T u0 = uc[slot[0]], u1 = uc[slot[1]], u2 = uc[slot[2]], u3 = uc[slot[3]];
+        const T e01 = uc[slot[4]], e02 = uc[slot[5]], e03 = uc[slot[6]];
+        const T e12 = uc[slot[7]], e13 = uc[slot[8]], e23 = uc[slot[9]];
+        const T bs0 = bq1 * u0 + b4 * (e01 + e02 + e03);
+        const T bs1 = bq1 * u1 + b4 * (e01 + e12 + e13);
+        const T bs2 = bq1 * u2 + b4 * (e02 + e12 + e23);
+        const T bs3 = bq1 * u3 + b4 * (e03 + e13 + e23);
+        dbase[0][c] = bs1 - bs0;
+        dbase[1][c] = bs2 - bs1;
+        dbase[2][c] = bs3 - bs2;
+        if (HAS_BC) U0[c] = fvb * (u0 + u1 + u2 + u3) + feo * (e01 + e02 + e03 + e12 + e13 + e23);
+      }
     }
 
-    // lattice coordinates: cube corner and Freudenthal vertex offsets
     const T qx = T(a0 + ci), qy = T(b0 + cj), qz = T(c0 + ck);
-    // centroid offset beta*(3 e_p0 + 2 e_p1 + e_p2)
-    T cofs[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-      cofs[d] = QB * T(3 * (p0 == d) + 2 * (p1 == d) + (p2 == d));
-    // Mpi rows: rows p0,p1,p2 of M = n Jm^{-1}
     T Mp[3][3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -268,42 +318,38 @@ __global__ void __launch_bounds__(256) stokes_tile_kernel(const ApplyParams<T> P
       Mp[2][d] = cM[3 * p2 + d];
     }
 
-    // test-side accumulators
-    T Tacc[4][3], Vd[4][3], Eacc[6][3];
+    // Rsum = sum_q R^q: since grad lambda_a is constant on the tet, T_a = sum_q s_a^q = Rsum grad lambda_a
+    T Rsum[3][3], Eacc[6][3], Zsum[3];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int c = 0; c < 3; ++c)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) Tacc[a][c] = Vd[a][c] = T(0);
+      for (int j = 0; j < 3; ++j) Rsum[c][j] = T(0);
 #pragma unroll
     for (int e = 0; e < 6; ++e)
 #pragma unroll
       for (int c = 0; c < 3; ++c) Eacc[e][c] = T(0);
-    T bq[4];
-    T Zsum[3] = {T(0), T(0), T(0)};
-    T Zv[4][3];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) Zv[a][0] = Zv[a][1] = Zv[a][2] = T(0);
+    for (int c = 0; c < 3; ++c) Zsum[c] = T(0);
+    T bq[4];
 
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      // lattice position of the quadrature point: q + cofs + (alpha-beta) S_q
-      const T sq0 = (q >= 1 && p0 == 0) || (q >= 2 && p1 == 0) || q == 3 ? T(1) : T(0);
-      const T sq1 = (q >= 1 && p0 == 1) || (q >= 2 && p1 == 1) || q == 3 ? T(1) : T(0);
-      const T sq2 = (q >= 1 && p0 == 2) || (q >= 2 && p1 == 2) || q == 3 ? T(1) : T(0);
-      const T xi0 = qx + cofs[0] + (QA - QB) * sq0;
-      const T xi1 = qy + cofs[1] + (QA - QB) * sq1;
-      const T xi2 = qz + cofs[2] + (QA - QB) * sq2;
+      // lattice position of qp q: corner + beta (3 e_p0 + 2 e_p1 + e_p2) + (alpha - beta) S_q
+      const int Sq = q == 0 ? 0 : (q == 1 ? S1 : (q == 2 ? S2 : 7));
+      const T xi0 = qx + QB * T(3 * (p0 == 0) + 2 * (p1 == 0) + (p2 == 0)) + (QA - QB) * T(Sq & 1);
+      const T xi1 = qy + QB * T(3 * (p0 == 1) + 2 * (p1 == 1) + (p2 == 1)) + (QA - QB) * T((Sq >> 1) & 1);
+      const T xi2 = qz + QB * T(3 * (p0 == 2) + 2 * (p1 == 2) + (p2 == 2)) + (QA - QB) * T(Sq >> 2);
       T x[3];
 #pragma unroll
       for (int r = 0; r < 3; ++r) x[r] = cv0[r] + cJn[3 * r] * xi0 + cJn[3 * r + 1] * xi1 + cJn[3 * r + 2] * xi2;
       const T r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
       const T rinv = rsqrt_t<T>(r2);
       T K[3][3];
-      T hr = T(1);
-      if (P.blending) {
-        const T h = x[0] * cnh[0] + x[1] * cnh[1] + x[2] * cnh[2];
-        const T hinv = T(1) / h;
-        hr = h * rinv * dinv;                  // 1 / s  with s = delta rho / h
+      T hr = T(1), h = T(0);
+      if (BLEND) {
+        h = x[0] * cnh[0] + x[1] * cnh[1] + x[2] * cnh[2];
+        const T hinv = rcp_t<T>(h);
+        hr = h * rinv * dinv;                  // 1/s, s = delta rho / h
         const T ri2 = rinv * rinv;
         T v[3];
 #pragma unroll
@@ -322,18 +368,24 @@ __global__ void __launch_bounds__(256) stokes_tile_kernel(const ApplyParams<T> P
       }
       const T coefB = C0 * hr * hr;   // w |det J| s
       const T Wq = coefB * hr;        // w |det J|
-      const T etaq = QB * eta_sum + (QA - QB) * eta_v[q];
 
-      // lattice gradient differences D_j = c_{j+1} - c_j at this qp, and grad' = D K
+      // nodal values u_{a,q} at this qp (vertex q and the three edges (a,q))
       T trace = T(0);
       T Gp[3][3];
+      T wsum[3], wq[3];
       if (HAS_U) {
         T D[3][3];
 #pragma unroll
-        for (int j = 0; j < 3; ++j)
+        for (int c = 0; c < 3; ++c) {
+          const T* uc = us + c * NSLOT2;
+          T w[4];
 #pragma unroll
-          for (int c = 0; c < 3; ++c)
-            D[j][c] = (baseg[j + 1][c] - baseg[j][c]) + dq * (uu[wnode(j + 1, q)][c] - uu[wnode(j, q)][c]);
+          for (int a = 0; a < 4; ++a) w[a] = uc[slot[wnode(a, q)]];
+#pragma unroll
+          for (int j = 0; j < 3; ++j) D[j][c] = dbase[j][c] + dq * (w[j + 1] - w[j]);
+          wq[c] = w[q];
+          wsum[c] = w[0] + w[1] + w[2] + w[3] - w[q];
+        }
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -341,27 +393,15 @@ __global__ void __launch_bounds__(256) stokes_tile_kernel(const ApplyParams<T> P
         trace = Gp[0][0] + Gp[1][1] + Gp[2][2];
       }
 
-      // B: div u + grad ln rho . u
+      // B: weights of -(div u + grad ln rho . u)
       if (OUT_P) {
         T b = coefB * trace;
-        if (P.withc_b) {
-          const T rad = P.blending ? (x[0] * cnh[0] + x[1] * cnh[1] + x[2] * cnh[2]) * dinv : r2 * rinv;
-          const T g = interp_table<T>(P.dlnrho, P.n_dlnrho, rad, P.r_cmb, P.r_surf);
-          // u at the qp: P2 values beta(2beta-1), alpha(2alpha-1) at vertices, 4beta^2, 4 alpha beta at edges
-          const T fvb = QB * (T(2) * QB - T(1)), fva = QA * (T(2) * QA - T(1));
-          const T feo = T(4) * QB * QB, fei = T(4) * QA * QB;
+        if (HAS_BC) {
+          const T rad = BLEND ? h * dinv : r2 * rinv;
+          const T g = dlnrho_at<T>(P, rad);
           T eu = T(0);
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            T sv = uu[0][c] + uu[1][c] + uu[2][c] + uu[3][c];
-            T se = uu[4][c] + uu[5][c] + uu[6][c] + uu[7][c] + uu[8][c] + uu[9][c];
-            T sqe = T(0);
-#pragma unroll
-            for (int b2 = 0; b2 < 4; ++b2)
-              if (b2 != q) sqe += uu[4 + edge_of(q, b2)][c];
-            const T uq = fvb * sv + (fva - fvb) * uu[q][c] + feo * se + (fei - feo) * sqe;
-            eu += uq * x[c];
-          }
+          for (int c = 0; c < 3; ++c) eu += (U0[c] + (fva - fvb) * wq[c] + (fei - feo) * wsum[c]) * x[c];
           b += Wq * g * eu * rinv;
         }
         bq[q] = b;
@@ -371,8 +411,8 @@ __global__ void __launch_bounds__(256) stokes_tile_kernel(const ApplyParams<T> P
         // stress (scaled): sigma = coefA eps(G') - coefB p_q I
         T S[3][3];
         if (OP & OP_A) {
-          const T coefA = T(2) * etaq * C0 * hr;
-          const T t3 = trace * (T(1) / T(3));
+          const T coefA = T(2) * (QB * eta_sum + (QA - QB) * eta_v[q]) * C0 * hr;
+          const T t3 = trace * T(1.0 / 3.0);
           S[0][0] = coefA * (Gp[0][0] - t3);
           S[1][1] = coefA * (Gp[1][1] - t3);
           S[2][2] = coefA * (Gp[2][2] - t3);
@@ -385,62 +425,71 @@ __global__ void __launch_bounds__(256) stokes_tile_kernel(const ApplyParams<T> P
 #pragma unroll
             for (int d = 0; d < 3; ++d) S[c][d] = T(0);
         }
+        T pq = T(0);
         if (HAS_P) {
-          const T pq = QB * p_sum + (QA - QB) * p_v[q];
+          pq = QB * p_sum + (QA - QB) * p_v[q];
           const T sp = coefB * pq;
           S[0][0] -= sp;
           S[1][1] -= sp;
           S[2][2] -= sp;
         }
         // R = S K^T (columns in permuted lattice order), s_a = R grad_lat lambda_a
-        T Rm[3][3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-          for (int j = 0; j < 3; ++j) Rm[c][j] = S[c][0] * K[j][0] + S[c][1] * K[j][1] + S[c][2] * K[j][2];
         T sv[4][3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          sv[0][c] = -Rm[c][0];
-          sv[1][c] = Rm[c][0] - Rm[c][1];
-          sv[2][c] = Rm[c][1] - Rm[c][2];
-          sv[3][c] = Rm[c][2];
+          const T r0 = S[c][0] * K[0][0] + S[c][1] * K[0][1] + S[c][2] * K[0][2];
+          const T r1 = S[c][0] * K[1][0] + S[c][1] * K[1][1] + S[c][2] * K[1][2];
+          const T r2c = S[c][0] * K[2][0] + S[c][1] * K[2][1] + S[c][2] * K[2][2];
+          sv[0][c] = -r0;
+          sv[1][c] = r0 - r1;
+          sv[2][c] = r1 - r2c;
+          sv[3][c] = r2c;
+          Rsum[c][0] += r0;
+          Rsum[c][1] += r1;
+          Rsum[c][2] += r2c;
         }
-        // (B+C)^T: the C part -W p_q g (x/|x|) . phi_i, distributed through the P2 values
+        // vertex q takes dq s_q^q now; T and E accumulate the rest
+        T vq[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) vq[c] = dq * sv[q][c];
+        // (B+C)^T: the C part -W p_q g (x/|x|) . phi_i through the P2 values at the qp
         if (HAS_CT) {
-          const T rad = P.blending ? (x[0] * cnh[0] + x[1] * cnh[1] + x[2] * cnh[2]) * dinv : r2 * rinv;
-          const T g = interp_table<T>(P.dlnrho, P.n_dlnrho, rad, P.r_cmb, P.r_surf);
-          const T pq = QB * p_sum + (QA - QB) * p_v[q];
+          const T rad = BLEND ? h * dinv : r2 * rinv;
+          const T g = dlnrho_at<T>(P, rad);
           const T zc = -Wq * pq * g * rinv;
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            Zsum[c] += zc * x[c];
-            Zv[q][c] = zc * x[c];
+            const T z = zc * x[c];
+            Zsum[c] += z;
+            vq[c] += (fva - fvb) * z;
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+              if (a != q) Eacc[edge_of(a, q)][c] += ((fei - feo) / dq) * z;
           }
         }
 #pragma unroll
+        for (int c = 0; c < 3; ++c) atomicAdd(&ys[c * NSLOT2 + slot[q]], vq[c]);
+#pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            Tacc[a][c] += sv[a][c];
-            if (a == q) Vd[a][c] = sv[a][c];
-            else Eacc[edge_of(a, q)][c] += sv[a][c];
-          }
+          for (int c = 0; c < 3; ++c)
+            if (a != q) Eacc[edge_of(a, q)][c] += sv[a][c];
       }
     }  // qp loop
 
     if (OUT_U) {
-      // P2 basis values at the qps: vertex beta(2beta-1) (alpha(2alpha-1) at its own qp),
-      // edge 4 beta^2 (4 alpha beta at the qps of its two vertices)
-      const T fvb = QB * (T(2) * QB - T(1)), fva = QA * (T(2) * QA - T(1));
-      const T feo = T(4) * QB * QB, fei = T(4) * QA * QB;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         T* y = ys + c * NSLOT2;
+        T Tacc[4];
+        Tacc[0] = -Rsum[c][0];
+        Tacc[1] = Rsum[c][0] - Rsum[c][1];
+        Tacc[2] = Rsum[c][1] - Rsum[c][2];
+        Tacc[3] = Rsum[c][2];
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-          T val = bq1 * Tacc[a][c] + dq * Vd[a][c];
-          if (HAS_CT) val += fvb * Zsum[c] + (fva - fvb) * Zv[a][c];
+          T val = bq1 * Tacc[a];
+          if (HAS_CT) val += fvb * Zsum[c];
           atomicAdd(&y[slot[a]], val);
         }
 #pragma unroll
@@ -448,8 +497,8 @@ __global__ void __launch_bounds__(256) stokes_tile_kernel(const ApplyParams<T> P
 #pragma unroll
           for (int b = a + 1; b < 4; ++b) {
             const int e = edge_of(a, b);
-            T val = b4 * (Tacc[a][c] + Tacc[b][c]) + dq * Eacc[e][c];
-            if (HAS_CT) val += feo * Zsum[c] + (fei - feo) * (Zv[a][c] + Zv[b][c]);
+            T val = b4 * (Tacc[a] + Tacc[b]) + dq * Eacc[e][c];
+            if (HAS_CT) val += feo * Zsum[c];
             atomicAdd(&y[slot[4 + e]], val);
           }
       }
@@ -457,18 +506,24 @@ __global__ void __launch_bounds__(256) stokes_tile_kernel(const ApplyParams<T> P
     if (OUT_P) {
       const T sb = bq[0] + bq[1] + bq[2] + bq[3];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) atomicAdd(&yp_s[base1 + o1[a]], -(QB * sb + (QA - QB) * bq[a]));
+      for (int a = 0; a < 4; ++a) atomicAdd(&yp_s[slot[a]], -(QB * sb + (QA - QB) * bq[a]));
     }
   }
   __syncthreads();
 
   // ---- add the block to the global result (output-side projections) ----
   if (OUT_U) {
-    const int nn = P.nb2.total;
-    for (int s = tid; s < NSLOT2; s += blockDim.x) {
-      const int id = gid2[s];
-      if (id < 0) continue;
-      const int cl = cls2[s];
+    const int nn = P.n_p2;
+    for (int s = tid; s < NSLOT2; s += kSweepThreads) {
+      const int code = gid2[s];
+      if (code < 0) continue;
+      const int id = code & 0x1fffffff;
+      const int gc = code >> 29;
+      int cl = NODE_FREE;
+      if (P.constrained && gc != 0) {
+        const int bc = gc == 1 ? P.bc_surface : P.bc_cmb;
+        cl = bc == BC_DIRICHLET ? NODE_DIRICHLET : NODE_FREESLIP;
+      }
       if (cl == NODE_DIRICHLET) {
         // identity rows of the constrained operator (A part); B^T rows stay zero
         if (OP & OP_A) {
@@ -480,18 +535,14 @@ __global__ void __launch_bounds__(256) stokes_tile_kernel(const ApplyParams<T> P
       }
       T v0 = ys[s], v1 = ys[NSLOT2 + s], v2 = ys[2 * NSLOT2 + s];
       if (cl == NODE_FREESLIP) {
-        const int dA = s % NB2, dB = (s / NB2) % NB2, dC = s / (NB2 * NB2);
-        const T xa = T(2 * a0 + dA) / T(N), xb = T(2 * b0 + dB) / T(N), xc = T(2 * c0 + dC) / T(N);
-        T x[3];
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-          x[r] = G.v0[r] + G.Jm[3 * r] * xa + G.Jm[3 * r + 1] * xb + G.Jm[3 * r + 2] * xc;
-        const T ri = rsqrt_t<T>(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
-        const T nx = x[0] * ri, ny = x[1] * ri, nz = x[2] * ri;
-        const T un = v0 * nx + v1 * ny + v2 * nz;
-        v0 -= un * nx;
-        v1 -= un * ny;
-        v2 -= un * nz;
+        int dA, dB, dC;
+        slot_coords(s, dA, dB, dC);
+        T nr[3];
+        lattice_normal<T>(G, 2 * a0 + dA, 2 * b0 + dB, 2 * c0 + dC, N, nr);
+        const T un = v0 * nr[0] + v1 * nr[1] + v2 * nr[2];
+        v0 -= un * nr[0];
+        v1 -= un * nr[1];
+        v2 -= un * nr[2];
       }
       atomicAdd(&P.yu[id], v0);
       atomicAdd(&P.yu[nn + id], v1);
@@ -499,7 +550,7 @@ __global__ void __launch_bounds__(256) stokes_tile_kernel(const ApplyParams<T> P
     }
   }
   if (OUT_P) {
-    for (int s = tid; s < NSLOT1; s += blockDim.x) {
+    for (int s = tid; s < NSLOT1; s += kSweepThreads) {
       const int id = gid1[s];
       if (id >= 0) atomicAdd(&P.yp[id], yp_s[s]);
     }

@@ -195,6 +195,7 @@ mfs_status mfs_mesh_shell(mfs_ctx* ctx, double r_cmb, double r_surf, int l_max, 
     st = upload(&L.d_tiles, H.tiles.data(), H.tiles.size(), s);
     if (st == MFS_OK) st = upload(&L.d_tets, H.tets.data(), H.tets.size(), s);
     if (st == MFS_OK) st = upload(&L.d_classes, H.classes.data(), H.classes.size(), s);
+    if (st == MFS_OK) st = build_id_tables(M, L);
     if (st == MFS_OK) MFS_CUDA(cudaStreamSynchronize(s));   // host vectors die here
     M->levels.push_back(L);
   }
@@ -215,6 +216,8 @@ mfs_status mfs_mesh_destroy(mfs_mesh* M) {
     cudaFree(L.d_tiles);
     cudaFree(L.d_tets);
     cudaFree(L.d_classes);
+    cudaFree(L.d_ids2);
+    cudaFree(L.d_ids1);
   }
   delete M;
   return MFS_OK;

@@ -16,12 +16,12 @@ constexpr int kMacroEdges = 102;
 constexpr int kMacroFaces = 140;
 constexpr int kMacroCells = 60;
 
-// Tile of TT^3 lattice cubes handled by one CTA (P2 node block (2TT+1)^3).
+// Tile of TT^3 lattice cubes handled by one CTA: its P2 node block has (2TT+1)^3 points,
+// stored as 8 parity classes of (TT+1)^3 slots; its P1 vertex block has (TT+1)^3 points.
 constexpr int TT = 4;
-constexpr int NB2 = 2 * TT + 1;        // P2 block edge (fine lattice points)
 constexpr int NB1 = TT + 1;            // P1 block edge
-constexpr int NSLOT2 = NB2 * NB2 * NB2;
 constexpr int NSLOT1 = NB1 * NB1 * NB1;
+constexpr int NSLOT2 = 8 * NSLOT1;
 
 // Numbering of the lattice points of one level (N intervals per macro edge): macro
 // vertices, then macro-edge interiors, macro-face interiors, macro-cell interiors.
@@ -72,8 +72,9 @@ struct Tile {
   int16_t cls;
 };
 
-// Operator sets of the fused micro-tet sweep; OP_CT: the B^T part is (B + C)^T.
-enum { OP_A = 1, OP_BT = 2, OP_B = 4, OP_CT = 8 };
+// Operator sets of the fused micro-tet sweep; OP_CT: the B^T part is (B + C)^T;
+// OP_BC: the B part is (B + C).
+enum { OP_A = 1, OP_BT = 2, OP_B = 4, OP_CT = 8, OP_BC = 16 };
 
 // Boundary condition types (match include/mfs.h).
 enum { BC_DIRICHLET = 0, BC_FREESLIP = 1 };
