@@ -1,0 +1,122 @@
+"""Pins of the oracle's multigrid and Stokes solver (no GPU)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.mesh import MacroMesh, Level
+from oracle.fem import p2_values
+from oracle.solver import (DEFAULTS, Hierarchy, StokesOracle, chebyshev, cg, direct_solve,
+                           prolongation)
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def test_default_parameters_match_paper_table():
+    gold = json.load(open(os.path.join(HERE, "golden", "solver_parameters.json")))
+    for k, v in DEFAULTS.items():
+        assert gold[k] == v, k
+
+
+def test_chebyshev_error_reduction_closed_form():
+    """On A = diag(lambda), D = I, b = 0 the error after one step of degree k is
+    T_k((theta - lambda)/delta) / T_k(theta/delta) (Chebyshev polynomial optimality)."""
+    lo, hi = 0.1, 2.0
+    lam = np.linspace(0.05, 2.2, 41)
+    theta, delta = (hi + lo) / 2, (hi - lo) / 2
+
+    def T(k, x):
+        x = np.asarray(x, dtype=float)
+        out = np.empty_like(x)
+        m = np.abs(x) <= 1
+        out[m] = np.cos(k * np.arccos(x[m]))
+        out[~m] = np.cosh(k * np.arccosh(np.abs(x[~m]))) * np.sign(x[~m]) ** k
+        return out
+    for k in (1, 2, 3, 5):
+        x = chebyshev(lambda v: lam * v, np.ones_like(lam), lambda v: v, np.ones_like(lam),
+                      np.zeros_like(lam), 1, k, lo, hi)
+        ref = T(k, (theta - lam) / delta) / T(k, np.array([theta / delta]))[0]
+        assert np.allclose(x, ref, rtol=1e-12, atol=1e-14)
+
+
+def test_cg_solves_spd():
+    rng = np.random.default_rng(3)
+    Q = rng.standard_normal((30, 30))
+    A = Q @ Q.T + 30 * np.eye(30)
+    b = rng.standard_normal(30)
+    x, it = cg(lambda v: A @ v, b, rtol=1e-12, maxit=200)
+    assert np.allclose(A @ x, b, rtol=0, atol=1e-9 * np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("lc", [0, 1, 2])
+def test_prolongation_exact_for_quadratics(lc):
+    """P2 spaces are nested in straight coordinates: prolongating the coarse interpolant
+    of a quadratic reproduces the fine interpolant exactly."""
+    mesh = MacroMesh()
+    Lc, Lf = Level(mesh, lc), Level(mesh, lc + 1)
+    P = prolongation(mesh, lc)
+    rng = np.random.default_rng(lc)
+    c = rng.standard_normal(10)
+
+    def q(x):
+        x0, x1, x2 = x[:, 0], x[:, 1], x[:, 2]
+        return (c[0] + c[1] * x0 + c[2] * x1 + c[3] * x2 + c[4] * x0 * x0 + c[5] * x1 * x1
+                + c[6] * x2 * x2 + c[7] * x0 * x1 + c[8] * x0 * x2 + c[9] * x1 * x2)
+    assert np.abs(P @ q(Lc.p2_straight) - q(Lf.p2_straight)).max() < 1e-12
+    # rows sum to one (partition of unity)
+    assert np.allclose(np.asarray(P.sum(axis=1)).ravel(), 1.0)
+
+
+@pytest.fixture(scope="module")
+def hier2():
+    mesh = MacroMesh()
+    L = Level(mesh, 2)
+    eta = W.viscosity_radial(L.p1_x)
+    return Hierarchy(mesh, 2, eta, dlnrho_table=W.dlnrho_table_config1())
+
+
+def test_vcycle_symmetric_with_exact_coarse(hier2):
+    H = hier2
+    rng = np.random.default_rng(0)
+    n = 3 * H.levels[2].n_p2
+    u = H.cons[2].P0(rng.standard_normal(n))
+    v = H.cons[2].P0(rng.standard_normal(n))
+    Mu = H.vcycle(2, u, 3, 2, coarse_exact=True)
+    Mv = H.vcycle(2, v, 3, 2, coarse_exact=True)
+    assert abs(v @ Mu - u @ Mv) <= 1e-12 * abs(v @ Mu)
+    assert u @ Mu > 0 and v @ Mv > 0
+
+
+def test_vcycle_contracts(hier2):
+    H = hier2
+    rng = np.random.default_rng(1)
+    n = 3 * H.levels[2].n_p2
+    b = H.cons[2].P0(rng.standard_normal(n))
+    A = H.co[2].apply_A
+    x = np.zeros(n)
+    res = []
+    for _ in range(4):
+        x = x + H.vcycle(2, b - A(x), 3, 2)
+        res.append(np.linalg.norm(b - A(x)) / np.linalg.norm(b))
+    assert res[-1] < 2e-3 and all(r2 < 0.5 * r1 for r1, r2 in zip(res, res[1:]))
+
+
+@pytest.mark.slow
+def test_stokes_fgmres_matches_direct(hier2):
+    H = hier2
+    S = StokesOracle(H)
+    rng = np.random.default_rng(2)
+    n, npp = 3 * H.levels[2].n_p2, H.levels[2].n_p1
+    f = rng.standard_normal(n)
+    g = np.zeros(npp)
+    u, p, it, hist = S.solve(f, g, np.zeros(n), np.zeros(npp), rtol=1e-8)
+    assert hist[-1] <= 1e-8 * hist[0]
+    assert it < 40
+    ud, pd = direct_solve(H, f, g, np.zeros(n), np.zeros(npp))
+    assert np.linalg.norm(u - ud) / np.linalg.norm(ud) < 1e-5
+    assert np.linalg.norm(p - pd) / np.linalg.norm(pd) < 1e-5
+    # the direct solution has (near) zero projected residual
+    r = S.residual(f, g, ud, pd)
+    assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(S.residual(f, g, 0 * ud, 0 * pd))
