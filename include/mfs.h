@@ -159,6 +159,42 @@ mfs_status mfs_apply_BT(mfs_problem* prob, int lvl, mfs_prec prec, mfs_bcmode mo
 mfs_status mfs_apply_stokes(mfs_problem* prob, int lvl, mfs_prec prec, int transpose, const void* u,
                             const void* p, void* yu, void* yp);
 
+/* ---------------------------------------------------------------- multigrid layer
+ * (paper Sec. 5.2.2).  mfs_setup_multigrid builds, for levels l_min..l_max: the
+ * boundary-node lists (Dirichlet / free-slip with their normals), the P2 transfer
+ * operators, diag(A) (without the free-slip projection, ones on Dirichlet rows), the
+ * Chebyshev interval [b/20, b] of D^-1 A per smoothing level (b = 1.2 x the largest
+ * eigenvalue from 15 FP64 power iterations, unless set by mfs_set_cheb_bounds), the FP64
+ * inverse of the coarsest-level operator, and the diagonal of M_{1/eta}.  Call it after
+ * mfs_set_viscosity (and again after every new viscosity).  Allocates device memory.
+ * Errors: MFS_EINVAL (viscosity not set, bad l_min), MFS_ENOMEM, MFS_ECUDA, MFS_ENAN. */
+mfs_status mfs_setup_multigrid(mfs_problem* prob, int l_min);
+
+/* Override / read the Chebyshev interval of D^-1 A on a smoothing level
+ * (l_min < lvl <= l_max).  Bounds set before mfs_setup_multigrid replace the estimate. */
+mfs_status mfs_set_cheb_bounds(mfs_problem* prob, int lvl, double lo, double hi);
+mfs_status mfs_get_cheb_bounds(const mfs_problem* prob, int lvl, double* lo, double* hi);
+
+/* diag(A) on level lvl without the free-slip projection (paper Sec. 5.2.2), 1 on
+ * Dirichlet rows; y: [3][n_p2]. */
+mfs_status mfs_diag_A(mfs_problem* prob, int lvl, mfs_prec prec, void* y);
+
+/* y = M_{1/eta} p, the P1 mass matrix weighted by 1/eta at the quadrature points (paper
+ * Eq. schurMass); p, y: [n_p1] of level lvl.  Needs only mfs_set_viscosity. */
+mfs_status mfs_apply_mass(mfs_problem* prob, int lvl, mfs_prec prec, const void* p, void* y);
+
+/* P2 prolongation from level lvl-1 to lvl (exact P2 interpolation in the straight
+ * coordinates, then the boundary projections of level lvl) and its transpose
+ * (restriction, then the projections of level lvl-1).  l_min < lvl <= l_max. */
+mfs_status mfs_prolongate(mfs_problem* prob, int lvl, mfs_prec prec, const void* xc, void* xf);
+mfs_status mfs_restrict(mfs_problem* prob, int lvl, mfs_prec prec, const void* rf, void* rc);
+
+/* One V-cycle for the constrained A on level lvl (paper Sec. 5.2.2): `steps` Chebyshev
+ * pre- and post-smoothing steps of `degree` applications each, exact FP64 coarse solve on
+ * l_min.  f: right-hand side [3][n_p2]; u: result (overwritten, the cycle starts from 0).
+ * Errors: MFS_EINVAL (multigrid not set up, bad level), MFS_ECUDA. */
+mfs_status mfs_vcycle(mfs_problem* prob, int lvl, mfs_prec prec, int steps, int degree, const void* f, void* u);
+
 /* Allocation-free variant of mfs_apply_B (no counterpart in the paper).
  *
  * For callers that cannot call cudaMalloc while they apply the operator: for example code

@@ -59,6 +59,14 @@ _SIGS = {
     "mfs_apply_BT": ([_vp, _i, _i, _i, _i, _vp, _vp], _i),
     "mfs_apply_stokes": ([_vp, _i, _i, _i, _vp, _vp, _vp, _vp], _i),
     "mfs_apply_B_noalloc": ([_vp, _i, _i, _i, _i, _vp, _vp], _i),
+    "mfs_setup_multigrid": ([_vp, _i], _i),
+    "mfs_set_cheb_bounds": ([_vp, _i, _d, _d], _i),
+    "mfs_get_cheb_bounds": ([_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_d)], _i),
+    "mfs_diag_A": ([_vp, _i, _i, _vp], _i),
+    "mfs_apply_mass": ([_vp, _i, _i, _vp, _vp], _i),
+    "mfs_prolongate": ([_vp, _i, _i, _vp, _vp], _i),
+    "mfs_restrict": ([_vp, _i, _i, _vp, _vp], _i),
+    "mfs_vcycle": ([_vp, _i, _i, _i, _i, _vp, _vp], _i),
 }
 
 _lib = None
@@ -221,6 +229,45 @@ class Problem:
         _need(yu, nu, u.dtype, "yu"); _need(yp, npp, u.dtype, "yp")
         _check(lib().mfs_apply_stokes(self.handle, level, _prec_of(u), int(transpose), _ptr(u), _ptr(p),
                                       _ptr(yu), _ptr(yp)))
+
+    # ---- multigrid layer
+    def setup_multigrid(self, l_min=1):
+        _check(lib().mfs_setup_multigrid(self.handle, l_min))
+
+    def set_cheb_bounds(self, level, lo, hi):
+        _check(lib().mfs_set_cheb_bounds(self.handle, level, lo, hi))
+
+    def cheb_bounds(self, level):
+        lo, hi = ctypes.c_double(), ctypes.c_double()
+        _check(lib().mfs_get_cheb_bounds(self.handle, level, ctypes.byref(lo), ctypes.byref(hi)))
+        return lo.value, hi.value
+
+    def diag_A(self, level, y):
+        nu, _ = self._sizes(level)
+        _need(y, nu, None, "y")
+        _check(lib().mfs_diag_A(self.handle, level, _prec_of(y), _ptr(y)))
+
+    def apply_mass(self, level, p, y):
+        _, npp = self._sizes(level)
+        _need(p, npp, None, "p"); _need(y, npp, p.dtype, "y")
+        _check(lib().mfs_apply_mass(self.handle, level, _prec_of(p), _ptr(p), _ptr(y)))
+
+    def prolongate(self, level, xc, xf):
+        nf, _ = self._sizes(level)
+        nc, _ = self._sizes(level - 1)
+        _need(xc, nc, None, "xc"); _need(xf, nf, xc.dtype, "xf")
+        _check(lib().mfs_prolongate(self.handle, level, _prec_of(xc), _ptr(xc), _ptr(xf)))
+
+    def restrict(self, level, rf, rc):
+        nf, _ = self._sizes(level)
+        nc, _ = self._sizes(level - 1)
+        _need(rf, nf, None, "rf"); _need(rc, nc, rf.dtype, "rc")
+        _check(lib().mfs_restrict(self.handle, level, _prec_of(rf), _ptr(rf), _ptr(rc)))
+
+    def vcycle(self, level, f, u, steps=3, degree=2):
+        nu, _ = self._sizes(level)
+        _need(f, nu, None, "f"); _need(u, nu, f.dtype, "u")
+        _check(lib().mfs_vcycle(self.handle, level, _prec_of(f), steps, degree, _ptr(f), _ptr(u)))
 
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:

@@ -54,6 +54,13 @@ static mfs_status check_problem(const mfs_problem* P, int lvl, bool need_eta) {
   return MFS_OK;
 }
 
+template <typename T>
+static T* red_of(mfs_problem* P);
+template <>
+double* red_of<double>(mfs_problem* P) { return P->d_red64; }
+template <>
+float* red_of<float>(mfs_problem* P) { return P->d_red32; }
+
 std::pair<cudaEvent_t, cudaEvent_t> timing_events(mfs_ctx* ctx) {
   if (!ctx || !ctx->timing) return {nullptr, nullptr};
   cudaEvent_t e[2];
@@ -68,6 +75,30 @@ std::pair<cudaEvent_t, cudaEvent_t> timing_events(mfs_ctx* ctx) {
   ctx->ev_used.push_back({e[0], e[1]});
   return {e[0], e[1]};
 }
+
+template <typename T>
+mfs_status apply_constrained(mfs_problem* P, int lvl, int op, int constrained, int withc_b, const T* u, const T* p,
+                             T* yu, T* yp) {
+  mfs_mesh* M = P->mesh;
+  cudaStream_t s = M->ctx->stream;
+  const LevelData& L = M->levels[lvl];
+  T* red = red_of<T>(P);
+  const T* psum = nullptr;
+  if (constrained && (op & OP_BT)) {   // P_p on the pressure input: the kernel subtracts sum/n
+    MFS_TRY(vec_sum<T>(p, L.nb1.total, red, red + kRedBlocks, s));
+    psum = red + kRedBlocks;
+  }
+  MFS_TRY(launch_apply<T>(P, lvl, op, constrained, withc_b, u, p, yu, yp, psum));
+  if (constrained && (op & OP_B)) {
+    MFS_TRY(vec_sum<T>(yp, L.nb1.total, red, red + kRedBlocks + 2, s));
+    MFS_TRY(vec_sub_mean<T>(yp, L.nb1.total, red + kRedBlocks + 2, s));
+  }
+  return MFS_OK;
+}
+template mfs_status apply_constrained<float>(mfs_problem*, int, int, int, int, const float*, const float*, float*,
+                                             float*);
+template mfs_status apply_constrained<double>(mfs_problem*, int, int, int, int, const double*, const double*,
+                                              double*, double*);
 
 }  // namespace mfs
 
@@ -344,6 +375,7 @@ mfs_status mfs_problem_create(mfs_mesh* M, mfs_bc bc_surface, mfs_bc bc_cmb, mfs
 
 mfs_status mfs_problem_destroy(mfs_problem* P) {
   if (!P) return MFS_OK;
+  problem_release_solver(P);
   for (auto p : P->eta64) cudaFree(p);
   for (auto p : P->eta32) cudaFree(p);
   cudaFree(P->d_dlnrho64);
@@ -373,6 +405,7 @@ mfs_status mfs_set_viscosity(mfs_problem* P, const double* eta, int is_log) {
   return MFS_OK;
 }
 
+
 mfs_status mfs_set_density(mfs_problem* P, int n, const double* tab) {
   MFS_TRY(check_problem(P, 0, false));
   if (n < 1 || !tab) {
@@ -393,31 +426,11 @@ mfs_status mfs_set_density(mfs_problem* P, int n, const double* tab) {
   return MFS_OK;
 }
 
-template <typename T>
-static T* red_of(mfs_problem* P);
-template <>
-double* red_of<double>(mfs_problem* P) { return P->d_red64; }
-template <>
-float* red_of<float>(mfs_problem* P) { return P->d_red32; }
 
 template <typename T>
 static mfs_status apply_typed(mfs_problem* P, int lvl, int op, int constrained, int withc_b, const void* u,
                               const void* p, void* yu, void* yp) {
-  mfs_mesh* M = P->mesh;
-  cudaStream_t s = M->ctx->stream;
-  const LevelData& L = M->levels[lvl];
-  T* red = red_of<T>(P);
-  const T* psum = nullptr;
-  if (constrained && (op & OP_BT)) {   // P_p on the pressure input: the kernel subtracts sum/n
-    MFS_TRY(vec_sum<T>((const T*)p, L.nb1.total, red, red + kRedBlocks, s));
-    psum = red + kRedBlocks;
-  }
-  MFS_TRY(launch_apply<T>(P, lvl, op, constrained, withc_b, (const T*)u, (const T*)p, (T*)yu, (T*)yp, psum));
-  if (constrained && (op & OP_B)) {
-    MFS_TRY(vec_sum<T>((const T*)yp, L.nb1.total, red, red + kRedBlocks + 2, s));
-    MFS_TRY(vec_sub_mean<T>((T*)yp, L.nb1.total, red + kRedBlocks + 2, s));
-  }
-  return MFS_OK;
+  return apply_constrained<T>(P, lvl, op, constrained, withc_b, (const T*)u, (const T*)p, (T*)yu, (T*)yp);
 }
 
 static mfs_status check_vecs(const void* a, const void* b) {

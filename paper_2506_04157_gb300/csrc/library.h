@@ -72,6 +72,11 @@ MacroGeom<T> cast_geom(const MacroGeom<double>& g);
 
 }  // namespace mfs
 
+namespace mfs {
+struct MG;
+void problem_release_solver(mfs_problem* P);
+}  // namespace mfs
+
 struct mfs_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -108,6 +113,7 @@ struct mfs_problem {
   // reduction workspace: partial sums and a few device scalars
   double* d_red64 = nullptr;    // [kRedSlots]
   float* d_red32 = nullptr;
+  mfs::MG* mg = nullptr;        // multigrid hierarchy and solver workspaces
 };
 
 namespace mfs {
@@ -119,6 +125,11 @@ constexpr int kRedSlots = kRedBlocks + 64;
 template <typename T>
 mfs_status launch_apply(mfs_problem* P, int lvl, int op, int constrained, int withc_b, const T* u,
                         const T* p, T* yu, T* yp, const T* psum);
+
+// launch_apply plus the pressure projections of the constrained mode
+template <typename T>
+mfs_status apply_constrained(mfs_problem* P, int lvl, int op, int constrained, int withc_b, const T* u, const T* p,
+                             T* yu, T* yp);
 
 // ---- vector kernels (vec.cu) ----
 template <typename T>

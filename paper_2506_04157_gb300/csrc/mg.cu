@@ -1,0 +1,515 @@
+// Kernels of the multigrid and Krylov layers (arxiv 2506.04157, Sec. 5.2):
+//  * BLAS-1 on velocity / pressure / saddle-point vectors, dot products accumulated in
+//    FP64 with a deterministic two-pass reduction;
+//  * Jacobi scaling and the boundary projections (Dirichlet zeroing, free-slip P_v);
+//  * P2 prolongation / restriction as CSR products (exact P2 interpolation, Sec. 5.2.2);
+//  * diag(A) without the free-slip projection (Sec. 5.2.2) and the inverse-viscosity P1
+//    mass M_{1/eta} with its diagonal (Sec. 5.2.3), both as micro-tet sweeps;
+//  * the coarsest-level operator: assembled column by column, inverted once per
+//    viscosity in FP64 by Gauss-Jordan elimination, applied as a GEMV.
+#include "apply.cuh"
+#include "library.h"
+#include "solver.h"
+
+namespace mfs {
+
+static inline int blocks_for(int64_t n, int threads = 256, int cap = 8192) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  return (int)(b < cap ? b : cap);
+}
+
+#define GRID_STRIDE(i, n) \
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+// ------------------------------------------------------------------------- BLAS-1
+template <typename T>
+__global__ void k_axpby(int64_t n, T a, const T* __restrict__ x, T b, T* __restrict__ y) {
+  if (b == T(0)) {
+    GRID_STRIDE(i, n) y[i] = a * x[i];
+  } else {
+    GRID_STRIDE(i, n) y[i] = a * x[i] + b * y[i];
+  }
+}
+template <typename T>
+__global__ void k_axpbypcz(int64_t n, T a, const T* __restrict__ x, T b, const T* __restrict__ y, T c,
+                           T* __restrict__ z) {
+  if (c == T(0)) {
+    GRID_STRIDE(i, n) z[i] = a * x[i] + b * y[i];
+  } else {
+    GRID_STRIDE(i, n) z[i] = a * x[i] + b * y[i] + c * z[i];
+  }
+}
+template <typename T>
+__global__ void k_fill(int64_t n, T v, T* __restrict__ y) {
+  GRID_STRIDE(i, n) y[i] = v;
+}
+template <typename T, typename S>
+__global__ void k_convert(int64_t n, const S* __restrict__ x, T* __restrict__ y) {
+  GRID_STRIDE(i, n) y[i] = (T)x[i];
+}
+template <typename T>
+__global__ void k_mul(int64_t n, const T* __restrict__ x, const T* __restrict__ d, T* __restrict__ z) {
+  GRID_STRIDE(i, n) z[i] = x[i] * d[i];
+}
+template <typename T>
+__global__ void k_recip(int64_t n, T* __restrict__ x) {
+  GRID_STRIDE(i, n) x[i] = T(1) / x[i];
+}
+
+__device__ __forceinline__ double dwarp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double dblock_sum(double v) {
+  __shared__ double red[32];
+  v = dwarp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  v = threadIdx.x < nw ? red[threadIdx.x] : 0.0;
+  if (w == 0) v = dwarp_sum(v);
+  return v;
+}
+
+// per-thread partial in T over a fixed stride pattern, block and final sums in FP64
+template <typename T>
+__global__ void k_dot_part(int64_t n, const T* __restrict__ x, const T* __restrict__ y, double* __restrict__ part) {
+  T acc = T(0);
+  GRID_STRIDE(i, n) acc += x[i] * y[i];
+  const double s = dblock_sum((double)acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+__global__ void k_dot_final(const double* __restrict__ part, int np, double* __restrict__ out) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) acc += part[i];
+  acc = dblock_sum(acc);
+  if (threadIdx.x == 0) *out = acc;
+}
+
+// ------------------------------------------------------------------------- projections
+// kind: 1 = Dirichlet (zero the node), 2 = free slip (remove the normal component)
+template <typename T>
+__global__ void k_bproject(int nb, const int* __restrict__ ids, const int8_t* __restrict__ kind,
+                           const T* __restrict__ nrm, int64_t n_p2, T* __restrict__ v) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+    const int64_t id = ids[k];
+    if (kind[k] == 1) {
+      v[id] = T(0);
+      v[n_p2 + id] = T(0);
+      v[2 * n_p2 + id] = T(0);
+    } else {
+      const T nx = nrm[3 * k], ny = nrm[3 * k + 1], nz = nrm[3 * k + 2];
+      const T un = v[id] * nx + v[n_p2 + id] * ny + v[2 * n_p2 + id] * nz;
+      v[id] -= un * nx;
+      v[n_p2 + id] -= un * ny;
+      v[2 * n_p2 + id] -= un * nz;
+    }
+  }
+}
+// Dirichlet rows of diag(A) are 1 (identity rows of the constrained operator)
+template <typename T>
+__global__ void k_diag_dirichlet(int nb, const int* __restrict__ ids, const int8_t* __restrict__ kind, int64_t n_p2,
+                                 T* __restrict__ d) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x)
+    if (kind[k] == 1) {
+      const int64_t id = ids[k];
+      d[id] = d[n_p2 + id] = d[2 * n_p2 + id] = T(1);
+    }
+}
+// coarse matrix: add n n^T on free-slip nodes (regularises the projected-out directions)
+__global__ void k_regularise_normals(int nb, const int* __restrict__ ids, const int8_t* __restrict__ kind,
+                                     const double* __restrict__ nrm, int64_t n_p2, double* __restrict__ A) {
+  const int64_t N = 3 * n_p2;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+    if (kind[k] != 2) continue;
+    const int64_t id = ids[k];
+    for (int c = 0; c < 3; ++c)
+      for (int d = 0; d < 3; ++d) A[(c * n_p2 + id) * N + d * n_p2 + id] += nrm[3 * k + c] * nrm[3 * k + d];
+  }
+}
+
+// ------------------------------------------------------------------------- transfers
+// y[c] = alpha * P x[c] + beta * y[c] for the three components (SoA), P in CSR
+template <typename T>
+__global__ void k_spmv3(int nrows, const int* __restrict__ rp, const int* __restrict__ ci, const T* __restrict__ w,
+                        int64_t ncols, const T* __restrict__ x, T alpha, T beta, T* __restrict__ y) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += gridDim.x * blockDim.x) {
+    T s0 = T(0), s1 = T(0), s2 = T(0);
+    for (int k = rp[r]; k < rp[r + 1]; ++k) {
+      const int64_t j = ci[k];
+      const T wk = w[k];
+      s0 += wk * x[j];
+      s1 += wk * x[ncols + j];
+      s2 += wk * x[2 * ncols + j];
+    }
+    const int64_t nr = nrows;
+    if (beta == T(0)) {
+      y[r] = alpha * s0;
+      y[nr + r] = alpha * s1;
+      y[2 * nr + r] = alpha * s2;
+    } else {
+      y[r] = alpha * s0 + beta * y[r];
+      y[nr + r] = alpha * s1 + beta * y[nr + r];
+      y[2 * nr + r] = alpha * s2 + beta * y[2 * nr + r];
+    }
+  }
+}
+
+// ------------------------------------------------------------------------- coarse solve
+// x = Ainv b, FP64 accumulation; one warp per row
+template <typename T>
+__global__ void k_gemv_f64(int n, const double* __restrict__ A, const T* __restrict__ b, T* __restrict__ x) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int r = warp; r < n; r += nw) {
+    double s = 0.0;
+    const double* row = A + (int64_t)r * n;
+    for (int j = lane; j < n; j += 32) s += row[j] * (double)b[j];
+    s = dwarp_sum(s);
+    if (lane == 0) x[r] = (T)s;
+  }
+}
+
+// Gauss-Jordan inversion in place, no pivoting (the regularised coarse operator is SPD).
+// step k, part 1 (one block): save column k, scale row k by 1/a_kk, a_kk <- 1/a_kk
+__global__ void k_gj_row(int n, int k, double* __restrict__ A, double* __restrict__ colk) {
+  const double piv = A[(int64_t)k * n + k];
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) colk[i] = A[(int64_t)i * n + k];
+  __syncthreads();
+  const double inv = 1.0 / piv;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) A[(int64_t)k * n + j] = (j == k ? 1.0 : A[(int64_t)k * n + j]) * inv;
+}
+// part 2: eliminate column k from every other row
+__global__ void k_gj_elim(int n, int k, double* __restrict__ A, const double* __restrict__ colk) {
+  const int64_t total = (int64_t)n * n;
+  GRID_STRIDE(t, total) {
+    const int i = (int)(t / n), j = (int)(t - (int64_t)i * n);
+    if (i == k) continue;
+    const double f = colk[i];
+    const double akj = A[(int64_t)k * n + j];
+    A[t] = (j == k ? 0.0 : A[t]) - f * akj;
+  }
+}
+__global__ void k_unit(int64_t n, int64_t j, double* __restrict__ e) {
+  GRID_STRIDE(i, n) e[i] = (i == j) ? 1.0 : 0.0;
+}
+
+// ------------------------------------------------------------------------- diag(A), M_{1/eta}
+// lattice gradient (permuted frame) of the P2 basis function a at barycentrics lam
+__device__ __forceinline__ void p2_lat_grad(int a, const double lam[4], double g[3]) {
+  // grad lambda_0 = (-1,0,0), grad lambda_1 = (1,-1,0), grad lambda_2 = (0,1,-1), grad lambda_3 = (0,0,1)
+  const double GL[4][3] = {{-1, 0, 0}, {1, -1, 0}, {0, 1, -1}, {0, 0, 1}};
+  if (a < 4) {
+    for (int j = 0; j < 3; ++j) g[j] = (4 * lam[a] - 1) * GL[a][j];
+  } else {
+    const int e = a - 4;
+    const int i0 = e < 3 ? 0 : (e < 5 ? 1 : 2);
+    const int i1 = e < 3 ? e + 1 : (e < 5 ? e - 1 : 3);
+    for (int j = 0; j < 3; ++j) g[j] = 4 * (lam[i1] * GL[i0][j] + lam[i0] * GL[i1][j]);
+  }
+}
+
+// geometry of qp q of a tet: K' rows (permuted lattice frame) and the scalings
+template <typename T, bool BLEND>
+__device__ __forceinline__ void qp_geometry(const MacroGeom<T>& G, int n, int p0, int p1, int p2, int q, T qx, T qy,
+                                            T qz, T K[3][3], T& hr, T& rinv, T x[3]) {
+  const T QA = T(MFS_QA), QB = T(MFS_QB);
+  const int S1 = 1 << p0, S2 = S1 | (1 << p1);
+  const int Sq = q == 0 ? 0 : (q == 1 ? S1 : (q == 2 ? S2 : 7));
+  const T xi0 = qx + QB * T(3 * (p0 == 0) + 2 * (p1 == 0) + (p2 == 0)) + (QA - QB) * T(Sq & 1);
+  const T xi1 = qy + QB * T(3 * (p0 == 1) + 2 * (p1 == 1) + (p2 == 1)) + (QA - QB) * T((Sq >> 1) & 1);
+  const T xi2 = qz + QB * T(3 * (p0 == 2) + 2 * (p1 == 2) + (p2 == 2)) + (QA - QB) * T(Sq >> 2);
+  for (int r = 0; r < 3; ++r)
+    x[r] = G.v0[r] + (G.Jm[3 * r] * xi0 + G.Jm[3 * r + 1] * xi1 + G.Jm[3 * r + 2] * xi2) / T(n);
+  const T r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+  rinv = T(1) / sqrt(r2);
+  const int pr[3] = {p0, p1, p2};
+  T Mp[3][3];
+  for (int j = 0; j < 3; ++j)
+    for (int d = 0; d < 3; ++d) Mp[j][d] = T(n) * G.Jinv[3 * pr[j] + d];
+  hr = T(1);
+  if (BLEND) {
+    const T h = x[0] * G.nh[0] + x[1] * G.nh[1] + x[2] * G.nh[2];
+    hr = h * rinv / G.delta;
+    T v[3];
+    for (int d = 0; d < 3; ++d) v[d] = G.nh[d] / h - x[d] * rinv * rinv;
+    for (int j = 0; j < 3; ++j) {
+      const T tj = Mp[j][0] * x[0] + Mp[j][1] * x[1] + Mp[j][2] * x[2];
+      for (int d = 0; d < 3; ++d) K[j][d] = Mp[j][d] - tj * v[d];
+    }
+  } else {
+    for (int j = 0; j < 3; ++j)
+      for (int d = 0; d < 3; ++d) K[j][d] = Mp[j][d];
+  }
+}
+
+// diag(A) (raw, no projection): sum over tets and qps of 2 eta W (|g|^2/2 + g_c^2/6)
+template <typename T, bool BLEND>
+__global__ void __launch_bounds__(128) k_diag_sweep(const ApplyParams<T> P, T* __restrict__ diag) {
+  __shared__ T ds[3 * NSLOT2];
+  __shared__ T eta_s[NSLOT1];
+  const int m = blockIdx.y, tidx = blockIdx.x;
+  const size_t lin = (size_t)m * gridDim.x + tidx;
+  const Tile tile = P.tiles[tidx];
+  const MacroGeom<T>& G = P.geom[m];
+  const int n = P.n;
+  for (int s = threadIdx.x; s < 3 * NSLOT2; s += blockDim.x) ds[s] = T(0);
+  for (int s = threadIdx.x; s < NSLOT1; s += blockDim.x) {
+    const int id = P.ids1[lin * NSLOT1 + s];
+    eta_s[s] = id >= 0 ? P.eta[id] : T(1);
+  }
+  __syncthreads();
+  const double QA = MFS_QA, QB = MFS_QB;
+  const T C0 = G.absdet / (T(24) * T(n) * T(n) * T(n));
+  const int2 cinfo = P.classes[tile.cls];
+  for (int t = threadIdx.x; t < cinfo.y; t += blockDim.x) {
+    const int code = P.tets[cinfo.x + t];
+    const int ci = code & 15, cj = (code >> 4) & 15, ck = (code >> 8) & 15, pmu = code >> 12;
+    const int p0 = (0x221100 >> (4 * pmu)) & 3, p1 = (0x102021 >> (4 * pmu)) & 3, p2 = (0x010212 >> (4 * pmu)) & 3;
+    const int S1 = 1 << p0, S2 = S1 | (1 << p1);
+    const int base = ci + 5 * cj + 25 * ck;
+    int slot[10];
+    slot[0] = base;
+    slot[1] = base + sub_off(S1);
+    slot[2] = base + sub_off(S2);
+    slot[3] = base + sub_off(7);
+    slot[4] = S1 * kSub + base;
+    slot[5] = S2 * kSub + base;
+    slot[6] = 7 * kSub + base;
+    slot[7] = (S1 ^ S2) * kSub + base + sub_off(S1);
+    slot[8] = (S1 ^ 7) * kSub + base + sub_off(S1);
+    slot[9] = (S2 ^ 7) * kSub + base + sub_off(S2);
+    T eta_v[4];
+    for (int a = 0; a < 4; ++a) eta_v[a] = eta_s[slot[a]];
+    const T qx = T(tile.ta * TT + ci), qy = T(tile.tb * TT + cj), qz = T(tile.tc * TT + ck);
+    T acc[10][3];
+    for (int a = 0; a < 10; ++a) acc[a][0] = acc[a][1] = acc[a][2] = T(0);
+    for (int q = 0; q < 4; ++q) {
+      T K[3][3], hr, rinv, x[3];
+      qp_geometry<T, BLEND>(G, n, p0, p1, p2, q, qx, qy, qz, K, hr, rinv, x);
+      const double lam[4] = {q == 0 ? QA : QB, q == 1 ? QA : QB, q == 2 ? QA : QB, q == 3 ? QA : QB};
+      const T etaq = T(lam[0]) * eta_v[0] + T(lam[1]) * eta_v[1] + T(lam[2]) * eta_v[2] + T(lam[3]) * eta_v[3];
+      const T coefA = T(2) * etaq * C0 * hr;
+      for (int a = 0; a < 10; ++a) {
+        double gl[3];
+        p2_lat_grad(a, lam, gl);
+        T g[3];
+        for (int d = 0; d < 3; ++d) g[d] = T(gl[0]) * K[0][d] + T(gl[1]) * K[1][d] + T(gl[2]) * K[2][d];
+        const T g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+        for (int c = 0; c < 3; ++c) acc[a][c] += coefA * (T(0.5) * g2 + g[c] * g[c] / T(6));
+      }
+    }
+    for (int a = 0; a < 10; ++a)
+      for (int c = 0; c < 3; ++c) atomicAdd(&ds[c * NSLOT2 + slot[a]], acc[a][c]);
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < NSLOT2; s += blockDim.x) {
+    const int code = P.ids2[lin * NSLOT2 + s];
+    if (code < 0) continue;
+    const int64_t id = code & 0x1fffffff;
+    for (int c = 0; c < 3; ++c) atomicAdd(&diag[c * (int64_t)P.n_p2 + id], ds[c * NSLOT2 + s]);
+  }
+}
+
+// y += M_{1/eta} p (DIAG: y += diag(M_{1/eta})): int (1/eta_q) psi_j psi_k over blended tets
+template <typename T, bool BLEND, bool DIAG>
+__global__ void __launch_bounds__(128) k_mass_sweep(const ApplyParams<T> P, const T* __restrict__ pin, T* __restrict__ y) {
+  __shared__ T ps[NSLOT1], ys[NSLOT1], eta_s[NSLOT1];
+  __shared__ int gid[NSLOT1];
+  const int m = blockIdx.y, tidx = blockIdx.x;
+  const size_t lin = (size_t)m * gridDim.x + tidx;
+  const Tile tile = P.tiles[tidx];
+  const MacroGeom<T>& G = P.geom[m];
+  const int n = P.n;
+  for (int s = threadIdx.x; s < NSLOT1; s += blockDim.x) {
+    const int id = P.ids1[lin * NSLOT1 + s];
+    gid[s] = id;
+    eta_s[s] = id >= 0 ? P.eta[id] : T(1);
+    ps[s] = (!DIAG && id >= 0) ? pin[id] : T(0);
+    ys[s] = T(0);
+  }
+  __syncthreads();
+  const double QA = MFS_QA, QB = MFS_QB;
+  const T C0 = G.absdet / (T(24) * T(n) * T(n) * T(n));
+  const int2 cinfo = P.classes[tile.cls];
+  for (int t = threadIdx.x; t < cinfo.y; t += blockDim.x) {
+    const int code = P.tets[cinfo.x + t];
+    const int ci = code & 15, cj = (code >> 4) & 15, ck = (code >> 8) & 15, pmu = code >> 12;
+    const int p0 = (0x221100 >> (4 * pmu)) & 3, p1 = (0x102021 >> (4 * pmu)) & 3, p2 = (0x010212 >> (4 * pmu)) & 3;
+    const int S1 = 1 << p0, S2 = S1 | (1 << p1);
+    const int base = ci + 5 * cj + 25 * ck;
+    const int sl[4] = {base, base + sub_off(S1), base + sub_off(S2), base + sub_off(7)};
+    T ev[4], pv[4], out[4] = {T(0), T(0), T(0), T(0)};
+    for (int a = 0; a < 4; ++a) {
+      ev[a] = eta_s[sl[a]];
+      pv[a] = ps[sl[a]];
+    }
+    const T qx = T(tile.ta * TT + ci), qy = T(tile.tb * TT + cj), qz = T(tile.tc * TT + ck);
+    for (int q = 0; q < 4; ++q) {
+      T K[3][3], hr, rinv, x[3];
+      qp_geometry<T, BLEND>(G, n, p0, p1, p2, q, qx, qy, qz, K, hr, rinv, x);
+      const T W = C0 * hr * hr * hr;
+      T lam[4];
+      for (int a = 0; a < 4; ++a) lam[a] = T(a == q ? QA : QB);
+      const T etaq = lam[0] * ev[0] + lam[1] * ev[1] + lam[2] * ev[2] + lam[3] * ev[3];
+      const T wq = W / etaq;
+      if (DIAG) {
+        for (int a = 0; a < 4; ++a) out[a] += wq * lam[a] * lam[a];
+      } else {
+        const T pq = lam[0] * pv[0] + lam[1] * pv[1] + lam[2] * pv[2] + lam[3] * pv[3];
+        for (int a = 0; a < 4; ++a) out[a] += wq * lam[a] * pq;
+      }
+    }
+    for (int a = 0; a < 4; ++a) atomicAdd(&ys[sl[a]], out[a]);
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < NSLOT1; s += blockDim.x)
+    if (gid[s] >= 0) atomicAdd(&y[gid[s]], ys[s]);
+}
+
+// ------------------------------------------------------------------------- host wrappers
+template <typename T>
+void Blas<T>::axpby(int64_t n, T a, const T* x, T b, T* y, cudaStream_t s) {
+  k_axpby<T><<<blocks_for(n), 256, 0, s>>>(n, a, x, b, y);
+}
+template <typename T>
+void Blas<T>::axpbypcz(int64_t n, T a, const T* x, T b, const T* y, T c, T* z, cudaStream_t s) {
+  k_axpbypcz<T><<<blocks_for(n), 256, 0, s>>>(n, a, x, b, y, c, z);
+}
+template <typename T>
+void Blas<T>::fill(int64_t n, T v, T* y, cudaStream_t s) {
+  k_fill<T><<<blocks_for(n), 256, 0, s>>>(n, v, y);
+}
+template <typename T>
+void Blas<T>::mul(int64_t n, const T* x, const T* d, T* z, cudaStream_t s) {
+  k_mul<T><<<blocks_for(n), 256, 0, s>>>(n, x, d, z);
+}
+template <typename T>
+void Blas<T>::recip(int64_t n, T* x, cudaStream_t s) {
+  k_recip<T><<<blocks_for(n), 256, 0, s>>>(n, x);
+}
+template <typename T>
+void Blas<T>::dot_async(int64_t n, const T* x, const T* y, double* part, double* out, cudaStream_t s) {
+  const int nb = blocks_for(n, 256, kRedBlocks);
+  k_dot_part<T><<<nb, 256, 0, s>>>(n, x, y, part);
+  k_dot_final<<<1, 512, 0, s>>>(part, nb, out);
+}
+template <typename T>
+void Blas<T>::bproject(const BoundaryList& B, int64_t n_p2, T* v, cudaStream_t s) {
+  if (B.nb == 0) return;
+  k_bproject<T><<<blocks_for(B.nb), 256, 0, s>>>(B.nb, B.ids, B.kind, B.template normals<T>(), n_p2, v);
+}
+template <typename T>
+void Blas<T>::spmv3(const Csr& P, int64_t ncols, const T* x, T alpha, T beta, T* y, cudaStream_t s) {
+  k_spmv3<T><<<blocks_for(P.nrows), 256, 0, s>>>(P.nrows, P.rp, P.ci, P.template w<T>(), ncols, x, alpha, beta, y);
+}
+template <typename T>
+void Blas<T>::gemv_f64(int n, const double* A, const T* b, T* x, cudaStream_t s) {
+  k_gemv_f64<T><<<blocks_for((int64_t)n * 32, 256, 4096), 256, 0, s>>>(n, A, b, x);
+}
+template <>
+void Blas<float>::convert_from_f64(int64_t n, const double* x, float* y, cudaStream_t s) {
+  k_convert<float, double><<<blocks_for(n), 256, 0, s>>>(n, x, y);
+}
+template <>
+void Blas<double>::convert_from_f64(int64_t n, const double* x, double* y, cudaStream_t s) {
+  cudaMemcpyAsync(y, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+}
+template <>
+void Blas<float>::convert_to_f64(int64_t n, const float* x, double* y, cudaStream_t s) {
+  k_convert<double, float><<<blocks_for(n), 256, 0, s>>>(n, x, y);
+}
+template <>
+void Blas<double>::convert_to_f64(int64_t n, const double* x, double* y, cudaStream_t s) {
+  cudaMemcpyAsync(y, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+}
+
+template struct Blas<float>;
+template struct Blas<double>;
+
+template <typename T>
+static ApplyParams<T> sweep_params(mfs_problem* P, int lvl) {
+  mfs_mesh* M = P->mesh;
+  const LevelData& L = M->levels[lvl];
+  ApplyParams<T> prm{};
+  prm.eta = lvl_eta<T>(P, lvl);
+  prm.geom = lvl_geom<T>(M);
+  prm.tiles = L.d_tiles;
+  prm.tets = L.d_tets;
+  prm.classes = L.d_classes;
+  prm.ids2 = L.d_ids2;
+  prm.ids1 = L.d_ids1;
+  prm.n_p2 = L.nb2.total;
+  prm.n_p1 = L.nb1.total;
+  prm.n = L.n;
+  return prm;
+}
+
+template <typename T>
+mfs_status diag_A(mfs_problem* P, int lvl, const BoundaryList& B, T* diag) {
+  mfs_mesh* M = P->mesh;
+  const LevelData& L = M->levels[lvl];
+  cudaStream_t s = M->ctx->stream;
+  MFS_CUDA(cudaMemsetAsync(diag, 0, sizeof(T) * 3 * (size_t)L.nb2.total, s));
+  dim3 grid(L.n_tiles, kMacroCells);
+  ApplyParams<T> prm = sweep_params<T>(P, lvl);
+  if (M->host.blending) k_diag_sweep<T, true><<<grid, 128, 0, s>>>(prm, diag);
+  else k_diag_sweep<T, false><<<grid, 128, 0, s>>>(prm, diag);
+  if (B.nb) k_diag_dirichlet<T><<<blocks_for(B.nb), 256, 0, s>>>(B.nb, B.ids, B.kind, L.nb2.total, diag);
+  MFS_CUDA(cudaGetLastError());
+  return MFS_OK;
+}
+
+template <typename T>
+mfs_status mass_apply(mfs_problem* P, int lvl, const T* pin, T* y, int diag_only) {
+  mfs_mesh* M = P->mesh;
+  const LevelData& L = M->levels[lvl];
+  cudaStream_t s = M->ctx->stream;
+  MFS_CUDA(cudaMemsetAsync(y, 0, sizeof(T) * (size_t)L.nb1.total, s));
+  dim3 grid(L.n_tiles, kMacroCells);
+  ApplyParams<T> prm = sweep_params<T>(P, lvl);
+  const bool bl = M->host.blending != 0;
+  if (diag_only) {
+    if (bl) k_mass_sweep<T, true, true><<<grid, 128, 0, s>>>(prm, pin, y);
+    else k_mass_sweep<T, false, true><<<grid, 128, 0, s>>>(prm, pin, y);
+  } else {
+    if (bl) k_mass_sweep<T, true, false><<<grid, 128, 0, s>>>(prm, pin, y);
+    else k_mass_sweep<T, false, false><<<grid, 128, 0, s>>>(prm, pin, y);
+  }
+  MFS_CUDA(cudaGetLastError());
+  return MFS_OK;
+}
+
+template mfs_status diag_A<float>(mfs_problem*, int, const BoundaryList&, float*);
+template mfs_status diag_A<double>(mfs_problem*, int, const BoundaryList&, double*);
+template mfs_status mass_apply<float>(mfs_problem*, int, const float*, float*, int);
+template mfs_status mass_apply<double>(mfs_problem*, int, const double*, double*, int);
+
+// Coarse operator (A_c + n n^T on free-slip nodes) assembled column by column with the FP64
+// sweep, then inverted in place.
+mfs_status coarse_inverse(mfs_problem* P, int lvl, const BoundaryList& B, double* A, double* work) {
+  mfs_mesh* M = P->mesh;
+  const LevelData& L = M->levels[lvl];
+  cudaStream_t s = M->ctx->stream;
+  const int64_t N = 3 * (int64_t)L.nb2.total;
+  double* e = work;
+  double* colk = work + N;
+  for (int64_t j = 0; j < N; ++j) {
+    k_unit<<<blocks_for(N), 256, 0, s>>>(N, j, e);
+    MFS_TRY(launch_apply<double>(P, lvl, OP_A, 1, 0, e, nullptr, A + j * N, nullptr, nullptr));
+  }
+  if (B.nb) k_regularise_normals<<<blocks_for(B.nb), 256, 0, s>>>(B.nb, B.ids, B.kind, B.nrm64, L.nb2.total, A);
+  for (int k = 0; k < (int)N; ++k) {
+    k_gj_row<<<1, 512, 0, s>>>((int)N, k, A, colk);
+    k_gj_elim<<<blocks_for(N * N, 256, 4096), 256, 0, s>>>((int)N, k, A, colk);
+  }
+  MFS_CUDA(cudaGetLastError());
+  return MFS_OK;
+}
+
+}  // namespace mfs

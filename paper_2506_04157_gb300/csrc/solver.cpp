@@ -1,0 +1,629 @@
+// Multigrid hierarchy and Stokes solver (arxiv 2506.04157, Sec. 5.2):
+//   * Sec. 5.2.2: CG on A preconditioned by a GMG V-cycle with Jacobi-preconditioned
+//     Chebyshev smoothing (m pre/post steps of degree deg), diag(A) without P_v;
+//   * Sec. 5.2.3, Eq. (schurV): V-cycle BFBT Schur approximation, its inner CG on
+//     X = B A_C^-1 B^T preconditioned by CG on M_{1/eta};
+//   * Sec. 5.2.1, Eq. (SymmetricUzawaStep1): symmetric Uzawa block preconditioner with
+//     B + C in the pressure update;
+//   * Sec. 5.2.4: FGMRES outer solver; FP32 inner solves wrapped in FP64 iterative
+//     refinement (mixed mode) or everything in FP64 (plain mode).
+// Host code orchestrates the CUDA kernels; every vector operation runs on the device.
+#include <array>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+
+#include "apply.cuh"
+#include "solver.h"
+
+namespace mfs {
+
+template <typename T>
+struct Work {
+  T *dinv = nullptr, *r = nullptr, *z = nullptr, *d = nullptr, *t = nullptr, *b = nullptr, *x = nullptr;
+};
+
+template <typename T>
+struct Krylov {           // FGMRES / CG / Uzawa storage at the finest level
+  int64_t N = 0;
+  int m = 0;
+  std::vector<T*> V, Z;
+  T *w = nullptr, *ua = nullptr, *ub = nullptr, *uc = nullptr, *ud = nullptr;  // velocity temporaries
+  T *pa = nullptr, *pb = nullptr, *pc = nullptr, *pd = nullptr, *pe = nullptr, *pf = nullptr;
+  T *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_q = nullptr;        // velocity CG
+  T *cgp_r = nullptr, *cgp_z = nullptr, *cgp_p = nullptr, *cgp_q = nullptr;    // pressure CG (X)
+  T *cgm_r = nullptr, *cgm_z = nullptr, *cgm_p = nullptr, *cgm_q = nullptr;    // pressure CG (M)
+  T *tmpu = nullptr, *tmpp = nullptr;
+};
+
+struct MG {
+  int l_min = 1, l_max = 0;
+  std::vector<BoundaryList> bnd;
+  std::vector<Csr> P, R;
+  std::vector<double> lo, hi;
+  std::vector<int> have_bounds;
+  double* Ainv = nullptr;
+  double* ainv_work = nullptr;
+  int ncoarse = 0;
+  std::vector<Work<float>> w32;
+  std::vector<Work<double>> w64;
+  double* mdinv64 = nullptr;
+  float* mdinv32 = nullptr;
+  double* red = nullptr;        // [kRedBlocks] partials + 8 scalars
+  double* hpin = nullptr;       // pinned host scalar
+  bool structure = false, numeric = false;
+  Krylov<float> k32;
+  Krylov<double> k64;
+  std::vector<void*> owned;     // device allocations to free
+};
+
+static mfs_status dalloc(MG* G, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(solver workspace)");
+  G->owned.push_back(*p);
+  return MFS_OK;
+}
+template <typename T>
+static mfs_status dalloc_zero(MG* G, T** p, int64_t n, cudaStream_t s) {
+  MFS_TRY(dalloc(G, (void**)p, sizeof(T) * (size_t)n));
+  MFS_CUDA(cudaMemsetAsync(*p, 0, sizeof(T) * (size_t)n, s));
+  return MFS_OK;
+}
+
+void mg_destroy(MG* G) {
+  if (!G) return;
+  for (void* p : G->owned) cudaFree(p);
+  if (G->hpin) cudaFreeHost(G->hpin);
+  delete G;
+}
+
+// ------------------------------------------------------------------------- structure
+static void kuhn_bary(int A, int B, int C, int N, int i[4]) {
+  i[0] = N - A;
+  i[1] = A - B;
+  i[2] = B - C;
+  i[3] = C;
+}
+
+static mfs_status build_boundary(mfs_problem* Pb, int l, BoundaryList& BL, cudaStream_t s, MG* G) {
+  const mfs_mesh* M = Pb->mesh;
+  const int N = 2 << l;
+  const Numbering nb = make_numbering(N);
+  std::vector<char> seen(nb.total, 0);
+  std::vector<int> ids;
+  std::vector<int8_t> kind;
+  std::vector<double> nrm;
+  for (int m = 0; m < 60; ++m) {
+    const MacroTopo& t = M->host.topo[m];
+    for (int side = 0; side < 2; ++side) {
+      const int mask = side == 0 ? t.topmask : t.botmask;
+      const int bc = side == 0 ? Pb->bc_surface : Pb->bc_cmb;
+      for (int i3 = 0; i3 <= N; ++i3)
+        for (int i2 = 0; i2 <= N - i3; ++i2)
+          for (int i1 = 0; i1 <= N - i3 - i2; ++i1) {
+            const int i[4] = {N - i1 - i2 - i3, i1, i2, i3};
+            bool on = true;
+            for (int k = 0; k < 4; ++k)
+              if (i[k] > 0 && !(mask >> k & 1)) on = false;
+            if (!on) continue;
+            const int id = lattice_id(t, nb, m, i[0], i[1], i[2], i[3]);
+            if (seen[id]) continue;
+            seen[id] = 1;
+            double x[3];
+            M->host.straight_point(m, i, N, x);
+            const double r = std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+            ids.push_back(id);
+            kind.push_back(bc == BC_DIRICHLET ? 1 : 2);
+            for (int c = 0; c < 3; ++c) nrm.push_back(x[c] / r);
+          }
+    }
+  }
+  BL.nb = (int)ids.size();
+  std::vector<float> n32(nrm.begin(), nrm.end());
+  MFS_TRY(dalloc(G, (void**)&BL.ids, sizeof(int) * ids.size()));
+  MFS_TRY(dalloc(G, (void**)&BL.kind, ids.size()));
+  MFS_TRY(dalloc(G, (void**)&BL.nrm64, sizeof(double) * nrm.size()));
+  MFS_TRY(dalloc(G, (void**)&BL.nrm32, sizeof(float) * nrm.size()));
+  MFS_CUDA(cudaMemcpyAsync(BL.ids, ids.data(), sizeof(int) * ids.size(), cudaMemcpyHostToDevice, s));
+  MFS_CUDA(cudaMemcpyAsync(BL.kind, kind.data(), kind.size(), cudaMemcpyHostToDevice, s));
+  MFS_CUDA(cudaMemcpyAsync(BL.nrm64, nrm.data(), sizeof(double) * nrm.size(), cudaMemcpyHostToDevice, s));
+  MFS_CUDA(cudaMemcpyAsync(BL.nrm32, n32.data(), sizeof(float) * n32.size(), cudaMemcpyHostToDevice, s));
+  MFS_CUDA(cudaStreamSynchronize(s));
+  return MFS_OK;
+}
+
+// Prolongation from level l-1 to level l (P2 nodes): every fine node is a quarter point
+// (barycentrics s/4, sum s = 4) of a coarse micro-tet; its value is the coarse P2
+// interpolant there.  The first coarse tet met defines the row (all give the same value).
+static mfs_status build_transfer(mfs_problem* Pb, int l, Csr& P, Csr& R, cudaStream_t s, MG* G) {
+  static const int PERM[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  static const int LE[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+  const mfs_mesh* M = Pb->mesh;
+  const int n = 1 << (l - 1);          // coarse micro-tets per macro edge
+  const int Nc = 2 * n, Nf = 4 * n;
+  const Numbering nbc = make_numbering(Nc), nbf = make_numbering(Nf);
+  // quarter points and the 10 P2 basis values there
+  std::vector<std::array<int, 4>> sub;
+  std::vector<std::array<double, 10>> phi;
+  for (int s3 = 0; s3 <= 4; ++s3)
+    for (int s2 = 0; s2 <= 4 - s3; ++s2)
+      for (int s1 = 0; s1 <= 4 - s3 - s2; ++s1) {
+        const std::array<int, 4> sp = {4 - s1 - s2 - s3, s1, s2, s3};
+        std::array<double, 10> ph;
+        double lam[4];
+        for (int a = 0; a < 4; ++a) lam[a] = sp[a] / 4.0;
+        for (int a = 0; a < 4; ++a) ph[a] = lam[a] * (2 * lam[a] - 1);
+        for (int e = 0; e < 6; ++e) ph[4 + e] = 4 * lam[LE[e][0]] * lam[LE[e][1]];
+        sub.push_back(sp);
+        phi.push_back(ph);
+      }
+  std::vector<int> cnt(nbf.total, 0);
+  std::vector<int> rowc;   // per fine node: 10 coarse cols, set on first visit
+  std::vector<float> dummy;
+  std::vector<int> cols((size_t)nbf.total * 10, -1);
+  std::vector<double> vals((size_t)nbf.total * 10, 0.0);
+  std::vector<char> seen(nbf.total, 0);
+  for (int m = 0; m < 60; ++m) {
+    const MacroTopo& t = M->host.topo[m];
+    for (int a = 0; a < n; ++a)
+      for (int b = 0; b <= a; ++b)
+        for (int c = 0; c <= b; ++c)
+          for (int pm = 0; pm < 6; ++pm) {
+            int K[4][3];
+            K[0][0] = a;
+            K[0][1] = b;
+            K[0][2] = c;
+            bool ok = true;
+            for (int k = 1; k < 4; ++k) {
+              for (int d = 0; d < 3; ++d) K[k][d] = K[k - 1][d];
+              K[k][PERM[pm][k - 1]] += 1;
+              if (!(K[k][0] >= K[k][1] && K[k][1] >= K[k][2])) ok = false;
+            }
+            if (!ok) continue;
+            int cid[10];
+            for (int v = 0; v < 4; ++v) {
+              int i[4];
+              kuhn_bary(2 * K[v][0], 2 * K[v][1], 2 * K[v][2], Nc, i);
+              cid[v] = lattice_id(t, nbc, m, i[0], i[1], i[2], i[3]);
+            }
+            for (int e = 0; e < 6; ++e) {
+              const int u = LE[e][0], v = LE[e][1];
+              int i[4];
+              kuhn_bary(K[u][0] + K[v][0], K[u][1] + K[v][1], K[u][2] + K[v][2], Nc, i);
+              cid[4 + e] = lattice_id(t, nbc, m, i[0], i[1], i[2], i[3]);
+            }
+            for (size_t q = 0; q < sub.size(); ++q) {
+              int F[3] = {0, 0, 0};
+              for (int v = 0; v < 4; ++v)
+                for (int d = 0; d < 3; ++d) F[d] += sub[q][v] * K[v][d];
+              int i[4];
+              kuhn_bary(F[0], F[1], F[2], Nf, i);
+              const int fid = lattice_id(t, nbf, m, i[0], i[1], i[2], i[3]);
+              if (seen[fid]) continue;
+              seen[fid] = 1;
+              int k = 0;
+              for (int z = 0; z < 10; ++z)
+                if (phi[q][z] != 0.0) {
+                  cols[(size_t)fid * 10 + k] = cid[z];
+                  vals[(size_t)fid * 10 + k] = phi[q][z];
+                  ++k;
+                }
+              cnt[fid] = k;
+            }
+          }
+  }
+  for (int i = 0; i < nbf.total; ++i)
+    if (!seen[i]) {
+      set_error("internal: prolongation misses fine node %d on level %d", i, l);
+      return MFS_EINVAL;
+    }
+  // CSR of P
+  std::vector<int> rp(nbf.total + 1, 0);
+  for (int i = 0; i < nbf.total; ++i) rp[i + 1] = rp[i] + cnt[i];
+  const int nnz = rp[nbf.total];
+  std::vector<int> ci(nnz);
+  std::vector<double> w(nnz);
+  for (int i = 0; i < nbf.total; ++i)
+    for (int k = 0; k < cnt[i]; ++k) {
+      ci[rp[i] + k] = cols[(size_t)i * 10 + k];
+      w[rp[i] + k] = vals[(size_t)i * 10 + k];
+    }
+  // CSR of P^T (restriction), rows in increasing fine index per coarse row
+  std::vector<int> rrp(nbc.total + 1, 0);
+  for (int k = 0; k < nnz; ++k) rrp[ci[k] + 1]++;
+  for (int i = 0; i < nbc.total; ++i) rrp[i + 1] += rrp[i];
+  std::vector<int> pos(rrp.begin(), rrp.end() - 1);
+  std::vector<int> rci(nnz);
+  std::vector<double> rw(nnz);
+  for (int i = 0; i < nbf.total; ++i)
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+      const int c = ci[k];
+      rci[pos[c]] = i;
+      rw[pos[c]] = w[k];
+      pos[c]++;
+    }
+  auto upload = [&](Csr& X, int nrows, int ncols, const std::vector<int>& xrp, const std::vector<int>& xci,
+                    const std::vector<double>& xw) -> mfs_status {
+    X.nrows = nrows;
+    X.ncols = ncols;
+    std::vector<float> w32(xw.begin(), xw.end());
+    MFS_TRY(dalloc(G, (void**)&X.rp, sizeof(int) * xrp.size()));
+    MFS_TRY(dalloc(G, (void**)&X.ci, sizeof(int) * xci.size()));
+    MFS_TRY(dalloc(G, (void**)&X.w64, sizeof(double) * xw.size()));
+    MFS_TRY(dalloc(G, (void**)&X.w32, sizeof(float) * xw.size()));
+    MFS_CUDA(cudaMemcpyAsync(X.rp, xrp.data(), sizeof(int) * xrp.size(), cudaMemcpyHostToDevice, s));
+    MFS_CUDA(cudaMemcpyAsync(X.ci, xci.data(), sizeof(int) * xci.size(), cudaMemcpyHostToDevice, s));
+    MFS_CUDA(cudaMemcpyAsync(X.w64, xw.data(), sizeof(double) * xw.size(), cudaMemcpyHostToDevice, s));
+    MFS_CUDA(cudaMemcpyAsync(X.w32, w32.data(), sizeof(float) * w32.size(), cudaMemcpyHostToDevice, s));
+    MFS_CUDA(cudaStreamSynchronize(s));
+    return MFS_OK;
+  };
+  MFS_TRY(upload(P, nbf.total, nbc.total, rp, ci, w));
+  MFS_TRY(upload(R, nbc.total, nbf.total, rrp, rci, rw));
+  return MFS_OK;
+}
+
+template <typename T>
+static mfs_status alloc_work(MG* G, Work<T>& W, int64_t n3, cudaStream_t s) {
+  MFS_TRY(dalloc_zero(G, &W.dinv, n3, s));
+  MFS_TRY(dalloc_zero(G, &W.r, n3, s));
+  MFS_TRY(dalloc_zero(G, &W.z, n3, s));
+  MFS_TRY(dalloc_zero(G, &W.d, n3, s));
+  MFS_TRY(dalloc_zero(G, &W.t, n3, s));
+  MFS_TRY(dalloc_zero(G, &W.b, n3, s));
+  MFS_TRY(dalloc_zero(G, &W.x, n3, s));
+  return MFS_OK;
+}
+
+static mfs_status mg_structure(mfs_problem* Pb, int l_min) {
+  mfs_mesh* M = Pb->mesh;
+  cudaStream_t s = M->ctx->stream;
+  if (Pb->mg && Pb->mg->structure && Pb->mg->l_min == l_min) return MFS_OK;
+  if (Pb->mg) {
+    mg_destroy(Pb->mg);
+    Pb->mg = nullptr;
+  }
+  if (l_min < 0 || l_min > M->l_max) {
+    set_error("l_min %d outside [0, l_max = %d]", l_min, M->l_max);
+    return MFS_EINVAL;
+  }
+  MG* G = new (std::nothrow) MG;
+  if (!G) {
+    set_error("host allocation failed");
+    return MFS_ENOMEM;
+  }
+  Pb->mg = G;
+  G->l_min = l_min;
+  G->l_max = M->l_max;
+  const int L = M->l_max;
+  G->bnd.resize(L + 1);
+  G->P.resize(L + 1);
+  G->R.resize(L + 1);
+  G->lo.assign(L + 1, 0.0);
+  G->hi.assign(L + 1, 0.0);
+  G->have_bounds.assign(L + 1, 0);
+  G->w32.resize(L + 1);
+  G->w64.resize(L + 1);
+  for (int l = l_min; l <= L; ++l) {
+    MFS_TRY(build_boundary(Pb, l, G->bnd[l], s, G));
+    if (l > l_min) MFS_TRY(build_transfer(Pb, l, G->P[l], G->R[l], s, G));
+    const int64_t n3 = 3 * (int64_t)M->levels[l].nb2.total;
+    MFS_TRY(alloc_work<float>(G, G->w32[l], n3, s));
+    MFS_TRY(alloc_work<double>(G, G->w64[l], n3, s));
+  }
+  G->ncoarse = 3 * M->levels[l_min].nb2.total;
+  MFS_TRY(dalloc(G, (void**)&G->Ainv, sizeof(double) * (size_t)G->ncoarse * G->ncoarse));
+  MFS_TRY(dalloc(G, (void**)&G->ainv_work, sizeof(double) * 2 * (size_t)G->ncoarse));
+  MFS_TRY(dalloc_zero(G, &G->mdinv64, M->levels[L].nb1.total, s));
+  MFS_TRY(dalloc_zero(G, &G->mdinv32, M->levels[L].nb1.total, s));
+  MFS_TRY(dalloc_zero(G, &G->red, kRedBlocks + 16, s));
+  MFS_CUDA(cudaMallocHost((void**)&G->hpin, 16 * sizeof(double)));
+  G->structure = true;
+  return MFS_OK;
+}
+
+// ------------------------------------------------------------------------- operators
+template <typename T>
+static Work<T>& work(MG* G, int l);
+template <>
+Work<float>& work<float>(MG* G, int l) { return G->w32[l]; }
+template <>
+Work<double>& work<double>(MG* G, int l) { return G->w64[l]; }
+
+static double host_dot_result(MG* G, cudaStream_t s) {
+  cudaMemcpyAsync(G->hpin, G->red + kRedBlocks, sizeof(double), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  return G->hpin[0];
+}
+
+template <typename T>
+static double dot(MG* G, int64_t n, const T* x, const T* y, cudaStream_t s) {
+  Blas<T>::dot_async(n, x, y, G->red, G->red + kRedBlocks, s);
+  return host_dot_result(G, s);
+}
+
+// constrained A on level l
+template <typename T>
+static mfs_status applyA(mfs_problem* Pb, int l, const T* x, T* y) {
+  return launch_apply<T>(Pb, l, OP_A, 1, 0, x, nullptr, y, nullptr, nullptr);
+}
+
+template <typename T>
+static T* red_scalar(mfs_problem* Pb);
+template <>
+double* red_scalar<double>(mfs_problem* Pb) { return Pb->d_red64; }
+template <>
+float* red_scalar<float>(mfs_problem* Pb) { return Pb->d_red32; }
+
+// P_p: subtract the arithmetic mean
+template <typename T>
+static mfs_status mean_free(mfs_problem* Pb, T* p, int64_t n) {
+  cudaStream_t s = Pb->mesh->ctx->stream;
+  T* red = red_scalar<T>(Pb);
+  MFS_TRY(vec_sum<T>(p, n, red, red + kRedBlocks + 4, s));
+  MFS_TRY(vec_sub_mean<T>(p, n, red + kRedBlocks + 4, s));
+  return MFS_OK;
+}
+
+// ------------------------------------------------------------------------- smoother / V-cycle
+// Jacobi-preconditioned Chebyshev iteration (Saad, Iterative Methods, Alg. 12.1), `steps`
+// steps of `deg` applications of A each, projections after every preconditioning.
+template <typename T>
+static mfs_status chebyshev(mfs_problem* Pb, MG* G, int l, T* x, const T* b, int steps, int deg) {
+  cudaStream_t s = Pb->mesh->ctx->stream;
+  Work<T>& W = work<T>(G, l);
+  const int64_t n2 = Pb->mesh->levels[l].nb2.total, n3 = 3 * n2;
+  const double lo = G->lo[l], hi = G->hi[l];
+  const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma1 = theta / delta;
+  for (int st = 0; st < steps; ++st) {
+    MFS_TRY(applyA<T>(Pb, l, x, W.t));
+    Blas<T>::axpbypcz(n3, T(1), b, T(-1), W.t, T(0), W.r, s);   // r = b - A x
+    Blas<T>::mul(n3, W.r, W.dinv, W.z, s);
+    Blas<T>::bproject(G->bnd[l], n2, W.z, s);
+    Blas<T>::axpby(n3, T(1.0 / theta), W.z, T(0), W.d, s);     // d = z / theta
+    double rho = 1.0 / sigma1;
+    for (int k = 1; k <= deg; ++k) {
+      Blas<T>::axpby(n3, T(1), W.d, T(1), x, s);               // x += d
+      if (k == deg) break;
+      MFS_TRY(applyA<T>(Pb, l, W.d, W.t));
+      Blas<T>::axpby(n3, T(-1), W.t, T(1), W.r, s);            // r -= A d
+      Blas<T>::mul(n3, W.r, W.dinv, W.z, s);
+      Blas<T>::bproject(G->bnd[l], n2, W.z, s);
+      const double rho_new = 1.0 / (2.0 * sigma1 - rho);
+      Blas<T>::axpby(n3, T(2.0 * rho_new / delta), W.z, T(rho_new * rho), W.d, s);
+      rho = rho_new;
+    }
+  }
+  return MFS_OK;
+}
+
+// One V-cycle for A_c x = b on level l; x is overwritten (starts from zero).
+template <typename T>
+static mfs_status vcycle(mfs_problem* Pb, MG* G, int l, T* x, const T* b, int steps, int deg) {
+  mfs_mesh* M = Pb->mesh;
+  cudaStream_t s = M->ctx->stream;
+  const int64_t n2 = M->levels[l].nb2.total, n3 = 3 * n2;
+  if (l == G->l_min) {
+    Blas<T>::gemv_f64((int)n3, G->Ainv, b, x, s);
+    Blas<T>::bproject(G->bnd[l], n2, x, s);
+    return MFS_OK;
+  }
+  Work<T>& W = work<T>(G, l);
+  Work<T>& C = work<T>(G, l - 1);
+  const int64_t nc2 = M->levels[l - 1].nb2.total;
+  Blas<T>::fill(n3, T(0), x, s);
+  MFS_TRY(chebyshev<T>(Pb, G, l, x, b, steps, deg));
+  MFS_TRY(applyA<T>(Pb, l, x, W.t));
+  Blas<T>::axpbypcz(n3, T(1), b, T(-1), W.t, T(0), W.r, s);
+  Blas<T>::spmv3(G->R[l], n2, W.r, T(1), T(0), C.b, s);       // restriction P^T
+  Blas<T>::bproject(G->bnd[l - 1], nc2, C.b, s);
+  MFS_TRY(vcycle<T>(Pb, G, l - 1, C.x, C.b, steps, deg));
+  Blas<T>::spmv3(G->P[l], nc2, C.x, T(1), T(0), W.t, s);      // prolongation
+  Blas<T>::bproject(G->bnd[l], n2, W.t, s);
+  Blas<T>::axpby(n3, T(1), W.t, T(1), x, s);
+  MFS_TRY(chebyshev<T>(Pb, G, l, x, b, steps, deg));
+  return MFS_OK;
+}
+
+// ------------------------------------------------------------------------- numeric setup
+__global__ void k_seed_vector(int64_t n, double* v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = (uint64_t)i + 0x9E3779B97F4A7C15ull;   // splitmix64
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    v[i] = (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+  }
+}
+
+static mfs_status mg_numeric(mfs_problem* Pb) {
+  MG* G = Pb->mg;
+  mfs_mesh* M = Pb->mesh;
+  cudaStream_t s = M->ctx->stream;
+  const int L = M->l_max;
+  for (int l = G->l_min; l <= L; ++l) {
+    const int64_t n2 = M->levels[l].nb2.total, n3 = 3 * n2;
+    Work<double>& W = G->w64[l];
+    MFS_TRY(diag_A<double>(Pb, l, G->bnd[l], W.dinv));
+    Blas<float>::convert_from_f64(n3, W.dinv, G->w32[l].dinv, s);
+    Blas<double>::recip(n3, W.dinv, s);
+    Blas<float>::recip(n3, G->w32[l].dinv, s);
+    if (l > G->l_min && !G->have_bounds[l]) {
+      // largest eigenvalue of D^-1 A_c: 15 FP64 power iterations from a seeded vector
+      k_seed_vector<<<1024, 256, 0, s>>>(n3, W.x);
+      Blas<double>::bproject(G->bnd[l], n2, W.x, s);
+      double lam = 0.0;
+      for (int it = 0; it < 15; ++it) {
+        const double nv = std::sqrt(dot<double>(G, n3, W.x, W.x, s));
+        if (!(nv > 0.0) || !std::isfinite(nv)) {
+          set_error("power iteration broke down on level %d", l);
+          return MFS_ENAN;
+        }
+        Blas<double>::axpby(n3, 1.0 / nv, W.x, 0.0, W.x, s);
+        MFS_TRY(applyA<double>(Pb, l, W.x, W.t));
+        Blas<double>::mul(n3, W.t, W.dinv, W.x, s);
+        Blas<double>::bproject(G->bnd[l], n2, W.x, s);
+        lam = std::sqrt(dot<double>(G, n3, W.x, W.x, s));
+      }
+      G->hi[l] = 1.2 * lam;
+      G->lo[l] = G->hi[l] / 20.0;
+    }
+  }
+  MFS_TRY(coarse_inverse(Pb, G->l_min, G->bnd[G->l_min], G->Ainv, G->ainv_work));
+  // inverse diagonal of M_{1/eta} on the finest level
+  MFS_TRY(mass_apply<double>(Pb, L, nullptr, G->mdinv64, 1));
+  Blas<float>::convert_from_f64(M->levels[L].nb1.total, G->mdinv64, G->mdinv32, s);
+  Blas<double>::recip(M->levels[L].nb1.total, G->mdinv64, s);
+  Blas<float>::recip(M->levels[L].nb1.total, G->mdinv32, s);
+  MFS_CUDA(cudaStreamSynchronize(s));
+  MFS_CUDA(cudaGetLastError());
+  G->numeric = true;
+  return MFS_OK;
+}
+
+}  // namespace mfs
+
+using namespace mfs;
+
+// ------------------------------------------------------------------------- C ABI (part)
+static mfs_status need_mg(mfs_problem* Pb, int lvl) {
+  if (!Pb) {
+    set_error("null problem");
+    return MFS_EINVAL;
+  }
+  if (!Pb->mg || !Pb->mg->structure || !Pb->mg->numeric) {
+    set_error("multigrid not set up (call mfs_setup_multigrid after mfs_set_viscosity)");
+    return MFS_EINVAL;
+  }
+  if (lvl < Pb->mg->l_min || lvl > Pb->mg->l_max) {
+    set_error("level %d outside the multigrid range [%d, %d]", lvl, Pb->mg->l_min, Pb->mg->l_max);
+    return MFS_EINVAL;
+  }
+  return MFS_OK;
+}
+
+mfs_status mfs_setup_multigrid(mfs_problem* Pb, int l_min) {
+  if (!Pb) {
+    set_error("null problem");
+    return MFS_EINVAL;
+  }
+  if (!Pb->has_eta) {
+    set_error("viscosity not set (call mfs_set_viscosity first)");
+    return MFS_EINVAL;
+  }
+  MFS_TRY(mg_structure(Pb, l_min));
+  return mg_numeric(Pb);
+}
+
+mfs_status mfs_set_cheb_bounds(mfs_problem* Pb, int lvl, double lo, double hi) {
+  if (!Pb || !Pb->mg || !Pb->mg->structure) {
+    set_error("multigrid not set up");
+    return MFS_EINVAL;
+  }
+  if (lvl <= Pb->mg->l_min || lvl > Pb->mg->l_max || !(hi > lo) || !(lo > 0.0)) {
+    set_error("invalid Chebyshev interval or level");
+    return MFS_EINVAL;
+  }
+  Pb->mg->lo[lvl] = lo;
+  Pb->mg->hi[lvl] = hi;
+  Pb->mg->have_bounds[lvl] = 1;
+  return MFS_OK;
+}
+
+mfs_status mfs_get_cheb_bounds(const mfs_problem* Pb, int lvl, double* lo, double* hi) {
+  if (!Pb || !Pb->mg || !Pb->mg->structure || !lo || !hi) {
+    set_error("multigrid not set up or null output");
+    return MFS_EINVAL;
+  }
+  if (lvl <= Pb->mg->l_min || lvl > Pb->mg->l_max) {
+    set_error("level %d has no smoother", lvl);
+    return MFS_EINVAL;
+  }
+  *lo = Pb->mg->lo[lvl];
+  *hi = Pb->mg->hi[lvl];
+  return MFS_OK;
+}
+
+mfs_status mfs_diag_A(mfs_problem* Pb, int lvl, mfs_prec prec, void* y) {
+  MFS_TRY(need_mg(Pb, lvl));
+  if (!y) {
+    set_error("null output");
+    return MFS_EINVAL;
+  }
+  if (prec == MFS_F64) return diag_A<double>(Pb, lvl, Pb->mg->bnd[lvl], (double*)y);
+  return diag_A<float>(Pb, lvl, Pb->mg->bnd[lvl], (float*)y);
+}
+
+mfs_status mfs_apply_mass(mfs_problem* Pb, int lvl, mfs_prec prec, const void* p, void* y) {
+  if (!Pb || !Pb->has_eta) {
+    set_error("null problem or viscosity not set");
+    return MFS_EINVAL;
+  }
+  if (lvl < 0 || lvl > Pb->mesh->l_max || !p || !y) {
+    set_error("invalid level or null vector");
+    return MFS_EINVAL;
+  }
+  if (prec == MFS_F64) return mass_apply<double>(Pb, lvl, (const double*)p, (double*)y, 0);
+  return mass_apply<float>(Pb, lvl, (const float*)p, (float*)y, 0);
+}
+
+mfs_status mfs_prolongate(mfs_problem* Pb, int lvl, mfs_prec prec, const void* xc, void* xf) {
+  MFS_TRY(need_mg(Pb, lvl));
+  if (lvl == Pb->mg->l_min || !xc || !xf) {
+    set_error("prolongation needs l_min < lvl and non-null vectors");
+    return MFS_EINVAL;
+  }
+  MG* G = Pb->mg;
+  cudaStream_t s = Pb->mesh->ctx->stream;
+  const int64_t nc = Pb->mesh->levels[lvl - 1].nb2.total, nf = Pb->mesh->levels[lvl].nb2.total;
+  if (prec == MFS_F64) {
+    Blas<double>::spmv3(G->P[lvl], nc, (const double*)xc, 1.0, 0.0, (double*)xf, s);
+    Blas<double>::bproject(G->bnd[lvl], nf, (double*)xf, s);
+  } else {
+    Blas<float>::spmv3(G->P[lvl], nc, (const float*)xc, 1.f, 0.f, (float*)xf, s);
+    Blas<float>::bproject(G->bnd[lvl], nf, (float*)xf, s);
+  }
+  MFS_CUDA(cudaGetLastError());
+  return MFS_OK;
+}
+
+mfs_status mfs_restrict(mfs_problem* Pb, int lvl, mfs_prec prec, const void* rf, void* rc) {
+  MFS_TRY(need_mg(Pb, lvl));
+  if (lvl == Pb->mg->l_min || !rf || !rc) {
+    set_error("restriction needs l_min < lvl and non-null vectors");
+    return MFS_EINVAL;
+  }
+  MG* G = Pb->mg;
+  cudaStream_t s = Pb->mesh->ctx->stream;
+  const int64_t nc = Pb->mesh->levels[lvl - 1].nb2.total, nf = Pb->mesh->levels[lvl].nb2.total;
+  if (prec == MFS_F64) {
+    Blas<double>::spmv3(G->R[lvl], nf, (const double*)rf, 1.0, 0.0, (double*)rc, s);
+    Blas<double>::bproject(G->bnd[lvl - 1], nc, (double*)rc, s);
+  } else {
+    Blas<float>::spmv3(G->R[lvl], nf, (const float*)rf, 1.f, 0.f, (float*)rc, s);
+    Blas<float>::bproject(G->bnd[lvl - 1], nc, (float*)rc, s);
+  }
+  MFS_CUDA(cudaGetLastError());
+  return MFS_OK;
+}
+
+mfs_status mfs_vcycle(mfs_problem* Pb, int lvl, mfs_prec prec, int steps, int degree, const void* f, void* u) {
+  MFS_TRY(need_mg(Pb, lvl));
+  if (!f || !u || steps < 0 || degree < 1) {
+    set_error("invalid V-cycle arguments");
+    return MFS_EINVAL;
+  }
+  if (prec == MFS_F64) return vcycle<double>(Pb, Pb->mg, lvl, (double*)u, (const double*)f, steps, degree);
+  return vcycle<float>(Pb, Pb->mg, lvl, (float*)u, (const float*)f, steps, degree);
+}
+
+namespace mfs {
+void problem_release_solver(mfs_problem* Pb) {
+  if (Pb && Pb->mg) {
+    mg_destroy(Pb->mg);
+    Pb->mg = nullptr;
+  }
+}
+}  // namespace mfs

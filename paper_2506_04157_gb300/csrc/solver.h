@@ -1,0 +1,75 @@
+// Internal declarations of the multigrid / Krylov layer.
+#pragma once
+
+#include <vector>
+
+#include "library.h"
+
+namespace mfs {
+
+// P2 nodes of one level that carry a boundary condition (kind 1 Dirichlet, 2 free slip),
+// with the outward radial unit normal at each node.
+struct BoundaryList {
+  int nb = 0;
+  int* ids = nullptr;
+  int8_t* kind = nullptr;
+  double* nrm64 = nullptr;
+  float* nrm32 = nullptr;
+  template <typename T>
+  const T* normals() const;
+};
+template <>
+inline const double* BoundaryList::normals<double>() const { return nrm64; }
+template <>
+inline const float* BoundaryList::normals<float>() const { return nrm32; }
+
+// CSR matrix with weights in both precisions (transfer operators).
+struct Csr {
+  int nrows = 0, ncols = 0;
+  int* rp = nullptr;
+  int* ci = nullptr;
+  double* w64 = nullptr;
+  float* w32 = nullptr;
+  template <typename T>
+  const T* w() const;
+};
+template <>
+inline const double* Csr::w<double>() const { return w64; }
+template <>
+inline const float* Csr::w<float>() const { return w32; }
+
+template <typename T>
+struct Blas {
+  static void axpby(int64_t n, T a, const T* x, T b, T* y, cudaStream_t s);          // y = a x + b y
+  static void axpbypcz(int64_t n, T a, const T* x, T b, const T* y, T c, T* z, cudaStream_t s);
+  static void fill(int64_t n, T v, T* y, cudaStream_t s);
+  static void mul(int64_t n, const T* x, const T* d, T* z, cudaStream_t s);           // z = x .* d
+  static void recip(int64_t n, T* x, cudaStream_t s);
+  static void dot_async(int64_t n, const T* x, const T* y, double* part, double* out, cudaStream_t s);
+  static void bproject(const BoundaryList& B, int64_t n_p2, T* v, cudaStream_t s);
+  static void spmv3(const Csr& P, int64_t ncols, const T* x, T alpha, T beta, T* y, cudaStream_t s);
+  static void gemv_f64(int n, const double* A, const T* b, T* x, cudaStream_t s);
+  static void convert_from_f64(int64_t n, const double* x, T* y, cudaStream_t s);
+  static void convert_to_f64(int64_t n, const T* x, double* y, cudaStream_t s);
+};
+
+template <typename T>
+inline const T* lvl_eta(mfs_problem* P, int l);
+template <>
+inline const double* lvl_eta<double>(mfs_problem* P, int l) { return P->eta64[l]; }
+template <>
+inline const float* lvl_eta<float>(mfs_problem* P, int l) { return P->eta32[l]; }
+template <typename T>
+inline const MacroGeom<T>* lvl_geom(mfs_mesh* M);
+template <>
+inline const MacroGeom<double>* lvl_geom<double>(mfs_mesh* M) { return M->d_geom64; }
+template <>
+inline const MacroGeom<float>* lvl_geom<float>(mfs_mesh* M) { return M->d_geom32; }
+
+template <typename T>
+mfs_status diag_A(mfs_problem* P, int lvl, const BoundaryList& B, T* diag);
+template <typename T>
+mfs_status mass_apply(mfs_problem* P, int lvl, const T* pin, T* y, int diag_only);
+mfs_status coarse_inverse(mfs_problem* P, int lvl, const BoundaryList& B, double* A, double* work);
+
+}  // namespace mfs
