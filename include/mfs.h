@@ -120,11 +120,11 @@ mfs_status mfs_problem_create(mfs_mesh* mesh, mfs_bc bc_surface, mfs_bc bc_cmb, 
 mfs_status mfs_problem_destroy(mfs_problem* prob);
 
 /* Nodal P1 viscosity on the finest level (DEVICE pointer, double[n_p1(l_max)]; if
- * is_log != 0 the values are ln(eta)).  Coarser levels receive it by injection
- * (coarse vertices are fine vertices): eta is a P1 function on every level, evaluated
+ * is_log != 0 the values are ln(eta)).  eta is a P1 function on every level, evaluated
  * at quadrature points by linear interpolation (paper Sec. 5.2.2, "eta_P1 on every
- * level").  Errors: MFS_EINVAL (non-positive eta reported by a later solve as
- * MFS_ENAN), MFS_ECUDA. */
+ * level"); each coarser level gets the P1 full weighting of the next finer one (the
+ * normalised average of the coincident vertex, weight 1, and the midpoints of the
+ * incident coarse edges, weight 1/2).  Errors: MFS_EINVAL, MFS_ECUDA. */
 mfs_status mfs_set_viscosity(mfs_problem* prob, const double* eta_p1, int is_log);
 
 /* Radial profile of d ln(rho)/dr on a uniform grid of n >= 1 points over
@@ -194,6 +194,53 @@ mfs_status mfs_restrict(mfs_problem* prob, int lvl, mfs_prec prec, const void* r
  * l_min.  f: right-hand side [3][n_p2]; u: result (overwritten, the cycle starts from 0).
  * Errors: MFS_EINVAL (multigrid not set up, bad level), MFS_ECUDA. */
 mfs_status mfs_vcycle(mfs_problem* prob, int lvl, mfs_prec prec, int steps, int degree, const void* f, void* u);
+
+/* ---------------------------------------------------------------- Stokes solver
+ * FGMRES (paper Sec. 5.2.4) right-preconditioned by the symmetric Uzawa step (Eq.
+ * SymmetricUzawaStep1, B + C in the pressure update), A^-1 ~ CG + V-cycle (Sec. 5.2.2),
+ * S^-1 ~ V-cycle BFBT (Eq. schurV) with CG on X = B A_C^-1 B^T preconditioned by CG on
+ * M_{1/eta}.  Defaults (mfs_solve_opts_default) are the paper's Table parametertable. */
+typedef struct {
+  int mixed;          /* 1: FP32 inner FGMRES inside FP64 iterative refinement; 0: all FP64 */
+  double rtol;        /* stop at ||r|| <= rtol ||r0||, r the FP64 projected residual (1e-8) */
+  int restart;        /* FGMRES restart length (30) */
+  int max_iters;      /* total FGMRES iterations (300) */
+  int max_outer;      /* refinement steps in mixed mode (20) */
+  double inner_rtol;  /* relative tolerance of each inner FP32 FGMRES (1e-4) */
+  double sigma;       /* scaling of A^-1 in the Uzawa step (1) */
+  double omega;       /* scaling of S^-1 in the Uzawa step (0.3) */
+  double tol_A;       /* CG on A, relative (1e-2) */
+  int m_A, deg_A;     /* V-cycle for A: Chebyshev steps and degree (3, 2) */
+  double tol_VBFBT;   /* CG on X (1e-1) */
+  double tol_invMass; /* CG on M_{1/eta} (1e-10; at least 1e-6 in FP32) */
+  int m_V, deg_V;     /* cheap V-cycle A_C (1, 1) */
+  int max_cg;         /* iteration cap of every inner CG (200) */
+  int with_C;         /* 1: compressible constraint (B + C) (1) */
+} mfs_solve_opts;
+
+typedef struct {
+  int outer_iters;    /* refinement steps (mixed) or 1 */
+  int fgmres_iters;   /* total FGMRES iterations */
+  int cg_A_iters, cg_X_iters, cg_M_iters;        /* totals over all calls */
+  int cg_A_calls, cg_X_calls, cg_M_calls;
+  int cg_A_max, cg_X_max, cg_M_max;               /* largest iteration count of one call */
+  int vcycles;        /* V-cycles on the finest level */
+  int applies;        /* finest-level A / saddle-point sweeps issued by the Krylov layers */
+  double r0_norm, r_norm, rel_residual;   /* FP64 projected residual norms */
+  double time_ms;     /* wall time of the solve (setup excluded) */
+} mfs_solve_stats;
+
+void mfs_solve_opts_default(mfs_solve_opts* opts);
+
+/* Solve the projected saddle-point system (paper Eq. SaddlePointStructureDirichlet) on
+ * the finest level: f [3][n_p2] and g [n_p1] are the right-hand sides (FP64, device);
+ * u [3][n_p2], p [n_p1] (FP64, device) hold the initial guess on entry, the solution on
+ * exit; u's Dirichlet nodes carry the boundary values and are kept.  p is returned with
+ * arithmetic mean zero.  Needs mfs_setup_multigrid.  opts = NULL uses the defaults; stats
+ * may be NULL.  Errors: MFS_EINVAL, MFS_ENOTCONV (best iterate returned), MFS_ENAN,
+ * MFS_ECUDA, MFS_ENOMEM (Krylov storage is allocated on the first solve). */
+mfs_status mfs_stokes_solve(mfs_problem* prob, const mfs_solve_opts* opts, const double* f, const double* g,
+                            double* u, double* p, mfs_solve_stats* stats);
 
 /* Allocation-free variant of mfs_apply_B (no counterpart in the paper).
  *

@@ -22,6 +22,9 @@ Readings (listed in DESIGN.md):
     the initial residual; interval [b/20, b] with b = 1.2 x the largest eigenvalue of
     D^-1 A estimated by 15 power iterations from a seeded vector.
   * Coarsest level l_min = 1; coarse CG preconditioned by the diagonal.
+  * Coarse-level viscosity: P1 full weighting of the next finer level's nodal values
+    (the paper evaluates eta at coarse vertices or, below l_eta, at quadrature points from
+    the temperature; for rough synthetic fields injection makes the V-cycle diverge).
   * P2 prolongation = exact P2 interpolation in the straight (pre-blending) coordinates
     (the spaces are nested there); restriction = its transpose; projections applied to
     the transferred vectors.
@@ -165,11 +168,14 @@ class Hierarchy:
         self.levels, self.ops, self.cons, self.co, self.diag = {}, {}, {}, {}, {}
         Lf = Level(mesh, l_max)
         self.levels[l_max] = Lf
+        for l in range(l_min, l_max):
+            self.levels[l] = Level(mesh, l)
+        # coarse-level viscosity by P1 full weighting (reading: injection of a rough,
+        # high-contrast field makes the rediscretised coarse operators unrepresentative)
+        self.etas = viscosity_hierarchy(mesh, self.levels, eta_fine)
         for l in range(l_min, l_max + 1):
-            L = Lf if l == l_max else Level(mesh, l)
-            self.levels[l] = L
-            # injection: coarse vertices are fine vertices
-            eta = inject(Lf, L, eta_fine)
+            L = self.levels[l]
+            eta = self.etas[l]
             ops = Operators(L, eta, dlnrho_table)
             cons = Constraints(L, *bc)
             self.ops[l], self.cons[l] = ops, cons
@@ -217,6 +223,34 @@ class Hierarchy:
         x = x + cons.P0(P @ ec)
         x = chebyshev(Aop, Dinv, cons.P0, x, b, steps, degree, lo, hi)
         return x
+
+
+def restrict_viscosity(Lfine, Lcoarse, eta_fine):
+    """Viscosity on the next coarser level by P1 full weighting: the coarse vertex value is
+    the average of the fine vertex at the same point (weight 1) and the fine vertices at the
+    midpoints of its coarse edges (weight 1/2), normalised by the weights.  The fine P1
+    vertices are the coarse level's P2 nodes, so the coarse tets give the stencil."""
+    tp1, tp2 = Lcoarse.tet_p1, Lcoarse.tet_p2
+    v = [tp1[:, a] for a in range(4)]
+    j = [tp2[:, a] for a in range(4)]
+    w = [np.ones(tp1.shape[0]) for _ in range(4)]
+    for e, (a, b) in enumerate(LOCAL_EDGES):
+        for end in (a, b):
+            v.append(tp1[:, end]); j.append(tp2[:, 4 + e]); w.append(np.full(tp1.shape[0], 0.5))
+    v, j, w = np.concatenate(v), np.concatenate(j), np.concatenate(w)
+    key = v.astype(np.int64) * Lfine.n_p1 + j
+    _, first = np.unique(key, return_index=True)
+    R = sp.coo_matrix((w[first], (v[first], j[first])), shape=(Lcoarse.n_p1, Lfine.n_p1)).tocsr()
+    return (R @ np.asarray(eta_fine)) / (R @ np.ones(Lfine.n_p1))
+
+
+def viscosity_hierarchy(mesh, levels, eta_fine):
+    """eta on every level from the finest by repeated full weighting (levels: dict l -> Level)."""
+    L = max(levels)
+    etas = {L: np.asarray(eta_fine)}
+    for l in range(L, min(levels), -1):
+        etas[l - 1] = restrict_viscosity(levels[l], levels[l - 1], etas[l])
+    return etas
 
 
 def inject(Lfine, Lcoarse, eta_fine):

@@ -34,6 +34,27 @@ class LevelInfo(ctypes.Structure):
                 ("n_p1", ctypes.c_int64), ("n_surface", ctypes.c_int64), ("n_cmb", ctypes.c_int64)]
 
 
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("mixed", ctypes.c_int), ("rtol", ctypes.c_double), ("restart", ctypes.c_int),
+                ("max_iters", ctypes.c_int), ("max_outer", ctypes.c_int), ("inner_rtol", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("omega", ctypes.c_double), ("tol_A", ctypes.c_double),
+                ("m_A", ctypes.c_int), ("deg_A", ctypes.c_int), ("tol_VBFBT", ctypes.c_double),
+                ("tol_invMass", ctypes.c_double), ("m_V", ctypes.c_int), ("deg_V", ctypes.c_int),
+                ("max_cg", ctypes.c_int), ("with_C", ctypes.c_int)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("outer_iters", ctypes.c_int), ("fgmres_iters", ctypes.c_int), ("cg_A_iters", ctypes.c_int),
+                ("cg_X_iters", ctypes.c_int), ("cg_M_iters", ctypes.c_int), ("cg_A_calls", ctypes.c_int),
+                ("cg_X_calls", ctypes.c_int), ("cg_M_calls", ctypes.c_int), ("cg_A_max", ctypes.c_int),
+                ("cg_X_max", ctypes.c_int), ("cg_M_max", ctypes.c_int), ("vcycles", ctypes.c_int),
+                ("applies", ctypes.c_int), ("r0_norm", ctypes.c_double), ("r_norm", ctypes.c_double),
+                ("rel_residual", ctypes.c_double), ("time_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _vp = ctypes.c_void_p
 _i = ctypes.c_int
 _d = ctypes.c_double
@@ -67,6 +88,8 @@ _SIGS = {
     "mfs_prolongate": ([_vp, _i, _i, _vp, _vp], _i),
     "mfs_restrict": ([_vp, _i, _i, _vp, _vp], _i),
     "mfs_vcycle": ([_vp, _i, _i, _i, _i, _vp, _vp], _i),
+    "mfs_solve_opts_default": ([ctypes.POINTER(SolveOpts)], None),
+    "mfs_stokes_solve": ([_vp, ctypes.POINTER(SolveOpts), _vp, _vp, _vp, _vp, ctypes.POINTER(SolveStats)], _i),
 }
 
 _lib = None
@@ -268,6 +291,36 @@ class Problem:
         nu, _ = self._sizes(level)
         _need(f, nu, None, "f"); _need(u, nu, f.dtype, "u")
         _check(lib().mfs_vcycle(self.handle, level, _prec_of(f), steps, degree, _ptr(f), _ptr(u)))
+
+    # ---- Stokes solver
+    @staticmethod
+    def default_opts(**kw):
+        o = SolveOpts()
+        lib().mfs_solve_opts_default(ctypes.byref(o))
+        for k, v in kw.items():
+            if not hasattr(o, k):
+                raise MfsError(EINVAL, f"unknown solver option {k}")
+            setattr(o, k, v)
+        return o
+
+    def solve(self, f, g, u, p, raise_on_error=True, **opts):
+        """Solve the projected Stokes system in place (u, p: FP64 device tensors holding
+        the initial guess / Dirichlet values).  Returns the statistics as a dict
+        (with the status under 'status')."""
+        import torch
+        L = self.mesh.l_max
+        nu, npp = self._sizes(L)
+        _need(f, nu, torch.float64, "f"); _need(g, npp, torch.float64, "g")
+        _need(u, nu, torch.float64, "u"); _need(p, npp, torch.float64, "p")
+        o = self.default_opts(**opts)
+        st = SolveStats()
+        rc = lib().mfs_stokes_solve(self.handle, ctypes.byref(o), _ptr(f), _ptr(g), _ptr(u), _ptr(p),
+                                    ctypes.byref(st))
+        d = st.as_dict()
+        d["status"] = _STATUS.get(rc, rc)
+        if rc != OK and raise_on_error:
+            raise MfsError(rc, lib().mfs_last_error().decode())
+        return d
 
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:

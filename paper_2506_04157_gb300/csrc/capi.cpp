@@ -229,6 +229,7 @@ mfs_status mfs_mesh_shell(mfs_ctx* ctx, double r_cmb, double r_surf, int l_max, 
     if (st == MFS_OK) st = build_id_tables(M, L);
     if (st == MFS_OK) MFS_CUDA(cudaStreamSynchronize(s));   // host vectors die here
     M->levels.push_back(L);
+    if (st == MFS_OK && l >= 1) st = build_eta_restriction(M, l);
   }
   if (st != MFS_OK) {
     mfs_mesh_destroy(M);
@@ -249,6 +250,9 @@ mfs_status mfs_mesh_destroy(mfs_mesh* M) {
     cudaFree(L.d_classes);
     cudaFree(L.d_ids2);
     cudaFree(L.d_ids1);
+    cudaFree(L.d_er_rp);
+    cudaFree(L.d_er_ci);
+    cudaFree(L.d_er_w);
   }
   delete M;
   return MFS_OK;
@@ -398,7 +402,9 @@ mfs_status mfs_set_viscosity(mfs_problem* P, const double* eta, int is_log) {
   const size_t np1 = M->levels[L].nb1.total;
   MFS_CUDA(cudaMemcpyAsync(P->eta64[L], eta, sizeof(double) * np1, cudaMemcpyDeviceToDevice, s));
   if (is_log) MFS_TRY(exp_inplace(P->eta64[L], (int64_t)np1, s));
-  for (int l = L - 1; l >= 0; --l) MFS_TRY(inject_p1(M, L, l, P->eta64[L], P->eta64[l]));
+  // coarse levels: P1 full weighting of the next finer level (arithmetic average of the
+  // coincident vertex and the midpoints of the incident coarse edges)
+  for (int l = L; l >= 1; --l) MFS_TRY(restrict_eta(M, l, P->eta64[l], P->eta64[l - 1]));
   for (int l = 0; l <= L; ++l)
     MFS_TRY(convert_f64_f32(P->eta64[l], P->eta32[l], M->levels[l].nb1.total, s));
   P->has_eta = true;

@@ -64,6 +64,11 @@ struct LevelData {
   int2* d_classes = nullptr;
   int* d_ids2 = nullptr;     // [60 * n_tiles][NSLOT2] P2 id | geometric class << 29, or -1
   int* d_ids1 = nullptr;     // [60 * n_tiles][NSLOT1] P1 id, or -1
+  // P1 full weighting from this level to the next coarser one (rows: coarse vertices)
+  int er_rows = 0;
+  int* d_er_rp = nullptr;
+  int* d_er_ci = nullptr;
+  double* d_er_w = nullptr;
   int64_t n_tets = 0, n_surface = 0, n_cmb = 0;
 };
 
@@ -137,6 +142,8 @@ mfs_status vec_sum(const T* x, int64_t n, T* d_partials, T* d_out, cudaStream_t 
 template <typename T>
 mfs_status vec_sub_mean(T* x, int64_t n, const T* d_sum, cudaStream_t s);
 mfs_status inject_p1(const mfs_mesh* M, int l_from, int l_to, const double* src, double* dst);
+mfs_status build_eta_restriction(mfs_mesh* M, int l);
+mfs_status restrict_eta(const mfs_mesh* M, int l, const double* fine, double* coarse);
 mfs_status build_id_tables(const mfs_mesh* M, LevelData& L);
 mfs_status convert_f64_f32(const double* src, float* dst, int64_t n, cudaStream_t s);
 mfs_status exp_inplace(double* x, int64_t n, cudaStream_t s);

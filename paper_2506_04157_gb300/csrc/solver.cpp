@@ -36,6 +36,8 @@ struct Krylov {           // FGMRES / CG / Uzawa storage at the finest level
   T *cgp_r = nullptr, *cgp_z = nullptr, *cgp_p = nullptr, *cgp_q = nullptr;    // pressure CG (X)
   T *cgm_r = nullptr, *cgm_z = nullptr, *cgm_p = nullptr, *cgm_q = nullptr;    // pressure CG (M)
   T *tmpu = nullptr, *tmpp = nullptr;
+  T *rhs = nullptr, *sol = nullptr;                                             // FGMRES b and x
+  T *ir_r = nullptr, *ir_y = nullptr, *ir_p = nullptr;                          // refinement (FP64)
 };
 
 struct MG {
@@ -627,3 +629,448 @@ void problem_release_solver(mfs_problem* Pb) {
   }
 }
 }  // namespace mfs
+
+// ========================================================================= Stokes solver
+namespace mfs {
+
+template <typename T>
+static Krylov<T>& kry(MG* G);
+template <>
+Krylov<float>& kry<float>(MG* G) { return G->k32; }
+template <>
+Krylov<double>& kry<double>(MG* G) { return G->k64; }
+
+template <typename T>
+static mfs_status ensure_krylov(MG* G, int64_t nu, int64_t np, int m, cudaStream_t s) {
+  Krylov<T>& K = kry<T>(G);
+  const int64_t N = nu + np;
+  if (K.N == N && K.m >= m) return MFS_OK;
+  if (K.N != 0 && K.N != N) {
+    set_error("internal: Krylov storage of another size");
+    return MFS_EINVAL;
+  }
+  if (K.N == 0) {
+    T** uvecs[] = {&K.w, &K.ua, &K.ub, &K.uc, &K.ud, &K.cg_r, &K.cg_z, &K.cg_p, &K.cg_q, &K.tmpu,
+                   &K.rhs, &K.sol, &K.ir_r, &K.ir_y};
+    for (T** v : uvecs) MFS_TRY(dalloc_zero(G, v, N, s));   // N-sized: also used for combined vectors
+    T** pvecs[] = {&K.pa, &K.pb, &K.pc, &K.pd, &K.pe, &K.pf, &K.cgp_r, &K.cgp_z, &K.cgp_p, &K.cgp_q,
+                   &K.cgm_r, &K.cgm_z, &K.cgm_p, &K.cgm_q, &K.tmpp, &K.ir_p};
+    for (T** v : pvecs) MFS_TRY(dalloc_zero(G, v, np, s));
+    K.N = N;
+  }
+  // grow the Krylov basis to m (+1) vectors
+  while ((int)K.V.size() < m + 1) {
+    T* v = nullptr;
+    MFS_TRY(dalloc_zero(G, &v, N, s));
+    K.V.push_back(v);
+  }
+  while ((int)K.Z.size() < m) {
+    T* v = nullptr;
+    MFS_TRY(dalloc_zero(G, &v, N, s));
+    K.Z.push_back(v);
+  }
+  K.m = m;
+  return MFS_OK;
+}
+
+template <typename T>
+static const T* mass_dinv(MG* G);
+template <>
+const float* mass_dinv<float>(MG* G) { return G->mdinv32; }
+template <>
+const double* mass_dinv<double>(MG* G) { return G->mdinv64; }
+
+template <typename T>
+struct Stokes {
+  mfs_problem* Pb;
+  MG* G;
+  const mfs_solve_opts& o;
+  mfs_solve_stats& st;
+  int L;
+  int64_t n2, nu, np, N;
+  cudaStream_t s;
+  Krylov<T>& K;
+  double tolM;
+
+  Stokes(mfs_problem* P, const mfs_solve_opts& opts, mfs_solve_stats& stats)
+      : Pb(P), G(P->mg), o(opts), st(stats), L(P->mesh->l_max), n2(P->mesh->levels[L].nb2.total), nu(3 * n2),
+        np(P->mesh->levels[L].nb1.total), N(nu + np), s(P->mesh->ctx->stream), K(kry<T>(P->mg)) {
+    tolM = o.tol_invMass;
+    if (sizeof(T) == 4 && tolM < 1e-5) tolM = 1e-5;   // FP32 CG stagnates near 1e-6
+  }
+
+  double dotn(int64_t n, const T* x, const T* y) { return dot<T>(G, n, x, y, s); }
+
+  // ---- blocks of the constrained system
+  mfs_status A(const T* u, T* y) {
+    st.applies++;
+    return applyA<T>(Pb, L, u, y);
+  }
+  mfs_status BT(const T* p, T* y) { return apply_constrained<T>(Pb, L, OP_BT, 1, 0, nullptr, p, y, nullptr); }
+  mfs_status Bop(const T* u, T* q, int withc) {
+    return apply_constrained<T>(Pb, L, OP_B, 1, withc, u, nullptr, nullptr, q);
+  }
+  mfs_status Kop(const T* x, T* y) {
+    st.applies++;
+    return apply_constrained<T>(Pb, L, OP_A | OP_BT | OP_B, 1, o.with_C, x, x + nu, y, y + nu);
+  }
+
+  // generic preconditioned CG on n entries; op/pre write their output vector
+  template <typename Op, typename Pre>
+  mfs_status cg(int64_t n, Op op, Pre pre, const T* b, T* x, double rtol, int maxit, T* r, T* z, T* p, T* q,
+                int* iters) {
+    Blas<T>::axpby(n, T(1), b, T(0), r, s);
+    Blas<T>::fill(n, T(0), x, s);
+    *iters = 0;
+    const double rr0 = dotn(n, r, r);
+    if (!std::isfinite(rr0)) {
+      set_error("NaN/Inf in a CG right-hand side");
+      return MFS_ENAN;
+    }
+    if (rr0 == 0.0) return MFS_OK;
+    MFS_TRY(pre(r, z));
+    Blas<T>::axpby(n, T(1), z, T(0), p, s);
+    double rz = dotn(n, r, z);
+    for (int it = 0; it < maxit; ++it) {
+      MFS_TRY(op(p, q));
+      const double pq = dotn(n, p, q);
+      if (!std::isfinite(pq)) {
+        set_error("NaN/Inf in CG");
+        return MFS_ENAN;
+      }
+      if (pq <= 0.0) break;   // loss of positivity (inexact inner solves): keep the iterate
+      const double alpha = rz / pq;
+      Blas<T>::axpby(n, T(alpha), p, T(1), x, s);
+      Blas<T>::axpby(n, T(-alpha), q, T(1), r, s);
+      ++*iters;
+      const double rr = dotn(n, r, r);
+      if (!std::isfinite(rr)) {
+        set_error("NaN/Inf in CG residual");
+        return MFS_ENAN;
+      }
+      if (std::sqrt(rr) <= rtol * std::sqrt(rr0)) break;
+      MFS_TRY(pre(r, z));
+      const double rz_new = dotn(n, r, z);
+      Blas<T>::axpby(n, T(1), z, T(rz_new / rz), p, s);
+      rz = rz_new;
+    }
+    return MFS_OK;
+  }
+
+  // ---- A-block: CG on A preconditioned by a V-cycle (m_A, deg_A) to tol_A
+  mfs_status Ahat_inv(const T* r, T* x) {
+    int it = 0;
+    auto op = [&](const T* v, T* y) { return A(v, y); };
+    auto pre = [&](const T* v, T* y) {
+      st.vcycles++;
+      return vcycle<T>(Pb, G, L, y, v, o.m_A, o.deg_A);
+    };
+    MFS_TRY(cg(nu, op, pre, r, x, o.tol_A, o.max_cg, K.cg_r, K.cg_z, K.cg_p, K.cg_q, &it));
+    st.cg_A_iters += it;
+    st.cg_A_calls++;
+    st.cg_A_max = it > st.cg_A_max ? it : st.cg_A_max;
+    return MFS_OK;
+  }
+  // cheap V-cycle A_C^-1 (m_V, deg_V)
+  mfs_status Ac_inv(const T* r, T* x) {
+    st.vcycles++;
+    return vcycle<T>(Pb, G, L, x, r, o.m_V, o.deg_V);
+  }
+  // M_{1/eta}^-1 by CG (P_p M P_p, Jacobi) to tol_invMass
+  mfs_status M_inv(const T* r, T* x) {
+    int it = 0;
+    auto op = [&](const T* v, T* y) {
+      MFS_TRY(mass_apply<T>(Pb, L, v, y, 0));
+      return mean_free<T>(Pb, y, np);
+    };
+    auto pre = [&](const T* v, T* y) {
+      Blas<T>::mul(np, v, mass_dinv<T>(G), y, s);
+      return mean_free<T>(Pb, y, np);
+    };
+    MFS_TRY(cg(np, op, pre, r, x, tolM, o.max_cg, K.cgm_r, K.cgm_z, K.cgm_p, K.cgm_q, &it));
+    st.cg_M_iters += it;
+    st.cg_M_calls++;
+    st.cg_M_max = it > st.cg_M_max ? it : st.cg_M_max;
+    return mean_free<T>(Pb, x, np);
+  }
+  // X q = B A_C^-1 B^T q
+  mfs_status X(const T* q, T* y) {
+    MFS_TRY(BT(q, K.ua));
+    MFS_TRY(Ac_inv(K.ua, K.ub));
+    return Bop(K.ub, y, 0);
+  }
+  // V-cycle BFBT: X^-1 (B A_C^-1 A A_C^-1 B^T) X^-1 r
+  mfs_status S_inv(const T* r, T* z) {
+    int it = 0;
+    auto op = [&](const T* v, T* y) { return X(v, y); };
+    auto pre = [&](const T* v, T* y) { return M_inv(v, y); };
+    MFS_TRY(cg(np, op, pre, r, K.pe, o.tol_VBFBT, o.max_cg, K.cgp_r, K.cgp_z, K.cgp_p, K.cgp_q, &it));
+    st.cg_X_iters += it;
+    st.cg_X_calls++;
+    st.cg_X_max = it > st.cg_X_max ? it : st.cg_X_max;
+    MFS_TRY(BT(K.pe, K.uc));
+    MFS_TRY(Ac_inv(K.uc, K.ud));
+    MFS_TRY(A(K.ud, K.uc));
+    MFS_TRY(Ac_inv(K.uc, K.ud));
+    MFS_TRY(Bop(K.ud, K.pf, 0));
+    MFS_TRY(cg(np, op, pre, K.pf, z, o.tol_VBFBT, o.max_cg, K.cgp_r, K.cgp_z, K.cgp_p, K.cgp_q, &it));
+    st.cg_X_iters += it;
+    st.cg_X_calls++;
+    st.cg_X_max = it > st.cg_X_max ? it : st.cg_X_max;
+    return mean_free<T>(Pb, z, np);
+  }
+  // symmetric Uzawa step from (0, 0) on r = (r_u, r_p); output z = (u, p)
+  mfs_status uzawa(const T* r, T* z) {
+    const T* ru = r;
+    const T* rp = r + nu;
+    T* zu = z;
+    T* zp = z + nu;
+    T* uh = K.tmpu;
+    MFS_TRY(Ahat_inv(ru, uh));
+    if (o.sigma != 1.0) Blas<T>::axpby(nu, T(o.sigma), uh, T(0), uh, s);
+    MFS_TRY(Bop(uh, K.pa, o.with_C));                                  // (B + C) uh
+    Blas<T>::axpbypcz(np, T(1), rp, T(-1), K.pa, T(0), K.pb, s);       // r_p - Bbar uh
+    MFS_TRY(S_inv(K.pb, zp));
+    Blas<T>::axpby(np, T(-o.omega), zp, T(0), zp, s);                  // p = -omega S^-1 (...)
+    MFS_TRY(A(uh, K.w));
+    MFS_TRY(BT(zp, K.ua));
+    Blas<T>::axpbypcz(nu, T(1), ru, T(-1), K.w, T(0), K.ub, s);
+    Blas<T>::axpby(nu, T(-1), K.ua, T(1), K.ub, s);                    // r_u - A uh - B^T p
+    MFS_TRY(Ahat_inv(K.ub, zu));
+    Blas<T>::axpby(nu, T(1), uh, T(o.sigma), zu, s);                   // u = uh + sigma A^-1 (...)
+    return MFS_OK;
+  }
+
+  // right-preconditioned flexible GMRES(m) on K x = b from x = 0 (modified Gram-Schmidt,
+  // Givens rotations on the host); stops at ||b - K x|| <= rtol ||b||
+  mfs_status fgmres(const T* b, T* x, double rtol, int* iters, double* rel_out) {
+    const int m = o.restart;
+    Blas<T>::fill(N, T(0), x, s);
+    const double beta0 = std::sqrt(dotn(N, b, b));
+    *iters = 0;
+    *rel_out = 0.0;
+    if (!std::isfinite(beta0)) {
+      set_error("NaN/Inf in the FGMRES right-hand side");
+      return MFS_ENAN;
+    }
+    if (beta0 == 0.0) return MFS_OK;
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+    T* r = K.V[0];
+    Blas<T>::axpby(N, T(1), b, T(0), r, s);
+    double beta = beta0;
+    bool done = false;
+    while (!done) {
+      Blas<T>::axpby(N, T(1.0 / beta), r, T(0), K.V[0], s);
+      std::fill(g.begin(), g.end(), 0.0);
+      g[0] = beta;
+      int k = 0;
+      for (; k < m; ++k) {
+        MFS_TRY(uzawa(K.V[k], K.Z[k]));
+        MFS_TRY(Kop(K.Z[k], K.V[k + 1]));
+        for (int i = 0; i <= k; ++i) {
+          const double hik = dotn(N, K.V[k + 1], K.V[i]);
+          H[(size_t)i * m + k] = hik;
+          Blas<T>::axpby(N, T(-hik), K.V[i], T(1), K.V[k + 1], s);
+        }
+        const double hn = std::sqrt(dotn(N, K.V[k + 1], K.V[k + 1]));
+        if (!std::isfinite(hn)) {
+          set_error("NaN/Inf in FGMRES");
+          return MFS_ENAN;
+        }
+        H[(size_t)(k + 1) * m + k] = hn;
+        if (hn > 0.0) Blas<T>::axpby(N, T(1.0 / hn), K.V[k + 1], T(0), K.V[k + 1], s);
+        for (int i = 0; i < k; ++i) {
+          const double a = H[(size_t)i * m + k], bb = H[(size_t)(i + 1) * m + k];
+          H[(size_t)i * m + k] = cs[i] * a + sn[i] * bb;
+          H[(size_t)(i + 1) * m + k] = -sn[i] * a + cs[i] * bb;
+        }
+        const double a = H[(size_t)k * m + k], bb = H[(size_t)(k + 1) * m + k];
+        const double den = std::hypot(a, bb);
+        cs[k] = den > 0 ? a / den : 1.0;
+        sn[k] = den > 0 ? bb / den : 0.0;
+        H[(size_t)k * m + k] = den;
+        H[(size_t)(k + 1) * m + k] = 0.0;
+        g[k + 1] = -sn[k] * g[k];
+        g[k] = cs[k] * g[k];
+        ++*iters;
+        st.fgmres_iters++;
+        if (std::fabs(g[k + 1]) <= rtol * beta0 || *iters >= o.max_iters || hn == 0.0) {
+          ++k;
+          done = true;
+          break;
+        }
+      }
+      // solve the triangular system and update x with the preconditioned directions
+      const int kk = k;
+      for (int i = kk - 1; i >= 0; --i) {
+        double t = g[i];
+        for (int j = i + 1; j < kk; ++j) t -= H[(size_t)i * m + j] * y[j];
+        y[i] = t / H[(size_t)i * m + i];
+      }
+      for (int i = 0; i < kk; ++i) Blas<T>::axpby(N, T(y[i]), K.Z[i], T(1), x, s);
+      // true residual for the restart / final report
+      MFS_TRY(Kop(x, K.V[1]));
+      r = K.V[0];
+      Blas<T>::axpbypcz(N, T(1), b, T(-1), K.V[1], T(0), r, s);
+      beta = std::sqrt(dotn(N, r, r));
+      *rel_out = beta / beta0;
+      if (beta <= rtol * beta0 || *iters >= o.max_iters) done = true;
+    }
+    return MFS_OK;
+  }
+};
+
+// remove normal components at free-slip nodes only (Dirichlet values untouched)
+__global__ void k_freeslip_only(int nb, const int* __restrict__ ids, const int8_t* __restrict__ kind,
+                                const double* __restrict__ nrm, int64_t n_p2, double* __restrict__ v) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+    if (kind[k] != 2) continue;
+    const int64_t id = ids[k];
+    const double nx = nrm[3 * k], ny = nrm[3 * k + 1], nz = nrm[3 * k + 2];
+    const double un = v[id] * nx + v[n_p2 + id] * ny + v[2 * n_p2 + id] * nz;
+    v[id] -= un * nx;
+    v[n_p2 + id] -= un * ny;
+    v[2 * n_p2 + id] -= un * nz;
+  }
+}
+static void k_project_freeslip_only(const BoundaryList& B, int64_t n_p2, double* v, cudaStream_t s) {
+  if (B.nb) k_freeslip_only<<<(B.nb + 255) / 256, 256, 0, s>>>(B.nb, B.ids, B.kind, B.nrm64, n_p2, v);
+}
+
+// FP64 projected residual of the full system: r_u = P0 (f - A u - B^T P_p p),
+// r_p = P_p (g - (B + C) u); raw operators so that u carries the Dirichlet values.
+static mfs_status residual64(mfs_problem* Pb, const mfs_solve_opts& o, const double* f, const double* g,
+                             const double* u, const double* p, double* r, double* ptmp, double* y) {
+  MG* G = Pb->mg;
+  const int L = Pb->mesh->l_max;
+  const int64_t n2 = Pb->mesh->levels[L].nb2.total, nu = 3 * n2, np = Pb->mesh->levels[L].nb1.total;
+  cudaStream_t s = Pb->mesh->ctx->stream;
+  MFS_CUDA(cudaMemcpyAsync(ptmp, p, sizeof(double) * np, cudaMemcpyDeviceToDevice, s));
+  MFS_TRY(mean_free<double>(Pb, ptmp, np));
+  MFS_TRY(launch_apply<double>(Pb, L, OP_A | OP_BT | OP_B, 0, o.with_C, u, ptmp, y, y + nu, nullptr));
+  Blas<double>::axpbypcz(nu, 1.0, f, -1.0, y, 0.0, r, s);
+  Blas<double>::bproject(G->bnd[L], n2, r, s);
+  Blas<double>::axpbypcz(np, 1.0, g, -1.0, y + nu, 0.0, r + nu, s);
+  MFS_TRY(mean_free<double>(Pb, r + nu, np));
+  return MFS_OK;
+}
+
+static mfs_status stokes_solve(mfs_problem* Pb, const mfs_solve_opts& o, const double* f, const double* g, double* u,
+                               double* p, mfs_solve_stats& st) {
+  MG* G = Pb->mg;
+  const int L = Pb->mesh->l_max;
+  const int64_t n2 = Pb->mesh->levels[L].nb2.total, nu = 3 * n2, np = Pb->mesh->levels[L].nb1.total, N = nu + np;
+  cudaStream_t s = Pb->mesh->ctx->stream;
+  MFS_TRY(ensure_krylov<double>(G, nu, np, o.mixed ? 1 : o.restart, s));
+  if (o.mixed) MFS_TRY(ensure_krylov<float>(G, nu, np, o.restart, s));
+  Krylov<double>& K64 = G->k64;
+  double* r = K64.ir_r;      // FP64 projected residual
+  double* y = K64.ir_y;      // operator output / scaled residual
+  double* ptmp = K64.ir_p;
+  double* d = K64.sol;       // correction
+  const auto t0 = std::chrono::steady_clock::now();
+  // free-slip nodes: the velocity is tangential (the constrained operator cannot see normal
+  // components, so they must not enter u); Dirichlet values are kept
+  k_project_freeslip_only(G->bnd[L], n2, u, s);
+  MFS_TRY(residual64(Pb, o, f, g, u, p, r, ptmp, y));
+  const double r0 = std::sqrt(dot<double>(G, N, r, r, s));
+  st.r0_norm = r0;
+  st.r_norm = r0;
+  st.rel_residual = r0 > 0 ? 1.0 : 0.0;
+  if (!std::isfinite(r0)) {
+    set_error("NaN/Inf in the initial residual");
+    return MFS_ENAN;
+  }
+  mfs_status status = MFS_OK;
+  double rn = r0;
+  for (int outer = 0; outer < (o.mixed ? o.max_outer : 1) && rn > o.rtol * r0; ++outer) {
+    int its = 0;
+    double rel = 0.0;
+    if (o.mixed) {
+      Stokes<float> S(Pb, o, st);
+      float* r32 = G->k32.rhs;
+      float* d32 = G->k32.sol;
+      // scaled residual to FP32
+      Blas<double>::axpby(N, 1.0 / rn, r, 0.0, y, s);
+      Blas<float>::convert_from_f64(N, y, r32, s);
+      status = S.fgmres(r32, d32, o.inner_rtol, &its, &rel);
+      if (status != MFS_OK) return status;
+      Blas<float>::convert_to_f64(N, d32, d, s);
+    } else {
+      Stokes<double> S(Pb, o, st);
+      Blas<double>::axpby(N, 1.0 / rn, r, 0.0, K64.rhs, s);
+      status = S.fgmres(K64.rhs, d, o.rtol * r0 / rn, &its, &rel);
+      if (status != MFS_OK) return status;
+    }
+    // corrections live in the constrained space: project in FP64 before the update
+    Blas<double>::bproject(G->bnd[L], n2, d, s);
+    Blas<double>::axpby(nu, rn, d, 1.0, u, s);
+    Blas<double>::axpby(np, rn, d + nu, 1.0, p, s);
+    MFS_TRY(residual64(Pb, o, f, g, u, p, r, ptmp, y));
+    rn = std::sqrt(dot<double>(G, N, r, r, s));
+    st.outer_iters++;
+    if (!std::isfinite(rn)) {
+      set_error("NaN/Inf in the refined residual");
+      return MFS_ENAN;
+    }
+    if (st.fgmres_iters >= o.max_iters) break;
+  }
+  MFS_TRY(mean_free<double>(Pb, p, np));
+  MFS_CUDA(cudaStreamSynchronize(s));
+  st.r_norm = rn;
+  st.rel_residual = r0 > 0 ? rn / r0 : 0.0;
+  st.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (rn > o.rtol * r0) {
+    set_error("not converged: relative residual %.3e > %.3e after %d FGMRES iterations", st.rel_residual, o.rtol,
+              st.fgmres_iters);
+    return MFS_ENOTCONV;
+  }
+  return MFS_OK;
+}
+
+}  // namespace mfs
+
+void mfs_solve_opts_default(mfs_solve_opts* o) {
+  if (!o) return;
+  o->mixed = 1;
+  o->rtol = 1e-8;
+  o->restart = 30;
+  o->max_iters = 300;
+  o->max_outer = 20;
+  o->inner_rtol = 1e-4;
+  o->sigma = 1.0;
+  o->omega = 0.3;
+  o->tol_A = 1e-2;
+  o->m_A = 3;
+  o->deg_A = 2;
+  o->tol_VBFBT = 1e-1;
+  o->tol_invMass = 1e-10;
+  o->m_V = 1;
+  o->deg_V = 1;
+  o->max_cg = 200;
+  o->with_C = 1;
+}
+
+mfs_status mfs_stokes_solve(mfs_problem* Pb, const mfs_solve_opts* opts, const double* f, const double* g, double* u,
+                            double* p, mfs_solve_stats* stats) {
+  if (!Pb || !f || !g || !u || !p) {
+    set_error("null argument");
+    return MFS_EINVAL;
+  }
+  if (!Pb->mg || !Pb->mg->numeric) {
+    set_error("multigrid not set up (call mfs_setup_multigrid after mfs_set_viscosity)");
+    return MFS_EINVAL;
+  }
+  mfs_solve_opts o;
+  if (opts) o = *opts;
+  else mfs_solve_opts_default(&o);
+  if (o.restart < 1 || o.restart > 200 || !(o.rtol > 0) || o.m_A < 0 || o.deg_A < 1 || o.m_V < 0 || o.deg_V < 1) {
+    set_error("invalid solver options");
+    return MFS_EINVAL;
+  }
+  mfs_solve_stats st;
+  std::memset(&st, 0, sizeof(st));
+  const mfs_status rc = stokes_solve(Pb, o, f, g, u, p, st);
+  if (stats) *stats = st;
+  return rc;
+}

@@ -1,6 +1,9 @@
 // Vector kernels: deterministic two-pass sums, mean removal (P_p of Sec. 5.1),
 // viscosity injection to coarser levels (Sec. 5.2.2: eta as a P1 function on every
 // level, coarse vertices are fine vertices), precision conversion.
+#include <algorithm>
+#include <vector>
+
 #include "library.h"
 
 namespace mfs {
@@ -131,6 +134,105 @@ mfs_status exp_inplace(double* x, int64_t n, cudaStream_t s) {
   int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
   if (blocks < 1) blocks = 1;
   exp_kernel<<<blocks, 256, 0, s>>>(x, n);
+  MFS_CUDA(cudaGetLastError());
+  return MFS_OK;
+}
+
+}  // namespace mfs
+
+namespace mfs {
+
+// P1 full weighting from level l to l-1, built from the Freudenthal micro-tets of level
+// l-1: the P1 vertices of level l are the P2 nodes of level l-1 (vertices and edge
+// midpoints of its micro-tets).
+mfs_status build_eta_restriction(mfs_mesh* M, int l) {
+  static const int PERM[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  static const int LE[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+  LevelData& L = M->levels[l];
+  const int n = 1 << (l - 1);
+  const Numbering nbc = make_numbering(n), nbf = make_numbering(2 * n);
+  std::vector<char> seen(nbf.total, 0);
+  std::vector<int> tv, tj;
+  std::vector<double> tw;
+  for (int m = 0; m < 60; ++m) {
+    const MacroTopo& t = M->host.topo[m];
+    for (int a = 0; a < n; ++a)
+      for (int b = 0; b <= a; ++b)
+        for (int c = 0; c <= b; ++c)
+          for (int pm = 0; pm < 6; ++pm) {
+            int K[4][3] = {{a, b, c}};
+            bool ok = true;
+            for (int k = 1; k < 4; ++k) {
+              for (int d = 0; d < 3; ++d) K[k][d] = K[k - 1][d];
+              K[k][PERM[pm][k - 1]] += 1;
+              if (!(K[k][0] >= K[k][1] && K[k][1] >= K[k][2])) ok = false;
+            }
+            if (!ok) continue;
+            int v[4];
+            for (int q = 0; q < 4; ++q) {
+              v[q] = lattice_id(t, nbc, m, n - K[q][0], K[q][0] - K[q][1], K[q][1] - K[q][2], K[q][2]);
+              const int A = 2 * K[q][0], B = 2 * K[q][1], C = 2 * K[q][2];
+              const int j = lattice_id(t, nbf, m, 2 * n - A, A - B, B - C, C);
+              if (!seen[j]) {
+                seen[j] = 1;
+                tv.push_back(v[q]);
+                tj.push_back(j);
+                tw.push_back(1.0);
+              }
+            }
+            for (int e = 0; e < 6; ++e) {
+              const int p = LE[e][0], q = LE[e][1];
+              const int A = K[p][0] + K[q][0], B = K[p][1] + K[q][1], C = K[p][2] + K[q][2];
+              const int j = lattice_id(t, nbf, m, 2 * n - A, A - B, B - C, C);
+              if (seen[j]) continue;
+              seen[j] = 1;
+              tv.push_back(v[p]);
+              tj.push_back(j);
+              tw.push_back(0.5);
+              tv.push_back(v[q]);
+              tj.push_back(j);
+              tw.push_back(0.5);
+            }
+          }
+  }
+  std::vector<int> rp(nbc.total + 1, 0);
+  for (int v : tv) rp[v + 1]++;
+  for (int i = 0; i < nbc.total; ++i) rp[i + 1] += rp[i];
+  std::vector<int> pos(rp.begin(), rp.end() - 1), ci(tv.size());
+  std::vector<double> w(tv.size()), rs(nbc.total, 0.0);
+  for (size_t k = 0; k < tv.size(); ++k) rs[tv[k]] += tw[k];
+  for (size_t k = 0; k < tv.size(); ++k) {
+    const int r = tv[k];
+    ci[pos[r]] = tj[k];
+    w[pos[r]] = tw[k] / rs[r];
+    pos[r]++;
+  }
+  cudaStream_t s = M->ctx->stream;
+  L.er_rows = nbc.total;
+  MFS_CUDA(cudaMalloc((void**)&L.d_er_rp, sizeof(int) * rp.size()));
+  MFS_CUDA(cudaMalloc((void**)&L.d_er_ci, sizeof(int) * ci.size()));
+  MFS_CUDA(cudaMalloc((void**)&L.d_er_w, sizeof(double) * w.size()));
+  MFS_CUDA(cudaMemcpyAsync(L.d_er_rp, rp.data(), sizeof(int) * rp.size(), cudaMemcpyHostToDevice, s));
+  MFS_CUDA(cudaMemcpyAsync(L.d_er_ci, ci.data(), sizeof(int) * ci.size(), cudaMemcpyHostToDevice, s));
+  MFS_CUDA(cudaMemcpyAsync(L.d_er_w, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice, s));
+  MFS_CUDA(cudaStreamSynchronize(s));
+  return MFS_OK;
+}
+
+__global__ void restrict_eta_kernel(int rows, const int* __restrict__ rp, const int* __restrict__ ci,
+                                    const double* __restrict__ w, const double* __restrict__ fine,
+                                    double* __restrict__ coarse) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int k = rp[r]; k < rp[r + 1]; ++k) s += w[k] * fine[ci[k]];
+    coarse[r] = s;
+  }
+}
+
+mfs_status restrict_eta(const mfs_mesh* M, int l, const double* fine, double* coarse) {
+  const LevelData& L = M->levels[l];
+  const int blocks = std::max(1, std::min((L.er_rows + 255) / 256, 4096));
+  restrict_eta_kernel<<<blocks, 256, 0, M->ctx->stream>>>(L.er_rows, L.d_er_rp, L.d_er_ci, L.d_er_w, fine, coarse);
   MFS_CUDA(cudaGetLastError());
   return MFS_OK;
 }

@@ -12,17 +12,26 @@ import paper_2506_04157_gb300 as mfs
 import workloads as W
 from oracle.mesh import MacroMesh, Level
 from oracle.fem import Operators, Constraints, ConstrainedOperators, project_mean_zero
+from oracle.solver import viscosity_hierarchy
 
 TOL = {torch.float64: 1e-12, torch.float32: 1e-5}
 DLNRHO = W.dlnrho_table_config1()
 
 
 @functools.lru_cache(maxsize=None)
-def oracle(l, blending, bc=("dirichlet", "freeslip")):
+def levels(blending, l_max=3):
+    """Oracle levels 0..l_max and eta on each: the formula on the finest level, P1 full
+    weighting below (the library's coarse-level viscosity)."""
     mesh = MacroMesh(blending=blending)
-    L = Level(mesh, l)
-    eta = W.viscosity_radial(L.p1_x)
-    ops = Operators(L, eta, dlnrho_table=DLNRHO)
+    Ls = {l: Level(mesh, l) for l in range(l_max + 1)}
+    return mesh, Ls, viscosity_hierarchy(mesh, Ls, W.viscosity_radial(Ls[l_max].p1_x))
+
+
+@functools.lru_cache(maxsize=None)
+def oracle(l, blending, bc=("dirichlet", "freeslip")):
+    mesh, Ls, etas = levels(blending)
+    L = Ls[l]
+    ops = Operators(L, etas[l], dlnrho_table=DLNRHO)
     bcmap = {"dirichlet": 0, "freeslip": 1}
     cons = Constraints(L, bcmap[bc[0]], bcmap[bc[1]])
     return L, ops, ConstrainedOperators(ops, cons)
