@@ -195,6 +195,32 @@ def run_ours(args, rank, world, device):
     e2e_ms = e0.elapsed_time(e1) / n_e2e
     e2e_value = world * dofs / (e2e_ms * 1e-3) / 1e9
 
+    # time to solve: multigrid setup (diag, eigenvalue estimates, coarse inverse) plus the
+    # solve to relative residual 1e-8 measured in FP64, on the same problem
+    solve = None
+    if args.solve:
+        x2 = mesh.coords(level).T
+        T = W.temperature_blobs(x2, 3)
+        xh = x2 / np.linalg.norm(x2, axis=1, keepdims=True)
+        f = torch.tensor(np.concatenate([T * xh[:, 0], T * xh[:, 1], T * xh[:, 2]]) * 1e-3, device=dev)
+        g = torch.zeros(npp, dtype=torch.float64, device=dev)
+        solve = {}
+        modes = [("mixed", 1)] + ([("fp64", 0)] if args.solve_fp64 else [])
+        for name, mixed in modes:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            prob.setup_multigrid(1)
+            torch.cuda.synchronize()
+            t_setup = time.perf_counter() - t0
+            u = torch.zeros(nu, dtype=torch.float64, device=dev)
+            p = torch.zeros(npp, dtype=torch.float64, device=dev)
+            st = prob.solve(f, g, u, p, mixed=mixed, raise_on_error=False)
+            torch.cuda.synchronize()
+            t_all = time.perf_counter() - t0
+            solve[name] = {"time_to_solve_s": round(t_all, 3), "setup_s": round(t_setup, 3),
+                           "solve_s": round(st["time_ms"] / 1e3, 3), "rel_residual_fp64": st["rel_residual"],
+                           "status": st["status"], "fgmres_iters": st["fgmres_iters"],
+                           "refinement_steps": st["outer_iters"], "vcycles": st["vcycles"]}
     if rank != 0:
         return None
     peaks = read_peaks()
@@ -221,6 +247,8 @@ def run_ours(args, rank, world, device):
         "clocks": clocks,
         "hbm_peak_measured_gbs": peaks.get("hbm_gbs"),
     }
+    if solve is not None:
+        line["time_to_solve"] = solve
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(level, budget_s=args.cpu_seconds)
     return line
@@ -281,6 +309,10 @@ def main():
     ap.add_argument("--level", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--solve", dest="solve", action="store_true", default=True,
+                    help="also time the mixed-precision solve to 1e-8 (default)")
+    ap.add_argument("--no-solve", dest="solve", action="store_false")
+    ap.add_argument("--solve-fp64", action="store_true", help="also time the plain FP64 solve (minutes at level 5)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -513,3 +513,70 @@ mfs_status coarse_inverse(mfs_problem* P, int lvl, const BoundaryList& B, double
 }
 
 }  // namespace mfs
+
+namespace mfs {
+
+// ------------------------------------------------------------------------- device-side CG
+// Scalars of a device-resident CG (slots of a double array, see solver.h CG_*).
+__global__ void k_cg_init(double* __restrict__ sc) {
+  sc[CG_IT] = 0.0;
+  sc[CG_ACTIVE] = (sc[CG_RR0] > 0.0 && sc[CG_RZ] > 0.0) ? 1.0 : 0.0;
+  sc[CG_ALPHA] = sc[CG_BETA] = 0.0;
+}
+__global__ void k_cg_alpha(double* __restrict__ sc) {
+  const bool ok = sc[CG_ACTIVE] > 0.0 && sc[CG_PQ] > 0.0;
+  sc[CG_ALPHA] = ok ? sc[CG_RZ] / sc[CG_PQ] : 0.0;
+  if (!ok) sc[CG_ACTIVE] = 0.0;
+}
+template <typename T>
+__global__ void k_cg_xr(int64_t n, const double* __restrict__ sc, const T* __restrict__ p, const T* __restrict__ q,
+                        T* __restrict__ x, T* __restrict__ r) {
+  const T a = (T)sc[CG_ALPHA];
+  if (a == T(0)) return;
+  GRID_STRIDE(i, n) {
+    x[i] += a * p[i];
+    r[i] -= a * q[i];
+  }
+}
+__global__ void k_cg_beta(double* __restrict__ sc, double tol2, double maxit) {
+  if (sc[CG_ACTIVE] > 0.0) {
+    const double rzn = sc[CG_RZN];
+    sc[CG_BETA] = rzn / sc[CG_RZ];
+    sc[CG_RZ] = rzn;
+    sc[CG_IT] += 1.0;
+    if (!(sc[CG_RR] > tol2 * sc[CG_RR0]) || sc[CG_IT] >= maxit || !(rzn > 0.0)) sc[CG_ACTIVE] = 0.0;
+  } else {
+    sc[CG_BETA] = 0.0;
+  }
+}
+template <typename T>
+__global__ void k_cg_p(int64_t n, const double* __restrict__ sc, const T* __restrict__ z, T* __restrict__ p) {
+  if (!(sc[CG_ACTIVE] > 0.0)) return;
+  const T b = (T)sc[CG_BETA];
+  GRID_STRIDE(i, n) p[i] = z[i] + b * p[i];
+}
+
+template <typename T>
+void CgDev<T>::init(double* sc, cudaStream_t s) {
+  k_cg_init<<<1, 1, 0, s>>>(sc);
+}
+template <typename T>
+void CgDev<T>::alpha(double* sc, cudaStream_t s) {
+  k_cg_alpha<<<1, 1, 0, s>>>(sc);
+}
+template <typename T>
+void CgDev<T>::xr(int64_t n, const double* sc, const T* p, const T* q, T* x, T* r, cudaStream_t s) {
+  k_cg_xr<T><<<blocks_for(n), 256, 0, s>>>(n, sc, p, q, x, r);
+}
+template <typename T>
+void CgDev<T>::beta(double* sc, double tol2, int maxit, cudaStream_t s) {
+  k_cg_beta<<<1, 1, 0, s>>>(sc, tol2, (double)maxit);
+}
+template <typename T>
+void CgDev<T>::pupd(int64_t n, const double* sc, const T* z, T* p, cudaStream_t s) {
+  k_cg_p<T><<<blocks_for(n), 256, 0, s>>>(n, sc, z, p);
+}
+template struct CgDev<float>;
+template struct CgDev<double>;
+
+}  // namespace mfs

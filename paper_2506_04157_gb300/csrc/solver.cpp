@@ -59,6 +59,15 @@ struct MG {
   Krylov<float> k32;
   Krylov<double> k64;
   std::vector<void*> owned;     // device allocations to free
+  // device-resident CG: scalar slots, a capture stream and cached graphs of CG chunks
+  double* cgsc = nullptr;
+  cudaStream_t cap = nullptr;
+  struct Graph {
+    int prec;
+    const void* x;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;
 };
 
 static mfs_status dalloc(MG* G, void** p, size_t bytes) {
@@ -76,6 +85,8 @@ static mfs_status dalloc_zero(MG* G, T** p, int64_t n, cudaStream_t s) {
 
 void mg_destroy(MG* G) {
   if (!G) return;
+  for (auto& g : G->graphs) cudaGraphExecDestroy(g.exec);
+  if (G->cap) cudaStreamDestroy(G->cap);
   for (void* p : G->owned) cudaFree(p);
   if (G->hpin) cudaFreeHost(G->hpin);
   delete G;
@@ -321,6 +332,8 @@ static mfs_status mg_structure(mfs_problem* Pb, int l_min) {
   MFS_TRY(dalloc_zero(G, &G->mdinv64, M->levels[L].nb1.total, s));
   MFS_TRY(dalloc_zero(G, &G->mdinv32, M->levels[L].nb1.total, s));
   MFS_TRY(dalloc_zero(G, &G->red, kRedBlocks + 16, s));
+  MFS_TRY(dalloc_zero(G, &G->cgsc, CG_NSLOTS, s));
+  MFS_CUDA(cudaStreamCreateWithFlags(&G->cap, cudaStreamNonBlocking));
   MFS_CUDA(cudaMallocHost((void**)&G->hpin, 16 * sizeof(double)));
   G->structure = true;
   return MFS_OK;
@@ -718,8 +731,12 @@ struct Stokes {
   // generic preconditioned CG on n entries; op/pre write their output vector
   template <typename Op, typename Pre>
   mfs_status cg(int64_t n, Op op, Pre pre, const T* b, T* x, double rtol, int maxit, T* r, T* z, T* p, T* q,
-                int* iters) {
+                int* iters, int proj = 0) {
+    // proj: 1 keeps a pressure residual mean-free, 2 keeps a velocity residual in the
+    // constrained space (FP32 rounding leaves residue in directions the operator ignores)
     Blas<T>::axpby(n, T(1), b, T(0), r, s);
+    if (proj == 1) MFS_TRY(mean_free<T>(Pb, r, n));
+    if (proj == 2) Blas<T>::bproject(G->bnd[L], n2, r, s);
     Blas<T>::fill(n, T(0), x, s);
     *iters = 0;
     const double rr0 = dotn(n, r, r);
@@ -742,6 +759,8 @@ struct Stokes {
       const double alpha = rz / pq;
       Blas<T>::axpby(n, T(alpha), p, T(1), x, s);
       Blas<T>::axpby(n, T(-alpha), q, T(1), r, s);
+      if (proj == 1) MFS_TRY(mean_free<T>(Pb, r, n));
+      if (proj == 2) Blas<T>::bproject(G->bnd[L], n2, r, s);
       ++*iters;
       const double rr = dotn(n, r, r);
       if (!std::isfinite(rr)) {
@@ -765,7 +784,7 @@ struct Stokes {
       st.vcycles++;
       return vcycle<T>(Pb, G, L, y, v, o.m_A, o.deg_A);
     };
-    MFS_TRY(cg(nu, op, pre, r, x, o.tol_A, o.max_cg, K.cg_r, K.cg_z, K.cg_p, K.cg_q, &it));
+    MFS_TRY(cg(nu, op, pre, r, x, o.tol_A, o.max_cg, K.cg_r, K.cg_z, K.cg_p, K.cg_q, &it, 2));
     st.cg_A_iters += it;
     st.cg_A_calls++;
     st.cg_A_max = it > st.cg_A_max ? it : st.cg_A_max;
@@ -776,18 +795,77 @@ struct Stokes {
     st.vcycles++;
     return vcycle<T>(Pb, G, L, x, r, o.m_V, o.deg_V);
   }
-  // M_{1/eta}^-1 by CG (P_p M P_p, Jacobi) to tol_invMass
+  // M_{1/eta}^-1 by CG (P_p M P_p, Jacobi) to tol_invMass, run on the device: the scalars
+  // stay in device memory and chunks of kChunk iterations replay a captured CUDA graph
+  // (finished iterations are no-ops); the host reads one flag per chunk.
+  static constexpr int kChunk = 8;
+  void mass_iteration(cudaStream_t cs, T* x) {
+    const double tol2 = tolM * tolM;
+    mass_apply<T>(Pb, L, K.cgm_p, K.cgm_q, 0);
+    mean_free<T>(Pb, K.cgm_q, np);
+    Blas<T>::dot_async(np, K.cgm_p, K.cgm_q, G->red, G->cgsc + CG_PQ, cs);
+    CgDev<T>::alpha(G->cgsc, cs);
+    CgDev<T>::xr(np, G->cgsc, K.cgm_p, K.cgm_q, x, K.cgm_r, cs);
+    mean_free<T>(Pb, K.cgm_r, np);
+    Blas<T>::dot_async(np, K.cgm_r, K.cgm_r, G->red, G->cgsc + CG_RR, cs);
+    Blas<T>::mul(np, K.cgm_r, mass_dinv<T>(G), K.cgm_z, cs);
+    mean_free<T>(Pb, K.cgm_z, np);
+    Blas<T>::dot_async(np, K.cgm_r, K.cgm_z, G->red, G->cgsc + CG_RZN, cs);
+    CgDev<T>::beta(G->cgsc, tol2, o.max_cg, cs);
+    CgDev<T>::pupd(np, G->cgsc, K.cgm_z, K.cgm_p, cs);
+  }
+  mfs_status mass_graph(T* x, cudaGraphExec_t* out) {
+    const int prec = sizeof(T) == 8 ? 0 : 1;
+    for (auto& g : G->graphs)
+      if (g.prec == prec && g.x == x) {
+        *out = g.exec;
+        return MFS_OK;
+      }
+    mfs_ctx* C = Pb->mesh->ctx;
+    cudaStream_t saved = C->stream;
+    C->stream = G->cap;
+    cudaError_t e = cudaStreamBeginCapture(G->cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      for (int k = 0; k < kChunk; ++k) mass_iteration(G->cap, x);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(G->cap, &graph);
+    C->stream = saved;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+    cudaGraphExec_t exec;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    G->graphs.push_back({prec, x, exec});
+    *out = exec;
+    return MFS_OK;
+  }
   mfs_status M_inv(const T* r, T* x) {
-    int it = 0;
-    auto op = [&](const T* v, T* y) {
-      MFS_TRY(mass_apply<T>(Pb, L, v, y, 0));
-      return mean_free<T>(Pb, y, np);
-    };
-    auto pre = [&](const T* v, T* y) {
-      Blas<T>::mul(np, v, mass_dinv<T>(G), y, s);
-      return mean_free<T>(Pb, y, np);
-    };
-    MFS_TRY(cg(np, op, pre, r, x, tolM, o.max_cg, K.cgm_r, K.cgm_z, K.cgm_p, K.cgm_q, &it));
+    cudaGraphExec_t exec;
+    MFS_TRY(mass_graph(x, &exec));
+    Blas<T>::axpby(np, T(1), r, T(0), K.cgm_r, s);
+    MFS_TRY(mean_free<T>(Pb, K.cgm_r, np));
+    Blas<T>::fill(np, T(0), x, s);
+    Blas<T>::mul(np, K.cgm_r, mass_dinv<T>(G), K.cgm_z, s);
+    MFS_TRY(mean_free<T>(Pb, K.cgm_z, np));
+    Blas<T>::axpby(np, T(1), K.cgm_z, T(0), K.cgm_p, s);
+    Blas<T>::dot_async(np, K.cgm_r, K.cgm_z, G->red, G->cgsc + CG_RZ, s);
+    Blas<T>::dot_async(np, K.cgm_r, K.cgm_r, G->red, G->cgsc + CG_RR0, s);
+    CgDev<T>::init(G->cgsc, s);
+    double flags[CG_NSLOTS];
+    for (int it = 0; it < o.max_cg; it += kChunk) {
+      MFS_CUDA(cudaGraphLaunch(exec, s));
+      MFS_CUDA(cudaMemcpyAsync(G->hpin, G->cgsc, sizeof(double) * CG_NSLOTS, cudaMemcpyDeviceToHost, s));
+      MFS_CUDA(cudaStreamSynchronize(s));
+      std::memcpy(flags, G->hpin, sizeof(flags));
+      if (!std::isfinite(flags[CG_RR])) {
+        set_error("NaN/Inf in the mass-matrix CG");
+        return MFS_ENAN;
+      }
+      if (!(flags[CG_ACTIVE] > 0.0)) break;
+    }
+    const int it = (int)flags[CG_IT];
     st.cg_M_iters += it;
     st.cg_M_calls++;
     st.cg_M_max = it > st.cg_M_max ? it : st.cg_M_max;
@@ -804,7 +882,7 @@ struct Stokes {
     int it = 0;
     auto op = [&](const T* v, T* y) { return X(v, y); };
     auto pre = [&](const T* v, T* y) { return M_inv(v, y); };
-    MFS_TRY(cg(np, op, pre, r, K.pe, o.tol_VBFBT, o.max_cg, K.cgp_r, K.cgp_z, K.cgp_p, K.cgp_q, &it));
+    MFS_TRY(cg(np, op, pre, r, K.pe, o.tol_VBFBT, o.max_cg, K.cgp_r, K.cgp_z, K.cgp_p, K.cgp_q, &it, 1));
     st.cg_X_iters += it;
     st.cg_X_calls++;
     st.cg_X_max = it > st.cg_X_max ? it : st.cg_X_max;
@@ -813,7 +891,7 @@ struct Stokes {
     MFS_TRY(A(K.ud, K.uc));
     MFS_TRY(Ac_inv(K.uc, K.ud));
     MFS_TRY(Bop(K.ud, K.pf, 0));
-    MFS_TRY(cg(np, op, pre, K.pf, z, o.tol_VBFBT, o.max_cg, K.cgp_r, K.cgp_z, K.cgp_p, K.cgp_q, &it));
+    MFS_TRY(cg(np, op, pre, K.pf, z, o.tol_VBFBT, o.max_cg, K.cgp_r, K.cgp_z, K.cgp_p, K.cgp_q, &it, 1));
     st.cg_X_iters += it;
     st.cg_X_calls++;
     st.cg_X_max = it > st.cg_X_max ? it : st.cg_X_max;

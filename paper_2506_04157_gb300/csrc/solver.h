@@ -53,6 +53,18 @@ struct Blas {
   static void convert_to_f64(int64_t n, const T* x, double* y, cudaStream_t s);
 };
 
+// slots of the device-resident CG scalars
+enum { CG_RZ = 0, CG_RZN, CG_PQ, CG_RR, CG_RR0, CG_ALPHA, CG_BETA, CG_IT, CG_ACTIVE, CG_NSLOTS };
+
+template <typename T>
+struct CgDev {
+  static void init(double* sc, cudaStream_t s);                  // it = 0, active = rr0 > 0
+  static void alpha(double* sc, cudaStream_t s);                 // alpha = rz / pq
+  static void xr(int64_t n, const double* sc, const T* p, const T* q, T* x, T* r, cudaStream_t s);
+  static void beta(double* sc, double tol2, int maxit, cudaStream_t s);   // beta, rz, it, active
+  static void pupd(int64_t n, const double* sc, const T* z, T* p, cudaStream_t s);
+};
+
 template <typename T>
 inline const T* lvl_eta(mfs_problem* P, int l);
 template <>
