@@ -51,17 +51,21 @@ def read_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle sampling during the timed region."""
+    """nvidia-smi clock/throttle sampling (20 ms period) with host timestamps; summary()
+    uses the samples inside the timed window, else those of the adjacent busy window
+    (warm-up through the end of the run), and says which."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.lines = []
+        self.window = None
 
-    def __enter__(self):
+    def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
@@ -70,8 +74,10 @@ class ClockSampler:
             self.proc = None
         return self
 
-    def __exit__(self, *a):
-        self.lines = []
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
+
+    def stop(self):
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -80,24 +86,27 @@ class ClockSampler:
                 self.proc.kill()
                 out, _ = self.proc.communicate()
             self.lines = [l for l in out.splitlines() if l.strip()]
+            self.proc = None
 
     def summary(self):
-        sm, mx, reasons = [], [], set()
+        import datetime
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in getattr(self, "lines", []):
+        for l in self.lines:
             f = [x.strip() for x in l.split(",")]
             try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(f[2]), float(f[3]), [nm for k, nm in enumerate(names)
+                                                            if len(f) > 6 + k and f[6 + k].lower() == "active"]))
             except (ValueError, IndexError):
                 continue
-            for k, nm in enumerate(names):
-                if len(f) > 5 + k and f[5 + k].lower() == "active":
-                    reasons.add(nm)
-        if not sm:
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        inside = [r for r in rows if self.window and self.window[0] <= r[0] <= self.window[1]]
+        use, where = (inside, "timed") if inside else (rows, "adjacent busy window")
+        reasons = sorted({x for r in use for x in r[3]})
+        return {"sm_mhz": statistics.median([r[1] for r in use]), "sm_max_mhz": max(r[2] for r in use),
+                "reasons": reasons, "samples": len(use), "window": where}
 
 
 def setup_problem(level, device):
@@ -141,6 +150,7 @@ def run_ours(args, rank, world, device):
         u, p, yu, yp = sets[i % nsets]
         prob.apply_stokes(level, u, p, yu, yp)
 
+    clk = ClockSampler(device).start()
     for i in range(args.warmup):
         step(i)
     torch.cuda.synchronize()
@@ -150,13 +160,14 @@ def run_ours(args, rank, world, device):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ctx.kernel_time()
     ctx.enable_timing(True)
-    with ClockSampler(device) as clk:
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for i in range(args.steps):
-            step(i)
-        e1.record(stream)
-        torch.cuda.synchronize()
+    torch.cuda.synchronize()
+    tw0 = time.time()
+    e0.record(stream)
+    for i in range(args.steps):
+        step(i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk.mark(tw0, time.time())
     ctx.enable_timing(False)
     ktot, klaunch = ctx.kernel_time()
     if world > 1:
@@ -221,6 +232,7 @@ def run_ours(args, rank, world, device):
                            "solve_s": round(st["time_ms"] / 1e3, 3), "rel_residual_fp64": st["rel_residual"],
                            "status": st["status"], "fgmres_iters": st["fgmres_iters"],
                            "refinement_steps": st["outer_iters"], "vcycles": st["vcycles"]}
+    clk.stop()
     if rank != 0:
         return None
     peaks = read_peaks()

@@ -205,7 +205,7 @@ typedef struct {
   double rtol;        /* stop at ||r|| <= rtol ||r0||, r the FP64 projected residual (1e-8) */
   int restart;        /* FGMRES restart length (30) */
   int max_iters;      /* total FGMRES iterations (300) */
-  int max_outer;      /* refinement steps in mixed mode (20) */
+  int max_outer;      /* refinement steps (restarts on the true FP64 residual) (20) */
   double inner_rtol;  /* relative tolerance of each inner FP32 FGMRES (1e-4) */
   double sigma;       /* scaling of A^-1 in the Uzawa step (1) */
   double omega;       /* scaling of S^-1 in the Uzawa step (0.3) */
@@ -241,6 +241,21 @@ void mfs_solve_opts_default(mfs_solve_opts* opts);
  * MFS_ECUDA, MFS_ENOMEM (Krylov storage is allocated on the first solve). */
 mfs_status mfs_stokes_solve(mfs_problem* prob, const mfs_solve_opts* opts, const double* f, const double* g,
                             double* u, double* p, mfs_solve_stats* stats);
+
+/* ---------------------------------------------------------------- adjoint (not in the paper)
+ * Adjoint solve K^T lam = (ju, jp) with K^T = [A (B+C)^T; B 0] on the constrained space
+ * (the multiplier's Dirichlet values are zeroed on entry), by the same FGMRES / symmetric
+ * Uzawa / V-cycle BFBT solver with the constraint and momentum pressure blocks swapped.
+ * ju [3][n_p2], jp [n_p1]: gradient of the objective w.r.t. (u, p) (FP64, device);
+ * lam_u, lam_p: initial guess in, multiplier out.  Errors as mfs_stokes_solve. */
+mfs_status mfs_adjoint_solve(mfs_problem* prob, const mfs_solve_opts* opts, const double* ju, const double* jp,
+                             double* lam_u, double* lam_p, mfs_solve_stats* stats);
+
+/* Gradient of the objective w.r.t. the nodal log-viscosity of the finest level:
+ *   g_k = -eta_k sum_q 2 w_q |det J_q| psi_k(q) eps(u)(q) : eps(lam)(q)
+ * (A is linear in the P1 viscosity), u the forward velocity (with its Dirichlet values),
+ * lam the adjoint velocity; all FP64 device vectors, g [n_p1].  Errors: MFS_EINVAL, MFS_ECUDA. */
+mfs_status mfs_grad_log_eta(mfs_problem* prob, const double* u, const double* lam_u, double* g);
 
 /* Allocation-free variant of mfs_apply_B (no counterpart in the paper).
  *

@@ -89,6 +89,8 @@ _SIGS = {
     "mfs_restrict": ([_vp, _i, _i, _vp, _vp], _i),
     "mfs_vcycle": ([_vp, _i, _i, _i, _i, _vp, _vp], _i),
     "mfs_solve_opts_default": ([ctypes.POINTER(SolveOpts)], None),
+    "mfs_adjoint_solve": ([_vp, ctypes.POINTER(SolveOpts), _vp, _vp, _vp, _vp, ctypes.POINTER(SolveStats)], _i),
+    "mfs_grad_log_eta": ([_vp, _vp, _vp, _vp], _i),
     "mfs_stokes_solve": ([_vp, ctypes.POINTER(SolveOpts), _vp, _vp, _vp, _vp, ctypes.POINTER(SolveStats)], _i),
 }
 
@@ -321,6 +323,31 @@ class Problem:
         if rc != OK and raise_on_error:
             raise MfsError(rc, lib().mfs_last_error().decode())
         return d
+
+    def adjoint_solve(self, ju, jp, lam_u, lam_p, raise_on_error=True, **opts):
+        """Solve K^T lam = (ju, jp) in place (FP64 device tensors); returns statistics."""
+        import torch
+        L = self.mesh.l_max
+        nu, npp = self._sizes(L)
+        _need(ju, nu, torch.float64, "ju"); _need(jp, npp, torch.float64, "jp")
+        _need(lam_u, nu, torch.float64, "lam_u"); _need(lam_p, npp, torch.float64, "lam_p")
+        o = self.default_opts(**opts)
+        st = SolveStats()
+        rc = lib().mfs_adjoint_solve(self.handle, ctypes.byref(o), _ptr(ju), _ptr(jp), _ptr(lam_u), _ptr(lam_p),
+                                     ctypes.byref(st))
+        d = st.as_dict()
+        d["status"] = _STATUS.get(rc, rc)
+        if rc != OK and raise_on_error:
+            raise MfsError(rc, lib().mfs_last_error().decode())
+        return d
+
+    def grad_log_eta(self, u, lam_u, g):
+        import torch
+        L = self.mesh.l_max
+        nu, npp = self._sizes(L)
+        _need(u, nu, torch.float64, "u"); _need(lam_u, nu, torch.float64, "lam_u")
+        _need(g, npp, torch.float64, "g")
+        _check(lib().mfs_grad_log_eta(self.handle, _ptr(u), _ptr(lam_u), _ptr(g)))
 
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:

@@ -580,3 +580,111 @@ template struct CgDev<float>;
 template struct CgDev<double>;
 
 }  // namespace mfs
+
+namespace mfs {
+
+// ------------------------------------------------------------------------- adjoint gradient
+// dJ/d(log eta_k) = -eta_k lam^T (dA/d eta_k) u with A linear in the P1 viscosity:
+// (dA/d eta_k)_ij = sum_q 2 w|det J| psi_k(q) eps(phi_j):eps(phi_i).  u is the full forward
+// velocity (with its Dirichlet values), lam the constrained adjoint velocity.
+__global__ void __launch_bounds__(128) k_grad_sweep(const ApplyParams<double> P, int blend, const double* __restrict__ u,
+                                                    const double* __restrict__ lam, double* __restrict__ g) {
+  __shared__ double gs[NSLOT1];
+  __shared__ int gid1[NSLOT1];
+  const int m = blockIdx.y, tidx = blockIdx.x;
+  const size_t lin = (size_t)m * gridDim.x + tidx;
+  const Tile tile = P.tiles[tidx];
+  const MacroGeom<double>& G = P.geom[m];
+  const int n = P.n;
+  const int64_t n2 = P.n_p2;
+  for (int s = threadIdx.x; s < NSLOT1; s += blockDim.x) {
+    gs[s] = 0.0;
+    gid1[s] = P.ids1[lin * NSLOT1 + s];
+  }
+  __syncthreads();
+  const double QA = MFS_QA, QB = MFS_QB;
+  const double C0 = G.absdet / (24.0 * n * (double)n * n);
+  const int2 cinfo = P.classes[tile.cls];
+  const int* tab2 = P.ids2 + lin * NSLOT2;
+  for (int t = threadIdx.x; t < cinfo.y; t += blockDim.x) {
+    const int code = P.tets[cinfo.x + t];
+    const int ci = code & 15, cj = (code >> 4) & 15, ck = (code >> 8) & 15, pmu = code >> 12;
+    const int p0 = (0x221100 >> (4 * pmu)) & 3, p1 = (0x102021 >> (4 * pmu)) & 3, p2 = (0x010212 >> (4 * pmu)) & 3;
+    const int S1 = 1 << p0, S2 = S1 | (1 << p1);
+    const int base = ci + 5 * cj + 25 * ck;
+    int slot[10];
+    slot[0] = base;
+    slot[1] = base + sub_off(S1);
+    slot[2] = base + sub_off(S2);
+    slot[3] = base + sub_off(7);
+    slot[4] = S1 * kSub + base;
+    slot[5] = S2 * kSub + base;
+    slot[6] = 7 * kSub + base;
+    slot[7] = (S1 ^ S2) * kSub + base + sub_off(S1);
+    slot[8] = (S1 ^ 7) * kSub + base + sub_off(S1);
+    slot[9] = (S2 ^ 7) * kSub + base + sub_off(S2);
+    double uv[10][3], lv[10][3];
+    for (int a = 0; a < 10; ++a) {
+      const int64_t id = tab2[slot[a]] & 0x1fffffff;
+      for (int c = 0; c < 3; ++c) {
+        uv[a][c] = u[c * n2 + id];
+        lv[a][c] = lam[c * n2 + id];
+      }
+    }
+    const double qx = tile.ta * TT + ci, qy = tile.tb * TT + cj, qz = tile.tc * TT + ck;
+    double out[4] = {0, 0, 0, 0};
+    for (int q = 0; q < 4; ++q) {
+      double K[3][3], hr, rinv, x[3];
+      if (blend) qp_geometry<double, true>(G, n, p0, p1, p2, q, qx, qy, qz, K, hr, rinv, x);
+      else qp_geometry<double, false>(G, n, p0, p1, p2, q, qx, qy, qz, K, hr, rinv, x);
+      const double lam_q[4] = {q == 0 ? QA : QB, q == 1 ? QA : QB, q == 2 ? QA : QB, q == 3 ? QA : QB};
+      // gradients (scaled) of u and lam: sum_a value_a (x) (lattice grad of phi_a) K
+      double Gu[3][3] = {{0}}, Gl[3][3] = {{0}};
+      for (int a = 0; a < 10; ++a) {
+        double gl[3];
+        p2_lat_grad(a, lam_q, gl);
+        double gx[3];
+        for (int d = 0; d < 3; ++d) gx[d] = gl[0] * K[0][d] + gl[1] * K[1][d] + gl[2] * K[2][d];
+        for (int c = 0; c < 3; ++c)
+          for (int d = 0; d < 3; ++d) {
+            Gu[c][d] += uv[a][c] * gx[d];
+            Gl[c][d] += lv[a][c] * gx[d];
+          }
+      }
+      const double tu = (Gu[0][0] + Gu[1][1] + Gu[2][2]) / 3.0, tl = (Gl[0][0] + Gl[1][1] + Gl[2][2]) / 3.0;
+      double contr = 0.0;
+      for (int c = 0; c < 3; ++c)
+        for (int d = 0; d < 3; ++d) {
+          const double eu = 0.5 * (Gu[c][d] + Gu[d][c]) - (c == d ? tu : 0.0);
+          const double el = 0.5 * (Gl[c][d] + Gl[d][c]) - (c == d ? tl : 0.0);
+          contr += eu * el;
+        }
+      // w|det J| s^2 = C0 hr ; dA/d eta contributes 2 psi_k
+      const double wq = 2.0 * C0 * hr * contr;
+      for (int k = 0; k < 4; ++k) out[k] += wq * lam_q[k];
+    }
+    for (int k = 0; k < 4; ++k) atomicAdd(&gs[slot[k]], out[k]);
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < NSLOT1; s += blockDim.x)
+    if (gid1[s] >= 0) atomicAdd(&g[gid1[s]], gs[s]);
+}
+
+__global__ void k_scale_by_minus_eta(int64_t n, const double* __restrict__ eta, double* __restrict__ g) {
+  GRID_STRIDE(i, n) g[i] = -eta[i] * g[i];
+}
+
+mfs_status grad_log_eta(mfs_problem* P, int lvl, const double* u, const double* lam, double* g) {
+  mfs_mesh* M = P->mesh;
+  const LevelData& L = M->levels[lvl];
+  cudaStream_t s = M->ctx->stream;
+  MFS_CUDA(cudaMemsetAsync(g, 0, sizeof(double) * (size_t)L.nb1.total, s));
+  dim3 grid(L.n_tiles, kMacroCells);
+  ApplyParams<double> prm = sweep_params<double>(P, lvl);
+  k_grad_sweep<<<grid, 128, 0, s>>>(prm, M->host.blending, u, lam, g);
+  k_scale_by_minus_eta<<<blocks_for(L.nb1.total), 256, 0, s>>>(L.nb1.total, P->eta64[lvl], g);
+  MFS_CUDA(cudaGetLastError());
+  return MFS_OK;
+}
+
+}  // namespace mfs

@@ -704,10 +704,12 @@ struct Stokes {
   cudaStream_t s;
   Krylov<T>& K;
   double tolM;
+  int transpose;   // 1: the adjoint operator [A (B+C)^T; B 0]
 
-  Stokes(mfs_problem* P, const mfs_solve_opts& opts, mfs_solve_stats& stats)
+  Stokes(mfs_problem* P, const mfs_solve_opts& opts, mfs_solve_stats& stats, int transp = 0)
       : Pb(P), G(P->mg), o(opts), st(stats), L(P->mesh->l_max), n2(P->mesh->levels[L].nb2.total), nu(3 * n2),
-        np(P->mesh->levels[L].nb1.total), N(nu + np), s(P->mesh->ctx->stream), K(kry<T>(P->mg)) {
+        np(P->mesh->levels[L].nb1.total), N(nu + np), s(P->mesh->ctx->stream), K(kry<T>(P->mg)),
+        transpose(transp) {
     tolM = o.tol_invMass;
     if (sizeof(T) == 4 && tolM < 1e-5) tolM = 1e-5;   // FP32 CG stagnates near 1e-6
   }
@@ -723,9 +725,18 @@ struct Stokes {
   mfs_status Bop(const T* u, T* q, int withc) {
     return apply_constrained<T>(Pb, L, OP_B, 1, withc, u, nullptr, nullptr, q);
   }
+  // the momentum row's pressure block: B^T, or (B+C)^T in the adjoint operator
+  mfs_status BTrow(const T* p, T* y) {
+    const int op = (transpose && o.with_C) ? (OP_BT | OP_CT) : OP_BT;
+    return apply_constrained<T>(Pb, L, op, 1, 0, nullptr, p, y, nullptr);
+  }
+  // the constraint row: (B+C), or B in the adjoint operator
+  int withc_row() const { return transpose ? 0 : o.with_C; }
   mfs_status Kop(const T* x, T* y) {
     st.applies++;
-    return apply_constrained<T>(Pb, L, OP_A | OP_BT | OP_B, 1, o.with_C, x, x + nu, y, y + nu);
+    if (transpose && o.with_C)
+      return apply_constrained<T>(Pb, L, OP_A | OP_BT | OP_CT | OP_B, 1, 0, x, x + nu, y, y + nu);
+    return apply_constrained<T>(Pb, L, OP_A | OP_BT | OP_B, 1, withc_row(), x, x + nu, y, y + nu);
   }
 
   // generic preconditioned CG on n entries; op/pre write their output vector
@@ -906,12 +917,12 @@ struct Stokes {
     T* uh = K.tmpu;
     MFS_TRY(Ahat_inv(ru, uh));
     if (o.sigma != 1.0) Blas<T>::axpby(nu, T(o.sigma), uh, T(0), uh, s);
-    MFS_TRY(Bop(uh, K.pa, o.with_C));                                  // (B + C) uh
+    MFS_TRY(Bop(uh, K.pa, withc_row()));                               // (B + C) uh (B: adjoint)
     Blas<T>::axpbypcz(np, T(1), rp, T(-1), K.pa, T(0), K.pb, s);       // r_p - Bbar uh
     MFS_TRY(S_inv(K.pb, zp));
     Blas<T>::axpby(np, T(-o.omega), zp, T(0), zp, s);                  // p = -omega S^-1 (...)
     MFS_TRY(A(uh, K.w));
-    MFS_TRY(BT(zp, K.ua));
+    MFS_TRY(BTrow(zp, K.ua));
     Blas<T>::axpbypcz(nu, T(1), ru, T(-1), K.w, T(0), K.ub, s);
     Blas<T>::axpby(nu, T(-1), K.ua, T(1), K.ub, s);                    // r_u - A uh - B^T p
     MFS_TRY(Ahat_inv(K.ub, zu));
@@ -1018,14 +1029,18 @@ static void k_project_freeslip_only(const BoundaryList& B, int64_t n_p2, double*
 // FP64 projected residual of the full system: r_u = P0 (f - A u - B^T P_p p),
 // r_p = P_p (g - (B + C) u); raw operators so that u carries the Dirichlet values.
 static mfs_status residual64(mfs_problem* Pb, const mfs_solve_opts& o, const double* f, const double* g,
-                             const double* u, const double* p, double* r, double* ptmp, double* y) {
+                             const double* u, const double* p, double* r, double* ptmp, double* y, int transpose) {
   MG* G = Pb->mg;
   const int L = Pb->mesh->l_max;
   const int64_t n2 = Pb->mesh->levels[L].nb2.total, nu = 3 * n2, np = Pb->mesh->levels[L].nb1.total;
   cudaStream_t s = Pb->mesh->ctx->stream;
   MFS_CUDA(cudaMemcpyAsync(ptmp, p, sizeof(double) * np, cudaMemcpyDeviceToDevice, s));
   MFS_TRY(mean_free<double>(Pb, ptmp, np));
-  MFS_TRY(launch_apply<double>(Pb, L, OP_A | OP_BT | OP_B, 0, o.with_C, u, ptmp, y, y + nu, nullptr));
+  if (transpose && o.with_C)
+    MFS_TRY(launch_apply<double>(Pb, L, OP_A | OP_BT | OP_CT | OP_B, 0, 0, u, ptmp, y, y + nu, nullptr));
+  else
+    MFS_TRY(launch_apply<double>(Pb, L, OP_A | OP_BT | OP_B, 0, transpose ? 0 : o.with_C, u, ptmp, y, y + nu,
+                                 nullptr));
   Blas<double>::axpbypcz(nu, 1.0, f, -1.0, y, 0.0, r, s);
   Blas<double>::bproject(G->bnd[L], n2, r, s);
   Blas<double>::axpbypcz(np, 1.0, g, -1.0, y + nu, 0.0, r + nu, s);
@@ -1034,7 +1049,7 @@ static mfs_status residual64(mfs_problem* Pb, const mfs_solve_opts& o, const dou
 }
 
 static mfs_status stokes_solve(mfs_problem* Pb, const mfs_solve_opts& o, const double* f, const double* g, double* u,
-                               double* p, mfs_solve_stats& st) {
+                               double* p, mfs_solve_stats& st, int transpose) {
   MG* G = Pb->mg;
   const int L = Pb->mesh->l_max;
   const int64_t n2 = Pb->mesh->levels[L].nb2.total, nu = 3 * n2, np = Pb->mesh->levels[L].nb1.total, N = nu + np;
@@ -1050,7 +1065,7 @@ static mfs_status stokes_solve(mfs_problem* Pb, const mfs_solve_opts& o, const d
   // free-slip nodes: the velocity is tangential (the constrained operator cannot see normal
   // components, so they must not enter u); Dirichlet values are kept
   k_project_freeslip_only(G->bnd[L], n2, u, s);
-  MFS_TRY(residual64(Pb, o, f, g, u, p, r, ptmp, y));
+  MFS_TRY(residual64(Pb, o, f, g, u, p, r, ptmp, y, transpose));
   const double r0 = std::sqrt(dot<double>(G, N, r, r, s));
   st.r0_norm = r0;
   st.r_norm = r0;
@@ -1061,11 +1076,11 @@ static mfs_status stokes_solve(mfs_problem* Pb, const mfs_solve_opts& o, const d
   }
   mfs_status status = MFS_OK;
   double rn = r0;
-  for (int outer = 0; outer < (o.mixed ? o.max_outer : 1) && rn > o.rtol * r0; ++outer) {
+  for (int outer = 0; outer < o.max_outer && rn > o.rtol * r0; ++outer) {
     int its = 0;
     double rel = 0.0;
     if (o.mixed) {
-      Stokes<float> S(Pb, o, st);
+      Stokes<float> S(Pb, o, st, transpose);
       float* r32 = G->k32.rhs;
       float* d32 = G->k32.sol;
       // scaled residual to FP32
@@ -1075,7 +1090,7 @@ static mfs_status stokes_solve(mfs_problem* Pb, const mfs_solve_opts& o, const d
       if (status != MFS_OK) return status;
       Blas<float>::convert_to_f64(N, d32, d, s);
     } else {
-      Stokes<double> S(Pb, o, st);
+      Stokes<double> S(Pb, o, st, transpose);
       Blas<double>::axpby(N, 1.0 / rn, r, 0.0, K64.rhs, s);
       status = S.fgmres(K64.rhs, d, o.rtol * r0 / rn, &its, &rel);
       if (status != MFS_OK) return status;
@@ -1084,7 +1099,7 @@ static mfs_status stokes_solve(mfs_problem* Pb, const mfs_solve_opts& o, const d
     Blas<double>::bproject(G->bnd[L], n2, d, s);
     Blas<double>::axpby(nu, rn, d, 1.0, u, s);
     Blas<double>::axpby(np, rn, d + nu, 1.0, p, s);
-    MFS_TRY(residual64(Pb, o, f, g, u, p, r, ptmp, y));
+    MFS_TRY(residual64(Pb, o, f, g, u, p, r, ptmp, y, transpose));
     rn = std::sqrt(dot<double>(G, N, r, r, s));
     st.outer_iters++;
     if (!std::isfinite(rn)) {
@@ -1148,7 +1163,42 @@ mfs_status mfs_stokes_solve(mfs_problem* Pb, const mfs_solve_opts* opts, const d
   }
   mfs_solve_stats st;
   std::memset(&st, 0, sizeof(st));
-  const mfs_status rc = stokes_solve(Pb, o, f, g, u, p, st);
+  const mfs_status rc = stokes_solve(Pb, o, f, g, u, p, st, 0);
   if (stats) *stats = st;
   return rc;
+}
+
+mfs_status mfs_adjoint_solve(mfs_problem* Pb, const mfs_solve_opts* opts, const double* ju, const double* jp,
+                             double* lam_u, double* lam_p, mfs_solve_stats* stats) {
+  if (!Pb || !ju || !jp || !lam_u || !lam_p) {
+    set_error("null argument");
+    return MFS_EINVAL;
+  }
+  if (!Pb->mg || !Pb->mg->numeric) {
+    set_error("multigrid not set up (call mfs_setup_multigrid after mfs_set_viscosity)");
+    return MFS_EINVAL;
+  }
+  mfs_solve_opts o;
+  if (opts) o = *opts;
+  else mfs_solve_opts_default(&o);
+  mfs_solve_stats st;
+  std::memset(&st, 0, sizeof(st));
+  // homogeneous constraints for the multiplier: zero its Dirichlet values
+  const int L = Pb->mesh->l_max;
+  Blas<double>::bproject(Pb->mg->bnd[L], Pb->mesh->levels[L].nb2.total, lam_u, Pb->mesh->ctx->stream);
+  const mfs_status rc = stokes_solve(Pb, o, ju, jp, lam_u, lam_p, st, 1);
+  if (stats) *stats = st;
+  return rc;
+}
+
+mfs_status mfs_grad_log_eta(mfs_problem* Pb, const double* u, const double* lam_u, double* g) {
+  if (!Pb || !u || !lam_u || !g) {
+    set_error("null argument");
+    return MFS_EINVAL;
+  }
+  if (!Pb->has_eta) {
+    set_error("viscosity not set");
+    return MFS_EINVAL;
+  }
+  return grad_log_eta(Pb, Pb->mesh->l_max, u, lam_u, g);
 }

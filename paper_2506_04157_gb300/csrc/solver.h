@@ -83,5 +83,7 @@ mfs_status diag_A(mfs_problem* P, int lvl, const BoundaryList& B, T* diag);
 template <typename T>
 mfs_status mass_apply(mfs_problem* P, int lvl, const T* pin, T* y, int diag_only);
 mfs_status coarse_inverse(mfs_problem* P, int lvl, const BoundaryList& B, double* A, double* work);
+// g_k = -eta_k sum_tets sum_q 2 w|det J| psi_k(q) eps(u)(q) : eps(lam)(q)   (FP64)
+mfs_status grad_log_eta(mfs_problem* P, int lvl, const double* u, const double* lam, double* g);
 
 }  // namespace mfs
