@@ -31,6 +31,12 @@
 
 namespace mfs {
 
+#ifndef MFS_EDGE_ACC_REGS
+#define MFS_EDGE_ACC_REGS 1   // 1: edge contributions accumulated in registers over the qps
+#endif
+#ifndef MFS_SLOT_TABLE
+#define MFS_SLOT_TABLE 0      // 1: slot offsets from a constant table, 0: computed
+#endif
 #ifndef MFS_SWEEP_MINBLOCKS
 #define MFS_SWEEP_MINBLOCKS 4   // resident CTAs per SM the register allocation targets
 #endif
@@ -124,6 +130,35 @@ __device__ __forceinline__ void lattice_normal(const MacroGeom<T>& G, int A, int
   nrm[2] = x[2] * ri;
 }
 
+// Slot offsets (relative to the cube base i + 5j + 25k) of the 10 P2 nodes of each of
+// the 6 Freudenthal types (vertices of the path 0, e_p0, e_p0+e_p1, (1,1,1), then the
+// edges 01,02,03,12,13,23 in their parity classes).
+struct SlotTable {
+  int off[6][10];
+};
+__host__ __device__ constexpr int perm_at(int pm, int k) {
+  return k == 0 ? (0x221100 >> (4 * pm)) & 3 : (k == 1 ? (0x102021 >> (4 * pm)) & 3 : (0x010212 >> (4 * pm)) & 3);
+}
+__host__ __device__ constexpr int slot_off(int pm, int a) {
+  return a == 0 ? 0
+         : a == 1 ? sub_off(1 << perm_at(pm, 0))
+         : a == 2 ? sub_off((1 << perm_at(pm, 0)) | (1 << perm_at(pm, 1)))
+         : a == 3 ? sub_off(7)
+         : a == 4 ? (1 << perm_at(pm, 0)) * kSub
+         : a == 5 ? ((1 << perm_at(pm, 0)) | (1 << perm_at(pm, 1))) * kSub
+         : a == 6 ? 7 * kSub
+         : a == 7 ? ((1 << perm_at(pm, 1))) * kSub + sub_off(1 << perm_at(pm, 0))
+         : a == 8 ? ((1 << perm_at(pm, 0)) ^ 7) * kSub + sub_off(1 << perm_at(pm, 0))
+                  : (((1 << perm_at(pm, 0)) | (1 << perm_at(pm, 1))) ^ 7) * kSub +
+                        sub_off((1 << perm_at(pm, 0)) | (1 << perm_at(pm, 1)));
+}
+static __constant__ SlotTable c_slots = {{
+#define MFS_ROW(pm) {slot_off(pm, 0), slot_off(pm, 1), slot_off(pm, 2), slot_off(pm, 3), slot_off(pm, 4), \
+                     slot_off(pm, 5), slot_off(pm, 6), slot_off(pm, 7), slot_off(pm, 8), slot_off(pm, 9)}
+    MFS_ROW(0), MFS_ROW(1), MFS_ROW(2), MFS_ROW(3), MFS_ROW(4), MFS_ROW(5)
+#undef MFS_ROW
+}};
+
 // bytes of dynamic shared memory of one sweep CTA
 template <typename T, int OP>
 constexpr size_t sweep_smem_bytes() {
@@ -151,6 +186,8 @@ __global__ void __launch_bounds__(kSweepThreads, MFS_SWEEP_MINBLOCKS) stokes_til
   int* gid2 = reinterpret_cast<int*>(yp_s + (OUT_P ? NSLOT1 : 0));
   int* gid1 = gid2 + NSLOT2;
   __shared__ T cM[9], cJn[9], cv0[3], cnh[3];
+  __shared__ T qpo[6][4][3];      // physical offset of qp q of type pm from the cube corner
+  __shared__ T dtab[64];          // d ln rho / dr table (first 64 entries)
 
   const int m = blockIdx.y;
   const int tidx = blockIdx.x;
@@ -169,6 +206,21 @@ __global__ void __launch_bounds__(kSweepThreads, MFS_SWEEP_MINBLOCKS) stokes_til
     cv0[tid] = G.v0[tid];
     cnh[tid] = G.nh[tid];
   }
+  if (tid < 72) {
+    // lattice offset of qp q of type pm: beta (3 e_p0 + 2 e_p1 + e_p2) + (alpha - beta) S_q
+    const int pm = tid / 12, q = (tid / 3) % 4, r = tid % 3;
+    const int p0 = perm_at(pm, 0), p1 = perm_at(pm, 1), p2 = perm_at(pm, 2);
+    const int S1 = 1 << p0, S2 = S1 | (1 << p1);
+    const int Sq = q == 0 ? 0 : (q == 1 ? S1 : (q == 2 ? S2 : 7));
+    const T QA = T(MFS_QA), QB = T(MFS_QB);
+    T o = T(0);
+    for (int d = 0; d < 3; ++d) {
+      const T lat = QB * T(3 * (p0 == d) + 2 * (p1 == d) + (p2 == d)) + (QA - QB) * T((Sq >> d) & 1);
+      o += G.Jm[3 * r + d] * lat;
+    }
+    qpo[pm][q][r] = o / T(n);
+  }
+  if (tid < 64 && tid < P.n_dlnrho) dtab[tid] = P.dlnrho[tid];
 
   // ---- stage the P2 node block (u, with the input-side projections) ----
   // All table entries of this thread first, then all node values: independent loads in flight.
@@ -260,29 +312,20 @@ __global__ void __launch_bounds__(kSweepThreads, MFS_SWEEP_MINBLOCKS) stokes_til
   for (int t = tid; t < cinfo.y; t += kSweepThreads) {
     const int code = P.tets[cinfo.x + t];
     const int ci = code & 15, cj = (code >> 4) & 15, ck = (code >> 8) & 15, pmu = code >> 12;
-    const int p0 = (0x221100 >> (4 * pmu)) & 3;
-    const int p1 = (0x102021 >> (4 * pmu)) & 3;
-    const int p2 = (0x010212 >> (4 * pmu)) & 3;
-    // corner masks of the Freudenthal path 0, e_p0, e_p0+e_p1, (1,1,1)
-    const int S1 = 1 << p0, S2 = S1 | (1 << p1);
+    const int p0 = perm_at(pmu, 0), p1 = perm_at(pmu, 1), p2 = perm_at(pmu, 2);
     const int base = ci + 5 * cj + 25 * ck;
-    int slot[10];
-    slot[0] = base;
-    slot[1] = base + sub_off(S1);
-    slot[2] = base + sub_off(S2);
-    slot[3] = base + sub_off(7);
-    slot[4] = S1 * kSub + base;                           // edge 01
-    slot[5] = S2 * kSub + base;                           // edge 02
-    slot[6] = 7 * kSub + base;                            // edge 03
-    slot[7] = (S1 ^ S2) * kSub + base + sub_off(S1);      // edge 12
-    slot[8] = (S1 ^ 7) * kSub + base + sub_off(S1);       // edge 13
-    slot[9] = (S2 ^ 7) * kSub + base + sub_off(S2);       // edge 23
+#if MFS_SLOT_TABLE
+    const int* soff = c_slots.off[pmu];
+#define SLOT(a) (base + soff[a])
+#else
+#define SLOT(a) (base + slot_off(pmu, (a)))
+#endif
 
     T eta_v[4], p_v[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-      eta_v[a] = eta_s[slot[a]];          // P1 block uses the same sub-block indexing
-      if (HAS_P) p_v[a] = p_s[slot[a]];
+      eta_v[a] = eta_s[SLOT(a)];          // P1 block uses the vertex sub-block indexing
+      if (HAS_P) p_v[a] = p_s[SLOT(a)];
     }
     const T eta_sum = eta_v[0] + eta_v[1] + eta_v[2] + eta_v[3];
     T p_sum = T(0);
@@ -295,9 +338,9 @@ __global__ void __launch_bounds__(kSweepThreads, MFS_SWEEP_MINBLOCKS) stokes_til
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const T* uc = us + c * NSLOT2;
-        const T u0 = uc[slot[0]], u1 = uc[slot[1]], u2 = uc[slot[2]], u3 = uc[slot[3]];
-        const T e01 = uc[slot[4]], e02 = uc[slot[5]], e03 = uc[slot[6]];
-        const T e12 = uc[slot[7]], e13 = uc[slot[8]], e23 = uc[slot[9]];
+        const T u0 = uc[SLOT(0)], u1 = uc[SLOT(1)], u2 = uc[SLOT(2)], u3 = uc[SLOT(3)];
+        const T e01 = uc[SLOT(4)], e02 = uc[SLOT(5)], e03 = uc[SLOT(6)];
+        const T e12 = uc[SLOT(7)], e13 = uc[SLOT(8)], e23 = uc[SLOT(9)];
         const T bs0 = bq1 * u0 + b4 * (e01 + e02 + e03);
         const T bs1 = bq1 * u1 + b4 * (e01 + e12 + e13);
         const T bs2 = bq1 * u2 + b4 * (e02 + e12 + e23);
@@ -309,39 +352,32 @@ __global__ void __launch_bounds__(kSweepThreads, MFS_SWEEP_MINBLOCKS) stokes_til
       }
     }
 
+    // cube corner position
     const T qx = T(a0 + ci), qy = T(b0 + cj), qz = T(c0 + ck);
-    T Mp[3][3];
+    T xc[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      Mp[0][d] = cM[3 * p0 + d];
-      Mp[1][d] = cM[3 * p1 + d];
-      Mp[2][d] = cM[3 * p2 + d];
-    }
+    for (int r = 0; r < 3; ++r) xc[r] = cv0[r] + cJn[3 * r] * qx + cJn[3 * r + 1] * qy + cJn[3 * r + 2] * qz;
 
     // Rsum = sum_q R^q: since grad lambda_a is constant on the tet, T_a = sum_q s_a^q = Rsum grad lambda_a
-    T Rsum[3][3], Eacc[6][3], Zsum[3];
+    T Rsum[3][3], Zsum[3];
+#if MFS_EDGE_ACC_REGS
+    T Eacc[6][3];   // E_ab = s_a^b + s_b^a (+ the C-part of (B+C)^T), times dq at the end
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
+    for (int e = 0; e < 6; ++e) Eacc[e][0] = Eacc[e][1] = Eacc[e][2] = T(0);
+#endif
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      Zsum[c] = T(0);
 #pragma unroll
       for (int j = 0; j < 3; ++j) Rsum[c][j] = T(0);
-#pragma unroll
-    for (int e = 0; e < 6; ++e)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) Eacc[e][c] = T(0);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) Zsum[c] = T(0);
+    }
     T bq[4];
 
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      // lattice position of qp q: corner + beta (3 e_p0 + 2 e_p1 + e_p2) + (alpha - beta) S_q
-      const int Sq = q == 0 ? 0 : (q == 1 ? S1 : (q == 2 ? S2 : 7));
-      const T xi0 = qx + QB * T(3 * (p0 == 0) + 2 * (p1 == 0) + (p2 == 0)) + (QA - QB) * T(Sq & 1);
-      const T xi1 = qy + QB * T(3 * (p0 == 1) + 2 * (p1 == 1) + (p2 == 1)) + (QA - QB) * T((Sq >> 1) & 1);
-      const T xi2 = qz + QB * T(3 * (p0 == 2) + 2 * (p1 == 2) + (p2 == 2)) + (QA - QB) * T(Sq >> 2);
       T x[3];
 #pragma unroll
-      for (int r = 0; r < 3; ++r) x[r] = cv0[r] + cJn[3 * r] * xi0 + cJn[3 * r + 1] * xi1 + cJn[3 * r + 2] * xi2;
+      for (int r = 0; r < 3; ++r) x[r] = xc[r] + qpo[pmu][q][r];
       const T r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
       const T rinv = rsqrt_t<T>(r2);
       T K[3][3];
@@ -356,15 +392,20 @@ __global__ void __launch_bounds__(kSweepThreads, MFS_SWEEP_MINBLOCKS) stokes_til
         for (int d = 0; d < 3; ++d) v[d] = cnh[d] * hinv - x[d] * ri2;
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-          const T tj = Mp[j][0] * x[0] + Mp[j][1] * x[1] + Mp[j][2] * x[2];
-#pragma unroll
-          for (int d = 0; d < 3; ++d) K[j][d] = Mp[j][d] - tj * v[d];
+          const int pj = j == 0 ? p0 : (j == 1 ? p1 : p2);
+          const T m0 = cM[3 * pj], m1 = cM[3 * pj + 1], m2 = cM[3 * pj + 2];
+          const T tj = m0 * x[0] + m1 * x[1] + m2 * x[2];
+          K[j][0] = m0 - tj * v[0];
+          K[j][1] = m1 - tj * v[1];
+          K[j][2] = m2 - tj * v[2];
         }
       } else {
 #pragma unroll
-        for (int j = 0; j < 3; ++j)
+        for (int j = 0; j < 3; ++j) {
+          const int pj = j == 0 ? p0 : (j == 1 ? p1 : p2);
 #pragma unroll
-          for (int d = 0; d < 3; ++d) K[j][d] = Mp[j][d];
+          for (int d = 0; d < 3; ++d) K[j][d] = cM[3 * pj + d];
+        }
       }
       const T coefB = C0 * hr * hr;   // w |det J| s
       const T Wq = coefB * hr;        // w |det J|
@@ -380,7 +421,7 @@ __global__ void __launch_bounds__(kSweepThreads, MFS_SWEEP_MINBLOCKS) stokes_til
           const T* uc = us + c * NSLOT2;
           T w[4];
 #pragma unroll
-          for (int a = 0; a < 4; ++a) w[a] = uc[slot[wnode(a, q)]];
+          for (int a = 0; a < 4; ++a) w[a] = uc[SLOT(wnode(a, q))];
 #pragma unroll
           for (int j = 0; j < 3; ++j) D[j][c] = dbase[j][c] + dq * (w[j + 1] - w[j]);
           wq[c] = w[q];
@@ -393,16 +434,31 @@ __global__ void __launch_bounds__(kSweepThreads, MFS_SWEEP_MINBLOCKS) stokes_til
         trace = Gp[0][0] + Gp[1][1] + Gp[2][2];
       }
 
+      T gr = T(0);
+      if ((OUT_P && HAS_BC) || HAS_CT) {
+        const T rad = BLEND ? h * dinv : r2 * rinv;
+        if (P.n_dlnrho <= 1) {
+          gr = dtab[0];
+        } else {
+          const T top = T(P.n_dlnrho - 1);
+          T sg = (rad - P.r_cmb) * P.inv_dr * top;
+          sg = sg < T(0) ? T(0) : (sg > top ? top : sg);
+          int ig = (int)sg;
+          ig = ig > P.n_dlnrho - 2 ? P.n_dlnrho - 2 : ig;
+          const T fg = sg - T(ig);
+          gr = (ig + 1 < 64) ? (T(1) - fg) * dtab[ig] + fg * dtab[ig + 1]
+                             : (T(1) - fg) * P.dlnrho[ig] + fg * P.dlnrho[ig + 1];
+        }
+      }
+
       // B: weights of -(div u + grad ln rho . u)
       if (OUT_P) {
         T b = coefB * trace;
         if (HAS_BC) {
-          const T rad = BLEND ? h * dinv : r2 * rinv;
-          const T g = dlnrho_at<T>(P, rad);
           T eu = T(0);
 #pragma unroll
           for (int c = 0; c < 3; ++c) eu += (U0[c] + (fva - fvb) * wq[c] + (fei - feo) * wsum[c]) * x[c];
-          b += Wq * g * eu * rinv;
+          b += Wq * gr * eu * rinv;
         }
         bq[q] = b;
       }
@@ -433,47 +489,52 @@ __global__ void __launch_bounds__(kSweepThreads, MFS_SWEEP_MINBLOCKS) stokes_til
           S[1][1] -= sp;
           S[2][2] -= sp;
         }
-        // R = S K^T (columns in permuted lattice order), s_a = R grad_lat lambda_a
-        T sv[4][3];
+        // R = S K^T (columns in permuted lattice order), s_a = R grad_lat lambda_a; the
+        // qp-specific terms dq s_a^q go to vertex q (a == q) and to the edges (a, q)
+        T zq[3] = {T(0), T(0), T(0)};
+        if (HAS_CT) {
+          const T zc = -Wq * pq * gr * rinv;   // (B+C)^T: the C part through the P2 values
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            zq[c] = zc * x[c];
+            Zsum[c] += zq[c];
+          }
+        }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           const T r0 = S[c][0] * K[0][0] + S[c][1] * K[0][1] + S[c][2] * K[0][2];
           const T r1 = S[c][0] * K[1][0] + S[c][1] * K[1][1] + S[c][2] * K[1][2];
           const T r2c = S[c][0] * K[2][0] + S[c][1] * K[2][1] + S[c][2] * K[2][2];
-          sv[0][c] = -r0;
-          sv[1][c] = r0 - r1;
-          sv[2][c] = r1 - r2c;
-          sv[3][c] = r2c;
           Rsum[c][0] += r0;
           Rsum[c][1] += r1;
           Rsum[c][2] += r2c;
-        }
-        // vertex q takes dq s_q^q now; T and E accumulate the rest
-        T vq[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) vq[c] = dq * sv[q][c];
-        // (B+C)^T: the C part -W p_q g (x/|x|) . phi_i through the P2 values at the qp
-        if (HAS_CT) {
-          const T rad = BLEND ? h * dinv : r2 * rinv;
-          const T g = dlnrho_at<T>(P, rad);
-          const T zc = -Wq * pq * g * rinv;
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const T z = zc * x[c];
-            Zsum[c] += z;
-            vq[c] += (fva - fvb) * z;
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-              if (a != q) Eacc[edge_of(a, q)][c] += ((fei - feo) / dq) * z;
+          T sv[4];
+          sv[0] = -r0;
+          sv[1] = r0 - r1;
+          sv[2] = r1 - r2c;
+          sv[3] = r2c;
+          T* y = ys + c * NSLOT2;
+#if MFS_EDGE_ACC_REGS
+          {
+            T val = dq * sv[q];
+            if (HAS_CT) val += (fva - fvb) * zq[c];
+            atomicAdd(&y[SLOT(q)], val);
           }
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+            if (a != q) {
+              Eacc[edge_of(a, q)][c] += sv[a];
+              if (HAS_CT) Eacc[edge_of(a, q)][c] += ((fei - feo) / dq) * zq[c];
+            }
+#else
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            T val = dq * sv[a];
+            if (HAS_CT) val += (a == q ? (fva - fvb) : (fei - feo)) * zq[c];
+            atomicAdd(&y[SLOT(wnode(a, q))], val);
+          }
+#endif
         }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) atomicAdd(&ys[c * NSLOT2 + slot[q]], vq[c]);
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int c = 0; c < 3; ++c)
-            if (a != q) Eacc[edge_of(a, q)][c] += sv[a][c];
       }
     }  // qp loop
 
@@ -490,24 +551,27 @@ __global__ void __launch_bounds__(kSweepThreads, MFS_SWEEP_MINBLOCKS) stokes_til
         for (int a = 0; a < 4; ++a) {
           T val = bq1 * Tacc[a];
           if (HAS_CT) val += fvb * Zsum[c];
-          atomicAdd(&y[slot[a]], val);
+          atomicAdd(&y[SLOT(a)], val);
         }
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
           for (int b = a + 1; b < 4; ++b) {
-            const int e = edge_of(a, b);
-            T val = b4 * (Tacc[a] + Tacc[b]) + dq * Eacc[e][c];
+            T val = b4 * (Tacc[a] + Tacc[b]);
+#if MFS_EDGE_ACC_REGS
+            val += dq * Eacc[edge_of(a, b)][c];
+#endif
             if (HAS_CT) val += feo * Zsum[c];
-            atomicAdd(&y[slot[4 + e]], val);
+            atomicAdd(&y[SLOT(4 + edge_of(a, b))], val);
           }
       }
     }
     if (OUT_P) {
       const T sb = bq[0] + bq[1] + bq[2] + bq[3];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) atomicAdd(&yp_s[slot[a]], -(QB * sb + (QA - QB) * bq[a]));
+      for (int a = 0; a < 4; ++a) atomicAdd(&yp_s[SLOT(a)], -(QB * sb + (QA - QB) * bq[a]));
     }
+#undef SLOT
   }
   __syncthreads();
 
