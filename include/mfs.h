@@ -59,6 +59,7 @@ typedef enum { MFS_RAW = 0, MFS_CONSTRAINED = 1 } mfs_bcmode;
 typedef struct mfs_ctx mfs_ctx;
 typedef struct mfs_mesh mfs_mesh;
 typedef struct mfs_problem mfs_problem;
+typedef struct mfs_batch mfs_batch;
 
 typedef struct {
   int level;
@@ -256,6 +257,36 @@ mfs_status mfs_adjoint_solve(mfs_problem* prob, const mfs_solve_opts* opts, cons
  * (A is linear in the P1 viscosity), u the forward velocity (with its Dirichlet values),
  * lam the adjoint velocity; all FP64 device vectors, g [n_p1].  Errors: MFS_EINVAL, MFS_ECUDA. */
 mfs_status mfs_grad_log_eta(mfs_problem* prob, const double* u, const double* lam_u, double* g);
+
+/* ---------------------------------------------------------------- ensembles (not in the paper)
+ * A batch groups n problems on one context (each with its own mesh, refinement level,
+ * boundary conditions and viscosity; all blended or all polyhedral).  Allocates device
+ * memory.  Errors: MFS_EINVAL, MFS_ENOMEM, MFS_ECUDA. */
+mfs_status mfs_batch_create(mfs_ctx* ctx, int n, mfs_problem* const* probs, mfs_batch** out);
+mfs_status mfs_batch_destroy(mfs_batch* batch);
+
+/* The constrained fused saddle-point apply (as mfs_apply_stokes, compressible) of every
+ * member on its finest level, with ONE micro-tet sweep launch covering all members' tiles
+ * (plus batched zeroing and pressure mean removal).  u, p, yu, yp: HOST arrays of n device
+ * pointers.  Errors: MFS_EINVAL, MFS_ECUDA. */
+mfs_status mfs_batch_apply_stokes(mfs_batch* batch, mfs_prec prec, int transpose, const void* const* u,
+                                  const void* const* p, void* const* yu, void* const* yp);
+
+/* mfs_stokes_solve for every member in turn (each needs mfs_setup_multigrid); stats: n
+ * entries or NULL.  Returns the first error, MFS_ENOTCONV after trying every member. */
+mfs_status mfs_batch_solve(mfs_batch* batch, const mfs_solve_opts* opts, const double* const* f,
+                           const double* const* g, double* const* u, double* const* p, mfs_solve_stats* stats);
+
+/* ---------------------------------------------------------------- autotuning (not in the paper)
+ * For every level of the problem's mesh, times the FP32 hot sweeps (fused saddle-point
+ * apply and A alone) in their two compiled register budgets (4 or 3 resident CTAs per SM)
+ * with CUDA events and keeps the faster for all later applies on that mesh.  cache_path
+ * (may be NULL): a text file read first (levels found there are not timed) and written
+ * with the choices and timings.  Allocates and frees temporary device vectors.
+ * Errors: MFS_EINVAL, MFS_ENOMEM, MFS_ECUDA. */
+mfs_status mfs_autotune(mfs_problem* prob, const char* cache_path);
+/* The variant in use on a level (0: default budget, 1: wider registers). */
+mfs_status mfs_get_tuning(const mfs_problem* prob, int lvl, int* variant);
 
 /* Allocation-free variant of mfs_apply_B (no counterpart in the paper).
  *

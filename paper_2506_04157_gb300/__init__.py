@@ -91,6 +91,12 @@ _SIGS = {
     "mfs_solve_opts_default": ([ctypes.POINTER(SolveOpts)], None),
     "mfs_adjoint_solve": ([_vp, ctypes.POINTER(SolveOpts), _vp, _vp, _vp, _vp, ctypes.POINTER(SolveStats)], _i),
     "mfs_grad_log_eta": ([_vp, _vp, _vp, _vp], _i),
+    "mfs_autotune": ([_vp, ctypes.c_char_p], _i),
+    "mfs_get_tuning": ([_vp, _i, ctypes.POINTER(_i)], _i),
+    "mfs_batch_create": ([_vp, _i, _vp, ctypes.POINTER(_vp)], _i),
+    "mfs_batch_destroy": ([_vp], _i),
+    "mfs_batch_apply_stokes": ([_vp, _i, _i, _vp, _vp, _vp, _vp], _i),
+    "mfs_batch_solve": ([_vp, ctypes.POINTER(SolveOpts), _vp, _vp, _vp, _vp, _vp], _i),
     "mfs_stokes_solve": ([_vp, ctypes.POINTER(SolveOpts), _vp, _vp, _vp, _vp, ctypes.POINTER(SolveStats)], _i),
 }
 
@@ -294,6 +300,17 @@ class Problem:
         _need(f, nu, None, "f"); _need(u, nu, f.dtype, "u")
         _check(lib().mfs_vcycle(self.handle, level, _prec_of(f), steps, degree, _ptr(f), _ptr(u)))
 
+    # ---- autotuning
+    def autotune(self, cache_path=None):
+        """Pick the faster sweep variant per level (cached in cache_path if given)."""
+        _check(lib().mfs_autotune(self.handle, cache_path.encode() if cache_path else None))
+        out = []
+        for l in range(self.mesh.l_max + 1):
+            v = ctypes.c_int()
+            _check(lib().mfs_get_tuning(self.handle, l, ctypes.byref(v)))
+            out.append(v.value)
+        return out
+
     # ---- Stokes solver
     @staticmethod
     def default_opts(**kw):
@@ -352,4 +369,43 @@ class Problem:
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:
             _lib.mfs_problem_destroy(self.handle)
+            self.handle = None
+
+
+def _ptr_array(tensors):
+    arr = (ctypes.c_void_p * len(tensors))(*[t.data_ptr() for t in tensors])
+    return arr
+
+
+class Batch:
+    """An ensemble of problems on one context: one sweep launch applies all of them."""
+
+    def __init__(self, ctx, problems):
+        self.problems = list(problems)
+        h = ctypes.c_void_p()
+        arr = (ctypes.c_void_p * len(self.problems))(*[p.handle.value for p in self.problems])
+        _check(lib().mfs_batch_create(ctx.handle, len(self.problems), arr, ctypes.byref(h)))
+        self.handle, self.ctx = h, ctx
+
+    def apply_stokes(self, us, ps, yus, yps, transpose=False):
+        for P, u, p, yu, yp in zip(self.problems, us, ps, yus, yps):
+            nu, npp = P._sizes(P.mesh.l_max)
+            _need(u, nu, None, "u"); _need(p, npp, u.dtype, "p")
+            _need(yu, nu, u.dtype, "yu"); _need(yp, npp, u.dtype, "yp")
+        prec = _prec_of(us[0])
+        _check(lib().mfs_batch_apply_stokes(self.handle, prec, int(transpose), _ptr_array(us), _ptr_array(ps),
+                                            _ptr_array(yus), _ptr_array(yps)))
+
+    def solve(self, fs, gs, us, ps, **opts):
+        o = Problem.default_opts(**opts)
+        stats = (SolveStats * len(self.problems))()
+        rc = lib().mfs_batch_solve(self.handle, ctypes.byref(o), _ptr_array(fs), _ptr_array(gs), _ptr_array(us),
+                                   _ptr_array(ps), stats)
+        if rc != OK:
+            raise MfsError(rc, lib().mfs_last_error().decode())
+        return [s.as_dict() for s in stats]
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.mfs_batch_destroy(self.handle)
             self.handle = None

@@ -168,7 +168,7 @@ constexpr size_t sweep_smem_bytes() {
 }
 
 template <typename T, int OP, bool BLEND>
-__global__ void __launch_bounds__(kSweepThreads, MFS_SWEEP_MINBLOCKS) stokes_tile_kernel(const ApplyParams<T> P) {
+__device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m, const int tidx, const int n_tiles) {
   constexpr bool HAS_U = (OP & (OP_A | OP_B)) != 0;
   constexpr bool HAS_P = (OP & OP_BT) != 0;
   constexpr bool OUT_U = (OP & (OP_A | OP_BT)) != 0;
@@ -189,9 +189,7 @@ __global__ void __launch_bounds__(kSweepThreads, MFS_SWEEP_MINBLOCKS) stokes_til
   __shared__ T qpo[6][4][3];      // physical offset of qp q of type pm from the cube corner
   __shared__ T dtab[64];          // d ln rho / dr table (first 64 entries)
 
-  const int m = blockIdx.y;
-  const int tidx = blockIdx.x;
-  const size_t tile_lin = (size_t)m * gridDim.x + tidx;
+  const size_t tile_lin = (size_t)m * n_tiles + tidx;
   const Tile tile = P.tiles[tidx];
   const MacroGeom<T>& G = P.geom[m];
   const int a0 = tile.ta * TT, b0 = tile.tb * TT, c0 = tile.tc * TT;
@@ -619,6 +617,28 @@ __global__ void __launch_bounds__(kSweepThreads, MFS_SWEEP_MINBLOCKS) stokes_til
       if (id >= 0) atomicAdd(&P.yp[id], yp_s[s]);
     }
   }
+}
+
+// one problem: grid (tiles, 60 macros)
+template <typename T, int OP, bool BLEND>
+__global__ void __launch_bounds__(kSweepThreads, MFS_SWEEP_MINBLOCKS) stokes_tile_kernel(const ApplyParams<T> P) {
+  sweep_tile<T, OP, BLEND>(P, blockIdx.y, blockIdx.x, gridDim.x);
+}
+// the same sweep compiled for one fewer resident CTA per SM (more registers per thread);
+// the autotuner picks between the two per level
+template <typename T, int OP, bool BLEND>
+__global__ void __launch_bounds__(kSweepThreads, MFS_SWEEP_MINBLOCKS - 1)
+    stokes_tile_kernel_wide(const ApplyParams<T> P) {
+  sweep_tile<T, OP, BLEND>(P, blockIdx.y, blockIdx.x, gridDim.x);
+}
+
+// an ensemble in one launch: block b works on tile map[b] = (problem, macro * 65536 + tile)
+template <typename T, int OP, bool BLEND>
+__global__ void __launch_bounds__(kSweepThreads, MFS_SWEEP_MINBLOCKS)
+    stokes_tile_batch_kernel(const ApplyParams<T>* __restrict__ params, const int2* __restrict__ map,
+                             const int* __restrict__ n_tiles) {
+  const int2 w = map[blockIdx.x];
+  sweep_tile<T, OP, BLEND>(params[w.x], w.y >> 16, w.y & 0xffff, n_tiles[w.x]);
 }
 
 }  // namespace mfs

@@ -21,27 +21,102 @@ struct PrecData<float> {
   static const float* dlnrho(mfs_problem* P) { return P->d_dlnrho32; }
 };
 
-template <typename T, int OP, bool BLEND>
+template <typename T, int OP, bool BLEND, int WIDE>
 static cudaError_t sweep_attr() {
   // opt in to more than 48 KB of dynamic shared memory once per instantiation
-  static cudaError_t e = cudaFuncSetAttribute(stokes_tile_kernel<T, OP, BLEND>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)sweep_smem_bytes<T, OP>());
+  static cudaError_t e = cudaFuncSetAttribute(
+      WIDE ? stokes_tile_kernel_wide<T, OP, BLEND> : stokes_tile_kernel<T, OP, BLEND>,
+      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem_bytes<T, OP>());
   return e;
 }
 
-template <typename T, int OP>
-static mfs_status run_sweep(const ApplyParams<T>& prm, int n_tiles, int blending, mfs_ctx* ctx) {
+template <typename T, int OP, int WIDE>
+static mfs_status run_sweep_v(const ApplyParams<T>& prm, int n_tiles, int blending, mfs_ctx* ctx) {
   dim3 grid(n_tiles, kMacroCells);
   const size_t smem = sweep_smem_bytes<T, OP>();
-  const cudaError_t attr = blending ? sweep_attr<T, OP, true>() : sweep_attr<T, OP, false>();
+  const cudaError_t attr = blending ? sweep_attr<T, OP, true, WIDE>() : sweep_attr<T, OP, false, WIDE>();
   MFS_CUDA(attr);
   auto ev = timing_events(ctx);
   if (ev.first) cudaEventRecord(ev.first, ctx->stream);
-  if (blending) stokes_tile_kernel<T, OP, true><<<grid, kSweepThreads, smem, ctx->stream>>>(prm);
-  else stokes_tile_kernel<T, OP, false><<<grid, kSweepThreads, smem, ctx->stream>>>(prm);
+  if (WIDE) {
+    if (blending) stokes_tile_kernel_wide<T, OP, true><<<grid, kSweepThreads, smem, ctx->stream>>>(prm);
+    else stokes_tile_kernel_wide<T, OP, false><<<grid, kSweepThreads, smem, ctx->stream>>>(prm);
+  } else {
+    if (blending) stokes_tile_kernel<T, OP, true><<<grid, kSweepThreads, smem, ctx->stream>>>(prm);
+    else stokes_tile_kernel<T, OP, false><<<grid, kSweepThreads, smem, ctx->stream>>>(prm);
+  }
   if (ev.second) cudaEventRecord(ev.second, ctx->stream);
   return MFS_OK;
+}
+
+// the hot FP32 sweeps (A alone: smoothers; fused forward: Krylov) have a tunable variant
+template <typename T, int OP>
+static mfs_status run_sweep(const ApplyParams<T>& prm, int n_tiles, int blending, mfs_ctx* ctx, int variant) {
+  constexpr bool tunable = sizeof(T) == 4 && (OP == OP_A || OP == (OP_A | OP_BT | OP_B | OP_BC));
+  if constexpr (tunable) {
+    if (variant == 1) return run_sweep_v<T, OP, 1>(prm, n_tiles, blending, ctx);
+  }
+  return run_sweep_v<T, OP, 0>(prm, n_tiles, blending, ctx);
+}
+
+template <typename T>
+ApplyParams<T> fill_params(mfs_problem* P, int lvl, int constrained, const T* u, const T* p, T* yu, T* yp,
+                           const T* psum) {
+  mfs_mesh* M = P->mesh;
+  const LevelData& L = M->levels[lvl];
+  ApplyParams<T> prm;
+  prm.u = u;
+  prm.p = p;
+  prm.yu = yu;
+  prm.yp = yp;
+  prm.eta = PrecData<T>::eta(P, lvl);
+  prm.dlnrho = PrecData<T>::dlnrho(P);
+  prm.n_dlnrho = P->n_dlnrho;
+  prm.psum = psum;
+  prm.geom = PrecData<T>::geom(M);
+  prm.tiles = L.d_tiles;
+  prm.tets = L.d_tets;
+  prm.classes = L.d_classes;
+  prm.ids2 = L.d_ids2;
+  prm.ids1 = L.d_ids1;
+  prm.n_p2 = L.nb2.total;
+  prm.n_p1 = L.nb1.total;
+  prm.n = L.n;
+  prm.r_cmb = (T)M->host.r_cmb;
+  prm.inv_dr = (T)(1.0 / (M->host.r_surf - M->host.r_cmb));
+  prm.constrained = constrained;
+  prm.bc_surface = P->bc_surface;
+  prm.bc_cmb = P->bc_cmb;
+  return prm;
+}
+
+template <typename T, int OP>
+static mfs_status run_batch(const ApplyParams<T>* dparams, const int2* map, const int* ntiles, int nblocks,
+                            int blending, cudaStream_t s) {
+  const size_t smem = sweep_smem_bytes<T, OP>();
+  static cudaError_t e1 = cudaFuncSetAttribute(stokes_tile_batch_kernel<T, OP, true>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static cudaError_t e0 = cudaFuncSetAttribute(stokes_tile_batch_kernel<T, OP, false>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  MFS_CUDA(blending ? e1 : e0);
+  if (blending) stokes_tile_batch_kernel<T, OP, true><<<nblocks, kSweepThreads, smem, s>>>(dparams, map, ntiles);
+  else stokes_tile_batch_kernel<T, OP, false><<<nblocks, kSweepThreads, smem, s>>>(dparams, map, ntiles);
+  MFS_CUDA(cudaGetLastError());
+  return MFS_OK;
+}
+
+// ensemble sweep: op in {forward fused, transposed fused}; params already on the device
+template <typename T>
+mfs_status launch_batch(const ApplyParams<T>* dparams, const int2* map, const int* ntiles, int nblocks, int op,
+                        int blending, cudaStream_t s) {
+  switch (op) {
+    case OP_A | OP_BT | OP_B | OP_BC:
+      return run_batch<T, OP_A | OP_BT | OP_B | OP_BC>(dparams, map, ntiles, nblocks, blending, s);
+    case OP_A | OP_BT | OP_B: return run_batch<T, OP_A | OP_BT | OP_B>(dparams, map, ntiles, nblocks, blending, s);
+    case OP_A | OP_BT | OP_CT | OP_B:
+      return run_batch<T, OP_A | OP_BT | OP_CT | OP_B>(dparams, map, ntiles, nblocks, blending, s);
+    default: set_error("internal: unsupported batched operator %d", op); return MFS_EINVAL;
+  }
 }
 
 template <typename T>
@@ -78,13 +153,13 @@ mfs_status launch_apply(mfs_problem* P, int lvl, int op, int constrained, int wi
   if ((op & OP_B) && withc_b) op |= OP_BC;
   const int bl = M->host.blending;
   switch (op) {
-    case OP_A: MFS_TRY((run_sweep<T, OP_A>(prm, L.n_tiles, bl, M->ctx))); break;
-    case OP_BT: MFS_TRY((run_sweep<T, OP_BT>(prm, L.n_tiles, bl, M->ctx))); break;
-    case OP_BT | OP_CT: MFS_TRY((run_sweep<T, OP_BT | OP_CT>(prm, L.n_tiles, bl, M->ctx))); break;
-    case OP_B: MFS_TRY((run_sweep<T, OP_B>(prm, L.n_tiles, bl, M->ctx))); break;
-    case OP_B | OP_BC: MFS_TRY((run_sweep<T, OP_B | OP_BC>(prm, L.n_tiles, bl, M->ctx))); break;
-    case OP_A | OP_BT | OP_B | OP_BC: MFS_TRY((run_sweep<T, OP_A | OP_BT | OP_B | OP_BC>(prm, L.n_tiles, bl, M->ctx))); break;
-    case OP_A | OP_BT | OP_CT | OP_B: MFS_TRY((run_sweep<T, OP_A | OP_BT | OP_CT | OP_B>(prm, L.n_tiles, bl, M->ctx))); break;
+    case OP_A: MFS_TRY((run_sweep<T, OP_A>(prm, L.n_tiles, bl, M->ctx, L.variant))); break;
+    case OP_BT: MFS_TRY((run_sweep<T, OP_BT>(prm, L.n_tiles, bl, M->ctx, L.variant))); break;
+    case OP_BT | OP_CT: MFS_TRY((run_sweep<T, OP_BT | OP_CT>(prm, L.n_tiles, bl, M->ctx, L.variant))); break;
+    case OP_B: MFS_TRY((run_sweep<T, OP_B>(prm, L.n_tiles, bl, M->ctx, L.variant))); break;
+    case OP_B | OP_BC: MFS_TRY((run_sweep<T, OP_B | OP_BC>(prm, L.n_tiles, bl, M->ctx, L.variant))); break;
+    case OP_A | OP_BT | OP_B | OP_BC: MFS_TRY((run_sweep<T, OP_A | OP_BT | OP_B | OP_BC>(prm, L.n_tiles, bl, M->ctx, L.variant))); break;
+    case OP_A | OP_BT | OP_CT | OP_B: MFS_TRY((run_sweep<T, OP_A | OP_BT | OP_CT | OP_B>(prm, L.n_tiles, bl, M->ctx, L.variant))); break;
     default: set_error("internal: unsupported operator combination %d", op); return MFS_EINVAL;
   }
   MFS_CUDA(cudaGetLastError());

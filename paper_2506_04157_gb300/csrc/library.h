@@ -70,6 +70,7 @@ struct LevelData {
   int* d_er_ci = nullptr;
   double* d_er_w = nullptr;
   int64_t n_tets = 0, n_surface = 0, n_cmb = 0;
+  int variant = 0;   // sweep variant chosen by mfs_autotune (0: default register budget)
 };
 
 template <typename T>
@@ -130,6 +131,15 @@ constexpr int kRedSlots = kRedBlocks + 64;
 template <typename T>
 mfs_status launch_apply(mfs_problem* P, int lvl, int op, int constrained, int withc_b, const T* u,
                         const T* p, T* yu, T* yp, const T* psum);
+
+template <typename T>
+struct ApplyParams;
+template <typename T>
+ApplyParams<T> fill_params(mfs_problem* P, int lvl, int constrained, const T* u, const T* p, T* yu, T* yp,
+                           const T* psum);
+template <typename T>
+mfs_status launch_batch(const ApplyParams<T>* dparams, const int2* map, const int* ntiles, int nblocks, int op,
+                        int blending, cudaStream_t s);
 
 // launch_apply plus the pressure projections of the constrained mode
 template <typename T>

@@ -1,0 +1,92 @@
+"""Ensembles in one sweep launch, and the sweep autotuner: results equal the per-problem
+applies / solves."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2506_04157_gb300 as mfs
+import workloads as W
+
+
+def make_problem(ctx, level, seed, contrast, bc=("dirichlet", "freeslip")):
+    mesh = mfs.Mesh(ctx, level)
+    prob = mfs.Problem(mesh, *bc)
+    x1 = mesh.coords(level, p2=False).T
+    prob.set_viscosity(torch.tensor(W.viscosity_plumes(x1, seed, contrast), device="cuda"))
+    prob.set_density(W.dlnrho_table_compressible())
+    return prob
+
+
+@pytest.fixture(scope="module")
+def ensemble():
+    ctx = mfs.Context(0)
+    probs = [make_problem(ctx, 3, 100, 1e4), make_problem(ctx, 2, 101, 1e6, ("freeslip", "dirichlet")),
+             make_problem(ctx, 4, 102, 1e5), make_problem(ctx, 3, 103, 1e6)]
+    return ctx, probs, mfs.Batch(ctx, probs)
+
+
+@pytest.mark.parametrize("transpose", [False, True])
+@pytest.mark.parametrize("dt", [torch.float64, torch.float32])
+def test_batch_apply_matches_individual(ensemble, dt, transpose):
+    ctx, probs, batch = ensemble
+    us, ps, yus, yps = [], [], [], []
+    for i, P in enumerate(probs):
+        nu, npp = P._sizes(P.mesh.l_max)
+        us.append(torch.tensor(W.random_field(nu, 10 + i), dtype=dt, device="cuda"))
+        ps.append(torch.tensor(W.random_field(npp, 20 + i), dtype=dt, device="cuda"))
+        yus.append(torch.empty(nu, dtype=dt, device="cuda"))
+        yps.append(torch.empty(npp, dtype=dt, device="cuda"))
+    batch.apply_stokes(us, ps, yus, yps, transpose=transpose)
+    tol = 1e-12 if dt == torch.float64 else 1e-5
+    for P, u, p, yu, yp in zip(probs, us, ps, yus, yps):
+        ru, rp = torch.empty_like(yu), torch.empty_like(yp)
+        P.apply_stokes(P.mesh.l_max, u, p, ru, rp, transpose=transpose)
+        assert (torch.linalg.norm(yu - ru) / torch.linalg.norm(ru)).item() <= tol
+        assert (torch.linalg.norm(yp - rp) / torch.linalg.norm(rp)).item() <= tol
+
+
+def test_batch_solve_matches_individual(ensemble):
+    ctx, probs, batch = ensemble
+    small = [make_problem(ctx, 3, 110, 1e4), make_problem(ctx, 2, 111, 1e3, ("freeslip", "dirichlet"))]
+    b2 = mfs.Batch(ctx, small)
+    fs, gs = [], []
+    for i, P in enumerate(small):
+        P.setup_multigrid(1)
+        x2 = P.mesh.coords(P.mesh.l_max).T
+        T = W.temperature_blobs(x2, 30 + i)
+        xh = x2 / np.linalg.norm(x2, axis=1, keepdims=True)
+        fs.append(torch.tensor(np.concatenate([T * xh[:, 0], T * xh[:, 1], T * xh[:, 2]]), device="cuda"))
+        gs.append(torch.zeros(P._sizes(P.mesh.l_max)[1], dtype=torch.float64, device="cuda"))
+    us = [torch.zeros_like(f) for f in fs]
+    ps = [torch.zeros_like(g) for g in gs]
+    stats = b2.solve(fs, gs, us, ps, mixed=0)
+    for P, f, g, u, p, st in zip(small, fs, gs, us, ps, stats):
+        assert st["rel_residual"] <= 1e-8
+        u1, p1 = torch.zeros_like(u), torch.zeros_like(p)
+        P.solve(f, g, u1, p1, mixed=0)
+        assert (torch.linalg.norm(u - u1) / torch.linalg.norm(u1)).item() < 1e-6
+
+
+def test_autotune_keeps_results(ensemble, tmp_path):
+    ctx, probs, batch = ensemble
+    P = probs[2]
+    L = P.mesh.l_max
+    nu, npp = P._sizes(L)
+    u = torch.tensor(W.random_field(nu, 5), dtype=torch.float32, device="cuda")
+    p = torch.tensor(W.random_field(npp, 6), dtype=torch.float32, device="cuda")
+    y0u, y0p = torch.empty_like(u), torch.empty_like(p)
+    P.apply_stokes(L, u, p, y0u, y0p)
+    cache = str(tmp_path / "tune.json")
+    choice = P.autotune(cache)
+    assert all(v in (0, 1) for v in choice) and len(choice) == L + 1
+    rows = json.load(open(cache))
+    assert [r["variant"] for r in rows] == choice
+    assert P.autotune(cache) == choice          # read back from the cache
+    y1u, y1p = torch.empty_like(u), torch.empty_like(p)
+    P.apply_stokes(L, u, p, y1u, y1p)
+    assert (torch.linalg.norm(y1u - y0u) / torch.linalg.norm(y0u)).item() <= 1e-5
