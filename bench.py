@@ -109,6 +109,18 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(use), "window": where}
 
 
+def aggregate(ms_local, steps, units_per_rank, world, device):
+    """Max of the timed region over ranks; whole-job throughput = all ranks' units / that
+    time (replicas: every rank processes its own copy of the workload)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_per_step = float(t.item()) / steps
+    return ms_per_step, world * units_per_rank / (ms_per_step * 1e-3) / 1e9
+
+
 def setup_problem(level, device):
     import numpy as np
     import torch
@@ -173,12 +185,7 @@ def run_ours(args, rank, world, device):
     if world > 1:
         dist.barrier()
     ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    ms_per_step = ms_max / args.steps
-    value = world * dofs / (ms_per_step * 1e-3) / 1e9
+    ms_per_step, value = aggregate(ms, args.steps, dofs, world, dev)
 
     # end to end through the public API with host buffers (pinned), copies inside the timing
     hu = torch.tensor(W.random_field(nu, 7, np.float32)).pin_memory()

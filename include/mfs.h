@@ -160,6 +160,14 @@ mfs_status mfs_apply_BT(mfs_problem* prob, int lvl, mfs_prec prec, mfs_bcmode mo
 mfs_status mfs_apply_stokes(mfs_problem* prob, int lvl, mfs_prec prec, int transpose, const void* u,
                             const void* p, void* yu, void* yp);
 
+/* Buoyancy load vector on the finest level (paper Eq. SaddlePointStructure,
+ * f_i = -int (Ra/Pe) rho alpha T g . phi_i with g = -x/|x|):
+ *   f_(a,c) = scale int rho(r) T (x/|x|)_c phi_a dx,
+ * T_p2 a nodal P2 field [n_p2] (FP64, device), rho(r) = exp(int_{r_surf}^{r} d ln rho/dr)
+ * from the mfs_set_density table (piecewise linear, integrated exactly; rho(r_surf) = 1),
+ * f: [3][n_p2] (FP64, device, overwritten).  Errors: MFS_EINVAL, MFS_ECUDA. */
+mfs_status mfs_rhs_buoyancy(mfs_problem* prob, const double* T_p2, double scale, double* f);
+
 /* ---------------------------------------------------------------- multigrid layer
  * (paper Sec. 5.2.2).  mfs_setup_multigrid builds, for levels l_min..l_max: the
  * boundary-node lists (Dirichlet / free-slip with their normals), the P2 transfer

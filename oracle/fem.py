@@ -284,3 +284,33 @@ def tets_touching(level, p2_nodes=None, p1_nodes=None):
     if p1_nodes is not None:
         mask |= np.isin(level.tet_p1, p1_nodes).any(axis=1)
     return np.nonzero(mask)[0]
+
+
+def rho_profile(table, r, r_cmb, r_surf):
+    """rho(r) = exp(int_{r_surf}^{r} d ln rho/dr) for the piecewise-linear table, by
+    composite Simpson integration on a fine grid (rho(r_surf) = 1)."""
+    r = np.asarray(r, dtype=np.float64)
+    out = np.empty_like(r)
+    for i, rr in np.ndenumerate(r):
+        s = np.linspace(rr, r_surf, 2001)
+        g = interp_table(table, s, r_cmb, r_surf)
+        h = (r_surf - rr) / 2000.0
+        integ = h / 3 * (g[0] + g[-1] + 4 * g[1:-1:2].sum() + 2 * g[2:-1:2].sum())
+        out[i] = np.exp(-integ)
+    return out
+
+
+def buoyancy_rhs(level, T_p2, dlnrho_table, scale=1.0):
+    """f_(a,c) = scale sum_e sum_q W_q rho(r_q) T_q (x_q/|x_q|)_c phi_a(q), element by element."""
+    mesh = level.mesh
+    geo = Geometry(mesh, level.tet_x, level.tet_prism)
+    Tq = np.asarray(T_p2)[level.tet_p2] @ geo.phi.T                       # (E,Q)
+    r = np.linalg.norm(geo.x, axis=-1)
+    rho = rho_profile(dlnrho_table, r, mesh.r_cmb, mesh.r_surf)
+    xh = geo.x / r[..., None]
+    c = scale * geo.W * rho * Tq                                          # (E,Q)
+    fe = np.einsum("eq,eqd,qa->eda", c, xh, geo.phi)                      # (E,3,10)
+    f = np.zeros(3 * level.n_p2)
+    idx = np.stack([level.tet_p2 + d * level.n_p2 for d in range(3)], axis=1)   # (E,3,10)
+    np.add.at(f, idx.reshape(-1), fe.reshape(-1))
+    return f

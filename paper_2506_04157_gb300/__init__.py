@@ -92,6 +92,7 @@ _SIGS = {
     "mfs_adjoint_solve": ([_vp, ctypes.POINTER(SolveOpts), _vp, _vp, _vp, _vp, ctypes.POINTER(SolveStats)], _i),
     "mfs_grad_log_eta": ([_vp, _vp, _vp, _vp], _i),
     "mfs_autotune": ([_vp, ctypes.c_char_p], _i),
+    "mfs_rhs_buoyancy": ([_vp, _vp, _d, _vp], _i),
     "mfs_get_tuning": ([_vp, _i, ctypes.POINTER(_i)], _i),
     "mfs_batch_create": ([_vp, _i, _vp, ctypes.POINTER(_vp)], _i),
     "mfs_batch_destroy": ([_vp], _i),
@@ -299,6 +300,13 @@ class Problem:
         nu, _ = self._sizes(level)
         _need(f, nu, None, "f"); _need(u, nu, f.dtype, "u")
         _check(lib().mfs_vcycle(self.handle, level, _prec_of(f), steps, degree, _ptr(f), _ptr(u)))
+
+    def rhs_buoyancy(self, T_p2, f, scale=1.0):
+        """f = scale * int rho T (x/|x|) . phi (FP64 device tensors: T [n_p2], f [3 n_p2])."""
+        import torch
+        nu, _ = self._sizes(self.mesh.l_max)
+        _need(T_p2, nu // 3, torch.float64, "T_p2"); _need(f, nu, torch.float64, "f")
+        _check(lib().mfs_rhs_buoyancy(self.handle, _ptr(T_p2), float(scale), _ptr(f)))
 
     # ---- autotuning
     def autotune(self, cache_path=None):

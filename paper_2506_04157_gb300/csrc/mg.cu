@@ -688,3 +688,110 @@ mfs_status grad_log_eta(mfs_problem* P, int lvl, const double* u, const double* 
 }
 
 }  // namespace mfs
+
+namespace mfs {
+
+// ------------------------------------------------------------------------- buoyancy load vector
+// f_(a,c) = scale sum_q w|det J| rho(r_q) T_q (x_q/|x_q|)_c phi_a(q); T nodal P2 (FP64), rho from
+// the d ln rho / dr table integrated exactly (piecewise linear) with rho(r_surf) = 1.
+__device__ double rho_of(const double* tab, int nt, double r, double r0, double r1) {
+  if (nt <= 1) return exp(tab[0] * (r - r1));
+  const double h = (r1 - r0) / (nt - 1);
+  double s = (r - r0) / h;
+  s = s < 0 ? 0 : (s > nt - 1 ? nt - 1 : s);
+  int i = (int)s;
+  i = i > nt - 2 ? nt - 2 : i;
+  const double f = s - i;
+  // integral of g from r to r1: the part of cell i above r, then the full cells above
+  const double gr = (1 - f) * tab[i] + f * tab[i + 1];
+  double integ = 0.5 * (gr + tab[i + 1]) * (1 - f) * h;
+  for (int k = i + 1; k < nt - 1; ++k) integ += 0.5 * (tab[k] + tab[k + 1]) * h;
+  return exp(-integ);
+}
+
+__global__ void __launch_bounds__(128) k_buoyancy_sweep(const ApplyParams<double> P, int blend, const double* __restrict__ T,
+                                                        double scale, double r_surf, double* __restrict__ f) {
+  __shared__ double fs[3 * NSLOT2];
+  const int m = blockIdx.y, tidx = blockIdx.x;
+  const size_t lin = (size_t)m * gridDim.x + tidx;
+  const Tile tile = P.tiles[tidx];
+  const MacroGeom<double>& G = P.geom[m];
+  const int n = P.n;
+  const int64_t n2 = P.n_p2;
+  const int* tab2 = P.ids2 + lin * NSLOT2;
+  for (int s = threadIdx.x; s < 3 * NSLOT2; s += blockDim.x) fs[s] = 0.0;
+  __syncthreads();
+  const double QA = MFS_QA, QB = MFS_QB;
+  const double C0 = G.absdet / (24.0 * n * (double)n * n);
+  const int2 cinfo = P.classes[tile.cls];
+  for (int t = threadIdx.x; t < cinfo.y; t += blockDim.x) {
+    const int code = P.tets[cinfo.x + t];
+    const int ci = code & 15, cj = (code >> 4) & 15, ck = (code >> 8) & 15, pmu = code >> 12;
+    const int p0 = perm_at(pmu, 0), p1 = perm_at(pmu, 1), p2 = perm_at(pmu, 2);
+    const int base = ci + 5 * cj + 25 * ck;
+    double Tv[10];
+    for (int a = 0; a < 10; ++a) Tv[a] = T[tab2[base + slot_off(pmu, a)] & 0x1fffffff];
+    const double qx = tile.ta * TT + ci, qy = tile.tb * TT + cj, qz = tile.tc * TT + ck;
+    double out[10][3];
+    for (int a = 0; a < 10; ++a) out[a][0] = out[a][1] = out[a][2] = 0.0;
+    for (int q = 0; q < 4; ++q) {
+      double K[3][3], hr, rinv, x[3];
+      if (blend) qp_geometry<double, true>(G, n, p0, p1, p2, q, qx, qy, qz, K, hr, rinv, x);
+      else qp_geometry<double, false>(G, n, p0, p1, p2, q, qx, qy, qz, K, hr, rinv, x);
+      const double lam[4] = {q == 0 ? QA : QB, q == 1 ? QA : QB, q == 2 ? QA : QB, q == 3 ? QA : QB};
+      double phi[10];
+      for (int a = 0; a < 4; ++a) phi[a] = lam[a] * (2 * lam[a] - 1);
+      phi[4] = 4 * lam[0] * lam[1];
+      phi[5] = 4 * lam[0] * lam[2];
+      phi[6] = 4 * lam[0] * lam[3];
+      phi[7] = 4 * lam[1] * lam[2];
+      phi[8] = 4 * lam[1] * lam[3];
+      phi[9] = 4 * lam[2] * lam[3];
+      double Tq = 0.0;
+      for (int a = 0; a < 10; ++a) Tq += phi[a] * Tv[a];
+      const double h = x[0] * G.nh[0] + x[1] * G.nh[1] + x[2] * G.nh[2];
+      const double rad = blend ? h / G.delta : 1.0 / rinv;
+      const double W = C0 * hr * hr * hr;
+      const double rho = rho_of(P.dlnrho, P.n_dlnrho, rad, (double)P.r_cmb, r_surf);
+      const double c = scale * W * rho * Tq * rinv;
+      for (int a = 0; a < 10; ++a)
+        for (int d = 0; d < 3; ++d) out[a][d] += c * x[d] * phi[a];
+    }
+    for (int a = 0; a < 10; ++a)
+      for (int d = 0; d < 3; ++d) atomicAdd(&fs[d * NSLOT2 + base + slot_off(pmu, a)], out[a][d]);
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < NSLOT2; s += blockDim.x) {
+    const int code = tab2[s];
+    if (code < 0) continue;
+    const int64_t id = code & 0x1fffffff;
+    for (int d = 0; d < 3; ++d) atomicAdd(&f[d * n2 + id], fs[d * NSLOT2 + s]);
+  }
+}
+
+mfs_status rhs_buoyancy(mfs_problem* P, int lvl, const double* T, double scale, double* f) {
+  mfs_mesh* M = P->mesh;
+  const LevelData& L = M->levels[lvl];
+  cudaStream_t s = M->ctx->stream;
+  MFS_CUDA(cudaMemsetAsync(f, 0, sizeof(double) * 3 * (size_t)L.nb2.total, s));
+  dim3 grid(L.n_tiles, kMacroCells);
+  ApplyParams<double> prm = sweep_params<double>(P, lvl);
+  prm.dlnrho = P->d_dlnrho64;
+  prm.n_dlnrho = P->n_dlnrho;
+  prm.r_cmb = M->host.r_cmb;
+  k_buoyancy_sweep<<<grid, 128, 0, s>>>(prm, M->host.blending, T, scale, M->host.r_surf, f);
+  MFS_CUDA(cudaGetLastError());
+  return MFS_OK;
+}
+
+}  // namespace mfs
+
+using namespace mfs;
+
+mfs_status mfs_rhs_buoyancy(mfs_problem* P, const double* T_p2, double scale, double* f) {
+  if (!P || !T_p2 || !f) {
+    set_error("null argument");
+    return MFS_EINVAL;
+  }
+  return rhs_buoyancy(P, P->mesh->l_max, T_p2, scale, f);
+}

@@ -1,0 +1,44 @@
+"""bench.py's multi-rank aggregation on CPU with two gloo ranks: the slowest rank's time
+sets the step time and the value counts every rank's work."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    ms_local = 100.0 if rank == 0 else 250.0
+    out = bench.aggregate(ms_local, 10, 1_000_000, world, "cpu")
+    q.put((rank, out))
+    dist.destroy_process_group()
+
+
+def test_two_rank_aggregation():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = dict(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+    for rank in (0, 1):
+        ms_per_step, value = res[rank]
+        assert ms_per_step == pytest.approx(25.0)
+        assert value == pytest.approx(2 * 1_000_000 / 0.025 / 1e9)

@@ -107,3 +107,20 @@ def test_power_iteration_estimate():
     lo, hi = prob.cheb_bounds(2)
     assert abs(hi - H.bounds[2][1]) <= 0.05 * H.bounds[2][1]
     assert np.isclose(lo, hi / 20)
+
+
+@pytest.mark.parametrize("table", [(-0.3781, -0.3781), (-1.0, -0.2, 0.5, -0.7)])
+def test_buoyancy_rhs(table):
+    from oracle.fem import buoyancy_rhs
+    mesh = MacroMesh()
+    L = Level(mesh, 2)
+    ctx = mfs.Context(0)
+    gm = mfs.Mesh(ctx, 2)
+    prob = mfs.Problem(gm)
+    prob.set_viscosity(torch.tensor(W.viscosity_radial(L.p1_x), device="cuda"))
+    prob.set_density(np.array(table))
+    T = W.temperature_blobs(L.p2_x, 9)
+    f = torch.empty(3 * L.n_p2, dtype=torch.float64, device="cuda")
+    prob.rhs_buoyancy(torch.tensor(T, device="cuda"), f, scale=2.5)
+    ref = buoyancy_rhs(L, T, np.array(table), scale=2.5)
+    assert rel(f.cpu().numpy(), ref) <= 1e-10
