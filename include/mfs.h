@@ -237,6 +237,10 @@ typedef struct {
   int applies;        /* finest-level A / saddle-point sweeps issued by the Krylov layers */
   double r0_norm, r_norm, rel_residual;   /* FP64 projected residual norms */
   double time_ms;     /* wall time of the solve (setup excluded) */
+  /* wall time inside the preconditioner's parts (each ends in a host synchronisation, so
+   * the times include the device work): A-block CG (A_hat^-1), Schur solve (V-cycle BFBT,
+   * with the mass CGs it calls), and the mass CGs alone */
+  double time_Ahat_ms, time_Sinv_ms, time_Minv_ms;
 } mfs_solve_stats;
 
 void mfs_solve_opts_default(mfs_solve_opts* opts);

@@ -287,17 +287,20 @@ def tets_touching(level, p2_nodes=None, p1_nodes=None):
 
 
 def rho_profile(table, r, r_cmb, r_surf):
-    """rho(r) = exp(int_{r_surf}^{r} d ln rho/dr) for the piecewise-linear table, by
-    composite Simpson integration on a fine grid (rho(r_surf) = 1)."""
+    """rho(r) = exp(int_{r_surf}^{r} d ln rho/dr) for the piecewise-linear table (rho(r_surf)
+    = 1).  The antiderivative of a piecewise-linear function is exact with the trapezoidal
+    rule on its breakpoints: G at the table nodes by cumulative trapezoids, inside a cell
+    one more trapezoid up to r."""
+    table = np.atleast_1d(np.asarray(table, dtype=np.float64))
     r = np.asarray(r, dtype=np.float64)
-    out = np.empty_like(r)
-    for i, rr in np.ndenumerate(r):
-        s = np.linspace(rr, r_surf, 2001)
-        g = interp_table(table, s, r_cmb, r_surf)
-        h = (r_surf - rr) / 2000.0
-        integ = h / 3 * (g[0] + g[-1] + 4 * g[1:-1:2].sum() + 2 * g[2:-1:2].sum())
-        out[i] = np.exp(-integ)
-    return out
+    if table.size == 1:
+        return np.exp(table[0] * (r - r_surf))
+    nodes = np.linspace(r_cmb, r_surf, table.size)
+    G_nodes = np.concatenate([[0.0], np.cumsum(0.5 * (table[1:] + table[:-1]) * np.diff(nodes))])
+    rc = np.clip(r, r_cmb, r_surf)
+    k = np.minimum(np.searchsorted(nodes, rc, side="right") - 1, table.size - 2)
+    G_r = G_nodes[k] + 0.5 * (table[k] + interp_table(table, rc, r_cmb, r_surf)) * (rc - nodes[k])
+    return np.exp(-(G_nodes[-1] - G_r))
 
 
 def buoyancy_rhs(level, T_p2, dlnrho_table, scale=1.0):

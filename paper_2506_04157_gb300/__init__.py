@@ -49,7 +49,9 @@ class SolveStats(ctypes.Structure):
                 ("cg_X_calls", ctypes.c_int), ("cg_M_calls", ctypes.c_int), ("cg_A_max", ctypes.c_int),
                 ("cg_X_max", ctypes.c_int), ("cg_M_max", ctypes.c_int), ("vcycles", ctypes.c_int),
                 ("applies", ctypes.c_int), ("r0_norm", ctypes.c_double), ("r_norm", ctypes.c_double),
-                ("rel_residual", ctypes.c_double), ("time_ms", ctypes.c_double)]
+                ("rel_residual", ctypes.c_double), ("time_ms", ctypes.c_double),
+                ("time_Ahat_ms", ctypes.c_double), ("time_Sinv_ms", ctypes.c_double),
+                ("time_Minv_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

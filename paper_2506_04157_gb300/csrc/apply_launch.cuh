@@ -121,7 +121,7 @@ mfs_status launch_batch(const ApplyParams<T>* dparams, const int2* map, const in
 
 template <typename T>
 mfs_status launch_apply(mfs_problem* P, int lvl, int op, int constrained, int withc_b, const T* u,
-                             const T* p, T* yu, T* yp, const T* psum) {
+                             const T* p, T* yu, T* yp, const T* psum, int zero_out) {
   mfs_mesh* M = P->mesh;
   const LevelData& L = M->levels[lvl];
   cudaStream_t s = M->ctx->stream;
@@ -148,8 +148,8 @@ mfs_status launch_apply(mfs_problem* P, int lvl, int op, int constrained, int wi
   prm.constrained = constrained;
   prm.bc_surface = P->bc_surface;
   prm.bc_cmb = P->bc_cmb;
-  if (op & (OP_A | OP_BT)) MFS_CUDA(cudaMemsetAsync(yu, 0, sizeof(T) * 3 * (size_t)L.nb2.total, s));
-  if (op & OP_B) MFS_CUDA(cudaMemsetAsync(yp, 0, sizeof(T) * (size_t)L.nb1.total, s));
+  if (zero_out && (op & (OP_A | OP_BT))) MFS_CUDA(cudaMemsetAsync(yu, 0, sizeof(T) * 3 * (size_t)L.nb2.total, s));
+  if (zero_out && (op & OP_B)) MFS_CUDA(cudaMemsetAsync(yp, 0, sizeof(T) * (size_t)L.nb1.total, s));
   if ((op & OP_B) && withc_b) op |= OP_BC;
   const int bl = M->host.blending;
   switch (op) {

@@ -96,6 +96,7 @@ mfs_status mfs_autotune(mfs_problem* P, const char* cache_path) {
     timed = true;
   }
   for (int l = 0; l <= L; ++l) M->levels[l].variant = chosen[l];
+  M->tuning_gen++;
   if (cache_path && timed) {
     if (FILE* f = std::fopen(cache_path, "w")) {
       std::fprintf(f, "[\n");

@@ -105,6 +105,7 @@ struct mfs_mesh {
   mfs::MacroGeom<double>* d_geom64 = nullptr;
   mfs::MacroGeom<float>* d_geom32 = nullptr;
   std::vector<mfs::LevelData> levels;
+  int tuning_gen = 0;   // bumped when a level's sweep variant changes (captured graphs go stale)
 };
 
 struct mfs_problem {
@@ -128,9 +129,11 @@ constexpr int kRedBlocks = 512;     // partial sums of the two-pass reductions
 constexpr int kRedSlots = kRedBlocks + 64;
 
 // ---- launchers (apply.cu) ----
+// The sweep adds into yu / yp; they are zeroed first unless zero_out == 0 (the caller
+// guarantees zeros, e.g. the smoother's fused update leaves its apply buffer zeroed).
 template <typename T>
 mfs_status launch_apply(mfs_problem* P, int lvl, int op, int constrained, int withc_b, const T* u,
-                        const T* p, T* yu, T* yp, const T* psum);
+                        const T* p, T* yu, T* yp, const T* psum, int zero_out = 1);
 
 template <typename T>
 struct ApplyParams;

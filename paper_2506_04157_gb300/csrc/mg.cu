@@ -75,12 +75,29 @@ __device__ __forceinline__ double dblock_sum(double v) {
   return v;
 }
 
+// Block sum of per-thread partials held in T: the warp stage adds in T (FP32 lanes are
+// 64x the FP64 rate on this part), the across-warp stage in FP64; thread 0 gets the sum.
+template <typename T>
+__device__ __forceinline__ double block_sum_mixed(T v) {
+  __shared__ double red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = (double)v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)((blockDim.x + 31) >> 5); ++k) s += red[k];
+  return s;
+}
+
 // per-thread partial in T over a fixed stride pattern, block and final sums in FP64
 template <typename T>
 __global__ void k_dot_part(int64_t n, const T* __restrict__ x, const T* __restrict__ y, double* __restrict__ part) {
   T acc = T(0);
   GRID_STRIDE(i, n) acc += x[i] * y[i];
-  const double s = dblock_sum((double)acc);
+  const double s = block_sum_mixed(acc);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 __global__ void k_dot_final(const double* __restrict__ part, int np, double* __restrict__ out) {
@@ -155,6 +172,125 @@ __global__ void k_spmv3(int nrows, const int* __restrict__ rp, const int* __rest
       y[r] = alpha * s0 + beta * y[r];
       y[nr + r] = alpha * s1 + beta * y[nr + r];
       y[2 * nr + r] = alpha * s2 + beta * y[2 * nr + r];
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_restrict_residual(int nrows, const int* __restrict__ rp, const int* __restrict__ ci,
+                                    const T* __restrict__ w, int64_t ncols, const T* __restrict__ b,
+                                    const T* __restrict__ t, T* __restrict__ y) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += gridDim.x * blockDim.x) {
+    T s0 = T(0), s1 = T(0), s2 = T(0);
+    for (int k = rp[r]; k < rp[r + 1]; ++k) {
+      const int64_t j = ci[k];
+      const T wk = w[k];
+      s0 += wk * (b[j] - t[j]);
+      s1 += wk * (b[ncols + j] - t[ncols + j]);
+      s2 += wk * (b[2 * ncols + j] - t[2 * ncols + j]);
+    }
+    const int64_t nr = nrows;
+    y[r] = s0;
+    y[nr + r] = s1;
+    y[2 * nr + r] = s2;
+  }
+}
+template <typename T>
+__global__ void k_prolong_add(int nrows, const int* __restrict__ rp, const int* __restrict__ ci,
+                              const T* __restrict__ w, int64_t ncols, const T* __restrict__ xc, T* __restrict__ x,
+                              T* __restrict__ t) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += gridDim.x * blockDim.x) {
+    T s0 = T(0), s1 = T(0), s2 = T(0);
+    for (int k = rp[r]; k < rp[r + 1]; ++k) {
+      const int64_t j = ci[k];
+      const T wk = w[k];
+      s0 += wk * xc[j];
+      s1 += wk * xc[ncols + j];
+      s2 += wk * xc[2 * ncols + j];
+    }
+    const int64_t nr = nrows;
+    x[r] += s0;
+    x[nr + r] += s1;
+    x[2 * nr + r] += s2;
+    t[r] = t[nr + r] = t[2 * nr + r] = T(0);
+  }
+}
+// Jacobi-preconditioned Chebyshev update of one smoothing application (see Blas::cheb_update).
+// Streams 16-byte vectors (V elements per access) from offset `first`; elements before it
+// and the ragged tail go element by element.
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+};
+template <typename T, int V>
+__device__ __forceinline__ void cheb_elems(int mode, const T* b, T* t, T* r, const T* dinv, T* d, T* x, T cz, T cd,
+                                           int64_t i) {
+  using VT = typename Vec16<T>::type;
+  T bv[V], tv[V], rv[V], iv[V], dv[V], xv[V];
+  auto ld = [&](const T* p, T* o) {
+    if (V == 1) o[0] = p[i];
+    else *reinterpret_cast<VT*>(o) = *reinterpret_cast<const VT*>(p + i);
+  };
+  auto st = [&](T* p, const T* o) {
+    if (V == 1) p[i] = o[0];
+    else *reinterpret_cast<VT*>(p + i) = *reinterpret_cast<const VT*>(o);
+  };
+  ld(dinv, iv);
+  if (mode != 2) ld(b, bv);
+  if (mode != 0) ld(t, tv);
+  if (mode == 2) ld(r, rv);
+  if (cd != T(0)) ld(d, dv);
+  if (mode != 0) ld(x, xv);
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    const T rk = mode == 0 ? bv[k] : (mode == 1 ? bv[k] : rv[k]) - tv[k];
+    rv[k] = rk;
+    T dk = cz * iv[k] * rk;
+    if (cd != T(0)) dk += cd * dv[k];
+    dv[k] = dk;
+    xv[k] = mode == 0 ? dk : xv[k] + dk;
+    tv[k] = T(0);
+  }
+  st(t, tv);
+  st(r, rv);
+  st(d, dv);
+  st(x, xv);
+}
+template <typename T>
+__global__ void k_cheb_update(int64_t n, int64_t first, int mode, const T* __restrict__ b, T* __restrict__ t,
+                              T* __restrict__ r, const T* __restrict__ dinv, T* __restrict__ d, T* __restrict__ x, T cz,
+                              T cd) {
+  constexpr int V = 16 / sizeof(T);
+  const int64_t nv = (n - first) / V;
+  GRID_STRIDE(k, nv) cheb_elems<T, V>(mode, b, t, r, dinv, d, x, cz, cd, first + k * V);
+  const int64_t rest = first + nv * V;
+  GRID_STRIDE(i, first) cheb_elems<T, 1>(mode, b, t, r, dinv, d, x, cz, cd, i);
+  GRID_STRIDE(i, n - rest) cheb_elems<T, 1>(mode, b, t, r, dinv, d, x, cz, cd, rest + i);
+}
+template <typename T>
+__global__ void k_bproject2(int nb, const int* __restrict__ ids, const int8_t* __restrict__ kind,
+                            const T* __restrict__ nrm, int64_t n_p2, T* __restrict__ v, T* __restrict__ w) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+    const int64_t id = ids[k];
+    if (kind[k] == 1) {
+      v[id] = v[n_p2 + id] = v[2 * n_p2 + id] = T(0);
+      w[id] = w[n_p2 + id] = w[2 * n_p2 + id] = T(0);
+    } else {
+      const T nx = nrm[3 * k], ny = nrm[3 * k + 1], nz = nrm[3 * k + 2];
+      const T un = v[id] * nx + v[n_p2 + id] * ny + v[2 * n_p2 + id] * nz;
+      v[id] -= un * nx;
+      v[n_p2 + id] -= un * ny;
+      v[2 * n_p2 + id] -= un * nz;
+      const T wn = w[id] * nx + w[n_p2 + id] * ny + w[2 * n_p2 + id] * nz;
+      w[id] -= wn * nx;
+      w[n_p2 + id] -= wn * ny;
+      w[2 * n_p2 + id] -= wn * nz;
     }
   }
 }
@@ -318,7 +454,9 @@ __global__ void __launch_bounds__(128) k_diag_sweep(const ApplyParams<T> P, T* _
 
 // y += M_{1/eta} p (DIAG: y += diag(M_{1/eta})): int (1/eta_q) psi_j psi_k over blended tets
 template <typename T, bool BLEND, bool DIAG>
-__global__ void __launch_bounds__(128) k_mass_sweep(const ApplyParams<T> P, const T* __restrict__ pin, T* __restrict__ y) {
+__global__ void __launch_bounds__(128) k_mass_sweep(const ApplyParams<T> P, const T* __restrict__ pin, T* __restrict__ y,
+                                                     const double* __restrict__ active) {
+  if (active && !(*active > 0.0)) return;
   __shared__ T ps[NSLOT1], ys[NSLOT1], eta_s[NSLOT1];
   __shared__ int gid[NSLOT1];
   const int m = blockIdx.y, tidx = blockIdx.x;
@@ -409,6 +547,33 @@ void Blas<T>::spmv3(const Csr& P, int64_t ncols, const T* x, T alpha, T beta, T*
   k_spmv3<T><<<blocks_for(P.nrows), 256, 0, s>>>(P.nrows, P.rp, P.ci, P.template w<T>(), ncols, x, alpha, beta, y);
 }
 template <typename T>
+void Blas<T>::cheb_update(int64_t n, int mode, const T* b, T* t, T* r, const T* dinv, T* d, T* x, T cz, T cd,
+                          cudaStream_t s) {
+  // all operands must share the offset from a 16-byte boundary for the vector loads
+  const uintptr_t mis = reinterpret_cast<uintptr_t>(dinv) & 15;
+  const void* ptrs[6] = {b, t, r, dinv, d, x};
+  bool same = true;
+  for (const void* q : ptrs) same = same && (reinterpret_cast<uintptr_t>(q) & 15) == mis;
+  int64_t first = same ? (int64_t)(((16 - mis) & 15) / sizeof(T)) : n;
+  if (first > n) first = n;
+  constexpr int V = 16 / sizeof(T);
+  const int64_t work = first == n ? n : (n - first) / V + V;   // misaligned operands: scalar loop
+  k_cheb_update<T><<<blocks_for(work), 256, 0, s>>>(n, first, mode, b, t, r, dinv, d, x, cz, cd);
+}
+template <typename T>
+void Blas<T>::bproject2(const BoundaryList& B, int64_t n_p2, T* v, T* w, cudaStream_t s) {
+  if (B.nb == 0) return;
+  k_bproject2<T><<<blocks_for(B.nb), 256, 0, s>>>(B.nb, B.ids, B.kind, B.template normals<T>(), n_p2, v, w);
+}
+template <typename T>
+void Blas<T>::restrict_residual(const Csr& R, int64_t ncols, const T* b, const T* t, T* y, cudaStream_t s) {
+  k_restrict_residual<T><<<blocks_for(R.nrows), 256, 0, s>>>(R.nrows, R.rp, R.ci, R.template w<T>(), ncols, b, t, y);
+}
+template <typename T>
+void Blas<T>::prolong_add(const Csr& P, int64_t ncols, const T* xc, T* x, T* t, cudaStream_t s) {
+  k_prolong_add<T><<<blocks_for(P.nrows), 256, 0, s>>>(P.nrows, P.rp, P.ci, P.template w<T>(), ncols, xc, x, t);
+}
+template <typename T>
 void Blas<T>::gemv_f64(int n, const double* A, const T* b, T* x, cudaStream_t s) {
   k_gemv_f64<T><<<blocks_for((int64_t)n * 32, 256, 4096), 256, 0, s>>>(n, A, b, x);
 }
@@ -466,20 +631,20 @@ mfs_status diag_A(mfs_problem* P, int lvl, const BoundaryList& B, T* diag) {
 }
 
 template <typename T>
-mfs_status mass_apply(mfs_problem* P, int lvl, const T* pin, T* y, int diag_only) {
+mfs_status mass_apply(mfs_problem* P, int lvl, const T* pin, T* y, int diag_only, const double* active, int zero_out) {
   mfs_mesh* M = P->mesh;
   const LevelData& L = M->levels[lvl];
   cudaStream_t s = M->ctx->stream;
-  MFS_CUDA(cudaMemsetAsync(y, 0, sizeof(T) * (size_t)L.nb1.total, s));
+  if (zero_out) MFS_CUDA(cudaMemsetAsync(y, 0, sizeof(T) * (size_t)L.nb1.total, s));
   dim3 grid(L.n_tiles, kMacroCells);
   ApplyParams<T> prm = sweep_params<T>(P, lvl);
   const bool bl = M->host.blending != 0;
   if (diag_only) {
-    if (bl) k_mass_sweep<T, true, true><<<grid, 128, 0, s>>>(prm, pin, y);
-    else k_mass_sweep<T, false, true><<<grid, 128, 0, s>>>(prm, pin, y);
+    if (bl) k_mass_sweep<T, true, true><<<grid, 128, 0, s>>>(prm, pin, y, active);
+    else k_mass_sweep<T, false, true><<<grid, 128, 0, s>>>(prm, pin, y, active);
   } else {
-    if (bl) k_mass_sweep<T, true, false><<<grid, 128, 0, s>>>(prm, pin, y);
-    else k_mass_sweep<T, false, false><<<grid, 128, 0, s>>>(prm, pin, y);
+    if (bl) k_mass_sweep<T, true, false><<<grid, 128, 0, s>>>(prm, pin, y, active);
+    else k_mass_sweep<T, false, false><<<grid, 128, 0, s>>>(prm, pin, y, active);
   }
   MFS_CUDA(cudaGetLastError());
   return MFS_OK;
@@ -487,8 +652,124 @@ mfs_status mass_apply(mfs_problem* P, int lvl, const T* pin, T* y, int diag_only
 
 template mfs_status diag_A<float>(mfs_problem*, int, const BoundaryList&, float*);
 template mfs_status diag_A<double>(mfs_problem*, int, const BoundaryList&, double*);
-template mfs_status mass_apply<float>(mfs_problem*, int, const float*, float*, int);
-template mfs_status mass_apply<double>(mfs_problem*, int, const double*, double*, int);
+// stored quadrature weights of M_{1/eta} (FP64), see mass_weights
+template <bool BLEND>
+__global__ void __launch_bounds__(128) k_mass_weights(const ApplyParams<double> P, double* __restrict__ w) {
+  __shared__ double eta_s[NSLOT1];
+  const int m = blockIdx.y, tidx = blockIdx.x;
+  const size_t lin = (size_t)m * gridDim.x + tidx;
+  const Tile tile = P.tiles[tidx];
+  const MacroGeom<double>& G = P.geom[m];
+  const int n = P.n;
+  for (int s = threadIdx.x; s < NSLOT1; s += blockDim.x) {
+    const int id = P.ids1[lin * NSLOT1 + s];
+    eta_s[s] = id >= 0 ? P.eta[id] : 1.0;
+  }
+  __syncthreads();
+  const double QA = MFS_QA, QB = MFS_QB;
+  const double C0 = G.absdet / (24.0 * n * (double)n * n);
+  const int2 cinfo = P.classes[tile.cls];
+  for (int t = threadIdx.x; t < cinfo.y; t += blockDim.x) {
+    const int code = P.tets[cinfo.x + t];
+    const int ci = code & 15, cj = (code >> 4) & 15, ck = (code >> 8) & 15, pmu = code >> 12;
+    const int p0 = perm_at(pmu, 0), p1 = perm_at(pmu, 1), p2 = perm_at(pmu, 2);
+    const int base = ci + 5 * cj + 25 * ck;
+    double ev[4];
+    for (int a = 0; a < 4; ++a) ev[a] = eta_s[base + slot_off(pmu, a)];
+    const double qx = tile.ta * TT + ci, qy = tile.tb * TT + cj, qz = tile.tc * TT + ck;
+    for (int q = 0; q < 4; ++q) {
+      double K[3][3], hr, rinv, x[3];
+      qp_geometry<double, BLEND>(G, n, p0, p1, p2, q, qx, qy, qz, K, hr, rinv, x);
+      double etaq = 0.0;
+      for (int a = 0; a < 4; ++a) etaq += (a == q ? QA : QB) * ev[a];
+      w[(lin * 4 + q) * kMassSlots + t] = C0 * hr * hr * hr / etaq;
+    }
+  }
+}
+
+mfs_status mass_weights(mfs_problem* P, int lvl, double* w) {
+  mfs_mesh* M = P->mesh;
+  const LevelData& L = M->levels[lvl];
+  cudaStream_t s = M->ctx->stream;
+  dim3 grid(L.n_tiles, kMacroCells);
+  ApplyParams<double> prm = sweep_params<double>(P, lvl);
+  if (M->host.blending) k_mass_weights<true><<<grid, 128, 0, s>>>(prm, w);
+  else k_mass_weights<false><<<grid, 128, 0, s>>>(prm, w);
+  MFS_CUDA(cudaGetLastError());
+  return MFS_OK;
+}
+
+// y = M_{1/eta} p from the stored weights: with p(q) = sum_b lambda_b(q) p_b,
+// y_a = sum_q w_q lambda_a(q) p(q) (DIAG: sum_q w_q lambda_a(q)^2)
+template <typename T, bool DIAG>
+__global__ void __launch_bounds__(128) k_mass_sweep_w(const ApplyParams<T> P, const T* __restrict__ w,
+                                                      const T* __restrict__ pin, T* __restrict__ y,
+                                                      const double* __restrict__ active) {
+  if (active && !(*active > 0.0)) return;
+  __shared__ T ps[NSLOT1], ys[NSLOT1];
+  __shared__ int gid[NSLOT1];
+  const int m = blockIdx.y, tidx = blockIdx.x;
+  const size_t lin = (size_t)m * gridDim.x + tidx;
+  const Tile tile = P.tiles[tidx];
+  for (int s = threadIdx.x; s < NSLOT1; s += blockDim.x) {
+    const int id = P.ids1[lin * NSLOT1 + s];
+    gid[s] = id;
+    ps[s] = (!DIAG && id >= 0) ? pin[id] : T(0);
+    ys[s] = T(0);
+  }
+  __syncthreads();
+  const T QA = T(MFS_QA), QB = T(MFS_QB);
+  const int2 cinfo = P.classes[tile.cls];
+  const T* wt = w + lin * 4 * kMassSlots;
+  for (int t = threadIdx.x; t < cinfo.y; t += blockDim.x) {
+    const int code = P.tets[cinfo.x + t];
+    const int ci = code & 15, cj = (code >> 4) & 15, ck = (code >> 8) & 15, pmu = code >> 12;
+    const int base = ci + 5 * cj + 25 * ck;
+    int sl[4];
+    T wq[4], pv[4];
+    for (int a = 0; a < 4; ++a) {
+      sl[a] = base + slot_off(pmu, a);
+      wq[a] = wt[a * kMassSlots + t];
+      pv[a] = ps[sl[a]];
+    }
+    if (DIAG) {
+      const T sw = wq[0] + wq[1] + wq[2] + wq[3];
+      for (int a = 0; a < 4; ++a) atomicAdd(&ys[sl[a]], QB * QB * sw + (QA * QA - QB * QB) * wq[a]);
+    } else {
+      const T psum = pv[0] + pv[1] + pv[2] + pv[3];
+      T wp[4], swp = T(0);
+      for (int q = 0; q < 4; ++q) {
+        wp[q] = wq[q] * (QB * psum + (QA - QB) * pv[q]);
+        swp += wp[q];
+      }
+      for (int a = 0; a < 4; ++a) atomicAdd(&ys[sl[a]], QB * swp + (QA - QB) * wp[a]);
+    }
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < NSLOT1; s += blockDim.x)
+    if (gid[s] >= 0) atomicAdd(&y[gid[s]], ys[s]);
+}
+
+template <typename T>
+mfs_status mass_apply_w(mfs_problem* P, int lvl, const T* w, const T* pin, T* y, int diag_only, const double* active,
+                        int zero_out) {
+  mfs_mesh* M = P->mesh;
+  const LevelData& L = M->levels[lvl];
+  cudaStream_t s = M->ctx->stream;
+  if (zero_out) MFS_CUDA(cudaMemsetAsync(y, 0, sizeof(T) * (size_t)L.nb1.total, s));
+  dim3 grid(L.n_tiles, kMacroCells);
+  ApplyParams<T> prm = sweep_params<T>(P, lvl);
+  if (diag_only) k_mass_sweep_w<T, true><<<grid, 128, 0, s>>>(prm, w, pin, y, active);
+  else k_mass_sweep_w<T, false><<<grid, 128, 0, s>>>(prm, w, pin, y, active);
+  MFS_CUDA(cudaGetLastError());
+  return MFS_OK;
+}
+template mfs_status mass_apply_w<float>(mfs_problem*, int, const float*, const float*, float*, int, const double*, int);
+template mfs_status mass_apply_w<double>(mfs_problem*, int, const double*, const double*, double*, int,
+                                         const double*, int);
+
+template mfs_status mass_apply<float>(mfs_problem*, int, const float*, float*, int, const double*, int);
+template mfs_status mass_apply<double>(mfs_problem*, int, const double*, double*, int, const double*, int);
 
 // Coarse operator (A_c + n n^T on free-slip nodes) assembled column by column with the FP64
 // sweep, then inverted in place.
@@ -575,6 +856,121 @@ void CgDev<T>::beta(double* sc, double tol2, int maxit, cudaStream_t s) {
 template <typename T>
 void CgDev<T>::pupd(int64_t n, const double* sc, const T* z, T* p, cudaStream_t s) {
   k_cg_p<T><<<blocks_for(n), 256, 0, s>>>(n, sc, z, p);
+}
+// true in the last block to finish (the others' partials are then visible in L2)
+// (call after thread 0 has written the block's partials)
+__device__ __forceinline__ bool last_block_done(unsigned* counter) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  return last;
+}
+template <int K>
+__device__ __forceinline__ void final_sums(const double* part, int nb, double out[K]) {
+  for (int k = 0; k < K; ++k) {
+    double a = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) a += __ldcg(part + k * nb + i);
+    out[k] = dblock_sum(a);
+  }
+}
+template <typename T>
+__global__ void k_mcg_dots(int64_t n, const T* __restrict__ p, const T* __restrict__ q, double* __restrict__ part,
+                           unsigned* __restrict__ counter, double* __restrict__ sc) {
+  if (!(sc[CG_ACTIVE] > 0.0)) return;   // the same for every block: set by earlier launches
+  T sq_t = T(0), spq_t = T(0);
+  GRID_STRIDE(i, n) {
+    const T qi = q[i];
+    sq_t += qi;
+    spq_t += p[i] * qi;
+  }
+  const double sq = block_sum_mixed(sq_t);
+  const double spq = block_sum_mixed(spq_t);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = sq;
+    part[gridDim.x + blockIdx.x] = spq;
+  }
+  if (!last_block_done(counter)) return;
+  double f[2];
+  final_sums<2>(part, gridDim.x, f);
+  if (threadIdx.x == 0) {
+    *counter = 0u;
+    sc[CG_MEANQ] = f[0] / (double)n;
+    sc[CG_PQ] = f[1];             // p is mean-free: p.(q - mean q) = p.q
+    const bool ok = f[1] > 0.0;
+    sc[CG_ALPHA] = ok ? sc[CG_RZ] / f[1] : 0.0;
+    if (!ok) sc[CG_ACTIVE] = 0.0;
+  }
+}
+template <typename T>
+__global__ void k_mcg_update(int64_t n, const T* __restrict__ p, T* __restrict__ q, T* __restrict__ x,
+                             T* __restrict__ r, T* __restrict__ z, const T* __restrict__ dinv,
+                             double* __restrict__ part, unsigned* __restrict__ counter, double* __restrict__ sc,
+                             double tol2, double maxit) {
+  if (!(sc[CG_ACTIVE] > 0.0)) return;
+  const T a = (T)sc[CG_ALPHA], mq = (T)sc[CG_MEANQ];
+  T srr_t = T(0), srz_t = T(0), sz_t = T(0), sr_t = T(0);
+  GRID_STRIDE(i, n) {
+    x[i] += a * p[i];
+    const T ri = r[i] - a * (q[i] - mq);
+    q[i] = T(0);
+    r[i] = ri;
+    const T zi = dinv[i] * ri;
+    z[i] = zi;
+    srr_t += ri * ri;
+    srz_t += ri * zi;
+    sz_t += zi;
+    sr_t += ri;
+  }
+  const double srr = block_sum_mixed(srr_t);
+  const double srz = block_sum_mixed(srz_t);
+  const double sz = block_sum_mixed(sz_t);
+  const double sr = block_sum_mixed(sr_t);
+  if (threadIdx.x == 0) {
+    const int nb = gridDim.x;
+    part[blockIdx.x] = srr;
+    part[nb + blockIdx.x] = srz;
+    part[2 * nb + blockIdx.x] = sz;
+    part[3 * nb + blockIdx.x] = sr;
+  }
+  if (!last_block_done(counter)) return;
+  double f[4];
+  final_sums<4>(part, gridDim.x, f);
+  if (threadIdx.x == 0) {
+    *counter = 0u;
+    const double meanz = f[2] / (double)n;
+    const double rzn = f[1] - meanz * f[3];   // r . (z - mean z)
+    sc[CG_RR] = f[0];
+    sc[CG_MEANZ] = meanz;
+    sc[CG_RZN] = rzn;
+    sc[CG_BETA] = rzn / sc[CG_RZ];
+    sc[CG_RZ] = rzn;
+    sc[CG_IT] += 1.0;
+    if (!(f[0] > tol2 * sc[CG_RR0]) || sc[CG_IT] >= maxit || !(rzn > 0.0)) sc[CG_ACTIVE] = 0.0;
+  }
+}
+template <typename T>
+__global__ void k_mcg_p(int64_t n, const T* __restrict__ z, T* __restrict__ p, const double* __restrict__ sc) {
+  if (!(sc[CG_ACTIVE] > 0.0)) return;
+  const T b = (T)sc[CG_BETA], mz = (T)sc[CG_MEANZ];
+  GRID_STRIDE(i, n) p[i] = (z[i] - mz) + b * p[i];
+}
+template <typename T>
+void CgDev<T>::mass_dots(int64_t n, const T* p, const T* q, double* part, unsigned* counter, double* sc,
+                         cudaStream_t s) {
+  k_mcg_dots<T><<<blocks_for(n, 256, kRedBlocks), 256, 0, s>>>(n, p, q, part, counter, sc);
+}
+template <typename T>
+void CgDev<T>::mass_update(int64_t n, const T* p, T* q, T* x, T* r, T* z, const T* dinv, double* part,
+                           unsigned* counter, double* sc, double tol2, int maxit, cudaStream_t s) {
+  k_mcg_update<T><<<blocks_for(n, 256, kRedBlocks), 256, 0, s>>>(n, p, q, x, r, z, dinv, part, counter, sc, tol2,
+                                                                 (double)maxit);
+}
+template <typename T>
+void CgDev<T>::mass_pupd(int64_t n, const T* z, T* p, const double* sc, cudaStream_t s) {
+  k_mcg_p<T><<<blocks_for(n), 256, 0, s>>>(n, z, p, sc);
 }
 template struct CgDev<float>;
 template struct CgDev<double>;

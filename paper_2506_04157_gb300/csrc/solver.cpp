@@ -51,6 +51,8 @@ struct MG {
   int ncoarse = 0;
   std::vector<Work<float>> w32;
   std::vector<Work<double>> w64;
+  double* mw64 = nullptr;       // stored quadrature weights of M_{1/eta} on the finest level
+  float* mw32 = nullptr;
   double* mdinv64 = nullptr;
   float* mdinv32 = nullptr;
   double* red = nullptr;        // [kRedBlocks] partials + 8 scalars
@@ -61,14 +63,34 @@ struct MG {
   std::vector<void*> owned;     // device allocations to free
   // device-resident CG: scalar slots, a capture stream and cached graphs of CG chunks
   double* cgsc = nullptr;
+  double* mcg_part = nullptr;   // [4 * kRedBlocks] block partials of the mass CG
+  unsigned* mcg_counter = nullptr;
   cudaStream_t cap = nullptr;
   struct Graph {
     int prec;
     const void* x;
+    double tol;
+    int maxit;
     cudaGraphExec_t exec;
   };
   std::vector<Graph> graphs;
+  // captured V-cycles, keyed by precision, level, smoother shape and buffers; dropped
+  // whenever the Chebyshev intervals change, stale when the sweep tuning changes
+  struct VGraph {
+    int prec, l, steps, deg;
+    const void* x;
+    const void* b;
+    int tuning_gen, uses;
+    cudaGraphExec_t exec;
+  };
+  std::vector<VGraph> vgraphs;
 };
+
+static void drop_vgraphs(MG* G) {
+  for (auto& g : G->vgraphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  G->vgraphs.clear();
+}
 
 static mfs_status dalloc(MG* G, void** p, size_t bytes) {
   cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
@@ -86,6 +108,7 @@ static mfs_status dalloc_zero(MG* G, T** p, int64_t n, cudaStream_t s) {
 void mg_destroy(MG* G) {
   if (!G) return;
   for (auto& g : G->graphs) cudaGraphExecDestroy(g.exec);
+  drop_vgraphs(G);
   if (G->cap) cudaStreamDestroy(G->cap);
   for (void* p : G->owned) cudaFree(p);
   if (G->hpin) cudaFreeHost(G->hpin);
@@ -329,10 +352,14 @@ static mfs_status mg_structure(mfs_problem* Pb, int l_min) {
   G->ncoarse = 3 * M->levels[l_min].nb2.total;
   MFS_TRY(dalloc(G, (void**)&G->Ainv, sizeof(double) * (size_t)G->ncoarse * G->ncoarse));
   MFS_TRY(dalloc(G, (void**)&G->ainv_work, sizeof(double) * 2 * (size_t)G->ncoarse));
+  MFS_TRY(dalloc_zero(G, &G->mw64, mass_weight_count(M->levels[L]), s));
+  MFS_TRY(dalloc_zero(G, &G->mw32, mass_weight_count(M->levels[L]), s));
   MFS_TRY(dalloc_zero(G, &G->mdinv64, M->levels[L].nb1.total, s));
   MFS_TRY(dalloc_zero(G, &G->mdinv32, M->levels[L].nb1.total, s));
   MFS_TRY(dalloc_zero(G, &G->red, kRedBlocks + 16, s));
   MFS_TRY(dalloc_zero(G, &G->cgsc, CG_NSLOTS, s));
+  MFS_TRY(dalloc_zero(G, &G->mcg_part, 4 * kRedBlocks, s));
+  MFS_TRY(dalloc_zero(G, &G->mcg_counter, 4, s));
   MFS_CUDA(cudaStreamCreateWithFlags(&G->cap, cudaStreamNonBlocking));
   MFS_CUDA(cudaMallocHost((void**)&G->hpin, 16 * sizeof(double)));
   G->structure = true;
@@ -364,6 +391,11 @@ template <typename T>
 static mfs_status applyA(mfs_problem* Pb, int l, const T* x, T* y) {
   return launch_apply<T>(Pb, l, OP_A, 1, 0, x, nullptr, y, nullptr, nullptr);
 }
+// the same into a buffer known to hold zeros
+template <typename T>
+static mfs_status applyA_acc(mfs_problem* Pb, int l, const T* x, T* y) {
+  return launch_apply<T>(Pb, l, OP_A, 1, 0, x, nullptr, y, nullptr, nullptr, 0);
+}
 
 template <typename T>
 static T* red_scalar(mfs_problem* Pb);
@@ -382,63 +414,124 @@ static mfs_status mean_free(mfs_problem* Pb, T* p, int64_t n) {
   return MFS_OK;
 }
 
+// adds the wall time of its scope to a millisecond counter
+struct WallTimer {
+  double& acc;
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  explicit WallTimer(double& a) : acc(a) {}
+  ~WallTimer() { acc += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count(); }
+};
+
 // ------------------------------------------------------------------------- smoother / V-cycle
 // Jacobi-preconditioned Chebyshev iteration (Saad, Iterative Methods, Alg. 12.1), `steps`
-// steps of `deg` applications of A each, projections after every preconditioning.
+// steps of `deg` applications of A each.  Every application is one sweep into the level's
+// buffer t (kept zeroed between uses) and one fused update of r, d and x; the boundary
+// projections act on d and x after the update (the update is linear and x stays in the
+// projected space).  x_zero: x = 0 on entry, so the first step needs no apply.
 template <typename T>
-static mfs_status chebyshev(mfs_problem* Pb, MG* G, int l, T* x, const T* b, int steps, int deg) {
+static mfs_status chebyshev(mfs_problem* Pb, MG* G, int l, T* x, const T* b, int steps, int deg, bool x_zero) {
   cudaStream_t s = Pb->mesh->ctx->stream;
   Work<T>& W = work<T>(G, l);
   const int64_t n2 = Pb->mesh->levels[l].nb2.total, n3 = 3 * n2;
   const double lo = G->lo[l], hi = G->hi[l];
   const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma1 = theta / delta;
   for (int st = 0; st < steps; ++st) {
-    MFS_TRY(applyA<T>(Pb, l, x, W.t));
-    Blas<T>::axpbypcz(n3, T(1), b, T(-1), W.t, T(0), W.r, s);   // r = b - A x
-    Blas<T>::mul(n3, W.r, W.dinv, W.z, s);
-    Blas<T>::bproject(G->bnd[l], n2, W.z, s);
-    Blas<T>::axpby(n3, T(1.0 / theta), W.z, T(0), W.d, s);     // d = z / theta
+    int mode = 0;                                                    // r = b
+    if (st > 0 || !x_zero) {
+      MFS_TRY(applyA_acc<T>(Pb, l, x, W.t));
+      mode = 1;                                                      // r = b - A x
+    }
+    Blas<T>::cheb_update(n3, mode, b, W.t, W.r, W.dinv, W.d, x, T(1.0 / theta), T(0), s);   // d = z / theta
+    Blas<T>::bproject2(G->bnd[l], n2, W.d, x, s);
     double rho = 1.0 / sigma1;
-    for (int k = 1; k <= deg; ++k) {
-      Blas<T>::axpby(n3, T(1), W.d, T(1), x, s);               // x += d
-      if (k == deg) break;
-      MFS_TRY(applyA<T>(Pb, l, W.d, W.t));
-      Blas<T>::axpby(n3, T(-1), W.t, T(1), W.r, s);            // r -= A d
-      Blas<T>::mul(n3, W.r, W.dinv, W.z, s);
-      Blas<T>::bproject(G->bnd[l], n2, W.z, s);
+    for (int k = 2; k <= deg; ++k) {
+      MFS_TRY(applyA_acc<T>(Pb, l, W.d, W.t));
       const double rho_new = 1.0 / (2.0 * sigma1 - rho);
-      Blas<T>::axpby(n3, T(2.0 * rho_new / delta), W.z, T(rho_new * rho), W.d, s);
+      Blas<T>::cheb_update(n3, 2, b, W.t, W.r, W.dinv, W.d, x, T(2.0 * rho_new / delta), T(rho_new * rho), s);
+      Blas<T>::bproject2(G->bnd[l], n2, W.d, x, s);
       rho = rho_new;
     }
   }
   return MFS_OK;
 }
 
-// One V-cycle for A_c x = b on level l; x is overwritten (starts from zero).
+// One V-cycle for A_c x = b on level l from x = 0; x is overwritten.
 template <typename T>
-static mfs_status vcycle(mfs_problem* Pb, MG* G, int l, T* x, const T* b, int steps, int deg) {
+static mfs_status vcycle_launch(mfs_problem* Pb, MG* G, int l, T* x, const T* b, int steps, int deg) {
   mfs_mesh* M = Pb->mesh;
   cudaStream_t s = M->ctx->stream;
-  const int64_t n2 = M->levels[l].nb2.total, n3 = 3 * n2;
+  const int64_t n2 = M->levels[l].nb2.total;
   if (l == G->l_min) {
-    Blas<T>::gemv_f64((int)n3, G->Ainv, b, x, s);
+    Blas<T>::gemv_f64((int)(3 * n2), G->Ainv, b, x, s);
     Blas<T>::bproject(G->bnd[l], n2, x, s);
     return MFS_OK;
   }
   Work<T>& W = work<T>(G, l);
   Work<T>& C = work<T>(G, l - 1);
   const int64_t nc2 = M->levels[l - 1].nb2.total;
-  Blas<T>::fill(n3, T(0), x, s);
-  MFS_TRY(chebyshev<T>(Pb, G, l, x, b, steps, deg));
-  MFS_TRY(applyA<T>(Pb, l, x, W.t));
-  Blas<T>::axpbypcz(n3, T(1), b, T(-1), W.t, T(0), W.r, s);
-  Blas<T>::spmv3(G->R[l], n2, W.r, T(1), T(0), C.b, s);       // restriction P^T
+  MFS_TRY(chebyshev<T>(Pb, G, l, x, b, steps, deg, true));
+  MFS_TRY(applyA_acc<T>(Pb, l, x, W.t));
+  Blas<T>::restrict_residual(G->R[l], n2, b, W.t, C.b, s);        // P^T (b - A x)
   Blas<T>::bproject(G->bnd[l - 1], nc2, C.b, s);
-  MFS_TRY(vcycle<T>(Pb, G, l - 1, C.x, C.b, steps, deg));
-  Blas<T>::spmv3(G->P[l], nc2, C.x, T(1), T(0), W.t, s);      // prolongation
-  Blas<T>::bproject(G->bnd[l], n2, W.t, s);
-  Blas<T>::axpby(n3, T(1), W.t, T(1), x, s);
-  MFS_TRY(chebyshev<T>(Pb, G, l, x, b, steps, deg));
+  MFS_TRY(vcycle_launch<T>(Pb, G, l - 1, C.x, C.b, steps, deg));
+  Blas<T>::prolong_add(G->P[l], nc2, C.x, x, W.t, s);             // x += P x_c, t = 0
+  Blas<T>::bproject(G->bnd[l], n2, x, s);
+  MFS_TRY(chebyshev<T>(Pb, G, l, x, b, steps, deg, false));
+  return MFS_OK;
+}
+
+// A V-cycle is a fixed launch sequence: from its second use on (the first one runs the
+// kernels' lazy setup) it is replayed from a captured CUDA graph.  With per-sweep timing
+// on, it is always launched eagerly.
+template <typename T>
+static mfs_status vcycle(mfs_problem* Pb, MG* G, int l, T* x, const T* b, int steps, int deg) {
+  mfs_mesh* M = Pb->mesh;
+  mfs_ctx* C = M->ctx;
+  if (C->timing) return vcycle_launch<T>(Pb, G, l, x, b, steps, deg);
+  const int prec = sizeof(T) == 8 ? 0 : 1;
+  size_t k = 0;
+  for (; k < G->vgraphs.size(); ++k) {
+    const MG::VGraph& g = G->vgraphs[k];
+    if (g.prec == prec && g.l == l && g.steps == steps && g.deg == deg && g.x == x && g.b == b) break;
+  }
+  if (k == G->vgraphs.size()) {
+    if (G->vgraphs.size() >= 64) {   // many distinct caller buffers: start over
+      drop_vgraphs(G);
+      k = 0;
+    }
+    G->vgraphs.push_back({prec, l, steps, deg, x, b, M->tuning_gen, 0, nullptr});
+  }
+  MG::VGraph& g = G->vgraphs[k];
+  if (g.exec && g.tuning_gen != M->tuning_gen) {
+    cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+    g.uses = 0;
+  }
+  if (!g.exec) {
+    if (g.uses++ == 0) return vcycle_launch<T>(Pb, G, l, x, b, steps, deg);
+    cudaStream_t saved = C->stream;
+    C->stream = G->cap;
+    cudaError_t e = cudaStreamBeginCapture(G->cap, cudaStreamCaptureModeThreadLocal);
+    mfs_status st = MFS_OK;
+    if (e == cudaSuccess) st = vcycle_launch<T>(Pb, G, l, x, b, steps, deg);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(G->cap, &graph);
+    C->stream = saved;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    if (st != MFS_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      g.exec = nullptr;
+      return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    g.tuning_gen = M->tuning_gen;
+  }
+  MFS_CUDA(cudaGraphLaunch(g.exec, C->stream));
   return MFS_OK;
 }
 
@@ -488,12 +581,15 @@ static mfs_status mg_numeric(mfs_problem* Pb) {
   }
   MFS_TRY(coarse_inverse(Pb, G->l_min, G->bnd[G->l_min], G->Ainv, G->ainv_work));
   // inverse diagonal of M_{1/eta} on the finest level
-  MFS_TRY(mass_apply<double>(Pb, L, nullptr, G->mdinv64, 1));
+  MFS_TRY(mass_weights(Pb, L, G->mw64));
+  Blas<float>::convert_from_f64(mass_weight_count(M->levels[L]), G->mw64, G->mw32, s);
+  MFS_TRY(mass_apply_w<double>(Pb, L, G->mw64, nullptr, G->mdinv64, 1));
   Blas<float>::convert_from_f64(M->levels[L].nb1.total, G->mdinv64, G->mdinv32, s);
   Blas<double>::recip(M->levels[L].nb1.total, G->mdinv64, s);
   Blas<float>::recip(M->levels[L].nb1.total, G->mdinv32, s);
   MFS_CUDA(cudaStreamSynchronize(s));
   MFS_CUDA(cudaGetLastError());
+  drop_vgraphs(G);   // new Chebyshev intervals
   G->numeric = true;
   return MFS_OK;
 }
@@ -544,6 +640,7 @@ mfs_status mfs_set_cheb_bounds(mfs_problem* Pb, int lvl, double lo, double hi) {
   Pb->mg->lo[lvl] = lo;
   Pb->mg->hi[lvl] = hi;
   Pb->mg->have_bounds[lvl] = 1;
+  drop_vgraphs(Pb->mg);
   return MFS_OK;
 }
 
@@ -579,6 +676,11 @@ mfs_status mfs_apply_mass(mfs_problem* Pb, int lvl, mfs_prec prec, const void* p
   if (lvl < 0 || lvl > Pb->mesh->l_max || !p || !y) {
     set_error("invalid level or null vector");
     return MFS_EINVAL;
+  }
+  MG* G = Pb->mg;
+  if (G && G->numeric && lvl == G->l_max) {   // stored weights on the finest level
+    if (prec == MFS_F64) return mass_apply_w<double>(Pb, lvl, G->mw64, (const double*)p, (double*)y, 0);
+    return mass_apply_w<float>(Pb, lvl, G->mw32, (const float*)p, (float*)y, 0);
   }
   if (prec == MFS_F64) return mass_apply<double>(Pb, lvl, (const double*)p, (double*)y, 0);
   return mass_apply<float>(Pb, lvl, (const float*)p, (float*)y, 0);
@@ -692,6 +794,12 @@ template <>
 const float* mass_dinv<float>(MG* G) { return G->mdinv32; }
 template <>
 const double* mass_dinv<double>(MG* G) { return G->mdinv64; }
+template <typename T>
+static const T* mass_w(MG* G);
+template <>
+const float* mass_w<float>(MG* G) { return G->mw32; }
+template <>
+const double* mass_w<double>(MG* G) { return G->mw64; }
 
 template <typename T>
 struct Stokes {
@@ -789,6 +897,7 @@ struct Stokes {
 
   // ---- A-block: CG on A preconditioned by a V-cycle (m_A, deg_A) to tol_A
   mfs_status Ahat_inv(const T* r, T* x) {
+    WallTimer tm(st.time_Ahat_ms);
     int it = 0;
     auto op = [&](const T* v, T* y) { return A(v, y); };
     auto pre = [&](const T* v, T* y) {
@@ -812,23 +921,16 @@ struct Stokes {
   static constexpr int kChunk = 8;
   void mass_iteration(cudaStream_t cs, T* x) {
     const double tol2 = tolM * tolM;
-    mass_apply<T>(Pb, L, K.cgm_p, K.cgm_q, 0);
-    mean_free<T>(Pb, K.cgm_q, np);
-    Blas<T>::dot_async(np, K.cgm_p, K.cgm_q, G->red, G->cgsc + CG_PQ, cs);
-    CgDev<T>::alpha(G->cgsc, cs);
-    CgDev<T>::xr(np, G->cgsc, K.cgm_p, K.cgm_q, x, K.cgm_r, cs);
-    mean_free<T>(Pb, K.cgm_r, np);
-    Blas<T>::dot_async(np, K.cgm_r, K.cgm_r, G->red, G->cgsc + CG_RR, cs);
-    Blas<T>::mul(np, K.cgm_r, mass_dinv<T>(G), K.cgm_z, cs);
-    mean_free<T>(Pb, K.cgm_z, np);
-    Blas<T>::dot_async(np, K.cgm_r, K.cgm_z, G->red, G->cgsc + CG_RZN, cs);
-    CgDev<T>::beta(G->cgsc, tol2, o.max_cg, cs);
-    CgDev<T>::pupd(np, G->cgsc, K.cgm_z, K.cgm_p, cs);
+    mass_apply_w<T>(Pb, L, mass_w<T>(G), K.cgm_p, K.cgm_q, 0, G->cgsc + CG_ACTIVE, 0);   // q = M p (q held 0)
+    CgDev<T>::mass_dots(np, K.cgm_p, K.cgm_q, G->mcg_part, G->mcg_counter, G->cgsc, cs);
+    CgDev<T>::mass_update(np, K.cgm_p, K.cgm_q, x, K.cgm_r, K.cgm_z, mass_dinv<T>(G), G->mcg_part, G->mcg_counter,
+                          G->cgsc, tol2, o.max_cg, cs);
+    CgDev<T>::mass_pupd(np, K.cgm_z, K.cgm_p, G->cgsc, cs);
   }
   mfs_status mass_graph(T* x, cudaGraphExec_t* out) {
     const int prec = sizeof(T) == 8 ? 0 : 1;
     for (auto& g : G->graphs)
-      if (g.prec == prec && g.x == x) {
+      if (g.prec == prec && g.x == x && g.tol == tolM && g.maxit == o.max_cg) {
         *out = g.exec;
         return MFS_OK;
       }
@@ -848,16 +950,18 @@ struct Stokes {
     e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-    G->graphs.push_back({prec, x, exec});
+    G->graphs.push_back({prec, x, tolM, o.max_cg, exec});
     *out = exec;
     return MFS_OK;
   }
   mfs_status M_inv(const T* r, T* x) {
+    WallTimer tm(st.time_Minv_ms);
     cudaGraphExec_t exec;
     MFS_TRY(mass_graph(x, &exec));
     Blas<T>::axpby(np, T(1), r, T(0), K.cgm_r, s);
     MFS_TRY(mean_free<T>(Pb, K.cgm_r, np));
     Blas<T>::fill(np, T(0), x, s);
+    Blas<T>::fill(np, T(0), K.cgm_q, s);
     Blas<T>::mul(np, K.cgm_r, mass_dinv<T>(G), K.cgm_z, s);
     MFS_TRY(mean_free<T>(Pb, K.cgm_z, np));
     Blas<T>::axpby(np, T(1), K.cgm_z, T(0), K.cgm_p, s);
@@ -890,6 +994,7 @@ struct Stokes {
   }
   // V-cycle BFBT: X^-1 (B A_C^-1 A A_C^-1 B^T) X^-1 r
   mfs_status S_inv(const T* r, T* z) {
+    WallTimer tm(st.time_Sinv_ms);
     int it = 0;
     auto op = [&](const T* v, T* y) { return X(v, y); };
     auto pre = [&](const T* v, T* y) { return M_inv(v, y); };

@@ -51,10 +51,19 @@ struct Blas {
   static void gemv_f64(int n, const double* A, const T* b, T* x, cudaStream_t s);
   static void convert_from_f64(int64_t n, const double* x, T* y, cudaStream_t s);
   static void convert_to_f64(int64_t n, const T* x, double* y, cudaStream_t s);
+  // Chebyshev update, one pass: r = b (mode 0), b - t (mode 1) or r - t (mode 2);
+  // d = cz dinv r + cd d; x = (mode 0 ? 0 : x) + d; t = 0
+  static void cheb_update(int64_t n, int mode, const T* b, T* t, T* r, const T* dinv, T* d, T* x, T cz, T cd,
+                          cudaStream_t s);
+  static void bproject2(const BoundaryList& B, int64_t n_p2, T* v, T* w, cudaStream_t s);   // both vectors
+  // y = R (b - t) (restriction of a residual), R in CSR over the fine columns
+  static void restrict_residual(const Csr& R, int64_t ncols, const T* b, const T* t, T* y, cudaStream_t s);
+  // x += P xc (prolongation of a coarse correction); t = 0 on the fine rows
+  static void prolong_add(const Csr& P, int64_t ncols, const T* xc, T* x, T* t, cudaStream_t s);
 };
 
 // slots of the device-resident CG scalars
-enum { CG_RZ = 0, CG_RZN, CG_PQ, CG_RR, CG_RR0, CG_ALPHA, CG_BETA, CG_IT, CG_ACTIVE, CG_NSLOTS };
+enum { CG_RZ = 0, CG_RZN, CG_PQ, CG_RR, CG_RR0, CG_ALPHA, CG_BETA, CG_IT, CG_ACTIVE, CG_MEANQ, CG_MEANZ, CG_NSLOTS };
 
 template <typename T>
 struct CgDev {
@@ -63,6 +72,16 @@ struct CgDev {
   static void xr(int64_t n, const double* sc, const T* p, const T* q, T* x, T* r, cudaStream_t s);
   static void beta(double* sc, double tol2, int maxit, cudaStream_t s);   // beta, rz, it, active
   static void pupd(int64_t n, const double* sc, const T* z, T* p, cudaStream_t s);
+  // One iteration of CG on P_p M P_p (P_p: mean removal; Jacobi preconditioner, p kept
+  // mean-free) after the sweep q = M p, in three launches whose reductions finish in the
+  // last block to arrive: (1) alpha = rz / p.q and mean(q); (2) x += alpha p,
+  // r -= alpha (q - mean q), z = dinv r, q = 0, then beta, convergence and mean(z);
+  // (3) p = (z - mean z) + beta p.  part: 4 * kRedBlocks doubles, counter: one zeroed uint.
+  static void mass_dots(int64_t n, const T* p, const T* q, double* part, unsigned* counter, double* sc,
+                        cudaStream_t s);
+  static void mass_update(int64_t n, const T* p, T* q, T* x, T* r, T* z, const T* dinv, double* part,
+                          unsigned* counter, double* sc, double tol2, int maxit, cudaStream_t s);
+  static void mass_pupd(int64_t n, const T* z, T* p, const double* sc, cudaStream_t s);
 };
 
 template <typename T>
@@ -80,8 +99,20 @@ inline const MacroGeom<float>* lvl_geom<float>(mfs_mesh* M) { return M->d_geom32
 
 template <typename T>
 mfs_status diag_A(mfs_problem* P, int lvl, const BoundaryList& B, T* diag);
+// Quadrature weights of M_{1/eta} on level lvl: w[((tile * 4) + q) * kMassSlots + t] =
+// w_q |det J_q| / eta(x_q) for the t-th micro-tet of the tile (the tile's class list order).
+constexpr int kMassSlots = 6 * TT * TT * TT;
+inline int64_t mass_weight_count(const LevelData& L) { return (int64_t)kMacroCells * L.n_tiles * 4 * kMassSlots; }
+mfs_status mass_weights(mfs_problem* P, int lvl, double* w);
+// y = M_{1/eta} p (or its diagonal) from stored weights; `active` and zero_out as below
 template <typename T>
-mfs_status mass_apply(mfs_problem* P, int lvl, const T* pin, T* y, int diag_only);
+mfs_status mass_apply_w(mfs_problem* P, int lvl, const T* w, const T* pin, T* y, int diag_only,
+                        const double* active = nullptr, int zero_out = 1);
+// y = M_{1/eta} p (or its diagonal); with `active` the sweep is a no-op unless *active > 0,
+// zero_out = 0 adds into a zeroed y
+template <typename T>
+mfs_status mass_apply(mfs_problem* P, int lvl, const T* pin, T* y, int diag_only, const double* active = nullptr,
+                      int zero_out = 1);
 mfs_status coarse_inverse(mfs_problem* P, int lvl, const BoundaryList& B, double* A, double* work);
 // g_k = -eta_k sum_tets sum_q 2 w|det J| psi_k(q) eps(u)(q) : eps(lam)(q)   (FP64)
 mfs_status grad_log_eta(mfs_problem* P, int lvl, const double* u, const double* lam, double* g);

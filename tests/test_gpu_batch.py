@@ -68,8 +68,11 @@ def test_batch_solve_matches_individual(ensemble):
     for P, f, g, u, p, st in zip(small, fs, gs, us, ps, stats):
         assert st["rel_residual"] <= 1e-8
         u1, p1 = torch.zeros_like(u), torch.zeros_like(p)
-        P.solve(f, g, u1, p1, mixed=0)
-        assert (torch.linalg.norm(u - u1) / torch.linalg.norm(u1)).item() < 1e-6
+        st1 = P.solve(f, g, u1, p1, mixed=0)
+        assert st1["rel_residual"] <= 1e-8
+        # Both iterates stop at a relative residual of 1e-8; atomic accumulation order makes
+        # their Krylov paths differ by rounding, so they agree only to about kappa(K) * 1e-8.
+        assert (torch.linalg.norm(u - u1) / torch.linalg.norm(u1)).item() < 1e-5
 
 
 def test_autotune_keeps_results(ensemble, tmp_path):

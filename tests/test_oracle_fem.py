@@ -237,3 +237,15 @@ def test_buoyancy_rhs_against_radial_integral(g):
         f = buoyancy_rhs(L, np.ones(L.n_p2), np.array([g, g]))
         errs.append(abs(f @ L.p2_x.T.reshape(-1) - exact) / exact)
     assert errs[1] < 5e-4 and errs[1] < errs[0] / 8
+
+
+def test_rho_profile_piecewise_against_adaptive_quadrature():
+    """A table with kinks: adaptive quadrature split at the breakpoints is independent."""
+    from scipy.integrate import quad
+    from oracle.fem import rho_profile, interp_table
+    tab, r0, R = np.array([-1.0, -0.2, 0.5, -0.7]), 0.5, 1.0
+    nodes = np.linspace(r0, R, tab.size)
+    for r in (0.5, 0.61, 0.74, 0.9, 1.0):
+        val, _ = quad(lambda s: float(interp_table(tab, np.array([s]), r0, R)[0]), r, R,
+                      points=[x for x in nodes if r < x < R], epsabs=1e-14, epsrel=1e-14)
+        assert abs(rho_profile(tab, np.array([r]), r0, R)[0] - np.exp(-val)) <= 1e-13
