@@ -11,7 +11,7 @@ Paper passages followed (arxiv 2506.04157):
   * Sec. 5.2.2: eta is a P1 function on every level, evaluated at quadrature points.
   * Sec. 5.2.3, Eq. (schurMass): the inverse-viscosity weighted P1 mass matrix.
 
-Readings (listed in DESIGN.md):
+Readings:
   * A_ij = int 2 eta eps(phi_j):eps(phi_i): the printed second term drops eta; the
     stress tau = 2 eta eps of Sec. 2 fixes it.
   * Quadrature: the symmetric 4-point degree-2 rule (weights 1/24).

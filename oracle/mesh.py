@@ -13,7 +13,7 @@ Paper passages followed (arxiv 2506.04157):
   * Sec. 4.2 / Eq. (Lagrange): P2 nodes are the vertex and edge-midpoint Lagrange
     points, split into inner, surface and CMB sets.
 
-Readings where the paper is silent (all listed in the design doc):
+Readings where the paper is silent:
   * Prism split: each quad face of a prism is cut along the diagonal through its
     lowest-numbered vertex; with bottom vertices a<b<c and tops a'<b'<c' this gives
     the tets (a,b,c,c'), (a,b,c',b'), (a,b',c',a').

@@ -16,7 +16,7 @@ Paper passages followed (arxiv 2506.04157):
   * Sec. 5.2.4: FGMRES outer solver preconditioned by the block preconditioner.
   * Table parametertable: the default parameters.
 
-Readings (listed in DESIGN.md):
+Readings:
   * Chebyshev iteration in the form of Saad, Iterative Methods, Alg. 12.1 (with the
     Jacobi preconditioner), "degree k" = k applications of A per smoothing step including
     the initial residual; interval [b/20, b] with b = 1.2 x the largest eigenvalue of
