@@ -215,7 +215,8 @@ typedef struct {
   int restart;        /* FGMRES restart length (30) */
   int max_iters;      /* total FGMRES iterations (300) */
   int max_outer;      /* refinement steps (restarts on the true FP64 residual) (20) */
-  double inner_rtol;  /* relative tolerance of each inner FP32 FGMRES (1e-4) */
+  double inner_rtol;  /* relative tolerance of each inner FP32 FGMRES (1e-4); the last step stops
+                         once the target rtol is within a factor 2 */
   double sigma;       /* scaling of A^-1 in the Uzawa step (1) */
   double omega;       /* scaling of S^-1 in the Uzawa step (0.3) */
   double tol_A;       /* CG on A, relative (1e-2) */

@@ -37,10 +37,13 @@ namespace mfs {
 #ifndef MFS_SLOT_TABLE
 #define MFS_SLOT_TABLE 0      // 1: slot offsets from a constant table, 0: computed
 #endif
-#ifndef MFS_SWEEP_MINBLOCKS
-#define MFS_SWEEP_MINBLOCKS 4   // resident CTAs per SM the register allocation targets
+#ifndef MFS_SWEEP_THREADS
+#define MFS_SWEEP_THREADS 192   // threads per sweep CTA (micro-tets per round)
 #endif
-constexpr int kSweepThreads = 192;
+#ifndef MFS_SWEEP_MINBLOCKS
+#define MFS_SWEEP_MINBLOCKS (768 / MFS_SWEEP_THREADS)   // resident CTAs per SM the registers target
+#endif
+constexpr int kSweepThreads = MFS_SWEEP_THREADS;
 constexpr int kSub = 125;   // 5x5x5 parity sub-block
 
 template <typename T>
@@ -632,13 +635,17 @@ __global__ void __launch_bounds__(kSweepThreads, MFS_SWEEP_MINBLOCKS - 1)
   sweep_tile<T, OP, BLEND>(P, blockIdx.y, blockIdx.x, gridDim.x);
 }
 
-// an ensemble in one launch: block b works on tile map[b] = (problem, macro * 65536 + tile)
+// an ensemble in one persistent launch: CTA c works on the tiles map[c], map[c + grid], ...
+// with map[b] = (problem, macro * 65536 + tile)
 template <typename T, int OP, bool BLEND>
 __global__ void __launch_bounds__(kSweepThreads, MFS_SWEEP_MINBLOCKS)
     stokes_tile_batch_kernel(const ApplyParams<T>* __restrict__ params, const int2* __restrict__ map,
-                             const int* __restrict__ n_tiles) {
-  const int2 w = map[blockIdx.x];
-  sweep_tile<T, OP, BLEND>(params[w.x], w.y >> 16, w.y & 0xffff, n_tiles[w.x]);
+                             const int* __restrict__ n_tiles, int n_items) {
+  for (int b = blockIdx.x; b < n_items; b += gridDim.x) {
+    const int2 w = map[b];
+    sweep_tile<T, OP, BLEND>(params[w.x], w.y >> 16, w.y & 0xffff, n_tiles[w.x]);
+    __syncthreads();   // the next tile's staging reuses the shared memory
+  }
 }
 
 }  // namespace mfs

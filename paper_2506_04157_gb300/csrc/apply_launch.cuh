@@ -99,8 +99,26 @@ static mfs_status run_batch(const ApplyParams<T>* dparams, const int2* map, cons
   static cudaError_t e0 = cudaFuncSetAttribute(stokes_tile_batch_kernel<T, OP, false>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   MFS_CUDA(blending ? e1 : e0);
-  if (blending) stokes_tile_batch_kernel<T, OP, true><<<nblocks, kSweepThreads, smem, s>>>(dparams, map, ntiles);
-  else stokes_tile_batch_kernel<T, OP, false><<<nblocks, kSweepThreads, smem, s>>>(dparams, map, ntiles);
+  // persistent grid: as many CTAs as fit on the device at once
+  static int grid_cap[2] = {0, 0};
+  int& cap = grid_cap[blending ? 1 : 0];
+  if (cap == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    MFS_CUDA(cudaGetDevice(&dev));
+    MFS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (blending)
+      MFS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stokes_tile_batch_kernel<T, OP, true>,
+                                                               kSweepThreads, smem));
+    else
+      MFS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stokes_tile_batch_kernel<T, OP, false>,
+                                                               kSweepThreads, smem));
+    cap = sms * (per_sm > 0 ? per_sm : 1);
+  }
+  const int grid = nblocks < cap ? nblocks : cap;
+  if (blending)
+    stokes_tile_batch_kernel<T, OP, true><<<grid, kSweepThreads, smem, s>>>(dparams, map, ntiles, nblocks);
+  else
+    stokes_tile_batch_kernel<T, OP, false><<<grid, kSweepThreads, smem, s>>>(dparams, map, ntiles, nblocks);
   MFS_CUDA(cudaGetLastError());
   return MFS_OK;
 }

@@ -23,6 +23,13 @@ struct mfs_batch {
   int64_t* d_np1 = nullptr;
   double* d_part = nullptr;     // [n][kBatchRed] partial sums
   double* d_sums = nullptr;     // [2][n] sums (as T)
+  // The device work of the last argument set (operator, precision, 4n vector pointers, the
+  // members' coefficient versions) is
+  // replayed from a captured CUDA graph from its second consecutive use on; the device
+  // pointer and parameter arrays always hold that argument set's values.
+  std::vector<const void*> key;
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t cap = nullptr;
 };
 
 namespace mfs {
@@ -80,19 +87,10 @@ __global__ void k_batch_sub_mean(T* const* __restrict__ ptrs, const int64_t* __r
     x[i] -= mean;
 }
 
+// pressure sums, zeroing, the one-launch sweep, output mean removal (device arrays set)
 template <typename T>
-static mfs_status batch_apply_typed(mfs_batch* B, int transpose, int with_C, const void* const* u, const void* const* p,
-                                    void* const* yu, void* const* yp) {
+static mfs_status batch_device_work(mfs_batch* B, int op, cudaStream_t s) {
   const int n = (int)B->probs.size();
-  cudaStream_t s = B->ctx->stream;
-  void** hp = B->h_ptrs;
-  for (int b = 0; b < n; ++b) {
-    hp[b] = const_cast<void*>(u[b]);
-    hp[n + b] = const_cast<void*>(p[b]);
-    hp[2 * n + b] = yu[b];
-    hp[3 * n + b] = yp[b];
-  }
-  MFS_CUDA(cudaMemcpyAsync(B->d_ptrs, hp, sizeof(void*) * 4 * n, cudaMemcpyHostToDevice, s));
   T* const* dp_p = (T* const*)(B->d_ptrs + n);
   T* const* dp_yu = (T* const*)(B->d_ptrs + 2 * n);
   T* const* dp_yp = (T* const*)(B->d_ptrs + 3 * n);
@@ -103,15 +101,6 @@ static mfs_status batch_apply_typed(mfs_batch* B, int transpose, int with_C, con
   // zero the accumulated outputs
   k_batch_zero<T><<<dim3(512, n), 256, 0, s>>>(dp_yu, B->d_np2, 3);
   k_batch_zero<T><<<dim3(64, n), 256, 0, s>>>(dp_yp, B->d_np1, 1);
-  // per-instance sweep parameters
-  ApplyParams<T>* hpar = (ApplyParams<T>*)B->h_params;
-  for (int b = 0; b < n; ++b) {
-    mfs_problem* P = B->probs[b];
-    hpar[b] = fill_params<T>(P, P->mesh->l_max, 1, (const T*)u[b], (const T*)p[b], (T*)yu[b], (T*)yp[b], sums + b);
-  }
-  MFS_CUDA(cudaMemcpyAsync(B->d_params, hpar, sizeof(ApplyParams<T>) * n, cudaMemcpyHostToDevice, s));
-  const int op = transpose ? (with_C ? OP_A | OP_BT | OP_CT | OP_B : OP_A | OP_BT | OP_B)
-                           : (with_C ? OP_A | OP_BT | OP_B | OP_BC : OP_A | OP_BT | OP_B);
   auto ev = timing_events(B->ctx);
   if (ev.first) cudaEventRecord(ev.first, s);
   MFS_TRY(launch_batch<T>((const ApplyParams<T>*)B->d_params, B->d_map, B->d_ntiles, B->nblocks, op, B->blending, s));
@@ -124,12 +113,77 @@ static mfs_status batch_apply_typed(mfs_batch* B, int transpose, int with_C, con
   return MFS_OK;
 }
 
+template <typename T>
+static mfs_status batch_apply_typed(mfs_batch* B, int transpose, int with_C, const void* const* u, const void* const* p,
+                                    void* const* yu, void* const* yp) {
+  const int n = (int)B->probs.size();
+  cudaStream_t s = B->ctx->stream;
+  const int op = transpose ? (with_C ? OP_A | OP_BT | OP_CT | OP_B : OP_A | OP_BT | OP_B)
+                           : (with_C ? OP_A | OP_BT | OP_B | OP_BC : OP_A | OP_BT | OP_B);
+  std::vector<const void*> key(5 * n + 1);
+  key[0] = reinterpret_cast<const void*>((uintptr_t)(op * 2 + (sizeof(T) == 8 ? 1 : 0)));
+  for (int b = 0; b < n; ++b) {
+    key[1 + b] = u[b];
+    key[1 + n + b] = p[b];
+    key[1 + 2 * n + b] = yu[b];
+    key[1 + 3 * n + b] = yp[b];
+    key[1 + 4 * n + b] = reinterpret_cast<const void*>((uintptr_t)B->probs[b]->version);   // coefficients
+  }
+  if (key == B->key && !B->ctx->timing) {
+    if (!B->graph) {   // second consecutive use of this argument set: capture
+      cudaError_t e = cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal);
+      mfs_status st = MFS_OK;
+      if (e == cudaSuccess) st = batch_device_work<T>(B, op, B->cap);
+      cudaGraph_t g = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(B->cap, &g);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+      if (st != MFS_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+      }
+      if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&B->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        B->graph = nullptr;
+        return cuda_fail(e, "cudaGraphInstantiate");
+      }
+    }
+    MFS_CUDA(cudaGraphLaunch(B->graph, s));
+    return MFS_OK;
+  }
+  if (B->graph) {
+    cudaGraphExecDestroy(B->graph);
+    B->graph = nullptr;
+  }
+  B->key.swap(key);
+  // new argument set: device pointer and parameter arrays, then the work eagerly
+  void** hp = B->h_ptrs;
+  for (int b = 0; b < n; ++b) {
+    hp[b] = const_cast<void*>(u[b]);
+    hp[n + b] = const_cast<void*>(p[b]);
+    hp[2 * n + b] = yu[b];
+    hp[3 * n + b] = yp[b];
+  }
+  MFS_CUDA(cudaMemcpyAsync(B->d_ptrs, hp, sizeof(void*) * 4 * n, cudaMemcpyHostToDevice, s));
+  T* sums = (T*)B->d_sums;
+  ApplyParams<T>* hpar = (ApplyParams<T>*)B->h_params;
+  for (int b = 0; b < n; ++b) {
+    mfs_problem* P = B->probs[b];
+    hpar[b] = fill_params<T>(P, P->mesh->l_max, 1, (const T*)u[b], (const T*)p[b], (T*)yu[b], (T*)yp[b], sums + b);
+  }
+  MFS_CUDA(cudaMemcpyAsync(B->d_params, hpar, sizeof(ApplyParams<T>) * n, cudaMemcpyHostToDevice, s));
+  return batch_device_work<T>(B, op, s);
+}
+
 }  // namespace mfs
 
 using namespace mfs;
 
 mfs_status mfs_batch_destroy(mfs_batch* B) {
   if (!B) return MFS_OK;
+  if (B->graph) cudaGraphExecDestroy(B->graph);
+  if (B->cap) cudaStreamDestroy(B->cap);
   cudaFree(B->d_map);
   cudaFree(B->d_ntiles);
   cudaFree(B->d_params);
@@ -194,6 +248,7 @@ mfs_status mfs_batch_create(mfs_ctx* ctx, int n, mfs_problem* const* probs, mfs_
   chk(cudaMalloc((void**)&B->d_sums, sizeof(double) * 2 * n));
   chk(cudaMallocHost(&B->h_params, sizeof(ApplyParams<double>) * n));
   chk(cudaMallocHost((void**)&B->h_ptrs, sizeof(void*) * 4 * n));
+  chk(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
   if (e == cudaSuccess) {
     chk(cudaMemcpyAsync(B->d_map, map.data(), sizeof(int2) * map.size(), cudaMemcpyHostToDevice, s));
     chk(cudaMemcpyAsync(B->d_ntiles, nt.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));

@@ -391,6 +391,7 @@ mfs_status mfs_problem_destroy(mfs_problem* P) {
 }
 
 mfs_status mfs_set_viscosity(mfs_problem* P, const double* eta, int is_log) {
+  if (P) P->version++;
   MFS_TRY(check_problem(P, 0, false));
   if (!eta) {
     set_error("null viscosity pointer");
@@ -413,6 +414,7 @@ mfs_status mfs_set_viscosity(mfs_problem* P, const double* eta, int is_log) {
 
 
 mfs_status mfs_set_density(mfs_problem* P, int n, const double* tab) {
+  if (P) P->version++;
   MFS_TRY(check_problem(P, 0, false));
   if (n < 1 || !tab) {
     set_error("density table needs n >= 1 entries");

@@ -121,6 +121,7 @@ struct mfs_problem {
   double* d_red64 = nullptr;    // [kRedSlots]
   float* d_red32 = nullptr;
   mfs::MG* mg = nullptr;        // multigrid hierarchy and solver workspaces
+  int version = 0;              // bumped by every coefficient change (captured graphs go stale)
 };
 
 namespace mfs {

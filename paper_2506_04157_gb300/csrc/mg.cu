@@ -176,29 +176,60 @@ __global__ void k_spmv3(int nrows, const int* __restrict__ rp, const int* __rest
   }
 }
 
+// projection of one node's velocity: zero at Dirichlet nodes, normal component removed at
+// free-slip nodes (k = position in the boundary list)
+template <typename T>
+__device__ __forceinline__ void project_node(int k, const int8_t* __restrict__ kind, const T* __restrict__ nrm, T& v0,
+                                             T& v1, T& v2) {
+  if (kind[k] == 1) {
+    v0 = v1 = v2 = T(0);
+  } else {
+    const T nx = nrm[3 * k], ny = nrm[3 * k + 1], nz = nrm[3 * k + 2];
+    const T un = v0 * nx + v1 * ny + v2 * nz;
+    v0 -= un * nx;
+    v1 -= un * ny;
+    v2 -= un * nz;
+  }
+}
+
+// one warp per coarse row: lanes split the row's entries, a shuffle tree adds them
 template <typename T>
 __global__ void k_restrict_residual(int nrows, const int* __restrict__ rp, const int* __restrict__ ci,
                                     const T* __restrict__ w, int64_t ncols, const T* __restrict__ b,
-                                    const T* __restrict__ t, T* __restrict__ y) {
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += gridDim.x * blockDim.x) {
+                                    const T* __restrict__ t, T* __restrict__ y, const int* __restrict__ cmap,
+                                    const int8_t* __restrict__ kind, const T* __restrict__ nrm) {
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrows; r += nw) {
     T s0 = T(0), s1 = T(0), s2 = T(0);
-    for (int k = rp[r]; k < rp[r + 1]; ++k) {
+    for (int k = rp[r] + lane; k < rp[r + 1]; k += 32) {
       const int64_t j = ci[k];
       const T wk = w[k];
       s0 += wk * (b[j] - t[j]);
       s1 += wk * (b[ncols + j] - t[ncols + j]);
       s2 += wk * (b[2 * ncols + j] - t[2 * ncols + j]);
     }
-    const int64_t nr = nrows;
-    y[r] = s0;
-    y[nr + r] = s1;
-    y[2 * nr + r] = s2;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if (lane == 0) {
+      const int kb = cmap[r];
+      if (kb >= 0) project_node(kb, kind, nrm, s0, s1, s2);
+      const int64_t nr = nrows;
+      y[r] = s0;
+      y[nr + r] = s1;
+      y[2 * nr + r] = s2;
+    }
   }
 }
 template <typename T>
 __global__ void k_prolong_add(int nrows, const int* __restrict__ rp, const int* __restrict__ ci,
                               const T* __restrict__ w, int64_t ncols, const T* __restrict__ xc, T* __restrict__ x,
-                              T* __restrict__ t) {
+                              T* __restrict__ t, const int* __restrict__ fmap, const int8_t* __restrict__ kind,
+                              const T* __restrict__ nrm) {
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += gridDim.x * blockDim.x) {
     T s0 = T(0), s1 = T(0), s2 = T(0);
     for (int k = rp[r]; k < rp[r + 1]; ++k) {
@@ -209,88 +240,55 @@ __global__ void k_prolong_add(int nrows, const int* __restrict__ rp, const int* 
       s2 += wk * xc[2 * ncols + j];
     }
     const int64_t nr = nrows;
-    x[r] += s0;
-    x[nr + r] += s1;
-    x[2 * nr + r] += s2;
+    T x0 = x[r] + s0, x1 = x[nr + r] + s1, x2 = x[2 * nr + r] + s2;
+    const int kb = fmap[r];
+    if (kb >= 0) project_node(kb, kind, nrm, x0, x1, x2);
+    x[r] = x0;
+    x[nr + r] = x1;
+    x[2 * nr + r] = x2;
     t[r] = t[nr + r] = t[2 * nr + r] = T(0);
   }
 }
-// Jacobi-preconditioned Chebyshev update of one smoothing application (see Blas::cheb_update).
-// Streams 16-byte vectors (V elements per access) from offset `first`; elements before it
-// and the ragged tail go element by element.
+// Jacobi-preconditioned Chebyshev update of one smoothing application (see Blas::cheb_update),
+// one thread per node with its three components
 template <typename T>
-struct Vec16;
-template <>
-struct Vec16<float> {
-  using type = float4;
-};
-template <>
-struct Vec16<double> {
-  using type = double2;
-};
-template <typename T, int V>
-__device__ __forceinline__ void cheb_elems(int mode, const T* b, T* t, T* r, const T* dinv, T* d, T* x, T cz, T cd,
-                                           int64_t i) {
-  using VT = typename Vec16<T>::type;
-  T bv[V], tv[V], rv[V], iv[V], dv[V], xv[V];
-  auto ld = [&](const T* p, T* o) {
-    if (V == 1) o[0] = p[i];
-    else *reinterpret_cast<VT*>(o) = *reinterpret_cast<const VT*>(p + i);
-  };
-  auto st = [&](T* p, const T* o) {
-    if (V == 1) p[i] = o[0];
-    else *reinterpret_cast<VT*>(p + i) = *reinterpret_cast<const VT*>(o);
-  };
-  ld(dinv, iv);
-  if (mode != 2) ld(b, bv);
-  if (mode != 0) ld(t, tv);
-  if (mode == 2) ld(r, rv);
-  if (cd != T(0)) ld(d, dv);
-  if (mode != 0) ld(x, xv);
+__global__ void k_cheb_update(int64_t n2, int mode, const T* __restrict__ b, T* __restrict__ t, T* __restrict__ r,
+                              const T* __restrict__ dinv, T* __restrict__ d, T* __restrict__ x, T cz, T cd,
+                              const int* __restrict__ nmap, const int8_t* __restrict__ kind,
+                              const T* __restrict__ nrm) {
+  GRID_STRIDE(i, n2) {
+    T bv[3], tv[3], rv[3], iv[3], dv[3], xv[3];
 #pragma unroll
-  for (int k = 0; k < V; ++k) {
-    const T rk = mode == 0 ? bv[k] : (mode == 1 ? bv[k] : rv[k]) - tv[k];
-    rv[k] = rk;
-    T dk = cz * iv[k] * rk;
-    if (cd != T(0)) dk += cd * dv[k];
-    dv[k] = dk;
-    xv[k] = mode == 0 ? dk : xv[k] + dk;
-    tv[k] = T(0);
-  }
-  st(t, tv);
-  st(r, rv);
-  st(d, dv);
-  st(x, xv);
-}
-template <typename T>
-__global__ void k_cheb_update(int64_t n, int64_t first, int mode, const T* __restrict__ b, T* __restrict__ t,
-                              T* __restrict__ r, const T* __restrict__ dinv, T* __restrict__ d, T* __restrict__ x, T cz,
-                              T cd) {
-  constexpr int V = 16 / sizeof(T);
-  const int64_t nv = (n - first) / V;
-  GRID_STRIDE(k, nv) cheb_elems<T, V>(mode, b, t, r, dinv, d, x, cz, cd, first + k * V);
-  const int64_t rest = first + nv * V;
-  GRID_STRIDE(i, first) cheb_elems<T, 1>(mode, b, t, r, dinv, d, x, cz, cd, i);
-  GRID_STRIDE(i, n - rest) cheb_elems<T, 1>(mode, b, t, r, dinv, d, x, cz, cd, rest + i);
-}
-template <typename T>
-__global__ void k_bproject2(int nb, const int* __restrict__ ids, const int8_t* __restrict__ kind,
-                            const T* __restrict__ nrm, int64_t n_p2, T* __restrict__ v, T* __restrict__ w) {
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
-    const int64_t id = ids[k];
-    if (kind[k] == 1) {
-      v[id] = v[n_p2 + id] = v[2 * n_p2 + id] = T(0);
-      w[id] = w[n_p2 + id] = w[2 * n_p2 + id] = T(0);
-    } else {
-      const T nx = nrm[3 * k], ny = nrm[3 * k + 1], nz = nrm[3 * k + 2];
-      const T un = v[id] * nx + v[n_p2 + id] * ny + v[2 * n_p2 + id] * nz;
-      v[id] -= un * nx;
-      v[n_p2 + id] -= un * ny;
-      v[2 * n_p2 + id] -= un * nz;
-      const T wn = w[id] * nx + w[n_p2 + id] * ny + w[2 * n_p2 + id] * nz;
-      w[id] -= wn * nx;
-      w[n_p2 + id] -= wn * ny;
-      w[2 * n_p2 + id] -= wn * nz;
+    for (int c = 0; c < 3; ++c) {
+      const int64_t k = c * n2 + i;
+      iv[c] = dinv[k];
+      if (mode != 2) bv[c] = b[k];
+      if (mode != 0) tv[c] = t[k];
+      if (mode == 2) rv[c] = r[k];
+      if (cd != T(0)) dv[c] = d[k];
+      if (mode != 0) xv[c] = x[k];
+    }
+    const int kb = nmap[i];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T rk = mode == 0 ? bv[c] : (mode == 1 ? bv[c] : rv[c]) - tv[c];
+      rv[c] = rk;
+      T dk = cz * iv[c] * rk;
+      if (cd != T(0)) dk += cd * dv[c];
+      dv[c] = dk;
+      xv[c] = mode == 0 ? dk : xv[c] + dk;
+    }
+    if (kb >= 0) {
+      project_node(kb, kind, nrm, dv[0], dv[1], dv[2]);
+      project_node(kb, kind, nrm, xv[0], xv[1], xv[2]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int64_t k = c * n2 + i;
+      t[k] = T(0);
+      r[k] = rv[c];
+      d[k] = dv[c];
+      x[k] = xv[c];
     }
   }
 }
@@ -547,31 +545,22 @@ void Blas<T>::spmv3(const Csr& P, int64_t ncols, const T* x, T alpha, T beta, T*
   k_spmv3<T><<<blocks_for(P.nrows), 256, 0, s>>>(P.nrows, P.rp, P.ci, P.template w<T>(), ncols, x, alpha, beta, y);
 }
 template <typename T>
-void Blas<T>::cheb_update(int64_t n, int mode, const T* b, T* t, T* r, const T* dinv, T* d, T* x, T cz, T cd,
+void Blas<T>::cheb_update(int64_t n2, int mode, const T* b, T* t, T* r, const T* dinv, T* d, T* x, T cz, T cd,
+                          const BoundaryList& B, cudaStream_t s) {
+  k_cheb_update<T><<<blocks_for(n2), 256, 0, s>>>(n2, mode, b, t, r, dinv, d, x, cz, cd, B.nodemap, B.kind,
+                                                  B.template normals<T>());
+}
+template <typename T>
+void Blas<T>::restrict_residual(const Csr& R, int64_t ncols, const T* b, const T* t, T* y, const BoundaryList& Bc,
+                                cudaStream_t s) {
+  k_restrict_residual<T><<<blocks_for((int64_t)R.nrows * 32, 256, 16384), 256, 0, s>>>(
+      R.nrows, R.rp, R.ci, R.template w<T>(), ncols, b, t, y, Bc.nodemap, Bc.kind, Bc.template normals<T>());
+}
+template <typename T>
+void Blas<T>::prolong_add(const Csr& P, int64_t ncols, const T* xc, T* x, T* t, const BoundaryList& Bf,
                           cudaStream_t s) {
-  // all operands must share the offset from a 16-byte boundary for the vector loads
-  const uintptr_t mis = reinterpret_cast<uintptr_t>(dinv) & 15;
-  const void* ptrs[6] = {b, t, r, dinv, d, x};
-  bool same = true;
-  for (const void* q : ptrs) same = same && (reinterpret_cast<uintptr_t>(q) & 15) == mis;
-  int64_t first = same ? (int64_t)(((16 - mis) & 15) / sizeof(T)) : n;
-  if (first > n) first = n;
-  constexpr int V = 16 / sizeof(T);
-  const int64_t work = first == n ? n : (n - first) / V + V;   // misaligned operands: scalar loop
-  k_cheb_update<T><<<blocks_for(work), 256, 0, s>>>(n, first, mode, b, t, r, dinv, d, x, cz, cd);
-}
-template <typename T>
-void Blas<T>::bproject2(const BoundaryList& B, int64_t n_p2, T* v, T* w, cudaStream_t s) {
-  if (B.nb == 0) return;
-  k_bproject2<T><<<blocks_for(B.nb), 256, 0, s>>>(B.nb, B.ids, B.kind, B.template normals<T>(), n_p2, v, w);
-}
-template <typename T>
-void Blas<T>::restrict_residual(const Csr& R, int64_t ncols, const T* b, const T* t, T* y, cudaStream_t s) {
-  k_restrict_residual<T><<<blocks_for(R.nrows), 256, 0, s>>>(R.nrows, R.rp, R.ci, R.template w<T>(), ncols, b, t, y);
-}
-template <typename T>
-void Blas<T>::prolong_add(const Csr& P, int64_t ncols, const T* xc, T* x, T* t, cudaStream_t s) {
-  k_prolong_add<T><<<blocks_for(P.nrows), 256, 0, s>>>(P.nrows, P.rp, P.ci, P.template w<T>(), ncols, xc, x, t);
+  k_prolong_add<T><<<blocks_for(P.nrows), 256, 0, s>>>(P.nrows, P.rp, P.ci, P.template w<T>(), ncols, xc, x, t,
+                                                       Bf.nodemap, Bf.kind, Bf.template normals<T>());
 }
 template <typename T>
 void Blas<T>::gemv_f64(int n, const double* A, const T* b, T* x, cudaStream_t s) {
@@ -815,8 +804,9 @@ __global__ void k_cg_xr(int64_t n, const double* __restrict__ sc, const T* __res
   const T a = (T)sc[CG_ALPHA];
   if (a == T(0)) return;
   GRID_STRIDE(i, n) {
-    x[i] += a * p[i];
-    r[i] -= a * q[i];
+    const T xi = x[i], pi = p[i], ri = r[i], qi = q[i];
+    x[i] = xi + a * pi;
+    r[i] = ri - a * qi;
   }
 }
 __global__ void k_cg_beta(double* __restrict__ sc, double tol2, double maxit) {
@@ -881,10 +871,20 @@ __global__ void k_mcg_dots(int64_t n, const T* __restrict__ p, const T* __restri
                            unsigned* __restrict__ counter, double* __restrict__ sc) {
   if (!(sc[CG_ACTIVE] > 0.0)) return;   // the same for every block: set by earlier launches
   T sq_t = T(0), spq_t = T(0);
-  GRID_STRIDE(i, n) {
-    const T qi = q[i];
-    sq_t += qi;
-    spq_t += p[i] * qi;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < n; i0 += 4 * stride) {
+    T pv[4], qv[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t i = i0 + k * stride;
+      pv[k] = i < n ? p[i] : T(0);
+      qv[k] = i < n ? q[i] : T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      sq_t += qv[k];
+      spq_t += pv[k] * qv[k];
+    }
   }
   const double sq = block_sum_mixed(sq_t);
   const double spq = block_sum_mixed(spq_t);
@@ -912,17 +912,38 @@ __global__ void k_mcg_update(int64_t n, const T* __restrict__ p, T* __restrict__
   if (!(sc[CG_ACTIVE] > 0.0)) return;
   const T a = (T)sc[CG_ALPHA], mq = (T)sc[CG_MEANQ];
   T srr_t = T(0), srz_t = T(0), sz_t = T(0), sr_t = T(0);
-  GRID_STRIDE(i, n) {
-    x[i] += a * p[i];
-    const T ri = r[i] - a * (q[i] - mq);
-    q[i] = T(0);
-    r[i] = ri;
-    const T zi = dinv[i] * ri;
-    z[i] = zi;
-    srr_t += ri * ri;
-    srz_t += ri * zi;
-    sz_t += zi;
-    sr_t += ri;
+  // four grid-strided elements per round, all loads before the first store: twenty loads
+  // in flight per thread instead of one element's latency after another
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < n; i0 += 4 * stride) {
+    T pv[4], qv[4], xv[4], rv[4], dv[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t i = i0 + k * stride;
+      if (i < n) {
+        pv[k] = p[i];
+        qv[k] = q[i];
+        xv[k] = x[i];
+        rv[k] = r[i];
+        dv[k] = dinv[i];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t i = i0 + k * stride;
+      if (i < n) {
+        x[i] = xv[k] + a * pv[k];
+        const T ri = rv[k] - a * (qv[k] - mq);
+        q[i] = T(0);
+        r[i] = ri;
+        const T zi = dv[k] * ri;
+        z[i] = zi;
+        srr_t += ri * ri;
+        srz_t += ri * zi;
+        sz_t += zi;
+        sr_t += ri;
+      }
+    }
   }
   const double srr = block_sum_mixed(srr_t);
   const double srz = block_sum_mixed(srz_t);
@@ -960,13 +981,13 @@ __global__ void k_mcg_p(int64_t n, const T* __restrict__ z, T* __restrict__ p, c
 template <typename T>
 void CgDev<T>::mass_dots(int64_t n, const T* p, const T* q, double* part, unsigned* counter, double* sc,
                          cudaStream_t s) {
-  k_mcg_dots<T><<<blocks_for(n, 256, kRedBlocks), 256, 0, s>>>(n, p, q, part, counter, sc);
+  k_mcg_dots<T><<<blocks_for(n, 256, kMassRedBlocks), 256, 0, s>>>(n, p, q, part, counter, sc);
 }
 template <typename T>
 void CgDev<T>::mass_update(int64_t n, const T* p, T* q, T* x, T* r, T* z, const T* dinv, double* part,
                            unsigned* counter, double* sc, double tol2, int maxit, cudaStream_t s) {
-  k_mcg_update<T><<<blocks_for(n, 256, kRedBlocks), 256, 0, s>>>(n, p, q, x, r, z, dinv, part, counter, sc, tol2,
-                                                                 (double)maxit);
+  k_mcg_update<T><<<blocks_for(n, 256, kMassRedBlocks), 256, 0, s>>>(n, p, q, x, r, z, dinv, part, counter, sc,
+                                                                     tol2, (double)maxit);
 }
 template <typename T>
 void CgDev<T>::mass_pupd(int64_t n, const T* z, T* p, const double* sc, cudaStream_t s) {

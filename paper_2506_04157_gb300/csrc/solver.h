@@ -12,6 +12,7 @@ namespace mfs {
 struct BoundaryList {
   int nb = 0;
   int* ids = nullptr;
+  int* nodemap = nullptr;   // [n_p2]: position of the node in the list, -1 for interior nodes
   int8_t* kind = nullptr;
   double* nrm64 = nullptr;
   float* nrm32 = nullptr;
@@ -51,16 +52,22 @@ struct Blas {
   static void gemv_f64(int n, const double* A, const T* b, T* x, cudaStream_t s);
   static void convert_from_f64(int64_t n, const double* x, T* y, cudaStream_t s);
   static void convert_to_f64(int64_t n, const T* x, double* y, cudaStream_t s);
-  // Chebyshev update, one pass: r = b (mode 0), b - t (mode 1) or r - t (mode 2);
-  // d = cz dinv r + cd d; x = (mode 0 ? 0 : x) + d; t = 0
-  static void cheb_update(int64_t n, int mode, const T* b, T* t, T* r, const T* dinv, T* d, T* x, T cz, T cd,
+  // Chebyshev update of a velocity vector ([3][n_p2]), one pass per node: r = b (mode 0),
+  // b - t (mode 1) or r - t (mode 2); d = cz dinv r + cd d; x = (mode 0 ? 0 : x) + d;
+  // t = 0; then the boundary projection of d and x at the node
+  static void cheb_update(int64_t n_p2, int mode, const T* b, T* t, T* r, const T* dinv, T* d, T* x, T cz, T cd,
+                          const BoundaryList& B, cudaStream_t s);
+  // y = P_c R (b - t) (restriction of a residual, projected on the coarse level Bc)
+  static void restrict_residual(const Csr& R, int64_t ncols, const T* b, const T* t, T* y, const BoundaryList& Bc,
+                                cudaStream_t s);
+  // x += P xc, projected on the fine level Bf (prolongation of a coarse correction); t = 0
+  static void prolong_add(const Csr& P, int64_t ncols, const T* xc, T* x, T* t, const BoundaryList& Bf,
                           cudaStream_t s);
-  static void bproject2(const BoundaryList& B, int64_t n_p2, T* v, T* w, cudaStream_t s);   // both vectors
-  // y = R (b - t) (restriction of a residual), R in CSR over the fine columns
-  static void restrict_residual(const Csr& R, int64_t ncols, const T* b, const T* t, T* y, cudaStream_t s);
-  // x += P xc (prolongation of a coarse correction); t = 0 on the fine rows
-  static void prolong_add(const Csr& P, int64_t ncols, const T* xc, T* x, T* t, cudaStream_t s);
 };
+
+// blocks (at most) of the mass-CG reduction kernels (each thread takes four elements per
+// round; more blocks would lengthen the serial arrival count of the last-block reduction)
+constexpr int kMassRedBlocks = 512;
 
 // slots of the device-resident CG scalars
 enum { CG_RZ = 0, CG_RZN, CG_PQ, CG_RR, CG_RR0, CG_ALPHA, CG_BETA, CG_IT, CG_ACTIVE, CG_MEANQ, CG_MEANZ, CG_NSLOTS };
@@ -76,7 +83,7 @@ struct CgDev {
   // mean-free) after the sweep q = M p, in three launches whose reductions finish in the
   // last block to arrive: (1) alpha = rz / p.q and mean(q); (2) x += alpha p,
   // r -= alpha (q - mean q), z = dinv r, q = 0, then beta, convergence and mean(z);
-  // (3) p = (z - mean z) + beta p.  part: 4 * kRedBlocks doubles, counter: one zeroed uint.
+  // (3) p = (z - mean z) + beta p.  part: 4 * kMassRedBlocks doubles, counter: one zeroed uint.
   static void mass_dots(int64_t n, const T* p, const T* q, double* part, unsigned* counter, double* sc,
                         cudaStream_t s);
   static void mass_update(int64_t n, const T* p, T* q, T* x, T* r, T* z, const T* dinv, double* part,

@@ -93,3 +93,49 @@ def test_autotune_keeps_results(ensemble, tmp_path):
     y1u, y1p = torch.empty_like(u), torch.empty_like(p)
     P.apply_stokes(L, u, p, y1u, y1p)
     assert (torch.linalg.norm(y1u - y0u) / torch.linalg.norm(y0u)).item() <= 1e-5
+
+
+def test_ensemble_64_members_uneven_levels():
+    """The ensemble workload at full size: 64 shells, refinement levels drawn from {3, 4, 5},
+    log-uniform viscosity contrast in [1e4, 1e6], seeds 100 + i.  The one-launch (persistent)
+    batched apply equals the per-member applies; repeating the call replays the captured
+    graph, a new set of vectors goes back to eager launches."""
+    ctx = mfs.Context(0)
+    rng = np.random.default_rng(3)
+    levels = rng.integers(3, 6, size=64)
+    contrasts = 10.0 ** rng.uniform(4.0, 6.0, size=64)
+    meshes = {int(l): mfs.Mesh(ctx, int(l)) for l in sorted(set(levels.tolist()))}
+    probs = []
+    for i, (l, c) in enumerate(zip(levels, contrasts)):
+        P = mfs.Problem(meshes[int(l)])
+        x1 = meshes[int(l)].coords(int(l), p2=False).T
+        P.set_viscosity(torch.tensor(W.viscosity_plumes(x1, 100 + i, float(c)), device="cuda"))
+        P.set_density(W.dlnrho_table_compressible())
+        probs.append(P)
+    batch = mfs.Batch(ctx, probs)
+    dt = torch.float32
+    us, ps, yus, yps = [], [], [], []
+    for i, P in enumerate(probs):
+        nu, npp = P._sizes(P.mesh.l_max)
+        us.append(torch.tensor(W.random_field(nu, 300 + i), dtype=dt, device="cuda"))
+        ps.append(torch.tensor(W.random_field(npp, 400 + i), dtype=dt, device="cuda"))
+        yus.append(torch.empty(nu, dtype=dt, device="cuda"))
+        yps.append(torch.empty(npp, dtype=dt, device="cuda"))
+    refs = []
+    for P, u, p in zip(probs, us, ps):
+        ru, rp = torch.empty_like(u), torch.empty_like(p)
+        P.apply_stokes(P.mesh.l_max, u, p, ru, rp)
+        refs.append((ru, rp))
+    for rep in range(3):   # eager, captured, replayed
+        for y in yus + yps:
+            y.fill_(float("nan"))
+        batch.apply_stokes(us, ps, yus, yps)
+        for (ru, rp), yu, yp in zip(refs, yus, yps):
+            assert (torch.linalg.norm(yu - ru) / torch.linalg.norm(ru)).item() <= 1e-5
+            assert (torch.linalg.norm(yp - rp) / torch.linalg.norm(rp)).item() <= 1e-5
+    # other output vectors: eager again, same results
+    yus2 = [torch.empty_like(y) for y in yus]
+    yps2 = [torch.empty_like(y) for y in yps]
+    batch.apply_stokes(us, ps, yus2, yps2)
+    for (ru, rp), yu, yp in zip(refs, yus2, yps2):
+        assert (torch.linalg.norm(yu - ru) / torch.linalg.norm(ru)).item() <= 1e-5
