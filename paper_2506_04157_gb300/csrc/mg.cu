@@ -793,78 +793,57 @@ __global__ void k_cg_init(double* __restrict__ sc) {
   sc[CG_ACTIVE] = (sc[CG_RR0] > 0.0 && sc[CG_RZ] > 0.0) ? 1.0 : 0.0;
   sc[CG_ALPHA] = sc[CG_BETA] = 0.0;
 }
-__global__ void k_cg_alpha(double* __restrict__ sc) {
-  const bool ok = sc[CG_ACTIVE] > 0.0 && sc[CG_PQ] > 0.0;
-  sc[CG_ALPHA] = ok ? sc[CG_RZ] / sc[CG_PQ] : 0.0;
-  if (!ok) sc[CG_ACTIVE] = 0.0;
-}
-template <typename T>
-__global__ void k_cg_xr(int64_t n, const double* __restrict__ sc, const T* __restrict__ p, const T* __restrict__ q,
-                        T* __restrict__ x, T* __restrict__ r) {
-  const T a = (T)sc[CG_ALPHA];
-  if (a == T(0)) return;
-  GRID_STRIDE(i, n) {
-    const T xi = x[i], pi = p[i], ri = r[i], qi = q[i];
-    x[i] = xi + a * pi;
-    r[i] = ri - a * qi;
-  }
-}
-__global__ void k_cg_beta(double* __restrict__ sc, double tol2, double maxit) {
-  if (sc[CG_ACTIVE] > 0.0) {
-    const double rzn = sc[CG_RZN];
-    sc[CG_BETA] = rzn / sc[CG_RZ];
-    sc[CG_RZ] = rzn;
-    sc[CG_IT] += 1.0;
-    if (!(sc[CG_RR] > tol2 * sc[CG_RR0]) || sc[CG_IT] >= maxit || !(rzn > 0.0)) sc[CG_ACTIVE] = 0.0;
-  } else {
-    sc[CG_BETA] = 0.0;
-  }
-}
-template <typename T>
-__global__ void k_cg_p(int64_t n, const double* __restrict__ sc, const T* __restrict__ z, T* __restrict__ p) {
-  if (!(sc[CG_ACTIVE] > 0.0)) return;
-  const T b = (T)sc[CG_BETA];
-  GRID_STRIDE(i, n) p[i] = z[i] + b * p[i];
-}
 
 template <typename T>
 void CgDev<T>::init(double* sc, cudaStream_t s) {
   k_cg_init<<<1, 1, 0, s>>>(sc);
 }
-template <typename T>
-void CgDev<T>::alpha(double* sc, cudaStream_t s) {
-  k_cg_alpha<<<1, 1, 0, s>>>(sc);
-}
-template <typename T>
-void CgDev<T>::xr(int64_t n, const double* sc, const T* p, const T* q, T* x, T* r, cudaStream_t s) {
-  k_cg_xr<T><<<blocks_for(n), 256, 0, s>>>(n, sc, p, q, x, r);
-}
-template <typename T>
-void CgDev<T>::beta(double* sc, double tol2, int maxit, cudaStream_t s) {
-  k_cg_beta<<<1, 1, 0, s>>>(sc, tol2, (double)maxit);
-}
-template <typename T>
-void CgDev<T>::pupd(int64_t n, const double* sc, const T* z, T* p, cudaStream_t s) {
-  k_cg_p<T><<<blocks_for(n), 256, 0, s>>>(n, sc, z, p);
-}
-// true in the last block to finish (the others' partials are then visible in L2)
-// (call after thread 0 has written the block's partials)
-__device__ __forceinline__ bool last_block_done(unsigned* counter) {
-  __shared__ bool last;
-  if (threadIdx.x == 0) {
+// Grid-wide sums of K quantities in one pass: per-thread partials in T, warps add in T
+// (FP32 lanes are 64x the FP64 rate here), the block's warps and then the grid's blocks
+// in FP64; the last block to arrive adds the block partials in a fixed order
+// (deterministic).  All K sums share each barrier: one __syncthreads per level.
+template <int K, typename T>
+__device__ __forceinline__ void block_partials(T (&v)[K], double* part) {
+  __shared__ double red[K][32];
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) red[k][w] = (double)v[k];
+  __syncthreads();
+  if (threadIdx.x < K) {
+    double s = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[threadIdx.x][i];
+    part[threadIdx.x * gridDim.x + blockIdx.x] = s;
     __threadfence();
+  }
+}
+// after block_partials: true in the last block to arrive (the counter is left zeroed)
+__device__ __forceinline__ bool last_block_arrived(unsigned* counter) {
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
     last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    if (last) *counter = 0u;
   }
   __syncthreads();
   return last;
 }
+// in the last block: warp k adds quantity k over the blocks; out (shared) gets the K sums
 template <int K>
-__device__ __forceinline__ void final_sums(const double* part, int nb, double out[K]) {
-  for (int k = 0; k < K; ++k) {
+__device__ __forceinline__ void grid_final(const double* part, double* out) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nb = gridDim.x;
+  if (w < K) {
     double a = 0.0;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) a += __ldcg(part + k * nb + i);
-    out[k] = dblock_sum(a);
+    for (int i = lane; i < nb; i += 32) a += __ldcg(part + w * nb + i);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) out[w] = a;
   }
+  __syncthreads();
 }
 template <typename T>
 __global__ void k_mcg_dots(int64_t n, const T* __restrict__ p, const T* __restrict__ q, double* __restrict__ part,
@@ -886,17 +865,12 @@ __global__ void k_mcg_dots(int64_t n, const T* __restrict__ p, const T* __restri
       spq_t += pv[k] * qv[k];
     }
   }
-  const double sq = block_sum_mixed(sq_t);
-  const double spq = block_sum_mixed(spq_t);
+  T v[2] = {sq_t, spq_t};
+  block_partials<2>(v, part);
+  if (!last_block_arrived(counter)) return;
+  __shared__ double f[2];
+  grid_final<2>(part, f);
   if (threadIdx.x == 0) {
-    part[blockIdx.x] = sq;
-    part[gridDim.x + blockIdx.x] = spq;
-  }
-  if (!last_block_done(counter)) return;
-  double f[2];
-  final_sums<2>(part, gridDim.x, f);
-  if (threadIdx.x == 0) {
-    *counter = 0u;
     sc[CG_MEANQ] = f[0] / (double)n;
     sc[CG_PQ] = f[1];             // p is mean-free: p.(q - mean q) = p.q
     const bool ok = f[1] > 0.0;
@@ -945,22 +919,12 @@ __global__ void k_mcg_update(int64_t n, const T* __restrict__ p, T* __restrict__
       }
     }
   }
-  const double srr = block_sum_mixed(srr_t);
-  const double srz = block_sum_mixed(srz_t);
-  const double sz = block_sum_mixed(sz_t);
-  const double sr = block_sum_mixed(sr_t);
+  T v[4] = {srr_t, srz_t, sz_t, sr_t};
+  block_partials<4>(v, part);
+  if (!last_block_arrived(counter)) return;
+  __shared__ double f[4];
+  grid_final<4>(part, f);
   if (threadIdx.x == 0) {
-    const int nb = gridDim.x;
-    part[blockIdx.x] = srr;
-    part[nb + blockIdx.x] = srz;
-    part[2 * nb + blockIdx.x] = sz;
-    part[3 * nb + blockIdx.x] = sr;
-  }
-  if (!last_block_done(counter)) return;
-  double f[4];
-  final_sums<4>(part, gridDim.x, f);
-  if (threadIdx.x == 0) {
-    *counter = 0u;
     const double meanz = f[2] / (double)n;
     const double rzn = f[1] - meanz * f[3];   // r . (z - mean z)
     sc[CG_RR] = f[0];

@@ -75,10 +75,6 @@ enum { CG_RZ = 0, CG_RZN, CG_PQ, CG_RR, CG_RR0, CG_ALPHA, CG_BETA, CG_IT, CG_ACT
 template <typename T>
 struct CgDev {
   static void init(double* sc, cudaStream_t s);                  // it = 0, active = rr0 > 0
-  static void alpha(double* sc, cudaStream_t s);                 // alpha = rz / pq
-  static void xr(int64_t n, const double* sc, const T* p, const T* q, T* x, T* r, cudaStream_t s);
-  static void beta(double* sc, double tol2, int maxit, cudaStream_t s);   // beta, rz, it, active
-  static void pupd(int64_t n, const double* sc, const T* z, T* p, cudaStream_t s);
   // One iteration of CG on P_p M P_p (P_p: mean removal; Jacobi preconditioner, p kept
   // mean-free) after the sweep q = M p, in three launches whose reductions finish in the
   // last block to arrive: (1) alpha = rz / p.q and mean(q); (2) x += alpha p,
