@@ -228,7 +228,8 @@ def run_ours(args, rank, world, device):
         solve = {}
         # mixed: median of `solve_reps` solves (iteration counts vary with the order of the
         # FP32 atomic accumulations); FP64: one solve
-        modes = [("mixed", 1, args.solve_reps)] + ([("fp64", 0, 1)] if args.solve_fp64 and world == 1 else [])
+        modes = [("mixed", 1, args.solve_reps), ("mixed_fp64_outer", 2, args.solve_reps)]
+        modes += [("fp64", 0, 1)] if args.solve_fp64 and world == 1 else []
         for name, mixed, reps in modes:
             runs = []
             for _ in range(reps):

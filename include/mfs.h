@@ -210,7 +210,10 @@ mfs_status mfs_vcycle(mfs_problem* prob, int lvl, mfs_prec prec, int steps, int 
  * S^-1 ~ V-cycle BFBT (Eq. schurV) with CG on X = B A_C^-1 B^T preconditioned by CG on
  * M_{1/eta}.  Defaults (mfs_solve_opts_default) are the paper's Table parametertable. */
 typedef struct {
-  int mixed;          /* 1: FP32 inner FGMRES inside FP64 iterative refinement; 0: all FP64 */
+  int mixed;          /* 1: FP32 inner FGMRES inside FP64 iterative refinement (default);
+                         2: FP64 FGMRES (one FP64 fused apply per iteration) preconditioned by
+                            the FP32 Uzawa step with its FP32 V-cycles and CGs;
+                         0: all FP64 */
   double rtol;        /* stop at ||r|| <= rtol ||r0||, r the FP64 projected residual (1e-8) */
   int restart;        /* FGMRES restart length (30) */
   int max_iters;      /* total FGMRES iterations (300) */

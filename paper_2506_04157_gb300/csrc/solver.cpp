@@ -6,7 +6,8 @@
 //   * Sec. 5.2.1, Eq. (SymmetricUzawaStep1): symmetric Uzawa block preconditioner with
 //     B + C in the pressure update;
 //   * Sec. 5.2.4: FGMRES outer solver; FP32 inner solves wrapped in FP64 iterative
-//     refinement (mixed mode) or everything in FP64 (plain mode).
+//     refinement (mixed = 1), an FP64 FGMRES preconditioned by the FP32 Uzawa step
+//     (mixed = 2), or everything in FP64 (mixed = 0).
 // Host code orchestrates the CUDA kernels; every vector operation runs on the device.
 #include <algorithm>
 #include <array>
@@ -815,6 +816,9 @@ struct Stokes {
   Krylov<T>& K;
   double tolM;
   int transpose;   // 1: the adjoint operator [A (B+C)^T; B 0]
+  // FP64 outer Krylov with an FP32 preconditioner (mixed = 2): the preconditioner of this
+  // (FP64) instance is the FP32 instance's Uzawa step, through FP32 copies of its vectors
+  Stokes<float>* inner = nullptr;
 
   Stokes(mfs_problem* P, const mfs_solve_opts& opts, mfs_solve_stats& stats, int transp = 0)
       : Pb(P), G(P->mg), o(opts), st(stats), L(P->mesh->l_max), n2(P->mesh->levels[L].nb2.total), nu(3 * n2),
@@ -1037,6 +1041,20 @@ struct Stokes {
     return MFS_OK;
   }
 
+  mfs_status precondition(const T* r, T* z) {
+    if constexpr (sizeof(T) == 8) {
+      if (inner) {
+        float* r32 = G->k32.rhs;   // free in this mode: the FP32 FGMRES is not used
+        float* z32 = G->k32.sol;
+        Blas<float>::convert_from_f64(N, r, r32, s);
+        MFS_TRY(inner->uzawa(r32, z32));
+        Blas<float>::convert_to_f64(N, z32, z, s);
+        return MFS_OK;
+      }
+    }
+    return uzawa(r, z);
+  }
+
   // right-preconditioned flexible GMRES(m) on K x = b from x = 0 (modified Gram-Schmidt,
   // Givens rotations on the host); stops at ||b - K x|| <= rtol ||b||
   mfs_status fgmres(const T* b, T* x, double rtol, int* iters, double* rel_out) {
@@ -1061,7 +1079,7 @@ struct Stokes {
       g[0] = beta;
       int k = 0;
       for (; k < m; ++k) {
-        MFS_TRY(uzawa(K.V[k], K.Z[k]));
+        MFS_TRY(precondition(K.V[k], K.Z[k]));
         MFS_TRY(Kop(K.Z[k], K.V[k + 1]));
         for (int i = 0; i <= k; ++i) {
           const double hik = dotn(N, K.V[k + 1], K.V[i]);
@@ -1161,8 +1179,12 @@ static mfs_status stokes_solve(mfs_problem* Pb, const mfs_solve_opts& o, const d
   const int L = Pb->mesh->l_max;
   const int64_t n2 = Pb->mesh->levels[L].nb2.total, nu = 3 * n2, np = Pb->mesh->levels[L].nb1.total, N = nu + np;
   cudaStream_t s = Pb->mesh->ctx->stream;
-  MFS_TRY(ensure_krylov<double>(G, nu, np, o.mixed ? 1 : o.restart, s));
-  if (o.mixed) MFS_TRY(ensure_krylov<float>(G, nu, np, o.restart, s));
+  if (o.mixed < 0 || o.mixed > 2) {
+    set_error("mixed must be 0 (FP64), 1 (FP32 FGMRES in FP64 refinement) or 2 (FP64 FGMRES, FP32 preconditioner)");
+    return MFS_EINVAL;
+  }
+  MFS_TRY(ensure_krylov<double>(G, nu, np, o.mixed == 1 ? 1 : o.restart, s));
+  if (o.mixed) MFS_TRY(ensure_krylov<float>(G, nu, np, o.mixed == 1 ? o.restart : 1, s));
   Krylov<double>& K64 = G->k64;
   double* r = K64.ir_r;      // FP64 projected residual
   double* y = K64.ir_y;      // operator output / scaled residual
@@ -1186,7 +1208,14 @@ static mfs_status stokes_solve(mfs_problem* Pb, const mfs_solve_opts& o, const d
   for (int outer = 0; outer < o.max_outer && rn > o.rtol * r0; ++outer) {
     int its = 0;
     double rel = 0.0;
-    if (o.mixed) {
+    if (o.mixed == 2) {
+      Stokes<float> S32(Pb, o, st, transpose);
+      Stokes<double> S(Pb, o, st, transpose);
+      S.inner = &S32;
+      Blas<double>::axpby(N, 1.0 / rn, r, 0.0, K64.rhs, s);
+      status = S.fgmres(K64.rhs, d, o.rtol * r0 / rn, &its, &rel);
+      if (status != MFS_OK) return status;
+    } else if (o.mixed) {
       Stokes<float> S(Pb, o, st, transpose);
       float* r32 = G->k32.rhs;
       float* d32 = G->k32.sol;

@@ -53,6 +53,8 @@ def test_nan_rhs_and_iteration_cap(prob):
     p = torch.zeros_like(g)
     st = P.solve(fbad, g, u, p, raise_on_error=False)
     assert st["status"] == "MFS_ENAN"
+    st = P.solve(f, g, u, p, raise_on_error=False, mixed=3)   # no such precision mode
+    assert st["status"] == "MFS_EINVAL"
     u.zero_()
     p.zero_()
     st = P.solve(f, g, u, p, raise_on_error=False, max_iters=1, max_outer=1)

@@ -1,4 +1,5 @@
-"""GPU Stokes solves (mixed FP32 + FP64 refinement, and plain FP64) against the oracle:
+"""GPU Stokes solves (mixed FP32 + FP64 refinement, FP64 FGMRES with the FP32 preconditioner,
+and plain FP64) against the oracle:
 the oracle's own FP64 evaluation of the projected residual of the GPU iterate, and the
 oracle's direct solution of the projected system."""
 import functools
@@ -40,7 +41,7 @@ def rhs(L, seed=3):
     return f, np.zeros(L.n_p1)
 
 
-@pytest.mark.parametrize("mixed", [1, 0])
+@pytest.mark.parametrize("mixed", [1, 2, 0])
 @pytest.mark.parametrize("bc", [("dirichlet", "freeslip"), ("freeslip", "dirichlet")])
 def test_solve_level2(mixed, bc):
     H, S, ctx, gm, prob = setup(2, bc)
@@ -89,7 +90,7 @@ def test_solve_level3_plumes_mixed_vs_fp64():
     L = H.levels[3]
     f, g = rhs(L, 7)
     sols = {}
-    for mixed in (1, 0):
+    for mixed in (1, 2, 0):
         u = torch.zeros(3 * L.n_p2, dtype=torch.float64, device="cuda")
         p = torch.zeros(L.n_p1, dtype=torch.float64, device="cuda")
         st = prob.solve(torch.tensor(f, device="cuda"), torch.tensor(g, device="cuda"), u, p, mixed=mixed)
@@ -99,3 +100,4 @@ def test_solve_level3_plumes_mixed_vs_fp64():
         assert np.linalg.norm(S.residual(f, g, un, pn)) <= 1.5e-8 * r0
         sols[mixed] = (un, pn)
     assert np.linalg.norm(sols[1][0] - sols[0][0]) / np.linalg.norm(sols[0][0]) < 1e-5
+    assert np.linalg.norm(sols[2][0] - sols[0][0]) / np.linalg.norm(sols[0][0]) < 1e-5
