@@ -218,12 +218,11 @@ def run_ours(args, rank, world, device):
 
     # time to solve: multigrid setup (diag, eigenvalue estimates, coarse inverse) plus the
     # solve to relative residual 1e-8 measured in FP64, on the same problem
+    # forcing: the buoyancy load vector of a temperature field of 8 Gaussian blobs (seed 3)
+    # with the compressible density profile, gravity -x/|x|, scale 1
     solve = None
     if args.solve:
-        x2 = mesh.coords(level).T
-        T = W.temperature_blobs(x2, 3)
-        xh = x2 / np.linalg.norm(x2, axis=1, keepdims=True)
-        f = torch.tensor(np.concatenate([T * xh[:, 0], T * xh[:, 1], T * xh[:, 2]]) * 1e-3, device=dev)
+        f = buoyancy_forcing(mesh, prob, level, dev)
         g = torch.zeros(npp, dtype=torch.float64, device=dev)
         solve = {}
         # mixed: median of `solve_reps` solves (iteration counts vary with the order of the
@@ -288,6 +287,17 @@ def run_ours(args, rank, world, device):
     return line
 
 
+def buoyancy_forcing(mesh, prob, level, dev):
+    """f = int rho(r) T (x/|x|) . phi on the finest level (mfs_rhs_buoyancy), T the nodal P2
+    temperature of 8 Gaussian blobs (seed 3)."""
+    import torch
+    import workloads as W
+    T = torch.tensor(W.temperature_blobs(mesh.coords(level).T, 3), device=dev)
+    f = torch.empty(3 * T.numel(), dtype=torch.float64, device=dev)
+    prob.rhs_buoyancy(T, f, scale=1.0)
+    return f
+
+
 def profile_solve(level):
     """A window of solver work between cudaProfilerStart/Stop (everything before it warms
     up the captured graphs): the launch list of the V-cycles and one preconditioned FGMRES
@@ -299,10 +309,7 @@ def profile_solve(level):
     prob.setup_multigrid(1)
     u = torch.tensor(W.random_field(3 * inf.n_p2, 5, np.float32), device="cuda")
     y = torch.empty_like(u)
-    x2 = mesh.coords(level).T
-    T = W.temperature_blobs(x2, 3)
-    xh = x2 / np.linalg.norm(x2, axis=1, keepdims=True)
-    f = torch.tensor(np.concatenate([T * xh[:, 0], T * xh[:, 1], T * xh[:, 2]]) * 1e-3, device="cuda")
+    f = buoyancy_forcing(mesh, prob, level, "cuda")
     g = torch.zeros(inf.n_p1, dtype=torch.float64, device="cuda")
     uu = torch.zeros(3 * inf.n_p2, dtype=torch.float64, device="cuda")
     p = torch.zeros_like(g)

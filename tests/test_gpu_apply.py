@@ -110,3 +110,39 @@ def test_constrained_and_fused(l, dtype, bc):
     prob.apply_stokes(l, ud, pd, yu, yp, transpose=True)
     assert rel(yu.cpu().double().numpy(), co.apply_A(u) + co.apply_BbarT(p)) <= TOL[dtype]
     assert rel(yp.cpu().double().numpy(), co.apply_B(u)) <= TOL[dtype]
+
+
+def test_fused_apply_level5_sampled_rows():
+    """The bench's workload and launch at full size: level 5 (1,966,080 micro-tets), plume
+    viscosity of contrast 1e6 (seed 2), compressible density, the constrained fused apply in
+    FP32 and FP64.  The oracle evaluates sampled rows one by one from every micro-tet that
+    touches 256 interior P2 nodes and 128 P1 vertices, on the projected inputs: interior
+    velocity rows equal A P0 u + B^T P_p p; pressure rows equal (B+C) P0 u up to the one
+    constant that P_p removes from the whole output."""
+    from oracle.fem import stokes_apply_elements, tets_touching
+    lvl = 5
+    L = Level(MacroMesh(), lvl)
+    dl = W.dlnrho_table_compressible()
+    eta = W.viscosity_plumes(L.p1_x, seed=2, contrast=1e6)
+    ctx = mfs.Context(0)
+    gm = mfs.Mesh(ctx, lvl)
+    prob = mfs.Problem(gm, "dirichlet", "freeslip")
+    prob.set_viscosity(torch.tensor(eta, device="cuda"))
+    prob.set_density(dl)
+    rng = np.random.default_rng(11)
+    s2 = np.sort(rng.choice(np.flatnonzero(L.p2_class == 0), 256, replace=False))
+    s1 = np.sort(rng.choice(L.n_p1, 128, replace=False))
+    sel = tets_touching(L, p2_nodes=s2, p1_nodes=s1)
+    cons = Constraints(L, 0, 1)
+    rows = np.concatenate([s2, s2 + L.n_p2, s2 + 2 * L.n_p2])
+    for dtype in (torch.float32, torch.float64):
+        u, p = inputs(L, dtype, seed=21)
+        yu_ref, yp_ref = stokes_apply_elements(L, eta, dl, cons.P0(u), p - p.mean(), sel)
+        yu = torch.empty(3 * L.n_p2, dtype=dtype, device="cuda")
+        yp = torch.empty(L.n_p1, dtype=dtype, device="cuda")
+        prob.apply_stokes(lvl, dev(u, dtype), dev(p, dtype), yu, yp)
+        yu = yu.cpu().double().numpy()
+        yp = yp.cpu().double().numpy()
+        assert rel(yu[rows], yu_ref[rows]) <= TOL[dtype]
+        d = yp[s1] - yp_ref[s1]
+        assert np.linalg.norm(d - d.mean()) <= TOL[dtype] * np.linalg.norm(yp_ref[s1])
