@@ -354,7 +354,8 @@ def cpu_baseline(level, budget_s=12.0):
     t_full = t_used * ntet / done
     dofs = 3 * L.n_p2 + L.n_p1
     return {"value": round(dofs / t_full / 1e9, 6), "unit": "GDoF/s", "cores": 1, "kind": "oracle",
-            "sample": f"{done} of {ntet} micro-tets (random), {t_used:.1f} s, scaled to one full apply"}
+            "sample": f"{done} of {ntet} micro-tets (random), {t_used:.1f} s, scaled to one full apply",
+            "dofs_per_apply": dofs}
 
 
 def run_reference(args, rank, world):
@@ -368,8 +369,9 @@ def run_reference(args, rank, world):
             times.append(cb["value"])
     v = statistics.median(times)
     cb["value"] = v
+    ms_per_step = cb["dofs_per_apply"] / (v * 1e9) * 1e3   # one full apply at this rate
     return {"metric": METRIC, "value": v, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 1), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD, "level": args.level},
             "cpu_baseline": cb,
