@@ -229,6 +229,13 @@ typedef struct {
   int m_V, deg_V;     /* cheap V-cycle A_C (1, 1) */
   int max_cg;         /* iteration cap of every inner CG (200) */
   int with_C;         /* 1: compressible constraint (B + C) (1) */
+  int uzawa;          /* block preconditioner (Sec. 5.2.1): 0 symmetric Uzawa (Eq.
+                         SymmetricUzawaStep1, default), 1 inexact Uzawa (Eq.
+                         InexactUzawaStep1), 2 adjoint inexact Uzawa (Eq.
+                         AdjointInexactUzawaStep1); each applied from (0, 0) */
+  int schur;          /* Schur approximation (Sec. 5.2.3): 0 V-cycle BFBT (Eq. schurV, default),
+                         1 inverse-viscosity mass M_{1/eta}^-1 by CG to tol_invMass (Eq.
+                         schurMass), 2 diag(A)-BFBT (C = D = diag(A), solved like 0) */
 } mfs_solve_opts;
 
 typedef struct {

@@ -15,6 +15,11 @@ Paper passages followed (arxiv 2506.04157):
     CG to tol_VBFBT preconditioned by M_{1/eta} (itself solved by CG to tol_invMass).
   * Sec. 5.2.4: FGMRES outer solver preconditioned by the block preconditioner.
   * Table parametertable: the default parameters.
+  * Sec. 5.2.1, Eqs. (InexactUzawaStep1), (AdjointInexactUzawaStep1): the inexact and
+    adjoint inexact Uzawa steps (the alternatives to the symmetric step), each from (0, 0).
+  * Sec. 5.2.3, Eq. (schurMass): S_M^-1 = M_{1/eta}^-1 solved by CG to tol_invMass; the
+    diag(A)-BFBT approximation (C = D = diag(A) in the BFBT formula of Sec. 5.2.3), whose
+    B diag(A)^-1 B^T solve is structured like the V-cycle BFBT's.
 
 Readings:
   * Chebyshev iteration in the form of Saad, Iterative Methods, Alg. 12.1 (with the
@@ -40,7 +45,8 @@ from .fem import (Operators, Constraints, ConstrainedOperators, project_mean_zer
                   p2_values, QUAD_BARY)
 
 DEFAULTS = dict(sigma=1.0, omega=0.3, tol_A=1e-2, m_A=3, deg_A=2, tol_VBFBT=1e-1,
-                tol_invMass=1e-10, m_V=1, deg_V=1, tol_coarse=1e-2)
+                tol_invMass=1e-10, m_V=1, deg_V=1, tol_coarse=1e-2,
+                uzawa="symmetric", schur="vbfbt")
 
 
 # ------------------------------------------------------------------------- transfers
@@ -267,7 +273,9 @@ def inject(Lfine, Lcoarse, eta_fine):
 
 # ------------------------------------------------------------------------- Stokes solver
 class StokesOracle:
-    """FGMRES + symmetric Uzawa + V-cycle BFBT on the projected saddle-point system."""
+    """FGMRES + a Uzawa-type block preconditioner (symmetric by default; inexact, adjoint
+    inexact) with a Schur approximation (V-cycle BFBT by default; mass, diag(A)-BFBT) on
+    the projected saddle-point system."""
 
     def __init__(self, hier: Hierarchy, params=None):
         self.h = hier
@@ -304,23 +312,49 @@ class StokesOracle:
                   M=lambda v: project_mean_zero(self.Mdinv * v), rtol=self.p["tol_invMass"], maxit=500)
         return project_mean_zero(x)
 
+    def Dinv(self, r):
+        """diag(A)^-1 on the constrained velocity space."""
+        return self.cons.P0(r / self.h.diag[self.L])
+
+    def bfbt(self, r, Cinv):
+        """BFBT with C = D: (B C^-1 B^T)^-1 (B C^-1 A C^-1 B^T) (B C^-1 B^T)^-1 r, the outer
+        inverses by CG to tol_VBFBT preconditioned by M_{1/eta}."""
+        p = self.p
+        X = lambda q: self.co.apply_B(Cinv(self.co.apply_BT(q)))
+        y, _ = cg(X, project_mean_zero(r), M=self.Minv, rtol=p["tol_VBFBT"], maxit=200)
+        w = Cinv(self.co.apply_BT(y))
+        w = self.co.apply_B(Cinv(self.co.apply_A(w)))
+        z, _ = cg(X, project_mean_zero(w), M=self.Minv, rtol=p["tol_VBFBT"], maxit=200)
+        return project_mean_zero(z)
+
     def X(self, q):
         return self.co.apply_B(self.Ac_inv(self.co.apply_BT(q)))
 
     def Shat_inv(self, r):
-        """V-cycle BFBT: X^-1 (B A_C^-1 A A_C^-1 B^T) X^-1 r."""
-        p = self.p
-        y, _ = cg(self.X, project_mean_zero(r), M=self.Minv, rtol=p["tol_VBFBT"], maxit=200)
-        w = self.Ac_inv(self.co.apply_BT(y))
-        w = self.co.apply_B(self.Ac_inv(self.co.apply_A(w)))
-        z, _ = cg(self.X, project_mean_zero(w), M=self.Minv, rtol=p["tol_VBFBT"], maxit=200)
-        return project_mean_zero(z)
+        """The Schur approximation: V-cycle BFBT X^-1 (B A_C^-1 A A_C^-1 B^T) X^-1 r (Eq.
+        schurV), the inverse-viscosity mass M_{1/eta}^-1 r (Eq. schurMass), or diag(A)-BFBT."""
+        kind = self.p["schur"]
+        if kind == "mass":
+            return self.Minv(r)
+        if kind == "diagbfbt":
+            return self.bfbt(r, self.Dinv)
+        return self.bfbt(r, self.Ac_inv)
 
     def uzawa(self, r):
-        """Symmetric Uzawa step from (0, 0) on the residual r = (r_u, r_p)."""
+        """One Uzawa-type step from (0, 0) on the residual r = (r_u, r_p); B + C replaces B
+        in the pressure updates (Sec. 5.2.1)."""
         p = self.p
         ru, rp = r[:self.nu], r[self.nu:]
-        uh = p["sigma"] * self.Ahat_inv(ru)
+        kind = p["uzawa"]
+        if kind == "inexact":        # Eq. (InexactUzawaStep1)
+            un = p["sigma"] * self.Ahat_inv(ru)
+            pn = -p["omega"] * self.Shat_inv(rp - self.co.apply_Bbar(un))
+            return np.concatenate([un, pn])
+        if kind == "adjoint":        # Eq. (AdjointInexactUzawaStep1)
+            pn = -p["omega"] * self.Shat_inv(rp)
+            un = p["sigma"] * self.Ahat_inv(ru - self.co.apply_BT(pn))
+            return np.concatenate([un, pn])
+        uh = p["sigma"] * self.Ahat_inv(ru)                  # Eq. (SymmetricUzawaStep1)
         pn = -p["omega"] * self.Shat_inv(rp - self.co.apply_Bbar(uh))
         un = uh + p["sigma"] * self.Ahat_inv(ru - self.co.apply_A(uh) - self.co.apply_BT(pn))
         return np.concatenate([un, pn])

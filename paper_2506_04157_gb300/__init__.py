@@ -40,7 +40,8 @@ class SolveOpts(ctypes.Structure):
                 ("sigma", ctypes.c_double), ("omega", ctypes.c_double), ("tol_A", ctypes.c_double),
                 ("m_A", ctypes.c_int), ("deg_A", ctypes.c_int), ("tol_VBFBT", ctypes.c_double),
                 ("tol_invMass", ctypes.c_double), ("m_V", ctypes.c_int), ("deg_V", ctypes.c_int),
-                ("max_cg", ctypes.c_int), ("with_C", ctypes.c_int)]
+                ("max_cg", ctypes.c_int), ("with_C", ctypes.c_int), ("uzawa", ctypes.c_int),
+                ("schur", ctypes.c_int)]
 
 
 class SolveStats(ctypes.Structure):

@@ -992,15 +992,24 @@ struct Stokes {
     st.cg_M_max = it > st.cg_M_max ? it : st.cg_M_max;
     return mean_free<T>(Pb, x, np);
   }
-  // X q = B A_C^-1 B^T q
+  // diag(A)^-1 on the constrained velocity space (finest level)
+  mfs_status D_inv(const T* r, T* x) {
+    Blas<T>::mul(nu, r, work<T>(G, L).dinv, x, s);
+    Blas<T>::bproject(G->bnd[L], n2, x, s);
+    return MFS_OK;
+  }
+  // the C^-1 of the BFBT approximation: the cheap V-cycle (V-cycle BFBT) or diag(A)^-1
+  mfs_status C_inv(const T* r, T* x) { return o.schur == 2 ? D_inv(r, x) : Ac_inv(r, x); }
+  // X q = B C^-1 B^T q
   mfs_status X(const T* q, T* y) {
     MFS_TRY(BT(q, K.ua));
-    MFS_TRY(Ac_inv(K.ua, K.ub));
+    MFS_TRY(C_inv(K.ua, K.ub));
     return Bop(K.ub, y, 0);
   }
   // V-cycle BFBT: X^-1 (B A_C^-1 A A_C^-1 B^T) X^-1 r
   mfs_status S_inv(const T* r, T* z) {
     WallTimer tm(st.time_Sinv_ms);
+    if (o.schur == 1) return M_inv(r, z);   // Eq. schurMass: M_{1/eta}^-1 (mean-free)
     int it = 0;
     auto op = [&](const T* v, T* y) { return X(v, y); };
     auto pre = [&](const T* v, T* y) { return M_inv(v, y); };
@@ -1009,9 +1018,9 @@ struct Stokes {
     st.cg_X_calls++;
     st.cg_X_max = it > st.cg_X_max ? it : st.cg_X_max;
     MFS_TRY(BT(K.pe, K.uc));
-    MFS_TRY(Ac_inv(K.uc, K.ud));
+    MFS_TRY(C_inv(K.uc, K.ud));
     MFS_TRY(A(K.ud, K.uc));
-    MFS_TRY(Ac_inv(K.uc, K.ud));
+    MFS_TRY(C_inv(K.uc, K.ud));
     MFS_TRY(Bop(K.ud, K.pf, 0));
     MFS_TRY(cg(np, op, pre, K.pf, z, o.tol_VBFBT, o.max_cg, K.cgp_r, K.cgp_z, K.cgp_p, K.cgp_q, &it, 1));
     st.cg_X_iters += it;
@@ -1019,13 +1028,32 @@ struct Stokes {
     st.cg_X_max = it > st.cg_X_max ? it : st.cg_X_max;
     return mean_free<T>(Pb, z, np);
   }
-  // symmetric Uzawa step from (0, 0) on r = (r_u, r_p); output z = (u, p)
+  // Uzawa-type step from (0, 0) on r = (r_u, r_p); output z = (u, p).  B + C replaces B
+  // in the pressure updates (the adjoint operator swaps the roles, see Bop/BTrow).
   mfs_status uzawa(const T* r, T* z) {
     const T* ru = r;
     const T* rp = r + nu;
     T* zu = z;
     T* zp = z + nu;
-    T* uh = K.tmpu;
+    if (o.uzawa == 1) {   // inexact Uzawa, Eq. (InexactUzawaStep1)
+      MFS_TRY(Ahat_inv(ru, zu));
+      if (o.sigma != 1.0) Blas<T>::axpby(nu, T(o.sigma), zu, T(0), zu, s);
+      MFS_TRY(Bop(zu, K.pa, withc_row()));
+      Blas<T>::axpbypcz(np, T(1), rp, T(-1), K.pa, T(0), K.pb, s);     // r_p - Bbar u
+      MFS_TRY(S_inv(K.pb, zp));
+      Blas<T>::axpby(np, T(-o.omega), zp, T(0), zp, s);
+      return MFS_OK;
+    }
+    if (o.uzawa == 2) {   // adjoint inexact Uzawa, Eq. (AdjointInexactUzawaStep1)
+      MFS_TRY(S_inv(rp, zp));
+      Blas<T>::axpby(np, T(-o.omega), zp, T(0), zp, s);                // p = -omega S^-1 r_p
+      MFS_TRY(BTrow(zp, K.ua));
+      Blas<T>::axpbypcz(nu, T(1), ru, T(-1), K.ua, T(0), K.ub, s);     // r_u - B^T p
+      MFS_TRY(Ahat_inv(K.ub, zu));
+      if (o.sigma != 1.0) Blas<T>::axpby(nu, T(o.sigma), zu, T(0), zu, s);
+      return MFS_OK;
+    }
+    T* uh = K.tmpu;       // symmetric Uzawa, Eq. (SymmetricUzawaStep1)
     MFS_TRY(Ahat_inv(ru, uh));
     if (o.sigma != 1.0) Blas<T>::axpby(nu, T(o.sigma), uh, T(0), uh, s);
     MFS_TRY(Bop(uh, K.pa, withc_row()));                               // (B + C) uh (B: adjoint)
@@ -1183,6 +1211,11 @@ static mfs_status stokes_solve(mfs_problem* Pb, const mfs_solve_opts& o, const d
     set_error("mixed must be 0 (FP64), 1 (FP32 FGMRES in FP64 refinement) or 2 (FP64 FGMRES, FP32 preconditioner)");
     return MFS_EINVAL;
   }
+  if (o.uzawa < 0 || o.uzawa > 2 || o.schur < 0 || o.schur > 2) {
+    set_error("uzawa must be 0 (symmetric), 1 (inexact) or 2 (adjoint); schur 0 (V-cycle BFBT), 1 (mass) or "
+              "2 (diag(A)-BFBT)");
+    return MFS_EINVAL;
+  }
   MFS_TRY(ensure_krylov<double>(G, nu, np, o.mixed == 1 ? 1 : o.restart, s));
   if (o.mixed) MFS_TRY(ensure_krylov<float>(G, nu, np, o.mixed == 1 ? o.restart : 1, s));
   Krylov<double>& K64 = G->k64;
@@ -1281,6 +1314,8 @@ void mfs_solve_opts_default(mfs_solve_opts* o) {
   o->deg_V = 1;
   o->max_cg = 200;
   o->with_C = 1;
+  o->uzawa = 0;
+  o->schur = 0;
 }
 
 mfs_status mfs_stokes_solve(mfs_problem* Pb, const mfs_solve_opts* opts, const double* f, const double* g, double* u,

@@ -55,6 +55,8 @@ def test_nan_rhs_and_iteration_cap(prob):
     assert st["status"] == "MFS_ENAN"
     st = P.solve(f, g, u, p, raise_on_error=False, mixed=3)   # no such precision mode
     assert st["status"] == "MFS_EINVAL"
+    st = P.solve(f, g, u, p, raise_on_error=False, uzawa=5)   # no such block preconditioner
+    assert st["status"] == "MFS_EINVAL"
     u.zero_()
     p.zero_()
     st = P.solve(f, g, u, p, raise_on_error=False, max_iters=1, max_outer=1)

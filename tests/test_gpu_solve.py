@@ -101,3 +101,26 @@ def test_solve_level3_plumes_mixed_vs_fp64():
         sols[mixed] = (un, pn)
     assert np.linalg.norm(sols[1][0] - sols[0][0]) / np.linalg.norm(sols[0][0]) < 1e-5
     assert np.linalg.norm(sols[2][0] - sols[0][0]) / np.linalg.norm(sols[0][0]) < 1e-5
+
+
+@pytest.mark.parametrize("uzawa,schur", [(1, 0), (2, 0), (0, 1), (0, 2)])
+def test_solve_preconditioner_variants(uzawa, schur):
+    """The inexact and adjoint inexact Uzawa steps and the mass and diag(A)-BFBT Schur
+    approximations (Sec. 5.2.1, 5.2.3) reach the same solution as the oracle's direct solve
+    (tol_A = 1e-4 for the one-sided Uzawa steps, as in the paper's comparison)."""
+    H, S, ctx, gm, prob = setup(2)
+    L = H.levels[2]
+    f, g = rhs(L, 9)
+    u = torch.zeros(3 * L.n_p2, dtype=torch.float64, device="cuda")
+    p = torch.zeros(L.n_p1, dtype=torch.float64, device="cuda")
+    opts = dict(uzawa=uzawa, schur=schur)
+    if uzawa:
+        opts["tol_A"] = 1e-4
+    st = prob.solve(torch.tensor(f, device="cuda"), torch.tensor(g, device="cuda"), u, p, **opts)
+    assert st["status"] == "MFS_OK" and st["rel_residual"] <= 1e-8
+    un, pn = u.cpu().numpy(), p.cpu().numpy()
+    r0 = np.linalg.norm(S.residual(f, g, 0 * un, 0 * pn))
+    assert np.linalg.norm(S.residual(f, g, un, pn)) <= 1.5e-8 * r0
+    ud, pd = direct_solve(H, f, g, 0 * un, 0 * pn)
+    assert np.linalg.norm(un - ud) / np.linalg.norm(ud) < 1e-5
+    assert np.linalg.norm(pn - pd) / np.linalg.norm(pd) < 1e-5

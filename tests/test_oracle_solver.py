@@ -16,8 +16,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 
 def test_default_parameters_match_paper_table():
     gold = json.load(open(os.path.join(HERE, "golden", "solver_parameters.json")))
-    for k, v in DEFAULTS.items():
-        assert gold[k] == v, k
+    for k, v in gold.items():
+        if k != "_source":
+            assert DEFAULTS[k] == v, k
+    assert DEFAULTS["uzawa"] == "symmetric" and DEFAULTS["schur"] == "vbfbt"   # Sec. 5.2.4
 
 
 def test_chebyshev_error_reduction_closed_form():
@@ -120,3 +122,26 @@ def test_stokes_fgmres_matches_direct(hier2):
     # the direct solution has (near) zero projected residual
     r = S.residual(f, g, ud, pd)
     assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(S.residual(f, g, 0 * ud, 0 * pd))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("uzawa,schur", [("inexact", "vbfbt"), ("adjoint", "vbfbt"), ("symmetric", "mass"),
+                                         ("symmetric", "diagbfbt")])
+def test_stokes_preconditioner_variants_match_direct(hier2, uzawa, schur):
+    """Every block preconditioner / Schur approximation of Sec. 5.2 leaves the solution
+    unchanged: FGMRES with it reaches the direct solution (tol_A = 1e-4 for the one-sided
+    Uzawa steps, as in the paper's comparison)."""
+    H = hier2
+    params = dict(uzawa=uzawa, schur=schur)
+    if uzawa != "symmetric":
+        params["tol_A"] = 1e-4
+    S = StokesOracle(H, params)
+    rng = np.random.default_rng(2)
+    n, npp = 3 * H.levels[2].n_p2, H.levels[2].n_p1
+    f = rng.standard_normal(n)
+    g = np.zeros(npp)
+    u, p, it, hist = S.solve(f, g, np.zeros(n), np.zeros(npp), rtol=1e-8)
+    assert hist[-1] <= 1e-8 * hist[0]
+    ud, pd = direct_solve(H, f, g, np.zeros(n), np.zeros(npp))
+    assert np.linalg.norm(u - ud) / np.linalg.norm(ud) < 1e-5
+    assert np.linalg.norm(p - pd) / np.linalg.norm(pd) < 1e-5
