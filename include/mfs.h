@@ -135,6 +135,22 @@ mfs_status mfs_set_viscosity(mfs_problem* prob, const double* eta_p1, int is_log
  * Default: 0 (incompressible).  Errors: MFS_EINVAL. */
 mfs_status mfs_set_density(mfs_problem* prob, int n, const double* dlnrho_dr);
 
+/* Temperature-dependent viscosity (paper Sec. 7.2, Eq. ViscosityDef, Frank-Kamenetskii):
+ *   eta(x, T) = eta_base(|x|) exp(-E_A T + V_A (r_surf - |x|)),
+ * log10 eta_base given by n (1..64) values on a uniform radial grid over [r_cmb, r_surf]
+ * (HOST array, linear interpolation; the paper shows its profile only as a figure; it uses
+ * E_A = 4.610, V_A = 2.996).  Per Sec. 5.2.2 the levels above l_eta carry eta as a P1
+ * function of its values at the vertices, the levels l <= l_eta evaluate eta at every
+ * quadrature point from the P2 temperature (-1 <= l_eta < l_max; -1: P1 everywhere).
+ * Takes effect with mfs_set_temperature.  Errors: MFS_EINVAL, MFS_ECUDA. */
+mfs_status mfs_set_viscosity_law(mfs_problem* prob, double E_A, double V_A, int n, const double* log10_base,
+                                 int l_eta);
+/* The finest level's P2 temperature T_p2 [n_p2] (FP64, device): sets the viscosity of every
+ * level from the law (replaces mfs_set_viscosity; mfs_set_viscosity in turn drops the law).
+ * On levels <= l_eta only the A block is available (B and the fused applies return
+ * MFS_EINVAL there).  Errors: MFS_EINVAL (no law), MFS_ECUDA. */
+mfs_status mfs_set_temperature(mfs_problem* prob, const double* T_p2);
+
 /* y = A(eta) u on level lvl (paper Sec. 5.1, A_ij = int 2 eta eps(phi_j):eps(phi_i),
  * eps(u) = sym grad u - (div u) I/3; blending Jacobian evaluated at every quadrature
  * point of the symmetric 4-point degree-2 rule).  u, y: [3][n_p2(lvl)].  u and y must

@@ -86,8 +86,12 @@ class Geometry:
 def element_A(geo, eta_vertex):
     """(E,30,30) element matrices of A = int 2 eta eps(phi_j):eps(phi_i); local dof
     index c*10 + a for component c of node a; eta_vertex: (E,4) P1 nodal viscosity."""
+    return element_A_q(geo, eta_vertex @ QUAD_BARY.T)
+
+
+def element_A_q(geo, etaq):
+    """element_A with the viscosity given at the quadrature points, etaq: (E,Q)."""
     E = geo.grad.shape[0]
-    etaq = eta_vertex @ QUAD_BARY.T                                                        # (E,Q)
     g = geo.grad                                                                           # (E,Q,10,3)
     # grad(phi_a e_c) has row c equal to g_a: build eps for all 30 vector basis fns
     eps = np.zeros((E, 4, 3, 10, 3, 3))
@@ -133,11 +137,24 @@ def assemble(rows, cols, vals, shape):
     return sp.coo_matrix((vals.reshape(-1), (R, C)), shape=shape).tocsr()
 
 
+def viscosity_law(x, T, law):
+    """Frank-Kamenetskii viscosity (Sec. 7.2, Eq. ViscosityDef):
+        eta(x, T) = eta_base(|x|) exp(-E_A T + V_A (r_surf - |x|)),
+    law: dict with E_A, V_A, r_cmb, r_surf and log10_base, the base profile's log10 values on
+    a uniform radial grid over [r_cmb, r_surf] (linear interpolation; the paper gives the
+    profile as a figure)."""
+    r = np.linalg.norm(np.asarray(x, dtype=np.float64), axis=-1)
+    base = 10.0 ** interp_table(law["log10_base"], r, law["r_cmb"], law["r_surf"])
+    return base * np.exp(-law["E_A"] * np.asarray(T, dtype=np.float64) + law["V_A"] * (law["r_surf"] - r))
+
+
 class Operators:
     """Assembled FP64 blocks on one level (matrix entries are the definition, the
-    matrix-vector product is the operator application)."""
+    matrix-vector product is the operator application).  With `law` and the level's P2
+    temperature T_p2, A takes the viscosity at the quadrature points, eta(x_q, T(x_q)) with
+    T(x_q) the P2 interpolant (Sec. 5.2.2, levels up to l_eta); M_{1/eta} keeps eta_p1."""
 
-    def __init__(self, level, eta_p1, dlnrho_table=(0.0,), chunk=4096):
+    def __init__(self, level, eta_p1, dlnrho_table=(0.0,), chunk=4096, law=None, T_p2=None):
         mesh = level.mesh
         nu, npp = 3 * level.n_p2, level.n_p1
         E = level.tet_p2.shape[0]
@@ -149,7 +166,11 @@ class Operators:
             ev = eta_p1[level.tet_p1[sl]]
             vd = velocity_dofs(level, sl)
             pd = level.tet_p1[sl]
-            As.append(assemble(vd, vd, element_A(geo, ev), (nu, nu)))
+            if law is not None:
+                Tq = np.asarray(T_p2, dtype=np.float64)[level.tet_p2[sl]] @ geo.phi.T          # (E,Q)
+                As.append(assemble(vd, vd, element_A_q(geo, viscosity_law(geo.x, Tq, law)), (nu, nu)))
+            else:
+                As.append(assemble(vd, vd, element_A(geo, ev), (nu, nu)))
             Bs.append(assemble(pd, vd, element_B(geo), (npp, nu)))
             Cs.append(assemble(pd, vd, element_C(geo, mesh, dlnrho_table), (npp, nu)))
             etaq = ev @ QUAD_BARY.T

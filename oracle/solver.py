@@ -17,6 +17,9 @@ Paper passages followed (arxiv 2506.04157):
   * Table parametertable: the default parameters.
   * Sec. 5.2.1, Eqs. (InexactUzawaStep1), (AdjointInexactUzawaStep1): the inexact and
     adjoint inexact Uzawa steps (the alternatives to the symmetric step), each from (0, 0).
+  * Sec. 5.2.2 and Sec. 7.2, Eq. (ViscosityDef): with a temperature-dependent viscosity law,
+    eta at the vertices of the levels above l_eta and at the quadrature points (from the
+    P2 temperature) on the levels up to l_eta.
   * Sec. 5.2.3, Eq. (schurMass): S_M^-1 = M_{1/eta}^-1 solved by CG to tol_invMass; the
     diag(A)-BFBT approximation (C = D = diag(A) in the BFBT formula of Sec. 5.2.3), whose
     B diag(A)^-1 B^T solve is structured like the V-cycle BFBT's.
@@ -42,7 +45,7 @@ import scipy.sparse as sp
 
 from .mesh import MacroMesh, Level, LOCAL_EDGES, kuhn_to_bary, micro_tets_kuhn
 from .fem import (Operators, Constraints, ConstrainedOperators, project_mean_zero,
-                  p2_values, QUAD_BARY)
+                  p2_values, QUAD_BARY, viscosity_law)
 
 DEFAULTS = dict(sigma=1.0, omega=0.3, tol_A=1e-2, m_A=3, deg_A=2, tol_VBFBT=1e-1,
                 tol_invMass=1e-10, m_V=1, deg_V=1, tol_coarse=1e-2,
@@ -169,7 +172,7 @@ class Hierarchy:
     """Per-level constrained operators, diagonals, transfers and Chebyshev bounds."""
 
     def __init__(self, mesh, l_max, eta_fine, dlnrho_table=(0.0,), bc=(0, 1), l_min=1,
-                 bounds=None, with_C=True):
+                 bounds=None, with_C=True, law=None, T_fine=None, l_eta=-1):
         self.mesh, self.l_min, self.l_max = mesh, l_min, l_max
         self.levels, self.ops, self.cons, self.co, self.diag = {}, {}, {}, {}, {}
         Lf = Level(mesh, l_max)
@@ -177,12 +180,25 @@ class Hierarchy:
         for l in range(l_min, l_max):
             self.levels[l] = Level(mesh, l)
         # coarse-level viscosity by P1 full weighting (reading: injection of a rough,
-        # high-contrast field makes the rediscretised coarse operators unrepresentative)
-        self.etas = viscosity_hierarchy(mesh, self.levels, eta_fine)
+        # high-contrast field makes the rediscretised coarse operators unrepresentative).
+        # With a temperature-dependent law (Sec. 5.2.2): eta(x_V, T(x_V)) at the vertices of
+        # every level above l_eta, eta(x_q, T(x_q)) at the quadrature points up to l_eta.
+        self.T = {}
+        if law is not None:
+            self.etas = {}
+            for l in range(l_min, l_max + 1):
+                T2, T1 = temperature_on_level(Lf, self.levels[l], T_fine)
+                self.T[l] = T2
+                self.etas[l] = viscosity_law(self.levels[l].p1_x, T1, law)
+        else:
+            self.etas = viscosity_hierarchy(mesh, self.levels, eta_fine)
         for l in range(l_min, l_max + 1):
             L = self.levels[l]
             eta = self.etas[l]
-            ops = Operators(L, eta, dlnrho_table)
+            if law is not None and l <= l_eta:
+                ops = Operators(L, eta, dlnrho_table, law=law, T_p2=self.T[l])
+            else:
+                ops = Operators(L, eta, dlnrho_table)
             cons = Constraints(L, *bc)
             self.ops[l], self.cons[l] = ops, cons
             self.co[l] = ConstrainedOperators(ops, cons, with_C=with_C)
@@ -229,6 +245,18 @@ class Hierarchy:
         x = x + cons.P0(P @ ec)
         x = chebyshev(Aop, Dinv, cons.P0, x, b, steps, degree, lo, hi)
         return x
+
+
+def temperature_on_level(Lfine, Lcoarse, T_fine):
+    """A P2 field of the finest level on a coarser level: every P2 node and P1 vertex of the
+    coarse level is a P2 node of the finest level (nested lattices); matched by position."""
+    from scipy.spatial import cKDTree
+    tree = cKDTree(Lfine.p2_x)
+    d2, i2 = tree.query(Lcoarse.p2_x)
+    d1, i1 = tree.query(Lcoarse.p1_x)
+    assert d2.max() < 1e-10 and d1.max() < 1e-10
+    T_fine = np.asarray(T_fine, dtype=np.float64)
+    return T_fine[i2], T_fine[i1]
 
 
 def restrict_viscosity(Lfine, Lcoarse, eta_fine):

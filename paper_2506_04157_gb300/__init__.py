@@ -95,6 +95,8 @@ _SIGS = {
     "mfs_adjoint_solve": ([_vp, ctypes.POINTER(SolveOpts), _vp, _vp, _vp, _vp, ctypes.POINTER(SolveStats)], _i),
     "mfs_grad_log_eta": ([_vp, _vp, _vp, _vp], _i),
     "mfs_autotune": ([_vp, ctypes.c_char_p], _i),
+    "mfs_set_viscosity_law": ([_vp, _d, _d, _i, _vp, _i], _i),
+    "mfs_set_temperature": ([_vp, _vp], _i),
     "mfs_rhs_buoyancy": ([_vp, _vp, _d, _vp], _i),
     "mfs_get_tuning": ([_vp, _i, ctypes.POINTER(_i)], _i),
     "mfs_batch_create": ([_vp, _i, _vp, ctypes.POINTER(_vp)], _i),
@@ -303,6 +305,19 @@ class Problem:
         nu, _ = self._sizes(level)
         _need(f, nu, None, "f"); _need(u, nu, f.dtype, "u")
         _check(lib().mfs_vcycle(self.handle, level, _prec_of(f), steps, degree, _ptr(f), _ptr(u)))
+
+    def set_viscosity_law(self, log10_base, E_A=4.610, V_A=2.996, l_eta=-1):
+        """Frank-Kamenetskii viscosity law; quadrature-point viscosity on levels <= l_eta."""
+        tab = np.ascontiguousarray(np.asarray(log10_base, dtype=np.float64).ravel())
+        _check(lib().mfs_set_viscosity_law(self.handle, float(E_A), float(V_A), tab.size,
+                                            tab.ctypes.data_as(ctypes.c_void_p), int(l_eta)))
+
+    def set_temperature(self, T_p2):
+        """Finest-level P2 temperature (FP64 device tensor): sets the viscosity from the law."""
+        import torch
+        nu, _ = self._sizes(self.mesh.l_max)
+        _need(T_p2, nu // 3, torch.float64, "T_p2")
+        _check(lib().mfs_set_temperature(self.handle, _ptr(T_p2)))
 
     def rhs_buoyancy(self, T_p2, f, scale=1.0):
         """f = scale * int rho T (x/|x|) . phi (FP64 device tensors: T [n_p2], f [3 n_p2])."""

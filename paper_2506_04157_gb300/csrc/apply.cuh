@@ -65,6 +65,11 @@ struct ApplyParams {
   int n;                  // cubes per macro edge
   int n_dlnrho;
   T r_cmb, inv_dr;        // table grid: s = (r - r_cmb) * inv_dr * (n_dlnrho - 1)
+  // OP_ETAQ: eta(x, T) = 10^lbase(|x|) exp(-E_A T + V_A (r_surf - |x|)) at the qps
+  const T* temp;          // [n_p2] P2 temperature of this level
+  const T* lbase;         // log10 eta_base on a uniform radial grid over [r_cmb, r_surf]
+  int n_lbase;
+  T E_A, V_A, r_surf;
   int constrained;
   int bc_surface, bc_cmb;
 };
@@ -166,8 +171,29 @@ static __constant__ SlotTable c_slots = {{
 template <typename T, int OP>
 constexpr size_t sweep_smem_bytes() {
   return sizeof(T) * ((((OP & (OP_A | OP_B)) != 0) ? 3 * NSLOT2 : 0) + (((OP & (OP_A | OP_BT)) != 0) ? 3 * NSLOT2 : 0) +
-                      NSLOT1 + (((OP & OP_BT) != 0) ? NSLOT1 : 0) + (((OP & OP_B) != 0) ? NSLOT1 : 0)) +
+                      NSLOT1 + (((OP & OP_BT) != 0) ? NSLOT1 : 0) + (((OP & OP_B) != 0) ? NSLOT1 : 0) +
+                      (((OP & OP_ETAQ) != 0) ? NSLOT2 : 0)) +
          sizeof(int) * (NSLOT2 + NSLOT1);
+}
+
+template <typename T>
+__device__ __forceinline__ T exp_t(T x);
+template <>
+__device__ __forceinline__ float exp_t<float>(float x) { return expf(x); }
+template <>
+__device__ __forceinline__ double exp_t<double>(double x) { return exp(x); }
+
+// linear interpolation of a table on a uniform grid over [r0, r1] (clamped)
+template <typename T>
+__device__ __forceinline__ T radial_table(const T* tab, int n, T r, T r0, T r1) {
+  if (n <= 1) return tab[0];
+  const T top = T(n - 1);
+  T s = (r - r0) / (r1 - r0) * top;
+  s = s < T(0) ? T(0) : (s > top ? top : s);
+  int i = (int)s;
+  i = i > n - 2 ? n - 2 : i;
+  const T f = s - T(i);
+  return (T(1) - f) * tab[i] + f * tab[i + 1];
 }
 
 template <typename T, int OP, bool BLEND>
@@ -178,15 +204,18 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
   constexpr bool OUT_P = (OP & OP_B) != 0;
   constexpr bool HAS_CT = (OP & OP_CT) != 0;
   constexpr bool HAS_BC = (OP & OP_BC) != 0;
+  constexpr bool ETAQ = (OP & OP_ETAQ) != 0;
+  static_assert(!ETAQ || OP == (OP_A | OP_ETAQ), "the quadrature-point viscosity serves A alone");
 
-  // dynamic shared memory, layout of sweep_smem_bytes(): us, ys, eta_s, p_s, yp_s, gid2, gid1
+  // dynamic shared memory, layout of sweep_smem_bytes(): us, ys, eta_s, p_s, yp_s, ts, gid2, gid1
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* us = reinterpret_cast<T*>(smem_raw);
   T* ys = us + (HAS_U ? 3 * NSLOT2 : 0);
   T* eta_s = ys + (OUT_U ? 3 * NSLOT2 : 0);
   T* p_s = eta_s + NSLOT1;
   T* yp_s = p_s + (HAS_P ? NSLOT1 : 0);
-  int* gid2 = reinterpret_cast<int*>(yp_s + (OUT_P ? NSLOT1 : 0));
+  T* ts = yp_s + (OUT_P ? NSLOT1 : 0);   // ETAQ: P2 temperature of the tile
+  int* gid2 = reinterpret_cast<int*>(ts + (ETAQ ? NSLOT2 : 0));
   int* gid1 = gid2 + NSLOT2;
   __shared__ T cM[9], cJn[9], cv0[3], cnh[3];
   __shared__ T qpo[6][4][3];      // physical offset of qp q of type pm from the cube corner
@@ -222,6 +251,8 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
     qpo[pm][q][r] = o / T(n);
   }
   if (tid < 64 && tid < P.n_dlnrho) dtab[tid] = P.dlnrho[tid];
+  __shared__ T lbt[64];   // ETAQ: ln eta_base table (first 64 entries)
+  if (ETAQ && tid < 64 && tid < P.n_lbase) lbt[tid] = T(2.302585092994045684) * P.lbase[tid];
 
   // ---- stage the P2 node block (u, with the input-side projections) ----
   // All table entries of this thread first, then all node values: independent loads in flight.
@@ -242,6 +273,13 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
       uv[k][0] = __ldg(P.u + id);
       uv[k][1] = __ldg(P.u + P.n_p2 + id);
       uv[k][2] = __ldg(P.u + 2 * P.n_p2 + id);
+    }
+  }
+  if (ETAQ) {
+#pragma unroll
+    for (int k = 0; k < kG; ++k) {
+      const int s = tid + k * kSweepThreads;
+      if (s < NSLOT2) ts[s] = codes[k] >= 0 ? __ldg(P.temp + (codes[k] & 0x1fffffff)) : T(0);
     }
   }
 #pragma unroll
@@ -329,6 +367,15 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
       if (HAS_P) p_v[a] = p_s[SLOT(a)];
     }
     const T eta_sum = eta_v[0] + eta_v[1] + eta_v[2] + eta_v[3];
+    // ETAQ: sums of the P2 temperature over the tet's vertices and edges (the P2 value at a
+    // qp is fvb Tv + feo Te + (fva - fvb) T_q + (fei - feo) (edges at q))
+    T Tv = T(0), Te = T(0);
+    if (ETAQ) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) Tv += ts[SLOT(a)];
+#pragma unroll
+      for (int e = 4; e < 10; ++e) Te += ts[SLOT(e)];
+    }
     T p_sum = T(0);
     if (HAS_P) p_sum = p_v[0] + p_v[1] + p_v[2] + p_v[3];
 
@@ -468,7 +515,21 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
         // stress (scaled): sigma = coefA eps(G') - coefB p_q I
         T S[3][3];
         if (OP & OP_A) {
-          const T coefA = T(2) * (QB * eta_sum + (QA - QB) * eta_v[q]) * C0 * hr;
+          T etaq;
+          if (ETAQ) {
+            T Tq = fvb * Tv + feo * Te + (fva - fvb) * ts[SLOT(q)];
+            T te = T(0);
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+              if (a != q) te += ts[SLOT(wnode(a, q))];
+            Tq += (fei - feo) * te;
+            const T rad = BLEND ? h * dinv : r2 * rinv;
+            etaq = exp_t<T>(radial_table<T>(lbt, P.n_lbase, rad, P.r_cmb, P.r_surf) - P.E_A * Tq +
+                            P.V_A * (P.r_surf - rad));
+          } else {
+            etaq = QB * eta_sum + (QA - QB) * eta_v[q];
+          }
+          const T coefA = T(2) * etaq * C0 * hr;
           const T t3 = trace * T(1.0 / 3.0);
           S[0][0] = coefA * (Gp[0][0] - t3);
           S[1][1] = coefA * (Gp[1][1] - t3);

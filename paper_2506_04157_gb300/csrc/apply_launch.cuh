@@ -11,12 +11,16 @@ struct PrecData;
 template <>
 struct PrecData<double> {
   static const double* eta(mfs_problem* P, int l) { return P->eta64[l]; }
+  static const double* temp(mfs_problem* P, int l) { return P->temp64[l]; }
+  static const double* lbase(mfs_problem* P) { return P->d_lbase64; }
   static const MacroGeom<double>* geom(mfs_mesh* M) { return M->d_geom64; }
   static const double* dlnrho(mfs_problem* P) { return P->d_dlnrho64; }
 };
 template <>
 struct PrecData<float> {
   static const float* eta(mfs_problem* P, int l) { return P->eta32[l]; }
+  static const float* temp(mfs_problem* P, int l) { return P->temp32[l]; }
+  static const float* lbase(mfs_problem* P) { return P->d_lbase32; }
   static const MacroGeom<float>* geom(mfs_mesh* M) { return M->d_geom32; }
   static const float* dlnrho(mfs_problem* P) { return P->d_dlnrho32; }
 };
@@ -64,7 +68,7 @@ ApplyParams<T> fill_params(mfs_problem* P, int lvl, int constrained, const T* u,
                            const T* psum) {
   mfs_mesh* M = P->mesh;
   const LevelData& L = M->levels[lvl];
-  ApplyParams<T> prm;
+  ApplyParams<T> prm{};
   prm.u = u;
   prm.p = p;
   prm.yu = yu;
@@ -143,7 +147,7 @@ mfs_status launch_apply(mfs_problem* P, int lvl, int op, int constrained, int wi
   mfs_mesh* M = P->mesh;
   const LevelData& L = M->levels[lvl];
   cudaStream_t s = M->ctx->stream;
-  ApplyParams<T> prm;
+  ApplyParams<T> prm{};
   prm.u = u;
   prm.p = p;
   prm.yu = yu;
@@ -166,12 +170,28 @@ mfs_status launch_apply(mfs_problem* P, int lvl, int op, int constrained, int wi
   prm.constrained = constrained;
   prm.bc_surface = P->bc_surface;
   prm.bc_cmb = P->bc_cmb;
+  if (lvl <= P->l_eta && (op & OP_A)) {
+    // quadrature-point viscosity on this level
+    if (op != OP_A) {
+      set_error("level %d evaluates the viscosity at quadrature points: only A alone is available there (l_eta = %d)",
+                lvl, P->l_eta);
+      return MFS_EINVAL;
+    }
+    op = OP_A | OP_ETAQ;
+    prm.temp = PrecData<T>::temp(P, lvl);
+    prm.lbase = PrecData<T>::lbase(P);
+    prm.n_lbase = (int)P->lbase_host.size();
+    prm.E_A = (T)P->E_A;
+    prm.V_A = (T)P->V_A;
+    prm.r_surf = (T)M->host.r_surf;
+  }
   if (zero_out && (op & (OP_A | OP_BT))) MFS_CUDA(cudaMemsetAsync(yu, 0, sizeof(T) * 3 * (size_t)L.nb2.total, s));
   if (zero_out && (op & OP_B)) MFS_CUDA(cudaMemsetAsync(yp, 0, sizeof(T) * (size_t)L.nb1.total, s));
   if ((op & OP_B) && withc_b) op |= OP_BC;
   const int bl = M->host.blending;
   switch (op) {
     case OP_A: MFS_TRY((run_sweep<T, OP_A>(prm, L.n_tiles, bl, M->ctx, L.variant))); break;
+    case OP_A | OP_ETAQ: MFS_TRY((run_sweep<T, OP_A | OP_ETAQ>(prm, L.n_tiles, bl, M->ctx, 0))); break;
     case OP_BT: MFS_TRY((run_sweep<T, OP_BT>(prm, L.n_tiles, bl, M->ctx, L.variant))); break;
     case OP_BT | OP_CT: MFS_TRY((run_sweep<T, OP_BT | OP_CT>(prm, L.n_tiles, bl, M->ctx, L.variant))); break;
     case OP_B: MFS_TRY((run_sweep<T, OP_B>(prm, L.n_tiles, bl, M->ctx, L.variant))); break;

@@ -382,6 +382,10 @@ mfs_status mfs_problem_destroy(mfs_problem* P) {
   problem_release_solver(P);
   for (auto p : P->eta64) cudaFree(p);
   for (auto p : P->eta32) cudaFree(p);
+  for (auto p : P->temp64) cudaFree(p);
+  for (auto p : P->temp32) cudaFree(p);
+  cudaFree(P->d_lbase64);
+  cudaFree(P->d_lbase32);
   cudaFree(P->d_dlnrho64);
   cudaFree(P->d_dlnrho32);
   cudaFree(P->d_red64);
@@ -401,6 +405,7 @@ mfs_status mfs_set_viscosity(mfs_problem* P, const double* eta, int is_log) {
   cudaStream_t s = M->ctx->stream;
   const int L = M->l_max;
   const size_t np1 = M->levels[L].nb1.total;
+  P->l_eta = -1;   // P1 viscosity on every level (a viscosity law set earlier no longer applies)
   MFS_CUDA(cudaMemcpyAsync(P->eta64[L], eta, sizeof(double) * np1, cudaMemcpyDeviceToDevice, s));
   if (is_log) MFS_TRY(exp_inplace(P->eta64[L], (int64_t)np1, s));
   // coarse levels: P1 full weighting of the next finer level (arithmetic average of the
@@ -412,6 +417,101 @@ mfs_status mfs_set_viscosity(mfs_problem* P, const double* eta, int is_log) {
   return MFS_OK;
 }
 
+
+mfs_status mfs_set_viscosity_law(mfs_problem* P, double E_A, double V_A, int n, const double* log10_base, int l_eta) {
+  if (P) P->version++;
+  MFS_TRY(check_problem(P, 0, false));
+  const int L = P->mesh->l_max;
+  if (n < 1 || n > 64 || !log10_base || l_eta < -1 || l_eta >= L) {
+    set_error("viscosity law: 1 <= n <= 64 table entries and -1 <= l_eta < l_max = %d required", L);
+    return MFS_EINVAL;
+  }
+  cudaStream_t s = P->mesh->ctx->stream;
+  MFS_CUDA(cudaStreamSynchronize(s));
+  cudaFree(P->d_lbase64);
+  cudaFree(P->d_lbase32);
+  P->d_lbase64 = nullptr;
+  P->d_lbase32 = nullptr;
+  P->lbase_host.assign(log10_base, log10_base + n);
+  std::vector<float> t32(log10_base, log10_base + n);
+  MFS_TRY(upload(&P->d_lbase64, log10_base, (size_t)n, s));
+  MFS_TRY(upload(&P->d_lbase32, t32.data(), (size_t)n, s));
+  P->E_A = E_A;
+  P->V_A = V_A;
+  P->l_eta = -1;   // takes effect with mfs_set_temperature
+  P->law_l_eta = l_eta;
+  MFS_CUDA(cudaStreamSynchronize(s));
+  return MFS_OK;
+}
+
+mfs_status mfs_set_temperature(mfs_problem* P, const double* T_p2) {
+  if (P) P->version++;
+  MFS_TRY(check_problem(P, 0, false));
+  if (!T_p2 || P->lbase_host.empty()) {
+    set_error(T_p2 ? "no viscosity law (call mfs_set_viscosity_law first)" : "null temperature");
+    return MFS_EINVAL;
+  }
+  mfs_mesh* M = P->mesh;
+  cudaStream_t s = M->ctx->stream;
+  const int L = M->l_max;
+  const int NF = 2 << L;   // finest P2 lattice
+  const Numbering nbf = make_numbering(NF);
+  std::vector<double> Tf(nbf.total);
+  MFS_CUDA(cudaMemcpyAsync(Tf.data(), T_p2, sizeof(double) * Tf.size(), cudaMemcpyDeviceToHost, s));
+  MFS_CUDA(cudaStreamSynchronize(s));
+  const int nt = (int)P->lbase_host.size();
+  const double r0 = M->host.r_cmb, r1 = M->host.r_surf;
+  auto law = [&](const double x[3], double T) {   // Eq. (ViscosityDef)
+    const double r = std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+    double lb = P->lbase_host[0];
+    if (nt > 1) {
+      double t = (r - r0) / (r1 - r0) * (nt - 1);
+      t = t < 0 ? 0 : (t > nt - 1 ? nt - 1 : t);
+      int i = (int)t;
+      i = i > nt - 2 ? nt - 2 : i;
+      lb = (1 - (t - i)) * P->lbase_host[i] + (t - i) * P->lbase_host[i + 1];
+    }
+    return std::pow(10.0, lb) * std::exp(-P->E_A * T + P->V_A * (r1 - r));
+  };
+  const int l_eta = P->law_l_eta;
+  if ((int)P->temp64.size() < L + 1) {
+    P->temp64.resize(L + 1, nullptr);
+    P->temp32.resize(L + 1, nullptr);
+  }
+  for (int l = 0; l <= L; ++l) {
+    // P1 viscosity at the vertices: vertex i of level l is the finest P2 node i * NF / 2^l
+    const int N1 = 1 << l, sc1 = NF / N1;
+    std::vector<double> eta(M->levels[l].nb1.total);
+    for_each_point(M, N1, [&](int m, const int* i, int id) {
+      double xs[3], x[3];
+      M->host.straight_point(m, i, N1, xs);
+      if (M->host.blending) M->host.blend_point(m, xs, x);
+      else for (int r = 0; r < 3; ++r) x[r] = xs[r];
+      const int fi = lattice_id(M->host.topo[m], nbf, m, i[0] * sc1, i[1] * sc1, i[2] * sc1, i[3] * sc1);
+      eta[id] = law(x, Tf[fi]);
+    });
+    MFS_CUDA(cudaMemcpyAsync(P->eta64[l], eta.data(), sizeof(double) * eta.size(), cudaMemcpyHostToDevice, s));
+    MFS_TRY(convert_f64_f32(P->eta64[l], P->eta32[l], (int64_t)eta.size(), s));
+    if (l <= l_eta) {   // P2 temperature of the level for the quadrature-point viscosity
+      const int N2 = 2 << l, sc2 = NF / N2;
+      const int64_t n2 = M->levels[l].nb2.total;
+      std::vector<double> T2(n2);
+      for_each_point(M, N2, [&](int m, const int* i, int id) {
+        T2[id] = Tf[lattice_id(M->host.topo[m], nbf, m, i[0] * sc2, i[1] * sc2, i[2] * sc2, i[3] * sc2)];
+      });
+      if (!P->temp64[l]) {
+        MFS_CUDA(cudaMalloc((void**)&P->temp64[l], sizeof(double) * n2));
+        MFS_CUDA(cudaMalloc((void**)&P->temp32[l], sizeof(float) * n2));
+      }
+      MFS_CUDA(cudaMemcpyAsync(P->temp64[l], T2.data(), sizeof(double) * n2, cudaMemcpyHostToDevice, s));
+      MFS_TRY(convert_f64_f32(P->temp64[l], P->temp32[l], n2, s));
+    }
+    MFS_CUDA(cudaStreamSynchronize(s));   // the host buffers go out of scope
+  }
+  P->l_eta = l_eta;
+  P->has_eta = true;
+  return MFS_OK;
+}
 
 mfs_status mfs_set_density(mfs_problem* P, int n, const double* tab) {
   if (P) P->version++;

@@ -121,6 +121,16 @@ struct mfs_problem {
   double* d_red64 = nullptr;    // [kRedSlots]
   float* d_red32 = nullptr;
   mfs::MG* mg = nullptr;        // multigrid hierarchy and solver workspaces
+  // temperature-dependent viscosity law (mfs_set_viscosity_law / mfs_set_temperature):
+  // levels l <= l_eta evaluate eta at the quadrature points from temp64/32[l]
+  int l_eta = -1;                  // in effect (set with the temperature)
+  int law_l_eta = -1;              // requested by mfs_set_viscosity_law
+  double E_A = 0.0, V_A = 0.0;
+  std::vector<double> lbase_host;  // log10 eta_base table
+  double* d_lbase64 = nullptr;
+  float* d_lbase32 = nullptr;
+  std::vector<double*> temp64;  // per level, P2 temperature (levels <= l_eta)
+  std::vector<float*> temp32;
   int version = 0;              // bumped by every coefficient change (captured graphs go stale)
 };
 

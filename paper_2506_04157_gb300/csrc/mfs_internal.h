@@ -74,7 +74,9 @@ struct Tile {
 
 // Operator sets of the fused micro-tet sweep; OP_CT: the B^T part is (B + C)^T;
 // OP_BC: the B part is (B + C).
-enum { OP_A = 1, OP_BT = 2, OP_B = 4, OP_CT = 8, OP_BC = 16 };
+// OP_ETAQ (with OP_A alone): the viscosity at the quadrature points from the level's P2
+// temperature and the viscosity law (levels up to l_eta) instead of the P1 nodal values.
+enum { OP_A = 1, OP_BT = 2, OP_B = 4, OP_CT = 8, OP_BC = 16, OP_ETAQ = 32 };
 
 // Boundary condition types (match include/mfs.h).
 enum { BC_DIRICHLET = 0, BC_FREESLIP = 1 };

@@ -382,11 +382,13 @@ __device__ __forceinline__ void qp_geometry(const MacroGeom<T>& G, int n, int p0
   }
 }
 
-// diag(A) (raw, no projection): sum over tets and qps of 2 eta W (|g|^2/2 + g_c^2/6)
-template <typename T, bool BLEND>
+// diag(A) (raw, no projection): sum over tets and qps of 2 eta W (|g|^2/2 + g_c^2/6);
+// ETAQ: eta from the viscosity law at the quadrature points (levels up to l_eta)
+template <typename T, bool BLEND, bool ETAQ>
 __global__ void __launch_bounds__(128) k_diag_sweep(const ApplyParams<T> P, T* __restrict__ diag) {
   __shared__ T ds[3 * NSLOT2];
   __shared__ T eta_s[NSLOT1];
+  __shared__ T tsm[ETAQ ? NSLOT2 : 1];   // ETAQ: P2 temperature of the tile
   const int m = blockIdx.y, tidx = blockIdx.x;
   const size_t lin = (size_t)m * gridDim.x + tidx;
   const Tile tile = P.tiles[tidx];
@@ -397,6 +399,11 @@ __global__ void __launch_bounds__(128) k_diag_sweep(const ApplyParams<T> P, T* _
     const int id = P.ids1[lin * NSLOT1 + s];
     eta_s[s] = id >= 0 ? P.eta[id] : T(1);
   }
+  if (ETAQ)
+    for (int s = threadIdx.x; s < NSLOT2; s += blockDim.x) {
+      const int code = P.ids2[lin * NSLOT2 + s];
+      tsm[s] = code >= 0 ? P.temp[code & 0x1fffffff] : T(0);
+    }
   __syncthreads();
   const double QA = MFS_QA, QB = MFS_QB;
   const T C0 = G.absdet / (T(24) * T(n) * T(n) * T(n));
@@ -427,7 +434,22 @@ __global__ void __launch_bounds__(128) k_diag_sweep(const ApplyParams<T> P, T* _
       T K[3][3], hr, rinv, x[3];
       qp_geometry<T, BLEND>(G, n, p0, p1, p2, q, qx, qy, qz, K, hr, rinv, x);
       const double lam[4] = {q == 0 ? QA : QB, q == 1 ? QA : QB, q == 2 ? QA : QB, q == 3 ? QA : QB};
-      const T etaq = T(lam[0]) * eta_v[0] + T(lam[1]) * eta_v[1] + T(lam[2]) * eta_v[2] + T(lam[3]) * eta_v[3];
+      T etaq;
+      if (ETAQ) {   // eta(x_q, T(x_q)), T the P2 interpolant
+        T Tq = T(0);
+        for (int a = 0; a < 4; ++a) Tq += T(lam[a] * (2 * lam[a] - 1)) * tsm[slot[a]];
+        for (int e = 0; e < 6; ++e) {
+          const int i0 = e < 3 ? 0 : (e < 5 ? 1 : 2);
+          const int i1 = e < 3 ? e + 1 : (e < 5 ? e - 1 : 3);
+          Tq += T(4 * lam[i0] * lam[i1]) * tsm[slot[4 + e]];
+        }
+        const T h = x[0] * G.nh[0] + x[1] * G.nh[1] + x[2] * G.nh[2];
+        const T rad = BLEND ? h / G.delta : T(1) / rinv;
+        etaq = exp_t<T>(T(2.302585092994045684) * radial_table<T>(P.lbase, P.n_lbase, rad, P.r_cmb, P.r_surf) -
+                        P.E_A * Tq + P.V_A * (P.r_surf - rad));
+      } else {
+        etaq = T(lam[0]) * eta_v[0] + T(lam[1]) * eta_v[1] + T(lam[2]) * eta_v[2] + T(lam[3]) * eta_v[3];
+      }
       const T coefA = T(2) * etaq * C0 * hr;
       for (int a = 0; a < 10; ++a) {
         double gl[3];
@@ -601,6 +623,15 @@ static ApplyParams<T> sweep_params(mfs_problem* P, int lvl) {
   prm.n_p2 = L.nb2.total;
   prm.n_p1 = L.nb1.total;
   prm.n = L.n;
+  prm.r_cmb = (T)M->host.r_cmb;
+  if (lvl <= P->l_eta) {
+    prm.temp = lvl_temp<T>(P, lvl);
+    prm.lbase = lvl_lbase<T>(P);
+    prm.n_lbase = (int)P->lbase_host.size();
+    prm.E_A = (T)P->E_A;
+    prm.V_A = (T)P->V_A;
+    prm.r_surf = (T)M->host.r_surf;
+  }
   return prm;
 }
 
@@ -612,8 +643,13 @@ mfs_status diag_A(mfs_problem* P, int lvl, const BoundaryList& B, T* diag) {
   MFS_CUDA(cudaMemsetAsync(diag, 0, sizeof(T) * 3 * (size_t)L.nb2.total, s));
   dim3 grid(L.n_tiles, kMacroCells);
   ApplyParams<T> prm = sweep_params<T>(P, lvl);
-  if (M->host.blending) k_diag_sweep<T, true><<<grid, 128, 0, s>>>(prm, diag);
-  else k_diag_sweep<T, false><<<grid, 128, 0, s>>>(prm, diag);
+  if (lvl <= P->l_eta) {
+    if (M->host.blending) k_diag_sweep<T, true, true><<<grid, 128, 0, s>>>(prm, diag);
+    else k_diag_sweep<T, false, true><<<grid, 128, 0, s>>>(prm, diag);
+  } else {
+    if (M->host.blending) k_diag_sweep<T, true, false><<<grid, 128, 0, s>>>(prm, diag);
+    else k_diag_sweep<T, false, false><<<grid, 128, 0, s>>>(prm, diag);
+  }
   if (B.nb) k_diag_dirichlet<T><<<blocks_for(B.nb), 256, 0, s>>>(B.nb, B.ids, B.kind, L.nb2.total, diag);
   MFS_CUDA(cudaGetLastError());
   return MFS_OK;

@@ -94,6 +94,18 @@ inline const double* lvl_eta<double>(mfs_problem* P, int l) { return P->eta64[l]
 template <>
 inline const float* lvl_eta<float>(mfs_problem* P, int l) { return P->eta32[l]; }
 template <typename T>
+inline const T* lvl_temp(mfs_problem* P, int l);
+template <>
+inline const double* lvl_temp<double>(mfs_problem* P, int l) { return P->temp64[l]; }
+template <>
+inline const float* lvl_temp<float>(mfs_problem* P, int l) { return P->temp32[l]; }
+template <typename T>
+inline const T* lvl_lbase(mfs_problem* P);
+template <>
+inline const double* lvl_lbase<double>(mfs_problem* P) { return P->d_lbase64; }
+template <>
+inline const float* lvl_lbase<float>(mfs_problem* P) { return P->d_lbase32; }
+template <typename T>
 inline const MacroGeom<T>* lvl_geom(mfs_mesh* M);
 template <>
 inline const MacroGeom<double>* lvl_geom<double>(mfs_mesh* M) { return M->d_geom64; }

@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 from oracle.mesh import MacroMesh, Level, CLASS_INNER
+import workloads as W
 from oracle.fem import (Geometry, Operators, element_A, element_B, Constraints,
                         ConstrainedOperators, project_mean_zero)
 
@@ -249,3 +250,42 @@ def test_rho_profile_piecewise_against_adaptive_quadrature():
         val, _ = quad(lambda s: float(interp_table(tab, np.array([s]), r0, R)[0]), r, R,
                       points=[x for x in nodes if r < x < R], epsabs=1e-14, epsrel=1e-14)
         assert abs(rho_profile(tab, np.array([r]), r0, R)[0] - np.exp(-val)) <= 1e-13
+
+
+def _law(E_A=4.61, V_A=2.996, table=(1.0, 0.0, -1.0, 2.0)):
+    return dict(E_A=E_A, V_A=V_A, r_cmb=0.5, r_surf=1.0, log10_base=np.array(table, dtype=float))
+
+
+def test_quadrature_viscosity_temperature_scaling():
+    """A is linear in eta: with a uniform temperature tau, A(T = tau) = exp(-E_A tau) A(T = 0)."""
+    from oracle.fem import Operators
+    L = Level(MacroMesh(), 1)
+    law = _law()
+    eta1 = np.ones(L.n_p1)
+    A0 = Operators(L, eta1, law=law, T_p2=np.zeros(L.n_p2)).A
+    A1 = Operators(L, eta1, law=law, T_p2=np.full(L.n_p2, 0.37)).A
+    assert abs(A1 - np.exp(-4.61 * 0.37) * A0).max() <= 1e-12 * abs(A1).max()
+
+
+def test_quadrature_viscosity_activation_volume():
+    """exp(V_A (r_surf - r)) equals a base profile whose log10 is linear in r (a two-entry
+    table represents it exactly): both laws give the same A."""
+    from oracle.fem import Operators
+    L = Level(MacroMesh(), 1)
+    T = W.temperature_blobs(L.p2_x, 5)
+    v = 2.996
+    with_va = _law(E_A=1.3, V_A=v, table=(0.2, 0.2))
+    folded = _law(E_A=1.3, V_A=0.0, table=(0.2 + v * 0.5 / np.log(10.0), 0.2))
+    A1 = Operators(L, np.ones(L.n_p1), law=with_va, T_p2=T).A
+    A2 = Operators(L, np.ones(L.n_p1), law=folded, T_p2=T).A
+    assert abs(A1 - A2).max() <= 1e-12 * abs(A1).max()
+
+
+def test_temperature_injection_exact_for_linear_fields():
+    from oracle.solver import temperature_on_level
+    mesh = MacroMesh()
+    Lf, Lc = Level(mesh, 3), Level(mesh, 1)
+    a = np.array([0.3, -1.2, 0.7])
+    T2, T1 = temperature_on_level(Lf, Lc, Lf.p2_x @ a)
+    assert np.allclose(T2, Lc.p2_x @ a, rtol=0, atol=1e-13)
+    assert np.allclose(T1, Lc.p1_x @ a, rtol=0, atol=1e-13)
