@@ -77,6 +77,7 @@ class Geometry:
         Jinv = np.linalg.inv(J)
         gref = p2_ref_grads(QUAD_BARY)                                                     # (Q,10,3)
         self.grad = np.einsum("qad,eqdi->eqai", gref, Jinv)                                # (E,Q,10,3)
+        self.grad1 = np.einsum("ad,eqdi->eqai", _GRAD_LAMBDA, Jinv)                         # (E,Q,4,3) P1
         self.W = QUAD_W[None, :] * self.detJ                                               # (E,Q)
         self.x = mesh.blend(xq, prism[:, None])                                            # physical qp
         self.phi = p2_values(QUAD_BARY)                                                    # (Q,10)

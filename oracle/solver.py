@@ -23,6 +23,8 @@ Paper passages followed (arxiv 2506.04157):
   * Sec. 5.2.3, Eq. (schurMass): S_M^-1 = M_{1/eta}^-1 solved by CG to tol_invMass; the
     diag(A)-BFBT approximation (C = D = diag(A) in the BFBT formula of Sec. 5.2.3), whose
     B diag(A)^-1 B^T solve is structured like the V-cycle BFBT's.
+  * Sec. 5.2.3, Eq. (schurWBFBT) in its rescaled form: the weighted BFBT approximation
+    (oracle/wbfbt.py), with a_l, a_r of Table parametertable.
 
 Readings:
   * Chebyshev iteration in the form of Saad, Iterative Methods, Alg. 12.1 (with the
@@ -49,7 +51,7 @@ from .fem import (Operators, Constraints, ConstrainedOperators, project_mean_zer
 
 DEFAULTS = dict(sigma=1.0, omega=0.3, tol_A=1e-2, m_A=3, deg_A=2, tol_VBFBT=1e-1,
                 tol_invMass=1e-10, m_V=1, deg_V=1, tol_coarse=1e-2,
-                uzawa="symmetric", schur="vbfbt")
+                uzawa="symmetric", schur="vbfbt", a_l=1.0, a_r=1.0)
 
 
 # ------------------------------------------------------------------------- transfers
@@ -318,6 +320,12 @@ class StokesOracle:
         Md = ops.M_inv_eta.diagonal()
         self.M = ops.M_inv_eta
         self.Mdinv = 1.0 / Md
+        self.wl = self.wr = None
+        if self.p["schur"] == "wbfbt":
+            from .wbfbt import WbfbtOperators
+            eta = hier.etas[L]
+            self.wr = WbfbtOperators(hier.levels[L], eta, self.p["a_r"])
+            self.wl = self.wr if self.p["a_l"] == self.p["a_r"] else WbfbtOperators(hier.levels[L], eta, self.p["a_l"])
 
     # blocks of the constrained system
     def K(self, x):
@@ -360,10 +368,14 @@ class StokesOracle:
 
     def Shat_inv(self, r):
         """The Schur approximation: V-cycle BFBT X^-1 (B A_C^-1 A A_C^-1 B^T) X^-1 r (Eq.
-        schurV), the inverse-viscosity mass M_{1/eta}^-1 r (Eq. schurMass), or diag(A)-BFBT."""
+        schurV), the inverse-viscosity mass M_{1/eta}^-1 r (Eq. schurMass), diag(A)-BFBT, or
+        the weighted BFBT (Eq. schurWBFBT, rescaled form)."""
         kind = self.p["schur"]
         if kind == "mass":
             return self.Minv(r)
+        if kind == "wbfbt":
+            from .wbfbt import wbfbt_apply
+            return project_mean_zero(wbfbt_apply(self.co, self.cons, self.co.apply_A, self.wl, self.wr, r))
         if kind == "diagbfbt":
             return self.bfbt(r, self.Dinv)
         return self.bfbt(r, self.Ac_inv)
