@@ -251,7 +251,12 @@ typedef struct {
                          AdjointInexactUzawaStep1); each applied from (0, 0) */
   int schur;          /* Schur approximation (Sec. 5.2.3): 0 V-cycle BFBT (Eq. schurV, default),
                          1 inverse-viscosity mass M_{1/eta}^-1 by CG to tol_invMass (Eq.
-                         schurMass), 2 diag(A)-BFBT (C = D = diag(A), solved like 0) */
+                         schurMass), 2 diag(A)-BFBT (C = D = diag(A), solved like 0),
+                         3 weighted BFBT (Eq. schurWBFBT, rescaled form, see mfs_apply_schur) */
+  double a_l, a_r;    /* weighted-BFBT surface scalings: eta_{l,r} = a_{l,r}^2 eta on the micro-tets
+                         with a vertex on the outer surface (1, 1; Table parametertable) */
+  double tol_wBFBT;   /* CG on K_{1/sqrt(eta)}, relative or absolute, whichever is met first
+                         (1e-10; at least 1e-5 in FP32) */
 } mfs_solve_opts;
 
 typedef struct {
@@ -271,6 +276,35 @@ typedef struct {
 } mfs_solve_stats;
 
 void mfs_solve_opts_default(mfs_solve_opts* opts);
+
+/* ---------------------------------------------------------------- Schur approximations
+ * z = S^-1 r: one application of the Schur approximation opts->schur (opts = NULL: the
+ * default V-cycle BFBT) on the finest level, in precision prec, with the tolerances of opts,
+ * as the Uzawa step applies it.  r, z: [n_p1] device vectors of prec; z is mean-free.  Needs
+ * mfs_setup_multigrid.  stats (may be NULL) receives the inner CG counts and times.
+ * The weighted BFBT (schur = 3; Sec. 5.2.3, Eq. schurWBFBT with the near-surface rescaling):
+ *   S_w^-1 = K_{1/sqrt(eta_l)}^-1 (B M_{sqrt(eta_l)}^-1 A M_{sqrt(eta_r)}^-1 B^T) K_{1/sqrt(eta_r)}^-1,
+ * K by CG preconditioned with its own geometric V-cycle (Chebyshev m_A, deg_A) to tol_wBFBT,
+ * M the lumped vector mass (mfs_lumped_vmass).  Its operators are built on first use of a
+ * scaling and after every coefficient change (allocates device memory).
+ * Errors: MFS_EINVAL, MFS_ENAN, MFS_ENOMEM, MFS_ECUDA. */
+mfs_status mfs_apply_schur(mfs_problem* prob, const mfs_solve_opts* opts, mfs_prec prec, const void* r, void* z,
+                           mfs_solve_stats* stats);
+
+/* y = K_{1/sqrt(eta_a)} p on level lvl (multigrid range): the P1 Laplacian
+ *   K_ij = sum_tets sum_q w_q |det J_q| grad psi_j . grad psi_i / sqrt(eta_a(x_q))
+ * with natural boundary conditions (Sec. 5.2.3, the Poisson operator replacing
+ * B M_{sqrt(eta)}^-1 B^T), eta_a = a^2 eta on the micro-tets with a vertex on the outer surface
+ * and eta elsewhere, eta the P1 interpolant of the level's nodal viscosity.  p, y: [n_p1(lvl)]
+ * device vectors of prec.  Needs mfs_setup_multigrid.  Errors: MFS_EINVAL, MFS_ENOMEM, MFS_ECUDA. */
+mfs_status mfs_apply_poisson(mfs_problem* prob, int lvl, mfs_prec prec, double a, const void* p, void* y);
+
+/* d = the lumped vector mass M_{sqrt(eta_a)} on the finest level (Sec. 5.2.3, "potentially
+ * lumped"): per micro-tet the diagonal of int sqrt(eta_a) phi_i phi_j (P2, the 4-point rule)
+ * scaled to the element's total int sqrt(eta_a) (Hinton-Rock-Zienkiewicz lumping); one entry
+ * per P2 node, the same for every velocity component.  d: [n_p2] FP64 device vector.
+ * Errors: MFS_EINVAL, MFS_ECUDA. */
+mfs_status mfs_lumped_vmass(mfs_problem* prob, double a, double* d);
 
 /* Solve the projected saddle-point system (paper Eq. SaddlePointStructureDirichlet) on
  * the finest level: f [3][n_p2] and g [n_p1] are the right-hand sides (FP64, device);

@@ -41,7 +41,8 @@ class SolveOpts(ctypes.Structure):
                 ("m_A", ctypes.c_int), ("deg_A", ctypes.c_int), ("tol_VBFBT", ctypes.c_double),
                 ("tol_invMass", ctypes.c_double), ("m_V", ctypes.c_int), ("deg_V", ctypes.c_int),
                 ("max_cg", ctypes.c_int), ("with_C", ctypes.c_int), ("uzawa", ctypes.c_int),
-                ("schur", ctypes.c_int)]
+                ("schur", ctypes.c_int), ("a_l", ctypes.c_double), ("a_r", ctypes.c_double),
+                ("tol_wBFBT", ctypes.c_double)]
 
 
 class SolveStats(ctypes.Structure):
@@ -104,6 +105,9 @@ _SIGS = {
     "mfs_batch_apply_stokes": ([_vp, _i, _i, _vp, _vp, _vp, _vp], _i),
     "mfs_batch_solve": ([_vp, ctypes.POINTER(SolveOpts), _vp, _vp, _vp, _vp, _vp], _i),
     "mfs_stokes_solve": ([_vp, ctypes.POINTER(SolveOpts), _vp, _vp, _vp, _vp, ctypes.POINTER(SolveStats)], _i),
+    "mfs_apply_schur": ([_vp, ctypes.POINTER(SolveOpts), _i, _vp, _vp, ctypes.POINTER(SolveStats)], _i),
+    "mfs_apply_poisson": ([_vp, _i, _i, _d, _vp, _vp], _i),
+    "mfs_lumped_vmass": ([_vp, _d, _vp], _i),
 }
 
 _lib = None
@@ -289,6 +293,19 @@ class Problem:
         _need(p, npp, None, "p"); _need(y, npp, p.dtype, "y")
         _check(lib().mfs_apply_mass(self.handle, level, _prec_of(p), _ptr(p), _ptr(y)))
 
+    def apply_poisson(self, level, a, p, y):
+        """y = K_{1/sqrt(eta_a)} p (weighted-BFBT Poisson operator) on a multigrid level."""
+        _, npp = self._sizes(level)
+        _need(p, npp, None, "p"); _need(y, npp, p.dtype, "y")
+        _check(lib().mfs_apply_poisson(self.handle, level, _prec_of(p), float(a), _ptr(p), _ptr(y)))
+
+    def lumped_vmass(self, a, d):
+        """d = lumped M_{sqrt(eta_a)} diagonal (one FP64 entry per P2 node, finest level)."""
+        import torch
+        nu, _ = self._sizes(self.mesh.l_max)
+        _need(d, nu // 3, torch.float64, "d")
+        _check(lib().mfs_lumped_vmass(self.handle, float(a), _ptr(d)))
+
     def prolongate(self, level, xc, xf):
         nf, _ = self._sizes(level)
         nc, _ = self._sizes(level - 1)
@@ -366,6 +383,16 @@ class Problem:
         if rc != OK and raise_on_error:
             raise MfsError(rc, lib().mfs_last_error().decode())
         return d
+
+    def apply_schur(self, r, z, **opts):
+        """z = S^-1 r for the Schur approximation opts['schur'] (finest level, precision of r);
+        returns the statistics as a dict."""
+        _, npp = self._sizes(self.mesh.l_max)
+        _need(r, npp, None, "r"); _need(z, npp, r.dtype, "z")
+        o = self.default_opts(**opts)
+        st = SolveStats()
+        _check(lib().mfs_apply_schur(self.handle, ctypes.byref(o), _prec_of(r), _ptr(r), _ptr(z), ctypes.byref(st)))
+        return st.as_dict()
 
     def adjoint_solve(self, ju, jp, lam_u, lam_p, raise_on_error=True, **opts):
         """Solve K^T lam = (ju, jp) in place (FP64 device tensors); returns statistics."""

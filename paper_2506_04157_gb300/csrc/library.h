@@ -80,7 +80,9 @@ MacroGeom<T> cast_geom(const MacroGeom<double>& g);
 
 namespace mfs {
 struct MG;
+struct PoissonMG;
 void problem_release_solver(mfs_problem* P);
+void pmg_destroy(PoissonMG* W);
 }  // namespace mfs
 
 struct mfs_ctx {
@@ -121,6 +123,7 @@ struct mfs_problem {
   double* d_red64 = nullptr;    // [kRedSlots]
   float* d_red32 = nullptr;
   mfs::MG* mg = nullptr;        // multigrid hierarchy and solver workspaces
+  mfs::PoissonMG* pmg = nullptr;  // weighted-BFBT operators (K_{1/sqrt(eta)} GMG, lumped mass)
   // temperature-dependent viscosity law (mfs_set_viscosity_law / mfs_set_temperature):
   // levels l <= l_eta evaluate eta at the quadrature points from temp64/32[l]
   int l_eta = -1;                  // in effect (set with the temperature)
@@ -166,6 +169,8 @@ mfs_status vec_sum(const T* x, int64_t n, T* d_partials, T* d_out, cudaStream_t 
 template <typename T>
 mfs_status vec_sub_mean(T* x, int64_t n, const T* d_sum, cudaStream_t s);
 mfs_status inject_p1(const mfs_mesh* M, int l_from, int l_to, const double* src, double* dst);
+void p1_transfer_triplets(const mfs_mesh* M, int l, std::vector<int>& tv, std::vector<int>& tj,
+                          std::vector<double>& tw);
 mfs_status build_eta_restriction(mfs_mesh* M, int l);
 mfs_status restrict_eta(const mfs_mesh* M, int l, const double* fine, double* coarse);
 mfs_status build_id_tables(const mfs_mesh* M, LevelData& L);

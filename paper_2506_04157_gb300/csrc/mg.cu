@@ -9,6 +9,7 @@
 //    viscosity in FP64 by Gauss-Jordan elimination, applied as a GEMV.
 #include "apply.cuh"
 #include "library.h"
+#include "qp_geometry.cuh"
 #include "solver.h"
 
 namespace mfs {
@@ -333,55 +334,16 @@ __global__ void k_unit(int64_t n, int64_t j, double* __restrict__ e) {
   GRID_STRIDE(i, n) e[i] = (i == j) ? 1.0 : 0.0;
 }
 
+void gj_invert(int n, double* A, double* colk, cudaStream_t s) {
+  for (int k = 0; k < n; ++k) {
+    k_gj_row<<<1, 512, 0, s>>>(n, k, A, colk);
+    k_gj_elim<<<blocks_for((int64_t)n * n, 256, 4096), 256, 0, s>>>(n, k, A, colk);
+  }
+}
+
+void unit_vector(int64_t n, int64_t j, double* e, cudaStream_t s) { k_unit<<<blocks_for(n), 256, 0, s>>>(n, j, e); }
+
 // ------------------------------------------------------------------------- diag(A), M_{1/eta}
-// lattice gradient (permuted frame) of the P2 basis function a at barycentrics lam
-__device__ __forceinline__ void p2_lat_grad(int a, const double lam[4], double g[3]) {
-  // grad lambda_0 = (-1,0,0), grad lambda_1 = (1,-1,0), grad lambda_2 = (0,1,-1), grad lambda_3 = (0,0,1)
-  const double GL[4][3] = {{-1, 0, 0}, {1, -1, 0}, {0, 1, -1}, {0, 0, 1}};
-  if (a < 4) {
-    for (int j = 0; j < 3; ++j) g[j] = (4 * lam[a] - 1) * GL[a][j];
-  } else {
-    const int e = a - 4;
-    const int i0 = e < 3 ? 0 : (e < 5 ? 1 : 2);
-    const int i1 = e < 3 ? e + 1 : (e < 5 ? e - 1 : 3);
-    for (int j = 0; j < 3; ++j) g[j] = 4 * (lam[i1] * GL[i0][j] + lam[i0] * GL[i1][j]);
-  }
-}
-
-// geometry of qp q of a tet: K' rows (permuted lattice frame) and the scalings
-template <typename T, bool BLEND>
-__device__ __forceinline__ void qp_geometry(const MacroGeom<T>& G, int n, int p0, int p1, int p2, int q, T qx, T qy,
-                                            T qz, T K[3][3], T& hr, T& rinv, T x[3]) {
-  const T QA = T(MFS_QA), QB = T(MFS_QB);
-  const int S1 = 1 << p0, S2 = S1 | (1 << p1);
-  const int Sq = q == 0 ? 0 : (q == 1 ? S1 : (q == 2 ? S2 : 7));
-  const T xi0 = qx + QB * T(3 * (p0 == 0) + 2 * (p1 == 0) + (p2 == 0)) + (QA - QB) * T(Sq & 1);
-  const T xi1 = qy + QB * T(3 * (p0 == 1) + 2 * (p1 == 1) + (p2 == 1)) + (QA - QB) * T((Sq >> 1) & 1);
-  const T xi2 = qz + QB * T(3 * (p0 == 2) + 2 * (p1 == 2) + (p2 == 2)) + (QA - QB) * T(Sq >> 2);
-  for (int r = 0; r < 3; ++r)
-    x[r] = G.v0[r] + (G.Jm[3 * r] * xi0 + G.Jm[3 * r + 1] * xi1 + G.Jm[3 * r + 2] * xi2) / T(n);
-  const T r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
-  rinv = T(1) / sqrt(r2);
-  const int pr[3] = {p0, p1, p2};
-  T Mp[3][3];
-  for (int j = 0; j < 3; ++j)
-    for (int d = 0; d < 3; ++d) Mp[j][d] = T(n) * G.Jinv[3 * pr[j] + d];
-  hr = T(1);
-  if (BLEND) {
-    const T h = x[0] * G.nh[0] + x[1] * G.nh[1] + x[2] * G.nh[2];
-    hr = h * rinv / G.delta;
-    T v[3];
-    for (int d = 0; d < 3; ++d) v[d] = G.nh[d] / h - x[d] * rinv * rinv;
-    for (int j = 0; j < 3; ++j) {
-      const T tj = Mp[j][0] * x[0] + Mp[j][1] * x[1] + Mp[j][2] * x[2];
-      for (int d = 0; d < 3; ++d) K[j][d] = Mp[j][d] - tj * v[d];
-    }
-  } else {
-    for (int j = 0; j < 3; ++j)
-      for (int d = 0; d < 3; ++d) K[j][d] = Mp[j][d];
-  }
-}
-
 // diag(A) (raw, no projection): sum over tets and qps of 2 eta W (|g|^2/2 + g_c^2/6);
 // ETAQ: eta from the viscosity law at the quadrature points (levels up to l_eta)
 template <typename T, bool BLEND, bool ETAQ>
@@ -810,10 +772,7 @@ mfs_status coarse_inverse(mfs_problem* P, int lvl, const BoundaryList& B, double
     MFS_TRY(launch_apply<double>(P, lvl, OP_A, 1, 0, e, nullptr, A + j * N, nullptr, nullptr));
   }
   if (B.nb) k_regularise_normals<<<blocks_for(B.nb), 256, 0, s>>>(B.nb, B.ids, B.kind, B.nrm64, L.nb2.total, A);
-  for (int k = 0; k < (int)N; ++k) {
-    k_gj_row<<<1, 512, 0, s>>>((int)N, k, A, colk);
-    k_gj_elim<<<blocks_for(N * N, 256, 4096), 256, 0, s>>>((int)N, k, A, colk);
-  }
+  gj_invert((int)N, A, colk, s);
   MFS_CUDA(cudaGetLastError());
   return MFS_OK;
 }

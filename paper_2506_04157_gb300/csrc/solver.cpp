@@ -740,7 +740,15 @@ mfs_status mfs_vcycle(mfs_problem* Pb, int lvl, mfs_prec prec, int steps, int de
 }
 
 namespace mfs {
+int mg_lmin(const mfs_problem* Pb) {
+  return (Pb && Pb->mg && Pb->mg->structure && Pb->mg->numeric) ? Pb->mg->l_min : -1;
+}
+
 void problem_release_solver(mfs_problem* Pb) {
+  if (Pb && Pb->pmg) {
+    pmg_destroy(Pb->pmg);
+    Pb->pmg = nullptr;
+  }
   if (Pb && Pb->mg) {
     mg_destroy(Pb->mg);
     Pb->mg = nullptr;
@@ -814,7 +822,7 @@ struct Stokes {
   int64_t n2, nu, np, N;
   cudaStream_t s;
   Krylov<T>& K;
-  double tolM;
+  double tolM, tolW;
   int transpose;   // 1: the adjoint operator [A (B+C)^T; B 0]
   // FP64 outer Krylov with an FP32 preconditioner (mixed = 2): the preconditioner of this
   // (FP64) instance is the FP32 instance's Uzawa step, through FP32 copies of its vectors
@@ -826,6 +834,8 @@ struct Stokes {
         transpose(transp) {
     tolM = o.tol_invMass;
     if (sizeof(T) == 4 && tolM < 1e-5) tolM = 1e-5;   // FP32 CG stagnates near 1e-6
+    tolW = o.tol_wBFBT;
+    if (sizeof(T) == 4 && tolW < 1e-5) tolW = 1e-5;
   }
 
   double dotn(int64_t n, const T* x, const T* y) { return dot<T>(G, n, x, y, s); }
@@ -856,9 +866,10 @@ struct Stokes {
   // generic preconditioned CG on n entries; op/pre write their output vector
   template <typename Op, typename Pre>
   mfs_status cg(int64_t n, Op op, Pre pre, const T* b, T* x, double rtol, int maxit, T* r, T* z, T* p, T* q,
-                int* iters, int proj = 0) {
+                int* iters, int proj = 0, double atol = 0.0) {
     // proj: 1 keeps a pressure residual mean-free, 2 keeps a velocity residual in the
-    // constrained space (FP32 rounding leaves residue in directions the operator ignores)
+    // constrained space (FP32 rounding leaves residue in directions the operator ignores);
+    // stops at ||r|| <= max(rtol ||r0||, atol)
     Blas<T>::axpby(n, T(1), b, T(0), r, s);
     if (proj == 1) MFS_TRY(mean_free<T>(Pb, r, n));
     if (proj == 2) Blas<T>::bproject(G->bnd[L], n2, r, s);
@@ -892,7 +903,7 @@ struct Stokes {
         set_error("NaN/Inf in CG residual");
         return MFS_ENAN;
       }
-      if (std::sqrt(rr) <= rtol * std::sqrt(rr0)) break;
+      if (std::sqrt(rr) <= rtol * std::sqrt(rr0) || std::sqrt(rr) <= atol) break;
       MFS_TRY(pre(r, z));
       const double rz_new = dotn(n, r, z);
       Blas<T>::axpby(n, T(1), z, T(rz_new / rz), p, s);
@@ -1007,9 +1018,38 @@ struct Stokes {
     return Bop(K.ub, y, 0);
   }
   // V-cycle BFBT: X^-1 (B A_C^-1 A A_C^-1 B^T) X^-1 r
+  // K_{1/sqrt(eta_a)}^-1 r by CG preconditioned with its V-cycle (the A-block smoother
+  // shape), to tol_wBFBT relative or absolute, whichever is reached first
+  mfs_status K_inv(int side, const T* r, T* x) {
+    int it = 0;
+    auto op = [&](const T* v, T* y) { return poisson_apply<T>(Pb, side, L, v, y); };
+    auto pre = [&](const T* v, T* y) { return poisson_vcycle<T>(Pb, side, y, v, o.m_A, o.deg_A); };
+    MFS_TRY(cg(np, op, pre, r, x, tolW, o.max_cg, K.cgp_r, K.cgp_z, K.cgp_p, K.cgp_q, &it, 1, tolW));
+    st.cg_X_iters += it;
+    st.cg_X_calls++;
+    st.cg_X_max = it > st.cg_X_max ? it : st.cg_X_max;
+    return mean_free<T>(Pb, x, np);
+  }
+  // weighted BFBT (Eq. schurWBFBT, rescaled form):
+  //   K_{1/sqrt(eta_l)}^-1 (B M_{sqrt(eta_l)}^-1 A M_{sqrt(eta_r)}^-1 B^T) K_{1/sqrt(eta_r)}^-1 r
+  mfs_status wbfbt(const T* r, T* z) {
+    int sl = 0, sr = 0;
+    MFS_TRY(pmg_side(Pb, o.a_l, &sl));
+    MFS_TRY(pmg_side(Pb, o.a_r, &sr));
+    MFS_TRY(K_inv(sr, r, K.pe));
+    MFS_TRY(BT(K.pe, K.uc));
+    Blas<T>::mul(nu, K.uc, poisson_minv<T>(Pb, sr), K.ud, s);
+    Blas<T>::bproject(G->bnd[L], n2, K.ud, s);
+    MFS_TRY(A(K.ud, K.uc));
+    Blas<T>::mul(nu, K.uc, poisson_minv<T>(Pb, sl), K.ud, s);
+    Blas<T>::bproject(G->bnd[L], n2, K.ud, s);
+    MFS_TRY(Bop(K.ud, K.pf, 0));
+    return K_inv(sl, K.pf, z);
+  }
   mfs_status S_inv(const T* r, T* z) {
     WallTimer tm(st.time_Sinv_ms);
     if (o.schur == 1) return M_inv(r, z);   // Eq. schurMass: M_{1/eta}^-1 (mean-free)
+    if (o.schur == 3) return wbfbt(r, z);
     int it = 0;
     auto op = [&](const T* v, T* y) { return X(v, y); };
     auto pre = [&](const T* v, T* y) { return M_inv(v, y); };
@@ -1201,6 +1241,19 @@ static mfs_status residual64(mfs_problem* Pb, const mfs_solve_opts& o, const dou
   return MFS_OK;
 }
 
+static mfs_status check_schur_opts(const mfs_solve_opts& o) {
+  if (o.schur < 0 || o.schur > 3) {
+    set_error("schur must be 0 (V-cycle BFBT), 1 (mass), 2 (diag(A)-BFBT) or 3 (weighted BFBT)");
+    return MFS_EINVAL;
+  }
+  if (o.schur == 3 && (!(o.a_l > 0.0) || !(o.a_r > 0.0) || !std::isfinite(o.a_l) || !std::isfinite(o.a_r) ||
+                       !(o.tol_wBFBT > 0.0))) {
+    set_error("weighted BFBT needs positive finite a_l, a_r and a positive tol_wBFBT");
+    return MFS_EINVAL;
+  }
+  return MFS_OK;
+}
+
 static mfs_status stokes_solve(mfs_problem* Pb, const mfs_solve_opts& o, const double* f, const double* g, double* u,
                                double* p, mfs_solve_stats& st, int transpose) {
   MG* G = Pb->mg;
@@ -1211,9 +1264,9 @@ static mfs_status stokes_solve(mfs_problem* Pb, const mfs_solve_opts& o, const d
     set_error("mixed must be 0 (FP64), 1 (FP32 FGMRES in FP64 refinement) or 2 (FP64 FGMRES, FP32 preconditioner)");
     return MFS_EINVAL;
   }
-  if (o.uzawa < 0 || o.uzawa > 2 || o.schur < 0 || o.schur > 2) {
-    set_error("uzawa must be 0 (symmetric), 1 (inexact) or 2 (adjoint); schur 0 (V-cycle BFBT), 1 (mass) or "
-              "2 (diag(A)-BFBT)");
+  MFS_TRY(check_schur_opts(o));
+  if (o.uzawa < 0 || o.uzawa > 2) {
+    set_error("uzawa must be 0 (symmetric), 1 (inexact) or 2 (adjoint)");
     return MFS_EINVAL;
   }
   MFS_TRY(ensure_krylov<double>(G, nu, np, o.mixed == 1 ? 1 : o.restart, s));
@@ -1316,6 +1369,51 @@ void mfs_solve_opts_default(mfs_solve_opts* o) {
   o->with_C = 1;
   o->uzawa = 0;
   o->schur = 0;
+  o->a_l = 1.0;
+  o->a_r = 1.0;
+  o->tol_wBFBT = 1e-10;
+}
+
+mfs_status mfs_apply_schur(mfs_problem* Pb, const mfs_solve_opts* opts, mfs_prec prec, const void* r, void* z,
+                           mfs_solve_stats* stats) {
+  if (!Pb || !r || !z) {
+    set_error("null argument");
+    return MFS_EINVAL;
+  }
+  if (!Pb->mg || !Pb->mg->numeric) {
+    set_error("multigrid not set up (call mfs_setup_multigrid after mfs_set_viscosity)");
+    return MFS_EINVAL;
+  }
+  mfs_solve_opts o;
+  if (opts) o = *opts;
+  else mfs_solve_opts_default(&o);
+  MFS_TRY(check_schur_opts(o));
+  if (o.m_V < 0 || o.deg_V < 1 || o.m_A < 0 || o.deg_A < 1 || o.max_cg < 1) {
+    set_error("invalid solver options");
+    return MFS_EINVAL;
+  }
+  MG* G = Pb->mg;
+  const int L = Pb->mesh->l_max;
+  const int64_t nu = 3 * (int64_t)Pb->mesh->levels[L].nb2.total, np = Pb->mesh->levels[L].nb1.total;
+  cudaStream_t s = Pb->mesh->ctx->stream;
+  mfs_solve_stats st;
+  std::memset(&st, 0, sizeof(st));
+  mfs_status rc;
+  if (prec == MFS_F64) {
+    MFS_TRY(ensure_krylov<double>(G, nu, np, 1, s));
+    Stokes<double> S(Pb, o, st);
+    rc = S.S_inv((const double*)r, (double*)z);
+  } else {
+    MFS_TRY(ensure_krylov<float>(G, nu, np, 1, s));
+    Stokes<float> S(Pb, o, st);
+    rc = S.S_inv((const float*)r, (float*)z);
+  }
+  if (rc == MFS_OK) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "mfs_apply_schur");
+  }
+  if (stats) *stats = st;
+  return rc;
 }
 
 mfs_status mfs_stokes_solve(mfs_problem* Pb, const mfs_solve_opts* opts, const double* f, const double* g, double* u,

@@ -129,6 +129,29 @@ template <typename T>
 mfs_status mass_apply(mfs_problem* P, int lvl, const T* pin, T* y, int diag_only, const double* active = nullptr,
                       int zero_out = 1);
 mfs_status coarse_inverse(mfs_problem* P, int lvl, const BoundaryList& B, double* A, double* work);
+// in-place Gauss-Jordan inverse of an SPD n x n matrix (no pivoting); colk: n doubles
+void gj_invert(int n, double* A, double* colk, cudaStream_t s);
+void unit_vector(int64_t n, int64_t j, double* e, cudaStream_t s);
+
+// ---- weighted BFBT (Sec. 5.2.3, Eq. schurWBFBT, rescaled form; wbfbt.cu)
+// Operators for one surface scaling a (eta_a = a^2 eta on the micro-tets with a vertex on
+// the outer surface, eta elsewhere): K_{1/sqrt(eta_a)} on the multigrid levels with its
+// GMG, and the lumped M_{sqrt(eta_a)}^-1 on the finest level.  Built on first use of a and
+// rebuilt after a coefficient change; `side` identifies them in the calls below.
+mfs_status pmg_side(mfs_problem* P, double a, int* side);
+// coarsest multigrid level, or -1 before mfs_setup_multigrid
+int mg_lmin(const mfs_problem* P);
+// y = K_{1/sqrt(eta_a)} p on level lvl (multigrid range)
+template <typename T>
+mfs_status poisson_apply(mfs_problem* P, int side, int lvl, const T* p, T* y);
+// x = one V-cycle for K x = b on the finest level (x overwritten; m steps of degree deg)
+template <typename T>
+mfs_status poisson_vcycle(mfs_problem* P, int side, T* x, const T* b, int m, int deg);
+// lumped M_{sqrt(eta_a)}^-1 replicated per velocity component ([3][n_p2], finest level)
+template <typename T>
+const T* poisson_minv(mfs_problem* P, int side);
+// d = the lumped M_{sqrt(eta_a)} diagonal [n_p2] on the finest level (FP64, device)
+mfs_status lumped_vmass(mfs_problem* P, double a, double* d);
 // g_k = -eta_k sum_tets sum_q 2 w|det J| psi_k(q) eps(u)(q) : eps(lam)(q)   (FP64)
 mfs_status grad_log_eta(mfs_problem* P, int lvl, const double* u, const double* lam, double* g);
 

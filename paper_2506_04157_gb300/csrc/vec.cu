@@ -142,18 +142,22 @@ mfs_status exp_inplace(double* x, int64_t n, cudaStream_t s) {
 
 namespace mfs {
 
-// P1 full weighting from level l to l-1, built from the Freudenthal micro-tets of level
-// l-1: the P1 vertices of level l are the P2 nodes of level l-1 (vertices and edge
-// midpoints of its micro-tets).
-mfs_status build_eta_restriction(mfs_mesh* M, int l) {
+// Entries (coarse vertex, fine vertex, weight) of the P1 interpolation from level l-1 to
+// level l, built from the Freudenthal micro-tets of level l-1 (the P1 vertices of level l
+// are the P2 nodes of level l-1, vertices and edge midpoints of its micro-tets): weight 1
+// for the coincident vertex, 1/2 for each end of the coarse edge at a midpoint.  Each fine
+// vertex appears once.
+void p1_transfer_triplets(const mfs_mesh* M, int l, std::vector<int>& tv, std::vector<int>& tj,
+                          std::vector<double>& tw) {
   static const int PERM[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
   static const int LE[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
-  LevelData& L = M->levels[l];
   const int n = 1 << (l - 1);
-  const Numbering nbc = make_numbering(n), nbf = make_numbering(2 * n);
+  const Numbering nbf = make_numbering(2 * n);
+  const Numbering nbc = make_numbering(n);
   std::vector<char> seen(nbf.total, 0);
-  std::vector<int> tv, tj;
-  std::vector<double> tw;
+  tv.clear();
+  tj.clear();
+  tw.clear();
   for (int m = 0; m < 60; ++m) {
     const MacroTopo& t = M->host.topo[m];
     for (int a = 0; a < n; ++a)
@@ -195,6 +199,16 @@ mfs_status build_eta_restriction(mfs_mesh* M, int l) {
             }
           }
   }
+}
+
+// P1 full weighting from level l to l-1: the rows of the transposed P1 interpolation,
+// normalised to sum one.
+mfs_status build_eta_restriction(mfs_mesh* M, int l) {
+  LevelData& L = M->levels[l];
+  const Numbering nbc = make_numbering(1 << (l - 1));
+  std::vector<int> tv, tj;
+  std::vector<double> tw;
+  p1_transfer_triplets(M, l, tv, tj, tw);
   std::vector<int> rp(nbc.total + 1, 0);
   for (int v : tv) rp[v + 1]++;
   for (int i = 0; i < nbc.total; ++i) rp[i + 1] += rp[i];
