@@ -146,7 +146,8 @@ def test_schur_refusals():
 def test_solve_with_wbfbt(mixed, al):
     """FGMRES with the symmetric Uzawa step and the weighted BFBT (symmetric and asymmetric
     surface scaling) reaches the oracle's direct solution (omega = 0.03: the approximation's
-    spectrum reaches ~20-80 here)."""
+    spectrum reaches ~20-80 here).  Solved to 1e-10: with the contrast-1e4 plumes and a
+    rough forcing, a 1e-8 residual leaves a pressure error of ~5e-5."""
     H, ctx, gm, prob = setup(2)
     S = StokesOracle(H)
     L = H.levels[2]
@@ -156,11 +157,11 @@ def test_solve_with_wbfbt(mixed, al):
     u = torch.zeros(3 * L.n_p2, dtype=torch.float64, device="cuda")
     p = torch.zeros(L.n_p1, dtype=torch.float64, device="cuda")
     st = prob.solve(torch.tensor(f, device="cuda"), torch.tensor(g, device="cuda"), u, p, mixed=mixed, schur=3,
-                    a_l=al, omega=0.03, restart=50, max_iters=1500)
-    assert st["status"] == "MFS_OK" and st["rel_residual"] <= 1e-8, st
+                    a_l=al, omega=0.03, restart=50, max_iters=1500, rtol=1e-10)
+    assert st["status"] == "MFS_OK" and st["rel_residual"] <= 1e-10, st
     un, pn = u.cpu().numpy(), p.cpu().numpy()
     r0 = np.linalg.norm(S.residual(f, g, 0 * un, 0 * pn))
-    assert np.linalg.norm(S.residual(f, g, un, pn)) <= 1.5e-8 * r0
+    assert np.linalg.norm(S.residual(f, g, un, pn)) <= 1.5e-10 * r0
     ud, pd = direct_solve(H, f, g, 0 * un, 0 * pn)
     assert np.linalg.norm(un - ud) / np.linalg.norm(ud) < 1e-5
     assert np.linalg.norm(pn - pd) / np.linalg.norm(pd) < 1e-5
