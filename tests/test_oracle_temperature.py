@@ -1,0 +1,227 @@
+"""Pins of the temperature-step oracle (no GPU): variable-step BDF2 and extrapolation, the
+degree-5 conical quadrature, the P2 mass / diffusion / advection / adiabatic blocks, point
+location and P2 evaluation, the RK4 MMOC, and the step's steady fixed point."""
+from math import factorial
+
+import numpy as np
+import pytest
+
+from oracle.mesh import MacroMesh, Level, icosahedron
+from oracle.temperature import (bdf2_coefficients, extrapolate, conical_rule, QUAD5_BARY, QUAD5_W,
+                                TemperatureOperators, Locator, mmoc_departure, mmoc, temperature_step,
+                                solve_temperature)
+
+
+def test_bdf2_exact_for_quadratics():
+    """D[T(t^{n+1}), T(t^n), T(t^{n-1})] / tau^{n+1} = T'(t^{n+1}) for T quadratic in t, any
+    step ratio; the coefficients sum to zero; equal steps give (3/2, 2, 1/2)."""
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        t1, t0 = rng.uniform(0.01, 1.0, 2)
+        a, b, c, tn = rng.standard_normal(4)
+        T = lambda t: a + b * t + c * t * t
+        s1, s0, sm = bdf2_coefficients(t1, t0)
+        D = s1 * T(tn + t1) - s0 * T(tn) + sm * T(tn - t0)
+        assert abs(D / t1 - (b + 2 * c * (tn + t1))) <= 1e-11 * (1 + abs(b) + abs(c))
+        assert abs(s1 - s0 + sm) <= 1e-14 * s0
+    assert np.allclose(bdf2_coefficients(0.1, 0.1), (1.5, 2.0, 0.5), rtol=0, atol=1e-15)
+
+
+def test_extrapolation_exact_for_linear():
+    rng = np.random.default_rng(1)
+    t1, t0 = 0.3, 0.7
+    a, b = rng.standard_normal((2, 5))
+    x = lambda t: a + b * t
+    assert np.abs(extrapolate(x(0.0), x(-t0), t1, t0) - x(t1)).max() <= 1e-15 * 10
+
+
+def test_conical_rule_degree_five():
+    """Exact for every monomial of degree <= 5 (int z^a = a1! a2! a3! / (|a| + 3)!), not for all
+    of degree 6; positive weights summing to the reference volume 1/6."""
+    bary, w = QUAD5_BARY, QUAD5_W
+    z = bary[:, 1:]
+    assert w.min() > 0 and abs(w.sum() - 1 / 6) < 1e-16 and bary.shape == (27, 4)
+    worst6 = 0.0
+    for deg in range(7):
+        for a in range(deg + 1):
+            for b in range(deg + 1 - a):
+                c = deg - a - b
+                exact = factorial(a) * factorial(b) * factorial(c) / factorial(deg + 3)
+                err = abs((w * z[:, 0] ** a * z[:, 1] ** b * z[:, 2] ** c).sum() - exact)
+                if deg <= 5:
+                    assert err < 1e-16
+                else:
+                    worst6 = max(worst6, err)
+    assert worst6 > 1e-7
+
+
+def _shell_integral(f):
+    """int f over the polyhedral shell (icosahedra of circumradius 1 minus 1/2): 20 cones from
+    the origin per icosahedron, each integrated with the degree-7 conical rule."""
+    U, F = icosahedron()
+    bary, w = conical_rule(4)
+    total = 0.0
+    for R, sgn in [(1.0, 1.0), (0.5, -1.0)]:
+        for (a, b, c) in F:
+            V = np.array([[0, 0, 0], R * U[a], R * U[b], R * U[c]])
+            x = bary @ V
+            det = abs(np.linalg.det(np.stack([V[1] - V[0], V[2] - V[0], V[3] - V[0]], axis=-1)))
+            total += sgn * det * (w * f(x)).sum()
+    return total
+
+
+@pytest.fixture(scope="module")
+def poly2():
+    Lv = Level(MacroMesh(blending=False), 2)
+    return Lv, TemperatureOperators(Lv)
+
+
+def test_mass_integrates_quartics_polyhedral(poly2):
+    """f^T M g = int f g for quadratics f, g (held exactly by P2 on straight tets)."""
+    Lv, ops = poly2
+    x = Lv.p2_x
+    f = lambda y: 1 + y[:, 0] - 2 * y[:, 1] * y[:, 2] + 0.5 * y[:, 0] ** 2
+    g = lambda y: y[:, 1] ** 2 - y[:, 2] + 0.3 * y[:, 0] * y[:, 1]
+    val = f(x) @ (ops.M @ g(x))
+    ref = _shell_integral(lambda y: f(y) * g(y))
+    assert abs(val - ref) <= 1e-12 * abs(ref)
+
+
+def test_diffusion_of_linear_functions_polyhedral(poly2):
+    """rho = 1: x_i^T D x_j = delta_ij |shell|; constants lie in the kernel."""
+    Lv, ops = poly2
+    x = Lv.p2_x
+    vol = _shell_integral(lambda y: np.ones(len(y)))
+    assert np.abs(x.T @ (ops.D @ x) - vol * np.eye(3)).max() <= 1e-12 * vol
+    assert np.abs(ops.D @ np.ones(Lv.n_p2)).max() <= 1e-13
+
+
+def test_diffusion_density_term_sign():
+    """For a linear T and an interior test function, int grad T . grad(phi_i / rho) vanishes
+    (divergence theorem); the 1/rho-gradient term must cancel grad phi_i / rho to reach it.
+    With a smooth rho the quadrature residue falls like h^6; a flipped sign leaves O(h^3)."""
+    res = []
+    for L in [1, 2]:
+        Lv = Level(MacroMesh(blending=False), L)
+        ops = TemperatureOperators(Lv, (-0.3781,))
+        y = ops.D @ Lv.p2_x[:, 0]
+        res.append(np.abs(y[~ops.boundary]).max())
+    assert res[0] < 1e-6 and res[1] < res[0] / 30
+
+
+def test_advection_blocks_polyhedral(poly2):
+    """Constant u: C(u) x_1 = u_1 M 1.  Rotation u = w x x (divergence-free, tangential): the
+    interior block of C + C^T vanishes and the adiabatic block R(u) is zero."""
+    Lv, ops = poly2
+    x = Lv.p2_x
+    n = Lv.n_p2
+    c = np.array([0.4, -1.1, 0.7])
+    uc = np.repeat(c, n)
+    assert np.abs(ops.advection(uc) @ x[:, 0] - c[0] * (ops.M @ np.ones(n))).max() <= 1e-13
+    om = np.array([0.3, -0.5, 0.8])
+    ur = np.cross(om, x).T.reshape(-1)
+    C = ops.advection(ur)
+    inner = np.nonzero(~ops.boundary)[0]
+    S = (C + C.T)[inner][:, inner]
+    assert abs(S).max() <= 1e-14 * abs(C).max()
+    assert abs(ops.adiabatic(ur)).max() <= 1e-14
+    # radial u = x: R(u) = -int |x| phi phi, negative definite
+    Rr = ops.adiabatic(x.T.reshape(-1))
+    v = np.random.default_rng(2).standard_normal(n)
+    assert v @ (Rr @ v) < 0
+
+
+@pytest.mark.parametrize("blending", [False, True])
+def test_locate_and_evaluate_at_nodes(blending):
+    Lv = Level(MacroMesh(blending=blending), 2)
+    loc = Locator(Lv)
+    f = np.random.default_rng(3).standard_normal(Lv.n_p2)
+    assert np.abs(loc.eval_p2(f, Lv.p2_x) - f).max() <= 1e-12
+    # points inside tets: valid barycentrics; on straight tets a quadratic is reproduced
+    pts = Lv.p2_x[Lv.tet_p2[::37]].mean(axis=1)
+    tet, lam = loc.locate(pts)
+    assert np.all(lam >= 0) and np.allclose(lam.sum(axis=1), 1.0)
+    if not blending:
+        q = lambda y: 1 + y[:, 0] - 2 * y[:, 1] * y[:, 2] + 0.5 * y[:, 0] ** 2
+        assert np.abs(loc.eval_p2(q(Lv.p2_x), pts) - q(pts)).max() <= 1e-12
+
+
+def test_mmoc_rotation_exact_polyhedral():
+    """Rigid rotation u = w x x is linear, so P2 holds it exactly on straight tets, and one RK4
+    step of the autonomous linear ODE maps x to the degree-4 Taylor polynomial of exp(-tau W)
+    applied to x; a quadratic T is then evaluated exactly at the departure points (nodes whose
+    departure stays inside the shell's inscribed band)."""
+    Lv = Level(MacroMesh(blending=False), 2)
+    loc = Locator(Lv)
+    x = Lv.p2_x
+    om = np.array([0.3, -0.5, 0.8])
+    u = np.cross(om, x).T.reshape(-1)
+    tau = 0.05
+    Om = np.array([[0, -om[2], om[1]], [om[2], 0, -om[0]], [-om[1], om[0], 0]])
+    A = -tau * Om
+    P = np.eye(3) + A + A @ A / 2 + A @ A @ A / 6 + A @ A @ A @ A / 24
+    r = np.linalg.norm(x, axis=1)
+    band = (r > 0.55) & (r < 0.74)
+    X = mmoc_departure(loc, u, u, tau)
+    assert np.abs(X - x @ P.T)[band].max() <= 1e-13
+    q = lambda y: 1 + y[:, 0] - 2 * y[:, 1] * y[:, 2] + 0.5 * y[:, 0] ** 2
+    assert np.abs(mmoc(loc, q(x), u, u, tau) - q(x @ P.T))[band].max() <= 1e-13
+    # zero velocity: the identity
+    T = np.random.default_rng(4).standard_normal(Lv.n_p2)
+    assert np.abs(mmoc(loc, T, 0 * u, 0 * u, tau) - T).max() <= 1e-12
+
+
+def test_mmoc_time_interpolation():
+    """u linear in time (u_old at the start, u_new at the end of the step): with spatially
+    constant fields the departure is x - tau (u_old + u_new)/2 exactly (RK4 integrates a
+    linear-in-time right-hand side exactly)."""
+    Lv = Level(MacroMesh(blending=False), 1)
+    loc = Locator(Lv)
+    n = Lv.n_p2
+    a, b = np.array([0.2, 0.1, -0.3]), np.array([-0.1, 0.4, 0.2])
+    X0 = np.array([[0.62, 0.05, 0.1], [0.0, -0.65, 0.2], [0.3, 0.3, -0.55]])
+    X = mmoc_departure(loc, np.repeat(b, n), np.repeat(a, n), 0.1, X0)
+    assert np.abs(X - (X0 - 0.1 * 0.5 * (a + b))).max() <= 1e-14
+
+
+def test_mmoc_rotation_converges_blended():
+    """On the blended shell P2 holds neither the rotation nor T; the MMOC result approaches
+    T at the exact departure points with refinement (measured 1.7e-2 -> 4.4e-3 from level 1
+    to 2, pre-asymptotic)."""
+    errs = []
+    om = np.array([0.3, -0.5, 0.8])
+    Om = np.array([[0, -om[2], om[1]], [om[2], 0, -om[0]], [-om[1], om[0], 0]])
+    tau = 0.05
+    A = -tau * Om
+    P = np.eye(3) + A + A @ A / 2 + A @ A @ A / 6 + A @ A @ A @ A / 24
+    T = lambda y: np.sin(2 * y[:, 0]) * y[:, 1] + y[:, 2] ** 2
+    for L in [1, 2]:
+        Lv = Level(MacroMesh(), L)
+        loc = Locator(Lv)
+        x = Lv.p2_x
+        u = np.cross(om, x).T.reshape(-1)
+        Xe = x @ P.T
+        Xe *= (np.linalg.norm(x, axis=1) / np.linalg.norm(Xe, axis=1))[:, None]   # stay on the sphere
+        errs.append(np.abs(mmoc(loc, T(x), u, u, tau) - T(Xe)).max())
+    assert errs[1] < errs[0] / 3 and errs[1] < 6e-3
+
+
+def test_step_steady_fixed_point_and_harmonic_limit():
+    """With u = 0, H = 0, Di = 0 the discrete steady field T_d (D T_d = 0 inside, T = 1 on the
+    CMB, 0 on the surface) is a fixed point of the step for any step sizes (the BDF2
+    coefficients sum to zero); T_d approaches the harmonic (1/r - 1)/(1/r_cmb - 1)."""
+    errs = []
+    for L in [1, 2]:
+        Lv = Level(MacroMesh(), L)
+        ops = TemperatureOperators(Lv)
+        r = np.linalg.norm(Lv.p2_x, axis=1)
+        Tex = (1 / r - 1) / (1 / 0.5 - 1)
+        u0 = np.zeros(3 * Lv.n_p2)
+        # T_d by a huge step from any history: s1 M T + tau D T = M(...) -> D T = 0
+        Td = solve_temperature(ops, Tex, Tex, u0, 1e12, 1.0, dict(k=1.0), Tex)
+        errs.append(np.abs(Td - Tex).max())
+        if L == 2:
+            loc = Locator(Lv)
+            T1, _, _ = temperature_step(ops, loc, Td, Td, u0, u0, 0.01, 0.013, dict(k=1.0), Tex)
+            assert np.abs(T1 - Td).max() <= 1e-12
+    assert errs[1] < errs[0] / 4
