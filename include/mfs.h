@@ -316,6 +316,69 @@ mfs_status mfs_lumped_vmass(mfs_problem* prob, double a, double* d);
 mfs_status mfs_stokes_solve(mfs_problem* prob, const mfs_solve_opts* opts, const double* f, const double* g,
                             double* u, double* p, mfs_solve_stats* stats);
 
+/* ---------------------------------------------------------------- temperature step
+ * The energy equation's splitting step of Sec. 3 and Sec. 6 on the finest level: the
+ * temperature is a P2 scalar [n_p2] (FP64, device) with Dirichlet values on both spheres.
+ * Parameters are the nondimensional numbers and constants of Eq. (WeakTemp). */
+typedef struct {
+  double k, Pe, Cp, Di, alpha, H, Ra;  /* conductivity, Peclet, heat capacity, dissipation, expansivity,
+                                          internal heating, Rayleigh (1, 1, 1, 0, 1, 0, 1) */
+  double tol_T;       /* absolute FGMRES tolerance on the constrained residual (1e-10, Table
+                         parametertable) */
+  double rtol;        /* relative FGMRES tolerance, 0 = absolute only (0) */
+  int restart;        /* FGMRES restart length (30) */
+  int max_iters;      /* total FGMRES iterations (300) */
+  int max_cg;         /* iterations of each preconditioner CG (200) */
+  double cg_rtol;     /* relative tolerance of the FP32 preconditioner CG (1e-6) */
+} mfs_temp_params;
+
+typedef struct {
+  int fgmres_iters, cg_iters;
+  double r0_norm, r_norm;   /* FP64 constrained residual norms */
+  double time_ms;
+} mfs_temp_stats;
+
+void mfs_temp_params_default(mfs_temp_params* params);
+
+/* y = (cM M + cC C(u) + cD D + cR R(u)) x on the finest level (Eq. WeakTemp's blocks):
+ *   M = int phi_j phi_i, C(u) = int (u . grad phi_j) phi_i, R(u) = int (u . g) phi_j phi_i with
+ *   g = -x/|x|, D = int grad phi_j . grad(phi_i / rho) (sym = 1: int grad phi_j . grad phi_i / rho),
+ * integrated with a 27-point degree-5 rule over the blended micro-tets; rho from the density
+ * table (mfs_set_density).  constrained = 1: rows and columns of the nodes on both spheres
+ * replaced by the identity.  u: [3][n_p2] (may be NULL when cC = cR = 0); x, y: [n_p2]; all
+ * device vectors of prec.  Allocates the temperature workspace on first use.
+ * Errors: MFS_EINVAL, MFS_ENOMEM, MFS_ECUDA. */
+mfs_status mfs_temp_apply(mfs_problem* prob, mfs_prec prec, double cM, double cC, double cD, double cR, int sym,
+                          int constrained, const void* u, const void* x, void* y);
+
+/* b = the right-hand side of Eq. (WeakTemp) for the step (tau_np1, tau_n):
+ *   int phi_i [s0 T0_hat - sm Tm_hat + tau H/Cp + tau Pe Di/(Ra Cp) 2 eta(x, T*) eps(u*):eps(u*) / rho],
+ * s0 = (tau_np1 + tau_n)/tau_n, sm = tau_np1^2 / (tau_n (tau_np1 + tau_n)) (variable-step BDF2,
+ * Sec. 3), eps the deviatoric strain rate of u* [3][n_p2], eta the viscosity law
+ * (mfs_set_viscosity_law) at the points with T* interpolated.  u_star, T_star may be NULL when
+ * Di = 0.  All FP64 device vectors; rows of boundary nodes are not modified further.
+ * Errors: MFS_EINVAL, MFS_ENOMEM, MFS_ECUDA. */
+mfs_status mfs_temp_rhs(mfs_problem* prob, const mfs_temp_params* params, const double* T0_hat, const double* Tm_hat,
+                        const double* u_star, const double* T_star, double tau_np1, double tau_n, double* b);
+
+/* T_hat = MMOC(T, u_new, u_old, tau) (Sec. 3): every P2 node traced back over a step tau with one
+ * classical RK4 step along u(t) linear in time from u_old (start of the step) to u_new (end),
+ * and T evaluated there (departure points outside the shell moved radially onto it).  T, T_hat:
+ * [n_p2]; u_new, u_old: [3][n_p2]; X_dep: [3][n_p2] departure points, or NULL.  FP64 device
+ * vectors.  Errors: MFS_EINVAL, MFS_ENOMEM, MFS_ECUDA. */
+mfs_status mfs_mmoc(mfs_problem* prob, const double* T, const double* u_new, const double* u_old, double tau,
+                    double* T_hat, double* X_dep);
+
+/* One temperature step (Sec. 3 and Sec. 6): u* and T* by linear extrapolation (Eq.
+ * Extrapolation), T0_hat = MMOC(T_n, u*, u_n, tau_np1), Tm_hat = MMOC(MMOC(T_nm1, u*, u_n,
+ * tau_np1), u_n, u_nm1, tau_n), then Eq. (WeakTemp) for T_np1 with the Dirichlet values of T_bc
+ * on both spheres, solved by FGMRES (FP64) preconditioned by an FP32 Jacobi-CG on
+ * s1 M + tau k/(Pe Cp) D_s.  T_*: [n_p2], u_*: [3][n_p2], FP64 device vectors.
+ * Errors: MFS_EINVAL, MFS_ENOTCONV (best iterate returned), MFS_ENAN, MFS_ENOMEM, MFS_ECUDA. */
+mfs_status mfs_temperature_step(mfs_problem* prob, const mfs_temp_params* params, const double* T_n,
+                                const double* T_nm1, const double* u_n, const double* u_nm1, double tau_np1,
+                                double tau_n, const double* T_bc, double* T_np1, mfs_temp_stats* stats);
+
 /* ---------------------------------------------------------------- adjoint (not in the paper)
  * Adjoint solve K^T lam = (ju, jp) with K^T = [A (B+C)^T; B 0] on the constrained space
  * (the multiplier's Dirichlet values are zeroed on entry), by the same FGMRES / symmetric

@@ -108,6 +108,7 @@ DEFAULT_PARAMS = dict(k=1.0, Pe=1.0, Cp=1.0, Di=0.0, alpha=1.0, H=0.0, Ra=1.0)
 class TemperatureOperators:
     """Assembled P2 scalar blocks on one level:
         M_ij = int phi_j phi_i,   D_ij = int grad phi_j . grad(phi_i / rho),
+        Ds_ij = int grad phi_j . grad phi_i / rho  (the symmetric part of D),
     and, per velocity u ([3][n_p2]), C(u)_ij = int (u.grad phi_j) phi_i and
     R(u)_ij = int (u.g) phi_j phi_i with g = -x/|x|."""
 
@@ -116,7 +117,7 @@ class TemperatureOperators:
         mesh = level.mesh
         n = level.n_p2
         E = level.tet_p2.shape[0]
-        Ms, Ds = [], []
+        Ms, Ds, Ss = [], [], []
         for s in range(0, E, chunk):
             sl = slice(s, min(E, s + chunk))
             geo = GeometryRule(mesh, level.tet_x[sl], level.tet_prism[sl])
@@ -130,8 +131,10 @@ class TemperatureOperators:
             d = level.tet_p2[sl]
             Ms.append(assemble(d, d, np.einsum("eq,qa,qb->eab", geo.W, geo.phi, geo.phi), (n, n)))
             Ds.append(assemble(d, d, np.einsum("eq,eqad,eqbd->eab", geo.W, gtest, geo.grad), (n, n)))
+            Ss.append(assemble(d, d, np.einsum("eq,eqad,eqbd->eab", geo.W / rho, geo.grad, geo.grad), (n, n)))
         self.M = sum(Ms[1:], Ms[0]).tocsr()
         self.D = sum(Ds[1:], Ds[0]).tocsr()
+        self.Ds = sum(Ss[1:], Ss[0]).tocsr()
         cls = level.p2_class
         self.boundary = (cls == CLASS_SURFACE) | (cls == CLASS_CMB)
 
@@ -186,18 +189,33 @@ class TemperatureOperators:
         return out
 
 
-def solve_temperature(ops, T0_hat, Tm_hat, u_star, tau_np1, tau_n, params, T_bc, T_star=None, law=None):
-    """T^{n+1} of Eq. (WeakTemp) (reading: no tau on the s0/sm terms), Dirichlet values T_bc
-    on both spheres, by a sparse direct solve."""
+def temperature_matrix(ops, u_star, tau_np1, tau_n, params):
+    """Left-hand side of Eq. (WeakTemp): s1 M + tau (C(u*) + k/(Pe Cp) D - Di alpha/Cp R(u*))."""
     p = dict(DEFAULT_PARAMS, **(params or {}))
-    s1, s0, sm = bdf2_coefficients(tau_np1, tau_n)
+    s1, _, _ = bdf2_coefficients(tau_np1, tau_n)
     tau = float(tau_np1)
-    L = s1 * ops.M + tau * (ops.advection(u_star) + (p["k"] / (p["Pe"] * p["Cp"])) * ops.D
-                            - (p["Di"] * p["alpha"] / p["Cp"]) * ops.adiabatic(u_star))
+    return s1 * ops.M + tau * (ops.advection(u_star) + (p["k"] / (p["Pe"] * p["Cp"])) * ops.D
+                               - (p["Di"] * p["alpha"] / p["Cp"]) * ops.adiabatic(u_star))
+
+
+def temperature_rhs(ops, T0_hat, Tm_hat, u_star, tau_np1, tau_n, params, T_star=None, law=None):
+    """Right-hand side of Eq. (WeakTemp) (reading: no tau on the s0/sm terms); the shear
+    heating enters when Di != 0 and a viscosity law is given."""
+    p = dict(DEFAULT_PARAMS, **(params or {}))
+    _, s0, sm = bdf2_coefficients(tau_np1, tau_n)
+    tau = float(tau_np1)
     rhs = ops.M @ (s0 * np.asarray(T0_hat) - sm * np.asarray(Tm_hat))
     rhs = rhs + tau * (p["H"] / p["Cp"]) * (ops.M @ np.ones(ops.level.n_p2))
     if law is not None and p["Di"] != 0.0:
         rhs = rhs + tau * (p["Pe"] * p["Di"] / (p["Ra"] * p["Cp"])) * ops.shear_heating(u_star, T_star, law)
+    return rhs
+
+
+def solve_temperature(ops, T0_hat, Tm_hat, u_star, tau_np1, tau_n, params, T_bc, T_star=None, law=None):
+    """T^{n+1} of Eq. (WeakTemp) with Dirichlet values T_bc on both spheres, by a sparse
+    direct solve."""
+    L = temperature_matrix(ops, u_star, tau_np1, tau_n, params)
+    rhs = temperature_rhs(ops, T0_hat, Tm_hat, u_star, tau_np1, tau_n, params, T_star, law)
     bnd = ops.boundary
     Tb = np.where(bnd, np.asarray(T_bc, dtype=np.float64), 0.0)
     rhs = rhs - L @ Tb

@@ -59,6 +59,21 @@ class SolveStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class TempParams(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_double), ("Pe", ctypes.c_double), ("Cp", ctypes.c_double), ("Di", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("H", ctypes.c_double), ("Ra", ctypes.c_double),
+                ("tol_T", ctypes.c_double), ("rtol", ctypes.c_double), ("restart", ctypes.c_int),
+                ("max_iters", ctypes.c_int), ("max_cg", ctypes.c_int), ("cg_rtol", ctypes.c_double)]
+
+
+class TempStats(ctypes.Structure):
+    _fields_ = [("fgmres_iters", ctypes.c_int), ("cg_iters", ctypes.c_int), ("r0_norm", ctypes.c_double),
+                ("r_norm", ctypes.c_double), ("time_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _vp = ctypes.c_void_p
 _i = ctypes.c_int
 _d = ctypes.c_double
@@ -108,6 +123,12 @@ _SIGS = {
     "mfs_apply_schur": ([_vp, ctypes.POINTER(SolveOpts), _i, _vp, _vp, ctypes.POINTER(SolveStats)], _i),
     "mfs_apply_poisson": ([_vp, _i, _i, _d, _vp, _vp], _i),
     "mfs_lumped_vmass": ([_vp, _d, _vp], _i),
+    "mfs_temp_params_default": ([ctypes.POINTER(TempParams)], None),
+    "mfs_temp_apply": ([_vp, _i, _d, _d, _d, _d, _i, _i, _vp, _vp, _vp], _i),
+    "mfs_temp_rhs": ([_vp, ctypes.POINTER(TempParams), _vp, _vp, _vp, _vp, _d, _d, _vp], _i),
+    "mfs_mmoc": ([_vp, _vp, _vp, _vp, _d, _vp, _vp], _i),
+    "mfs_temperature_step": ([_vp, ctypes.POINTER(TempParams), _vp, _vp, _vp, _vp, _d, _d, _vp, _vp,
+                              ctypes.POINTER(TempStats)], _i),
 }
 
 _lib = None
@@ -393,6 +414,63 @@ class Problem:
         st = SolveStats()
         _check(lib().mfs_apply_schur(self.handle, ctypes.byref(o), _prec_of(r), _ptr(r), _ptr(z), ctypes.byref(st)))
         return st.as_dict()
+
+    # ---- temperature step (finest level; FP64 unless stated)
+    @staticmethod
+    def temp_params(**kw):
+        o = TempParams()
+        lib().mfs_temp_params_default(ctypes.byref(o))
+        for k, v in kw.items():
+            if not hasattr(o, k):
+                raise MfsError(EINVAL, f"unknown temperature parameter {k}")
+            setattr(o, k, v)
+        return o
+
+    def temp_apply(self, x, y, cM=1.0, cC=0.0, cD=0.0, cR=0.0, u=None, sym=False, constrained=False):
+        """y = (cM M + cC C(u) + cD D + cR R(u)) x (precision of x)."""
+        nu, _ = self._sizes(self.mesh.l_max)
+        _need(x, nu // 3, None, "x"); _need(y, nu // 3, x.dtype, "y")
+        if u is not None:
+            _need(u, nu, x.dtype, "u")
+        _check(lib().mfs_temp_apply(self.handle, _prec_of(x), cM, cC, cD, cR, int(sym), int(constrained),
+                                    _ptr(u) if u is not None else None, _ptr(x), _ptr(y)))
+
+    def temp_rhs(self, T0_hat, Tm_hat, tau_np1, tau_n, b, u_star=None, T_star=None, **params):
+        import torch
+        nu, _ = self._sizes(self.mesh.l_max)
+        for t, nm in [(T0_hat, "T0_hat"), (Tm_hat, "Tm_hat"), (b, "b")]:
+            _need(t, nu // 3, torch.float64, nm)
+        o = self.temp_params(**params)
+        _check(lib().mfs_temp_rhs(self.handle, ctypes.byref(o), _ptr(T0_hat), _ptr(Tm_hat),
+                                  _ptr(u_star) if u_star is not None else None,
+                                  _ptr(T_star) if T_star is not None else None, tau_np1, tau_n, _ptr(b)))
+
+    def mmoc(self, T, u_new, u_old, tau, T_hat, X_dep=None):
+        import torch
+        nu, _ = self._sizes(self.mesh.l_max)
+        _need(T, nu // 3, torch.float64, "T"); _need(T_hat, nu // 3, torch.float64, "T_hat")
+        _need(u_new, nu, torch.float64, "u_new"); _need(u_old, nu, torch.float64, "u_old")
+        if X_dep is not None:
+            _need(X_dep, nu, torch.float64, "X_dep")
+        _check(lib().mfs_mmoc(self.handle, _ptr(T), _ptr(u_new), _ptr(u_old), tau, _ptr(T_hat),
+                              _ptr(X_dep) if X_dep is not None else None))
+
+    def temperature_step(self, T_n, T_nm1, u_n, u_nm1, tau_np1, tau_n, T_bc, T_np1, raise_on_error=True, **params):
+        """One temperature step; returns the statistics as a dict (status under 'status')."""
+        import torch
+        nu, _ = self._sizes(self.mesh.l_max)
+        for t, nm in [(T_n, "T_n"), (T_nm1, "T_nm1"), (T_bc, "T_bc"), (T_np1, "T_np1")]:
+            _need(t, nu // 3, torch.float64, nm)
+        _need(u_n, nu, torch.float64, "u_n"); _need(u_nm1, nu, torch.float64, "u_nm1")
+        o = self.temp_params(**params)
+        st = TempStats()
+        rc = lib().mfs_temperature_step(self.handle, ctypes.byref(o), _ptr(T_n), _ptr(T_nm1), _ptr(u_n), _ptr(u_nm1),
+                                        tau_np1, tau_n, _ptr(T_bc), _ptr(T_np1), ctypes.byref(st))
+        d = st.as_dict()
+        d["status"] = _STATUS.get(rc, rc)
+        if rc != OK and raise_on_error:
+            raise MfsError(rc, lib().mfs_last_error().decode())
+        return d
 
     def adjoint_solve(self, ju, jp, lam_u, lam_p, raise_on_error=True, **opts):
         """Solve K^T lam = (ju, jp) in place (FP64 device tensors); returns statistics."""

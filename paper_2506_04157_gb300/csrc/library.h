@@ -81,8 +81,10 @@ MacroGeom<T> cast_geom(const MacroGeom<double>& g);
 namespace mfs {
 struct MG;
 struct PoissonMG;
+struct TempWork;
 void problem_release_solver(mfs_problem* P);
 void pmg_destroy(PoissonMG* W);
+void temp_destroy(TempWork* W);
 }  // namespace mfs
 
 struct mfs_ctx {
@@ -124,6 +126,7 @@ struct mfs_problem {
   float* d_red32 = nullptr;
   mfs::MG* mg = nullptr;        // multigrid hierarchy and solver workspaces
   mfs::PoissonMG* pmg = nullptr;  // weighted-BFBT operators (K_{1/sqrt(eta)} GMG, lumped mass)
+  mfs::TempWork* tw = nullptr;    // temperature-step workspace
   // temperature-dependent viscosity law (mfs_set_viscosity_law / mfs_set_temperature):
   // levels l <= l_eta evaluate eta at the quadrature points from temp64/32[l]
   int l_eta = -1;                  // in effect (set with the temperature)

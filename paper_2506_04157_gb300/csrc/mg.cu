@@ -1070,21 +1070,6 @@ namespace mfs {
 // ------------------------------------------------------------------------- buoyancy load vector
 // f_(a,c) = scale sum_q w|det J| rho(r_q) T_q (x_q/|x_q|)_c phi_a(q); T nodal P2 (FP64), rho from
 // the d ln rho / dr table integrated exactly (piecewise linear) with rho(r_surf) = 1.
-__device__ double rho_of(const double* tab, int nt, double r, double r0, double r1) {
-  if (nt <= 1) return exp(tab[0] * (r - r1));
-  const double h = (r1 - r0) / (nt - 1);
-  double s = (r - r0) / h;
-  s = s < 0 ? 0 : (s > nt - 1 ? nt - 1 : s);
-  int i = (int)s;
-  i = i > nt - 2 ? nt - 2 : i;
-  const double f = s - i;
-  // integral of g from r to r1: the part of cell i above r, then the full cells above
-  const double gr = (1 - f) * tab[i] + f * tab[i + 1];
-  double integ = 0.5 * (gr + tab[i + 1]) * (1 - f) * h;
-  for (int k = i + 1; k < nt - 1; ++k) integ += 0.5 * (tab[k] + tab[k + 1]) * h;
-  return exp(-integ);
-}
-
 __global__ void __launch_bounds__(128) k_buoyancy_sweep(const ApplyParams<double> P, int blend, const double* __restrict__ T,
                                                         double scale, double r_surf, double* __restrict__ f) {
   __shared__ double fs[3 * NSLOT2];

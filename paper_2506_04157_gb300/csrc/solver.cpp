@@ -745,6 +745,10 @@ int mg_lmin(const mfs_problem* Pb) {
 }
 
 void problem_release_solver(mfs_problem* Pb) {
+  if (Pb && Pb->tw) {
+    temp_destroy(Pb->tw);
+    Pb->tw = nullptr;
+  }
   if (Pb && Pb->pmg) {
     pmg_destroy(Pb->pmg);
     Pb->pmg = nullptr;

@@ -94,6 +94,8 @@ def test_diffusion_of_linear_functions_polyhedral(poly2):
     vol = _shell_integral(lambda y: np.ones(len(y)))
     assert np.abs(x.T @ (ops.D @ x) - vol * np.eye(3)).max() <= 1e-12 * vol
     assert np.abs(ops.D @ np.ones(Lv.n_p2)).max() <= 1e-13
+    # rho = 1: the symmetric part is D itself
+    assert abs(ops.Ds - ops.D).max() <= 1e-14 * abs(ops.D).max()
 
 
 def test_diffusion_density_term_sign():
@@ -106,6 +108,7 @@ def test_diffusion_density_term_sign():
         ops = TemperatureOperators(Lv, (-0.3781,))
         y = ops.D @ Lv.p2_x[:, 0]
         res.append(np.abs(y[~ops.boundary]).max())
+        assert abs(ops.Ds - ops.Ds.T).max() <= 1e-14 * abs(ops.Ds).max()
     assert res[0] < 1e-6 and res[1] < res[0] / 30
 
 
