@@ -228,3 +228,21 @@ def test_step_steady_fixed_point_and_harmonic_limit():
             T1, _, _ = temperature_step(ops, loc, Td, Td, u0, u0, 0.01, 0.013, dict(k=1.0), Tex)
             assert np.abs(T1 - Td).max() <= 1e-12
     assert errs[1] < errs[0] / 4
+
+
+def test_step_exact_for_linear_in_time_heating():
+    """u = 0, k = 0: the step solves dT/dt = H/Cp, whose solution T(t) = T0 + t H/Cp is linear
+    in time, so variable-step BDF2 reproduces it exactly from exact history at any step ratio
+    (this fixes the reading of Eq. WeakTemp without tau on the history terms: with it the
+    step would return tau-scaled history).  Dirichlet values are the exact solution too."""
+    Lv = Level(MacroMesh(), 1)
+    ops = TemperatureOperators(Lv)
+    loc = Locator(Lv)
+    T0 = np.cos(3 * Lv.p2_x[:, 0]) + Lv.p2_x[:, 1]
+    H, Cp = 0.7, 1.3
+    t1, t0 = 0.05, 0.08
+    u0 = np.zeros(3 * Lv.n_p2)
+    T_n, T_nm1 = T0, T0 - t0 * H / Cp
+    exact = T0 + t1 * H / Cp
+    T1, _, _ = temperature_step(ops, loc, T_n, T_nm1, u0, u0, t1, t0, dict(k=0.0, H=H, Cp=Cp), exact)
+    assert np.abs(T1 - exact).max() <= 1e-12
