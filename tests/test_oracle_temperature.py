@@ -246,3 +246,28 @@ def test_step_exact_for_linear_in_time_heating():
     exact = T0 + t1 * H / Cp
     T1, _, _ = temperature_step(ops, loc, T_n, T_nm1, u0, u0, t1, t0, dict(k=0.0, H=H, Cp=Cp), exact)
     assert np.abs(T1 - exact).max() <= 1e-12
+
+
+def test_coupled_step_buoyancy_scaling():
+    """Eq. (StokesSub) is linear in the buoyancy scale Ra alpha / Pe: doubling Ra doubles
+    (u, p); Ra = 0 leaves the fluid at rest; two coupled steps run from a rest state."""
+    from oracle.timeloop import CoupledOracle
+    law = dict(E_A=4.610, V_A=2.996, r_cmb=0.5, r_surf=1.0, log10_base=[0.0])
+    C = CoupledOracle(MacroMesh(), 1, law, dlnrho_table=(-0.3781,))
+    Lv = C.level
+    T = 0.5 + 0.1 * np.sin(4 * Lv.p2_x[:, 0]) * Lv.p2_x[:, 1]
+    u1, p1 = C.stokes(T, dict(Ra=1.0))
+    u2, p2 = C.stokes(T, dict(Ra=2.0))
+    assert np.abs(u2 - 2 * u1).max() <= 1e-10 * np.abs(u1).max() and np.abs(u1).max() > 0
+    assert np.abs(p2 - 2 * p1).max() <= 1e-10 * np.abs(p1).max()
+    u0, _ = C.stokes(T, dict(Ra=0.0))
+    assert np.abs(u0).max() == 0.0
+    r = np.linalg.norm(Lv.p2_x, axis=1)
+    T_bc = (1 / r - 1) / (1 / 0.5 - 1)
+    zero = np.zeros(3 * Lv.n_p2)
+    st = dict(T_n=T, T_nm1=T, u_n=zero, u_nm1=zero)
+    for _ in range(2):
+        st = C.step(st, 0.01, 0.01, dict(k=0.1, Ra=10.0), T_bc)
+    assert np.isfinite(st["T_n"]).all() and np.isfinite(st["u_n"]).all() and np.abs(st["u_n"]).max() > 0
+    bnd = C.ops.boundary
+    assert np.abs(st["T_n"][bnd] - T_bc[bnd]).max() <= 1e-14
