@@ -118,3 +118,33 @@ def test_temperature_step_matches_oracle():
                                **params)
     assert st["status"] == "MFS_OK"
     assert rel(T1.cpu().numpy(), ref) <= 1e-9, st
+
+
+def test_coupled_step_matches_oracle():
+    """Two coupled steps (temperature step, law viscosity, buoyancy, Stokes solve to 1e-10)
+    against the oracle's coupled step with an exact Stokes solve."""
+    from oracle.timeloop import CoupledOracle
+    from paper_2506_04157_gb300.timeloop import CoupledStepper
+    law = dict(E_A=4.610, V_A=2.996, r_cmb=0.5, r_surf=1.0, log10_base=[0.0])
+    C = CoupledOracle(MacroMesh(), 2, law, dlnrho_table=TABLE)
+    Lv = C.level
+    ctx = mfs.Context(0)
+    gm = mfs.Mesh(ctx, 2)
+    prob = mfs.Problem(gm, "dirichlet", "freeslip")
+    prob.set_density(TABLE)
+    prob.set_viscosity_law(law["log10_base"], E_A=law["E_A"], V_A=law["V_A"], l_eta=-1)
+    T = 0.5 + 0.1 * np.sin(4 * Lv.p2_x[:, 0]) * Lv.p2_x[:, 1]
+    r = np.linalg.norm(Lv.p2_x, axis=1)
+    T_bc = (1 / r - 1) / (1 / 0.5 - 1)
+    params = dict(k=0.1, Ra=10.0)
+    zero = np.zeros(3 * Lv.n_p2)
+    ref = dict(T_n=T, T_nm1=T, u_n=zero, u_nm1=zero)
+    S = CoupledStepper(prob, temp_params=dict(params, tol_T=1e-13), solve_opts=dict(rtol=1e-10, mixed=2))
+    st = dict(T_n=dev(T), T_nm1=dev(T), u_n=dev(zero), u_nm1=dev(zero), p=torch.zeros(Lv.n_p1, dtype=torch.float64,
+                                                                                        device="cuda"))
+    for _ in range(2):
+        ref = C.step(ref, 0.01, 0.01, params, T_bc)
+        st, stats = S.step(st, 0.01, 0.01, dev(T_bc))
+        assert stats["stokes"]["status"] == "MFS_OK"
+    assert rel(st["T_n"].cpu().numpy(), ref["T_n"]) <= 1e-7
+    assert rel(st["u_n"].cpu().numpy(), ref["u_n"]) <= 1e-5
