@@ -306,26 +306,31 @@ class Level:
         self.p1_x = mesh.blend(self.p1_straight, self.p1_prism)
 
     def _nodes(self, N):
-        mesh = self.mesh
-        tot = MacroMesh.counts(N)["total"]
-        X = np.full((tot, 3), np.nan)
-        cls = np.full(tot, -1, dtype=np.int64)
-        prism = np.full(tot, -1, dtype=np.int64)
-        lat = cell_lattice(N)
-        for m in range(N_MACRO_CELLS):
-            ids = mesh.node_ids(m, lat, N)
-            x = mesh.straight(m, lat, N)
-            lay = mesh.layer[mesh.cells[m]]
-            nz = lat > 0
-            top = np.all(~nz | (lay[None, :] == 1), axis=1)
-            bot = np.all(~nz | (lay[None, :] == 0), axis=1)
-            c = np.where(top, CLASS_SURFACE, np.where(bot, CLASS_CMB, CLASS_INNER))
-            seen = ~np.isnan(X[ids, 0])
-            if seen.any():
-                assert np.allclose(X[ids[seen]], x[seen], atol=1e-14, rtol=0)
-                assert np.all(cls[ids[seen]] == c[seen])
-            X[ids] = x
-            cls[ids] = c
-            prism[ids] = mesh.cell_prism[m]
-        assert not np.isnan(X).any()
-        return X, cls, prism
+        return lattice_nodes(self.mesh, N)
+
+
+def lattice_nodes(mesh, N):
+    """Straight positions, classes and prisms of all lattice points of the level with N
+    intervals per macro edge, by global id."""
+    tot = MacroMesh.counts(N)["total"]
+    X = np.full((tot, 3), np.nan)
+    cls = np.full(tot, -1, dtype=np.int64)
+    prism = np.full(tot, -1, dtype=np.int64)
+    lat = cell_lattice(N)
+    for m in range(N_MACRO_CELLS):
+        ids = mesh.node_ids(m, lat, N)
+        x = mesh.straight(m, lat, N)
+        lay = mesh.layer[mesh.cells[m]]
+        nz = lat > 0
+        top = np.all(~nz | (lay[None, :] == 1), axis=1)
+        bot = np.all(~nz | (lay[None, :] == 0), axis=1)
+        c = np.where(top, CLASS_SURFACE, np.where(bot, CLASS_CMB, CLASS_INNER))
+        seen = ~np.isnan(X[ids, 0])
+        if seen.any():
+            assert np.allclose(X[ids[seen]], x[seen], atol=1e-14, rtol=0)
+            assert np.all(cls[ids[seen]] == c[seen])
+        X[ids] = x
+        cls[ids] = c
+        prism[ids] = mesh.cell_prism[m]
+    assert not np.isnan(X).any()
+    return X, cls, prism
