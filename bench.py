@@ -271,6 +271,7 @@ def run_ours(args, rank, world, device):
                            "parts_s": {"A_block_cg": round(st["time_Ahat_ms"] / 1e3, 3),
                                        "schur_vbfbt": round(st["time_Sinv_ms"] / 1e3, 3),
                                        "of_which_mass_cg": round(st["time_Minv_ms"] / 1e3, 3)}}
+    schur = schur_applies(prob, level, inf, dev) if (args.solve and world == 1) else None
     clk.stop()
     if rank != 0:
         return None
@@ -303,6 +304,8 @@ def run_ours(args, rank, world, device):
     }
     if solve is not None:
         line["time_to_solve"] = solve
+    if schur is not None:
+        line["schur_apply"] = schur
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(level, budget_s=args.cpu_seconds)
     return line
@@ -317,6 +320,57 @@ def buoyancy_forcing(mesh, prob, level, dev):
     f = torch.empty(3 * T.numel(), dtype=torch.float64, device=dev)
     prob.rhs_buoyancy(T, f, scale=1.0)
     return f
+
+
+def schur_applies(prob, level, inf, dev):
+    """One application of each Schur approximation (FP32, the solver's tolerances; wall time
+    including the host synchronisations of their inner CGs, median of 3 after a warm-up) and
+    the weighted BFBT's K_{1/sqrt(eta)} sweep alone (CUDA events, 20 launches after 3): its
+    algorithmic bytes are the 6 FP32 element entries per micro-tet plus the P1 input and
+    output vectors."""
+    import numpy as np
+    import torch
+    import paper_2506_04157_gb300 as mfs
+    import workloads as W
+    npp = inf.n_p1
+    r = torch.tensor(W.random_field(npp, 41, np.float32), device=dev)
+    r -= r.mean()
+    z = torch.empty_like(r)
+    out = {}
+    try:
+        times = {}
+        for name, schur in (("vbfbt", 0), ("mass", 1), ("wbfbt", 3)):
+            prob.apply_schur(r, z, schur=schur)
+            ts, st = [], None
+            for _ in range(3):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st = prob.apply_schur(r, z, schur=schur)
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+            times[name] = {"ms": round(1e3 * sorted(ts)[1], 3), "cg_X_iters": st["cg_X_iters"],
+                           "cg_M_iters": st["cg_M_iters"]}
+        out["fp32_apply"] = times
+        y = torch.empty_like(r)
+        for _ in range(3):
+            prob.apply_poisson(level, 1.0, r, y)
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(20):
+            prob.apply_poisson(level, 1.0, r, y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        k_ms = e0.elapsed_time(e1) / 20
+        nbytes = 24 * inf.n_tets + 8 * npp
+        gbs = nbytes / (k_ms * 1e-3) / 1e9
+        hbm = read_peaks().get("hbm_gbs")
+        out["K_sweep"] = {"ms": round(k_ms, 5), "bytes": nbytes, "GB_s": round(gbs, 1),
+                          "frac_of_measured_hbm": round(gbs / hbm, 3) if hbm else None,
+                          "note": "K_{1/sqrt(eta)} apply (memset + sweep), FP32"}
+    except mfs.MfsError as e:
+        out["error"] = str(e)
+    return out
 
 
 def profile_solve(level):
