@@ -271,3 +271,20 @@ def test_coupled_step_buoyancy_scaling():
     assert np.isfinite(st["T_n"]).all() and np.isfinite(st["u_n"]).all() and np.abs(st["u_n"]).max() > 0
     bnd = C.ops.boundary
     assert np.abs(st["T_n"][bnd] - T_bc[bnd]).max() <= 1e-14
+
+
+def test_steady_state_harmonic_with_density():
+    """The diffusion form int grad T . grad(w / rho) is (-Laplace T, w / rho): for any rho the
+    steady state without sources is harmonic, so with the compressible density the discrete
+    steady field still approaches (1/r - 1)/(1/r_cmb - 1); a flipped sign of the 1/rho
+    gradient term would leave an O(1) deviation."""
+    errs = []
+    for L in [1, 2]:
+        Lv = Level(MacroMesh(), L)
+        ops = TemperatureOperators(Lv, (-0.3781,))
+        r = np.linalg.norm(Lv.p2_x, axis=1)
+        Tex = (1 / r - 1) / (1 / 0.5 - 1)
+        u0 = np.zeros(3 * Lv.n_p2)
+        Td = solve_temperature(ops, Tex, Tex, u0, 1e12, 1.0, dict(k=1.0), Tex)
+        errs.append(np.abs(Td - Tex).max())
+    assert errs[1] < errs[0] / 4 and errs[1] < 3e-3

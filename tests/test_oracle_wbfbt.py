@@ -176,3 +176,19 @@ def test_stokes_wbfbt_matches_direct(a_l):
     ud, pd = direct_solve(H, f, g, np.zeros(n), np.zeros(npp))
     assert np.linalg.norm(u - ud) / np.linalg.norm(ud) < 1e-5
     assert np.linalg.norm(p - pd) / np.linalg.norm(pd) < 1e-5
+
+
+def test_poisson_spectrally_equivalent_to_B_Minv_BT(level1_isoviscous):
+    """K_{1/sqrt(eta)} stands for B M_{sqrt(eta)}^-1 B^T (two operators built independently:
+    a P1 stiffness matrix, and the divergence blocks around the lumped vector mass): the
+    generalised eigenvalues of the pair on the mean-zero space are bounded above and below
+    by order-one constants, for a constant and a rough viscosity alike (measured at level 1:
+    [0.315, 1.708] with eta = 1, [0.139, 1.383] with the contrast-1e4 plumes); a wrong
+    weight exponent would stretch the range by up to the square root of the contrast."""
+    Lv, co, cons, S, Bm = level1_isoviscous
+    for eta in (np.ones(Lv.n_p1), W.viscosity_plumes(Lv.p1_x, seed=7, contrast=1e4)):
+        Wo = WbfbtOperators(Lv, eta)
+        n = Lv.n_p1
+        X = np.column_stack([co.apply_B(Wo.M_inv(co.apply_BT(e), cons)) for e in np.eye(n)])
+        ev = np.linalg.eigvals(np.linalg.solve(Bm.T @ Wo.K.toarray() @ Bm, Bm.T @ X @ Bm)).real
+        assert 0.1 < ev.min() and ev.max() < 3.0, (ev.min(), ev.max())
