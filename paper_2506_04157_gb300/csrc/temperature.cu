@@ -18,6 +18,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "apply.cuh"
@@ -563,10 +564,15 @@ static void visit_points(const mfs_mesh* M, int N, F f) {
         }
 }
 
-static bool g_rule_ready = false;
+// the rule's constant-memory copy, uploaded once per device
+static std::mutex g_rule_mutex;
+static std::vector<char> g_rule_ready;
 
 static mfs_status ensure_rule() {
-  if (g_rule_ready) return MFS_OK;
+  int dev = 0;
+  MFS_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(g_rule_mutex);
+  if ((int)g_rule_ready.size() > dev && g_rule_ready[dev]) return MFS_OK;
   double lam[kTQ][4], w[kTQ];
   if (!conical_rule27(lam, w)) {
     set_error("the conical quadrature rule failed its exactness check");
@@ -574,7 +580,8 @@ static mfs_status ensure_rule() {
   }
   MFS_CUDA(cudaMemcpyToSymbol(c_tq_lam, lam, sizeof(lam)));
   MFS_CUDA(cudaMemcpyToSymbol(c_tq_w, w, sizeof(w)));
-  g_rule_ready = true;
+  if ((int)g_rule_ready.size() <= dev) g_rule_ready.resize(dev + 1, 0);
+  g_rule_ready[dev] = 1;
   return MFS_OK;
 }
 
