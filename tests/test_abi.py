@@ -66,3 +66,23 @@ def test_numbering_coords_classes_match_oracle(lib, l, blending):
         cls = M.node_class(l, p2=p2)
         ref_c = L.p2_class if p2 else L.p1_class
         assert np.array_equal(cls, ref_c)
+
+
+def test_library_default_options_match_paper_table(lib):
+    """mfs_solve_opts_default carries the paper's Table parametertable (tests/golden; the
+    coarse-grid tolerance has no field: the coarse solve is an exact inverse), the temperature
+    defaults its tol_T; the ctypes mirrors have the sizes of the C structs of include/mfs.h
+    (136 and 96 bytes, compiled with gcc on x86 and Arm' ABIs)."""
+    import ctypes
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                       "solver_parameters.json")))
+    o = mfs.Problem.default_opts()
+    for k, v in gold.items():
+        if k not in ("_source", "tol_coarse"):
+            assert getattr(o, k) == v, k
+    assert (o.uzawa, o.schur, o.mixed, o.tol_wBFBT) == (0, 0, 1, 1e-10)
+    t = mfs.Problem.temp_params()
+    assert t.tol_T == 1e-10 and t.restart == 30
+    assert ctypes.sizeof(mfs.SolveOpts) == 136 and ctypes.sizeof(mfs.TempParams) == 96
