@@ -72,7 +72,7 @@ def test_library_default_options_match_paper_table(lib):
     """mfs_solve_opts_default carries the paper's Table parametertable (tests/golden; the
     coarse-grid tolerance has no field: the coarse solve is an exact inverse), the temperature
     defaults its tol_T; the ctypes mirrors have the sizes of the C structs of include/mfs.h
-    (136 and 96 bytes, compiled with gcc on x86 and Arm' ABIs)."""
+    (136 and 96 bytes under the LP64 ABI of x86_64 and aarch64)."""
     import ctypes
     import json
     import os
