@@ -253,22 +253,19 @@ def micro_tets_kuhn(n):
     """Freudenthal subdivision of the Kuhn simplex scaled by n, by brute force: every
     unit cube [q, q+1] of [0,n)^3 and every permutation pi gives the simplex
     q, q+e_pi0, q+e_pi0+e_pi1, q+(1,1,1); keep those inside n>=x1>=x2>=x3>=0.
+    Cubes in lexicographic (a, b, c) order, permutations in PERMS order within a cube.
     Returns (n^3, 4, 3) integer vertex coordinates."""
-    out = []
-    for a in range(n):
-        for b in range(n):
-            for c in range(n):
-                q = np.array([a, b, c])
-                for p in PERMS:
-                    v1 = q.copy(); v1[p[0]] += 1
-                    v2 = v1.copy(); v2[p[1]] += 1
-                    v3 = q + 1
-                    V = np.array([q, v1, v2, v3])
-                    ok = np.all(V[:, 0] <= n) and np.all(V[:, 0] >= V[:, 1]) and \
-                        np.all(V[:, 1] >= V[:, 2]) and np.all(V[:, 2] >= 0)
-                    if ok:
-                        out.append(V)
-    T = np.array(out, dtype=np.int64)
+    q = np.stack(np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij"), axis=-1).reshape(-1, 3)
+    eye = np.eye(3, dtype=np.int64)
+    cand = []
+    for p in PERMS:
+        v1 = q + eye[p[0]]
+        v2 = v1 + eye[p[1]]
+        cand.append(np.stack([q, v1, v2, q + 1], axis=1))                   # (n^3, 4, 3)
+    V = np.stack(cand, axis=1).reshape(-1, 4, 3)                             # cube-major, then perm
+    ok = (np.all(V[:, :, 0] <= n, axis=1) & np.all(V[:, :, 0] >= V[:, :, 1], axis=1)
+          & np.all(V[:, :, 1] >= V[:, :, 2], axis=1) & np.all(V[:, :, 2] >= 0, axis=1))
+    T = V[ok].astype(np.int64)
     assert T.shape[0] == n ** 3
     return T
 
