@@ -372,8 +372,9 @@ mfs_status mfs_mmoc(mfs_problem* prob, const double* T, const double* u_new, con
 /* One temperature step (Sec. 3 and Sec. 6): u* and T* by linear extrapolation (Eq.
  * Extrapolation), T0_hat = MMOC(T_n, u*, u_n, tau_np1), Tm_hat = MMOC(MMOC(T_nm1, u*, u_n,
  * tau_np1), u_n, u_nm1, tau_n), then Eq. (WeakTemp) for T_np1 with the Dirichlet values of T_bc
- * on both spheres, solved by FGMRES (FP64) preconditioned by an FP32 Jacobi-CG on
- * s1 M + tau k/(Pe Cp) D_s.  T_*: [n_p2], u_*: [3][n_p2], FP64 device vectors.
+ * on both spheres — without its advection term: the MMOC values carry the advection, and the
+ * solve is the energy equation without it (Sec. 3) — by FGMRES (FP64) preconditioned by an
+ * FP32 Jacobi-CG on s1 M + tau k/(Pe Cp) D_s.  T_*: [n_p2], u_*: [3][n_p2], FP64 device vectors.
  * Errors: MFS_EINVAL, MFS_ENOTCONV (best iterate returned), MFS_ENAN, MFS_ENOMEM, MFS_ECUDA. */
 mfs_status mfs_temperature_step(mfs_problem* prob, const mfs_temp_params* params, const double* T_n,
                                 const double* T_nm1, const double* u_n, const double* u_nm1, double tau_np1,

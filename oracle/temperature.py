@@ -15,8 +15,7 @@ Paper passages followed (arxiv 2506.04157):
         T^n_hat = MMOC(T^n, u*^{n+1}, u^n, tau^{n+1}),
         T^{n-1}_hat = MMOC(MMOC(T^{n-1}, u*^{n+1}, u^n, tau^{n+1}), u^n, u^{n-1}, tau^n).
   * Sec. 6, Eq. (WeakTemp): for all w in the P2 space vanishing on both spheres,
-      int s1 T w + tau (int (u*.grad T) w + k/(Pe Cp) int grad T . grad(w/rho)
-                        - Di alpha/Cp int T (u*.g) w)
+      int s1 T w + tau (k/(Pe Cp) int grad T . grad(w/rho) - Di alpha/Cp int T (u*.g) w)
         = int (s0 T0_hat - sm Tm_hat) w
           + tau (H/Cp int w + Pe Di/(Ra Cp) int (1/rho) 2 eta(x, T*) eps(u*):eps(u*) w),
     with Dirichlet values on the surface and the CMB; g = -x/|x|.
@@ -25,6 +24,12 @@ Readings:
   * Eq. (WeakTemp) as printed multiplies the s0/sm terms by tau^{n+1} as well; dividing
     D[.]/tau^{n+1} out of Eq. (DiffSolve) leaves them without it, and only that form is
     consistent (a steady field must be a fixed point, and the BDF2 coefficients sum to 0).
+  * Eqs. (DiffSolve) and (WeakTemp) as printed keep an advection term u*.grad T in the solve,
+    while Sec. 3 calls that solve the rest of the splitting step, the energy equation without
+    the advection: the MMOC values already follow the characteristics, so D[.]/tau is the
+    material derivative.  With the term the scheme advects twice and converges to another
+    equation (a manufactured rotation test keeps an O(1) error as tau -> 0), contradicting
+    the second-order convergence of Sec. 7.1; the solve omits it.
   * Quadrature: the P2 mass is of degree 4, beyond the 4-point rule of the Stokes blocks (with
     it the element mass has rank 4 of 10).  All temperature forms use Stroud's conical
     product rule with 3 Gauss-Jacobi points per direction (27 points, exact to degree 5,
@@ -190,17 +195,19 @@ class TemperatureOperators:
 
 
 def temperature_matrix(ops, u_star, tau_np1, tau_n, params):
-    """Left-hand side of Eq. (WeakTemp): s1 M + tau (C(u*) + k/(Pe Cp) D - Di alpha/Cp R(u*))."""
+    """Left-hand side of Eq. (WeakTemp) without the advection term (reading above):
+    s1 M + tau (k/(Pe Cp) D - Di alpha/Cp R(u*))."""
     p = dict(DEFAULT_PARAMS, **(params or {}))
     s1, _, _ = bdf2_coefficients(tau_np1, tau_n)
     tau = float(tau_np1)
-    return s1 * ops.M + tau * (ops.advection(u_star) + (p["k"] / (p["Pe"] * p["Cp"])) * ops.D
+    return s1 * ops.M + tau * ((p["k"] / (p["Pe"] * p["Cp"])) * ops.D
                                - (p["Di"] * p["alpha"] / p["Cp"]) * ops.adiabatic(u_star))
 
 
-def temperature_rhs(ops, T0_hat, Tm_hat, u_star, tau_np1, tau_n, params, T_star=None, law=None):
+def temperature_rhs(ops, T0_hat, Tm_hat, u_star, tau_np1, tau_n, params, T_star=None, law=None, load=None):
     """Right-hand side of Eq. (WeakTemp) (reading: no tau on the s0/sm terms); the shear
-    heating enters when Di != 0 and a viscosity law is given."""
+    heating enters when Di != 0 and a viscosity law is given; `load` (int f phi_i of an extra
+    source f, e.g. of a manufactured solution) is added times tau."""
     p = dict(DEFAULT_PARAMS, **(params or {}))
     _, s0, sm = bdf2_coefficients(tau_np1, tau_n)
     tau = float(tau_np1)
@@ -208,14 +215,17 @@ def temperature_rhs(ops, T0_hat, Tm_hat, u_star, tau_np1, tau_n, params, T_star=
     rhs = rhs + tau * (p["H"] / p["Cp"]) * (ops.M @ np.ones(ops.level.n_p2))
     if law is not None and p["Di"] != 0.0:
         rhs = rhs + tau * (p["Pe"] * p["Di"] / (p["Ra"] * p["Cp"])) * ops.shear_heating(u_star, T_star, law)
+    if load is not None:
+        rhs = rhs + tau * np.asarray(load)
     return rhs
 
 
-def solve_temperature(ops, T0_hat, Tm_hat, u_star, tau_np1, tau_n, params, T_bc, T_star=None, law=None):
+def solve_temperature(ops, T0_hat, Tm_hat, u_star, tau_np1, tau_n, params, T_bc, T_star=None, law=None,
+                      load=None):
     """T^{n+1} of Eq. (WeakTemp) with Dirichlet values T_bc on both spheres, by a sparse
     direct solve."""
     L = temperature_matrix(ops, u_star, tau_np1, tau_n, params)
-    rhs = temperature_rhs(ops, T0_hat, Tm_hat, u_star, tau_np1, tau_n, params, T_star, law)
+    rhs = temperature_rhs(ops, T0_hat, Tm_hat, u_star, tau_np1, tau_n, params, T_star, law, load)
     bnd = ops.boundary
     Tb = np.where(bnd, np.asarray(T_bc, dtype=np.float64), 0.0)
     rhs = rhs - L @ Tb
@@ -317,12 +327,12 @@ def mmoc(loc, T, u_new, u_old, tau):
     return loc.eval_p2(T, mmoc_departure(loc, u_new, u_old, tau))
 
 
-def temperature_step(ops, loc, T_n, T_nm1, u_n, u_nm1, tau_np1, tau_n, params, T_bc, law=None):
+def temperature_step(ops, loc, T_n, T_nm1, u_n, u_nm1, tau_np1, tau_n, params, T_bc, law=None, load=None):
     """One temperature step of Sec. 3 and Sec. 6: extrapolations, the two MMOC evaluations,
     and the solve of Eq. (WeakTemp).  Returns (T^{n+1}, u*^{n+1}, T*^{n+1})."""
     u_star = extrapolate(u_n, u_nm1, tau_np1, tau_n)
     T_star = extrapolate(T_n, T_nm1, tau_np1, tau_n)
     T0_hat = mmoc(loc, T_n, u_star, u_n, tau_np1)
     Tm_hat = mmoc(loc, mmoc(loc, T_nm1, u_star, u_n, tau_np1), u_n, u_nm1, tau_n)
-    T_np1 = solve_temperature(ops, T0_hat, Tm_hat, u_star, tau_np1, tau_n, params, T_bc, T_star, law)
+    T_np1 = solve_temperature(ops, T0_hat, Tm_hat, u_star, tau_np1, tau_n, params, T_bc, T_star, law, load)
     return T_np1, u_star, T_star

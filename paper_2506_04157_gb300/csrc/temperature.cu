@@ -13,7 +13,9 @@
 //    location in the blended shell (face by the largest e.n, inverse blending, macro Kuhn
 //    coordinates, Freudenthal cube and type);
 //  * the solve: FGMRES in FP64 preconditioned by a Jacobi-CG in FP32 on the symmetric part
-//    s1 M + tau k/(Pe Cp) D_s of the left-hand side.
+//    s1 M + tau k/(Pe Cp) D_s of the left-hand side.  The left-hand side has no advection
+//    block: Sec. 3 solves the energy equation without the advection after the MMOC (the
+//    printed u*.grad T term would advect twice and break the second-order convergence).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -849,7 +851,8 @@ static mfs_status temp_fgmres(mfs_problem* Pb, TempWork* W, const mfs_temp_param
   cudaStream_t s = Pb->mesh->ctx->stream;
   const int64_t n = W->n2;
   const int m = tp.restart;
-  const double cC = tau, cD = tau * tp.k / (tp.Pe * tp.Cp), cR = -tau * tp.Di * tp.alpha / tp.Cp;
+  // the solve has no advection block: the MMOC history values carry the advection
+  const double cC = 0.0, cD = tau * tp.k / (tp.Pe * tp.Cp), cR = -tau * tp.Di * tp.alpha / tp.Cp;
   // Jacobi diagonal of the preconditioner's operator (FP32)
   MFS_TRY(temp_apply<float>(Pb, W, (float)s1, 0.f, (float)cD, 0.f, 1, 1, nullptr, nullptr, W->d32, 1));
   Blas<float>::recip(n, W->d32, s);
@@ -1044,7 +1047,7 @@ mfs_status mfs_temperature_step(mfs_problem* Pb, const mfs_temp_params* params, 
   // right-hand side, then the Dirichlet values moved to it
   MFS_TRY(temp_rhs(Pb, tp, W->T0h, W->Tmh, W->ustar, W->Tstar, tau_np1, tau_n, W->b));
   const double s1 = (2 * tau_np1 + tau_n) / (tau_np1 + tau_n);
-  const double cC = tau_np1, cD = tau_np1 * tp.k / (tp.Pe * tp.Cp), cR = -tau_np1 * tp.Di * tp.alpha / tp.Cp;
+  const double cC = 0.0, cD = tau_np1 * tp.k / (tp.Pe * tp.Cp), cR = -tau_np1 * tp.Di * tp.alpha / tp.Cp;
   Blas<double>::fill(n, 0.0, W->xb, s);
   if (W->nb) k_set_at<<<tblk(W->nb), 256, 0, s>>>(W->nb, W->bids, T_bc, W->xb);
   MFS_TRY(temp_apply<double>(Pb, W, s1, cC, cD, cR, 0, 0, W->ustar, W->xb, W->w, 0));
