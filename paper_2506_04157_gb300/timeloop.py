@@ -4,7 +4,8 @@ on every level, the buoyancy load of Eq. (StokesSub) and the Stokes solve.
 
 Orchestration only: every step is a call into the library (its kernels); the state lives in
 FP64 device tensors.  With g = -x/|x| the momentum right-hand side is the buoyancy load
-(Ra alpha / Pe) int rho (T - T_ref) x/|x| . phi; the velocity has zero Dirichlet values."""
+(Ra alpha / Pe) int rho (T - T_ref) x/|x| . phi; the velocity's Dirichlet values are zero or
+a prescribed field (plate velocities on the surface, Sec. 7.2)."""
 from __future__ import annotations
 
 import torch
@@ -15,7 +16,7 @@ class CoupledStepper:
     (set_density) are set.  temp_params: mfs_temp_params fields (k, Pe, Cp, Di, alpha, H, Ra,
     tolerances); solve_opts: mfs_solve_opts fields for the Stokes solves."""
 
-    def __init__(self, problem, temp_params=None, solve_opts=None, l_min=1, T_ref=None):
+    def __init__(self, problem, temp_params=None, solve_opts=None, l_min=1, T_ref=None, u_bc=None):
         self.prob = problem
         self.tp = dict(temp_params or {})
         self.opts = dict(solve_opts or {})
@@ -28,6 +29,8 @@ class CoupledStepper:
         self.f = torch.zeros(nu, dtype=torch.float64, device=dev)
         self.g = torch.zeros(npp, dtype=torch.float64, device=dev)
         self._Td = torch.zeros(self.n2, dtype=torch.float64, device=dev)
+        # Dirichlet values of the velocity ([3][n_p2]; read at the Dirichlet nodes only)
+        self.u_bc = torch.zeros(nu, dtype=torch.float64, device=dev) if u_bc is None else u_bc
 
     def stokes(self, T, u, p):
         """(u, p) for the temperature T in place (u, p hold the initial guess); returns the
@@ -38,7 +41,7 @@ class CoupledStepper:
         torch.sub(T, self.T_ref, out=self._Td)
         scale = self.tp.get("Ra", 1.0) * self.tp.get("alpha", 1.0) / self.tp.get("Pe", 1.0)
         pr.rhs_buoyancy(self._Td, self.f, scale)
-        u.zero_()      # zero Dirichlet values
+        u.copy_(self.u_bc)   # initial guess carrying the Dirichlet values
         return pr.solve(self.f, self.g, u, p, **self.opts)
 
     def step(self, state, tau_np1, tau_n, T_bc):
