@@ -405,17 +405,27 @@ def profile_solve(level):
                       "vcycles": st["vcycles"], "status": st["status"]}))
 
 
+_ORACLE_WORKLOADS = {}
+
+
+def _oracle_workload(level):
+    """The oracle's level, viscosity and inputs of the bench workload (built once; not timed)."""
+    if level not in _ORACLE_WORKLOADS:
+        import workloads as W
+        from oracle.mesh import MacroMesh, Level
+        L = Level(MacroMesh(), level)
+        _ORACLE_WORKLOADS[level] = (L, W.viscosity_plumes(L.p1_x, seed=2, contrast=1e6),
+                                    W.random_field(3 * L.n_p2, 1), W.random_field(L.n_p1, 2))
+    return _ORACLE_WORKLOADS[level]
+
+
 def cpu_baseline(level, budget_s=12.0):
     """The FP64 oracle's fused apply on a bounded sample of micro-tets of the same
     workload, scaled to the full level (GDoF/s)."""
     import numpy as np
     import workloads as W
-    from oracle.mesh import MacroMesh, Level
     from oracle.fem import stokes_apply_elements
-    L = Level(MacroMesh(), level)
-    eta = W.viscosity_plumes(L.p1_x, seed=2, contrast=1e6)
-    u = W.random_field(3 * L.n_p2, 1)
-    p = W.random_field(L.n_p1, 2)
+    L, eta, u, p = _oracle_workload(level)
     ntet = L.tet_p2.shape[0]
     chunk = 4096
     done, t_used = 0, 0.0
@@ -431,6 +441,38 @@ def cpu_baseline(level, budget_s=12.0):
     return {"value": round(dofs / t_full / 1e9, 6), "unit": "GDoF/s", "cores": 1, "kind": "oracle",
             "sample": f"{done} of {ntet} micro-tets (random), {t_used:.1f} s, scaled to one full apply",
             "dofs_per_apply": dofs}
+
+
+def oracle_levels(budget_s=3.0):
+    """The oracle at the configured sizes it can run here: the fused apply at levels 2-4 (full
+    sweeps, level 4 sampled within budget_s) and the solve to 1e-8 of the level-2 shell
+    (config 1: radial viscosity, d ln rho/dr = -1; symmetric Uzawa, V-cycle BFBT, FGMRES)."""
+    import numpy as np
+    import workloads as W
+    from oracle.mesh import MacroMesh, Level
+    from oracle.fem import stokes_apply_elements
+    from oracle.solver import Hierarchy, StokesOracle
+    out = {}
+    for lvl in (2, 3, 4):
+        L = Level(MacroMesh(), lvl)
+        eta = W.viscosity_plumes(L.p1_x, seed=2, contrast=1e6)
+        u, p = W.random_field(3 * L.n_p2, 1), W.random_field(L.n_p1, 2)
+        ntet = L.tet_p2.shape[0]
+        sel = np.arange(ntet) if lvl < 4 else np.arange(min(ntet, 16384))
+        t0 = time.perf_counter()
+        stokes_apply_elements(L, eta, W.dlnrho_table_compressible(), u, p, sel)
+        dt = (time.perf_counter() - t0) * ntet / len(sel)
+        out[f"apply_L{lvl}_gdofs"] = round((3 * L.n_p2 + L.n_p1) / dt / 1e9, 7)
+    mesh = MacroMesh()
+    L2 = Level(mesh, 2)
+    H = Hierarchy(mesh, 2, W.viscosity_radial(L2.p1_x), dlnrho_table=W.dlnrho_table_config1())
+    f = W.random_field(3 * L2.n_p2, 3)
+    t0 = time.perf_counter()
+    _, _, it, _ = StokesOracle(H).solve(f, np.zeros(L2.n_p1), np.zeros(3 * L2.n_p2), np.zeros(L2.n_p1), rtol=1e-8)
+    out["solve_L2_s"] = round(time.perf_counter() - t0, 2)
+    out["solve_L2_fgmres_iters"] = int(it)
+    out["cores"] = 1
+    return out
 
 
 def run_reference(args, rank, world):
@@ -450,6 +492,7 @@ def run_reference(args, rank, world):
             "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD, "level": args.level},
             "cpu_baseline": cb,
+            "oracle_levels": oracle_levels(),
             "e2e": {"value": v, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
