@@ -443,6 +443,41 @@ def cpu_baseline(level, budget_s=12.0):
             "dofs_per_apply": dofs}
 
 
+def _sample_worker(level, budget_s, seed):
+    """One process of the all-cores CPU baseline: (micro-tets swept, seconds)."""
+    import numpy as np
+    import workloads as W
+    from oracle.fem import stokes_apply_elements
+    L, eta, u, p = _oracle_workload(level)
+    ntet = L.tet_p2.shape[0]
+    rng = np.random.default_rng(seed)
+    done, t_used = 0, 0.0
+    while t_used < budget_s:
+        sel = np.sort(rng.choice(ntet, size=4096, replace=False))
+        t0 = time.perf_counter()
+        stokes_apply_elements(L, eta, W.dlnrho_table_compressible(), u, p, sel)
+        t_used += time.perf_counter() - t0
+        done += 4096
+    return done, t_used
+
+
+def cpu_baseline_all_cores(level, budget_s=3.0, max_procs=16):
+    """The same sampled oracle apply in one process per host core (spawned; each builds its
+    own copy of the level), throughput summed over the processes (GDoF/s), or None."""
+    import multiprocessing as mp
+    n = max(1, min(os.cpu_count() or 1, max_procs))
+    try:
+        with mp.get_context("spawn").Pool(n) as pool:
+            res = pool.starmap(_sample_worker, [(level, budget_s, 1000 + k) for k in range(n)])
+    except Exception as e:   # reported, not fatal: the one-core baseline stands
+        return {"error": f"{type(e).__name__}: {e}"}
+    L, _, _, _ = _oracle_workload(level)
+    tets_per_s = sum(d / t for d, t in res)
+    dofs = 3 * L.n_p2 + L.n_p1
+    return {"value": round(dofs * tets_per_s / L.tet_p2.shape[0] / 1e9, 6), "unit": "GDoF/s", "cores": n,
+            "kind": "oracle", "sample": f"{n} processes x {budget_s:.0f} s of random 4096-tet chunks"}
+
+
 def oracle_levels(budget_s=3.0):
     """The oracle at the configured sizes it can run here: the fused apply at levels 2-4 (full
     sweeps, level 4 sampled within budget_s) and the solve to 1e-8 of the level-2 shell
@@ -493,6 +528,7 @@ def run_reference(args, rank, world):
             "config": {"workload": WORKLOAD, "level": args.level},
             "cpu_baseline": cb,
             "oracle_levels": oracle_levels(),
+            "cpu_baseline_all_cores": cpu_baseline_all_cores(args.level),
             "e2e": {"value": v, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
