@@ -427,7 +427,7 @@ def cpu_baseline(level, budget_s=12.0):
     from oracle.fem import stokes_apply_elements
     L, eta, u, p = _oracle_workload(level)
     ntet = L.tet_p2.shape[0]
-    chunk = 4096
+    chunk = min(4096, ntet)
     done, t_used = 0, 0.0
     rng = np.random.default_rng(0)
     while t_used < budget_s and done < ntet:
@@ -452,12 +452,13 @@ def _sample_worker(level, budget_s, seed):
     ntet = L.tet_p2.shape[0]
     rng = np.random.default_rng(seed)
     done, t_used = 0, 0.0
+    chunk = min(4096, ntet)
     while t_used < budget_s:
-        sel = np.sort(rng.choice(ntet, size=4096, replace=False))
+        sel = np.sort(rng.choice(ntet, size=chunk, replace=False))
         t0 = time.perf_counter()
         stokes_apply_elements(L, eta, W.dlnrho_table_compressible(), u, p, sel)
         t_used += time.perf_counter() - t0
-        done += 4096
+        done += chunk
     return done, t_used
 
 

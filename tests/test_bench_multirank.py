@@ -42,3 +42,25 @@ def test_two_rank_aggregation():
         ms_per_step, value = res[rank]
         assert ms_per_step == pytest.approx(25.0)
         assert value == pytest.approx(2 * 1_000_000 / 0.025 / 1e9)
+
+
+def test_reference_arm_json_line():
+    """bench.py --impl reference (the FP64 oracle on the host cores) prints one JSON line with
+    the contract's keys, at a small level so the check stays short."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--level", "2",
+                          "--steps", "2", "--warmup", "1", "--cpu-seconds", "1"],
+                         capture_output=True, text=True, timeout=600, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "GDoF/s" and d["value"] > 0 and d["higher_is_better"]
+    assert d["steps"] == 2 and d["warmup"] == 1 and d["ms_per_step"] > 0
+    assert {"value", "unit", "cores", "kind", "sample"} <= set(d["cpu_baseline"]) and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+    assert {"apply_L2_gdofs", "apply_L3_gdofs", "apply_L4_gdofs", "solve_L2_s"} <= set(d["oracle_levels"])
+    assert d["cpu_baseline_all_cores"]["value"] > 0 and d["cpu_baseline_all_cores"]["cores"] >= 1
