@@ -341,3 +341,21 @@ def test_second_order_in_time_with_mmoc_advection():
     assert e2 / e4 > 3.5 and e4 < 6e-3, (e2, e4)
     d2, d4 = run(2, True), run(4, True)
     assert d4 > 10 * e4 and d2 / d4 < 1.2, (d2, d4)
+
+
+def test_model_numbers_and_initial_temperature():
+    """The workload's model numbers are the paper's Table dimtable values (tests/golden), the
+    compressibility gamma = Di / Gamma0, and the initial temperature is the adiabat with 3 %
+    relative noise: within the band, reproducible per seed."""
+    import json
+    import os
+    import workloads as W
+    gold = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "model_numbers.json")))
+    assert (W.MODEL_RA, W.MODEL_DI, W.MODEL_PE) == (gold["Ra"], gold["Di"], gold["Pe"])
+    assert abs(gold["Di"] / gold["Gamma0"] - gold["gamma"]) < 1e-4 and W.GAMMA_COMPRESSIBLE == gold["gamma"]
+    assert W.T_ADIABATIC_ND == gold["T_adiabatic_K"] / gold["DeltaT_K"]
+    Lv = Level(MacroMesh(), 1)
+    T = W.temperature_adiabat(Lv.p2_x, 5)
+    ts = W.T_ADIABATIC_ND * np.exp(W.MODEL_DI * (1.0 - np.linalg.norm(Lv.p2_x, axis=1)))
+    assert np.all(np.abs(T / ts - 1.0) <= gold["noise"] + 1e-15)
+    assert np.array_equal(T, W.temperature_adiabat(Lv.p2_x, 5)) and not np.array_equal(T, W.temperature_adiabat(Lv.p2_x, 6))

@@ -91,3 +91,17 @@ WORKLOADS = {
     "shell-L6-contrast1e6": dict(level=6, viscosity="plumes", contrast=1e6, eta_seed=2,
                                  T_seed=3, dlnrho="compressible"),
 }
+
+
+# nondimensional numbers of the paper's mantle model (Table dimtable)
+MODEL_RA, MODEL_DI, MODEL_PE = 1.692e7, 0.4538, 2.822e4
+T_ADIABATIC_ND = 1600.0 / 3900.0     # T_adiabatic / Delta T
+
+
+def temperature_adiabat(x, seed, di=MODEL_DI, t_adiabatic=T_ADIABATIC_ND, noise=0.03):
+    """Initial temperature of the paper's model (Sec. 7.2): the reference adiabat
+    T^s = T_adiabatic exp(Di (r_surf - |x|)) times (1 + noise U(-1, 1)) per node (seeded)."""
+    rng = np.random.default_rng(seed)
+    ts = t_adiabatic * np.exp(di * (R_SURF - radius(x)))
+    return ts * (1.0 + noise * rng.uniform(-1.0, 1.0, ts.shape))
+
