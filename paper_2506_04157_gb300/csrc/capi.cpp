@@ -272,19 +272,6 @@ mfs_status mfs_mesh_info(const mfs_mesh* M, int lvl, mfs_level_info* out) {
   return MFS_OK;
 }
 
-// Visit every lattice point of every macro at N intervals: f(m, i[4], id).
-template <typename F>
-static void for_each_point(const mfs_mesh* M, int N, F f) {
-  const Numbering nb = make_numbering(N);
-  for (int m = 0; m < 60; ++m)
-    for (int i3 = 0; i3 <= N; ++i3)
-      for (int i2 = 0; i2 <= N - i3; ++i2)
-        for (int i1 = 0; i1 <= N - i3 - i2; ++i1) {
-          const int i[4] = {N - i1 - i2 - i3, i1, i2, i3};
-          f(m, i, lattice_id(M->host.topo[m], nb, m, i[0], i[1], i[2], i[3]));
-        }
-}
-
 mfs_status mfs_mesh_coords(const mfs_mesh* M, int lvl, int p2, int blended, double* xyz) {
   MFS_TRY(check_level(M, lvl));
   if (!xyz) {

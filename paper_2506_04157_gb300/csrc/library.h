@@ -112,6 +112,22 @@ struct mfs_mesh {
   int tuning_gen = 0;   // bumped when a level's sweep variant changes (captured graphs go stale)
 };
 
+namespace mfs {
+// Visit every lattice point of every macro at N intervals: f(m, i[4], id) with the point's
+// integer barycentrics i (sum N) in macro m and its global id.
+template <typename F>
+inline void for_each_point(const mfs_mesh* M, int N, F f) {
+  const Numbering nb = make_numbering(N);
+  for (int m = 0; m < 60; ++m)
+    for (int i3 = 0; i3 <= N; ++i3)
+      for (int i2 = 0; i2 <= N - i3; ++i2)
+        for (int i1 = 0; i1 <= N - i3 - i2; ++i1) {
+          const int i[4] = {N - i1 - i2 - i3, i1, i2, i3};
+          f(m, i, lattice_id(M->host.topo[m], nb, m, i[0], i[1], i[2], i[3]));
+        }
+}
+}  // namespace mfs
+
 struct mfs_problem {
   mfs_mesh* mesh = nullptr;
   int bc_surface = 0, bc_cmb = 1;

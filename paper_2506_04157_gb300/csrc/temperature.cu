@@ -553,19 +553,6 @@ struct TempWork {
   std::vector<void*> owned;
 };
 
-// Visit every lattice point of every macro at N intervals: f(m, i[4], id).
-template <typename F>
-static void visit_points(const mfs_mesh* M, int N, F f) {
-  const Numbering nb = make_numbering(N);
-  for (int m = 0; m < 60; ++m)
-    for (int i3 = 0; i3 <= N; ++i3)
-      for (int i2 = 0; i2 <= N - i3; ++i2)
-        for (int i1 = 0; i1 <= N - i3 - i2; ++i1) {
-          const int i[4] = {N - i1 - i2 - i3, i1, i2, i3};
-          f(m, i, lattice_id(M->host.topo[m], nb, m, i[0], i[1], i[2], i[3]));
-        }
-}
-
 // the rule's constant-memory copy, uploaded once per device
 static std::mutex g_rule_mutex;
 static std::vector<char> g_rule_ready;
@@ -624,7 +611,7 @@ static mfs_status temp_work(mfs_problem* Pb, int m, TempWork** out) {
   const int N = 2 << L;
   std::vector<double> xyz(3 * (size_t)n2);
   std::vector<int> bids;
-  visit_points(M, N, [&](int mc, const int* i, int id) {
+  for_each_point(M, N, [&](int mc, const int* i, int id) {
     double xs[3], x[3];
     M->host.straight_point(mc, i, N, xs);
     if (M->host.blending) M->host.blend_point(mc, xs, x);
@@ -632,7 +619,7 @@ static mfs_status temp_work(mfs_problem* Pb, int m, TempWork** out) {
     for (int r = 0; r < 3; ++r) xyz[r * (size_t)n2 + id] = x[r];
   });
   std::vector<char> seen(n2, 0);
-  visit_points(M, N, [&](int mc, const int* i, int id) {
+  for_each_point(M, N, [&](int mc, const int* i, int id) {
     const int mask = (i[0] > 0) | ((i[1] > 0) << 1) | ((i[2] > 0) << 2) | ((i[3] > 0) << 3);
     const MacroTopo& t = M->host.topo[mc];
     const bool on = ((mask & ~t.topmask & 15) == 0) || ((mask & ~t.botmask & 15) == 0);

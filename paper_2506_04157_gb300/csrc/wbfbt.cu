@@ -22,6 +22,7 @@
 #include "library.h"
 #include "qp_geometry.cuh"
 #include "solver.h"
+#include "sweep_params.cuh"
 
 namespace mfs {
 
@@ -334,24 +335,6 @@ __global__ void k_pcheb_next(int64_t n, const T* __restrict__ t, T* __restrict__
 }
 
 // ------------------------------------------------------------------------- host side
-template <typename T>
-static ApplyParams<T> wb_params(mfs_problem* P, int lvl) {
-  mfs_mesh* M = P->mesh;
-  const LevelData& L = M->levels[lvl];
-  ApplyParams<T> prm{};
-  prm.eta = lvl_eta<T>(P, lvl);
-  prm.geom = lvl_geom<T>(M);
-  prm.tiles = L.d_tiles;
-  prm.tets = L.d_tets;
-  prm.classes = L.d_classes;
-  prm.ids2 = L.d_ids2;
-  prm.ids1 = L.d_ids1;
-  prm.n_p2 = L.nb2.total;
-  prm.n_p1 = L.nb1.total;
-  prm.n = L.n;
-  prm.r_cmb = (T)M->host.r_cmb;
-  return prm;
-}
 
 template <typename T>
 static PoissonWork<T>& pwork(PoissonMG* W);
@@ -479,7 +462,7 @@ mfs_status poisson_apply(mfs_problem* Pb, int side, int lvl, const T* p, T* y) {
   cudaStream_t s = Pb->mesh->ctx->stream;
   MFS_CUDA(cudaMemsetAsync(y, 0, sizeof(T) * (size_t)Lv.nb1.total, s));
   dim3 grid(Lv.n_tiles, kMacroCells);
-  k_poisson_sweep<T, false><<<grid, 128, 0, s>>>(wb_params<T>(Pb, lvl), side_kw<T>(S, lvl), p, y);
+  k_poisson_sweep<T, false><<<grid, 128, 0, s>>>(sweep_params<T>(Pb, lvl), side_kw<T>(S, lvl), p, y);
   MFS_CUDA(cudaGetLastError());
   return MFS_OK;
 }
@@ -491,7 +474,7 @@ static mfs_status lumped_into(mfs_problem* Pb, double a, double* d) {
   cudaStream_t s = M->ctx->stream;
   MFS_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * (size_t)Lv.nb2.total, s));
   dim3 grid(Lv.n_tiles, kMacroCells);
-  const ApplyParams<double> prm = wb_params<double>(Pb, L);
+  const ApplyParams<double> prm = sweep_params<double>(Pb, L);
   if (M->host.blending) k_vmass_lumped<true><<<grid, 128, 0, s>>>(prm, a * a, d);
   else k_vmass_lumped<false><<<grid, 128, 0, s>>>(prm, a * a, d);
   MFS_CUDA(cudaGetLastError());
@@ -510,7 +493,7 @@ static mfs_status side_numeric(mfs_problem* Pb, int side) {
     const LevelData& Lv = M->levels[l];
     const int64_t n1 = Lv.nb1.total, cnt = poisson_weight_count(Lv);
     dim3 grid(Lv.n_tiles, kMacroCells);
-    const ApplyParams<double> prm = wb_params<double>(Pb, l);
+    const ApplyParams<double> prm = sweep_params<double>(Pb, l);
     MFS_CUDA(cudaMemsetAsync(S.kw64[l], 0, sizeof(double) * (size_t)cnt, s));
     if (M->host.blending) k_poisson_weights<true><<<grid, 128, 0, s>>>(prm, S.a * S.a, S.kw64[l]);
     else k_poisson_weights<false><<<grid, 128, 0, s>>>(prm, S.a * S.a, S.kw64[l]);
