@@ -51,7 +51,7 @@ from .fem import (Operators, Constraints, ConstrainedOperators, project_mean_zer
 
 DEFAULTS = dict(sigma=1.0, omega=0.3, tol_A=1e-2, m_A=3, deg_A=2, tol_VBFBT=1e-1,
                 tol_invMass=1e-10, m_V=1, deg_V=1, tol_coarse=1e-2,
-                uzawa="symmetric", schur="vbfbt", a_l=1.0, a_r=1.0)
+                uzawa="symmetric", schur="vbfbt", a_l=1.0, a_r=1.0, wbfbt_mass="consistent")
 
 
 # ------------------------------------------------------------------------- transfers
@@ -324,8 +324,10 @@ class StokesOracle:
         if self.p["schur"] == "wbfbt":
             from .wbfbt import WbfbtOperators
             eta = hier.etas[L]
-            self.wr = WbfbtOperators(hier.levels[L], eta, self.p["a_r"])
-            self.wl = self.wr if self.p["a_l"] == self.p["a_r"] else WbfbtOperators(hier.levels[L], eta, self.p["a_l"])
+            mass = self.p["wbfbt_mass"]
+            self.wr = WbfbtOperators(hier.levels[L], eta, self.p["a_r"], mass=mass)
+            self.wl = self.wr if self.p["a_l"] == self.p["a_r"] else WbfbtOperators(hier.levels[L], eta, self.p["a_l"],
+                                                                                     mass=mass)
 
     # blocks of the constrained system
     def K(self, x):

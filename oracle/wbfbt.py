@@ -1,6 +1,6 @@
 """Oracle of the weighted BFBT Schur approximation: the inverse-square-root-viscosity P1
-Laplacian K_{1/sqrt(eta)}, the square-root-viscosity lumped vector mass M_{sqrt(eta)} and
-their composition.
+Laplacian K_{1/sqrt(eta)}, the square-root-viscosity vector mass M_{sqrt(eta)} (consistent or
+lumped) and their composition.
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).  FP64, assembled scipy matrices.
 
@@ -16,10 +16,13 @@ Paper passages followed (arxiv 2506.04157):
   * Table parametertable: tol_wBFBT = 1e-10, a_l = a_r = 1.
 
 Readings:
-  * "Potentially lumped" vector mass: lumped by the diagonal scaling of Hinton, Rock and
-    Zienkiewicz (1976): each element's consistent-mass diagonal, scaled so that it keeps the
-    element's total mass.  (Row-sum lumping gives P2 vertices negative mass.)  The same
-    diagonal acts on all three velocity components.
+  * Vector mass M_{sqrt(eta)}: the paper allows a lumped one but solves it by CG to
+    tol_VectorMass, i.e. the consistent mass.  Both are built: consistent (P2 scalar mass with
+    weight sqrt(eta_a), the degree-5 conical rule since the P2 mass is of degree 4, the same
+    matrix for every velocity component, inverted exactly on the constrained velocity space,
+    (P0 M P0 + I - P0)^-1 P0: the limit of the CG) is the solver's default; lumped by the diagonal scaling of Hinton, Rock and Zienkiewicz (1976)
+    (each element's consistent-mass diagonal scaled to keep the element's total mass; row-sum
+    lumping gives P2 vertices negative mass) is the alternative the library implements.
   * The K solves (tolerance 1e-10 in the paper) are exact here: a sparse direct solve on
     the mean-zero subspace, the constant null space of the Neumann problem removed by a
     Lagrange multiplier.
@@ -37,6 +40,7 @@ import scipy.sparse.linalg as spla
 
 from .mesh import CLASS_SURFACE
 from .fem import Geometry, QUAD_BARY, assemble, velocity_dofs, project_mean_zero
+from .temperature import GeometryRule, QUAD5_BARY
 
 
 def surface_tets(level):
@@ -58,10 +62,12 @@ def element_lumped_mass_p2(geo, weight_q):
 
 
 class WbfbtOperators:
-    """K_{1/sqrt(eta_a)} (n_p1 x n_p1) and the lumped M_{sqrt(eta_a)} diagonal (n_p2) on one
-    level, eta_a = a^2 eta on D_eta and eta elsewhere (eta: nodal P1 viscosity)."""
+    """K_{1/sqrt(eta_a)} (n_p1 x n_p1), the lumped M_{sqrt(eta_a)} diagonal d (n_p2) and, with
+    mass="consistent", the consistent scalar M_{sqrt(eta_a)} (n_p2 x n_p2) on one level,
+    eta_a = a^2 eta on D_eta and eta elsewhere (eta: nodal P1 viscosity).  M_inv applies the
+    selected mass's inverse."""
 
-    def __init__(self, level, eta_p1, a=1.0, chunk=4096):
+    def __init__(self, level, eta_p1, a=1.0, chunk=4096, mass="lumped"):
         mesh = level.mesh
         eta_p1 = np.asarray(eta_p1, dtype=np.float64)
         surf = surface_tets(level)
@@ -79,6 +85,20 @@ class WbfbtOperators:
         self.K = sum(Ks[1:], Ks[0]).tocsr()
         self.d = d
         self.level = level
+        self.mass = mass
+        if mass == "consistent":
+            Ms = []
+            for s in range(0, E, chunk):
+                sl = slice(s, min(E, s + chunk))
+                geo = GeometryRule(mesh, level.tet_x[sl], level.tet_prism[sl])
+                etaq = eta_p1[level.tet_p1[sl]] @ QUAD5_BARY.T * np.where(surf[sl], a * a, 1.0)[:, None]
+                p2 = level.tet_p2[sl]
+                Ms.append(assemble(p2, p2, np.einsum("eq,qa,qb->eab", geo.W * np.sqrt(etaq), geo.phi, geo.phi),
+                                   (level.n_p2, level.n_p2)))
+            self.Mc = sum(Ms[1:], Ms[0]).tocsr()
+            self._mlu = {}
+        elif mass != "lumped":
+            raise ValueError(mass)
         n = level.n_p1
         one = sp.csr_matrix(np.ones((n, 1)))
         self._lu = spla.splu(sp.bmat([[self.K, one], [one.T, None]]).tocsc())
@@ -89,7 +109,15 @@ class WbfbtOperators:
         return project_mean_zero(self._lu.solve(rhs)[:-1])
 
     def M_inv(self, u, cons):
-        """Lumped M_{sqrt(eta_a)}^-1 on the constrained velocity space ([3][n_p2])."""
+        """M_{sqrt(eta_a)}^-1 (lumped or consistent) on the constrained velocity space ([3][n_p2])."""
+        if self.mass == "consistent":
+            key = id(cons)
+            if key not in self._mlu:   # (P0 M P0 + I - P0) on the three components
+                P0 = cons.Pv_matrix()
+                Mv = sp.block_diag([self.Mc] * 3).tocsr()
+                I = sp.identity(Mv.shape[0], format="csr")
+                self._mlu[key] = spla.splu((P0 @ Mv @ P0 + I - P0).tocsc())
+            return cons.P0(self._mlu[key].solve(cons.P0(u)))
         return cons.P0(np.asarray(u) / np.tile(self.d, 3))
 
 

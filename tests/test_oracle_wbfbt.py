@@ -192,3 +192,32 @@ def test_poisson_spectrally_equivalent_to_B_Minv_BT(level1_isoviscous):
         X = np.column_stack([co.apply_B(Wo.M_inv(co.apply_BT(e), cons)) for e in np.eye(n)])
         ev = np.linalg.eigvals(np.linalg.solve(Bm.T @ Wo.K.toarray() @ Bm, Bm.T @ X @ Bm)).real
         assert 0.1 < ev.min() and ev.max() < 3.0, (ev.min(), ev.max())
+
+
+def test_consistent_vector_mass():
+    """The consistent M_{sqrt(eta)} (degree-5 rule): f^T M g = sqrt(c) int f g for quadratics
+    f, g and eta = c on the polyhedral shell (against cone-by-cone integration of the two
+    icosahedra); symmetric positive definite; its constrained inverse inverts P0 M P0 on
+    constrained vectors."""
+    from oracle.temperature import conical_rule
+    from oracle.mesh import icosahedron
+    from oracle.fem import Constraints
+    Lv = Level(MacroMesh(blending=False), 1)
+    x = Lv.p2_x
+    f = lambda y: 1 + y[:, 0] - 2 * y[:, 1] * y[:, 2] + 0.5 * y[:, 0] ** 2
+    g = lambda y: y[:, 1] ** 2 - y[:, 2] + 0.3 * y[:, 0] * y[:, 1]
+    U, F = icosahedron()
+    bary, w = conical_rule(4)
+    ref = 0.0
+    for R, sgn in [(1.0, 1.0), (0.5, -1.0)]:
+        for (a, b, c) in F:
+            V = np.array([[0, 0, 0], R * U[a], R * U[b], R * U[c]])
+            y = bary @ V
+            ref += sgn * abs(np.linalg.det(np.stack([V[1] - V[0], V[2] - V[0], V[3] - V[0]], -1))) * (w * f(y) * g(y)).sum()
+    O = WbfbtOperators(Lv, np.full(Lv.n_p1, 4.0), mass="consistent")
+    assert abs(f(x) @ (O.Mc @ g(x)) - 2.0 * ref) <= 1e-12 * abs(ref)
+    assert abs(O.Mc - O.Mc.T).max() <= 1e-15 * abs(O.Mc).max()
+    cons = Constraints(Lv)
+    v = cons.P0(np.random.default_rng(3).standard_normal(3 * Lv.n_p2))
+    Mv = np.concatenate([O.Mc @ v.reshape(3, -1)[c] for c in range(3)])
+    assert np.abs(O.M_inv(cons.P0(Mv), cons) - v).max() <= 1e-10 * np.abs(v).max()
