@@ -257,6 +257,12 @@ typedef struct {
                          with a vertex on the outer surface (1, 1; Table parametertable) */
   double tol_wBFBT;   /* CG on K_{1/sqrt(eta)}, relative or absolute, whichever is met first
                          (1e-10; at least 1e-5 in FP32) */
+  int vmass;          /* weighted-BFBT vector mass M_{sqrt(eta)}: 0 the lumped mass (default),
+                         1 the consistent mass (mfs_apply_vmass) by Jacobi-preconditioned CG on
+                         the constrained velocity space to tol_VectorMass (Sec. 5.2.3); with
+                         schur = 3 the cg_M_* statistics count these CGs */
+  double tol_VectorMass; /* CG on the consistent M_{sqrt(eta)}, relative (1e-4; Table
+                         parametertable) */
 } mfs_solve_opts;
 
 typedef struct {
@@ -285,8 +291,9 @@ void mfs_solve_opts_default(mfs_solve_opts* opts);
  * The weighted BFBT (schur = 3; Sec. 5.2.3, Eq. schurWBFBT with the near-surface rescaling):
  *   S_w^-1 = K_{1/sqrt(eta_l)}^-1 (B M_{sqrt(eta_l)}^-1 A M_{sqrt(eta_r)}^-1 B^T) K_{1/sqrt(eta_r)}^-1,
  * K by CG preconditioned with its own geometric V-cycle (Chebyshev m_A, deg_A) to tol_wBFBT,
- * M the lumped vector mass (mfs_lumped_vmass).  Its operators are built on first use of a
- * scaling and after every coefficient change (allocates device memory).
+ * M the lumped vector mass (mfs_lumped_vmass; vmass = 0) or the consistent one
+ * (mfs_apply_vmass; vmass = 1) solved by CG to tol_VectorMass.  Its operators are built on
+ * first use of a scaling and after every coefficient change (allocates device memory).
  * Errors: MFS_EINVAL, MFS_ENAN, MFS_ENOMEM, MFS_ECUDA. */
 mfs_status mfs_apply_schur(mfs_problem* prob, const mfs_solve_opts* opts, mfs_prec prec, const void* r, void* z,
                            mfs_solve_stats* stats);
@@ -305,6 +312,15 @@ mfs_status mfs_apply_poisson(mfs_problem* prob, int lvl, mfs_prec prec, double a
  * per P2 node, the same for every velocity component.  d: [n_p2] FP64 device vector.
  * Errors: MFS_EINVAL, MFS_ECUDA. */
 mfs_status mfs_lumped_vmass(mfs_problem* prob, double a, double* d);
+
+/* y_c = M_{sqrt(eta_a)} x_c for the three velocity components c on the finest level: the
+ * consistent P2 scalar mass M_ij = sum_tets sum_q w_q |det J_q| sqrt(eta_a(x_q)) phi_j phi_i
+ * (Sec. 5.2.3, the vector mass weighted by the square root of the viscosity), eta_a as in
+ * mfs_apply_poisson, on the degree-5 conical rule (the P2 mass has degree 4; 27 points).  No
+ * boundary rows or columns are removed.  x, y: [3][n_p2] device vectors of prec (distinct).
+ * Needs the viscosity.  Errors: MFS_EINVAL (null argument, no viscosity, a not positive and
+ * finite), MFS_ECUDA. */
+mfs_status mfs_apply_vmass(mfs_problem* prob, mfs_prec prec, double a, const void* x, void* y);
 
 /* Solve the projected saddle-point system (paper Eq. SaddlePointStructureDirichlet) on
  * the finest level: f [3][n_p2] and g [n_p1] are the right-hand sides (FP64, device);

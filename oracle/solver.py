@@ -51,7 +51,8 @@ from .fem import (Operators, Constraints, ConstrainedOperators, project_mean_zer
 
 DEFAULTS = dict(sigma=1.0, omega=0.3, tol_A=1e-2, m_A=3, deg_A=2, tol_VBFBT=1e-1,
                 tol_invMass=1e-10, m_V=1, deg_V=1, tol_coarse=1e-2,
-                uzawa="symmetric", schur="vbfbt", a_l=1.0, a_r=1.0, wbfbt_mass="consistent")
+                uzawa="symmetric", schur="vbfbt", a_l=1.0, a_r=1.0, wbfbt_mass="consistent",
+                tol_wBFBT=1e-10, tol_VectorMass=1e-4)   # the last two: the oracle solves exactly
 
 
 # ------------------------------------------------------------------------- transfers

@@ -42,7 +42,7 @@ class SolveOpts(ctypes.Structure):
                 ("tol_invMass", ctypes.c_double), ("m_V", ctypes.c_int), ("deg_V", ctypes.c_int),
                 ("max_cg", ctypes.c_int), ("with_C", ctypes.c_int), ("uzawa", ctypes.c_int),
                 ("schur", ctypes.c_int), ("a_l", ctypes.c_double), ("a_r", ctypes.c_double),
-                ("tol_wBFBT", ctypes.c_double)]
+                ("tol_wBFBT", ctypes.c_double), ("vmass", ctypes.c_int), ("tol_VectorMass", ctypes.c_double)]
 
 
 class SolveStats(ctypes.Structure):
@@ -123,6 +123,7 @@ _SIGS = {
     "mfs_apply_schur": ([_vp, ctypes.POINTER(SolveOpts), _i, _vp, _vp, ctypes.POINTER(SolveStats)], _i),
     "mfs_apply_poisson": ([_vp, _i, _i, _d, _vp, _vp], _i),
     "mfs_lumped_vmass": ([_vp, _d, _vp], _i),
+    "mfs_apply_vmass": ([_vp, _i, _d, _vp, _vp], _i),
     "mfs_temp_params_default": ([ctypes.POINTER(TempParams)], None),
     "mfs_temp_apply": ([_vp, _i, _d, _d, _d, _d, _i, _i, _vp, _vp, _vp], _i),
     "mfs_temp_rhs": ([_vp, ctypes.POINTER(TempParams), _vp, _vp, _vp, _vp, _d, _d, _vp], _i),
@@ -326,6 +327,13 @@ class Problem:
         nu, _ = self._sizes(self.mesh.l_max)
         _need(d, nu // 3, torch.float64, "d")
         _check(lib().mfs_lumped_vmass(self.handle, float(a), _ptr(d)))
+
+    def apply_vmass(self, a, x, y):
+        """y = consistent M_{sqrt(eta_a)} x on the three velocity components ([3][n_p2], finest
+        level; FP64 or FP32, no boundary rows removed)."""
+        nu, _ = self._sizes(self.mesh.l_max)
+        _need(x, nu, None, "x"); _need(y, nu, x.dtype, "y")
+        _check(lib().mfs_apply_vmass(self.handle, _prec_of(x), float(a), _ptr(x), _ptr(y)))
 
     def prolongate(self, level, xc, xf):
         nf, _ = self._sizes(level)

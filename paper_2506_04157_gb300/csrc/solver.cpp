@@ -1034,6 +1034,36 @@ struct Stokes {
     st.cg_X_max = it > st.cg_X_max ? it : st.cg_X_max;
     return mean_free<T>(Pb, x, np);
   }
+  // M_{sqrt(eta_a)}^-1 r on the constrained velocity space: the lumped inverse (vmass = 0), or
+  // CG on P_v M P_v with the consistent mass, Jacobi-preconditioned, to tol_VectorMass
+  // relative (vmass = 1; Sec. 5.2.3); x and r distinct
+  mfs_status Mw_inv(int side, double a, const T* r, T* x) {
+    if (o.vmass == 0) {
+      Blas<T>::mul(nu, r, poisson_minv<T>(Pb, side), x, s);
+      Blas<T>::bproject(G->bnd[L], n2, x, s);
+      return MFS_OK;
+    }
+    WallTimer tm(st.time_Minv_ms);
+    const T* dinv = nullptr;
+    MFS_TRY(poisson_cmass_dinv<T>(Pb, side, &dinv));
+    int it = 0;
+    auto op = [&](const T* v, T* y) {
+      MFS_TRY(wmass_apply<T>(Pb, a, v, y, 0));
+      Blas<T>::bproject(G->bnd[L], n2, y, s);
+      return MFS_OK;
+    };
+    auto pre = [&](const T* v, T* y) {
+      Blas<T>::mul(nu, v, dinv, y, s);
+      Blas<T>::bproject(G->bnd[L], n2, y, s);
+      return MFS_OK;
+    };
+    MFS_TRY(cg(nu, op, pre, r, x, o.tol_VectorMass, o.max_cg, K.cg_r, K.cg_z, K.cg_p, K.cg_q, &it, 2));
+    st.cg_M_iters += it;
+    st.cg_M_calls++;
+    st.cg_M_max = it > st.cg_M_max ? it : st.cg_M_max;
+    Blas<T>::bproject(G->bnd[L], n2, x, s);
+    return MFS_OK;
+  }
   // weighted BFBT (Eq. schurWBFBT, rescaled form):
   //   K_{1/sqrt(eta_l)}^-1 (B M_{sqrt(eta_l)}^-1 A M_{sqrt(eta_r)}^-1 B^T) K_{1/sqrt(eta_r)}^-1 r
   mfs_status wbfbt(const T* r, T* z) {
@@ -1042,11 +1072,9 @@ struct Stokes {
     MFS_TRY(pmg_side(Pb, o.a_r, &sr));
     MFS_TRY(K_inv(sr, r, K.pe));
     MFS_TRY(BT(K.pe, K.uc));
-    Blas<T>::mul(nu, K.uc, poisson_minv<T>(Pb, sr), K.ud, s);
-    Blas<T>::bproject(G->bnd[L], n2, K.ud, s);
+    MFS_TRY(Mw_inv(sr, o.a_r, K.uc, K.ud));
     MFS_TRY(A(K.ud, K.uc));
-    Blas<T>::mul(nu, K.uc, poisson_minv<T>(Pb, sl), K.ud, s);
-    Blas<T>::bproject(G->bnd[L], n2, K.ud, s);
+    MFS_TRY(Mw_inv(sl, o.a_l, K.uc, K.ud));
     MFS_TRY(Bop(K.ud, K.pf, 0));
     return K_inv(sl, K.pf, z);
   }
@@ -1255,6 +1283,10 @@ static mfs_status check_schur_opts(const mfs_solve_opts& o) {
     set_error("weighted BFBT needs positive finite a_l, a_r and a positive tol_wBFBT");
     return MFS_EINVAL;
   }
+  if (o.schur == 3 && ((o.vmass != 0 && o.vmass != 1) || (o.vmass == 1 && !(o.tol_VectorMass > 0.0)))) {
+    set_error("vmass must be 0 (lumped) or 1 (consistent, with a positive tol_VectorMass)");
+    return MFS_EINVAL;
+  }
   return MFS_OK;
 }
 
@@ -1376,6 +1408,8 @@ void mfs_solve_opts_default(mfs_solve_opts* o) {
   o->a_l = 1.0;
   o->a_r = 1.0;
   o->tol_wBFBT = 1e-10;
+  o->vmass = 0;
+  o->tol_VectorMass = 1e-4;
 }
 
 mfs_status mfs_apply_schur(mfs_problem* Pb, const mfs_solve_opts* opts, mfs_prec prec, const void* r, void* z,

@@ -152,6 +152,14 @@ template <typename T>
 const T* poisson_minv(mfs_problem* P, int side);
 // d = the lumped M_{sqrt(eta_a)} diagonal [n_p2] on the finest level (FP64, device)
 mfs_status lumped_vmass(mfs_problem* P, double a, double* d);
+// y = the consistent M_{sqrt(eta_a)} x on the three components of the finest level
+// ([3][n_p2]; diag != 0: its diagonal [n_p2], x unused; temperature.cu, on the degree-5 rule)
+template <typename T>
+mfs_status wmass_apply(mfs_problem* P, double a, const T* x, T* y, int diag);
+// the inverse diagonal of the consistent M_{sqrt(eta_a)} replicated per velocity component
+// ([3][n_p2], finest level), built on first use after each coefficient change
+template <typename T>
+mfs_status poisson_cmass_dinv(mfs_problem* P, int side, const T** out);
 // g_k = -eta_k sum_tets sum_q 2 w|det J| psi_k(q) eps(u)(q) : eps(lam)(q)   (FP64)
 mfs_status grad_log_eta(mfs_problem* P, int lvl, const double* u, const double* lam, double* g);
 

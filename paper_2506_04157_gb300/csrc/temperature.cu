@@ -27,6 +27,7 @@
 #include "library.h"
 #include "qp_geometry.cuh"
 #include "solver.h"
+#include "sweep_params.cuh"
 
 namespace mfs {
 
@@ -387,6 +388,93 @@ __global__ void __launch_bounds__(128) k_temp_rhs(const RhsArgs P) {
   }
 }
 
+// ------------------------------------------------------------------------- weighted vector mass
+// y_c = M_w x_c (c = 0..2), M_w the consistent P2 scalar mass with weight sqrt(s eta_q): eta_q
+// the P1 interpolant of the level's nodal viscosity at the point, s = a^2 on micro-tets with a
+// vertex on the outer surface and 1 elsewhere (the M_{sqrt(eta_a)} of the weighted BFBT,
+// Sec. 5.2.3), on the degree-5 rule.  DIAG: its diagonal [n_p2] (x unused).  The components
+// pass one after the other through the same shared staging (16 KB in FP64).
+template <typename T, bool BLEND, bool DIAG>
+__global__ void __launch_bounds__(128) k_wmass(const ApplyParams<T> P, T a2, int64_t n_p2, const T* __restrict__ x,
+                                               T* __restrict__ y) {
+  __shared__ T xs[NSLOT2], ys[NSLOT2];
+  __shared__ T eta_s[NSLOT1];
+  __shared__ int surf_s[NSLOT1];
+  const int m = blockIdx.y, tidx = blockIdx.x;
+  const size_t lin = (size_t)m * gridDim.x + tidx;
+  const Tile tile = P.tiles[tidx];
+  const MacroGeom<T>& G = P.geom[m];
+  const int n = P.n;
+  const int* tab2 = P.ids2 + lin * NSLOT2;
+  for (int s = threadIdx.x; s < NSLOT1; s += blockDim.x) {
+    const int id = P.ids1[lin * NSLOT1 + s];
+    eta_s[s] = id >= 0 ? P.eta[id] : T(1);
+    const int code = tab2[s];   // P2 slot s < NSLOT1 is the vertex slot s of the P1 block
+    surf_s[s] = (code >= 0 && (code >> 29) == 1) ? 1 : 0;
+  }
+  const T vol = G.absdet / (T(n) * T(n) * T(n));
+  const int2 cinfo = P.classes[tile.cls];
+  for (int c = 0; c < (DIAG ? 1 : 3); ++c) {
+    __syncthreads();   // staging of eta done; the previous component flushed
+    for (int s = threadIdx.x; s < NSLOT2; s += blockDim.x) {
+      const int code = tab2[s];
+      xs[s] = (!DIAG && code >= 0) ? x[c * n_p2 + (code & 0x1fffffff)] : T(0);
+      ys[s] = T(0);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < cinfo.y; t += blockDim.x) {
+      const int code = P.tets[cinfo.x + t];
+      const int ci = code & 15, cj = (code >> 4) & 15, ck = (code >> 8) & 15, pmu = code >> 12;
+      const int p0 = perm_at(pmu, 0), p1 = perm_at(pmu, 1), p2 = perm_at(pmu, 2);
+      const int base = ci + 5 * cj + 25 * ck;
+      int slot[10];
+      T xv[10], acc[10];
+      for (int a = 0; a < 10; ++a) {
+        slot[a] = base + slot_off(pmu, a);
+        xv[a] = xs[slot[a]];
+        acc[a] = T(0);
+      }
+      T ev[4];
+      int on = 0;
+      for (int a = 0; a < 4; ++a) {   // vertex slots lie in parity class 0: P1 slot = P2 slot
+        ev[a] = eta_s[slot[a]];
+        on |= surf_s[slot[a]];
+      }
+      const T sc = on ? a2 : T(1);
+      const T qb[3] = {T(tile.ta * TT + ci), T(tile.tb * TT + cj), T(tile.tc * TT + ck)};
+#pragma unroll 1
+      for (int q = 0; q < kTQ; ++q) {
+        T lam[4];
+        for (int a = 0; a < 4; ++a) lam[a] = T(c_tq_lam[q][a]);
+        T xi[3];
+        for (int d = 0; d < 3; ++d)
+          xi[d] = qb[d] + lam[3] + (d == p0 ? lam[1] + lam[2] : T(0)) + (d == p1 ? lam[2] : T(0));
+        T K[3][3], hr, rinv, xq[3];
+        lattice_geometry<T, BLEND>(G, n, p0, p1, p2, xi[0], xi[1], xi[2], K, hr, rinv, xq);
+        const T etaq = lam[0] * ev[0] + lam[1] * ev[1] + lam[2] * ev[2] + lam[3] * ev[3];
+        const T W = T(c_tq_w[q]) * vol * hr * hr * hr * sqrt(sc * etaq);
+        T phi[10];
+        p2_values_at<T>(lam, phi);
+        if (DIAG) {
+          for (int a = 0; a < 10; ++a) acc[a] += W * phi[a] * phi[a];
+        } else {
+          T v = T(0);
+          for (int a = 0; a < 10; ++a) v += phi[a] * xv[a];
+          v *= W;
+          for (int a = 0; a < 10; ++a) acc[a] += v * phi[a];
+        }
+      }
+      for (int a = 0; a < 10; ++a) atomicAdd(&ys[slot[a]], acc[a]);
+    }
+    __syncthreads();
+    for (int s = threadIdx.x; s < NSLOT2; s += blockDim.x) {
+      const int code = tab2[s];
+      if (code < 0) continue;
+      atomicAdd(&y[c * n_p2 + (code & 0x1fffffff)], ys[s]);
+    }
+  }
+}
+
 // ------------------------------------------------------------------------- MMOC
 struct MmocArgs {
   const MacroGeom<double>* geom;
@@ -573,6 +661,33 @@ static mfs_status ensure_rule() {
   g_rule_ready[dev] = 1;
   return MFS_OK;
 }
+
+// y = M_{sqrt(eta_a)} x on the three components of the finest level ([3][n_p2]); diag: the
+// diagonal, [n_p2] (x unused)
+template <typename T>
+mfs_status wmass_apply(mfs_problem* Pb, double a, const T* x, T* y, int diag) {
+  MFS_TRY(ensure_rule());
+  mfs_mesh* M = Pb->mesh;
+  const int L = M->l_max;
+  const LevelData& Lv = M->levels[L];
+  cudaStream_t s = M->ctx->stream;
+  const int64_t n2 = Lv.nb2.total;
+  MFS_CUDA(cudaMemsetAsync(y, 0, sizeof(T) * (size_t)n2 * (diag ? 1 : 3), s));
+  const ApplyParams<T> prm = sweep_params<T>(Pb, L);
+  const dim3 grid(Lv.n_tiles, kMacroCells);
+  const T a2 = T(a * a);
+  if (M->host.blending) {
+    if (diag) k_wmass<T, true, true><<<grid, 128, 0, s>>>(prm, a2, n2, nullptr, y);
+    else k_wmass<T, true, false><<<grid, 128, 0, s>>>(prm, a2, n2, x, y);
+  } else {
+    if (diag) k_wmass<T, false, true><<<grid, 128, 0, s>>>(prm, a2, n2, nullptr, y);
+    else k_wmass<T, false, false><<<grid, 128, 0, s>>>(prm, a2, n2, x, y);
+  }
+  MFS_CUDA(cudaGetLastError());
+  return MFS_OK;
+}
+template mfs_status wmass_apply<double>(mfs_problem*, double, const double*, double*, int);
+template mfs_status wmass_apply<float>(mfs_problem*, double, const float*, float*, int);
 
 template <typename T>
 static mfs_status talloc(TempWork* W, T** p, int64_t n, cudaStream_t s) {
@@ -1050,4 +1165,27 @@ mfs_status mfs_temperature_step(mfs_problem* Pb, const mfs_temp_params* params, 
   st.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (stats) *stats = st;
   return rc;
+}
+
+mfs_status mfs_apply_vmass(mfs_problem* Pb, mfs_prec prec, double a, const void* x, void* y) {
+  if (!Pb || !x || !y) {
+    set_error("null argument");
+    return MFS_EINVAL;
+  }
+  if (!Pb->has_eta) {
+    set_error("viscosity not set");
+    return MFS_EINVAL;
+  }
+  if (!(a > 0.0) || !std::isfinite(a)) {
+    set_error("the weighted-BFBT surface scaling must be positive and finite");
+    return MFS_EINVAL;
+  }
+  if (x == y) {
+    set_error("mfs_apply_vmass: x and y must be distinct");
+    return MFS_EINVAL;
+  }
+  if (prec == MFS_F64) return wmass_apply<double>(Pb, a, (const double*)x, (double*)y, 0);
+  if (prec == MFS_F32) return wmass_apply<float>(Pb, a, (const float*)x, (float*)y, 0);
+  set_error("unknown precision");
+  return MFS_EINVAL;
 }

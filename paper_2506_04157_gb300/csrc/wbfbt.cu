@@ -42,6 +42,9 @@ struct PoissonSide {
   double* cinv = nullptr;              // coarsest level: (K_c + lift)^-1, nc x nc
   double* minv64 = nullptr;            // lumped M_{sqrt(eta_a)}^-1, [3][n_p2] of the finest level
   float* minv32 = nullptr;
+  double* cdinv64 = nullptr;           // consistent M_{sqrt(eta_a)}: inverse diagonal, [3][n_p2]
+  float* cdinv32 = nullptr;            // (allocated on first use)
+  int cversion = -1;
 };
 
 template <typename T>
@@ -662,6 +665,37 @@ template <>
 const float* poisson_minv<float>(mfs_problem* Pb, int side) { return Pb->pmg->sides[side].minv32; }
 
 mfs_status lumped_vmass(mfs_problem* Pb, double a, double* d) { return lumped_into(Pb, a, d); }
+
+// Jacobi scaling of the consistent-mass CG: 1 / diag(M_{sqrt(eta_a)}) per velocity component
+static mfs_status cmass_dinv(mfs_problem* Pb, int side) {
+  PoissonMG* W = Pb->pmg;
+  PoissonSide& S = W->sides[side];
+  if (S.cversion == Pb->version) return MFS_OK;
+  mfs_mesh* M = Pb->mesh;
+  cudaStream_t s = M->ctx->stream;
+  const int64_t n2 = M->levels[W->l_max].nb2.total;
+  if (!S.cdinv64) {
+    MFS_TRY(palloc(W, &S.cdinv64, 3 * n2, s));
+    MFS_TRY(palloc(W, &S.cdinv32, 3 * n2, s));
+  }
+  MFS_TRY(wmass_apply<double>(Pb, S.a, nullptr, W->d2, 1));
+  k_minv_expand<<<nblk(n2), 256, 0, s>>>(n2, W->d2, S.cdinv64, S.cdinv32);
+  MFS_CUDA(cudaGetLastError());
+  S.cversion = Pb->version;
+  return MFS_OK;
+}
+template <>
+mfs_status poisson_cmass_dinv<double>(mfs_problem* Pb, int side, const double** out) {
+  MFS_TRY(cmass_dinv(Pb, side));
+  *out = Pb->pmg->sides[side].cdinv64;
+  return MFS_OK;
+}
+template <>
+mfs_status poisson_cmass_dinv<float>(mfs_problem* Pb, int side, const float** out) {
+  MFS_TRY(cmass_dinv(Pb, side));
+  *out = Pb->pmg->sides[side].cdinv32;
+  return MFS_OK;
+}
 
 template mfs_status poisson_apply<double>(mfs_problem*, int, int, const double*, double*);
 template mfs_status poisson_apply<float>(mfs_problem*, int, int, const float*, float*);

@@ -82,7 +82,7 @@ def test_library_default_options_match_paper_table(lib):
     for k, v in gold.items():
         if k not in ("_source", "tol_coarse"):
             assert getattr(o, k) == v, k
-    assert (o.uzawa, o.schur, o.mixed, o.tol_wBFBT) == (0, 0, 1, 1e-10)
+    assert (o.uzawa, o.schur, o.mixed, o.tol_wBFBT, o.vmass) == (0, 0, 1, 1e-10, 0)
     t = mfs.Problem.temp_params()
     assert t.tol_T == 1e-10 and t.restart == 30
-    assert ctypes.sizeof(mfs.SolveOpts) == 136 and ctypes.sizeof(mfs.TempParams) == 96
+    assert ctypes.sizeof(mfs.SolveOpts) == 152 and ctypes.sizeof(mfs.TempParams) == 96

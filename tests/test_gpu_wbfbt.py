@@ -165,3 +165,85 @@ def test_solve_with_wbfbt(mixed, al):
     ud, pd = direct_solve(H, f, g, 0 * un, 0 * pn)
     assert np.linalg.norm(un - ud) / np.linalg.norm(ud) < 1e-5
     assert np.linalg.norm(pn - pd) / np.linalg.norm(pd) < 1e-5
+
+
+# ---- the consistent vector mass (vmass = 1).  Written after the last GPU session of this
+# build and checked on the CPU only (per-tet arithmetic against the oracle's element
+# matrices, the CG flow with the oracle's matrices): skipped until it has run on a GPU.
+UNRUN = pytest.mark.skip(reason="consistent vector-mass GPU path not yet run on a GPU")
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_cmass(L, a):
+    H = setup(L)[0]
+    return WbfbtOperators(H.levels[L], H.etas[L], a, mass="consistent")
+
+
+@UNRUN
+@pytest.mark.parametrize("dt", [torch.float64, torch.float32])
+@pytest.mark.parametrize("L,a", [(2, 1.0), (2, 3.0), (3, 2.0)])
+def test_consistent_vmass_apply(L, a, dt):
+    """y_c = M_{sqrt(eta_a)} x_c on each component against the oracle's assembled matrix."""
+    H, ctx, gm, prob = setup(L)
+    n2 = H.levels[L].n_p2
+    x = W.random_field(3 * n2, 40 + L)
+    if dt == torch.float32:
+        x = x.astype(np.float32).astype(np.float64)
+    y = torch.empty(3 * n2, dtype=dt, device="cuda")
+    prob.apply_vmass(a, torch.tensor(x, dtype=dt, device="cuda"), y)
+    Mc = oracle_cmass(L, a).Mc
+    ref = np.concatenate([Mc @ x[c * n2:(c + 1) * n2] for c in range(3)])
+    assert rel(y.double().cpu().numpy(), ref) <= TOL[dt], (L, a)
+
+
+@UNRUN
+@pytest.mark.parametrize("al,ar", [(1.0, 1.0), (1.0, 10.0)])
+def test_wbfbt_consistent_apply_fp64(al, ar):
+    """S_w^-1 r with the consistent mass: the GPU's CGs on K and on M converged far below the
+    oracle's exact solves."""
+    L = 2
+    H, ctx, gm, prob = setup(L)
+    n = H.levels[L].n_p1
+    r = project_mean_zero(W.random_field(n, 24))
+    z = torch.empty(n, dtype=torch.float64, device="cuda")
+    st = prob.apply_schur(torch.tensor(r, device="cuda"), z, schur=3, a_l=al, a_r=ar, tol_wBFBT=1e-13,
+                          vmass=1, tol_VectorMass=1e-13, max_cg=400)
+    wl, wr = oracle_cmass(L, al), oracle_cmass(L, ar)
+    ref = project_mean_zero(wbfbt_apply(H.co[L], H.cons[L], H.co[L].apply_A, wl, wr, r))
+    assert rel(z.cpu().numpy(), ref) <= 1e-8, st
+    assert st["cg_M_calls"] == 2 and 0 < st["cg_M_max"] < 400
+
+
+@UNRUN
+def test_solve_with_wbfbt_consistent_mass():
+    """FGMRES with the weighted BFBT on the consistent mass (the paper's tol_VectorMass = 1e-4)
+    reaches the oracle's direct solution."""
+    H, ctx, gm, prob = setup(2)
+    L = H.levels[2]
+    rng = np.random.default_rng(32)
+    f = rng.standard_normal(3 * L.n_p2) * 1e-3
+    g = np.zeros(L.n_p1)
+    u = torch.zeros(3 * L.n_p2, dtype=torch.float64, device="cuda")
+    p = torch.zeros(L.n_p1, dtype=torch.float64, device="cuda")
+    st = prob.solve(torch.tensor(f, device="cuda"), torch.tensor(g, device="cuda"), u, p, mixed=2, schur=3,
+                    vmass=1, omega=0.03, restart=50, max_iters=1500, rtol=1e-10)
+    assert st["status"] == "MFS_OK" and st["rel_residual"] <= 1e-10, st
+    ud, pd = direct_solve(H, f, g, 0 * f, 0 * g)
+    assert np.linalg.norm(u.cpu().numpy() - ud) / np.linalg.norm(ud) < 1e-5
+    assert np.linalg.norm(p.cpu().numpy() - pd) / np.linalg.norm(pd) < 1e-5
+
+
+@UNRUN
+def test_vmass_refusals():
+    H, ctx, gm, prob = setup(2)
+    n = H.levels[2].n_p1
+    r = torch.zeros(n, dtype=torch.float64, device="cuda")
+    z = torch.empty(n, dtype=torch.float64, device="cuda")
+    for bad in [dict(schur=3, vmass=2), dict(schur=3, vmass=1, tol_VectorMass=0.0)]:
+        with pytest.raises(mfs.MfsError):
+            prob.apply_schur(r, z, **bad)
+    x = torch.zeros(3 * H.levels[2].n_p2, dtype=torch.float64, device="cuda")
+    with pytest.raises(mfs.MfsError):
+        prob.apply_vmass(0.0, x, torch.empty_like(x))
+    with pytest.raises(mfs.MfsError):
+        prob.apply_vmass(1.0, x, x)
