@@ -221,3 +221,34 @@ def test_consistent_vector_mass():
     v = cons.P0(np.random.default_rng(3).standard_normal(3 * Lv.n_p2))
     Mv = np.concatenate([O.Mc @ v.reshape(3, -1)[c] for c in range(3)])
     assert np.abs(O.M_inv(cons.P0(Mv), cons) - v).max() <= 1e-10 * np.abs(v).max()
+
+
+def test_consistent_vector_mass_variable_viscosity_and_surface_scaling():
+    """Variable viscosity: on the polyhedral shell, where P2 reproduces quadratics f and g,
+    f^T M_{sqrt(eta_a)} g is the integral of sqrt(eta_a) f g with eta the P1 interpolant of the
+    nodal viscosity; a 512-point conical rule (degree 15) integrates it to far below the
+    degree-5 rule's error (sqrt(eta) is not a polynomial: 6e-6 relative here), while a
+    dropped square root moves the form by tens of percents.  The scaling a multiplies exactly
+    the surface micro-tets' share by a."""
+    from oracle.temperature import conical_rule
+    Lv = Level(MacroMesh(blending=False), 1)
+    eta = 10 ** np.random.default_rng(5).uniform(0.0, 1.0, Lv.n_p1)
+    f = lambda y: 1 + y[..., 0] - 2 * y[..., 1] * y[..., 2] + 0.5 * y[..., 0] ** 2
+    g = lambda y: y[..., 1] ** 2 - y[..., 2] + 0.3 * y[..., 0] * y[..., 1]
+    bary, w = conical_rule(8)
+    X = Lv.tet_x                                                       # (E,4,3)
+    y = np.einsum("qa,eai->eqi", bary, X)
+    det = np.abs(np.linalg.det(np.stack([X[:, 1] - X[:, 0], X[:, 2] - X[:, 0], X[:, 3] - X[:, 0]], -1)))
+    etaq = eta[Lv.tet_p1] @ bary.T                                     # (E,Q)
+    per_tet = det * ((w * np.sqrt(etaq) * f(y) * g(y)).sum(axis=1))
+    surf = surface_tets(Lv)
+    x = Lv.p2_x
+    M1 = WbfbtOperators(Lv, eta, 1.0, mass="consistent").Mc
+    M3 = WbfbtOperators(Lv, eta, 3.0, mass="consistent").Mc
+    got1 = f(x) @ (M1 @ g(x))
+    assert abs(got1 - per_tet.sum()) <= 1e-4 * abs(per_tet).sum(), (got1, per_tet.sum())
+    got3 = f(x) @ (M3 @ g(x))
+    assert abs((got3 - got1) - 2.0 * per_tet[surf].sum()) <= 1e-4 * abs(per_tet[surf]).sum()
+    # the weight eta instead of sqrt(eta) moves the form well outside that band
+    alt = (det * ((w * etaq * f(y) * g(y)).sum(axis=1))).sum()
+    assert abs(alt - per_tet.sum()) > 1e-1 * abs(per_tet).sum()
