@@ -14,16 +14,17 @@ import torch
 class CoupledStepper:
     """Time stepping on a problem whose viscosity law (set_viscosity_law) and density table
     (set_density) are set.  temp_params: mfs_temp_params fields (k, Pe, Cp, Di, alpha, H, Ra,
-    tolerances); solve_opts: mfs_solve_opts fields for the Stokes solves."""
+    tolerances); solve_opts: mfs_solve_opts fields for the Stokes solves; device: where the
+    state lives (default: the problem's CUDA device)."""
 
-    def __init__(self, problem, temp_params=None, solve_opts=None, l_min=1, T_ref=None, u_bc=None):
+    def __init__(self, problem, temp_params=None, solve_opts=None, l_min=1, T_ref=None, u_bc=None, device=None):
         self.prob = problem
         self.tp = dict(temp_params or {})
         self.opts = dict(solve_opts or {})
         self.l_min = l_min
         L = problem.mesh.l_max
         nu, npp = problem._sizes(L)
-        dev = "cuda"
+        dev = torch.device("cuda", problem.mesh.ctx.device) if device is None else torch.device(device)
         self.n2, self.np = nu // 3, npp
         self.T_ref = torch.zeros(self.n2, dtype=torch.float64, device=dev) if T_ref is None else T_ref
         self.f = torch.zeros(nu, dtype=torch.float64, device=dev)
@@ -33,8 +34,8 @@ class CoupledStepper:
         self.u_bc = torch.zeros(nu, dtype=torch.float64, device=dev) if u_bc is None else u_bc
 
     def stokes(self, T, u, p):
-        """(u, p) for the temperature T in place (u, p hold the initial guess); returns the
-        solver statistics."""
+        """(u, p) for the temperature T in place: u starts from the Dirichlet values u_bc (zero
+        elsewhere), p from its value on entry; returns the solver statistics."""
         pr = self.prob
         pr.set_temperature(T)
         pr.setup_multigrid(self.l_min)
