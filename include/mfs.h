@@ -148,7 +148,8 @@ mfs_status mfs_set_viscosity_law(mfs_problem* prob, double E_A, double V_A, int 
 /* The finest level's P2 temperature T_p2 [n_p2] (FP64, device): sets the viscosity of every
  * level from the law (replaces mfs_set_viscosity; mfs_set_viscosity in turn drops the law).
  * On levels <= l_eta only the A block is available (B and the fused applies return
- * MFS_EINVAL there).  Errors: MFS_EINVAL (no law), MFS_ECUDA. */
+ * MFS_EINVAL there).  Evaluated on the device; the first call per mesh builds vertex-to-node
+ * lookup maps (allocates device memory).  Errors: MFS_EINVAL (no law), MFS_ENOMEM, MFS_ECUDA. */
 mfs_status mfs_set_temperature(mfs_problem* prob, const double* T_p2);
 
 /* y = A(eta) u on level lvl (paper Sec. 5.1, A_ij = int 2 eta eps(phi_j):eps(phi_i),

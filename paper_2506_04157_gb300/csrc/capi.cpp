@@ -253,6 +253,9 @@ mfs_status mfs_mesh_destroy(mfs_mesh* M) {
     cudaFree(L.d_er_rp);
     cudaFree(L.d_er_ci);
     cudaFree(L.d_er_w);
+    cudaFree(L.d_vfine);
+    cudaFree(L.d_vrad);
+    cudaFree(L.d_p2fine);
   }
   delete M;
   return MFS_OK;
@@ -431,70 +434,109 @@ mfs_status mfs_set_viscosity_law(mfs_problem* P, double E_A, double V_A, int n, 
   return MFS_OK;
 }
 
+// The viscosity law's lookup maps of level l, built on the host once per mesh: the finest
+// P2 node coinciding with each P1 vertex and the vertex's radius (|x| of the blended point),
+// and (p2 != 0) the finest P2 node coinciding with each P2 node of the level.
+static mfs_status law_maps(mfs_mesh* M, int l, bool p2) {
+  LevelData& Lv = M->levels[l];
+  cudaStream_t s = M->ctx->stream;
+  const int L = M->l_max;
+  const int NF = 2 << L;   // finest P2 lattice
+  const Numbering nbf = make_numbering(NF);
+  if (!Lv.d_vfine || !Lv.d_vrad) {
+    const int N1 = 1 << l, sc1 = NF / N1;
+    std::vector<int> fine(Lv.nb1.total, -1);
+    std::vector<double> rad(Lv.nb1.total, 0.0);
+    for_each_point(M, N1, [&](int m, const int* i, int id) {
+      double xs[3], x[3];
+      M->host.straight_point(m, i, N1, xs);
+      if (M->host.blending) M->host.blend_point(m, xs, x);
+      else for (int r = 0; r < 3; ++r) x[r] = xs[r];
+      fine[id] = lattice_id(M->host.topo[m], nbf, m, i[0] * sc1, i[1] * sc1, i[2] * sc1, i[3] * sc1);
+      rad[id] = std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+    });
+    for (int f : fine)
+      if (f < 0 || f >= nbf.total) {
+        set_error("internal: vertex without a finest-level node on level %d", l);
+        return MFS_EINVAL;
+      }
+    cudaFree(Lv.d_vfine);
+    cudaFree(Lv.d_vrad);
+    Lv.d_vfine = nullptr;
+    Lv.d_vrad = nullptr;
+    int* dfine = nullptr;
+    double* drad = nullptr;
+    mfs_status st = upload(&dfine, fine.data(), fine.size(), s);
+    if (st == MFS_OK) st = upload(&drad, rad.data(), rad.size(), s);
+    cudaError_t e = cudaStreamSynchronize(s);   // the host vectors go out of scope
+    if (st == MFS_OK && e != cudaSuccess) st = cuda_fail(e, "law_maps");
+    if (st != MFS_OK) {
+      cudaFree(dfine);
+      cudaFree(drad);
+      return st;
+    }
+    Lv.d_vfine = dfine;
+    Lv.d_vrad = drad;
+  }
+  if (p2 && !Lv.d_p2fine) {
+    const int N2 = 2 << l, sc2 = NF / N2;
+    std::vector<int> fine(Lv.nb2.total, -1);
+    for_each_point(M, N2, [&](int m, const int* i, int id) {
+      fine[id] = lattice_id(M->host.topo[m], nbf, m, i[0] * sc2, i[1] * sc2, i[2] * sc2, i[3] * sc2);
+    });
+    for (int f : fine)
+      if (f < 0 || f >= nbf.total) {
+        set_error("internal: P2 node without a finest-level node on level %d", l);
+        return MFS_EINVAL;
+      }
+    int* dfine = nullptr;
+    mfs_status st = upload(&dfine, fine.data(), fine.size(), s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (st == MFS_OK && e != cudaSuccess) st = cuda_fail(e, "law_maps");
+    if (st != MFS_OK) {
+      cudaFree(dfine);
+      return st;
+    }
+    Lv.d_p2fine = dfine;
+  }
+  return MFS_OK;
+}
+
 mfs_status mfs_set_temperature(mfs_problem* P, const double* T_p2) {
   if (P) P->version++;
   MFS_TRY(check_problem(P, 0, false));
-  if (!T_p2 || P->lbase_host.empty()) {
+  if (!T_p2 || P->lbase_host.empty() || !P->d_lbase64) {
     set_error(T_p2 ? "no viscosity law (call mfs_set_viscosity_law first)" : "null temperature");
     return MFS_EINVAL;
   }
   mfs_mesh* M = P->mesh;
   cudaStream_t s = M->ctx->stream;
   const int L = M->l_max;
-  const int NF = 2 << L;   // finest P2 lattice
-  const Numbering nbf = make_numbering(NF);
-  std::vector<double> Tf(nbf.total);
-  MFS_CUDA(cudaMemcpyAsync(Tf.data(), T_p2, sizeof(double) * Tf.size(), cudaMemcpyDeviceToHost, s));
-  MFS_CUDA(cudaStreamSynchronize(s));
-  const int nt = (int)P->lbase_host.size();
-  const double r0 = M->host.r_cmb, r1 = M->host.r_surf;
-  auto law = [&](const double x[3], double T) {   // Eq. (ViscosityDef)
-    const double r = std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
-    double lb = P->lbase_host[0];
-    if (nt > 1) {
-      double t = (r - r0) / (r1 - r0) * (nt - 1);
-      t = t < 0 ? 0 : (t > nt - 1 ? nt - 1 : t);
-      int i = (int)t;
-      i = i > nt - 2 ? nt - 2 : i;
-      lb = (1 - (t - i)) * P->lbase_host[i] + (t - i) * P->lbase_host[i + 1];
-    }
-    return std::pow(10.0, lb) * std::exp(-P->E_A * T + P->V_A * (r1 - r));
-  };
   const int l_eta = P->law_l_eta;
   if ((int)P->temp64.size() < L + 1) {
     P->temp64.resize(L + 1, nullptr);
     P->temp32.resize(L + 1, nullptr);
   }
+  const int nt = (int)P->lbase_host.size();
   for (int l = 0; l <= L; ++l) {
-    // P1 viscosity at the vertices: vertex i of level l is the finest P2 node i * NF / 2^l
-    const int N1 = 1 << l, sc1 = NF / N1;
-    std::vector<double> eta(M->levels[l].nb1.total);
-    for_each_point(M, N1, [&](int m, const int* i, int id) {
-      double xs[3], x[3];
-      M->host.straight_point(m, i, N1, xs);
-      if (M->host.blending) M->host.blend_point(m, xs, x);
-      else for (int r = 0; r < 3; ++r) x[r] = xs[r];
-      const int fi = lattice_id(M->host.topo[m], nbf, m, i[0] * sc1, i[1] * sc1, i[2] * sc1, i[3] * sc1);
-      eta[id] = law(x, Tf[fi]);
-    });
-    MFS_CUDA(cudaMemcpyAsync(P->eta64[l], eta.data(), sizeof(double) * eta.size(), cudaMemcpyHostToDevice, s));
-    MFS_TRY(convert_f64_f32(P->eta64[l], P->eta32[l], (int64_t)eta.size(), s));
+    // Eq. (ViscosityDef) at every vertex of the level, with the temperature of the finest
+    // P2 node at the same point
+    MFS_TRY(law_maps(M, l, l <= l_eta));
+    const LevelData& Lv = M->levels[l];
+    MFS_TRY(law_eta(Lv.nb1.total, Lv.d_vfine, Lv.d_vrad, T_p2, P->d_lbase64, nt, P->E_A, P->V_A, M->host.r_cmb,
+                    M->host.r_surf, P->eta64[l], s));
+    MFS_TRY(convert_f64_f32(P->eta64[l], P->eta32[l], Lv.nb1.total, s));
     if (l <= l_eta) {   // P2 temperature of the level for the quadrature-point viscosity
-      const int N2 = 2 << l, sc2 = NF / N2;
-      const int64_t n2 = M->levels[l].nb2.total;
-      std::vector<double> T2(n2);
-      for_each_point(M, N2, [&](int m, const int* i, int id) {
-        T2[id] = Tf[lattice_id(M->host.topo[m], nbf, m, i[0] * sc2, i[1] * sc2, i[2] * sc2, i[3] * sc2)];
-      });
+      const int64_t n2 = Lv.nb2.total;
       if (!P->temp64[l]) {
         MFS_CUDA(cudaMalloc((void**)&P->temp64[l], sizeof(double) * n2));
         MFS_CUDA(cudaMalloc((void**)&P->temp32[l], sizeof(float) * n2));
       }
-      MFS_CUDA(cudaMemcpyAsync(P->temp64[l], T2.data(), sizeof(double) * n2, cudaMemcpyHostToDevice, s));
+      MFS_TRY(gather_f64(n2, Lv.d_p2fine, T_p2, P->temp64[l], s));
       MFS_TRY(convert_f64_f32(P->temp64[l], P->temp32[l], n2, s));
     }
-    MFS_CUDA(cudaStreamSynchronize(s));   // the host buffers go out of scope
   }
+  MFS_CUDA(cudaStreamSynchronize(s));
   P->l_eta = l_eta;
   P->has_eta = true;
   return MFS_OK;

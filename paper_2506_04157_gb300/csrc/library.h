@@ -71,6 +71,11 @@ struct LevelData {
   double* d_er_w = nullptr;
   int64_t n_tets = 0, n_surface = 0, n_cmb = 0;
   int variant = 0;   // sweep variant chosen by mfs_autotune (0: default register budget)
+  // viscosity law (built on first use): per P1 vertex the finest-level P2 node at the same
+  // point and the vertex's radius; per P2 node (levels below the finest) the finest node
+  int* d_vfine = nullptr;
+  double* d_vrad = nullptr;
+  int* d_p2fine = nullptr;
 };
 
 template <typename T>
@@ -195,5 +200,11 @@ mfs_status restrict_eta(const mfs_mesh* M, int l, const double* fine, double* co
 mfs_status build_id_tables(const mfs_mesh* M, LevelData& L);
 mfs_status convert_f64_f32(const double* src, float* dst, int64_t n, cudaStream_t s);
 mfs_status exp_inplace(double* x, int64_t n, cudaStream_t s);
+// eta[i] = 10^lbase(rad[i]) exp(-E_A T[fine[i]] + V_A (r1 - rad[i])), lbase linear in r on a
+// uniform grid of nt entries over [r0, r1] (Eq. ViscosityDef)
+mfs_status law_eta(int64_t n, const int* fine, const double* rad, const double* T, const double* lbase, int nt,
+                   double E_A, double V_A, double r0, double r1, double* eta, cudaStream_t s);
+// dst[i] = src[idx[i]]
+mfs_status gather_f64(int64_t n, const int* idx, const double* src, double* dst, cudaStream_t s);
 
 }  // namespace mfs

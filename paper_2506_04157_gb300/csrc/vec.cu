@@ -138,6 +138,46 @@ mfs_status exp_inplace(double* x, int64_t n, cudaStream_t s) {
   return MFS_OK;
 }
 
+__global__ void law_eta_kernel(int64_t n, const int* __restrict__ fine, const double* __restrict__ rad,
+                               const double* __restrict__ T, const double* __restrict__ lbase, int nt, double E_A,
+                               double V_A, double r0, double r1, double* __restrict__ eta) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double r = rad[i];
+    double lb = lbase[0];
+    if (nt > 1) {
+      double t = (r - r0) / (r1 - r0) * (nt - 1);
+      t = t < 0.0 ? 0.0 : (t > nt - 1 ? nt - 1 : t);
+      int k = (int)t;
+      k = k > nt - 2 ? nt - 2 : k;
+      lb = (1.0 - (t - k)) * lbase[k] + (t - k) * lbase[k + 1];
+    }
+    eta[i] = exp(2.302585092994045684 * lb - E_A * T[fine[i]] + V_A * (r1 - r));
+  }
+}
+
+mfs_status law_eta(int64_t n, const int* fine, const double* rad, const double* T, const double* lbase, int nt,
+                   double E_A, double V_A, double r0, double r1, double* eta, cudaStream_t s) {
+  int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+  if (blocks < 1) blocks = 1;
+  law_eta_kernel<<<blocks, 256, 0, s>>>(n, fine, rad, T, lbase, nt, E_A, V_A, r0, r1, eta);
+  MFS_CUDA(cudaGetLastError());
+  return MFS_OK;
+}
+
+__global__ void gather_f64_kernel(int64_t n, const int* __restrict__ idx, const double* __restrict__ src,
+                                  double* __restrict__ dst) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[idx[i]];
+}
+
+mfs_status gather_f64(int64_t n, const int* idx, const double* src, double* dst, cudaStream_t s) {
+  int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+  if (blocks < 1) blocks = 1;
+  gather_f64_kernel<<<blocks, 256, 0, s>>>(n, idx, src, dst);
+  MFS_CUDA(cudaGetLastError());
+  return MFS_OK;
+}
+
 }  // namespace mfs
 
 namespace mfs {
