@@ -145,3 +145,62 @@ def test_stokes_preconditioner_variants_match_direct(hier2, uzawa, schur):
     ud, pd = direct_solve(H, f, g, np.zeros(n), np.zeros(npp))
     assert np.linalg.norm(u - ud) / np.linalg.norm(ud) < 1e-5
     assert np.linalg.norm(p - pd) / np.linalg.norm(pd) < 1e-5
+
+
+@pytest.fixture(scope="module")
+def exact_blocks_level1():
+    """Level 1 (blended, free-slip CMB, compressible, variable viscosity) with the exact
+    inverses of the constrained A and of the Schur complement S = Bbar A^-1 B^T on mean-free
+    pressures, for the pins of the Uzawa steps below."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    mesh = MacroMesh()
+    Lv = Level(mesh, 1)
+    eta = W.viscosity_plumes(Lv.p1_x, seed=3, contrast=1e3)
+    H = Hierarchy(mesh, 1, eta, dlnrho_table=W.dlnrho_table_compressible(), bounds={})
+    co, cons = H.co[1], H.cons[1]
+    P0 = cons.Pv_matrix()
+    I = sp.identity(P0.shape[0], format="csc")
+    lu = spla.splu((P0 @ H.ops[1].A @ P0 + I - P0).tocsc())
+    Ainv = lambda r: cons.P0(lu.solve(cons.P0(r)))
+    n = Lv.n_p1
+    Qp = np.linalg.qr(np.eye(n) - 1.0 / n)[0][:, :n - 1]                  # mean-free basis
+    S = np.column_stack([co.apply_Bbar(Ainv(co.apply_BT(q))) for q in Qp.T])
+    Sr = Qp.T @ S
+    Sinv = lambda r: Qp @ np.linalg.solve(Sr, Qp.T @ r)
+    return H, Ainv, Sinv
+
+
+def _exact_oracle(H, Ainv, Sinv, kind):
+    S = StokesOracle(H, dict(uzawa=kind, sigma=1.0, omega=1.0))
+    S.Ahat_inv = Ainv
+    S.Shat_inv = Sinv
+    return S
+
+
+def _constrained_residual(S, seed):
+    rng = np.random.default_rng(seed)
+    r = rng.standard_normal(S.nu + S.np)
+    return np.concatenate([S.cons.P0(r[:S.nu]), r[S.nu:] - r[S.nu:].mean()])
+
+
+def test_symmetric_uzawa_with_exact_blocks_is_the_inverse(exact_blocks_level1):
+    """Eq. (SymmetricUzawaStep1) with exact A^-1, the exact Schur complement and sigma =
+    omega = 1 is the block LDU inverse of the constrained saddle-point operator: K z = r."""
+    S = _exact_oracle(*exact_blocks_level1, "symmetric")
+    r = _constrained_residual(S, 4)
+    z = S.uzawa(r)
+    assert np.linalg.norm(S.K(z) - r) <= 1e-9 * np.linalg.norm(r)
+
+
+@pytest.mark.parametrize("kind", ["inexact", "adjoint"])
+def test_one_sided_uzawa_with_exact_blocks_is_nilpotent_of_order_two(exact_blocks_level1, kind):
+    """Eqs. (InexactUzawaStep1), (AdjointInexactUzawaStep1) with exact blocks are the block
+    lower / upper triangular preconditioners: (K P^-1 - I)^2 = 0, while K P^-1 - I itself is
+    not zero (right-preconditioned GMRES converges in two steps)."""
+    S = _exact_oracle(*exact_blocks_level1, kind)
+    r = _constrained_residual(S, 5)
+    E = lambda v: S.K(S.uzawa(v)) - v
+    e1 = E(r)
+    assert np.linalg.norm(e1) > 1e-3 * np.linalg.norm(r)
+    assert np.linalg.norm(E(e1)) <= 1e-9 * np.linalg.norm(r)
