@@ -204,3 +204,22 @@ def test_one_sided_uzawa_with_exact_blocks_is_nilpotent_of_order_two(exact_block
     e1 = E(r)
     assert np.linalg.norm(e1) > 1e-3 * np.linalg.norm(r)
     assert np.linalg.norm(E(e1)) <= 1e-9 * np.linalg.norm(r)
+
+
+def test_bfbt_with_exact_inner_inverse_is_the_exact_schur_inverse(exact_blocks_level1):
+    """Eq. (schurV) with the exact A^-1 in place of the cheap V-cycle A_C^-1 collapses to
+    X^-1 (B A^-1 A A^-1 B^T) X^-1 = X^-1, X = B A^-1 B^T: the composition's order and the
+    middle factor are pinned by agreement with a dense inverse of X on mean-free pressures."""
+    H, Ainv, _ = exact_blocks_level1
+    S = StokesOracle(H, dict(tol_VBFBT=1e-13))
+    n = H.levels[1].n_p1
+    Qp = np.linalg.qr(np.eye(n) - 1.0 / n)[0][:, :n - 1]
+    X = Qp.T @ np.column_stack([S.co.apply_B(Ainv(S.co.apply_BT(q))) for q in Qp.T])
+    r = np.random.default_rng(6).standard_normal(n)
+    r -= r.mean()
+    ref = Qp @ np.linalg.solve(X, Qp.T @ r)
+    got = S.bfbt(r, Ainv)
+    assert np.linalg.norm(got - ref) <= 1e-8 * np.linalg.norm(ref)
+    # with the cheap V-cycle it is only an approximation
+    cheap = S.bfbt(r, S.Ac_inv)
+    assert np.linalg.norm(cheap - ref) > 1e-3 * np.linalg.norm(ref)
