@@ -359,3 +359,27 @@ def test_model_numbers_and_initial_temperature():
     ts = W.T_ADIABATIC_ND * np.exp(W.MODEL_DI * (1.0 - np.linalg.norm(Lv.p2_x, axis=1)))
     assert np.all(np.abs(T / ts - 1.0) <= gold["noise"] + 1e-15)
     assert np.array_equal(T, W.temperature_adiabat(Lv.p2_x, 5)) and not np.array_equal(T, W.temperature_adiabat(Lv.p2_x, 6))
+
+
+def test_shear_heating_closed_forms(poly2):
+    """Eq. (WeakTemp)'s shear heating int 2 eta eps(u):eps(u) phi_i / rho (eps deviatoric) on
+    the polyhedral shell, rho = 1: for an affine velocity u = G x (held exactly by P2) and a
+    constant viscosity, f^T h = 2 eta |dev sym G|^2 int f for quadratics f (cone-by-cone
+    integration); a pure dilatation u = x heats nothing; and a uniform temperature tau scales
+    the heating by exp(-E_A tau) exactly (Eq. ViscosityDef)."""
+    Lv, ops = poly2
+    x = Lv.p2_x
+    G = np.random.default_rng(8).standard_normal((3, 3))
+    u = (x @ G.T).T.reshape(-1)                         # [3][n_p2]
+    E = 0.5 * (G + G.T) - np.trace(G) / 3.0 * np.eye(3)
+    law = dict(E_A=0.0, V_A=0.0, r_cmb=0.5, r_surf=1.0, log10_base=[0.3, 0.3])
+    T0 = np.zeros(Lv.n_p2)
+    h = ops.shear_heating(u, T0, law)
+    f = lambda y: 1 + y[:, 0] - 2 * y[:, 1] * y[:, 2] + 0.5 * y[:, 0] ** 2
+    ref = 2.0 * 10 ** 0.3 * (E * E).sum() * _shell_integral(f)
+    assert abs(f(x) @ h - ref) <= 1e-11 * abs(ref)
+    assert np.abs(ops.shear_heating(x.T.reshape(-1), T0, law)).max() <= 1e-13 * np.abs(h).max()
+    law2 = dict(law, E_A=2.0)
+    tau = 0.37
+    assert np.allclose(ops.shear_heating(u, np.full(Lv.n_p2, tau), law2), np.exp(-2.0 * tau) * h,
+                       rtol=1e-13, atol=0)
