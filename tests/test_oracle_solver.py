@@ -223,3 +223,23 @@ def test_bfbt_with_exact_inner_inverse_is_the_exact_schur_inverse(exact_blocks_l
     # with the cheap V-cycle it is only an approximation
     cheap = S.bfbt(r, S.Ac_inv)
     assert np.linalg.norm(cheap - ref) > 1e-3 * np.linalg.norm(ref)
+
+
+def test_viscosity_full_weighting_constants_and_linear_fields():
+    """The coarse-level viscosity (P1 full weighting, normalised): constants are kept on
+    every vertex, and a field linear in the straight coordinates is kept on the vertices
+    inside a macro-tet, where the Freudenthal stencil of coarse edges is centrally symmetric
+    (the last 60 (N-1)(N-2)(N-3)/6 vertices of the numbering)."""
+    from oracle.solver import restrict_viscosity
+    mesh = MacroMesh()
+    Lf, Lc = Level(mesh, 3), Level(mesh, 2)
+    assert np.abs(restrict_viscosity(Lf, Lc, np.full(Lf.n_p1, 7.5)) - 7.5).max() <= 1e-14
+    a = np.array([0.3, -1.2, 0.7])
+    f = lambda X: 2.0 + X @ a
+    got = restrict_viscosity(Lf, Lc, f(Lf.p1_straight))
+    N = 4
+    n_ci = 60 * (N - 1) * (N - 2) * (N - 3) // 6
+    inner = slice(Lc.n_p1 - n_ci, Lc.n_p1)
+    assert np.abs(got[inner] - f(Lc.p1_straight)[inner]).max() <= 1e-13
+    # on the macro boundaries the stencil is not symmetric: there the weighting smooths
+    assert np.abs(got - f(Lc.p1_straight)).max() > 1e-6
