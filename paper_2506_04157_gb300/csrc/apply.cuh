@@ -269,7 +269,7 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
   for (int k = 0; k < kG; ++k) {
     uv[k][0] = uv[k][1] = uv[k][2] = T(0);
     if (HAS_U && codes[k] >= 0) {
-      const int id = codes[k] & 0x1fffffff;
+      const int id = slot_node(codes[k]);
       uv[k][0] = __ldg(P.u + id);
       uv[k][1] = __ldg(P.u + P.n_p2 + id);
       uv[k][2] = __ldg(P.u + 2 * P.n_p2 + id);
@@ -279,7 +279,7 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
 #pragma unroll
     for (int k = 0; k < kG; ++k) {
       const int s = tid + k * kSweepThreads;
-      if (s < NSLOT2) ts[s] = codes[k] >= 0 ? __ldg(P.temp + (codes[k] & 0x1fffffff)) : T(0);
+      if (s < NSLOT2) ts[s] = codes[k] >= 0 ? __ldg(P.temp + slot_node(codes[k])) : T(0);
     }
   }
 #pragma unroll
@@ -289,8 +289,8 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
     const int code = codes[k];
     gid2[s] = code;
     T v0 = uv[k][0], v1 = uv[k][1], v2 = uv[k][2];
-    if (HAS_U && code >= 0 && P.constrained && (code >> 29) != 0) {
-      const int gc = code >> 29;     // 1 surface, 2 CMB
+    if (HAS_U && code >= 0 && P.constrained && slot_class(code) != 0) {
+      const int gc = slot_class(code);     // 1 surface, 2 CMB
       const int bc = gc == 1 ? P.bc_surface : P.bc_cmb;
       if (bc == BC_DIRICHLET) {
         v0 = v1 = v2 = T(0);
@@ -643,8 +643,8 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
     for (int s = tid; s < NSLOT2; s += kSweepThreads) {
       const int code = gid2[s];
       if (code < 0) continue;
-      const int id = code & 0x1fffffff;
-      const int gc = code >> 29;
+      const int id = slot_node(code);
+      const int gc = slot_class(code);
       int cl = NODE_FREE;
       if (P.constrained && gc != 0) {
         const int bc = gc == 1 ? P.bc_surface : P.bc_cmb;

@@ -23,6 +23,14 @@ constexpr int NB1 = TT + 1;            // P1 block edge
 constexpr int NSLOT1 = NB1 * NB1 * NB1;
 constexpr int NSLOT2 = 8 * NSLOT1;
 
+// P2 slot-table entries: the global node id in bits 0-28 and its geometric class (0 interior,
+// 1 outer surface, 2 core-mantle boundary) in bits 29-30; -1 marks a slot outside the macro
+constexpr int kSlotClassShift = 29;
+constexpr int kSlotIdMask = (1 << kSlotClassShift) - 1;
+__host__ __device__ __forceinline__ int slot_code(int id, int cls) { return id | (cls << kSlotClassShift); }
+__host__ __device__ __forceinline__ int slot_node(int code) { return code & kSlotIdMask; }
+__host__ __device__ __forceinline__ int slot_class(int code) { return code >> kSlotClassShift; }
+
 // Numbering of the lattice points of one level (N intervals per macro edge): macro
 // vertices, then macro-edge interiors, macro-face interiors, macro-cell interiors.
 struct Numbering {

@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(128) k_diag_sweep(const ApplyParams<T> P, T* _
   if (ETAQ)
     for (int s = threadIdx.x; s < NSLOT2; s += blockDim.x) {
       const int code = P.ids2[lin * NSLOT2 + s];
-      tsm[s] = code >= 0 ? P.temp[code & 0x1fffffff] : T(0);
+      tsm[s] = code >= 0 ? P.temp[slot_node(code)] : T(0);
     }
   __syncthreads();
   const double QA = MFS_QA, QB = MFS_QB;
@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(128) k_diag_sweep(const ApplyParams<T> P, T* _
   for (int s = threadIdx.x; s < NSLOT2; s += blockDim.x) {
     const int code = P.ids2[lin * NSLOT2 + s];
     if (code < 0) continue;
-    const int64_t id = code & 0x1fffffff;
+    const int64_t id = slot_node(code);
     for (int c = 0; c < 3; ++c) atomicAdd(&diag[c * (int64_t)P.n_p2 + id], ds[c * NSLOT2 + s]);
   }
 }
@@ -976,7 +976,7 @@ __global__ void __launch_bounds__(128) k_grad_sweep(const ApplyParams<double> P,
     slot[9] = (S2 ^ 7) * kSub + base + sub_off(S2);
     double uv[10][3], lv[10][3];
     for (int a = 0; a < 10; ++a) {
-      const int64_t id = tab2[slot[a]] & 0x1fffffff;
+      const int64_t id = slot_node(tab2[slot[a]]);
       for (int c = 0; c < 3; ++c) {
         uv[a][c] = u[c * n2 + id];
         lv[a][c] = lam[c * n2 + id];
@@ -1066,7 +1066,7 @@ __global__ void __launch_bounds__(128) k_buoyancy_sweep(const ApplyParams<double
     const int p0 = perm_at(pmu, 0), p1 = perm_at(pmu, 1), p2 = perm_at(pmu, 2);
     const int base = ci + 5 * cj + 25 * ck;
     double Tv[10];
-    for (int a = 0; a < 10; ++a) Tv[a] = T[tab2[base + slot_off(pmu, a)] & 0x1fffffff];
+    for (int a = 0; a < 10; ++a) Tv[a] = T[slot_node(tab2[base + slot_off(pmu, a)])];
     const double qx = tile.ta * TT + ci, qy = tile.tb * TT + cj, qz = tile.tc * TT + ck;
     double out[10][3];
     for (int a = 0; a < 10; ++a) out[a][0] = out[a][1] = out[a][2] = 0.0;
@@ -1100,7 +1100,7 @@ __global__ void __launch_bounds__(128) k_buoyancy_sweep(const ApplyParams<double
   for (int s = threadIdx.x; s < NSLOT2; s += blockDim.x) {
     const int code = tab2[s];
     if (code < 0) continue;
-    const int64_t id = code & 0x1fffffff;
+    const int64_t id = slot_node(code);
     for (int d = 0; d < 3; ++d) atomicAdd(&f[d * n2 + id], fs[d * NSLOT2 + s]);
   }
 }

@@ -24,7 +24,7 @@ __global__ void id_tables_kernel(const MacroTopo* __restrict__ topo, const Tile*
         int gc = 0;
         if ((mask & ~t.topmask & 15) == 0) gc = 1;
         else if ((mask & ~t.botmask & 15) == 0) gc = 2;
-        code = id | (gc << 29);
+        code = slot_code(id, gc);
       }
     }
     ids2[lin * NSLOT2 + s] = code;
@@ -38,7 +38,7 @@ __global__ void id_tables_kernel(const MacroTopo* __restrict__ topo, const Tile*
 }
 
 mfs_status build_id_tables(const mfs_mesh* M, LevelData& L) {
-  if (L.nb2.total >= (1 << 29)) {
+  if (L.nb2.total > kSlotIdMask) {
     set_error("level %d too large for 29-bit node ids", L.l);
     return MFS_EINVAL;
   }

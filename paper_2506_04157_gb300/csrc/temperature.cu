@@ -200,8 +200,8 @@ __global__ void __launch_bounds__(128) k_temp_apply(const TempArgs<T> P) {
   for (int s = threadIdx.x; s < NSLOT2; s += blockDim.x) {
     const int code = tab2[s];
     const bool ok = code >= 0;
-    const bool drop = !ok || (P.constrained && (code >> 29) != 0);
-    const int64_t id = code & 0x1fffffff;
+    const bool drop = !ok || (P.constrained && slot_class(code) != 0);
+    const int64_t id = slot_node(code);
     xs[s] = (!DIAG && !drop) ? P.x[id] : T(0);
     ys[s] = T(0);
     if (VEL)
@@ -275,8 +275,8 @@ __global__ void __launch_bounds__(128) k_temp_apply(const TempArgs<T> P) {
   __syncthreads();
   for (int s = threadIdx.x; s < NSLOT2; s += blockDim.x) {
     const int code = tab2[s];
-    if (code < 0 || (P.constrained && (code >> 29) != 0)) continue;
-    atomicAdd(&P.y[code & 0x1fffffff], ys[s]);
+    if (code < 0 || (P.constrained && slot_class(code) != 0)) continue;
+    atomicAdd(&P.y[slot_node(code)], ys[s]);
   }
 }
 
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(128) k_temp_rhs(const RhsArgs P) {
   const int* tab2 = P.ids2 + lin * NSLOT2;
   for (int s = threadIdx.x; s < NSLOT2; s += blockDim.x) {
     const int code = tab2[s];
-    const int64_t id = code & 0x1fffffff;
+    const int64_t id = slot_node(code);
     hs[s] = code >= 0 ? P.s0 * P.T0[id] - P.sm * P.Tm[id] : 0.0;
     bs[s] = 0.0;
     if (SHEAR) {
@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(128) k_temp_rhs(const RhsArgs P) {
   for (int s = threadIdx.x; s < NSLOT2; s += blockDim.x) {
     const int code = tab2[s];
     if (code < 0) continue;
-    atomicAdd(&P.b[code & 0x1fffffff], bs[s]);
+    atomicAdd(&P.b[slot_node(code)], bs[s]);
   }
 }
 
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(128) k_wmass(const ApplyParams<T> P, T a2, int
     const int id = P.ids1[lin * NSLOT1 + s];
     eta_s[s] = id >= 0 ? P.eta[id] : T(1);
     const int code = tab2[s];   // P2 slot s < NSLOT1 is the vertex slot s of the P1 block
-    surf_s[s] = (code >= 0 && (code >> 29) == 1) ? 1 : 0;
+    surf_s[s] = (code >= 0 && slot_class(code) == 1) ? 1 : 0;
   }
   const T vol = G.absdet / (T(n) * T(n) * T(n));
   const int2 cinfo = P.classes[tile.cls];
@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(128) k_wmass(const ApplyParams<T> P, T a2, int
     __syncthreads();   // staging of eta done; the previous component flushed
     for (int s = threadIdx.x; s < NSLOT2; s += blockDim.x) {
       const int code = tab2[s];
-      xs[s] = (!DIAG && code >= 0) ? x[c * n_p2 + (code & 0x1fffffff)] : T(0);
+      xs[s] = (!DIAG && code >= 0) ? x[c * n_p2 + slot_node(code)] : T(0);
       ys[s] = T(0);
     }
     __syncthreads();
@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(128) k_wmass(const ApplyParams<T> P, T a2, int
     for (int s = threadIdx.x; s < NSLOT2; s += blockDim.x) {
       const int code = tab2[s];
       if (code < 0) continue;
-      atomicAdd(&y[c * n_p2 + (code & 0x1fffffff)], ys[s]);
+      atomicAdd(&y[c * n_p2 + slot_node(code)], ys[s]);
     }
   }
 }

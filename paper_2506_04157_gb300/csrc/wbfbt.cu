@@ -81,7 +81,7 @@ inline int nblk(int64_t n, int threads = 256, int cap = 8192) {
 // point, so the P2 table's geometric class marks the vertices on the outer surface.
 __device__ __forceinline__ int on_surface(const int* ids2, size_t lin, int s) {
   const int code = ids2[lin * NSLOT2 + s];
-  return (code >= 0 && (code >> 29) == 1) ? 1 : 0;
+  return (code >= 0 && slot_class(code) == 1) ? 1 : 0;
 }
 
 // Element entries k_ab (a < b) of K_{1/sqrt(eta_a)}: sum_q w|det J| grad psi_a . grad psi_b
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(128) k_vmass_lumped(const ApplyParams<double> 
   for (int s = threadIdx.x; s < NSLOT2; s += blockDim.x) {
     const int code = P.ids2[lin * NSLOT2 + s];
     if (code < 0) continue;
-    atomicAdd(&d[code & 0x1fffffff], ds[s]);
+    atomicAdd(&d[slot_node(code)], ds[s]);
   }
 }
 
