@@ -47,6 +47,18 @@ def test_errors_without_gpu_or_bad_args(lib):
     with pytest.raises(mfs.MfsError) as e:
         mfs.Problem(m)
     assert "host-only" in str(e.value)
+    # null handles are refused with MFS_EINVAL (1) and a message, before any device work
+    import ctypes
+    L = mfs.lib()
+    null = ctypes.c_void_p()
+    for name, args in [("mfs_apply_vmass", (null, 0, 1.0, null, null)),
+                       ("mfs_lumped_vmass", (null, 1.0, null)),
+                       ("mfs_apply_poisson", (null, 1, 0, 1.0, null, null)),
+                       ("mfs_apply_schur", (null, None, 0, null, null, None)),
+                       ("mfs_set_temperature", (null, null)),
+                       ("mfs_temperature_step", (null, None, null, null, null, null, 0.1, 0.1, null, null, None))]:
+        assert getattr(L, name)(*args) == 1, name
+        assert L.mfs_last_error(), name
 
 
 @pytest.mark.parametrize("blending", [True, False])
