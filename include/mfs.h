@@ -378,17 +378,21 @@ mfs_status mfs_temp_apply(mfs_problem* prob, mfs_prec prec, double cM, double cC
 mfs_status mfs_temp_rhs(mfs_problem* prob, const mfs_temp_params* params, const double* T0_hat, const double* Tm_hat,
                         const double* u_star, const double* T_star, double tau_np1, double tau_n, double* b);
 
-/* T_hat = MMOC(T, u_new, u_old, tau) (Sec. 3): every P2 node traced back over a step tau with one
- * classical RK4 step along u(t) linear in time from u_old (start of the step) to u_new (end),
- * and T evaluated there (departure points outside the shell moved radially onto it).  T, T_hat:
- * [n_p2]; u_new, u_old: [3][n_p2]; X_dep: [3][n_p2] departure points, or NULL.  FP64 device
- * vectors.  Errors: MFS_EINVAL, MFS_ENOMEM, MFS_ECUDA. */
+/* T_hat = MMOC(T, u_new, u_old, tau) (Sec. 3): one particle per P2 node traced back over a step
+ * tau with one classical RK4 step along u(t) linear in time from u_old (start of the step) to
+ * u_new (end), and T evaluated there (departure points outside the shell moved radially onto
+ * it).  The particles start at the nodes (X_start = NULL) or at the points X_start [3][n_p2]
+ * (a particle path continued over an earlier step).  T, T_hat: [n_p2]; u_new, u_old:
+ * [3][n_p2]; X_dep: [3][n_p2] departure points, or NULL.  FP64 device vectors.
+ * Errors: MFS_EINVAL, MFS_ENOMEM, MFS_ECUDA. */
 mfs_status mfs_mmoc(mfs_problem* prob, const double* T, const double* u_new, const double* u_old, double tau,
-                    double* T_hat, double* X_dep);
+                    const double* X_start, double* T_hat, double* X_dep);
 
 /* One temperature step (Sec. 3 and Sec. 6): u* and T* by linear extrapolation (Eq.
- * Extrapolation), T0_hat = MMOC(T_n, u*, u_n, tau_np1), Tm_hat = MMOC(MMOC(T_nm1, u*, u_n,
- * tau_np1), u_n, u_nm1, tau_n), then Eq. (WeakTemp) for T_np1 with the Dirichlet values of T_bc
+ * Extrapolation), T0_hat = MMOC(T_n, u*, u_n, tau_np1) at the departure points Y of the nodes,
+ * Tm_hat = T_nm1 at the feet of the same particles traced on from Y with (u_n, u_nm1, tau_n) —
+ * the characteristic X(t^{n+1}, t^{n-1}, x) that the nested MMOC of Sec. 3 approximates —
+ * then Eq. (WeakTemp) for T_np1 with the Dirichlet values of T_bc
  * on both spheres — without its advection term: the MMOC values carry the advection, and the
  * solve is the energy equation without it (Sec. 3) — by FGMRES (FP64) preconditioned by an
  * FP32 Jacobi-CG on s1 M + tau k/(Pe Cp) D_s.  T_*: [n_p2], u_*: [3][n_p2], FP64 device vectors.

@@ -13,7 +13,8 @@ Paper passages followed (arxiv 2506.04157):
     Runge-Kutta method along the velocity interpolated linearly in time between u^{n+1}_*
     (at t^{n+1}) and u^n (at t^n), T^n evaluated at the departure points;
         T^n_hat = MMOC(T^n, u*^{n+1}, u^n, tau^{n+1}),
-        T^{n-1}_hat = MMOC(MMOC(T^{n-1}, u*^{n+1}, u^n, tau^{n+1}), u^n, u^{n-1}, tau^n).
+        T^{n-1}_hat = MMOC(MMOC(T^{n-1}, u*^{n+1}, u^n, tau^{n+1}), u^n, u^{n-1}, tau^n),
+    approximations of T(t^n, X(t^{n+1}, t^n, x)) and T(t^{n-1}, X(t^{n+1}, t^{n-1}, x)).
   * Sec. 6, Eq. (WeakTemp): for all w in the P2 space vanishing on both spheres,
       int s1 T w + tau (k/(Pe Cp) int grad T . grad(w/rho) - Di alpha/Cp int T (u*.g) w)
         = int (s0 T0_hat - sm Tm_hat) w
@@ -37,8 +38,14 @@ Readings:
   * Particles start at the P2 nodes (the MMOC result is the nodal interpolant); one RK4 step
     of length tau per MMOC; a departure point outside the shell is moved radially onto the
     nearer sphere (blended) or onto the nearest point of the nearest micro-tet (polyhedral).
-  * The nested MMOC for T^{n-1}_hat is composed as printed (inner tracing over
-    [t^n, t^{n+1}], its nodal interpolant then traced over [t^{n-1}, t^n]).
+  * The nested MMOC for T^{n-1}_hat continues the particles: traced from the nodes over
+    [t^n, t^{n+1}] with u*^{n+1}, u^n (the inner MMOC's arguments), then on from where they
+    arrived over [t^{n-1}, t^n] with u^n, u^{n-1} (the outer MMOC's), and T^{n-1} evaluated once
+    at the end: the characteristic X(t^{n+1}, t^{n-1}, x) the paper defines.  Composing the two
+    MMOC maps as nodal fields in the printed nesting order would apply the two sub-steps to a
+    point in reverse order (the field MMOC(f)(x) = f(X(x)) composes its maps inside out):
+    that misses the characteristic by O(tau^3) per step for a velocity that changes in time
+    (and interpolates twice), against the RK4 error O(tau^5) of the continued particles.
   * eps is the deviatoric strain rate (as in A); eta(x, T*) from the viscosity law at the
     quadrature points with the P2 interpolant of T*.
   * rho(r) = exp(int_{r_surf}^r d ln rho/dr) from the density table (as for C and the buoyancy).
@@ -327,12 +334,23 @@ def mmoc(loc, T, u_new, u_old, tau):
     return loc.eval_p2(T, mmoc_departure(loc, u_new, u_old, tau))
 
 
+def mmoc_history(loc, T_n, T_nm1, u_star, u_n, u_nm1, tau_np1, tau_n):
+    """The two history values of the BDF2 step (Sec. 3): T^n and T^{n-1} at the feet of the
+    characteristics through the P2 nodes at t^{n+1}.  The particles leave the nodes at
+    t^{n+1}, reach Y at t^n (one RK4 step with u between u*^{n+1} and u^n) and are traced on
+    from Y to t^{n-1} (one step with u between u^n and u^{n-1}): T^{n-1} is evaluated once,
+    at the end of the same particle paths, T(t^{n-1}, X(t^{n+1}, t^{n-1}, x)) as defined with
+    Eq. (timeDerivative)."""
+    Y = mmoc_departure(loc, u_star, u_n, tau_np1)
+    Z = mmoc_departure(loc, u_n, u_nm1, tau_n, X=Y)
+    return loc.eval_p2(T_n, Y), loc.eval_p2(T_nm1, Z)
+
+
 def temperature_step(ops, loc, T_n, T_nm1, u_n, u_nm1, tau_np1, tau_n, params, T_bc, law=None, load=None):
     """One temperature step of Sec. 3 and Sec. 6: extrapolations, the two MMOC evaluations,
     and the solve of Eq. (WeakTemp).  Returns (T^{n+1}, u*^{n+1}, T*^{n+1})."""
     u_star = extrapolate(u_n, u_nm1, tau_np1, tau_n)
     T_star = extrapolate(T_n, T_nm1, tau_np1, tau_n)
-    T0_hat = mmoc(loc, T_n, u_star, u_n, tau_np1)
-    Tm_hat = mmoc(loc, mmoc(loc, T_nm1, u_star, u_n, tau_np1), u_n, u_nm1, tau_n)
+    T0_hat, Tm_hat = mmoc_history(loc, T_n, T_nm1, u_star, u_n, u_nm1, tau_np1, tau_n)
     T_np1 = solve_temperature(ops, T0_hat, Tm_hat, u_star, tau_np1, tau_n, params, T_bc, T_star, law, load)
     return T_np1, u_star, T_star

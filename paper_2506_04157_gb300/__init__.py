@@ -127,7 +127,7 @@ _SIGS = {
     "mfs_temp_params_default": ([ctypes.POINTER(TempParams)], None),
     "mfs_temp_apply": ([_vp, _i, _d, _d, _d, _d, _i, _i, _vp, _vp, _vp], _i),
     "mfs_temp_rhs": ([_vp, ctypes.POINTER(TempParams), _vp, _vp, _vp, _vp, _d, _d, _vp], _i),
-    "mfs_mmoc": ([_vp, _vp, _vp, _vp, _d, _vp, _vp], _i),
+    "mfs_mmoc": ([_vp, _vp, _vp, _vp, _d, _vp, _vp, _vp], _i),
     "mfs_temperature_step": ([_vp, ctypes.POINTER(TempParams), _vp, _vp, _vp, _vp, _d, _d, _vp, _vp,
                               ctypes.POINTER(TempStats)], _i),
 }
@@ -453,14 +453,18 @@ class Problem:
                                   _ptr(u_star) if u_star is not None else None,
                                   _ptr(T_star) if T_star is not None else None, tau_np1, tau_n, _ptr(b)))
 
-    def mmoc(self, T, u_new, u_old, tau, T_hat, X_dep=None):
+    def mmoc(self, T, u_new, u_old, tau, T_hat, X_dep=None, X_start=None):
+        """T_hat = T at the departure points of particles starting at the P2 nodes (or at
+        X_start [3][n_p2]) after one RK4 step back over tau; X_dep receives those points."""
         import torch
         nu, _ = self._sizes(self.mesh.l_max)
         _need(T, nu // 3, torch.float64, "T"); _need(T_hat, nu // 3, torch.float64, "T_hat")
         _need(u_new, nu, torch.float64, "u_new"); _need(u_old, nu, torch.float64, "u_old")
-        if X_dep is not None:
-            _need(X_dep, nu, torch.float64, "X_dep")
-        _check(lib().mfs_mmoc(self.handle, _ptr(T), _ptr(u_new), _ptr(u_old), tau, _ptr(T_hat),
+        for t, name in ((X_dep, "X_dep"), (X_start, "X_start")):
+            if t is not None:
+                _need(t, nu, torch.float64, name)
+        _check(lib().mfs_mmoc(self.handle, _ptr(T), _ptr(u_new), _ptr(u_old), tau,
+                              _ptr(X_start) if X_start is not None else None, _ptr(T_hat),
                               _ptr(X_dep) if X_dep is not None else None))
 
     def temperature_step(self, T_n, T_nm1, u_n, u_nm1, tau_np1, tau_n, T_bc, T_np1, raise_on_error=True, **params):

@@ -11,7 +11,8 @@
 //  * the particle MMOC: one classical RK4 step backwards from every P2 node along the velocity
 //    interpolated linearly in time, then the P2 field at the departure point, with point
 //    location in the blended shell (face by the largest e.n, inverse blending, macro Kuhn
-//    coordinates, Freudenthal cube and type);
+//    coordinates, Freudenthal cube and type); for T^{n-1} the same particles are traced on
+//    over the second step (the characteristic X(t^{n+1}, t^{n-1}, x) of Sec. 3);
 //  * the solve: FGMRES in FP64 preconditioned by a Jacobi-CG in FP32 on the symmetric part
 //    s1 M + tau k/(Pe Cp) D_s of the left-hand side.  The left-hand side has no advection
 //    block: Sec. 3 solves the energy equation without the advection after the MMOC (the
@@ -589,11 +590,14 @@ __device__ void velocity_at(const MmocArgs& A, const double* un, const double* u
   }
 }
 
-__global__ void k_mmoc(const MmocArgs A, const double* __restrict__ T, const double* __restrict__ un,
-                       const double* __restrict__ uo, double tau, double* __restrict__ That, double* __restrict__ Xout) {
+// particle i starts at node i (Xin = null) or at Xin[:, i]
+__global__ void k_mmoc(const MmocArgs A, const double* __restrict__ Xin, const double* __restrict__ T,
+                       const double* __restrict__ un, const double* __restrict__ uo, double tau,
+                       double* __restrict__ That, double* __restrict__ Xout) {
   TM_STRIDE(i, A.n_p2) {
     const int64_t n2 = A.n_p2;
-    const double x[3] = {A.xyz[i], A.xyz[n2 + i], A.xyz[2 * n2 + i]};
+    const double* X0 = Xin ? Xin : A.xyz;
+    const double x[3] = {X0[i], X0[n2 + i], X0[2 * n2 + i]};
     double k1[3], k2[3], k3[3], k4[3], y[3];
     velocity_at(A, un, uo, 1.0, 0.0, x, k1);
     for (int c = 0; c < 3; ++c) y[c] = x[c] - 0.5 * tau * k1[c];
@@ -874,8 +878,8 @@ static mfs_status temp_rhs(mfs_problem* Pb, const mfs_temp_params& tp, const dou
   return MFS_OK;
 }
 
-static mfs_status temp_mmoc(mfs_problem* Pb, TempWork* W, const double* T, const double* un, const double* uo,
-                            double tau, double* That, double* Xout) {
+static mfs_status temp_mmoc(mfs_problem* Pb, TempWork* W, const double* Xin, const double* T, const double* un,
+                            const double* uo, double tau, double* That, double* Xout) {
   mfs_mesh* M = Pb->mesh;
   const LevelData& Lv = M->levels[M->l_max];
   MmocArgs a{};
@@ -888,7 +892,7 @@ static mfs_status temp_mmoc(mfs_problem* Pb, TempWork* W, const double* T, const
   a.r_cmb = M->host.r_cmb;
   a.r_surf = M->host.r_surf;
   a.xyz = W->xyz;
-  k_mmoc<<<tblk(a.n_p2, 128), 128, 0, M->ctx->stream>>>(a, T, un, uo, tau, That, Xout);
+  k_mmoc<<<tblk(a.n_p2, 128), 128, 0, M->ctx->stream>>>(a, Xin, T, un, uo, tau, That, Xout);
   MFS_CUDA(cudaGetLastError());
   return MFS_OK;
 }
@@ -1108,7 +1112,7 @@ mfs_status mfs_temp_rhs(mfs_problem* Pb, const mfs_temp_params* params, const do
 }
 
 mfs_status mfs_mmoc(mfs_problem* Pb, const double* T, const double* u_new, const double* u_old, double tau,
-                    double* T_hat, double* X_dep) {
+                    const double* X_start, double* T_hat, double* X_dep) {
   MFS_TRY(temp_check(Pb));
   if (!T || !u_new || !u_old || !T_hat || !std::isfinite(tau)) {
     set_error("null vector or invalid step");
@@ -1116,7 +1120,11 @@ mfs_status mfs_mmoc(mfs_problem* Pb, const double* T, const double* u_new, const
   }
   TempWork* W = nullptr;
   MFS_TRY(temp_work(Pb, 1, &W));
-  return temp_mmoc(Pb, W, T, u_new, u_old, tau, T_hat, X_dep);
+  if (X_start && (X_start == X_dep)) {
+    set_error("X_start and X_dep must be distinct");
+    return MFS_EINVAL;
+  }
+  return temp_mmoc(Pb, W, X_start, T, u_new, u_old, tau, T_hat, X_dep);
 }
 
 mfs_status mfs_temperature_step(mfs_problem* Pb, const mfs_temp_params* params, const double* T_n,
@@ -1143,9 +1151,10 @@ mfs_status mfs_temperature_step(mfs_problem* Pb, const mfs_temp_params* params, 
   Blas<double>::axpbypcz(3 * n, 1.0 + r, u_n, -r, u_nm1, 0.0, W->ustar, s);
   Blas<double>::axpbypcz(n, 1.0 + r, T_n, -r, T_nm1, 0.0, W->Tstar, s);
   // MMOC for the two history values
-  MFS_TRY(temp_mmoc(Pb, W, T_n, W->ustar, u_n, tau_np1, W->T0h, nullptr));
-  MFS_TRY(temp_mmoc(Pb, W, T_nm1, W->ustar, u_n, tau_np1, W->tmp, nullptr));
-  MFS_TRY(temp_mmoc(Pb, W, W->tmp, u_n, u_nm1, tau_n, W->Tmh, nullptr));
+  // the particles leave the nodes at t^{n+1} and reach Y = W->tmp at t^n; the same particles
+  // are traced on to t^{n-1}, where T^{n-1} is read (the characteristic X(t^{n+1}, t^{n-1}, x))
+  MFS_TRY(temp_mmoc(Pb, W, nullptr, T_n, W->ustar, u_n, tau_np1, W->T0h, W->tmp));
+  MFS_TRY(temp_mmoc(Pb, W, W->tmp, T_nm1, u_n, u_nm1, tau_n, W->Tmh, nullptr));
   // right-hand side, then the Dirichlet values moved to it
   MFS_TRY(temp_rhs(Pb, tp, W->T0h, W->Tmh, W->ustar, W->Tstar, tau_np1, tau_n, W->b));
   const double s1 = (2 * tau_np1 + tau_n) / (tau_np1 + tau_n);

@@ -103,6 +103,12 @@ def test_mmoc_matches_oracle():
     Xr = mmoc_departure(loc, u_new, u_old, 0.03)
     assert np.abs(X.cpu().numpy().reshape(3, -1).T - Xr).max() <= 1e-12
     assert np.abs(Th.cpu().numpy() - mmoc(loc, T, u_new, u_old, 0.03)).max() <= 1e-10 * np.abs(T).max()
+    # the same particles traced on over a second step from where they arrived
+    X2 = torch.empty_like(X)
+    prob.mmoc(dev(T), dev(u_old), dev(u_new), 0.02, Th, X2, X_start=X)
+    Xr2 = mmoc_departure(loc, u_old, u_new, 0.02, X=Xr)
+    assert np.abs(X2.cpu().numpy().reshape(3, -1).T - Xr2).max() <= 1e-12
+    assert np.abs(Th.cpu().numpy() - loc.eval_p2(T, Xr2)).max() <= 1e-10 * np.abs(T).max()
 
 
 def test_temperature_step_matches_oracle():
