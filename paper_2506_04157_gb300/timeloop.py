@@ -51,8 +51,8 @@ class CoupledStepper:
         T1 = torch.empty_like(state["T_n"])
         st_T = self.prob.temperature_step(state["T_n"], state["T_nm1"], state["u_n"], state["u_nm1"], tau_np1, tau_n,
                                           T_bc, T1, **self.tp)
-        u1 = state["u_n"].clone()
-        p1 = state["p"].clone()
+        u1 = torch.empty_like(state["u_n"])   # stokes() starts it from the Dirichlet values
+        p1 = state["p"].clone()               # the pressure starts from the previous one
         st_S = self.stokes(T1, u1, p1)
         new = dict(T_n=T1, T_nm1=state["T_n"], u_n=u1, u_nm1=state["u_n"], p=p1)
         return new, dict(temperature=st_T, stokes=st_S)
