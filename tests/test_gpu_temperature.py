@@ -2,8 +2,8 @@
 P2 blocks M, D, D_s, C(u), R(u) (plain and constrained), the right-hand side with and without
 shear heating, the RK4 MMOC with its departure points, and one full step.
 
-Not yet run on a GB300: the module is marked unverified (skipped unless MFS_RUN_UNVERIFIED=1)
-until its first GPU run."""
+The temperature kernels have not run on a GPU yet: the module is marked unverified (skipped
+unless MFS_RUN_UNVERIFIED=1) until they have."""
 import functools
 
 import numpy as np

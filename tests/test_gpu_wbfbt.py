@@ -167,9 +167,9 @@ def test_solve_with_wbfbt(mixed, al):
     assert np.linalg.norm(pn - pd) / np.linalg.norm(pd) < 1e-5
 
 
-# ---- the consistent vector mass (vmass = 1).  Written after the last GPU session of this
-# build and checked on the CPU only (per-tet arithmetic against the oracle's element
-# matrices, the CG flow with the oracle's matrices): skipped until it has run on a GPU.
+# ---- the consistent vector mass (vmass = 1).  Its GPU code has been checked on the CPU only
+# (per-tet arithmetic against the oracle's element matrices, the CG flow with the oracle's
+# matrices): marked unverified until it has run on a GPU.
 UNRUN = pytest.mark.unverified
 
 
