@@ -217,7 +217,8 @@ def test_wbfbt_consistent_apply_fp64(al, ar):
 @UNRUN
 def test_solve_with_wbfbt_consistent_mass():
     """FGMRES with the weighted BFBT on the consistent mass (the paper's tol_VectorMass = 1e-4)
-    reaches the oracle's direct solution."""
+    and the default omega = 0.3 (the best scaling with this mass) reaches the oracle's direct
+    solution."""
     H, ctx, gm, prob = setup(2)
     L = H.levels[2]
     rng = np.random.default_rng(32)
@@ -226,7 +227,7 @@ def test_solve_with_wbfbt_consistent_mass():
     u = torch.zeros(3 * L.n_p2, dtype=torch.float64, device="cuda")
     p = torch.zeros(L.n_p1, dtype=torch.float64, device="cuda")
     st = prob.solve(torch.tensor(f, device="cuda"), torch.tensor(g, device="cuda"), u, p, mixed=2, schur=3,
-                    vmass=1, omega=0.03, restart=50, max_iters=1500, rtol=1e-10)
+                    vmass=1, restart=50, max_iters=1500, rtol=1e-10)
     assert st["status"] == "MFS_OK" and st["rel_residual"] <= 1e-10, st
     ud, pd = direct_solve(H, f, g, 0 * f, 0 * g)
     assert np.linalg.norm(u.cpu().numpy() - ud) / np.linalg.norm(ud) < 1e-5
