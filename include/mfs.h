@@ -261,7 +261,10 @@ typedef struct {
   int vmass;          /* weighted-BFBT vector mass M_{sqrt(eta)}: 0 the lumped mass (default),
                          1 the consistent mass (mfs_apply_vmass) by Jacobi-preconditioned CG on
                          the constrained velocity space to tol_VectorMass (Sec. 5.2.3); with
-                         schur = 3 the cg_M_* statistics count these CGs */
+                         schur = 3 the cg_M_* statistics count these CGs.  The consistent mass
+                         keeps the approximation's spectrum of order one under refinement and
+                         suits omega = 0.3; the lumped one's grows like 1/h and wants a
+                         smaller omega (about 0.03 on levels 1-2) */
   double tol_VectorMass; /* CG on the consistent M_{sqrt(eta)}, relative (1e-4; Table
                          parametertable) */
 } mfs_solve_opts;
