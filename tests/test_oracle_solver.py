@@ -243,3 +243,19 @@ def test_viscosity_full_weighting_constants_and_linear_fields():
     assert np.abs(got[inner] - f(Lc.p1_straight)[inner]).max() <= 1e-13
     # on the macro boundaries the stencil is not symmetric: there the weighting smooths
     assert np.abs(got - f(Lc.p1_straight)).max() > 1e-6
+
+
+def test_power_iteration_estimate_of_the_chebyshev_interval():
+    """The Chebyshev upper bound's estimate (15 power iterations on D^-1 A from the seeded
+    vector): on D^-1 A = diag(lambda) with a known spectrum the estimate approaches the largest
+    eigenvalue from below, within the power method's (lambda_2/lambda_1)^k rate, and the
+    projection keeps the projected-out directions out of it."""
+    from oracle.solver import power_max_eig
+    lam = np.concatenate([np.linspace(0.01, 1.6, 60), [1.8, 2.0]])
+    est = power_max_eig(lambda v: lam * v, np.ones(lam.size), lambda v: v, lam.size)
+    assert 1.8 < est <= 2.0 + 1e-12
+    assert 2.0 - est < 2.0 * (1.8 / 2.0) ** 14
+    # a projection that removes the top eigenvector leaves the next one as the estimate
+    proj = lambda v: np.concatenate([v[:-1], [0.0]])
+    est2 = power_max_eig(lambda v: lam * v, np.ones(lam.size), proj, lam.size)
+    assert 1.6 < est2 <= 1.8 + 1e-12
