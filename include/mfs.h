@@ -360,6 +360,14 @@ typedef struct {
 
 void mfs_temp_params_default(mfs_temp_params* params);
 
+/* The 27-point quadrature rule of the temperature blocks and the consistent vector mass, as
+ * the kernels use it: Stroud's conical product rule on the reference tet (Gauss-Jacobi points
+ * with weights (1-s)^2 and (1-t), Gauss-Legendre in the third direction; exact to degree 5;
+ * weights summing to 1/6).  lam: [27][4] barycentric coordinates, w: [27] (HOST arrays).
+ * Host-only (no device needed).  Errors: MFS_EINVAL (null pointer, or the rule failed its
+ * exactness check). */
+mfs_status mfs_temp_rule(double* lam, double* w);
+
 /* y = (cM M + cC C(u) + cD D + cR R(u)) x on the finest level (Eq. WeakTemp's blocks):
  *   M = int phi_j phi_i, C(u) = int (u . grad phi_j) phi_i, R(u) = int (u . g) phi_j phi_i with
  *   g = -x/|x|, D = int grad phi_j . grad(phi_i / rho) (sym = 1: int grad phi_j . grad phi_i / rho),

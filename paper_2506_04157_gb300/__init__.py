@@ -124,6 +124,7 @@ _SIGS = {
     "mfs_apply_poisson": ([_vp, _i, _i, _d, _vp, _vp], _i),
     "mfs_lumped_vmass": ([_vp, _d, _vp], _i),
     "mfs_apply_vmass": ([_vp, _i, _d, _vp, _vp], _i),
+    "mfs_temp_rule": ([_vp, _vp], _i),
     "mfs_temp_params_default": ([ctypes.POINTER(TempParams)], None),
     "mfs_temp_apply": ([_vp, _i, _d, _d, _d, _d, _i, _i, _vp, _vp, _vp], _i),
     "mfs_temp_rhs": ([_vp, ctypes.POINTER(TempParams), _vp, _vp, _vp, _vp, _d, _d, _vp], _i),
@@ -513,6 +514,14 @@ class Problem:
         if getattr(self, "handle", None) and _lib is not None:
             _lib.mfs_problem_destroy(self.handle)
             self.handle = None
+
+
+def temp_rule():
+    """(barycentrics [27, 4], weights [27]) of the library's degree-5 conical rule (host)."""
+    lam = np.empty((27, 4), dtype=np.float64)
+    w = np.empty(27, dtype=np.float64)
+    _check(lib().mfs_temp_rule(lam.ctypes.data_as(ctypes.c_void_p), w.ctypes.data_as(ctypes.c_void_p)))
+    return lam, w
 
 
 def _ptr_array(tensors):

@@ -1176,6 +1176,21 @@ mfs_status mfs_temperature_step(mfs_problem* Pb, const mfs_temp_params* params, 
   return rc;
 }
 
+mfs_status mfs_temp_rule(double* lam, double* w) {
+  if (!lam || !w) {
+    set_error("null argument");
+    return MFS_EINVAL;
+  }
+  double l[kTQ][4], ww[kTQ];
+  if (!conical_rule27(l, ww)) {
+    set_error("the conical quadrature rule failed its exactness check");
+    return MFS_EINVAL;
+  }
+  std::memcpy(lam, l, sizeof(l));
+  std::memcpy(w, ww, sizeof(ww));
+  return MFS_OK;
+}
+
 mfs_status mfs_apply_vmass(mfs_problem* Pb, mfs_prec prec, double a, const void* x, void* y) {
   if (!Pb || !x || !y) {
     set_error("null argument");

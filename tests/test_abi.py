@@ -98,3 +98,11 @@ def test_library_default_options_match_paper_table(lib):
     t = mfs.Problem.temp_params()
     assert t.tol_T == 1e-10 and t.restart == 30
     assert ctypes.sizeof(mfs.SolveOpts) == 152 and ctypes.sizeof(mfs.TempParams) == 96
+
+
+def test_library_quadrature_rule_matches_oracle(lib):
+    """The library's own Gauss-Jacobi construction of the 27-point conical rule (host code of
+    the temperature kernels) against the oracle's, built from scipy's Gauss-Jacobi roots."""
+    from oracle.temperature import QUAD5_BARY, QUAD5_W
+    lam, w = mfs.temp_rule()
+    assert np.abs(lam - QUAD5_BARY).max() <= 1e-15 and np.abs(w - QUAD5_W).max() <= 1e-16
