@@ -215,6 +215,14 @@ mfs_status mfs_apply_mass(mfs_problem* prob, int lvl, mfs_prec prec, const void*
 mfs_status mfs_prolongate(mfs_problem* prob, int lvl, mfs_prec prec, const void* xc, void* xf);
 mfs_status mfs_restrict(mfs_problem* prob, int lvl, mfs_prec prec, const void* rf, void* rc);
 
+/* The scalar P2 prolongation of mfs_prolongate before the projections, as a CSR matrix with
+ * n_p2(lvl) rows (fine nodes) and n_p2(lvl-1) columns: each fine node takes the coarse P2
+ * interpolant at its position, one entry per nonzero coarse basis value.  Host-only (a
+ * host-only mesh suffices).  nnz receives the entry count; rp [n_p2(lvl)+1], ci [nnz], w [nnz]
+ * are HOST arrays, each filled when not NULL (call once with NULLs to size them).
+ * 1 <= lvl <= l_max.  Errors: MFS_EINVAL. */
+mfs_status mfs_mesh_prolongation(const mfs_mesh* mesh, int lvl, int* nnz, int* rp, int* ci, double* w);
+
 /* One V-cycle for the constrained A on level lvl (paper Sec. 5.2.2): `steps` Chebyshev
  * pre- and post-smoothing steps of `degree` applications each, exact FP64 coarse solve on
  * l_min.  f: right-hand side [3][n_p2]; u: result (overwritten, the cycle starts from 0).

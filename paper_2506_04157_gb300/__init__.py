@@ -125,6 +125,7 @@ _SIGS = {
     "mfs_lumped_vmass": ([_vp, _d, _vp], _i),
     "mfs_apply_vmass": ([_vp, _i, _d, _vp, _vp], _i),
     "mfs_temp_rule": ([_vp, _vp], _i),
+    "mfs_mesh_prolongation": ([_vp, _i, _vp, _vp, _vp, _vp], _i),
     "mfs_temp_params_default": ([ctypes.POINTER(TempParams)], None),
     "mfs_temp_apply": ([_vp, _i, _d, _d, _d, _d, _i, _i, _vp, _vp, _vp], _i),
     "mfs_temp_rhs": ([_vp, ctypes.POINTER(TempParams), _vp, _vp, _vp, _vp, _d, _d, _vp], _i),
@@ -228,6 +229,17 @@ class Mesh:
         _check(lib().mfs_mesh_coords(self.handle, level, int(p2), int(blended),
                                      buf.ctypes.data_as(ctypes.c_void_p)))
         return buf
+
+    def prolongation(self, level):
+        """(rp, ci, w): CSR of the scalar P2 prolongation from level-1 to level (host)."""
+        nnz = ctypes.c_int()
+        _check(lib().mfs_mesh_prolongation(self.handle, level, ctypes.byref(nnz), None, None, None))
+        rp = np.empty(self.info(level).n_p2 + 1, dtype=np.int32)
+        ci = np.empty(nnz.value, dtype=np.int32)
+        w = np.empty(nnz.value, dtype=np.float64)
+        vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        _check(lib().mfs_mesh_prolongation(self.handle, level, ctypes.byref(nnz), vp(rp), vp(ci), vp(w)))
+        return rp, ci, w
 
     def node_class(self, level, p2=True):
         n = self.info(level).n_p2 if p2 else self.info(level).n_p1

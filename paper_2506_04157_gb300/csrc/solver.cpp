@@ -179,10 +179,12 @@ static mfs_status build_boundary(mfs_problem* Pb, int l, BoundaryList& BL, cudaS
 // Prolongation from level l-1 to level l (P2 nodes): every fine node is a quarter point
 // (barycentrics s/4, sum s = 4) of a coarse micro-tet; its value is the coarse P2
 // interpolant there.  The first coarse tet met defines the row (all give the same value).
-static mfs_status build_transfer(mfs_problem* Pb, int l, Csr& P, Csr& R, cudaStream_t s, MG* G) {
+// CSR (host) of the P2 prolongation from level l-1 to level l: every fine P2 node (a quarter
+// point of a coarse micro-tet) takes the coarse P2 interpolant there, the nonzero basis values
+static mfs_status prolongation_csr(const mfs_mesh* M, int l, std::vector<int>& rp, std::vector<int>& ci,
+                                   std::vector<double>& w) {
   static const int PERM[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
   static const int LE[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
-  const mfs_mesh* M = Pb->mesh;
   const int n = 1 << (l - 1);          // coarse micro-tets per macro edge
   const int Nc = 2 * n, Nf = 4 * n;
   const Numbering nbc = make_numbering(Nc), nbf = make_numbering(Nf);
@@ -202,8 +204,6 @@ static mfs_status build_transfer(mfs_problem* Pb, int l, Csr& P, Csr& R, cudaStr
         phi.push_back(ph);
       }
   std::vector<int> cnt(nbf.total, 0);
-  std::vector<int> rowc;   // per fine node: 10 coarse cols, set on first visit
-  std::vector<float> dummy;
   std::vector<int> cols((size_t)nbf.total * 10, -1);
   std::vector<double> vals((size_t)nbf.total * 10, 0.0);
   std::vector<char> seen(nbf.total, 0);
@@ -262,16 +262,26 @@ static mfs_status build_transfer(mfs_problem* Pb, int l, Csr& P, Csr& R, cudaStr
       return MFS_EINVAL;
     }
   // CSR of P
-  std::vector<int> rp(nbf.total + 1, 0);
+  rp.assign(nbf.total + 1, 0);
   for (int i = 0; i < nbf.total; ++i) rp[i + 1] = rp[i] + cnt[i];
   const int nnz = rp[nbf.total];
-  std::vector<int> ci(nnz);
-  std::vector<double> w(nnz);
+  ci.assign(nnz, 0);
+  w.assign(nnz, 0.0);
   for (int i = 0; i < nbf.total; ++i)
     for (int k = 0; k < cnt[i]; ++k) {
       ci[rp[i] + k] = cols[(size_t)i * 10 + k];
       w[rp[i] + k] = vals[(size_t)i * 10 + k];
     }
+  return MFS_OK;
+}
+
+static mfs_status build_transfer(mfs_problem* Pb, int l, Csr& P, Csr& R, cudaStream_t s, MG* G) {
+  const mfs_mesh* M = Pb->mesh;
+  const Numbering nbc = make_numbering(2 << (l - 1)), nbf = make_numbering(4 << (l - 1));
+  std::vector<int> rp, ci;
+  std::vector<double> w;
+  MFS_TRY(prolongation_csr(M, l, rp, ci, w));
+  const int nnz = rp[nbf.total];
   // CSR of P^T (restriction), rows in increasing fine index per coarse row
   std::vector<int> rrp(nbc.total + 1, 0);
   for (int k = 0; k < nnz; ++k) rrp[ci[k] + 1]++;
@@ -1410,6 +1420,21 @@ void mfs_solve_opts_default(mfs_solve_opts* o) {
   o->tol_wBFBT = 1e-10;
   o->vmass = 0;
   o->tol_VectorMass = 1e-4;
+}
+
+mfs_status mfs_mesh_prolongation(const mfs_mesh* M, int lvl, int* nnz, int* rp, int* ci, double* w) {
+  if (!M || !nnz || lvl < 1 || lvl > M->l_max) {
+    set_error("null argument or level outside 1..l_max");
+    return MFS_EINVAL;
+  }
+  std::vector<int> r, c;
+  std::vector<double> v;
+  MFS_TRY(prolongation_csr(M, lvl, r, c, v));
+  *nnz = (int)c.size();
+  if (rp) std::memcpy(rp, r.data(), sizeof(int) * r.size());
+  if (ci) std::memcpy(ci, c.data(), sizeof(int) * c.size());
+  if (w) std::memcpy(w, v.data(), sizeof(double) * v.size());
+  return MFS_OK;
 }
 
 mfs_status mfs_apply_schur(mfs_problem* Pb, const mfs_solve_opts* opts, mfs_prec prec, const void* r, void* z,

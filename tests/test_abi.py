@@ -106,3 +106,20 @@ def test_library_quadrature_rule_matches_oracle(lib):
     from oracle.temperature import QUAD5_BARY, QUAD5_W
     lam, w = mfs.temp_rule()
     assert np.abs(lam - QUAD5_BARY).max() <= 1e-15 and np.abs(w - QUAD5_W).max() <= 1e-16
+
+
+@pytest.mark.parametrize("l", [1, 2, 3])
+def test_library_prolongation_matches_oracle(lib, l):
+    """The library's host-built P2 prolongation (the CSR its transfer kernels use) equals the
+    oracle's, built independently from the same definition (coarse P2 interpolant at the fine
+    nodes), entry for entry."""
+    import scipy.sparse as sp
+    from oracle.mesh import MacroMesh
+    from oracle.solver import prolongation
+    m = mfs.Mesh(None, l)
+    rp, ci, w = m.prolongation(l)
+    nf, nc = m.info(l).n_p2, m.info(l - 1).n_p2
+    P = sp.csr_matrix((w, ci, rp), shape=(nf, nc))
+    R = prolongation(MacroMesh(), l - 1)
+    assert R.shape == P.shape
+    assert abs(P - R).max() == 0.0
