@@ -223,6 +223,15 @@ mfs_status mfs_restrict(mfs_problem* prob, int lvl, mfs_prec prec, const void* r
  * 1 <= lvl <= l_max.  Errors: MFS_EINVAL. */
 mfs_status mfs_mesh_prolongation(const mfs_mesh* mesh, int lvl, int* nnz, int* rp, int* ci, double* w);
 
+/* The P1 interpolation from level lvl-1 to lvl as (coarse vertex, fine vertex, weight)
+ * triplets: weight 1 where a fine vertex coincides with a coarse one, 1/2 for each end of the
+ * coarse edge whose midpoint it is.  The library builds from it the weighted-BFBT Poisson
+ * multigrid's transfers and, normalised row by row in the transpose, the full weighting that
+ * gives every coarser level its viscosity.  Host-only; nnz receives the count; coarse, fine,
+ * w: HOST arrays of nnz entries, each filled when not NULL.  1 <= lvl <= l_max.
+ * Errors: MFS_EINVAL. */
+mfs_status mfs_mesh_p1_interpolation(const mfs_mesh* mesh, int lvl, int* nnz, int* coarse, int* fine, double* w);
+
 /* One V-cycle for the constrained A on level lvl (paper Sec. 5.2.2): `steps` Chebyshev
  * pre- and post-smoothing steps of `degree` applications each, exact FP64 coarse solve on
  * l_min.  f: right-hand side [3][n_p2]; u: result (overwritten, the cycle starts from 0).

@@ -126,6 +126,7 @@ _SIGS = {
     "mfs_apply_vmass": ([_vp, _i, _d, _vp, _vp], _i),
     "mfs_temp_rule": ([_vp, _vp], _i),
     "mfs_mesh_prolongation": ([_vp, _i, _vp, _vp, _vp, _vp], _i),
+    "mfs_mesh_p1_interpolation": ([_vp, _i, _vp, _vp, _vp, _vp], _i),
     "mfs_temp_params_default": ([ctypes.POINTER(TempParams)], None),
     "mfs_temp_apply": ([_vp, _i, _d, _d, _d, _d, _i, _i, _vp, _vp, _vp], _i),
     "mfs_temp_rhs": ([_vp, ctypes.POINTER(TempParams), _vp, _vp, _vp, _vp, _d, _d, _vp], _i),
@@ -240,6 +241,17 @@ class Mesh:
         vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
         _check(lib().mfs_mesh_prolongation(self.handle, level, ctypes.byref(nnz), vp(rp), vp(ci), vp(w)))
         return rp, ci, w
+
+    def p1_interpolation(self, level):
+        """(coarse, fine, w): triplets of the P1 interpolation from level-1 to level (host)."""
+        nnz = ctypes.c_int()
+        _check(lib().mfs_mesh_p1_interpolation(self.handle, level, ctypes.byref(nnz), None, None, None))
+        cv = np.empty(nnz.value, dtype=np.int32)
+        fv = np.empty(nnz.value, dtype=np.int32)
+        w = np.empty(nnz.value, dtype=np.float64)
+        vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        _check(lib().mfs_mesh_p1_interpolation(self.handle, level, ctypes.byref(nnz), vp(cv), vp(fv), vp(w)))
+        return cv, fv, w
 
     def node_class(self, level, p2=True):
         n = self.info(level).n_p2 if p2 else self.info(level).n_p1

@@ -1437,6 +1437,21 @@ mfs_status mfs_mesh_prolongation(const mfs_mesh* M, int lvl, int* nnz, int* rp, 
   return MFS_OK;
 }
 
+mfs_status mfs_mesh_p1_interpolation(const mfs_mesh* M, int lvl, int* nnz, int* coarse, int* fine, double* w) {
+  if (!M || !nnz || lvl < 1 || lvl > M->l_max) {
+    set_error("null argument or level outside 1..l_max");
+    return MFS_EINVAL;
+  }
+  std::vector<int> tv, tj;
+  std::vector<double> tw;
+  p1_transfer_triplets(M, lvl, tv, tj, tw);
+  *nnz = (int)tv.size();
+  if (coarse) std::memcpy(coarse, tv.data(), sizeof(int) * tv.size());
+  if (fine) std::memcpy(fine, tj.data(), sizeof(int) * tj.size());
+  if (w) std::memcpy(w, tw.data(), sizeof(double) * tw.size());
+  return MFS_OK;
+}
+
 mfs_status mfs_apply_schur(mfs_problem* Pb, const mfs_solve_opts* opts, mfs_prec prec, const void* r, void* z,
                            mfs_solve_stats* stats) {
   if (!Pb || !r || !z) {

@@ -123,3 +123,26 @@ def test_library_prolongation_matches_oracle(lib, l):
     R = prolongation(MacroMesh(), l - 1)
     assert R.shape == P.shape
     assert abs(P - R).max() == 0.0
+
+
+@pytest.mark.parametrize("l", [1, 2, 3])
+def test_library_p1_interpolation_and_viscosity_weighting_match_oracle(lib, l):
+    """The library's host-built P1 interpolation reproduces linear fields exactly (on the
+    straight vertices), and its row-normalised transpose, the coarse-viscosity full
+    weighting, equals the oracle's restriction of a random field."""
+    import scipy.sparse as sp
+    from oracle.mesh import MacroMesh, Level
+    from oracle.solver import restrict_viscosity
+    m = mfs.Mesh(None, l)
+    cv, fv, w = m.p1_interpolation(l)
+    nf, nc = m.info(l).n_p1, m.info(l - 1).n_p1
+    T = sp.csr_matrix((w, (fv, cv)), shape=(nf, nc))
+    assert np.abs(np.asarray(T.sum(axis=1)).ravel() - 1.0).max() == 0.0
+    mesh = MacroMesh()
+    Lf, Lc = Level(mesh, l), Level(mesh, l - 1)
+    a = np.array([0.3, -0.7, 1.1])
+    assert np.abs(T @ (Lc.p1_straight @ a) - Lf.p1_straight @ a).max() <= 1e-14
+    eta = np.random.default_rng(l).uniform(1.0, 10.0, nf)
+    R = T.T.tocsr()
+    got = (R @ eta) / (R @ np.ones(nf))
+    assert np.abs(got - restrict_viscosity(Lf, Lc, eta)).max() <= 1e-14 * eta.max()
