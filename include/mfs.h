@@ -232,6 +232,15 @@ mfs_status mfs_mesh_prolongation(const mfs_mesh* mesh, int lvl, int* nnz, int* r
  * Errors: MFS_EINVAL. */
 mfs_status mfs_mesh_p1_interpolation(const mfs_mesh* mesh, int lvl, int* nnz, int* coarse, int* fine, double* w);
 
+/* The lookup maps mfs_set_temperature uses to evaluate the viscosity law (paper Sec. 7.2, Eq.
+ * ViscosityDef) on level lvl: the temperature of a P1 vertex, or of a P2 node on the levels
+ * up to l_eta that carry the quadrature-point viscosity (Sec. 5.2.2), is the finest level's
+ * P2 temperature at the same point.  Host-only.  vfine[n_p1]: index of the finest P2 node
+ * at each vertex of lvl; vrad[n_p1]: the vertex's radius |x| (blended point); p2fine[n_p2]:
+ * index of the finest P2 node at each P2 node of lvl.  HOST arrays, each filled when not
+ * NULL.  0 <= lvl <= l_max.  Errors: MFS_EINVAL. */
+mfs_status mfs_mesh_law_maps(const mfs_mesh* mesh, int lvl, int* vfine, double* vrad, int* p2fine);
+
 /* One V-cycle for the constrained A on level lvl (paper Sec. 5.2.2): `steps` Chebyshev
  * pre- and post-smoothing steps of `degree` applications each, exact FP64 coarse solve on
  * l_min.  f: right-hand side [3][n_p2]; u: result (overwritten, the cycle starts from 0).

@@ -127,6 +127,7 @@ _SIGS = {
     "mfs_temp_rule": ([_vp, _vp], _i),
     "mfs_mesh_prolongation": ([_vp, _i, _vp, _vp, _vp, _vp], _i),
     "mfs_mesh_p1_interpolation": ([_vp, _i, _vp, _vp, _vp, _vp], _i),
+    "mfs_mesh_law_maps": ([_vp, _i, _vp, _vp, _vp], _i),
     "mfs_temp_params_default": ([ctypes.POINTER(TempParams)], None),
     "mfs_temp_apply": ([_vp, _i, _d, _d, _d, _d, _i, _i, _vp, _vp, _vp], _i),
     "mfs_temp_rhs": ([_vp, ctypes.POINTER(TempParams), _vp, _vp, _vp, _vp, _d, _d, _vp], _i),
@@ -252,6 +253,16 @@ class Mesh:
         vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
         _check(lib().mfs_mesh_p1_interpolation(self.handle, level, ctypes.byref(nnz), vp(cv), vp(fv), vp(w)))
         return cv, fv, w
+
+    def law_maps(self, level):
+        """(vfine, vrad, p2fine): the viscosity law's finest-node maps of a level (host)."""
+        inf = self.info(level)
+        vfine = np.empty(inf.n_p1, dtype=np.int32)
+        vrad = np.empty(inf.n_p1, dtype=np.float64)
+        p2fine = np.empty(inf.n_p2, dtype=np.int32)
+        vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        _check(lib().mfs_mesh_law_maps(self.handle, level, vp(vfine), vp(vrad), vp(p2fine)))
+        return vfine, vrad, p2fine
 
     def node_class(self, level, p2=True):
         n = self.info(level).n_p2 if p2 else self.info(level).n_p1

@@ -434,19 +434,17 @@ mfs_status mfs_set_viscosity_law(mfs_problem* P, double E_A, double V_A, int n, 
   return MFS_OK;
 }
 
-// The viscosity law's lookup maps of level l, built on the host once per mesh: the finest
-// P2 node coinciding with each P1 vertex and the vertex's radius (|x| of the blended point),
-// and (p2 != 0) the finest P2 node coinciding with each P2 node of the level.
-static mfs_status law_maps(mfs_mesh* M, int l, bool p2) {
-  LevelData& Lv = M->levels[l];
-  cudaStream_t s = M->ctx->stream;
-  const int L = M->l_max;
-  const int NF = 2 << L;   // finest P2 lattice
+// The viscosity law's lookup maps of level l, built on the host: the finest P2 node
+// coinciding with each P1 vertex and the vertex's radius (|x| of the blended point), and
+// (when p2fine is given) the finest P2 node coinciding with each P2 node of the level.
+static mfs_status law_maps_host(const mfs_mesh* M, int l, std::vector<int>* vfine, std::vector<double>* vrad,
+                                std::vector<int>* p2fine) {
+  const int NF = 2 << M->l_max;   // finest P2 lattice
   const Numbering nbf = make_numbering(NF);
-  if (!Lv.d_vfine || !Lv.d_vrad) {
+  if (vfine || vrad) {
     const int N1 = 1 << l, sc1 = NF / N1;
-    std::vector<int> fine(Lv.nb1.total, -1);
-    std::vector<double> rad(Lv.nb1.total, 0.0);
+    std::vector<int> fine(make_numbering(N1).total, -1);
+    std::vector<double> rad(fine.size(), 0.0);
     for_each_point(M, N1, [&](int m, const int* i, int id) {
       double xs[3], x[3];
       M->host.straight_point(m, i, N1, xs);
@@ -460,6 +458,33 @@ static mfs_status law_maps(mfs_mesh* M, int l, bool p2) {
         set_error("internal: vertex without a finest-level node on level %d", l);
         return MFS_EINVAL;
       }
+    if (vfine) vfine->swap(fine);
+    if (vrad) vrad->swap(rad);
+  }
+  if (p2fine) {
+    const int N2 = 2 << l, sc2 = NF / N2;
+    std::vector<int> fine(make_numbering(N2).total, -1);
+    for_each_point(M, N2, [&](int m, const int* i, int id) {
+      fine[id] = lattice_id(M->host.topo[m], nbf, m, i[0] * sc2, i[1] * sc2, i[2] * sc2, i[3] * sc2);
+    });
+    for (int f : fine)
+      if (f < 0 || f >= nbf.total) {
+        set_error("internal: P2 node without a finest-level node on level %d", l);
+        return MFS_EINVAL;
+      }
+    p2fine->swap(fine);
+  }
+  return MFS_OK;
+}
+
+// The maps of law_maps_host on the device, built once per mesh (the P2 map only when p2).
+static mfs_status law_maps(mfs_mesh* M, int l, bool p2) {
+  LevelData& Lv = M->levels[l];
+  cudaStream_t s = M->ctx->stream;
+  if (!Lv.d_vfine || !Lv.d_vrad) {
+    std::vector<int> fine;
+    std::vector<double> rad;
+    MFS_TRY(law_maps_host(M, l, &fine, &rad, nullptr));
     cudaFree(Lv.d_vfine);
     cudaFree(Lv.d_vrad);
     Lv.d_vfine = nullptr;
@@ -479,16 +504,8 @@ static mfs_status law_maps(mfs_mesh* M, int l, bool p2) {
     Lv.d_vrad = drad;
   }
   if (p2 && !Lv.d_p2fine) {
-    const int N2 = 2 << l, sc2 = NF / N2;
-    std::vector<int> fine(Lv.nb2.total, -1);
-    for_each_point(M, N2, [&](int m, const int* i, int id) {
-      fine[id] = lattice_id(M->host.topo[m], nbf, m, i[0] * sc2, i[1] * sc2, i[2] * sc2, i[3] * sc2);
-    });
-    for (int f : fine)
-      if (f < 0 || f >= nbf.total) {
-        set_error("internal: P2 node without a finest-level node on level %d", l);
-        return MFS_EINVAL;
-      }
+    std::vector<int> fine;
+    MFS_TRY(law_maps_host(M, l, nullptr, nullptr, &fine));
     int* dfine = nullptr;
     mfs_status st = upload(&dfine, fine.data(), fine.size(), s);
     cudaError_t e = cudaStreamSynchronize(s);
@@ -499,6 +516,20 @@ static mfs_status law_maps(mfs_mesh* M, int l, bool p2) {
     }
     Lv.d_p2fine = dfine;
   }
+  return MFS_OK;
+}
+
+mfs_status mfs_mesh_law_maps(const mfs_mesh* M, int lvl, int* vfine, double* vrad, int* p2fine) {
+  if (!M || lvl < 0 || lvl > M->l_max) {
+    set_error("null mesh or level outside 0..l_max");
+    return MFS_EINVAL;
+  }
+  std::vector<int> f1, f2;
+  std::vector<double> rad;
+  MFS_TRY(law_maps_host(M, lvl, vfine ? &f1 : nullptr, vrad ? &rad : nullptr, p2fine ? &f2 : nullptr));
+  if (vfine) std::memcpy(vfine, f1.data(), sizeof(int) * f1.size());
+  if (vrad) std::memcpy(vrad, rad.data(), sizeof(double) * rad.size());
+  if (p2fine) std::memcpy(p2fine, f2.data(), sizeof(int) * f2.size());
   return MFS_OK;
 }
 

@@ -56,6 +56,7 @@ def test_errors_without_gpu_or_bad_args(lib):
                        ("mfs_apply_poisson", (null, 1, 0, 1.0, null, null)),
                        ("mfs_apply_schur", (null, None, 0, null, null, None)),
                        ("mfs_set_temperature", (null, null)),
+                       ("mfs_mesh_law_maps", (null, 0, null, null, null)),
                        ("mfs_temperature_step", (null, None, null, null, null, null, 0.1, 0.1, null, null, None))]:
         assert getattr(L, name)(*args) == 1, name
         assert L.mfs_last_error(), name
@@ -146,3 +147,26 @@ def test_library_p1_interpolation_and_viscosity_weighting_match_oracle(lib, l):
     R = T.T.tocsr()
     got = (R @ eta) / (R @ np.ones(nf))
     assert np.abs(got - restrict_viscosity(Lf, Lc, eta)).max() <= 1e-14 * eta.max()
+
+
+@pytest.mark.parametrize("blending", [True, False])
+def test_library_law_maps_match_oracle(lib, blending):
+    """The maps through which the device viscosity law reads the temperature (finest P2 node
+    at each vertex and, for the quadrature-point levels, at each P2 node; the vertex radius)
+    equal the oracle's matching by position (k-d tree over the finest level's P2 nodes) on
+    every level of a level-3 hierarchy, so that eta(x_V, T(x_V)) of Eq. ViscosityDef takes
+    the same temperature and radius on both sides."""
+    from oracle.solver import temperature_on_level
+    mesh = MacroMesh(blending=blending)
+    M = mfs.Mesh(None, 3, blending=blending)
+    Lf = Level(mesh, 3)
+    ids = np.arange(Lf.n_p2, dtype=np.float64)
+    for l in range(4):
+        L = Level(mesh, l)
+        vfine, vrad, p2fine = M.law_maps(l)
+        i2, i1 = temperature_on_level(Lf, L, ids)
+        assert np.array_equal(vfine, i1.astype(np.int32)), l
+        assert np.array_equal(p2fine, i2.astype(np.int32)), l
+        assert np.abs(vrad - np.linalg.norm(L.p1_x, axis=1)).max() <= 1e-15, l
+    with pytest.raises(mfs.MfsError):
+        M.law_maps(4)
