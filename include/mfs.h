@@ -425,6 +425,17 @@ mfs_status mfs_temp_rhs(mfs_problem* prob, const mfs_temp_params* params, const 
 mfs_status mfs_mmoc(mfs_problem* prob, const double* T, const double* u_new, const double* u_old, double tau,
                     const double* X_start, double* T_hat, double* X_dep);
 
+/* The MMOC particle step of mfs_mmoc (Sec. 3) run on the host, one particle after another,
+ * by the same per-particle code the kernel runs: for each of the n particles starting at
+ * X_start[:, i] ([3][n]), its departure point after one RK4 step back over tau with u linear
+ * in time from u_old to u_new, and T there.  mesh may be host-only (mfs_mesh_shell with a
+ * NULL context); the fields live on its finest level: T [n_p2], u_new, u_old [3][n_p2].
+ * Outputs T_hat [n] and X_out [3][n] (or NULL).  All HOST arrays.  Meant for checking the
+ * device path on a machine without a GPU and for small host-side traces.
+ * Errors: MFS_EINVAL. */
+mfs_status mfs_mmoc_host(const mfs_mesh* mesh, int n, const double* X_start, const double* T, const double* u_new,
+                         const double* u_old, double tau, double* T_hat, double* X_out);
+
 /* One temperature step (Sec. 3 and Sec. 6): u* and T* by linear extrapolation (Eq.
  * Extrapolation), T0_hat = MMOC(T_n, u*, u_n, tau_np1) at the departure points Y of the nodes,
  * Tm_hat = T_nm1 at the feet of the same particles traced on from Y with (u_n, u_nm1, tau_n) —

@@ -282,6 +282,12 @@ class Locator:
         if mesh.blending:   # radial clamp into the shell
             R = np.linalg.norm(X, axis=1)
             X = X * (np.clip(R, mesh.r_cmb, mesh.r_surf) / R)[:, None]
+        else:               # polyhedral shell: radially between the prism's inner and outer faces
+            dots = X @ mesh.prism_normal.T                              # (N, 20)
+            f = np.argmax(dots, axis=1)                                 # the face the ray crosses
+            t = dots[np.arange(X.shape[0]), f]
+            d = mesh.prism_delta[f]
+            X = X * (np.clip(t, mesh.r_cmb * d, mesh.r_surf * d) / t)[:, None]
         N = X.shape[0]
         score = np.full((N, 60), -np.inf)
         xt_all = np.zeros((N, 60, 3))

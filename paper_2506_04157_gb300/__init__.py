@@ -128,6 +128,7 @@ _SIGS = {
     "mfs_mesh_prolongation": ([_vp, _i, _vp, _vp, _vp, _vp], _i),
     "mfs_mesh_p1_interpolation": ([_vp, _i, _vp, _vp, _vp, _vp], _i),
     "mfs_mesh_law_maps": ([_vp, _i, _vp, _vp, _vp], _i),
+    "mfs_mmoc_host": ([_vp, _i, _vp, _vp, _vp, _vp, _d, _vp, _vp], _i),
     "mfs_temp_params_default": ([ctypes.POINTER(TempParams)], None),
     "mfs_temp_apply": ([_vp, _i, _d, _d, _d, _d, _i, _i, _vp, _vp, _vp], _i),
     "mfs_temp_rhs": ([_vp, ctypes.POINTER(TempParams), _vp, _vp, _vp, _vp, _d, _d, _vp], _i),
@@ -263,6 +264,23 @@ class Mesh:
         vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
         _check(lib().mfs_mesh_law_maps(self.handle, level, vp(vfine), vp(vrad), vp(p2fine)))
         return vfine, vrad, p2fine
+
+    def mmoc_host(self, X_start, T, u_new, u_old, tau):
+        """(T_hat, X_dep): the MMOC particle step on the host for particles at X_start (n, 3);
+        T [n_p2], u_new, u_old [3 n_p2] on the finest level (numpy float64)."""
+        X = np.ascontiguousarray(np.asarray(X_start, dtype=np.float64).T)
+        n = X.shape[1]
+        n2 = self.info(self.l_max).n_p2
+        T = np.ascontiguousarray(T, dtype=np.float64)
+        un = np.ascontiguousarray(u_new, dtype=np.float64)
+        uo = np.ascontiguousarray(u_old, dtype=np.float64)
+        if T.size != n2 or un.size != 3 * n2 or uo.size != 3 * n2:
+            raise ValueError("T needs n_p2 and u_new, u_old 3 n_p2 entries of the finest level")
+        Th = np.empty(n)
+        Xo = np.empty((3, n))
+        vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        _check(lib().mfs_mmoc_host(self.handle, n, vp(X), vp(T), vp(un), vp(uo), tau, vp(Th), vp(Xo)))
+        return Th, Xo.T
 
     def node_class(self, level, p2=True):
         n = self.info(level).n_p2 if p2 else self.info(level).n_p1

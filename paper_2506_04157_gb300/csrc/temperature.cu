@@ -166,7 +166,7 @@ __device__ __forceinline__ void p2_lattice_grads(const T lam[4], T gl[10][3]) {
   }
 }
 template <typename T>
-__device__ __forceinline__ void p2_values_at(const T lam[4], T phi[10]) {
+__host__ __device__ __forceinline__ void p2_values_at(const T lam[4], T phi[10]) {
   for (int a = 0; a < 4; ++a) phi[a] = lam[a] * (T(2) * lam[a] - T(1));
   phi[4] = T(4) * lam[0] * lam[1];
   phi[5] = T(4) * lam[0] * lam[2];
@@ -486,18 +486,25 @@ struct MmocArgs {
   const double* xyz;   // [3][n_p2] physical node positions
 };
 
-// P2 node ids and barycentrics of the micro-tet holding X (blended: X first moved radially
-// into the shell; a point just outside a macro is projected onto its Kuhn simplex)
-__device__ void mmoc_locate(const MmocArgs& A, const double Xin[3], int ids[10], double lam[4]) {
+// P2 node ids and barycentrics of the micro-tet holding X (X first moved radially into the
+// shell; a point just outside a macro is projected onto its Kuhn simplex)
+__host__ __device__ void mmoc_locate(const MmocArgs& A, const double Xin[3], int ids[10], double lam[4]) {
   const double R0 = sqrt(Xin[0] * Xin[0] + Xin[1] * Xin[1] + Xin[2] * Xin[2]);
   const double e[3] = {Xin[0] / R0, Xin[1] / R0, Xin[2] / R0};
-  const double R = A.blending ? fmin(fmax(R0, A.r_cmb), A.r_surf) : R0;
-  const double X[3] = {R * e[0], R * e[1], R * e[2]};
-  double dmax = -2.0;
+  double dmax = -2.0, dl = 1.0;   // the prism the direction points through: its face alignment, offset
   for (int m = 0; m < 60; ++m) {
     const double* nh = A.geom[m].nh;
-    dmax = fmax(dmax, e[0] * nh[0] + e[1] * nh[1] + e[2] * nh[2]);
+    const double d = e[0] * nh[0] + e[1] * nh[1] + e[2] * nh[2];
+    if (d > dmax) {
+      dmax = d;
+      dl = A.geom[m].delta;
+    }
   }
+  // radially onto the shell: between the spheres (blended), between the prism's inner and
+  // outer face planes nh.x = r delta (polyhedral)
+  const double R = A.blending ? fmin(fmax(R0, A.r_cmb), A.r_surf)
+                              : fmin(fmax(R0 * dmax, A.r_cmb * dl), A.r_surf * dl) / dmax;
+  const double X[3] = {R * e[0], R * e[1], R * e[2]};
   int bm = 0;
   double best = -1e300, bxi[3] = {0, 0, 0};
   for (int m = 0; m < 60; ++m) {
@@ -568,14 +575,14 @@ __device__ void mmoc_locate(const MmocArgs& A, const double Xin[3], int ids[10],
   }
 }
 
-__device__ __forceinline__ double p2_eval(const double* f, const int ids[10], const double phi[10]) {
+__host__ __device__ __forceinline__ double p2_eval(const double* f, const int ids[10], const double phi[10]) {
   double s = 0.0;
   for (int a = 0; a < 10; ++a) s += phi[a] * f[ids[a]];
   return s;
 }
 
 // u(X) = wn u_new(X) + wo u_old(X)
-__device__ void velocity_at(const MmocArgs& A, const double* un, const double* uo, double wn, double wo, const double X[3],
+__host__ __device__ void velocity_at(const MmocArgs& A, const double* un, const double* uo, double wn, double wo, const double X[3],
                             double out[3]) {
   int ids[10];
   double lam[4], phi[10];
@@ -590,6 +597,27 @@ __device__ void velocity_at(const MmocArgs& A, const double* un, const double* u
   }
 }
 
+// One particle (Sec. 3): departure point X of the particle at x after one classical RK4 step
+// backwards over tau, u linear in time from u_old (start) to u_new (end), and T there.  The
+// same code runs in k_mmoc and, on the host, in mfs_mmoc_host.
+__host__ __device__ void mmoc_particle(const MmocArgs& A, const double x[3], const double* T, const double* un,
+                                       const double* uo, double tau, double* That, double X[3]) {
+  double k1[3], k2[3], k3[3], k4[3], y[3];
+  velocity_at(A, un, uo, 1.0, 0.0, x, k1);
+  for (int c = 0; c < 3; ++c) y[c] = x[c] - 0.5 * tau * k1[c];
+  velocity_at(A, un, uo, 0.5, 0.5, y, k2);
+  for (int c = 0; c < 3; ++c) y[c] = x[c] - 0.5 * tau * k2[c];
+  velocity_at(A, un, uo, 0.5, 0.5, y, k3);
+  for (int c = 0; c < 3; ++c) y[c] = x[c] - tau * k3[c];
+  velocity_at(A, un, uo, 0.0, 1.0, y, k4);
+  for (int c = 0; c < 3; ++c) X[c] = x[c] - tau / 6.0 * (k1[c] + 2.0 * k2[c] + 2.0 * k3[c] + k4[c]);
+  int ids[10];
+  double lam[4], phi[10];
+  mmoc_locate(A, X, ids, lam);
+  p2_values_at<double>(lam, phi);
+  *That = p2_eval(T, ids, phi);
+}
+
 // particle i starts at node i (Xin = null) or at Xin[:, i]
 __global__ void k_mmoc(const MmocArgs A, const double* __restrict__ Xin, const double* __restrict__ T,
                        const double* __restrict__ un, const double* __restrict__ uo, double tau,
@@ -598,21 +626,8 @@ __global__ void k_mmoc(const MmocArgs A, const double* __restrict__ Xin, const d
     const int64_t n2 = A.n_p2;
     const double* X0 = Xin ? Xin : A.xyz;
     const double x[3] = {X0[i], X0[n2 + i], X0[2 * n2 + i]};
-    double k1[3], k2[3], k3[3], k4[3], y[3];
-    velocity_at(A, un, uo, 1.0, 0.0, x, k1);
-    for (int c = 0; c < 3; ++c) y[c] = x[c] - 0.5 * tau * k1[c];
-    velocity_at(A, un, uo, 0.5, 0.5, y, k2);
-    for (int c = 0; c < 3; ++c) y[c] = x[c] - 0.5 * tau * k2[c];
-    velocity_at(A, un, uo, 0.5, 0.5, y, k3);
-    for (int c = 0; c < 3; ++c) y[c] = x[c] - tau * k3[c];
-    velocity_at(A, un, uo, 0.0, 1.0, y, k4);
     double X[3];
-    for (int c = 0; c < 3; ++c) X[c] = x[c] - tau / 6.0 * (k1[c] + 2.0 * k2[c] + 2.0 * k3[c] + k4[c]);
-    int ids[10];
-    double lam[4], phi[10];
-    mmoc_locate(A, X, ids, lam);
-    p2_values_at<double>(lam, phi);
-    That[i] = p2_eval(T, ids, phi);
+    mmoc_particle(A, x, T, un, uo, tau, &That[i], X);
     if (Xout)
       for (int c = 0; c < 3; ++c) Xout[c * n2 + i] = X[c];
   }
@@ -1188,6 +1203,33 @@ mfs_status mfs_temp_rule(double* lam, double* w) {
   }
   std::memcpy(lam, l, sizeof(l));
   std::memcpy(w, ww, sizeof(ww));
+  return MFS_OK;
+}
+
+mfs_status mfs_mmoc_host(const mfs_mesh* M, int n, const double* X_start, const double* T, const double* u_new,
+                         const double* u_old, double tau, double* T_hat, double* X_out) {
+  if (!M || n < 0 || (n > 0 && (!X_start || !T || !u_new || !u_old || !T_hat)) || !std::isfinite(tau)) {
+    set_error("null mesh or field, negative particle count or non-finite tau");
+    return MFS_EINVAL;
+  }
+  const int nl = 1 << M->l_max;
+  MmocArgs a{};
+  a.geom = M->host.geom;
+  a.topo = M->host.topo;
+  a.nb2 = make_numbering(2 * nl);
+  a.n = nl;
+  a.n_p2 = a.nb2.total;
+  a.blending = M->host.blending;
+  a.r_cmb = M->host.r_cmb;
+  a.r_surf = M->host.r_surf;
+  a.xyz = nullptr;
+  for (int i = 0; i < n; ++i) {
+    const double x[3] = {X_start[i], X_start[(size_t)n + i], X_start[2 * (size_t)n + i]};
+    double X[3];
+    mmoc_particle(a, x, T, u_new, u_old, tau, &T_hat[i], X);
+    if (X_out)
+      for (int c = 0; c < 3; ++c) X_out[(size_t)c * n + i] = X[c];
+  }
   return MFS_OK;
 }
 

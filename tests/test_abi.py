@@ -170,3 +170,36 @@ def test_library_law_maps_match_oracle(lib, blending):
         assert np.abs(vrad - np.linalg.norm(L.p1_x, axis=1)).max() <= 1e-15, l
     with pytest.raises(mfs.MfsError):
         M.law_maps(4)
+
+
+@pytest.mark.parametrize("tau", [0.03, 0.3])
+@pytest.mark.parametrize("blending", [True, False])
+def test_library_mmoc_particle_step_matches_oracle(lib, blending, tau):
+    """The library's MMOC particle step (the code the mmoc kernel runs per particle: RK4 back
+    along u linear in time, point location, P2 evaluation; Sec. 3), run on the host, against
+    the oracle's k-d-tree-free locator and RK4: departure points to 1e-12 and T there, on a
+    rotation plus a non-affine field large enough to carry particles across macro faces and
+    out of the shell (moved back radially), and particle paths continued over a second step."""
+    from oracle.temperature import Locator, mmoc_departure
+    import workloads as W
+    mesh = MacroMesh(blending=blending)
+    Lv = Level(mesh, 2)
+    M = mfs.Mesh(None, 2, blending=blending)
+    x = Lv.p2_x
+    rng = np.random.default_rng(7)
+    u_new = (np.cross(rng.standard_normal(3), x) + 0.1 * np.sin(3 * x)).T.reshape(-1)
+    u_old = (np.cross(rng.standard_normal(3), x) + 0.3 * x).T.reshape(-1)
+    T = W.temperature_blobs(x, 4)
+    loc = Locator(Lv)
+    Th, X = M.mmoc_host(x, T, u_new, u_old, tau)
+    Xr = mmoc_departure(loc, u_new, u_old, tau)
+    assert np.abs(X - Xr).max() <= 1e-12
+    assert np.abs(Th - loc.eval_p2(T, Xr)).max() <= 1e-10 * np.abs(T).max()
+    if tau == 0.3:   # longer than a level-2 micro-tet edge (0.125 radially); some leave the shell
+        r = np.linalg.norm(X, axis=1)
+        assert np.linalg.norm(X - x, axis=1).max() > 0.125
+        assert (r > mesh.r_surf).any() or (r < mesh.r_cmb).any()
+    Th2, X2 = M.mmoc_host(X, T, u_old, u_new, 0.02)
+    Xr2 = mmoc_departure(loc, u_old, u_new, 0.02, X=Xr)
+    assert np.abs(X2 - Xr2).max() <= 1e-12
+    assert np.abs(Th2 - loc.eval_p2(T, Xr2)).max() <= 1e-10 * np.abs(T).max()
