@@ -149,6 +149,22 @@ def test_locate_and_evaluate_at_nodes(blending):
         assert np.abs(loc.eval_p2(q(Lv.p2_x), pts) - q(pts)).max() <= 1e-12
 
 
+@pytest.mark.parametrize("blending", [False, True])
+def test_locate_outside_moves_radially_onto_shell(blending):
+    """Reading of the MMOC's departure points outside the shell (Sec. 3 leaves them open): they
+    move radially onto the shell, onto the sphere (blended) or onto the prism's inner or outer
+    face plane (polyhedral), so a boundary node pushed radially out of the shell reads exactly
+    the field's value at that node, for any P2 field."""
+    Lv = Level(MacroMesh(blending=blending), 2)
+    loc = Locator(Lv)
+    f = np.random.default_rng(5).standard_normal(Lv.n_p2)
+    for cls, s in ((1, 1.2), (2, 0.8)):
+        sel = np.nonzero(Lv.p2_class == cls)[0]
+        assert sel.size > 0
+        got = loc.eval_p2(f, s * Lv.p2_x[sel])
+        assert np.abs(got - f[sel]).max() <= 1e-12, cls
+
+
 def test_mmoc_rotation_exact_polyhedral():
     """Rigid rotation u = w x x is linear, so P2 holds it exactly on straight tets, and one RK4
     step of the autonomous linear ODE maps x to the degree-4 Taylor polynomial of exp(-tau W)
