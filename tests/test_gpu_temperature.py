@@ -111,6 +111,25 @@ def test_mmoc_matches_oracle():
     assert np.abs(Th.cpu().numpy() - loc.eval_p2(T, Xr2)).max() <= 1e-10 * np.abs(T).max()
 
 
+def test_mmoc_polyhedral_shell():
+    """The MMOC on the polyhedral shell (no blending): departure points outside the shell move
+    radially onto the prism's inner or outer face plane on both sides; a step long enough to
+    cross micro-tets and leave the shell."""
+    Lv = Level(MacroMesh(blending=False), 2)
+    gm = mfs.Mesh(mfs.Context(0), 2, blending=False)
+    prob = mfs.Problem(gm, "dirichlet", "freeslip")
+    prob.set_density(TABLE)
+    u_new, T = fields(Lv, 6)
+    u_old, _ = fields(Lv, 7)
+    loc = Locator(Lv)
+    X = torch.empty(3 * Lv.n_p2, dtype=torch.float64, device="cuda")
+    Th = torch.empty(Lv.n_p2, dtype=torch.float64, device="cuda")
+    prob.mmoc(dev(T), dev(u_new), dev(u_old), 0.3, Th, X)
+    Xr = mmoc_departure(loc, u_new, u_old, 0.3)
+    assert np.abs(X.cpu().numpy().reshape(3, -1).T - Xr).max() <= 1e-12
+    assert np.abs(Th.cpu().numpy() - loc.eval_p2(T, Xr)).max() <= 1e-10 * np.abs(T).max()
+
+
 def test_temperature_step_matches_oracle():
     Lv, ops, ctx, gm, prob = setup(2)
     u_n, T_n = fields(Lv, 6)
