@@ -418,7 +418,8 @@ mfs_status mfs_temp_rhs(mfs_problem* prob, const mfs_temp_params* params, const 
 /* T_hat = MMOC(T, u_new, u_old, tau) (Sec. 3): one particle per P2 node traced back over a step
  * tau with one classical RK4 step along u(t) linear in time from u_old (start of the step) to
  * u_new (end), and T evaluated there (departure points outside the shell moved radially onto
- * it).  The particles start at the nodes (X_start = NULL) or at the points X_start [3][n_p2]
+ * it: onto the nearer sphere, or on the polyhedral shell onto the nearer of the inner and
+ * outer face planes of the prism the point's direction crosses).  The particles start at the nodes (X_start = NULL) or at the points X_start [3][n_p2]
  * (a particle path continued over an earlier step).  T, T_hat: [n_p2]; u_new, u_old:
  * [3][n_p2]; X_dep: [3][n_p2] departure points, or NULL.  FP64 device vectors.
  * Errors: MFS_EINVAL, MFS_ENOMEM, MFS_ECUDA. */

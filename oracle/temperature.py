@@ -37,7 +37,8 @@ Readings:
     positive weights) on the reference tet.
   * Particles start at the P2 nodes (the MMOC result is the nodal interpolant); one RK4 step
     of length tau per MMOC; a departure point outside the shell is moved radially onto the
-    nearer sphere (blended) or onto the nearest point of the nearest micro-tet (polyhedral).
+    nearer sphere (blended) or onto the nearer of the inner and outer face planes of the prism
+    its direction crosses (polyhedral).
   * The nested MMOC for T^{n-1}_hat continues the particles: traced from the nodes over
     [t^n, t^{n+1}] with u*^{n+1}, u^n (the inner MMOC's arguments), then on from where they
     arrived over [t^{n-1}, t^n] with u^n, u^{n-1} (the outer MMOC's), and T^{n-1} evaluated once
