@@ -57,6 +57,7 @@ def test_errors_without_gpu_or_bad_args(lib):
                        ("mfs_apply_schur", (null, None, 0, null, null, None)),
                        ("mfs_set_temperature", (null, null)),
                        ("mfs_mesh_law_maps", (null, 0, null, null, null)),
+                       ("mfs_mmoc_host", (null, 0, null, null, null, null, 0.1, null, null)),
                        ("mfs_temperature_step", (null, None, null, null, null, null, 0.1, 0.1, null, null, None))]:
         assert getattr(L, name)(*args) == 1, name
         assert L.mfs_last_error(), name
@@ -203,3 +204,19 @@ def test_library_mmoc_particle_step_matches_oracle(lib, blending, tau):
     Xr2 = mmoc_departure(loc, u_old, u_new, 0.02, X=Xr)
     assert np.abs(X2 - Xr2).max() <= 1e-12
     assert np.abs(Th2 - loc.eval_p2(T, Xr2)).max() <= 1e-10 * np.abs(T).max()
+
+
+def test_mmoc_host_refusals(lib):
+    """mfs_mmoc_host refuses a negative particle count, missing fields for a non-empty batch and
+    a non-finite step with MFS_EINVAL and a message; an empty batch is a no-op."""
+    import ctypes
+    M = mfs.Mesh(None, 1)
+    L = lib
+    null = None
+    buf = (ctypes.c_double * 8)()
+    for args in [(M.handle, -1, null, null, null, null, 0.1, null, null),
+                 (M.handle, 1, buf, null, buf, buf, 0.1, buf, null),
+                 (M.handle, 1, buf, buf, buf, buf, float("nan"), buf, null)]:
+        assert L.mfs_mmoc_host(*args) == 1
+        assert L.mfs_last_error()
+    assert L.mfs_mmoc_host(M.handle, 0, null, null, null, null, 0.1, null, null) == 0
