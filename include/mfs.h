@@ -200,6 +200,15 @@ mfs_status mfs_setup_multigrid(mfs_problem* prob, int l_min);
  * (l_min < lvl <= l_max).  Bounds set before mfs_setup_multigrid replace the estimate. */
 mfs_status mfs_set_cheb_bounds(mfs_problem* prob, int lvl, double lo, double hi);
 mfs_status mfs_get_cheb_bounds(const mfs_problem* prob, int lvl, double* lo, double* hi);
+/* Re-estimate the Chebyshev interval of level lvl (l_min < lvl <= l_max, multigrid set up)
+ * from a caller-given start vector: x0 (device, FP64, [3][n_p2] of that level; read only,
+ * projected by P_v and the Dirichlet elimination before the first step, any nonzero scale)
+ * replaces the library's seeded vector in the 15 FP64 power iterations on D^-1 A_c of
+ * mfs_setup_multigrid.  Stores [b/20, b], b = 1.2 * lambda, for the level's smoother and
+ * returns lambda (the last iterate's norm) in *lam_max (host).  Synchronises the stream.
+ * Errors: MFS_EINVAL (multigrid not set up, level without smoother, null pointer),
+ * MFS_ENAN (the iterate vanished or became non-finite), MFS_ECUDA. */
+mfs_status mfs_estimate_cheb_bounds(mfs_problem* prob, int lvl, const double* x0, double* lam_max);
 
 /* diag(A) on level lvl without the free-slip projection (paper Sec. 5.2.2), 1 on
  * Dirichlet rows; y: [3][n_p2]. */
@@ -485,15 +494,32 @@ mfs_status mfs_batch_solve(mfs_batch* batch, const mfs_solve_opts* opts, const d
                            const double* const* g, double* const* u, double* const* p, mfs_solve_stats* stats);
 
 /* ---------------------------------------------------------------- autotuning (not in the paper)
- * For every level of the problem's mesh, times the FP32 hot sweeps (fused saddle-point
- * apply and A alone) in their two compiled register budgets (4 or 3 resident CTAs per SM)
- * with CUDA events and keeps the faster for all later applies on that mesh.  cache_path
- * (may be NULL): a text file read first (levels found there are not timed) and written
- * with the choices and timings.  Allocates and frees temporary device vectors.
+ * The FP32 hot sweeps (fused saddle-point apply and A alone) have 5 launch variants per mesh
+ * level: 0 = shared-memory element body, 192 threads, 4 resident CTAs per SM (the default);
+ * 1 = the same with 3 CTAs per SM; 2, 3, 4 = register-resident element body with 192, 128
+ * or 96 threads and 2, 3 or 4 CTAs per SM.  All compute the same operator (rounding order
+ * aside).  mfs_autotune times every variant on every level of the problem's mesh with CUDA
+ * events and keeps the fastest for all later applies on that mesh.  cache_path (may be
+ * NULL): a text file read first (levels found there are not timed) and written with the
+ * choices and timings.  Allocates and frees temporary device vectors.
  * Errors: MFS_EINVAL, MFS_ENOMEM, MFS_ECUDA. */
 mfs_status mfs_autotune(mfs_problem* prob, const char* cache_path);
-/* The variant in use on a level (0: default budget, 1: wider registers). */
+/* The variant in use on a level. */
 mfs_status mfs_get_tuning(const mfs_problem* prob, int lvl, int* variant);
+/* Select the variant of a level by hand (0 <= variant < 5); it applies to every problem on
+ * the mesh.  Errors: MFS_EINVAL. */
+mfs_status mfs_set_tuning(mfs_problem* prob, int lvl, int variant);
+
+/* ---------------------------------------------------------------- measurement (not in the paper)
+ * Throughput of the device's fused multiply-add pipes, the denominators of the element
+ * sweeps' arithmetic roofline: kind 0 = FP32 (fma.rn.f32), 1 = FP32 packed pairs
+ * (fma.rn.f32x2, two FMAs per instruction), 2 = FP64 (fma.rn.f64).  Runs `launches`
+ * back-to-back launches of a kernel whose threads each carry 8 independent FMA chains of
+ * 128 * iters FMAs (64 warps per SM), timed with CUDA events on the context's stream after
+ * one warm-up launch; returns the rate (*tflops, counting an FMA as 2 flops) and the timed
+ * duration (*ms).  Allocates and frees a small output buffer; synchronises the stream.
+ * Errors: MFS_EINVAL (null pointer, kind outside 0..2, launches or iters < 1), MFS_ECUDA. */
+mfs_status mfs_fma_peak(mfs_ctx* ctx, int kind, int launches, int iters, double* tflops, double* ms);
 
 /* Allocation-free variant of mfs_apply_B (no counterpart in the paper).
  *

@@ -99,9 +99,11 @@ _SIGS = {
     "mfs_apply_BT": ([_vp, _i, _i, _i, _i, _vp, _vp], _i),
     "mfs_apply_stokes": ([_vp, _i, _i, _i, _vp, _vp, _vp, _vp], _i),
     "mfs_apply_B_noalloc": ([_vp, _i, _i, _i, _i, _vp, _vp], _i),
+    "mfs_fma_peak": ([_vp, _i, _i, _i, ctypes.POINTER(_d), ctypes.POINTER(_d)], _i),
     "mfs_setup_multigrid": ([_vp, _i], _i),
     "mfs_set_cheb_bounds": ([_vp, _i, _d, _d], _i),
     "mfs_get_cheb_bounds": ([_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_d)], _i),
+    "mfs_estimate_cheb_bounds": ([_vp, _i, _vp, ctypes.POINTER(_d)], _i),
     "mfs_diag_A": ([_vp, _i, _i, _vp], _i),
     "mfs_apply_mass": ([_vp, _i, _i, _vp, _vp], _i),
     "mfs_prolongate": ([_vp, _i, _i, _vp, _vp], _i),
@@ -115,6 +117,7 @@ _SIGS = {
     "mfs_set_temperature": ([_vp, _vp], _i),
     "mfs_rhs_buoyancy": ([_vp, _vp, _d, _vp], _i),
     "mfs_get_tuning": ([_vp, _i, ctypes.POINTER(_i)], _i),
+    "mfs_set_tuning": ([_vp, _i, _i], _i),
     "mfs_batch_create": ([_vp, _i, _vp, ctypes.POINTER(_vp)], _i),
     "mfs_batch_destroy": ([_vp], _i),
     "mfs_batch_apply_stokes": ([_vp, _i, _i, _vp, _vp, _vp, _vp], _i),
@@ -198,6 +201,13 @@ class Context:
 
     def enable_timing(self, on=True):
         _check(lib().mfs_ctx_timing(self.handle, int(on)))
+
+    def fma_peak(self, kind, launches=10, iters=20000):
+        """(TFLOP/s, ms) of the FMA-chain throughput kernel: kind "f32", "f32x2" or "f64"."""
+        k = {"f32": 0, "f32x2": 1, "f64": 2}[kind]
+        tf, ms = ctypes.c_double(), ctypes.c_double()
+        _check(lib().mfs_fma_peak(self.handle, k, launches, iters, ctypes.byref(tf), ctypes.byref(ms)))
+        return tf.value, ms.value
 
     def kernel_time(self):
         """(total ms, launches) of the timed element-sweep kernels since the last call."""
@@ -359,6 +369,16 @@ class Problem:
         _check(lib().mfs_get_cheb_bounds(self.handle, level, ctypes.byref(lo), ctypes.byref(hi)))
         return lo.value, hi.value
 
+    def estimate_cheb_bounds(self, level, x0):
+        """Re-run the power iteration of the level's Chebyshev interval from x0 (FP64 CUDA
+        tensor [3 n_p2]); returns the eigenvalue estimate."""
+        import torch
+        nu, _ = self._sizes(level)
+        _need(x0, nu, torch.float64, "x0")
+        lam = ctypes.c_double()
+        _check(lib().mfs_estimate_cheb_bounds(self.handle, level, _ptr(x0), ctypes.byref(lam)))
+        return lam.value
+
     def diag_A(self, level, y):
         nu, _ = self._sizes(level)
         _need(y, nu, None, "y")
@@ -427,8 +447,12 @@ class Problem:
         _check(lib().mfs_rhs_buoyancy(self.handle, _ptr(T_p2), float(scale), _ptr(f)))
 
     # ---- autotuning
+    def set_tuning(self, level, variant):
+        """Select the sweep launch variant of a level by hand (0..4, see include/mfs.h)."""
+        _check(lib().mfs_set_tuning(self.handle, level, variant))
+
     def autotune(self, cache_path=None):
-        """Pick the faster sweep variant per level (cached in cache_path if given)."""
+        """Pick the fastest sweep variant per level (cached in cache_path if given)."""
         _check(lib().mfs_autotune(self.handle, cache_path.encode() if cache_path else None))
         out = []
         for l in range(self.mesh.l_max + 1):

@@ -11,7 +11,7 @@ from concurrent.futures import ThreadPoolExecutor
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "lib")
-SOURCES = ["capi.cpp", "mesh_host.cpp", "apply_f32.cu", "apply_f64.cu", "tables.cu", "vec.cu", "noalloc.cu", "mg.cu", "solver.cpp", "wbfbt.cu", "temperature.cu", "batch.cu", "autotune.cpp"]
+SOURCES = ["capi.cpp", "mesh_host.cpp", "apply_f32.cu", "apply_f64.cu", "tables.cu", "vec.cu", "noalloc.cu", "mg.cu", "solver.cpp", "wbfbt.cu", "temperature.cu", "batch.cu", "autotune.cpp", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(HERE, "..", "include")]

@@ -196,7 +196,296 @@ __device__ __forceinline__ T radial_table(const T* tab, int n, T r, T r0, T r1) 
   return (T(1) - f) * tab[i] + f * tab[i + 1];
 }
 
-template <typename T, int OP, bool BLEND>
+// Element sweep with every value of a micro-tet held in registers (FP32 hot path): the 30
+// velocity values, the per-node output accumulators and the per-type geometry rows are
+// loaded or formed once per micro-tet, the four quadrature points are unrolled with their
+// node indices known at compile time, and each of the 10 nodes (and 4 vertices) receives one
+// shared-memory add at the end.  Same arithmetic as the shared-memory body of sweep_tile
+// (Sec. 4.1 geometry, Sec. 5.1 forms); only the storage of intermediates differs.
+template <typename T, int OP, bool BLEND, int NT>
+__device__ __forceinline__ void tet_sweep_regs(const ApplyParams<T>& P, const MacroGeom<T>& G, const Tile tile,
+                                               const T* us, T* ys, const T* eta_s, const T* p_s, T* yp_s,
+                                               const T* cM, const T* cJn, const T* cv0, const T* cnh,
+                                               const T* dtab, const int tid) {
+  constexpr bool HAS_U = (OP & (OP_A | OP_B)) != 0;
+  constexpr bool HAS_P = (OP & OP_BT) != 0;
+  constexpr bool OUT_U = (OP & (OP_A | OP_BT)) != 0;
+  constexpr bool OUT_P = (OP & OP_B) != 0;
+  constexpr bool HAS_CT = (OP & OP_CT) != 0;
+  constexpr bool HAS_BC = (OP & OP_BC) != 0;
+  constexpr bool NEED_GR = (OUT_P && HAS_BC) || HAS_CT;
+  const T QA = T(MFS_QA), QB = T(MFS_QB);
+  const T dd = QA - QB;
+  const T dq = T(4) * dd;                  // 4(alpha - beta)
+  const T bq1 = T(4) * QB - T(1);          // 4 beta - 1
+  const T b4 = T(4) * QB;                  // 4 beta
+  const T fvb = QB * (T(2) * QB - T(1)), fva = QA * (T(2) * QA - T(1));
+  const T feo = T(4) * QB * QB, fei = T(4) * QA * QB;
+  const int n = P.n;
+  const T C0 = G.absdet / (T(24) * T(n) * T(n) * T(n));
+  const T dinv = T(1) / G.delta;
+  const int a0 = tile.ta * TT, b0 = tile.tb * TT, c0 = tile.tc * TT;
+  // CTA-uniform geometry held in registers
+  T nh[3], v0[3], Jn[9], csum[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    nh[r] = cnh[r];
+    v0[r] = cv0[r];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) Jn[3 * r + d] = cJn[3 * r + d];
+    csum[r] = Jn[3 * r] + Jn[3 * r + 1] + Jn[3 * r + 2];
+  }
+  const int2 cinfo = P.classes[tile.cls];
+
+  for (int t = tid; t < cinfo.y; t += NT) {
+    const int code = P.tets[cinfo.x + t];
+    const int ci = code & 15, cj = (code >> 4) & 15, ck = (code >> 8) & 15, pmu = code >> 12;
+    const int p0 = perm_at(pmu, 0), p1 = perm_at(pmu, 1), p2 = perm_at(pmu, 2);
+    const int base = ci + 5 * cj + 25 * ck;
+
+    // nodal values of the micro-tet
+    T u[3][10];
+    if (HAS_U) {
+#pragma unroll
+      for (int a = 0; a < 10; ++a) {
+        const int sa = base + slot_off(pmu, a);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) u[c][a] = us[c * NSLOT2 + sa];
+      }
+    }
+    T ev[4], pv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      ev[a] = eta_s[base + slot_off(pmu, a)];
+      pv[a] = HAS_P ? p_s[base + slot_off(pmu, a)] : T(0);
+    }
+    const T eta_sum = ev[0] + ev[1] + ev[2] + ev[3];
+    const T p_sum = pv[0] + pv[1] + pv[2] + pv[3];
+
+    // geometry rows of this Freudenthal type: Mp = n Jm^-1 rows in permuted lattice order,
+    // and the lattice steps e_p0, e_p1, e_p2 mapped by Jm/n
+    T Mp[3][3], cp[3][3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      Mp[0][d] = cM[3 * p0 + d];
+      Mp[1][d] = cM[3 * p1 + d];
+      Mp[2][d] = cM[3 * p2 + d];
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      cp[0][r] = cJn[3 * r + p0];
+      cp[1][r] = cJn[3 * r + p1];
+      cp[2][r] = csum[r] - cp[0][r] - cp[1][r];
+    }
+    // quadrature point 0: cube corner + beta (3 e_p0 + 2 e_p1 + e_p2); the next points add
+    // (alpha - beta) e_p0, e_p1, e_p2 in turn
+    const T qx = T(a0 + ci), qy = T(b0 + cj), qz = T(c0 + ck);
+    T x[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+      x[r] = v0[r] + Jn[3 * r] * qx + Jn[3 * r + 1] * qy + Jn[3 * r + 2] * qz +
+             QB * (T(3) * cp[0][r] + T(2) * cp[1][r] + cp[2][r]);
+
+    // qp-independent parts of the lattice gradient: dbase_j = base_{j+1} - base_j
+    T dbase[3][3], U0[3];
+    if (HAS_U) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const T bs0 = bq1 * u[c][0] + b4 * (u[c][4] + u[c][5] + u[c][6]);
+        const T bs1 = bq1 * u[c][1] + b4 * (u[c][4] + u[c][7] + u[c][8]);
+        const T bs2 = bq1 * u[c][2] + b4 * (u[c][5] + u[c][7] + u[c][9]);
+        const T bs3 = bq1 * u[c][3] + b4 * (u[c][6] + u[c][8] + u[c][9]);
+        dbase[0][c] = bs1 - bs0;
+        dbase[1][c] = bs2 - bs1;
+        dbase[2][c] = bs3 - bs2;
+        if (HAS_BC)
+          U0[c] = fvb * (u[c][0] + u[c][1] + u[c][2] + u[c][3]) +
+                  feo * (u[c][4] + u[c][5] + u[c][6] + u[c][7] + u[c][8] + u[c][9]);
+      }
+    }
+
+    T Rs[3][3], Vq[4][3], Ea[6][3], Zs[3], bq[4];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      Zs[c] = T(0);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Rs[c][j] = T(0);
+#pragma unroll
+      for (int e = 0; e < 6; ++e) Ea[e][c] = T(0);
+    }
+
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (q > 0) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) x[r] += dd * cp[q - 1][r];
+      }
+      const T r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+      const T rinv = rsqrt_t<T>(r2);
+      T K[3][3];
+      T hr = T(1), h = T(0);
+      if (BLEND) {
+        h = x[0] * nh[0] + x[1] * nh[1] + x[2] * nh[2];
+        const T hinv = rcp_t<T>(h);
+        hr = h * rinv * dinv;
+        const T ri2 = rinv * rinv;
+        T v[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) v[d] = nh[d] * hinv - x[d] * ri2;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const T tj = Mp[j][0] * x[0] + Mp[j][1] * x[1] + Mp[j][2] * x[2];
+#pragma unroll
+          for (int d = 0; d < 3; ++d) K[j][d] = Mp[j][d] - tj * v[d];
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) K[j][d] = Mp[j][d];
+      }
+      const T coefB = C0 * hr * hr;
+      const T Wq = coefB * hr;
+
+      T trace = T(0), Gp[3][3], wsum[3], wq[3];
+      if (HAS_U) {
+        T D[3][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          T w[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) w[a] = u[c][wnode(a, q)];
+#pragma unroll
+          for (int j = 0; j < 3; ++j) D[j][c] = dbase[j][c] + dq * (w[j + 1] - w[j]);
+          wq[c] = w[q];
+          wsum[c] = w[0] + w[1] + w[2] + w[3] - w[q];
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) Gp[c][d] = D[0][c] * K[0][d] + D[1][c] * K[1][d] + D[2][c] * K[2][d];
+        trace = Gp[0][0] + Gp[1][1] + Gp[2][2];
+      }
+
+      T gr = T(0);
+      if (NEED_GR) {
+        const T rad = BLEND ? h * dinv : r2 * rinv;
+        if (P.n_dlnrho <= 1) {
+          gr = dtab[0];
+        } else {
+          const T top = T(P.n_dlnrho - 1);
+          T sg = (rad - P.r_cmb) * P.inv_dr * top;
+          sg = sg < T(0) ? T(0) : (sg > top ? top : sg);
+          int ig = (int)sg;
+          ig = ig > P.n_dlnrho - 2 ? P.n_dlnrho - 2 : ig;
+          const T fg = sg - T(ig);
+          gr = (ig + 1 < 64) ? (T(1) - fg) * dtab[ig] + fg * dtab[ig + 1]
+                             : (T(1) - fg) * P.dlnrho[ig] + fg * P.dlnrho[ig + 1];
+        }
+      }
+
+      if (OUT_P) {
+        T b = coefB * trace;
+        if (HAS_BC) {
+          T eu = T(0);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) eu += (U0[c] + (fva - fvb) * wq[c] + (fei - feo) * wsum[c]) * x[c];
+          b += Wq * gr * eu * rinv;
+        }
+        bq[q] = b;
+      }
+
+      if (OUT_U) {
+        T S[3][3];
+        if (OP & OP_A) {
+          const T etaq = QB * eta_sum + dd * ev[q];
+          const T coefA = T(2) * etaq * C0 * hr;
+          const T hA = T(0.5) * coefA;
+          const T t3 = trace * T(1.0 / 3.0);
+          S[0][0] = coefA * (Gp[0][0] - t3);
+          S[1][1] = coefA * (Gp[1][1] - t3);
+          S[2][2] = coefA * (Gp[2][2] - t3);
+          S[0][1] = S[1][0] = hA * (Gp[0][1] + Gp[1][0]);
+          S[0][2] = S[2][0] = hA * (Gp[0][2] + Gp[2][0]);
+          S[1][2] = S[2][1] = hA * (Gp[1][2] + Gp[2][1]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) S[c][d] = T(0);
+        }
+        T pq = T(0);
+        if (HAS_P) {
+          pq = QB * p_sum + dd * pv[q];
+          const T sp = coefB * pq;
+          S[0][0] -= sp;
+          S[1][1] -= sp;
+          S[2][2] -= sp;
+        }
+        T zq[3] = {T(0), T(0), T(0)};
+        if (HAS_CT) {
+          const T zc = -Wq * pq * gr * rinv;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            zq[c] = zc * x[c];
+            Zs[c] += zq[c];
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const T r0 = S[c][0] * K[0][0] + S[c][1] * K[0][1] + S[c][2] * K[0][2];
+          const T r1 = S[c][0] * K[1][0] + S[c][1] * K[1][1] + S[c][2] * K[1][2];
+          const T r2c = S[c][0] * K[2][0] + S[c][1] * K[2][1] + S[c][2] * K[2][2];
+          Rs[c][0] += r0;
+          Rs[c][1] += r1;
+          Rs[c][2] += r2c;
+          T sv[4];
+          sv[0] = -r0;
+          sv[1] = r0 - r1;
+          sv[2] = r1 - r2c;
+          sv[3] = r2c;
+          Vq[q][c] = dq * sv[q] + (HAS_CT ? (fva - fvb) * zq[c] : T(0));
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+            if (a != q) Ea[edge_of(a, q)][c] += sv[a] + (HAS_CT ? ((fei - feo) / dq) * zq[c] : T(0));
+        }
+      }
+    }  // qp loop
+
+    if (OUT_U) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        T* y = ys + c * NSLOT2;
+        T Tacc[4];
+        Tacc[0] = -Rs[c][0];
+        Tacc[1] = Rs[c][0] - Rs[c][1];
+        Tacc[2] = Rs[c][1] - Rs[c][2];
+        Tacc[3] = Rs[c][2];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          T val = bq1 * Tacc[a] + Vq[a][c];
+          if (HAS_CT) val += fvb * Zs[c];
+          atomicAdd(&y[base + slot_off(pmu, a)], val);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = a + 1; b < 4; ++b) {
+            T val = b4 * (Tacc[a] + Tacc[b]) + dq * Ea[edge_of(a, b)][c];
+            if (HAS_CT) val += feo * Zs[c];
+            atomicAdd(&y[base + slot_off(pmu, 4 + edge_of(a, b))], val);
+          }
+      }
+    }
+    if (OUT_P) {
+      const T sb = bq[0] + bq[1] + bq[2] + bq[3];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) atomicAdd(&yp_s[base + slot_off(pmu, a)], -(QB * sb + dd * bq[a]));
+    }
+  }
+}
+
+template <typename T, int OP, bool BLEND, int BODY = 0, int NT = kSweepThreads>
 __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m, const int tidx, const int n_tiles) {
   constexpr bool HAS_U = (OP & (OP_A | OP_B)) != 0;
   constexpr bool HAS_P = (OP & OP_BT) != 0;
@@ -256,12 +545,12 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
 
   // ---- stage the P2 node block (u, with the input-side projections) ----
   // All table entries of this thread first, then all node values: independent loads in flight.
-  constexpr int kG = (NSLOT2 + kSweepThreads - 1) / kSweepThreads;
+  constexpr int kG = (NSLOT2 + NT - 1) / NT;
   const int* tab2 = P.ids2 + tile_lin * NSLOT2;
   int codes[kG];
 #pragma unroll
   for (int k = 0; k < kG; ++k) {
-    const int s = tid + k * kSweepThreads;
+    const int s = tid + k * NT;
     codes[k] = s < NSLOT2 ? __ldg(tab2 + s) : -1;
   }
   T uv[kG][3];
@@ -278,13 +567,13 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
   if (ETAQ) {
 #pragma unroll
     for (int k = 0; k < kG; ++k) {
-      const int s = tid + k * kSweepThreads;
+      const int s = tid + k * NT;
       if (s < NSLOT2) ts[s] = codes[k] >= 0 ? __ldg(P.temp + slot_node(codes[k])) : T(0);
     }
   }
 #pragma unroll
   for (int k = 0; k < kG; ++k) {
-    const int s = tid + k * kSweepThreads;
+    const int s = tid + k * NT;
     if (s >= NSLOT2) break;
     const int code = codes[k];
     gid2[s] = code;
@@ -319,7 +608,7 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
   // ---- stage the P1 vertex block (eta, p) ----
   const int* tab1 = P.ids1 + tile_lin * NSLOT1;
   const T pm = (HAS_P && P.psum) ? *P.psum / T(P.n_p1) : T(0);
-  for (int s = tid; s < NSLOT1; s += kSweepThreads) {
+  for (int s = tid; s < NSLOT1; s += NT) {
     const int id = tab1[s];
     T e = T(1), pv = T(0);
     if (id >= 0) {
@@ -335,6 +624,9 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
   }
   __syncthreads();
 
+  if constexpr (BODY == 1) {
+    tet_sweep_regs<T, OP, BLEND, NT>(P, G, tile, us, ys, eta_s, p_s, yp_s, cM, cJn, cv0, cnh, dtab, tid);
+  } else {
   // ---- element sweep: one thread per micro-tet ----
   const T QA = T(MFS_QA), QB = T(MFS_QB);
   const T dq = T(4) * (QA - QB);           // 4(alpha - beta)
@@ -348,7 +640,7 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
   const T dinv = T(1) / G.delta;
   const int2 cinfo = P.classes[tile.cls];
 
-  for (int t = tid; t < cinfo.y; t += kSweepThreads) {
+  for (int t = tid; t < cinfo.y; t += NT) {
     const int code = P.tets[cinfo.x + t];
     const int ci = code & 15, cj = (code >> 4) & 15, ck = (code >> 8) & 15, pmu = code >> 12;
     const int p0 = perm_at(pmu, 0), p1 = perm_at(pmu, 1), p2 = perm_at(pmu, 2);
@@ -635,12 +927,13 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
     }
 #undef SLOT
   }
+  }   // BODY
   __syncthreads();
 
   // ---- add the block to the global result (output-side projections) ----
   if (OUT_U) {
     const int nn = P.n_p2;
-    for (int s = tid; s < NSLOT2; s += kSweepThreads) {
+    for (int s = tid; s < NSLOT2; s += NT) {
       const int code = gid2[s];
       if (code < 0) continue;
       const int id = slot_node(code);
@@ -676,7 +969,7 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
     }
   }
   if (OUT_P) {
-    for (int s = tid; s < NSLOT1; s += kSweepThreads) {
+    for (int s = tid; s < NSLOT1; s += NT) {
       const int id = gid1[s];
       if (id >= 0) atomicAdd(&P.yp[id], yp_s[s]);
     }
@@ -687,6 +980,12 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
 template <typename T, int OP, bool BLEND>
 __global__ void __launch_bounds__(kSweepThreads, MFS_SWEEP_MINBLOCKS) stokes_tile_kernel(const ApplyParams<T> P) {
   sweep_tile<T, OP, BLEND>(P, blockIdx.y, blockIdx.x, gridDim.x);
+}
+// the register-resident element body (FP32 hot path) with NT threads per CTA and MINB
+// resident CTAs per SM (the autotuner's variants 2-4)
+template <typename T, int OP, bool BLEND, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) stokes_tile_kernel_regs(const ApplyParams<T> P) {
+  sweep_tile<T, OP, BLEND, 1, NT>(P, blockIdx.y, blockIdx.x, gridDim.x);
 }
 // the same sweep compiled for one fewer resident CTA per SM (more registers per thread);
 // the autotuner picks between the two per level

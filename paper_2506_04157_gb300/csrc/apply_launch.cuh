@@ -1,6 +1,10 @@
 // Launcher of the fused micro-tet sweep (see apply.cuh); included once per precision.
 #pragma once
 
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "apply.cuh"
 #include "library.h"
 
@@ -25,42 +29,63 @@ struct PrecData<float> {
   static const float* dlnrho(mfs_problem* P) { return P->d_dlnrho32; }
 };
 
-template <typename T, int OP, bool BLEND, int WIDE>
-static cudaError_t sweep_attr() {
-  // opt in to more than 48 KB of dynamic shared memory once per instantiation
-  static cudaError_t e = cudaFuncSetAttribute(
-      WIDE ? stokes_tile_kernel_wide<T, OP, BLEND> : stokes_tile_kernel<T, OP, BLEND>,
-      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem_bytes<T, OP>());
+// Opt a kernel in to its dynamic shared memory once per (kernel, device): the attribute is a
+// property of the kernel on the device that is current when it is set.
+inline cudaError_t smem_opt_in(const void* func, size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({func, dev})) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) done.insert({func, dev});
   return e;
 }
 
-template <typename T, int OP, int WIDE>
-static mfs_status run_sweep_v(const ApplyParams<T>& prm, int n_tiles, int blending, mfs_ctx* ctx) {
+// Sweep variants (mfs_autotune chooses one per level for the FP32 hot sweeps):
+//   0: shared-memory element body, 192 threads, 4 resident CTAs per SM (80 registers)
+//   1: the same body with 3 resident CTAs per SM
+//   2: register-resident element body, 192 threads, 2 CTAs per SM
+//   3: register-resident element body, 128 threads, 3 CTAs per SM
+//   4: register-resident element body,  96 threads, 4 CTAs per SM
+template <typename T, int OP, bool BLEND>
+static void (*sweep_kernel(int variant, int* nt))(const ApplyParams<T>) {
+  switch (variant) {
+    case 1: *nt = kSweepThreads; return stokes_tile_kernel_wide<T, OP, BLEND>;
+    case 2: *nt = 192; return stokes_tile_kernel_regs<T, OP, BLEND, 192, 2>;
+    case 3: *nt = 128; return stokes_tile_kernel_regs<T, OP, BLEND, 128, 3>;
+    case 4: *nt = 96; return stokes_tile_kernel_regs<T, OP, BLEND, 96, 4>;
+    default: *nt = kSweepThreads; return stokes_tile_kernel<T, OP, BLEND>;
+  }
+}
+
+template <typename T, int OP, bool BLEND>
+static mfs_status run_sweep_v(const ApplyParams<T>& prm, int n_tiles, mfs_ctx* ctx, int variant) {
   dim3 grid(n_tiles, kMacroCells);
   const size_t smem = sweep_smem_bytes<T, OP>();
-  const cudaError_t attr = blending ? sweep_attr<T, OP, true, WIDE>() : sweep_attr<T, OP, false, WIDE>();
-  MFS_CUDA(attr);
+  int nt = kSweepThreads;
+  auto k = sweep_kernel<T, OP, BLEND>(variant, &nt);
+  MFS_CUDA(smem_opt_in((const void*)k, smem));
   auto ev = timing_events(ctx);
   if (ev.first) cudaEventRecord(ev.first, ctx->stream);
-  if (WIDE) {
-    if (blending) stokes_tile_kernel_wide<T, OP, true><<<grid, kSweepThreads, smem, ctx->stream>>>(prm);
-    else stokes_tile_kernel_wide<T, OP, false><<<grid, kSweepThreads, smem, ctx->stream>>>(prm);
-  } else {
-    if (blending) stokes_tile_kernel<T, OP, true><<<grid, kSweepThreads, smem, ctx->stream>>>(prm);
-    else stokes_tile_kernel<T, OP, false><<<grid, kSweepThreads, smem, ctx->stream>>>(prm);
-  }
+  k<<<grid, nt, smem, ctx->stream>>>(prm);
   if (ev.second) cudaEventRecord(ev.second, ctx->stream);
   return MFS_OK;
 }
 
-// the hot FP32 sweeps (A alone: smoothers; fused forward: Krylov) have a tunable variant
+// the hot FP32 sweeps (A alone: smoothers; fused forward: Krylov) have tunable variants
 template <typename T, int OP>
 static mfs_status run_sweep(const ApplyParams<T>& prm, int n_tiles, int blending, mfs_ctx* ctx, int variant) {
   constexpr bool tunable = sizeof(T) == 4 && (OP == OP_A || OP == (OP_A | OP_BT | OP_B | OP_BC));
   if constexpr (tunable) {
-    if (variant == 1) return run_sweep_v<T, OP, 1>(prm, n_tiles, blending, ctx);
+    if (variant > 0 && variant < kSweepVariants)
+      return blending ? run_sweep_v<T, OP, true>(prm, n_tiles, ctx, variant)
+                      : run_sweep_v<T, OP, false>(prm, n_tiles, ctx, variant);
   }
-  return run_sweep_v<T, OP, 0>(prm, n_tiles, blending, ctx);
+  return blending ? run_sweep_v<T, OP, true>(prm, n_tiles, ctx, 0) : run_sweep_v<T, OP, false>(prm, n_tiles, ctx, 0);
 }
 
 template <typename T>
@@ -98,15 +123,11 @@ template <typename T, int OP>
 static mfs_status run_batch(const ApplyParams<T>* dparams, const int2* map, const int* ntiles, int nblocks,
                             int blending, cudaStream_t s) {
   const size_t smem = sweep_smem_bytes<T, OP>();
-  static cudaError_t e1 = cudaFuncSetAttribute(stokes_tile_batch_kernel<T, OP, true>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  static cudaError_t e0 = cudaFuncSetAttribute(stokes_tile_batch_kernel<T, OP, false>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  MFS_CUDA(blending ? e1 : e0);
+  MFS_CUDA(smem_opt_in((const void*)(blending ? stokes_tile_batch_kernel<T, OP, true>
+                                              : stokes_tile_batch_kernel<T, OP, false>), smem));
   // persistent grid: as many CTAs as fit on the device at once
-  static int grid_cap[2] = {0, 0};
-  int& cap = grid_cap[blending ? 1 : 0];
-  if (cap == 0) {
+  int cap = 0;
+  {
     int dev = 0, sms = 0, per_sm = 0;
     MFS_CUDA(cudaGetDevice(&dev));
     MFS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

@@ -1,7 +1,8 @@
 // Autotuner of the sweep launch: per refinement level, the FP32 hot sweeps (fused
-// saddle-point apply, A alone) run in one of two register budgets (4 or 3 resident CTAs
-// per SM); the faster one, timed with CUDA events on this GPU, is kept.  Choices are
-// cached in a small text file so later runs skip the timing.
+// saddle-point apply, A alone) run in one of kSweepVariants launch shapes — the element body
+// (shared-memory or register-resident), the threads per CTA and the resident CTAs per SM
+// (apply_launch.cuh lists them); the fastest, timed with CUDA events on this GPU, is kept.
+// Choices are cached in a small text file so later runs skip the timing.
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -54,14 +55,14 @@ mfs_status mfs_autotune(mfs_problem* P, const char* cache_path) {
   mfs_mesh* M = P->mesh;
   const int L = M->l_max;
   std::vector<int> chosen(L + 1, -1);
-  std::vector<double> t0(L + 1, 0.0), t1(L + 1, 0.0);
+  std::vector<std::vector<double>> tv(L + 1, std::vector<double>(kSweepVariants, 0.0));
   if (cache_path) {
     if (FILE* f = std::fopen(cache_path, "r")) {
-      char line[256];
+      char line[512];
       while (std::fgets(line, sizeof(line), f)) {
         int lv = -1, v = -1;
-        if (std::sscanf(line, " {\"level\": %d, \"variant\": %d", &lv, &v) == 2 && lv >= 0 && lv <= L &&
-            (v == 0 || v == 1))
+        if (std::sscanf(line, " {\"level\": %d, \"variant\": %d", &lv, &v) == 2 && lv >= 0 && lv <= L && v >= 0 &&
+            v < kSweepVariants)
           chosen[lv] = v;
       }
       std::fclose(f);
@@ -81,8 +82,7 @@ mfs_status mfs_autotune(mfs_problem* P, const char* cache_path) {
     if (st == MFS_OK) {
       k_fill_pattern<<<256, 256, 0, M->ctx->stream>>>(nu, u, 1.0f);
       k_fill_pattern<<<64, 256, 0, M->ctx->stream>>>(np, p, 0.5f);
-      st = time_variant(P, l, 0, u, p, yu, yp, &t0[l]);
-      if (st == MFS_OK) st = time_variant(P, l, 1, u, p, yu, yp, &t1[l]);
+      for (int v = 0; v < kSweepVariants && st == MFS_OK; ++v) st = time_variant(P, l, v, u, p, yu, yp, &tv[l][v]);
     }
     cudaFree(u);
     cudaFree(yu);
@@ -92,7 +92,10 @@ mfs_status mfs_autotune(mfs_problem* P, const char* cache_path) {
       M->levels[l].variant = 0;
       return st;
     }
-    chosen[l] = t1[l] < t0[l] ? 1 : 0;
+    int best = 0;
+    for (int v = 1; v < kSweepVariants; ++v)
+      if (tv[l][v] < tv[l][best]) best = v;
+    chosen[l] = best;
     timed = true;
   }
   for (int l = 0; l <= L; ++l) M->levels[l].variant = chosen[l];
@@ -100,9 +103,11 @@ mfs_status mfs_autotune(mfs_problem* P, const char* cache_path) {
   if (cache_path && timed) {
     if (FILE* f = std::fopen(cache_path, "w")) {
       std::fprintf(f, "[\n");
-      for (int l = 0; l <= L; ++l)
-        std::fprintf(f, " {\"level\": %d, \"variant\": %d, \"ms_default\": %.6f, \"ms_wide\": %.6f}%s\n", l, chosen[l],
-                     t0[l], t1[l], l < L ? "," : "");
+      for (int l = 0; l <= L; ++l) {
+        std::fprintf(f, " {\"level\": %d, \"variant\": %d, \"ms\": [", l, chosen[l]);
+        for (int v = 0; v < kSweepVariants; ++v) std::fprintf(f, "%s%.6f", v ? ", " : "", tv[l][v]);
+        std::fprintf(f, "]}%s\n", l < L ? "," : "");
+      }
       std::fprintf(f, "]\n");
       std::fclose(f);
     }
@@ -116,5 +121,15 @@ mfs_status mfs_get_tuning(const mfs_problem* P, int lvl, int* variant) {
     return MFS_EINVAL;
   }
   *variant = P->mesh->levels[lvl].variant;
+  return MFS_OK;
+}
+
+mfs_status mfs_set_tuning(mfs_problem* P, int lvl, int variant) {
+  if (!P || lvl < 0 || lvl > P->mesh->l_max || variant < 0 || variant >= kSweepVariants) {
+    set_error("invalid arguments: level outside the mesh or variant outside 0..%d", kSweepVariants - 1);
+    return MFS_EINVAL;
+  }
+  P->mesh->levels[lvl].variant = variant;
+  P->mesh->tuning_gen++;
   return MFS_OK;
 }

@@ -19,6 +19,10 @@ struct mfs_batch {
   void* h_params = nullptr;     // pinned staging
   void** d_ptrs = nullptr;      // [4][n] device pointers u, p, yu, yp
   void** h_ptrs = nullptr;      // pinned staging
+  // recorded after the copies out of h_params / h_ptrs: the host waits on it before it
+  // rewrites them (a pinned-memory copy reads its source only when the stream reaches it)
+  cudaEvent_t staged = nullptr;
+  bool staged_pending = false;
   int64_t* d_np2 = nullptr;
   int64_t* d_np1 = nullptr;
   double* d_part = nullptr;     // [n][kBatchRed] partial sums
@@ -157,7 +161,12 @@ static mfs_status batch_apply_typed(mfs_batch* B, int transpose, int with_C, con
     B->graph = nullptr;
   }
   B->key.swap(key);
-  // new argument set: device pointer and parameter arrays, then the work eagerly
+  // new argument set: device pointer and parameter arrays, then the work eagerly; the
+  // staging buffers are reused only after the previous set's copies have read them
+  if (B->staged_pending) {
+    MFS_CUDA(cudaEventSynchronize(B->staged));
+    B->staged_pending = false;
+  }
   void** hp = B->h_ptrs;
   for (int b = 0; b < n; ++b) {
     hp[b] = const_cast<void*>(u[b]);
@@ -173,6 +182,8 @@ static mfs_status batch_apply_typed(mfs_batch* B, int transpose, int with_C, con
     hpar[b] = fill_params<T>(P, P->mesh->l_max, 1, (const T*)u[b], (const T*)p[b], (T*)yu[b], (T*)yp[b], sums + b);
   }
   MFS_CUDA(cudaMemcpyAsync(B->d_params, hpar, sizeof(ApplyParams<T>) * n, cudaMemcpyHostToDevice, s));
+  MFS_CUDA(cudaEventRecord(B->staged, s));
+  B->staged_pending = true;
   return batch_device_work<T>(B, op, s);
 }
 
@@ -184,6 +195,10 @@ mfs_status mfs_batch_destroy(mfs_batch* B) {
   if (!B) return MFS_OK;
   if (B->graph) cudaGraphExecDestroy(B->graph);
   if (B->cap) cudaStreamDestroy(B->cap);
+  if (B->staged) {
+    if (B->staged_pending) cudaEventSynchronize(B->staged);
+    cudaEventDestroy(B->staged);
+  }
   cudaFree(B->d_map);
   cudaFree(B->d_ntiles);
   cudaFree(B->d_params);
@@ -249,6 +264,7 @@ mfs_status mfs_batch_create(mfs_ctx* ctx, int n, mfs_problem* const* probs, mfs_
   chk(cudaMallocHost(&B->h_params, sizeof(ApplyParams<double>) * n));
   chk(cudaMallocHost((void**)&B->h_ptrs, sizeof(void*) * 4 * n));
   chk(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
+  chk(cudaEventCreateWithFlags(&B->staged, cudaEventDisableTiming));
   if (e == cudaSuccess) {
     chk(cudaMemcpyAsync(B->d_map, map.data(), sizeof(int2) * map.size(), cudaMemcpyHostToDevice, s));
     chk(cudaMemcpyAsync(B->d_ntiles, nt.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));

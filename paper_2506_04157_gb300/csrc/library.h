@@ -163,6 +163,10 @@ struct mfs_problem {
 
 namespace mfs {
 
+// launch variants of the FP32 hot sweeps (element body, threads per CTA, resident CTAs per
+// SM), chosen per level by mfs_autotune; apply_launch.cuh lists them
+constexpr int kSweepVariants = 5;
+
 constexpr int kRedBlocks = 512;     // partial sums of the two-pass reductions
 constexpr int kRedSlots = kRedBlocks + 64;
 

@@ -559,6 +559,35 @@ __global__ void k_seed_vector(int64_t n, double* v) {
   }
 }
 
+// Chebyshev interval of level l (reading of Sec. 5.2: [b/20, b], b = 1.2 lambda_max(D^-1 A_c)):
+// 15 FP64 power iterations on D^-1 A_c from the start vector held in the level's work vector
+// x (projected first; its scale does not matter).  Needs the level's inverse diagonal.
+static mfs_status power_bound(mfs_problem* Pb, int l, double* lam_out) {
+  MG* G = Pb->mg;
+  mfs_mesh* M = Pb->mesh;
+  cudaStream_t s = M->ctx->stream;
+  const int64_t n2 = M->levels[l].nb2.total, n3 = 3 * n2;
+  Work<double>& W = G->w64[l];
+  Blas<double>::bproject(G->bnd[l], n2, W.x, s);
+  double lam = 0.0;
+  for (int it = 0; it < 15; ++it) {
+    const double nv = std::sqrt(dot<double>(G, n3, W.x, W.x, s));
+    if (!(nv > 0.0) || !std::isfinite(nv)) {
+      set_error("power iteration broke down on level %d", l);
+      return MFS_ENAN;
+    }
+    Blas<double>::axpby(n3, 1.0 / nv, W.x, 0.0, W.x, s);
+    MFS_TRY(applyA<double>(Pb, l, W.x, W.t));
+    Blas<double>::mul(n3, W.t, W.dinv, W.x, s);
+    Blas<double>::bproject(G->bnd[l], n2, W.x, s);
+    lam = std::sqrt(dot<double>(G, n3, W.x, W.x, s));
+  }
+  G->hi[l] = 1.2 * lam;
+  G->lo[l] = G->hi[l] / 20.0;
+  *lam_out = lam;
+  return MFS_OK;
+}
+
 static mfs_status mg_numeric(mfs_problem* Pb) {
   MG* G = Pb->mg;
   mfs_mesh* M = Pb->mesh;
@@ -572,24 +601,9 @@ static mfs_status mg_numeric(mfs_problem* Pb) {
     Blas<double>::recip(n3, W.dinv, s);
     Blas<float>::recip(n3, G->w32[l].dinv, s);
     if (l > G->l_min && !G->have_bounds[l]) {
-      // largest eigenvalue of D^-1 A_c: 15 FP64 power iterations from a seeded vector
       k_seed_vector<<<1024, 256, 0, s>>>(n3, W.x);
-      Blas<double>::bproject(G->bnd[l], n2, W.x, s);
       double lam = 0.0;
-      for (int it = 0; it < 15; ++it) {
-        const double nv = std::sqrt(dot<double>(G, n3, W.x, W.x, s));
-        if (!(nv > 0.0) || !std::isfinite(nv)) {
-          set_error("power iteration broke down on level %d", l);
-          return MFS_ENAN;
-        }
-        Blas<double>::axpby(n3, 1.0 / nv, W.x, 0.0, W.x, s);
-        MFS_TRY(applyA<double>(Pb, l, W.x, W.t));
-        Blas<double>::mul(n3, W.t, W.dinv, W.x, s);
-        Blas<double>::bproject(G->bnd[l], n2, W.x, s);
-        lam = std::sqrt(dot<double>(G, n3, W.x, W.x, s));
-      }
-      G->hi[l] = 1.2 * lam;
-      G->lo[l] = G->hi[l] / 20.0;
+      MFS_TRY(power_bound(Pb, l, &lam));
     }
   }
   MFS_TRY(coarse_inverse(Pb, G->l_min, G->bnd[G->l_min], G->Ainv, G->ainv_work));
@@ -652,6 +666,25 @@ mfs_status mfs_set_cheb_bounds(mfs_problem* Pb, int lvl, double lo, double hi) {
   }
   Pb->mg->lo[lvl] = lo;
   Pb->mg->hi[lvl] = hi;
+  Pb->mg->have_bounds[lvl] = 1;
+  drop_vgraphs(Pb->mg);
+  return MFS_OK;
+}
+
+mfs_status mfs_estimate_cheb_bounds(mfs_problem* Pb, int lvl, const double* x0, double* lam_max) {
+  MFS_TRY(need_mg(Pb, lvl));
+  if (!x0 || !lam_max) {
+    set_error("null start vector or output");
+    return MFS_EINVAL;
+  }
+  if (lvl <= Pb->mg->l_min) {
+    set_error("level %d has no smoother", lvl);
+    return MFS_EINVAL;
+  }
+  mfs_mesh* M = Pb->mesh;
+  const int64_t n3 = 3 * (int64_t)M->levels[lvl].nb2.total;
+  MFS_CUDA(cudaMemcpyAsync(Pb->mg->w64[lvl].x, x0, sizeof(double) * n3, cudaMemcpyDeviceToDevice, M->ctx->stream));
+  MFS_TRY(power_bound(Pb, lvl, lam_max));
   Pb->mg->have_bounds[lvl] = 1;
   drop_vgraphs(Pb->mg);
   return MFS_OK;

@@ -112,13 +112,44 @@ def test_constrained_and_fused(l, dtype, bc):
     assert rel(yp.cpu().double().numpy(), co.apply_B(u)) <= TOL[dtype]
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("blending", [True, False])
+def test_sweep_variants(variant, blending):
+    """Every launch variant of the FP32 hot sweeps (shared-memory or register-resident element
+    body, 96-192 threads per CTA) gives the oracle's raw A, constrained A and constrained fused
+    [A B^T; (B+C) 0] on levels 1-3 to the FP32 tolerance."""
+    dtype = torch.float32
+    _, _, prob = gpu_problem(3, blending)
+    try:
+        for l in (1, 2, 3):
+            prob.set_tuning(l, variant)
+            L, ops, co = oracle(l, blending)
+            u, p = inputs(L, dtype, seed=7)
+            ud, pd = dev(u, dtype), dev(p, dtype)
+            yu = torch.empty(3 * L.n_p2, dtype=dtype, device="cuda")
+            yp = torch.empty(L.n_p1, dtype=dtype, device="cuda")
+            prob.apply_A(l, ud, yu)
+            assert rel(yu.cpu().double().numpy(), ops.A @ u) <= TOL[dtype], l
+            prob.apply_A(l, ud, yu, constrained=True)
+            assert rel(yu.cpu().double().numpy(), co.apply_A(u)) <= TOL[dtype], l
+            prob.apply_stokes(l, ud, pd, yu, yp)
+            assert rel(yu.cpu().double().numpy(), co.apply_A(u) + co.apply_BT(p)) <= TOL[dtype], l
+            assert rel(yp.cpu().double().numpy(), co.apply_Bbar(u)) <= TOL[dtype], l
+    finally:
+        for l in (1, 2, 3):
+            prob.set_tuning(l, 0)
+
+
 def test_fused_apply_level5_sampled_rows():
     """The bench's workload and launch at full size: level 5 (1,966,080 micro-tets), plume
     viscosity of contrast 1e6 (seed 2), compressible density, the constrained fused apply in
-    FP32 and FP64.  The oracle evaluates sampled rows one by one from every micro-tet that
-    touches 256 interior P2 nodes and 128 P1 vertices, on the projected inputs: interior
-    velocity rows equal A P0 u + B^T P_p p; pressure rows equal (B+C) P0 u up to the one
-    constant that P_p removes from the whole output."""
+    FP32 (sweep variants 0, 2 and 3) and FP64.  The oracle evaluates sampled rows one by one
+    from every micro-tet that touches 256 interior, 64 surface and 64 CMB P2 nodes and 128 P1 vertices (32 of them on the
+    spheres), on the projected inputs (Sec. 5.1, Eqs. SaddlePointStructureDirichlet /
+    InnerSaddlePointSystem): interior velocity rows equal A P0 u + B^T P_p p; surface rows
+    (Dirichlet) are the identity, y = u; CMB rows (free-slip) equal P_v (A P0 u + B^T P_p p)
+    with P_v u = u - (u.n)n at the node; pressure rows equal (B+C) P0 u up to the one constant
+    that P_p removes from the whole output.  Each node class is checked on its own."""
     from oracle.fem import stokes_apply_elements, tets_touching
     lvl = 5
     L = Level(MacroMesh(), lvl)
@@ -130,20 +161,40 @@ def test_fused_apply_level5_sampled_rows():
     prob.set_viscosity(torch.tensor(eta, device="cuda"))
     prob.set_density(dl)
     rng = np.random.default_rng(11)
-    s2 = np.sort(rng.choice(np.flatnonzero(L.p2_class == 0), 256, replace=False))
-    s1 = np.sort(rng.choice(L.n_p1, 128, replace=False))
+    s_in = np.sort(rng.choice(np.flatnonzero(L.p2_class == 0), 256, replace=False))
+    s_top = np.sort(rng.choice(np.flatnonzero(L.p2_class == 1), 64, replace=False))
+    s_cmb = np.sort(rng.choice(np.flatnonzero(L.p2_class == 2), 64, replace=False))
+    s1 = np.sort(np.concatenate([rng.choice(np.flatnonzero(L.p1_class == 0), 96, replace=False),
+                                 rng.choice(np.flatnonzero(L.p1_class != 0), 32, replace=False)]))
+    s2 = np.concatenate([s_in, s_cmb])
     sel = tets_touching(L, p2_nodes=s2, p1_nodes=s1)
     cons = Constraints(L, 0, 1)
-    rows = np.concatenate([s2, s2 + L.n_p2, s2 + 2 * L.n_p2])
-    for dtype in (torch.float32, torch.float64):
+    n2 = L.n_p2
+    rows = lambda s: np.concatenate([s, s + n2, s + 2 * n2])
+    nrm = L.p2_x[s_cmb] / np.linalg.norm(L.p2_x[s_cmb], axis=1, keepdims=True)
+    refs = {}
+    for dtype, variant in ((torch.float32, 0), (torch.float32, 2), (torch.float32, 3), (torch.float64, 0)):
+        prob.set_tuning(lvl, variant)
         u, p = inputs(L, dtype, seed=21)
-        yu_ref, yp_ref = stokes_apply_elements(L, eta, dl, cons.P0(u), p - p.mean(), sel)
-        yu = torch.empty(3 * L.n_p2, dtype=dtype, device="cuda")
+        if dtype not in refs:
+            refs[dtype] = stokes_apply_elements(L, eta, dl, cons.P0(u), p - p.mean(), sel)
+        yu_ref, yp_ref = refs[dtype]
+        yu = torch.empty(3 * n2, dtype=dtype, device="cuda")
         yp = torch.empty(L.n_p1, dtype=dtype, device="cuda")
         prob.apply_stokes(lvl, dev(u, dtype), dev(p, dtype), yu, yp)
         yu = yu.cpu().double().numpy()
         yp = yp.cpu().double().numpy()
-        assert rel(yu[rows], yu_ref[rows]) <= TOL[dtype]
+        assert rel(yu[rows(s_in)], yu_ref[rows(s_in)]) <= TOL[dtype]
+        # surface (Dirichlet): identity rows
+        assert rel(yu[rows(s_top)], u[rows(s_top)]) <= TOL[dtype]
+        # CMB (free-slip): the raw rows projected onto the tangent plane at the node
+        R = yu_ref[rows(s_cmb)].reshape(3, -1).T
+        R = R - np.einsum("ij,ij->i", R, nrm)[:, None] * nrm
+        G = yu[rows(s_cmb)].reshape(3, -1).T
+        assert rel(G, R) <= TOL[dtype]
+        assert np.abs(np.einsum("ij,ij->i", G, nrm)).max() <= 10 * TOL[dtype] * np.abs(G).max()
+        # pressure rows: the P_p constant is common to all rows, estimated from all samples
         d = yp[s1] - yp_ref[s1]
-        assert np.linalg.norm(d - d.mean()) <= TOL[dtype] * np.linalg.norm(yp_ref[s1])
-
+        d = d - d.mean()
+        for mask in (L.p1_class[s1] == 0, L.p1_class[s1] != 0):
+            assert np.linalg.norm(d[mask]) <= TOL[dtype] * np.linalg.norm(yp_ref[s1][mask])

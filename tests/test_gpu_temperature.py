@@ -1,16 +1,13 @@
 """GPU parity of the temperature step (Sec. 3, Sec. 6, Eq. WeakTemp) against the oracle: the
 P2 blocks M, D, D_s, C(u), R(u) (plain and constrained), the right-hand side with and without
-shear heating, the RK4 MMOC with its departure points, and one full step.
-
-The temperature kernels have not run on a GPU yet: the module is marked unverified (skipped
-unless MFS_RUN_UNVERIFIED=1) until they have."""
+shear heating, the RK4 MMOC with its departure points, and one full step."""
 import functools
 
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
-pytestmark = [pytest.mark.gpu, pytest.mark.unverified]
+pytestmark = pytest.mark.gpu
 
 import paper_2506_04157_gb300 as mfs
 import workloads as W

@@ -167,10 +167,7 @@ def test_solve_with_wbfbt(mixed, al):
     assert np.linalg.norm(pn - pd) / np.linalg.norm(pd) < 1e-5
 
 
-# ---- the consistent vector mass (vmass = 1).  Its GPU code has been checked on the CPU only
-# (per-tet arithmetic against the oracle's element matrices, the CG flow with the oracle's
-# matrices): marked unverified until it has run on a GPU.
-UNRUN = pytest.mark.unverified
+# ---- the consistent vector mass (vmass = 1)
 
 
 @functools.lru_cache(maxsize=None)
@@ -179,7 +176,6 @@ def oracle_cmass(L, a):
     return WbfbtOperators(H.levels[L], H.etas[L], a, mass="consistent")
 
 
-@UNRUN
 @pytest.mark.parametrize("dt", [torch.float64, torch.float32])
 @pytest.mark.parametrize("L,a", [(2, 1.0), (2, 3.0), (3, 2.0)])
 def test_consistent_vmass_apply(L, a, dt):
@@ -196,7 +192,6 @@ def test_consistent_vmass_apply(L, a, dt):
     assert rel(y.double().cpu().numpy(), ref) <= TOL[dt], (L, a)
 
 
-@UNRUN
 @pytest.mark.parametrize("al,ar", [(1.0, 1.0), (1.0, 10.0)])
 def test_wbfbt_consistent_apply_fp64(al, ar):
     """S_w^-1 r with the consistent mass: the GPU's CGs on K and on M converged far below the
@@ -214,7 +209,6 @@ def test_wbfbt_consistent_apply_fp64(al, ar):
     assert st["cg_M_calls"] == 2 and 0 < st["cg_M_max"] < 400
 
 
-@UNRUN
 def test_solve_with_wbfbt_consistent_mass():
     """FGMRES with the weighted BFBT on the consistent mass (the paper's tol_VectorMass = 1e-4)
     and the default omega = 0.3 (the best scaling with this mass) reaches the oracle's direct
@@ -234,7 +228,6 @@ def test_solve_with_wbfbt_consistent_mass():
     assert np.linalg.norm(p.cpu().numpy() - pd) / np.linalg.norm(pd) < 1e-5
 
 
-@UNRUN
 def test_vmass_refusals():
     H, ctx, gm, prob = setup(2)
     n = H.levels[2].n_p1
