@@ -1,16 +1,20 @@
 #!/usr/bin/env python
 """Benchmark of the blended P2-P1 Stokes hot path on one GB300.
 
-Workload: the spherical shell r in [0.5, 1] (60 macro-tets, radial blending), refinement
-level 5 (1,966,080 micro-tets, 8,325,576 velocity + pressure dofs), viscosity contrast
-1e6 (radial step x plumes x log-normal noise, seed 2), compressible density
-d ln rho/dr = -0.3781.  One step = one fused, constrained saddle-point apply
+Workload (headline): the spherical shell r in [0.5, 1] (60 macro-tets, radial blending),
+refinement level 6 (15,728,640 micro-tets, 63,406,854 velocity + 2,662,530 pressure dofs),
+viscosity contrast 1e6 (radial step x plumes x log-normal noise, seed 2), compressible
+density d ln rho/dr = -0.3781.  One step = one fused, constrained saddle-point apply
 [A B^T; (B+C) 0] (x, p) in FP32 — the operator application that the mixed-precision
 solver's Krylov, smoother and residual work is made of.
-Metric: GDoF/s = (N_u + N_p) / time per apply / 1e9.
+Metric: GDoF/s = (N_u + N_p) / time per apply / 1e9; and the time to a relative residual of
+1e-8 (measured in FP64) of the mixed-precision solve against the plain FP64 GPU solve of the
+same problem (assembled buoyancy forcing of a temperature field, compressible density).
+The level-5 workload (8,325,576 dofs) is reported beside it under "level5".
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same workload
-(micro-tets of the same level, scaled to the full apply).
+(micro-tets of the level-6 shell, evaluated row-sample-wise by oracle/sampled.py, scaled to
+the full apply).
 """
 from __future__ import annotations
 
@@ -26,23 +30,30 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "P2-P1 Stokes apply GDoF/s; time to 1e-8 residual, mixed vs FP64, 1 GB300"
-WORKLOAD = "shell-L5-contrast1e6: blended icosahedral shell, level 5, 8,325,576 dofs, FP32 fused constrained Stokes apply"
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
-# dram__bytes_read.sum + dram__bytes_write.sum of one fused level-5 launch, from an ncu
-# capture of this script's apply step (bench.py --no-solve --no-cpu-baseline --steps 3 --warmup 3)
-FUSED_L5_DRAM_BYTES = 100057856 + 10125056
+WORKLOADS = {
+    6: "shell-L6-contrast1e6: blended icosahedral shell, level 6, 66,069,384 dofs, FP32 fused constrained Stokes apply",
+    5: "shell-L5-contrast1e6: blended icosahedral shell, level 5, 8,325,576 dofs, FP32 fused constrained Stokes apply",
+}
+# dram__bytes_read.sum + dram__bytes_write.sum of one fused FP32 launch of the default sweep
+# variant, per level, from ncu captures of _one launch_ (profiles/ names the command); None
+# where no capture of the current kernel exists
+MEASURED_DRAM_BYTES = {6: 765551104 + 242633728, 5: 100033792 + 9007872}
+DEFAULT_KERNEL = "stokes_tile_kernel_fixed<float, A|BT|B|C, blended, 192 threads, 3 CTAs/SM>"
 
 
 def fused_stokes_flops_per_tet():
-    """Algorithmic FP32 flops of one micro-tet of the fused apply (FMA = 2 flops),
-    counted term by term from the per-quadrature-point algebra of the sweep kernel:
-    per tet 60 (nodal sums), per qp 4 x 300 (position 24,
-    blending Jacobian and K 57, viscosity/pressure at qp 6, lattice gradient 36,
-    physical gradient 45, divergence + compressible term 32, stress 25, test side 45,
-    accumulation 30), final distribution 123."""
+    """Algorithmic flops of one micro-tet of the fused apply (FMA = 2 flops), counted term by
+    term from the per-quadrature-point algebra of the sweep: per tet 60 (nodal sums), per qp
+    4 x 300 (position 24, blending Jacobian and K 57, viscosity/pressure at qp 6, lattice
+    gradient 36, physical gradient 45, divergence + compressible term 32, stress 25, test side
+    45, accumulation 30), final distribution 123."""
     return 60 + 4 * 300 + 123
+
+
+def algorithmic_bytes(n_p2, n_p1, word):
+    """Bytes one fused apply must move at least: u read and y written (3 n_p2 each), p read,
+    q written and the nodal viscosity read (n_p1 each); the per-macro geometry is negligible."""
+    return word * (6 * n_p2 + 3 * n_p1)
 
 
 def read_peaks():
@@ -139,22 +150,29 @@ def setup_problem(level, device):
     return ctx, mesh, prob, inf
 
 
-def run_ours(args, rank, world, device):
+def measure_peaks(ctx):
+    """FP32, packed-pair FP32 and FP64 FMA-pipe throughput (mfs_fma_peak: FMA-chain kernels,
+    CUDA events, 5 launches of about 0.1-0.2 s each), TFLOP/s."""
+    out = {}
+    for kind, iters in (("f32", 20000), ("f32x2", 20000), ("f64", 400)):
+        tf, ms = ctx.fma_peak(kind, launches=5, iters=iters)
+        out[kind] = {"tflops": round(tf, 3), "ms": round(ms, 2)}
+    return out
+
+
+def apply_bench(ctx, prob, inf, level, steps, warmup, world, rank, dev, clk=None):
+    """Device-timed fused constrained FP32 applies on rotating input sets (together larger than
+    L2), the sweep kernel's own time from CUDA events on the library's stream, the A block alone,
+    and the FP64 fused apply (kernel time)."""
     import numpy as np
     import torch
     import torch.distributed as dist
     import workloads as W
-
-    torch.cuda.set_device(device)
-    level = args.level
-    ctx, mesh, prob, inf = setup_problem(level, device)
     nu, npp = 3 * inf.n_p2, inf.n_p1
     dofs = nu + npp
-    dt = torch.float32
     bytes_per_set = 4 * (2 * nu + 2 * npp)
     l2 = 126 * 2 ** 20
     nsets = max(2, int(np.ceil(2 * l2 / bytes_per_set)))
-    dev = f"cuda:{device}"
     sets = []
     for k in range(nsets):
         u = torch.tensor(W.random_field(nu, 100 + k, np.float32), device=dev)
@@ -165,8 +183,7 @@ def run_ours(args, rank, world, device):
         u, p, yu, yp = sets[i % nsets]
         prob.apply_stokes(level, u, p, yu, yp)
 
-    clk = ClockSampler(device).start()
-    for i in range(args.warmup):
+    for i in range(warmup):
         step(i)
     torch.cuda.synchronize()
     if world > 1:
@@ -178,30 +195,55 @@ def run_ours(args, rank, world, device):
     torch.cuda.synchronize()
     tw0 = time.time()
     e0.record(stream)
-    for i in range(args.steps):
+    for i in range(steps):
         step(i)
     e1.record(stream)
     torch.cuda.synchronize()
-    clk.mark(tw0, time.time())
+    if clk is not None:
+        clk.mark(tw0, time.time())
     ctx.enable_timing(False)
     ktot, klaunch = ctx.kernel_time()
     if world > 1:
         dist.barrier()
     ms = e0.elapsed_time(e1)
-    ms_per_step, value = aggregate(ms, args.steps, dofs, world, dev)
-
+    ms_per_step, value = aggregate(ms, steps, dofs, world, dev)
     # the A block alone (constrained, the smoother's operator): N_u per sweep-kernel time
     ctx.kernel_time()
     ctx.enable_timing(True)
-    for i in range(args.steps):
+    for i in range(steps):
         u, p, yu, yp = sets[i % nsets]
         prob.apply_A(level, u, yu, constrained=True)
     torch.cuda.synchronize()
     ctx.enable_timing(False)
     a_tot, a_launch = ctx.kernel_time()
-    a_ms = a_tot / max(a_launch, 1)
+    # FP64 fused apply (plain-precision solver's operator), kernel time
+    u64 = sets[0][0].double()
+    p64 = sets[0][1].double()
+    yu64, yp64 = torch.empty_like(u64), torch.empty_like(p64)
+    prob.apply_stokes(level, u64, p64, yu64, yp64)
+    torch.cuda.synchronize()
+    n64 = 3 if level >= 6 else 10
+    ctx.kernel_time()
+    ctx.enable_timing(True)
+    for _ in range(n64):
+        prob.apply_stokes(level, u64, p64, yu64, yp64)
+    torch.cuda.synchronize()
+    ctx.enable_timing(False)
+    d_tot, d_launch = ctx.kernel_time()
+    del u64, p64, yu64, yp64
+    return {"value": value, "ms_per_step": ms_per_step, "kernel_ms": ktot / max(klaunch, 1),
+            "a_ms": a_tot / max(a_launch, 1), "fp64_kernel_ms": d_tot / max(d_launch, 1), "nsets": nsets,
+            "bytes_per_set": bytes_per_set, "sets": sets, "dofs": dofs}
 
-    # end to end through the public API with host buffers (pinned), copies inside the timing
+
+def e2e_bench(prob, inf, level, steps, world, dev):
+    """The same apply through the public API with host buffers: pinned host -> device copies of
+    (u, p), the apply, device -> host copies of (y_u, y_p), all inside the timed region."""
+    import numpy as np
+    import torch
+    import workloads as W
+    nu, npp = 3 * inf.n_p2, inf.n_p1
+    dt = torch.float32
     hu = torch.tensor(W.random_field(nu, 7, np.float32)).pin_memory()
     hp = torch.tensor(W.random_field(npp, 8, np.float32)).pin_memory()
     ou, op_ = torch.empty_like(hu).pin_memory(), torch.empty_like(hp).pin_memory()
@@ -218,94 +260,149 @@ def run_ours(args, rank, world, device):
     for _ in range(2):
         e2e_step()
     torch.cuda.synchronize()
-    n_e2e = max(3, args.steps // 2)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_e2e = max(3, steps // 2)
     e0.record(stream)
     for _ in range(n_e2e):
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / n_e2e
-    e2e_value = world * dofs / (e2e_ms * 1e-3) / 1e9
+    return {"value": round(world * (nu + npp) / (e2e_ms * 1e-3) / 1e9, 3), "unit": "GDoF/s",
+            "h2d_bytes_per_step": 4 * (nu + npp), "d2h_bytes_per_step": 4 * (nu + npp)}
 
-    # time to solve: multigrid setup (diag, eigenvalue estimates, coarse inverse) plus the
-    # solve to relative residual 1e-8 measured in FP64, on the same problem
-    # forcing: the buoyancy load vector of a temperature field of 8 Gaussian blobs (seed 3)
-    # with the compressible density profile, gravity -x/|x|, scale 1
-    solve = None
+
+def solve_bench(prob, mesh, level, dev, modes):
+    """Time to solve: multigrid setup (diag, eigenvalue estimates, coarse inverse) plus the
+    solve to relative residual 1e-8 measured in FP64.  Forcing: the assembled buoyancy load
+    vector (mfs_rhs_buoyancy) of a temperature field of 8 Gaussian blobs (seed 3) with the
+    compressible density profile, gravity -x/|x|, scale 1.  modes: (name, options, timed runs,
+    warm-up runs); the reported time is the median of the timed runs."""
+    import torch
+    nu, npp = 3 * mesh.info(level).n_p2, mesh.info(level).n_p1
+    f = buoyancy_forcing(mesh, prob, level, dev)
+    g = torch.zeros(npp, dtype=torch.float64, device=dev)
+    out = {}
+    for name, sopts, reps, warm in modes:
+        for _ in range(warm):   # graphs, Krylov storage, caches
+            u = torch.zeros(nu, dtype=torch.float64, device=dev)
+            p = torch.zeros(npp, dtype=torch.float64, device=dev)
+            prob.setup_multigrid(1)
+            prob.solve(f, g, u, p, raise_on_error=False, **sopts)
+        runs = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            prob.setup_multigrid(1)
+            torch.cuda.synchronize()
+            t_setup = time.perf_counter() - t0
+            u = torch.zeros(nu, dtype=torch.float64, device=dev)
+            p = torch.zeros(npp, dtype=torch.float64, device=dev)
+            st = prob.solve(f, g, u, p, raise_on_error=False, **sopts)
+            torch.cuda.synchronize()
+            runs.append((time.perf_counter() - t0, t_setup, st))
+        runs.sort(key=lambda r: r[0])
+        t_all, t_setup, st = runs[len(runs) // 2]
+        out[name] = {"time_to_solve_s": round(t_all, 3), "setup_s": round(t_setup, 3),
+                     "runs_s": [round(r[0], 3) for r in runs], "fgmres_iters_runs": [r[2]["fgmres_iters"] for r in runs],
+                     "solve_s": round(st["time_ms"] / 1e3, 3), "rel_residual_fp64": st["rel_residual"],
+                     "status": st["status"], "fgmres_iters": st["fgmres_iters"],
+                     "refinement_steps": st["outer_iters"], "vcycles": st["vcycles"],
+                     "parts_s": {"A_block_cg": round(st["time_Ahat_ms"] / 1e3, 3),
+                                 "schur_vbfbt": round(st["time_Sinv_ms"] / 1e3, 3),
+                                 "of_which_mass_cg": round(st["time_Minv_ms"] / 1e3, 3)}}
+        del u, p
+    return out
+
+
+def roofline(level, inf, kern_ms, fp64_ms, peaks):
+    """Arithmetic roofline of the fused sweep (FP32 default path and FP64): algorithmic flops
+    per launch / kernel time against the FMA-chain peaks measured in this run."""
+    flops = fused_stokes_flops_per_tet() * inf.n_tets
+    achieved = flops / (kern_ms * 1e-3) / 1e12
+    peak = peaks["f32"]["tflops"]
+    ach64 = flops / (fp64_ms * 1e-3) / 1e12
+    peak64 = peaks["f64"]["tflops"]
+    bytes32 = algorithmic_bytes(inf.n_p2, inf.n_p1, 4)
+    traffic = MEASURED_DRAM_BYTES.get(level)
+    return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic,
+            "traffic_source": f"ncu dram__bytes_read.sum + dram__bytes_write.sum of one level-{level} launch "
+                              f"(profiles/stokes_tile_kernel_fixed_f32_fused_dram.md)" if traffic is not None else None,
+            "kernel": DEFAULT_KERNEL, "kernel_ms": round(kern_ms, 5), "flops_per_launch": flops,
+            "flops_per_tet": fused_stokes_flops_per_tet(),
+            "algorithmic_bytes": bytes32, "algorithmic_GB_s": round(bytes32 / (kern_ms * 1e-3) / 1e9, 1),
+            "peak_basis": "measured in this run: FP32 FMA-chain kernel (mfs_fma_peak), of measured",
+            "fp64": {"bound": "alu", "achieved": round(ach64, 4), "peak": round(peak64, 4), "unit": "TFLOP/s",
+                     "frac": round(ach64 / peak64, 4), "kernel": "stokes_tile_kernel<double, A|BT|B|C, blended>",
+                     "kernel_ms": round(fp64_ms, 4), "peak_basis": "measured in this run: FP64 FMA-chain kernel"}}
+
+
+def run_ours(args, rank, world, device):
+    import torch
+    torch.cuda.set_device(device)
+    dev = f"cuda:{device}"
+    level = args.level
+    clk = ClockSampler(device).start()
+    ctx, mesh, prob, inf = setup_problem(level, device)
+    peaks = measure_peaks(ctx)
+    ab = apply_bench(ctx, prob, inf, level, args.steps, args.warmup, world, rank, dev, clk)
+    e2e = e2e_bench(prob, inf, level, args.steps, world, dev)
+    nu, npp = 3 * inf.n_p2, inf.n_p1
+    del ab["sets"]
+    line = {
+        "metric": METRIC, "value": round(ab["value"], 3), "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ab["ms_per_step"], 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOADS.get(level, f"shell-L{level}"), "level": level, "n_tets": inf.n_tets,
+                   "n_u": nu, "n_p": npp, "viscosity": "plumes contrast 1e6 seed 2",
+                   "density": "compressible, d ln rho/dr = -0.3781",
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": f"{ab['nsets']} rotating input sets of {ab['bytes_per_set'] / 2**20:.1f} MiB (> L2)",
+                   "sweep_variant": 6},
+        "roofline": roofline(level, inf, ab["kernel_ms"], ab["fp64_kernel_ms"], peaks),
+        "e2e": e2e,
+        "gpu_launches": int(args.steps * 6),   # per apply: 2 (p sum) + 1 sweep + 2 (q sum) + 1 (mean removal)
+        "a_block": {"kernel_ms": round(ab["a_ms"], 5), "gdofs": round(nu / (ab["a_ms"] * 1e-3) / 1e9, 3),
+                    "note": "constrained A sweep alone, N_u per kernel time"},
+        "measured_peaks": peaks,
+        "hbm_peak_measured_gbs": read_peaks().get("hbm_gbs"),
+    }
+    solve = {}
     if args.solve:
-        f = buoyancy_forcing(mesh, prob, level, dev)
-        g = torch.zeros(npp, dtype=torch.float64, device=dev)
-        solve = {}
-        # mixed schemes: median of `solve_reps` solves after one warm-up solve (iteration
-        # counts vary with the order of the FP32 atomic accumulations); FP64: one solve.
-        # The third mixed line is the adjoint inexact Uzawa step (tol_A 1e-4), the fastest
-        # block preconditioner with the FP64 outer FGMRES on this workload.
-        modes = [("mixed", dict(mixed=1), args.solve_reps), ("mixed_fp64_outer", dict(mixed=2), args.solve_reps),
-                 ("mixed_fp64_outer_adjoint_uzawa", dict(mixed=2, uzawa=2, tol_A=1e-4), args.solve_reps)]
-        modes += [("fp64", dict(mixed=0), 1)] if args.solve_fp64 and world == 1 else []
-        for name, sopts, reps in modes:
-            if reps > 1:   # warm-up: graphs, Krylov storage, caches
-                u = torch.zeros(nu, dtype=torch.float64, device=dev)
-                p = torch.zeros(npp, dtype=torch.float64, device=dev)
-                prob.setup_multigrid(1)
-                prob.solve(f, g, u, p, raise_on_error=False, **sopts)
-            runs = []
-            for _ in range(reps):
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                prob.setup_multigrid(1)
-                torch.cuda.synchronize()
-                t_setup = time.perf_counter() - t0
-                u = torch.zeros(nu, dtype=torch.float64, device=dev)
-                p = torch.zeros(npp, dtype=torch.float64, device=dev)
-                st = prob.solve(f, g, u, p, raise_on_error=False, **sopts)
-                torch.cuda.synchronize()
-                runs.append((time.perf_counter() - t0, t_setup, st))
-            runs.sort(key=lambda r: r[0])
-            t_all, t_setup, st = runs[len(runs) // 2]
-            solve[name] = {"time_to_solve_s": round(t_all, 3), "setup_s": round(t_setup, 3),
-                           "runs_s": [round(r[0], 3) for r in runs],
-                           "solve_s": round(st["time_ms"] / 1e3, 3), "rel_residual_fp64": st["rel_residual"],
-                           "status": st["status"], "fgmres_iters": st["fgmres_iters"],
-                           "refinement_steps": st["outer_iters"], "vcycles": st["vcycles"],
-                           "parts_s": {"A_block_cg": round(st["time_Ahat_ms"] / 1e3, 3),
-                                       "schur_vbfbt": round(st["time_Sinv_ms"] / 1e3, 3),
-                                       "of_which_mass_cg": round(st["time_Minv_ms"] / 1e3, 3)}}
-    schur = schur_applies(prob, level, inf, dev) if (args.solve and world == 1) else None
+        modes = [("mixed_fp64_outer", dict(mixed=2), 2, 1), ("mixed", dict(mixed=1), 1, 0)]
+        if args.solve_fp64 and world == 1:
+            modes.append(("fp64", dict(mixed=0), 1, 0))
+        solve[f"L{level}"] = solve_bench(prob, mesh, level, dev, modes)
+    del prob, mesh
+    torch.cuda.empty_cache()
+    # the level-5 workload beside it: apply, roofline, solves, Schur applications
+    if level != 5 and world == 1 and not args.no_level5:
+        ctx5, mesh5, prob5, inf5 = setup_problem(5, device)
+        ab5 = apply_bench(ctx5, prob5, inf5, 5, args.steps, args.warmup, 1, 0, dev)
+        del ab5["sets"]
+        line["level5"] = {"workload": WORKLOADS[5], "value": round(ab5["value"], 3), "unit": "GDoF/s",
+                          "ms_per_step": round(ab5["ms_per_step"], 5),
+                          "roofline": roofline(5, inf5, ab5["kernel_ms"], ab5["fp64_kernel_ms"], peaks),
+                          "a_block": {"kernel_ms": round(ab5["a_ms"], 5),
+                                      "gdofs": round(3 * inf5.n_p2 / (ab5["a_ms"] * 1e-3) / 1e9, 3)}}
+        if args.solve:
+            modes5 = [("mixed", dict(mixed=1), args.solve_reps, 1),
+                      ("mixed_fp64_outer", dict(mixed=2), args.solve_reps, 1),
+                      ("mixed_fp64_outer_adjoint_uzawa", dict(mixed=2, uzawa=2, tol_A=1e-4), args.solve_reps, 1)]
+            if args.solve_fp64_l5:
+                modes5.append(("fp64", dict(mixed=0), 1, 0))
+            solve["L5"] = solve_bench(prob5, mesh5, 5, dev, modes5)
+            line["level5"]["schur_apply"] = schur_applies(prob5, 5, inf5, dev)
+        del prob5, mesh5
+        torch.cuda.empty_cache()
     clk.stop()
     if rank != 0:
         return None
-    peaks = read_peaks()
-    clocks = clk.summary()
-    kern_ms = ktot / max(klaunch, 1)
-    flops = fused_stokes_flops_per_tet() * inf.n_tets
-    achieved = flops / (kern_ms * 1e-3) / 1e12
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    line = {
-        "metric": METRIC, "value": round(value, 3), "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "level": level, "n_tets": inf.n_tets, "n_u": nu, "n_p": npp,
-                   "viscosity": "plumes contrast 1e6 seed 2", "parallelism": "replicas" if world > 1 else "single",
-                   "l2": f"{nsets} rotating input sets of {bytes_per_set / 2**20:.1f} MiB (> L2)"},
-        "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
-                     "frac": round(achieved / peak, 4),
-                     "traffic": FUSED_L5_DRAM_BYTES if level == 5 else None,
-                     "kernel": "stokes_tile_kernel<float, A|BT|B|C>", "kernel_ms": round(kern_ms, 5),
-                     "flops_per_launch": flops,
-                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz max clock (derived, not in MEASURED_PEAKS)"},
-        "e2e": {"value": round(e2e_value, 3), "unit": "GDoF/s", "h2d_bytes_per_step": 4 * (nu + npp),
-                "d2h_bytes_per_step": 4 * (nu + npp)},
-        "gpu_launches": int(args.steps * 6),   # per apply: 2 (p sum) + 1 sweep + 2 (q sum) + 1 (mean removal)
-        "a_block": {"kernel_ms": round(a_ms, 5), "gdofs": round(nu / (a_ms * 1e-3) / 1e9, 3),
-                    "note": "constrained A sweep alone, N_u per kernel time"},
-        "clocks": clocks,
-        "hbm_peak_measured_gbs": peaks.get("hbm_gbs"),
-    }
-    if solve is not None:
+    if solve:
         line["time_to_solve"] = solve
-    if schur is not None:
-        line["schur_apply"] = schur
+    line["clocks"] = clk.summary()
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(level, budget_s=args.cpu_seconds)
     return line
@@ -409,62 +506,64 @@ _ORACLE_WORKLOADS = {}
 
 
 def _oracle_workload(level):
-    """The oracle's level, viscosity and inputs of the bench workload (built once; not timed)."""
+    """The oracle side of the bench workload, without building the level's global element
+    arrays: the per-macro micro-tet lattice (oracle/sampled.py), the plume viscosity at the
+    blended vertex positions, and random inputs (built once; not timed)."""
     if level not in _ORACLE_WORKLOADS:
         import workloads as W
-        from oracle.mesh import MacroMesh, Level
-        L = Level(MacroMesh(), level)
-        _ORACLE_WORKLOADS[level] = (L, W.viscosity_plumes(L.p1_x, seed=2, contrast=1e6),
-                                    W.random_field(3 * L.n_p2, 1), W.random_field(L.n_p1, 2))
+        from oracle.mesh import MacroMesh, lattice_nodes
+        from oracle.sampled import MacroRows
+        mesh = MacroMesh()
+        R = MacroRows(mesh, level)
+        X1, _, pr1 = lattice_nodes(mesh, 2 ** level)
+        eta = W.viscosity_plumes(mesh.blend(X1, pr1), seed=2, contrast=1e6)
+        _ORACLE_WORKLOADS[level] = (R, eta, W.random_field(3 * R.n_p2, 1), W.random_field(R.n_p1, 2))
     return _ORACLE_WORKLOADS[level]
 
 
-def cpu_baseline(level, budget_s=12.0):
-    """The FP64 oracle's fused apply on a bounded sample of micro-tets of the same
-    workload, scaled to the full level (GDoF/s)."""
+def _sample_apply(level, budget_s, seed, chunk=4096):
+    """(micro-tets swept, seconds): the FP64 oracle's fused element apply (A u + B^T p,
+    (B + C) u; oracle/sampled.py MacroRows.contributions) on random chunks of micro-tets of
+    random macros until budget_s of CPU time is used."""
     import numpy as np
     import workloads as W
-    from oracle.fem import stokes_apply_elements
-    L, eta, u, p = _oracle_workload(level)
-    ntet = L.tet_p2.shape[0]
-    chunk = min(4096, ntet)
+    R, eta, u, p = _oracle_workload(level)
+    ntet = R.kt.shape[0]
+    rng = np.random.default_rng(seed)
     done, t_used = 0, 0.0
-    rng = np.random.default_rng(0)
-    while t_used < budget_s and done < ntet:
-        sel = np.sort(rng.choice(ntet, size=chunk, replace=False))
+    dl = W.dlnrho_table_compressible()
+    while t_used < budget_s:
+        m = int(rng.integers(0, 60))
+        sel = np.sort(rng.choice(ntet, size=min(chunk, ntet), replace=False))
         t0 = time.perf_counter()
-        stokes_apply_elements(L, eta, W.dlnrho_table_compressible(), u, p, sel)
+        R.contributions(m, sel, eta, dl, u, p)
         t_used += time.perf_counter() - t0
-        done += chunk
-    t_full = t_used * ntet / done
-    dofs = 3 * L.n_p2 + L.n_p1
-    return {"value": round(dofs / t_full / 1e9, 6), "unit": "GDoF/s", "cores": 1, "kind": "oracle",
-            "sample": f"{done} of {ntet} micro-tets (random), {t_used:.1f} s, scaled to one full apply",
+        done += len(sel)
+    return done, t_used
+
+
+def cpu_baseline(level, budget_s=12.0):
+    """The FP64 oracle's fused apply on a bounded sample of micro-tets of the same workload,
+    one core, scaled to the full level (GDoF/s)."""
+    R, _, _, _ = _oracle_workload(level)
+    done, t_used = _sample_apply(level, budget_s, 0)
+    n_tets = 60 * R.kt.shape[0]
+    t_full = t_used * n_tets / done
+    dofs = 3 * R.n_p2 + R.n_p1
+    return {"value": round(dofs / t_full / 1e9, 7), "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done} of {n_tets} micro-tets of the level-{level} shell (random chunks of 4096 in random "
+                      f"macros), {t_used:.1f} s, scaled to one full apply",
             "dofs_per_apply": dofs}
 
 
 def _sample_worker(level, budget_s, seed):
     """One process of the all-cores CPU baseline: (micro-tets swept, seconds)."""
-    import numpy as np
-    import workloads as W
-    from oracle.fem import stokes_apply_elements
-    L, eta, u, p = _oracle_workload(level)
-    ntet = L.tet_p2.shape[0]
-    rng = np.random.default_rng(seed)
-    done, t_used = 0, 0.0
-    chunk = min(4096, ntet)
-    while t_used < budget_s:
-        sel = np.sort(rng.choice(ntet, size=chunk, replace=False))
-        t0 = time.perf_counter()
-        stokes_apply_elements(L, eta, W.dlnrho_table_compressible(), u, p, sel)
-        t_used += time.perf_counter() - t0
-        done += chunk
-    return done, t_used
+    return _sample_apply(level, budget_s, seed)
 
 
 def cpu_baseline_all_cores(level, budget_s=3.0, max_procs=16):
     """The same sampled oracle apply in one process per host core (spawned; each builds its
-    own copy of the level), throughput summed over the processes (GDoF/s), or None."""
+    own copy of the workload), throughput summed over the processes (GDoF/s), or None."""
     import multiprocessing as mp
     n = max(1, min(os.cpu_count() or 1, max_procs))
     try:
@@ -472,10 +571,10 @@ def cpu_baseline_all_cores(level, budget_s=3.0, max_procs=16):
             res = pool.starmap(_sample_worker, [(level, budget_s, 1000 + k) for k in range(n)])
     except Exception as e:   # reported, not fatal: the one-core baseline stands
         return {"error": f"{type(e).__name__}: {e}"}
-    L, _, _, _ = _oracle_workload(level)
+    R, _, _, _ = _oracle_workload(level)
     tets_per_s = sum(d / t for d, t in res)
-    dofs = 3 * L.n_p2 + L.n_p1
-    return {"value": round(dofs * tets_per_s / L.tet_p2.shape[0] / 1e9, 6), "unit": "GDoF/s", "cores": n,
+    dofs = 3 * R.n_p2 + R.n_p1
+    return {"value": round(dofs * tets_per_s / (60 * R.kt.shape[0]) / 1e9, 7), "unit": "GDoF/s", "cores": n,
             "kind": "oracle", "sample": f"{n} processes x {budget_s:.0f} s of random 4096-tet chunks"}
 
 
@@ -514,19 +613,25 @@ def oracle_levels(budget_s=3.0):
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    times = []
+    # each step: one bounded sample of the workload (random micro-tets of the level, their
+    # fused element apply); value = the sample's dofs-equivalent throughput, ms_per_step = the
+    # sample's measured duration
+    rates, step_ms = [], []
     cb = None
+    _oracle_workload(args.level)   # built once, outside the timed samples
     for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(args.level, budget_s=max(1.0, args.cpu_seconds / max(1, args.steps)))
+        t0 = time.perf_counter()
+        cb = cpu_baseline(args.level, budget_s=max(0.5, args.cpu_seconds / max(1, args.steps)))
         if i >= args.warmup:
-            times.append(cb["value"])
-    v = statistics.median(times)
+            rates.append(cb["value"])
+            step_ms.append(1e3 * (time.perf_counter() - t0))
+    v = statistics.median(rates)
     cb["value"] = v
-    ms_per_step = cb["dofs_per_apply"] / (v * 1e9) * 1e3   # one full apply at this rate
+    ms_per_step = statistics.median(step_ms)
     return {"metric": METRIC, "value": v, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 1), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "level": args.level},
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOADS.get(args.level, f"shell-L{args.level}"), "level": args.level},
             "cpu_baseline": cb,
             "oracle_levels": oracle_levels(),
             "cpu_baseline_all_cores": cpu_baseline_all_cores(args.level),
@@ -539,7 +644,8 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--level", type=int, default=5)
+    ap.add_argument("--level", type=int, default=6)
+    ap.add_argument("--no-level5", action="store_true", help="skip the level-5 lines beside the headline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--solve", dest="solve", action="store_true", default=True,
@@ -548,7 +654,8 @@ def main():
     ap.add_argument("--solve-fp64", dest="solve_fp64", action="store_true", default=True,
                     help="also time the plain FP64 GPU solve of the same problem (default at 1 GPU)")
     ap.add_argument("--no-solve-fp64", dest="solve_fp64", action="store_false")
-    ap.add_argument("--solve-reps", type=int, default=5, help="mixed-precision solves (median reported)")
+    ap.add_argument("--solve-fp64-l5", action="store_true", help="also the plain FP64 solve at level 5")
+    ap.add_argument("--solve-reps", type=int, default=3, help="level-5 mixed-precision solves (median reported)")
     ap.add_argument("--profile-solve", action="store_true",
                     help="profiler window only (cudaProfilerStart/Stop): one V-cycle (3,2), one V-cycle "
                          "(1,1) and a solve capped at one FGMRES iteration, for ncu --profile-from-start off")

@@ -223,6 +223,9 @@ mfs_status mfs_apply_mass(mfs_problem* prob, int lvl, mfs_prec prec, const void*
  * (restriction, then the projections of level lvl-1).  l_min < lvl <= l_max. */
 mfs_status mfs_prolongate(mfs_problem* prob, int lvl, mfs_prec prec, const void* xc, void* xf);
 mfs_status mfs_restrict(mfs_problem* prob, int lvl, mfs_prec prec, const void* rf, void* rc);
+/* x <- P0 x on level lvl (l_min <= lvl <= l_max, multigrid set up): Dirichlet velocity
+ * entries zeroed, free-slip nodes projected, u - (u.n)n (paper Sec. 5.1); x: [3][n_p2]. */
+mfs_status mfs_project(mfs_problem* prob, int lvl, mfs_prec prec, void* x);
 
 /* The scalar P2 prolongation of mfs_prolongate before the projections, as a CSR matrix with
  * n_p2(lvl) rows (fine nodes) and n_p2(lvl-1) columns: each fine node takes the coarse P2
@@ -493,11 +496,42 @@ mfs_status mfs_batch_apply_stokes(mfs_batch* batch, mfs_prec prec, int transpose
 mfs_status mfs_batch_solve(mfs_batch* batch, const mfs_solve_opts* opts, const double* const* f,
                            const double* const* g, double* const* u, double* const* p, mfs_solve_stats* stats);
 
+/* ---------------------------------------------------------------- sharding by macro-tets
+ * The hybrid hierarchical grid of paper Sec. 4.1 splits naturally by macro-tets: every
+ * micro-tet, and so every element contribution, belongs to exactly one macro; nodes on macro
+ * vertices, edges and faces are shared by the macros around them.  A multi-GPU run gives
+ * each rank a range of macros; the ranks' partial results are summed on the shared nodes
+ * (paper_2506_04157_gb300/shard.py holds that logic).
+ *
+ * Macro topology (host, level-independent): cells[4m + k] = global vertex id of local vertex
+ * k of macro m (increasing), edges[6m + e] = global macro-edge id of local edge e (pairs 01,
+ * 02, 03, 12, 13, 23), faces[4m + z] = global macro-face id of the face opposite local vertex
+ * z.  With the node numbering documented at the top of this file, the lattice points a macro
+ * touches on a level follow from these ids.  Buffers [240], [360], [240] ints, caller-owned.
+ * Errors: MFS_EINVAL (null pointer). */
+mfs_status mfs_mesh_macro_topology(const mfs_mesh* mesh, int* cells, int* edges, int* faces);
+
+/* Partial constrained apply over the micro-tets of macros m0 <= m < m1 (0 <= m0 < m1 <= 60)
+ * on level lvl: fused = 0 gives yu = the contributions of those micro-tets to A_c u;
+ * fused = 1 gives yu = A_c u + P0 B^T p and yp = (B + C) P0 u restricted alike.  Element
+ * arithmetic as in mfs_apply_stokes's constrained mode: P0 (Dirichlet columns dropped,
+ * free-slip projection) on the velocity input, P_v on the free-slip output rows, identity
+ * rows y = u at the Dirichlet nodes the range touches; but p is used as given (pass it
+ * mean-free) and yp is not made mean-free — with shared nodes summed over all ranks and the
+ * pressure mean then removed, the result is mfs_apply_stokes's (rounding aside).  Outputs are
+ * overwritten; entries of nodes the range does not touch are zero.  p, yp may be NULL when
+ * fused = 0.  Errors: MFS_EINVAL (range, level, null pointer, fused apply on a level that
+ * evaluates the viscosity at quadrature points), MFS_ECUDA. */
+mfs_status mfs_apply_part(mfs_problem* prob, int lvl, mfs_prec prec, int fused, int m0, int m1, const void* u,
+                          const void* p, void* yu, void* yp);
+
 /* ---------------------------------------------------------------- autotuning (not in the paper)
- * The FP32 hot sweeps (fused saddle-point apply and A alone) have 5 launch variants per mesh
- * level: 0 = shared-memory element body, 192 threads, 4 resident CTAs per SM (the default);
- * 1 = the same with 3 CTAs per SM; 2, 3, 4 = register-resident element body with 192, 128
- * or 96 threads and 2, 3 or 4 CTAs per SM.  All compute the same operator (rounding order
+ * The FP32 hot sweeps (fused saddle-point apply and A alone) have 7 launch variants per mesh
+ * level: 0 = shared-memory element body with float atomics, 192 threads, 4 resident CTAs
+ * per SM; 1 = the same with 3 CTAs per SM; 2-6 = register-resident element body with
+ * fixed-point (int32) accumulation of each tile in rounds with their own power-of-two
+ * scales, with (threads, CTAs per SM) = (192, 2), (128, 3), (128, 4), (256, 2), (192, 3).
+ * Variant 6 is the default of every level.  All compute the same operator (rounding order and the fixed-point rounding
  * aside).  mfs_autotune times every variant on every level of the problem's mesh with CUDA
  * events and keeps the fastest for all later applies on that mesh.  cache_path (may be
  * NULL): a text file read first (levels found there are not timed) and written with the
@@ -506,7 +540,7 @@ mfs_status mfs_batch_solve(mfs_batch* batch, const mfs_solve_opts* opts, const d
 mfs_status mfs_autotune(mfs_problem* prob, const char* cache_path);
 /* The variant in use on a level. */
 mfs_status mfs_get_tuning(const mfs_problem* prob, int lvl, int* variant);
-/* Select the variant of a level by hand (0 <= variant < 5); it applies to every problem on
+/* Select the variant of a level by hand (0 <= variant < 7); it applies to every problem on
  * the mesh.  Errors: MFS_EINVAL. */
 mfs_status mfs_set_tuning(mfs_problem* prob, int lvl, int variant);
 

@@ -100,6 +100,8 @@ _SIGS = {
     "mfs_apply_stokes": ([_vp, _i, _i, _i, _vp, _vp, _vp, _vp], _i),
     "mfs_apply_B_noalloc": ([_vp, _i, _i, _i, _i, _vp, _vp], _i),
     "mfs_fma_peak": ([_vp, _i, _i, _i, ctypes.POINTER(_d), ctypes.POINTER(_d)], _i),
+    "mfs_apply_part": ([_vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp], _i),
+    "mfs_mesh_macro_topology": ([_vp, _vp, _vp, _vp], _i),
     "mfs_setup_multigrid": ([_vp, _i], _i),
     "mfs_set_cheb_bounds": ([_vp, _i, _d, _d], _i),
     "mfs_get_cheb_bounds": ([_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_d)], _i),
@@ -108,6 +110,7 @@ _SIGS = {
     "mfs_apply_mass": ([_vp, _i, _i, _vp, _vp], _i),
     "mfs_prolongate": ([_vp, _i, _i, _vp, _vp], _i),
     "mfs_restrict": ([_vp, _i, _i, _vp, _vp], _i),
+    "mfs_project": ([_vp, _i, _i, _vp], _i),
     "mfs_vcycle": ([_vp, _i, _i, _i, _i, _vp, _vp], _i),
     "mfs_solve_opts_default": ([ctypes.POINTER(SolveOpts)], None),
     "mfs_adjoint_solve": ([_vp, ctypes.POINTER(SolveOpts), _vp, _vp, _vp, _vp, ctypes.POINTER(SolveStats)], _i),
@@ -292,6 +295,16 @@ class Mesh:
         _check(lib().mfs_mmoc_host(self.handle, n, vp(X), vp(T), vp(un), vp(uo), tau, vp(Th), vp(Xo)))
         return Th, Xo.T
 
+    def macro_topology(self):
+        """(cells [60,4], edges [60,6], faces [60,4]): global vertex, macro-edge and macro-face
+        ids of every macro-tet (host, int32)."""
+        cells = np.empty((60, 4), dtype=np.int32)
+        edges = np.empty((60, 6), dtype=np.int32)
+        faces = np.empty((60, 4), dtype=np.int32)
+        vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        _check(lib().mfs_mesh_macro_topology(self.handle, vp(cells), vp(edges), vp(faces)))
+        return cells, edges, faces
+
     def node_class(self, level, p2=True):
         n = self.info(level).n_p2 if p2 else self.info(level).n_p1
         buf = np.empty(n, dtype=np.int8)
@@ -335,6 +348,18 @@ class Problem:
         _need(u, nu, None, "u"); _need(q, npp, u.dtype, "q")
         _check(lib().mfs_apply_B(self.handle, level, _prec_of(u), int(constrained), int(with_C),
                                  _ptr(u), _ptr(q)))
+
+    def apply_part(self, level, m0, m1, u, yu, p=None, yp=None):
+        """Partial constrained apply over macros m0 <= m < m1 (mfs_apply_part): A_c alone when p
+        is None, else the fused [A_c, P0 B^T; (B+C) P0] with p used as given and yp not made
+        mean-free."""
+        nu, npp = self._sizes(level)
+        _need(u, nu, None, "u"); _need(yu, nu, u.dtype, "yu")
+        fused = p is not None
+        if fused:
+            _need(p, npp, u.dtype, "p"); _need(yp, npp, u.dtype, "yp")
+        _check(lib().mfs_apply_part(self.handle, level, _prec_of(u), int(fused), m0, m1, _ptr(u),
+                                    _ptr(p) if fused else None, _ptr(yu), _ptr(yp) if fused else None))
 
     def apply_B_noalloc(self, level, u, q, with_C=True, constrained=False):
         """mfs_apply_B without device allocation: the mean-removal scratch lives in a
@@ -420,6 +445,12 @@ class Problem:
         nc, _ = self._sizes(level - 1)
         _need(rf, nf, None, "rf"); _need(rc, nc, rf.dtype, "rc")
         _check(lib().mfs_restrict(self.handle, level, _prec_of(rf), _ptr(rf), _ptr(rc)))
+
+    def project(self, level, x):
+        """x <- P0 x in place (Dirichlet entries zeroed, free-slip nodes projected)."""
+        nu, _ = self._sizes(level)
+        _need(x, nu, None, "x")
+        _check(lib().mfs_project(self.handle, level, _prec_of(x), _ptr(x)))
 
     def vcycle(self, level, f, u, steps=3, degree=2):
         nu, _ = self._sizes(level)

@@ -72,6 +72,7 @@ struct ApplyParams {
   T E_A, V_A, r_surf;
   int constrained;
   int bc_surface, bc_cmb;
+  int m0;                 // first macro-tet of the launch (grid.y macros from m0; 0 = all 60)
 };
 
 // symmetric 4-point degree-2 rule: barycentrics (QA,QB,QB,QB) and permutations, w = 1/24
@@ -168,10 +169,12 @@ static __constant__ SlotTable c_slots = {{
 }};
 
 // bytes of dynamic shared memory of one sweep CTA
-template <typename T, int OP>
+// (NR: copies of the output block, one per round of the fixed-point body, else 1)
+template <typename T, int OP, int NR = 1>
 constexpr size_t sweep_smem_bytes() {
-  return sizeof(T) * ((((OP & (OP_A | OP_B)) != 0) ? 3 * NSLOT2 : 0) + (((OP & (OP_A | OP_BT)) != 0) ? 3 * NSLOT2 : 0) +
-                      NSLOT1 + (((OP & OP_BT) != 0) ? NSLOT1 : 0) + (((OP & OP_B) != 0) ? NSLOT1 : 0) +
+  return sizeof(T) * ((((OP & (OP_A | OP_B)) != 0) ? 3 * NSLOT2 : 0) +
+                      (((OP & (OP_A | OP_BT)) != 0) ? NR * 3 * NSLOT2 : 0) + NSLOT1 +
+                      (((OP & OP_BT) != 0) ? NSLOT1 : 0) + (((OP & OP_B) != 0) ? NR * NSLOT1 : 0) +
                       (((OP & OP_ETAQ) != 0) ? NSLOT2 : 0)) +
          sizeof(int) * (NSLOT2 + NSLOT1);
 }
@@ -196,17 +199,16 @@ __device__ __forceinline__ T radial_table(const T* tab, int n, T r, T r0, T r1) 
   return (T(1) - f) * tab[i] + f * tab[i + 1];
 }
 
-// Element sweep with every value of a micro-tet held in registers (FP32 hot path): the 30
-// velocity values, the per-node output accumulators and the per-type geometry rows are
-// loaded or formed once per micro-tet, the four quadrature points are unrolled with their
-// node indices known at compile time, and each of the 10 nodes (and 4 vertices) receives one
-// shared-memory add at the end.  Same arithmetic as the shared-memory body of sweep_tile
-// (Sec. 4.1 geometry, Sec. 5.1 forms); only the storage of intermediates differs.
-template <typename T, int OP, bool BLEND, int NT>
-__device__ __forceinline__ void tet_sweep_regs(const ApplyParams<T>& P, const MacroGeom<T>& G, const Tile tile,
-                                               const T* us, T* ys, const T* eta_s, const T* p_s, T* yp_s,
-                                               const T* cM, const T* cJn, const T* cv0, const T* cnh,
-                                               const T* dtab, const int tid) {
+// One micro-tet of the register-resident sweep: its 30 velocity and 4 pressure outputs
+// (node order: vertices 0-3, then edges 01, 02, 03, 12, 13, 23) from the staged tile block.
+// Same arithmetic as the shared-memory body of sweep_tile (Sec. 4.1 geometry, Sec. 5.1
+// forms); only the storage of intermediates differs.
+template <typename T, int OP, bool BLEND>
+__device__ __forceinline__ void tet_element(const ApplyParams<T>& P, const MacroGeom<T>& G, const int code,
+                                            const int a0, const int b0, const int c0, const T* us,
+                                            const T* eta_s, const T* p_s, const T* cM, const T* cJn,
+                                            const T (&v0)[3], const T (&Jn)[9], const T (&csum)[3],
+                                            const T (&nh)[3], const T* dtab, T (&yv)[3][10], T (&ypv)[4]) {
   constexpr bool HAS_U = (OP & (OP_A | OP_B)) != 0;
   constexpr bool HAS_P = (OP & OP_BT) != 0;
   constexpr bool OUT_U = (OP & (OP_A | OP_BT)) != 0;
@@ -224,9 +226,253 @@ __device__ __forceinline__ void tet_sweep_regs(const ApplyParams<T>& P, const Ma
   const int n = P.n;
   const T C0 = G.absdet / (T(24) * T(n) * T(n) * T(n));
   const T dinv = T(1) / G.delta;
-  const int a0 = tile.ta * TT, b0 = tile.tb * TT, c0 = tile.tc * TT;
-  // CTA-uniform geometry held in registers
-  T nh[3], v0[3], Jn[9], csum[3];
+  const int ci = code & 15, cj = (code >> 4) & 15, ck = (code >> 8) & 15, pmu = code >> 12;
+  const int p0 = perm_at(pmu, 0), p1 = perm_at(pmu, 1), p2 = perm_at(pmu, 2);
+  const int base = ci + 5 * cj + 25 * ck;
+
+  // nodal values of the micro-tet
+  T u[3][10];
+  if (HAS_U) {
+#pragma unroll
+    for (int a = 0; a < 10; ++a) {
+      const int sa = base + slot_off(pmu, a);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) u[c][a] = us[c * NSLOT2 + sa];
+    }
+  }
+  T ev[4], pv[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    ev[a] = eta_s[base + slot_off(pmu, a)];
+    pv[a] = HAS_P ? p_s[base + slot_off(pmu, a)] : T(0);
+  }
+  const T eta_sum = ev[0] + ev[1] + ev[2] + ev[3];
+  const T p_sum = pv[0] + pv[1] + pv[2] + pv[3];
+
+  // geometry rows of this Freudenthal type: Mp = n Jm^-1 rows in permuted lattice order,
+  // and the lattice steps e_p0, e_p1, e_p2 mapped by Jm/n
+  T Mp[3][3], cp[3][3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    Mp[0][d] = cM[3 * p0 + d];
+    Mp[1][d] = cM[3 * p1 + d];
+    Mp[2][d] = cM[3 * p2 + d];
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    cp[0][r] = cJn[3 * r + p0];
+    cp[1][r] = cJn[3 * r + p1];
+    cp[2][r] = csum[r] - cp[0][r] - cp[1][r];
+  }
+  // quadrature point 0: cube corner + beta (3 e_p0 + 2 e_p1 + e_p2); the next points add
+  // (alpha - beta) e_p0, e_p1, e_p2 in turn
+  const T qx = T(a0 + ci), qy = T(b0 + cj), qz = T(c0 + ck);
+  T x[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+    x[r] = v0[r] + Jn[3 * r] * qx + Jn[3 * r + 1] * qy + Jn[3 * r + 2] * qz +
+           QB * (T(3) * cp[0][r] + T(2) * cp[1][r] + cp[2][r]);
+
+  // qp-independent parts of the lattice gradient: dbase_j = base_{j+1} - base_j
+  T dbase[3][3], U0[3];
+  if (HAS_U) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T bs0 = bq1 * u[c][0] + b4 * (u[c][4] + u[c][5] + u[c][6]);
+      const T bs1 = bq1 * u[c][1] + b4 * (u[c][4] + u[c][7] + u[c][8]);
+      const T bs2 = bq1 * u[c][2] + b4 * (u[c][5] + u[c][7] + u[c][9]);
+      const T bs3 = bq1 * u[c][3] + b4 * (u[c][6] + u[c][8] + u[c][9]);
+      dbase[0][c] = bs1 - bs0;
+      dbase[1][c] = bs2 - bs1;
+      dbase[2][c] = bs3 - bs2;
+      if (HAS_BC)
+        U0[c] = fvb * (u[c][0] + u[c][1] + u[c][2] + u[c][3]) +
+                feo * (u[c][4] + u[c][5] + u[c][6] + u[c][7] + u[c][8] + u[c][9]);
+    }
+  }
+
+  T Rs[3][3], Vq[4][3], Ea[6][3], Zs[3], bq[4];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    Zs[c] = T(0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Rs[c][j] = T(0);
+#pragma unroll
+    for (int e = 0; e < 6; ++e) Ea[e][c] = T(0);
+  }
+
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (q > 0) {
+#pragma unroll
+      for (int r = 0; r < 3; ++r) x[r] += dd * cp[q - 1][r];
+    }
+    const T r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+    const T rinv = rsqrt_t<T>(r2);
+    T K[3][3];
+    T hr = T(1), h = T(0);
+    if (BLEND) {
+      h = x[0] * nh[0] + x[1] * nh[1] + x[2] * nh[2];
+      const T hinv = rcp_t<T>(h);
+      hr = h * rinv * dinv;
+      const T ri2 = rinv * rinv;
+      T v[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) v[d] = nh[d] * hinv - x[d] * ri2;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const T tj = Mp[j][0] * x[0] + Mp[j][1] * x[1] + Mp[j][2] * x[2];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) K[j][d] = Mp[j][d] - tj * v[d];
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) K[j][d] = Mp[j][d];
+    }
+    const T coefB = C0 * hr * hr;
+    const T Wq = coefB * hr;
+
+    T trace = T(0), Gp[3][3], wsum[3], wq[3];
+    if (HAS_U) {
+      T D[3][3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        T w[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) w[a] = u[c][wnode(a, q)];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) D[j][c] = dbase[j][c] + dq * (w[j + 1] - w[j]);
+        wq[c] = w[q];
+        wsum[c] = w[0] + w[1] + w[2] + w[3] - w[q];
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) Gp[c][d] = D[0][c] * K[0][d] + D[1][c] * K[1][d] + D[2][c] * K[2][d];
+      trace = Gp[0][0] + Gp[1][1] + Gp[2][2];
+    }
+
+    T gr = T(0);
+    if (NEED_GR) {
+      const T rad = BLEND ? h * dinv : r2 * rinv;
+      if (P.n_dlnrho <= 1) {
+        gr = dtab[0];
+      } else {
+        const T top = T(P.n_dlnrho - 1);
+        T sg = (rad - P.r_cmb) * P.inv_dr * top;
+        sg = sg < T(0) ? T(0) : (sg > top ? top : sg);
+        int ig = (int)sg;
+        ig = ig > P.n_dlnrho - 2 ? P.n_dlnrho - 2 : ig;
+        const T fg = sg - T(ig);
+        gr = (ig + 1 < 64) ? (T(1) - fg) * dtab[ig] + fg * dtab[ig + 1]
+                           : (T(1) - fg) * P.dlnrho[ig] + fg * P.dlnrho[ig + 1];
+      }
+    }
+
+    if (OUT_P) {
+      T b = coefB * trace;
+      if (HAS_BC) {
+        T eu = T(0);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) eu += (U0[c] + (fva - fvb) * wq[c] + (fei - feo) * wsum[c]) * x[c];
+        b += Wq * gr * eu * rinv;
+      }
+      bq[q] = b;
+    }
+
+    if (OUT_U) {
+      T S[3][3];
+      if (OP & OP_A) {
+        const T etaq = QB * eta_sum + dd * ev[q];
+        const T coefA = T(2) * etaq * C0 * hr;
+        const T hA = T(0.5) * coefA;
+        const T t3 = trace * T(1.0 / 3.0);
+        S[0][0] = coefA * (Gp[0][0] - t3);
+        S[1][1] = coefA * (Gp[1][1] - t3);
+        S[2][2] = coefA * (Gp[2][2] - t3);
+        S[0][1] = S[1][0] = hA * (Gp[0][1] + Gp[1][0]);
+        S[0][2] = S[2][0] = hA * (Gp[0][2] + Gp[2][0]);
+        S[1][2] = S[2][1] = hA * (Gp[1][2] + Gp[2][1]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) S[c][d] = T(0);
+      }
+      T pq = T(0);
+      if (HAS_P) {
+        pq = QB * p_sum + dd * pv[q];
+        const T sp = coefB * pq;
+        S[0][0] -= sp;
+        S[1][1] -= sp;
+        S[2][2] -= sp;
+      }
+      T zq[3] = {T(0), T(0), T(0)};
+      if (HAS_CT) {
+        const T zc = -Wq * pq * gr * rinv;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          zq[c] = zc * x[c];
+          Zs[c] += zq[c];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const T r0 = S[c][0] * K[0][0] + S[c][1] * K[0][1] + S[c][2] * K[0][2];
+        const T r1 = S[c][0] * K[1][0] + S[c][1] * K[1][1] + S[c][2] * K[1][2];
+        const T r2c = S[c][0] * K[2][0] + S[c][1] * K[2][1] + S[c][2] * K[2][2];
+        Rs[c][0] += r0;
+        Rs[c][1] += r1;
+        Rs[c][2] += r2c;
+        T sv[4];
+        sv[0] = -r0;
+        sv[1] = r0 - r1;
+        sv[2] = r1 - r2c;
+        sv[3] = r2c;
+        Vq[q][c] = dq * sv[q] + (HAS_CT ? (fva - fvb) * zq[c] : T(0));
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+          if (a != q) Ea[edge_of(a, q)][c] += sv[a] + (HAS_CT ? ((fei - feo) / dq) * zq[c] : T(0));
+      }
+    }
+  }  // qp loop
+
+  if (OUT_U) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      T Tacc[4];
+      Tacc[0] = -Rs[c][0];
+      Tacc[1] = Rs[c][0] - Rs[c][1];
+      Tacc[2] = Rs[c][1] - Rs[c][2];
+      Tacc[3] = Rs[c][2];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        yv[c][a] = bq1 * Tacc[a] + Vq[a][c];
+        if (HAS_CT) yv[c][a] += fvb * Zs[c];
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = a + 1; b < 4; ++b) {
+          T val = b4 * (Tacc[a] + Tacc[b]) + dq * Ea[edge_of(a, b)][c];
+          if (HAS_CT) val += feo * Zs[c];
+          yv[c][4 + edge_of(a, b)] = val;
+        }
+    }
+  }
+  if (OUT_P) {
+    const T sb = bq[0] + bq[1] + bq[2] + bq[3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) ypv[a] = -(QB * sb + dd * bq[a]);
+  }
+}
+
+// CTA-uniform geometry of the register-resident sweep, held in registers
+template <typename T>
+__device__ __forceinline__ void tile_uniforms(const T* cJn, const T* cv0, const T* cnh, T (&v0)[3], T (&Jn)[9],
+                                              T (&csum)[3], T (&nh)[3]) {
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
     nh[r] = cnh[r];
@@ -235,257 +481,143 @@ __device__ __forceinline__ void tet_sweep_regs(const ApplyParams<T>& P, const Ma
     for (int d = 0; d < 3; ++d) Jn[3 * r + d] = cJn[3 * r + d];
     csum[r] = Jn[3 * r] + Jn[3 * r + 1] + Jn[3 * r + 2];
   }
-  const int2 cinfo = P.classes[tile.cls];
+}
 
+// Register-resident element body, outputs added to the tile block with shared-memory float
+// atomics (one add per node and component of each micro-tet).
+template <typename T, int OP, bool BLEND, int NT>
+__device__ __forceinline__ void tet_sweep_regs(const ApplyParams<T>& P, const MacroGeom<T>& G, const Tile tile,
+                                               const T* us, T* ys, const T* eta_s, const T* p_s, T* yp_s,
+                                               const T* cM, const T* cJn, const T* cv0, const T* cnh,
+                                               const T* dtab, const int tid) {
+  constexpr bool OUT_U = (OP & (OP_A | OP_BT)) != 0;
+  constexpr bool OUT_P = (OP & OP_B) != 0;
+  T v0[3], Jn[9], csum[3], nh[3];
+  tile_uniforms<T>(cJn, cv0, cnh, v0, Jn, csum, nh);
+  const int a0 = tile.ta * TT, b0 = tile.tb * TT, c0 = tile.tc * TT;
+  const int2 cinfo = P.classes[tile.cls];
   for (int t = tid; t < cinfo.y; t += NT) {
     const int code = P.tets[cinfo.x + t];
-    const int ci = code & 15, cj = (code >> 4) & 15, ck = (code >> 8) & 15, pmu = code >> 12;
-    const int p0 = perm_at(pmu, 0), p1 = perm_at(pmu, 1), p2 = perm_at(pmu, 2);
-    const int base = ci + 5 * cj + 25 * ck;
-
-    // nodal values of the micro-tet
-    T u[3][10];
-    if (HAS_U) {
-#pragma unroll
-      for (int a = 0; a < 10; ++a) {
-        const int sa = base + slot_off(pmu, a);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) u[c][a] = us[c * NSLOT2 + sa];
-      }
-    }
-    T ev[4], pv[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      ev[a] = eta_s[base + slot_off(pmu, a)];
-      pv[a] = HAS_P ? p_s[base + slot_off(pmu, a)] : T(0);
-    }
-    const T eta_sum = ev[0] + ev[1] + ev[2] + ev[3];
-    const T p_sum = pv[0] + pv[1] + pv[2] + pv[3];
-
-    // geometry rows of this Freudenthal type: Mp = n Jm^-1 rows in permuted lattice order,
-    // and the lattice steps e_p0, e_p1, e_p2 mapped by Jm/n
-    T Mp[3][3], cp[3][3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      Mp[0][d] = cM[3 * p0 + d];
-      Mp[1][d] = cM[3 * p1 + d];
-      Mp[2][d] = cM[3 * p2 + d];
-    }
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      cp[0][r] = cJn[3 * r + p0];
-      cp[1][r] = cJn[3 * r + p1];
-      cp[2][r] = csum[r] - cp[0][r] - cp[1][r];
-    }
-    // quadrature point 0: cube corner + beta (3 e_p0 + 2 e_p1 + e_p2); the next points add
-    // (alpha - beta) e_p0, e_p1, e_p2 in turn
-    const T qx = T(a0 + ci), qy = T(b0 + cj), qz = T(c0 + ck);
-    T x[3];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-      x[r] = v0[r] + Jn[3 * r] * qx + Jn[3 * r + 1] * qy + Jn[3 * r + 2] * qz +
-             QB * (T(3) * cp[0][r] + T(2) * cp[1][r] + cp[2][r]);
-
-    // qp-independent parts of the lattice gradient: dbase_j = base_{j+1} - base_j
-    T dbase[3][3], U0[3];
-    if (HAS_U) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const T bs0 = bq1 * u[c][0] + b4 * (u[c][4] + u[c][5] + u[c][6]);
-        const T bs1 = bq1 * u[c][1] + b4 * (u[c][4] + u[c][7] + u[c][8]);
-        const T bs2 = bq1 * u[c][2] + b4 * (u[c][5] + u[c][7] + u[c][9]);
-        const T bs3 = bq1 * u[c][3] + b4 * (u[c][6] + u[c][8] + u[c][9]);
-        dbase[0][c] = bs1 - bs0;
-        dbase[1][c] = bs2 - bs1;
-        dbase[2][c] = bs3 - bs2;
-        if (HAS_BC)
-          U0[c] = fvb * (u[c][0] + u[c][1] + u[c][2] + u[c][3]) +
-                  feo * (u[c][4] + u[c][5] + u[c][6] + u[c][7] + u[c][8] + u[c][9]);
-      }
-    }
-
-    T Rs[3][3], Vq[4][3], Ea[6][3], Zs[3], bq[4];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      Zs[c] = T(0);
-#pragma unroll
-      for (int j = 0; j < 3; ++j) Rs[c][j] = T(0);
-#pragma unroll
-      for (int e = 0; e < 6; ++e) Ea[e][c] = T(0);
-    }
-
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (q > 0) {
-#pragma unroll
-        for (int r = 0; r < 3; ++r) x[r] += dd * cp[q - 1][r];
-      }
-      const T r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
-      const T rinv = rsqrt_t<T>(r2);
-      T K[3][3];
-      T hr = T(1), h = T(0);
-      if (BLEND) {
-        h = x[0] * nh[0] + x[1] * nh[1] + x[2] * nh[2];
-        const T hinv = rcp_t<T>(h);
-        hr = h * rinv * dinv;
-        const T ri2 = rinv * rinv;
-        T v[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) v[d] = nh[d] * hinv - x[d] * ri2;
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          const T tj = Mp[j][0] * x[0] + Mp[j][1] * x[1] + Mp[j][2] * x[2];
-#pragma unroll
-          for (int d = 0; d < 3; ++d) K[j][d] = Mp[j][d] - tj * v[d];
-        }
-      } else {
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-#pragma unroll
-          for (int d = 0; d < 3; ++d) K[j][d] = Mp[j][d];
-      }
-      const T coefB = C0 * hr * hr;
-      const T Wq = coefB * hr;
-
-      T trace = T(0), Gp[3][3], wsum[3], wq[3];
-      if (HAS_U) {
-        T D[3][3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          T w[4];
-#pragma unroll
-          for (int a = 0; a < 4; ++a) w[a] = u[c][wnode(a, q)];
-#pragma unroll
-          for (int j = 0; j < 3; ++j) D[j][c] = dbase[j][c] + dq * (w[j + 1] - w[j]);
-          wq[c] = w[q];
-          wsum[c] = w[0] + w[1] + w[2] + w[3] - w[q];
-        }
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-          for (int d = 0; d < 3; ++d) Gp[c][d] = D[0][c] * K[0][d] + D[1][c] * K[1][d] + D[2][c] * K[2][d];
-        trace = Gp[0][0] + Gp[1][1] + Gp[2][2];
-      }
-
-      T gr = T(0);
-      if (NEED_GR) {
-        const T rad = BLEND ? h * dinv : r2 * rinv;
-        if (P.n_dlnrho <= 1) {
-          gr = dtab[0];
-        } else {
-          const T top = T(P.n_dlnrho - 1);
-          T sg = (rad - P.r_cmb) * P.inv_dr * top;
-          sg = sg < T(0) ? T(0) : (sg > top ? top : sg);
-          int ig = (int)sg;
-          ig = ig > P.n_dlnrho - 2 ? P.n_dlnrho - 2 : ig;
-          const T fg = sg - T(ig);
-          gr = (ig + 1 < 64) ? (T(1) - fg) * dtab[ig] + fg * dtab[ig + 1]
-                             : (T(1) - fg) * P.dlnrho[ig] + fg * P.dlnrho[ig + 1];
-        }
-      }
-
-      if (OUT_P) {
-        T b = coefB * trace;
-        if (HAS_BC) {
-          T eu = T(0);
-#pragma unroll
-          for (int c = 0; c < 3; ++c) eu += (U0[c] + (fva - fvb) * wq[c] + (fei - feo) * wsum[c]) * x[c];
-          b += Wq * gr * eu * rinv;
-        }
-        bq[q] = b;
-      }
-
-      if (OUT_U) {
-        T S[3][3];
-        if (OP & OP_A) {
-          const T etaq = QB * eta_sum + dd * ev[q];
-          const T coefA = T(2) * etaq * C0 * hr;
-          const T hA = T(0.5) * coefA;
-          const T t3 = trace * T(1.0 / 3.0);
-          S[0][0] = coefA * (Gp[0][0] - t3);
-          S[1][1] = coefA * (Gp[1][1] - t3);
-          S[2][2] = coefA * (Gp[2][2] - t3);
-          S[0][1] = S[1][0] = hA * (Gp[0][1] + Gp[1][0]);
-          S[0][2] = S[2][0] = hA * (Gp[0][2] + Gp[2][0]);
-          S[1][2] = S[2][1] = hA * (Gp[1][2] + Gp[2][1]);
-        } else {
-#pragma unroll
-          for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int d = 0; d < 3; ++d) S[c][d] = T(0);
-        }
-        T pq = T(0);
-        if (HAS_P) {
-          pq = QB * p_sum + dd * pv[q];
-          const T sp = coefB * pq;
-          S[0][0] -= sp;
-          S[1][1] -= sp;
-          S[2][2] -= sp;
-        }
-        T zq[3] = {T(0), T(0), T(0)};
-        if (HAS_CT) {
-          const T zc = -Wq * pq * gr * rinv;
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            zq[c] = zc * x[c];
-            Zs[c] += zq[c];
-          }
-        }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const T r0 = S[c][0] * K[0][0] + S[c][1] * K[0][1] + S[c][2] * K[0][2];
-          const T r1 = S[c][0] * K[1][0] + S[c][1] * K[1][1] + S[c][2] * K[1][2];
-          const T r2c = S[c][0] * K[2][0] + S[c][1] * K[2][1] + S[c][2] * K[2][2];
-          Rs[c][0] += r0;
-          Rs[c][1] += r1;
-          Rs[c][2] += r2c;
-          T sv[4];
-          sv[0] = -r0;
-          sv[1] = r0 - r1;
-          sv[2] = r1 - r2c;
-          sv[3] = r2c;
-          Vq[q][c] = dq * sv[q] + (HAS_CT ? (fva - fvb) * zq[c] : T(0));
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-            if (a != q) Ea[edge_of(a, q)][c] += sv[a] + (HAS_CT ? ((fei - feo) / dq) * zq[c] : T(0));
-        }
-      }
-    }  // qp loop
-
+    T yv[3][10], ypv[4];
+    tet_element<T, OP, BLEND>(P, G, code, a0, b0, c0, us, eta_s, p_s, cM, cJn, v0, Jn, csum, nh, dtab, yv, ypv);
+    const int pmu = code >> 12;
+    const int base = (code & 15) + 5 * ((code >> 4) & 15) + 25 * ((code >> 8) & 15);
     if (OUT_U) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        T* y = ys + c * NSLOT2;
-        T Tacc[4];
-        Tacc[0] = -Rs[c][0];
-        Tacc[1] = Rs[c][0] - Rs[c][1];
-        Tacc[2] = Rs[c][1] - Rs[c][2];
-        Tacc[3] = Rs[c][2];
+      for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          T val = bq1 * Tacc[a] + Vq[a][c];
-          if (HAS_CT) val += fvb * Zs[c];
-          atomicAdd(&y[base + slot_off(pmu, a)], val);
-        }
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = a + 1; b < 4; ++b) {
-            T val = b4 * (Tacc[a] + Tacc[b]) + dq * Ea[edge_of(a, b)][c];
-            if (HAS_CT) val += feo * Zs[c];
-            atomicAdd(&y[base + slot_off(pmu, 4 + edge_of(a, b))], val);
-          }
-      }
+        for (int a = 0; a < 10; ++a) atomicAdd(&ys[c * NSLOT2 + base + slot_off(pmu, a)], yv[c][a]);
     }
     if (OUT_P) {
-      const T sb = bq[0] + bq[1] + bq[2] + bq[3];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) atomicAdd(&yp_s[base + slot_off(pmu, a)], -(QB * sb + dd * bq[a]));
+      for (int a = 0; a < 4; ++a) atomicAdd(&yp_s[base + slot_off(pmu, a)], ypv[a]);
     }
   }
 }
 
-template <typename T, int OP, bool BLEND, int BODY = 0, int NT = kSweepThreads>
+// Fixed-point accumulation (FP32 sweeps): the micro-tets of a tile are processed in NR rounds
+// of NT; each round has its own int32 copy of the tile block and its own power-of-two scale
+// 2^k_r, chosen after the round's outputs are known so that |output| * 2^k_r < 2^25 for every
+// output of the round.  A slot receives at most 24 contributions per round (the micro-tets
+// around a P2 node), so its integer sum stays below 2^30: no partial or final sum can overflow,
+// the per-add rounding error is at most 2^-26 of the round's largest output, and the sums
+// inside a tile are exact integer additions (native shared-memory reductions, no retry loop,
+// independent of the order of the adds).  The flush converts back: y = sum_r Y_r 2^-k_r.
+// Velocity and pressure outputs have separate scales.  A non-finite output (or one of
+// magnitude >= 2^120) marks the round, and the flush then writes NaN for the whole tile so that
+// the callers' NaN checks still see it.
+constexpr int kFixedMaxRounds = 3;
+__device__ __forceinline__ unsigned abs_bits(float x) { return __float_as_uint(x) & 0x7fffffffu; }
+// scale exponent k of a round from the largest |output| bits; 255 marks a bad round
+__device__ __forceinline__ int fixed_scale_exp(unsigned maxbits) {
+  const int e = (int)(maxbits >> 23) - 127;   // floor(log2 max|out|); -127 for zero / denormals
+  if (maxbits >= 0x7f800000u || e >= 120) return 255;
+  const int k = 24 - e;
+  return k > 100 ? 100 : k;
+}
+__device__ __forceinline__ float exp2_int(int k) { return __int_as_float((k + 127) << 23); }   // |k| <= 126
+__device__ __forceinline__ void red_shared_s32(int* addr, int v) {
+  asm volatile("red.shared.add.s32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(addr)), "r"(v) : "memory");
+}
+
+template <int OP, bool BLEND, int NT, int NR>
+__device__ __forceinline__ void tet_sweep_fixed(const ApplyParams<float>& P, const MacroGeom<float>& G, const Tile tile,
+                                                const float* us, int* ysi, const float* eta_s, const float* p_s,
+                                                int* ypi, const float* cM, const float* cJn, const float* cv0,
+                                                const float* cnh, const float* dtab, unsigned* rmax, const int tid) {
+  constexpr bool OUT_U = (OP & (OP_A | OP_BT)) != 0;
+  constexpr bool OUT_P = (OP & OP_B) != 0;
+  float v0[3], Jn[9], csum[3], nh[3];
+  tile_uniforms<float>(cJn, cv0, cnh, v0, Jn, csum, nh);
+  const int a0 = tile.ta * TT, b0 = tile.tb * TT, c0 = tile.tc * TT;
+  const int2 cinfo = P.classes[tile.cls];
+#pragma unroll 1
+  for (int r = 0; r < NR && r * NT < cinfo.y; ++r) {   // uniform over the CTA
+    const int t = r * NT + tid;
+    const bool active = t < cinfo.y;
+    float yv[3][10], ypv[4];
+    int code = 0;
+    if (active) {
+      code = P.tets[cinfo.x + t];
+      tet_element<float, OP, BLEND>(P, G, code, a0, b0, c0, us, eta_s, p_s, cM, cJn, v0, Jn, csum, nh, dtab, yv, ypv);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int a = 0; a < 10; ++a) yv[c][a] = 0.f;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) ypv[a] = 0.f;
+    }
+    unsigned mu = 0u, mp = 0u;
+    if (OUT_U) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int a = 0; a < 10; ++a) mu = max(mu, abs_bits(yv[c][a]));
+      mu = __reduce_max_sync(0xffffffffu, mu);
+    }
+    if (OUT_P) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) mp = max(mp, abs_bits(ypv[a]));
+      mp = __reduce_max_sync(0xffffffffu, mp);
+    }
+    if ((tid & 31) == 0) {
+      if (OUT_U) atomicMax(&rmax[2 * r], mu);
+      if (OUT_P) atomicMax(&rmax[2 * r + 1], mp);
+    }
+    __syncthreads();
+    if (active) {
+      const int pmu = code >> 12;
+      const int base = (code & 15) + 5 * ((code >> 4) & 15) + 25 * ((code >> 8) & 15);
+      if (OUT_U) {
+        const int k = fixed_scale_exp(rmax[2 * r]);
+        if (k != 255) {
+          const float S = exp2_int(k);
+          int* y = ysi + r * 3 * NSLOT2;
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int a = 0; a < 10; ++a)
+              red_shared_s32(&y[c * NSLOT2 + base + slot_off(pmu, a)], __float2int_rn(yv[c][a] * S));
+        }
+      }
+      if (OUT_P) {
+        const int k = fixed_scale_exp(rmax[2 * r + 1]);
+        if (k != 255) {
+          const float S = exp2_int(k);
+          int* y = ypi + r * NSLOT1;
+#pragma unroll
+          for (int a = 0; a < 4; ++a) red_shared_s32(&y[base + slot_off(pmu, a)], __float2int_rn(ypv[a] * S));
+        }
+      }
+    }
+  }
+}
+
+// BODY 0: shared-memory element body (float atomics, also inside the quadrature loop);
+// BODY 1: register-resident element body with float atomics; BODY 2: register-resident body
+// with fixed-point accumulation in NR rounds (FP32 only).
+template <typename T, int OP, bool BLEND, int BODY = 0, int NT = kSweepThreads, int NR = 1>
 __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m, const int tidx, const int n_tiles) {
   constexpr bool HAS_U = (OP & (OP_A | OP_B)) != 0;
   constexpr bool HAS_P = (OP & OP_BT) != 0;
@@ -495,15 +627,20 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
   constexpr bool HAS_BC = (OP & OP_BC) != 0;
   constexpr bool ETAQ = (OP & OP_ETAQ) != 0;
   static_assert(!ETAQ || OP == (OP_A | OP_ETAQ), "the quadrature-point viscosity serves A alone");
+  static_assert(BODY != 2 || (sizeof(T) == 4 && !ETAQ && NR >= 1 && NR <= kFixedMaxRounds && NR * NT >= 384),
+                "the fixed-point body is FP32, without quadrature-point viscosity, and covers a full tile");
+  constexpr int NCOPY = BODY == 2 ? NR : 1;
 
   // dynamic shared memory, layout of sweep_smem_bytes(): us, ys, eta_s, p_s, yp_s, ts, gid2, gid1
+  // (BODY 2: ys and yp_s hold NR int32 copies)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* us = reinterpret_cast<T*>(smem_raw);
   T* ys = us + (HAS_U ? 3 * NSLOT2 : 0);
-  T* eta_s = ys + (OUT_U ? 3 * NSLOT2 : 0);
+  T* eta_s = ys + (OUT_U ? NCOPY * 3 * NSLOT2 : 0);
   T* p_s = eta_s + NSLOT1;
   T* yp_s = p_s + (HAS_P ? NSLOT1 : 0);
-  T* ts = yp_s + (OUT_P ? NSLOT1 : 0);   // ETAQ: P2 temperature of the tile
+  T* ts = yp_s + (OUT_P ? NCOPY * NSLOT1 : 0);   // ETAQ: P2 temperature of the tile
+  __shared__ unsigned rmax[2 * kFixedMaxRounds];   // BODY 2: largest |output| bits per round
   int* gid2 = reinterpret_cast<int*>(ts + (ETAQ ? NSLOT2 : 0));
   int* gid1 = gid2 + NSLOT2;
   __shared__ T cM[9], cJn[9], cv0[3], cnh[3];
@@ -517,6 +654,7 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
   const int n = P.n, N = 2 * n;
   const int tid = threadIdx.x;
 
+  if (BODY == 2 && tid < 2 * kFixedMaxRounds) rmax[tid] = 0u;
   if (tid < 9) {
     cM[tid] = T(n) * G.Jinv[tid];
     cJn[tid] = G.Jm[tid] / T(n);
@@ -600,9 +738,12 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
       us[2 * NSLOT2 + s] = v2;
     }
     if (OUT_U) {
-      ys[s] = T(0);
-      ys[NSLOT2 + s] = T(0);
-      ys[2 * NSLOT2 + s] = T(0);
+#pragma unroll
+      for (int r = 0; r < NCOPY; ++r) {
+        ys[r * 3 * NSLOT2 + s] = T(0);
+        ys[r * 3 * NSLOT2 + NSLOT2 + s] = T(0);
+        ys[r * 3 * NSLOT2 + 2 * NSLOT2 + s] = T(0);
+      }
     }
   }
   // ---- stage the P1 vertex block (eta, p) ----
@@ -618,13 +759,17 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
     eta_s[s] = e;
     if (HAS_P) p_s[s] = pv;
     if (OUT_P) {
-      yp_s[s] = T(0);
+#pragma unroll
+      for (int r = 0; r < NCOPY; ++r) yp_s[r * NSLOT1 + s] = T(0);
       gid1[s] = id;
     }
   }
   __syncthreads();
 
-  if constexpr (BODY == 1) {
+  if constexpr (BODY == 2) {
+    tet_sweep_fixed<OP, BLEND, NT, NR>(P, G, tile, us, reinterpret_cast<int*>(ys), eta_s, p_s,
+                                       reinterpret_cast<int*>(yp_s), cM, cJn, cv0, cnh, dtab, rmax, tid);
+  } else if constexpr (BODY == 1) {
     tet_sweep_regs<T, OP, BLEND, NT>(P, G, tile, us, ys, eta_s, p_s, yp_s, cM, cJn, cv0, cnh, dtab, tid);
   } else {
   // ---- element sweep: one thread per micro-tet ----
@@ -952,7 +1097,23 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
         }
         continue;
       }
-      T v0 = ys[s], v1 = ys[NSLOT2 + s], v2 = ys[2 * NSLOT2 + s];
+      T v0, v1, v2;
+      if constexpr (BODY == 2) {
+        const int* yi = reinterpret_cast<const int*>(ys);
+        v0 = v1 = v2 = T(0);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          const int k = fixed_scale_exp(rmax[2 * r]);
+          const T inv = k == 255 ? T(__int_as_float(0x7fc00000)) : T(exp2_int(-k));
+          v0 += T(yi[r * 3 * NSLOT2 + s]) * inv;
+          v1 += T(yi[r * 3 * NSLOT2 + NSLOT2 + s]) * inv;
+          v2 += T(yi[r * 3 * NSLOT2 + 2 * NSLOT2 + s]) * inv;
+        }
+      } else {
+        v0 = ys[s];
+        v1 = ys[NSLOT2 + s];
+        v2 = ys[2 * NSLOT2 + s];
+      }
       if (cl == NODE_FREESLIP) {
         int dA, dB, dC;
         slot_coords(s, dA, dB, dC);
@@ -971,7 +1132,19 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
   if (OUT_P) {
     for (int s = tid; s < NSLOT1; s += NT) {
       const int id = gid1[s];
-      if (id >= 0) atomicAdd(&P.yp[id], yp_s[s]);
+      if (id < 0) continue;
+      T v = T(0);
+      if constexpr (BODY == 2) {
+        const int* yi = reinterpret_cast<const int*>(yp_s);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          const int k = fixed_scale_exp(rmax[2 * r + 1]);
+          v += T(yi[r * NSLOT1 + s]) * (k == 255 ? T(__int_as_float(0x7fc00000)) : T(exp2_int(-k)));
+        }
+      } else {
+        v = yp_s[s];
+      }
+      atomicAdd(&P.yp[id], v);
     }
   }
 }
@@ -979,20 +1152,25 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
 // one problem: grid (tiles, 60 macros)
 template <typename T, int OP, bool BLEND>
 __global__ void __launch_bounds__(kSweepThreads, MFS_SWEEP_MINBLOCKS) stokes_tile_kernel(const ApplyParams<T> P) {
-  sweep_tile<T, OP, BLEND>(P, blockIdx.y, blockIdx.x, gridDim.x);
+  sweep_tile<T, OP, BLEND>(P, P.m0 + blockIdx.y, blockIdx.x, gridDim.x);
 }
 // the register-resident element body (FP32 hot path) with NT threads per CTA and MINB
-// resident CTAs per SM (the autotuner's variants 2-4)
+// resident CTAs per SM; float atomics
 template <typename T, int OP, bool BLEND, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) stokes_tile_kernel_regs(const ApplyParams<T> P) {
-  sweep_tile<T, OP, BLEND, 1, NT>(P, blockIdx.y, blockIdx.x, gridDim.x);
+  sweep_tile<T, OP, BLEND, 1, NT>(P, P.m0 + blockIdx.y, blockIdx.x, gridDim.x);
+}
+// the register-resident element body with fixed-point accumulation in ceil(384 / NT) rounds
+template <typename T, int OP, bool BLEND, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) stokes_tile_kernel_fixed(const ApplyParams<T> P) {
+  sweep_tile<T, OP, BLEND, 2, NT, (384 + NT - 1) / NT>(P, P.m0 + blockIdx.y, blockIdx.x, gridDim.x);
 }
 // the same sweep compiled for one fewer resident CTA per SM (more registers per thread);
 // the autotuner picks between the two per level
 template <typename T, int OP, bool BLEND>
 __global__ void __launch_bounds__(kSweepThreads, MFS_SWEEP_MINBLOCKS - 1)
     stokes_tile_kernel_wide(const ApplyParams<T> P) {
-  sweep_tile<T, OP, BLEND>(P, blockIdx.y, blockIdx.x, gridDim.x);
+  sweep_tile<T, OP, BLEND>(P, P.m0 + blockIdx.y, blockIdx.x, gridDim.x);
 }
 
 // an ensemble in one persistent launch: CTA c works on the tiles map[c], map[c + grid], ...

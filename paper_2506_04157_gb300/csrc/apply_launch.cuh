@@ -46,28 +46,37 @@ inline cudaError_t smem_opt_in(const void* func, size_t smem) {
 }
 
 // Sweep variants (mfs_autotune chooses one per level for the FP32 hot sweeps):
-//   0: shared-memory element body, 192 threads, 4 resident CTAs per SM (80 registers)
+//   0: shared-memory element body, float atomics, 192 threads, 4 resident CTAs per SM
 //   1: the same body with 3 resident CTAs per SM
-//   2: register-resident element body, 192 threads, 2 CTAs per SM
-//   3: register-resident element body, 128 threads, 3 CTAs per SM
-//   4: register-resident element body,  96 threads, 4 CTAs per SM
+//   2: register-resident element body, fixed-point accumulation, 192 threads, 2 CTAs per SM
+//   3: the same, 128 threads, 3 CTAs per SM
+//   4: the same, 128 threads, 4 CTAs per SM (128 registers)
+//   5: the same, 256 threads, 2 CTAs per SM (128 registers)
+//   6: the same, 192 threads, 3 CTAs per SM (96 registers)
 template <typename T, int OP, bool BLEND>
-static void (*sweep_kernel(int variant, int* nt))(const ApplyParams<T>) {
-  switch (variant) {
-    case 1: *nt = kSweepThreads; return stokes_tile_kernel_wide<T, OP, BLEND>;
-    case 2: *nt = 192; return stokes_tile_kernel_regs<T, OP, BLEND, 192, 2>;
-    case 3: *nt = 128; return stokes_tile_kernel_regs<T, OP, BLEND, 128, 3>;
-    case 4: *nt = 96; return stokes_tile_kernel_regs<T, OP, BLEND, 96, 4>;
-    default: *nt = kSweepThreads; return stokes_tile_kernel<T, OP, BLEND>;
+static void (*sweep_kernel(int variant, int* nt, size_t* smem))(const ApplyParams<T>) {
+  if constexpr (sizeof(T) == 4 && (OP & OP_ETAQ) == 0) {
+    switch (variant) {
+      case 2: *nt = 192; *smem = sweep_smem_bytes<T, OP, 2>(); return stokes_tile_kernel_fixed<T, OP, BLEND, 192, 2>;
+      case 3: *nt = 128; *smem = sweep_smem_bytes<T, OP, 3>(); return stokes_tile_kernel_fixed<T, OP, BLEND, 128, 3>;
+      case 4: *nt = 128; *smem = sweep_smem_bytes<T, OP, 3>(); return stokes_tile_kernel_fixed<T, OP, BLEND, 128, 4>;
+      case 5: *nt = 256; *smem = sweep_smem_bytes<T, OP, 2>(); return stokes_tile_kernel_fixed<T, OP, BLEND, 256, 2>;
+      case 6: *nt = 192; *smem = sweep_smem_bytes<T, OP, 2>(); return stokes_tile_kernel_fixed<T, OP, BLEND, 192, 3>;
+      default: break;
+    }
   }
+  *nt = kSweepThreads;
+  *smem = sweep_smem_bytes<T, OP>();
+  if (variant == 1) return stokes_tile_kernel_wide<T, OP, BLEND>;
+  return stokes_tile_kernel<T, OP, BLEND>;
 }
 
 template <typename T, int OP, bool BLEND>
-static mfs_status run_sweep_v(const ApplyParams<T>& prm, int n_tiles, mfs_ctx* ctx, int variant) {
-  dim3 grid(n_tiles, kMacroCells);
-  const size_t smem = sweep_smem_bytes<T, OP>();
+static mfs_status run_sweep_v(const ApplyParams<T>& prm, int n_tiles, mfs_ctx* ctx, int variant, int n_macros) {
+  dim3 grid(n_tiles, n_macros);
+  size_t smem = 0;
   int nt = kSweepThreads;
-  auto k = sweep_kernel<T, OP, BLEND>(variant, &nt);
+  auto k = sweep_kernel<T, OP, BLEND>(variant, &nt, &smem);
   MFS_CUDA(smem_opt_in((const void*)k, smem));
   auto ev = timing_events(ctx);
   if (ev.first) cudaEventRecord(ev.first, ctx->stream);
@@ -78,14 +87,16 @@ static mfs_status run_sweep_v(const ApplyParams<T>& prm, int n_tiles, mfs_ctx* c
 
 // the hot FP32 sweeps (A alone: smoothers; fused forward: Krylov) have tunable variants
 template <typename T, int OP>
-static mfs_status run_sweep(const ApplyParams<T>& prm, int n_tiles, int blending, mfs_ctx* ctx, int variant) {
+static mfs_status run_sweep(const ApplyParams<T>& prm, int n_tiles, int blending, mfs_ctx* ctx, int variant,
+                           int n_macros) {
   constexpr bool tunable = sizeof(T) == 4 && (OP == OP_A || OP == (OP_A | OP_BT | OP_B | OP_BC));
   if constexpr (tunable) {
     if (variant > 0 && variant < kSweepVariants)
-      return blending ? run_sweep_v<T, OP, true>(prm, n_tiles, ctx, variant)
-                      : run_sweep_v<T, OP, false>(prm, n_tiles, ctx, variant);
+      return blending ? run_sweep_v<T, OP, true>(prm, n_tiles, ctx, variant, n_macros)
+                      : run_sweep_v<T, OP, false>(prm, n_tiles, ctx, variant, n_macros);
   }
-  return blending ? run_sweep_v<T, OP, true>(prm, n_tiles, ctx, 0) : run_sweep_v<T, OP, false>(prm, n_tiles, ctx, 0);
+  return blending ? run_sweep_v<T, OP, true>(prm, n_tiles, ctx, 0, n_macros)
+                  : run_sweep_v<T, OP, false>(prm, n_tiles, ctx, 0, n_macros);
 }
 
 template <typename T>
@@ -164,7 +175,7 @@ mfs_status launch_batch(const ApplyParams<T>* dparams, const int2* map, const in
 
 template <typename T>
 mfs_status launch_apply(mfs_problem* P, int lvl, int op, int constrained, int withc_b, const T* u,
-                             const T* p, T* yu, T* yp, const T* psum, int zero_out) {
+                             const T* p, T* yu, T* yp, const T* psum, int zero_out, int m0, int m1) {
   mfs_mesh* M = P->mesh;
   const LevelData& L = M->levels[lvl];
   cudaStream_t s = M->ctx->stream;
@@ -191,6 +202,8 @@ mfs_status launch_apply(mfs_problem* P, int lvl, int op, int constrained, int wi
   prm.constrained = constrained;
   prm.bc_surface = P->bc_surface;
   prm.bc_cmb = P->bc_cmb;
+  prm.m0 = m0;
+  const int nm = m1 - m0;
   if (lvl <= P->l_eta && (op & OP_A)) {
     // quadrature-point viscosity on this level
     if (op != OP_A) {
@@ -211,14 +224,14 @@ mfs_status launch_apply(mfs_problem* P, int lvl, int op, int constrained, int wi
   if ((op & OP_B) && withc_b) op |= OP_BC;
   const int bl = M->host.blending;
   switch (op) {
-    case OP_A: MFS_TRY((run_sweep<T, OP_A>(prm, L.n_tiles, bl, M->ctx, L.variant))); break;
-    case OP_A | OP_ETAQ: MFS_TRY((run_sweep<T, OP_A | OP_ETAQ>(prm, L.n_tiles, bl, M->ctx, 0))); break;
-    case OP_BT: MFS_TRY((run_sweep<T, OP_BT>(prm, L.n_tiles, bl, M->ctx, L.variant))); break;
-    case OP_BT | OP_CT: MFS_TRY((run_sweep<T, OP_BT | OP_CT>(prm, L.n_tiles, bl, M->ctx, L.variant))); break;
-    case OP_B: MFS_TRY((run_sweep<T, OP_B>(prm, L.n_tiles, bl, M->ctx, L.variant))); break;
-    case OP_B | OP_BC: MFS_TRY((run_sweep<T, OP_B | OP_BC>(prm, L.n_tiles, bl, M->ctx, L.variant))); break;
-    case OP_A | OP_BT | OP_B | OP_BC: MFS_TRY((run_sweep<T, OP_A | OP_BT | OP_B | OP_BC>(prm, L.n_tiles, bl, M->ctx, L.variant))); break;
-    case OP_A | OP_BT | OP_CT | OP_B: MFS_TRY((run_sweep<T, OP_A | OP_BT | OP_CT | OP_B>(prm, L.n_tiles, bl, M->ctx, L.variant))); break;
+    case OP_A: MFS_TRY((run_sweep<T, OP_A>(prm, L.n_tiles, bl, M->ctx, L.variant, nm))); break;
+    case OP_A | OP_ETAQ: MFS_TRY((run_sweep<T, OP_A | OP_ETAQ>(prm, L.n_tiles, bl, M->ctx, 0, nm))); break;
+    case OP_BT: MFS_TRY((run_sweep<T, OP_BT>(prm, L.n_tiles, bl, M->ctx, L.variant, nm))); break;
+    case OP_BT | OP_CT: MFS_TRY((run_sweep<T, OP_BT | OP_CT>(prm, L.n_tiles, bl, M->ctx, L.variant, nm))); break;
+    case OP_B: MFS_TRY((run_sweep<T, OP_B>(prm, L.n_tiles, bl, M->ctx, L.variant, nm))); break;
+    case OP_B | OP_BC: MFS_TRY((run_sweep<T, OP_B | OP_BC>(prm, L.n_tiles, bl, M->ctx, L.variant, nm))); break;
+    case OP_A | OP_BT | OP_B | OP_BC: MFS_TRY((run_sweep<T, OP_A | OP_BT | OP_B | OP_BC>(prm, L.n_tiles, bl, M->ctx, L.variant, nm))); break;
+    case OP_A | OP_BT | OP_CT | OP_B: MFS_TRY((run_sweep<T, OP_A | OP_BT | OP_CT | OP_B>(prm, L.n_tiles, bl, M->ctx, L.variant, nm))); break;
     default: set_error("internal: unsupported operator combination %d", op); return MFS_EINVAL;
   }
   MFS_CUDA(cudaGetLastError());

@@ -89,7 +89,7 @@ mfs_status mfs_autotune(mfs_problem* P, const char* cache_path) {
     cudaFree(p);
     cudaFree(yp);
     if (st != MFS_OK) {
-      M->levels[l].variant = 0;
+      M->levels[l].variant = kDefaultSweepVariant;
       return st;
     }
     int best = 0;

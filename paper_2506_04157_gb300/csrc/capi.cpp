@@ -620,6 +620,45 @@ static mfs_status dispatch(mfs_problem* P, int lvl, mfs_prec prec, int op, int c
   return apply_typed<float>(P, lvl, op, constrained, withc_b, u, p, yu, yp);
 }
 
+mfs_status mfs_apply_part(mfs_problem* P, int lvl, mfs_prec prec, int fused, int m0, int m1, const void* u,
+                          const void* p, void* yu, void* yp) {
+  if (!u || !yu || (fused && (!p || !yp))) {
+    set_error("null vector pointer");
+    return MFS_EINVAL;
+  }
+  if (m0 < 0 || m1 > kMacroCells || m0 >= m1) {
+    set_error("macro range [%d, %d) outside [0, %d) or empty", m0, m1, kMacroCells);
+    return MFS_EINVAL;
+  }
+  MFS_TRY(check_problem(P, lvl, true));
+  if (prec != MFS_F64 && prec != MFS_F32) {
+    set_error("invalid precision %d", (int)prec);
+    return MFS_EINVAL;
+  }
+  const int op = fused ? (OP_A | OP_BT | OP_B) : OP_A;
+  // constrained element arithmetic (P0 on the inputs, P_v on the outputs, identity rows at
+  // the Dirichlet nodes the range touches); p used as given, no mean removal of yp
+  if (prec == MFS_F64)
+    return launch_apply<double>(P, lvl, op, 1, fused, (const double*)u, (const double*)p, (double*)yu,
+                                (double*)yp, nullptr, 1, m0, m1);
+  return launch_apply<float>(P, lvl, op, 1, fused, (const float*)u, (const float*)p, (float*)yu, (float*)yp,
+                             nullptr, 1, m0, m1);
+}
+
+mfs_status mfs_mesh_macro_topology(const mfs_mesh* M, int* cells, int* edges, int* faces) {
+  if (!M || !cells || !edges || !faces) {
+    set_error("null mesh or output");
+    return MFS_EINVAL;
+  }
+  for (int m = 0; m < kMacroCells; ++m) {
+    const MacroTopo& t = M->host.topo[m];
+    for (int k = 0; k < 4; ++k) cells[4 * m + k] = t.vid[k];
+    for (int k = 0; k < 6; ++k) edges[6 * m + k] = t.eid[k];
+    for (int k = 0; k < 4; ++k) faces[4 * m + k] = t.fid[k];
+  }
+  return MFS_OK;
+}
+
 mfs_status mfs_apply_A(mfs_problem* P, int lvl, mfs_prec prec, mfs_bcmode mode, const void* u, void* y) {
   MFS_TRY(check_vecs(u, y));
   return dispatch(P, lvl, prec, OP_A, mode == MFS_CONSTRAINED, 0, u, nullptr, y, nullptr);

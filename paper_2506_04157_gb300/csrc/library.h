@@ -55,6 +55,13 @@ struct HostTiles {
 };
 HostTiles build_tiles(int n);
 
+// launch variants of the FP32 hot sweeps (element body, threads per CTA, resident CTAs per
+// SM), chosen per level by mfs_autotune; apply_launch.cuh lists them.  The default is the
+// fastest on the GB300 at levels 5 and 6: the register-resident body with fixed-point
+// accumulation, 192 threads, 3 CTAs per SM.
+constexpr int kSweepVariants = 7;
+constexpr int kDefaultSweepVariant = 6;
+
 struct LevelData {
   int l = 0, n = 1;
   Numbering nb2{}, nb1{};
@@ -70,7 +77,7 @@ struct LevelData {
   int* d_er_ci = nullptr;
   double* d_er_w = nullptr;
   int64_t n_tets = 0, n_surface = 0, n_cmb = 0;
-  int variant = 0;   // sweep variant chosen by mfs_autotune (0: default register budget)
+  int variant = kDefaultSweepVariant;   // sweep launch variant (mfs_autotune / mfs_set_tuning)
   // viscosity law (built on first use): per P1 vertex the finest-level P2 node at the same
   // point and the vertex's radius; per P2 node (levels below the finest) the finest node
   int* d_vfine = nullptr;
@@ -163,9 +170,6 @@ struct mfs_problem {
 
 namespace mfs {
 
-// launch variants of the FP32 hot sweeps (element body, threads per CTA, resident CTAs per
-// SM), chosen per level by mfs_autotune; apply_launch.cuh lists them
-constexpr int kSweepVariants = 5;
 
 constexpr int kRedBlocks = 512;     // partial sums of the two-pass reductions
 constexpr int kRedSlots = kRedBlocks + 64;
@@ -173,9 +177,11 @@ constexpr int kRedSlots = kRedBlocks + 64;
 // ---- launchers (apply.cu) ----
 // The sweep adds into yu / yp; they are zeroed first unless zero_out == 0 (the caller
 // guarantees zeros, e.g. the smoother's fused update leaves its apply buffer zeroed).
+// m0, m1: the launch covers the micro-tets of macros m0 <= m < m1 (all 60 by default).
 template <typename T>
 mfs_status launch_apply(mfs_problem* P, int lvl, int op, int constrained, int withc_b, const T* u,
-                        const T* p, T* yu, T* yp, const T* psum, int zero_out = 1);
+                        const T* p, T* yu, T* yp, const T* psum, int zero_out = 1, int m0 = 0,
+                        int m1 = kMacroCells);
 
 template <typename T>
 struct ApplyParams;

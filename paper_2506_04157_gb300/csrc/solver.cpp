@@ -752,6 +752,20 @@ mfs_status mfs_prolongate(mfs_problem* Pb, int lvl, mfs_prec prec, const void* x
   return MFS_OK;
 }
 
+mfs_status mfs_project(mfs_problem* Pb, int lvl, mfs_prec prec, void* x) {
+  MFS_TRY(need_mg(Pb, lvl));
+  if (!x || (prec != MFS_F64 && prec != MFS_F32)) {
+    set_error("null vector or invalid precision");
+    return MFS_EINVAL;
+  }
+  cudaStream_t s = Pb->mesh->ctx->stream;
+  const int64_t n2 = Pb->mesh->levels[lvl].nb2.total;
+  if (prec == MFS_F64) Blas<double>::bproject(Pb->mg->bnd[lvl], n2, (double*)x, s);
+  else Blas<float>::bproject(Pb->mg->bnd[lvl], n2, (float*)x, s);
+  MFS_CUDA(cudaGetLastError());
+  return MFS_OK;
+}
+
 mfs_status mfs_restrict(mfs_problem* Pb, int lvl, mfs_prec prec, const void* rf, void* rc) {
   MFS_TRY(need_mg(Pb, lvl));
   if (lvl == Pb->mg->l_min || !rf || !rc) {
