@@ -60,6 +60,7 @@ typedef struct mfs_ctx mfs_ctx;
 typedef struct mfs_mesh mfs_mesh;
 typedef struct mfs_problem mfs_problem;
 typedef struct mfs_batch mfs_batch;
+typedef struct mfs_mg_state mfs_mg_state;
 
 typedef struct {
   int level;
@@ -209,6 +210,20 @@ mfs_status mfs_get_cheb_bounds(const mfs_problem* prob, int lvl, double* lo, dou
  * Errors: MFS_EINVAL (multigrid not set up, level without smoother, null pointer),
  * MFS_ENAN (the iterate vanished or became non-finite), MFS_ECUDA. */
 mfs_status mfs_estimate_cheb_bounds(mfs_problem* prob, int lvl, const double* x0, double* lam_max);
+
+/* Checkpoint of the viscosity-dependent multigrid state (the forward solution of the paper's
+ * adjoint use "checkpointed per level"): device copies of every level's nodal viscosity (FP64,
+ * FP32) and inverse diagonal of A (FP64, FP32), the Chebyshev intervals, the coarse-level
+ * inverse, and the finest level's M_{1/eta} quadrature weights and inverse diagonal.
+ * mfs_mg_restore copies them back into the problem (same problem, same multigrid range), so a
+ * later adjoint solve runs on the state of the forward solve without recomputing it
+ * (mfs_set_viscosity + mfs_setup_multigrid).  Both synchronise the stream; the checkpoint
+ * allocates device memory (level 6: about 1.9 GB), freed by mfs_mg_state_destroy.
+ * Errors: MFS_EINVAL (multigrid not set up, quadrature-point viscosity in use (l_eta >= 0),
+ * state of another problem or of another level range), MFS_ECUDA. */
+mfs_status mfs_mg_checkpoint(mfs_problem* prob, mfs_mg_state** out);
+mfs_status mfs_mg_restore(mfs_problem* prob, const mfs_mg_state* state);
+mfs_status mfs_mg_state_destroy(mfs_mg_state* state);
 
 /* diag(A) on level lvl without the free-slip projection (paper Sec. 5.2.2), 1 on
  * Dirichlet rows; y: [3][n_p2]. */

@@ -111,6 +111,9 @@ _SIGS = {
     "mfs_prolongate": ([_vp, _i, _i, _vp, _vp], _i),
     "mfs_restrict": ([_vp, _i, _i, _vp, _vp], _i),
     "mfs_project": ([_vp, _i, _i, _vp], _i),
+    "mfs_mg_checkpoint": ([_vp, ctypes.POINTER(_vp)], _i),
+    "mfs_mg_restore": ([_vp, _vp], _i),
+    "mfs_mg_state_destroy": ([_vp], _i),
     "mfs_vcycle": ([_vp, _i, _i, _i, _i, _vp, _vp], _i),
     "mfs_solve_opts_default": ([ctypes.POINTER(SolveOpts)], None),
     "mfs_adjoint_solve": ([_vp, ctypes.POINTER(SolveOpts), _vp, _vp, _vp, _vp, ctypes.POINTER(SolveStats)], _i),
@@ -394,6 +397,16 @@ class Problem:
         _check(lib().mfs_get_cheb_bounds(self.handle, level, ctypes.byref(lo), ctypes.byref(hi)))
         return lo.value, hi.value
 
+    def mg_checkpoint(self):
+        """Device copy of the viscosity-dependent multigrid state (MgState; restore with
+        mg_restore)."""
+        h = ctypes.c_void_p()
+        _check(lib().mfs_mg_checkpoint(self.handle, ctypes.byref(h)))
+        return MgState(h)
+
+    def mg_restore(self, state):
+        _check(lib().mfs_mg_restore(self.handle, state.handle))
+
     def estimate_cheb_bounds(self, level, x0):
         """Re-run the power iteration of the level's Chebyshev interval from x0 (FP64 CUDA
         tensor [3 n_p2]); returns the eigenvalue estimate."""
@@ -635,6 +648,18 @@ def temp_rule():
 def _ptr_array(tensors):
     arr = (ctypes.c_void_p * len(tensors))(*[t.data_ptr() for t in tensors])
     return arr
+
+
+class MgState:
+    """A checkpoint of a problem's viscosity-dependent multigrid state (mfs_mg_checkpoint)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.mfs_mg_state_destroy(self.handle)
+            self.handle = None
 
 
 class Batch:

@@ -586,6 +586,11 @@ mfs_status mfs_set_density(mfs_problem* P, int n, const double* tab) {
   cudaFree(P->d_dlnrho32);
   P->d_dlnrho64 = nullptr;
   P->d_dlnrho32 = nullptr;
+  // a table of equal entries is the constant d ln rho / dr: stored as one entry, so that the
+  // sweeps take the constant directly instead of interpolating at every quadrature point
+  bool constant = true;
+  for (int k = 1; k < n; ++k) constant = constant && tab[k] == tab[0];
+  if (constant) n = 1;
   std::vector<float> t32(tab, tab + n);
   MFS_TRY(upload(&P->d_dlnrho64, tab, (size_t)n, s));
   MFS_TRY(upload(&P->d_dlnrho32, t32.data(), (size_t)n, s));

@@ -671,6 +671,125 @@ mfs_status mfs_set_cheb_bounds(mfs_problem* Pb, int lvl, double lo, double hi) {
   return MFS_OK;
 }
 
+// ------------------------------------------------------------------------- checkpoint
+// The viscosity-dependent state of the hierarchy, copied on the device: per level the nodal
+// viscosity (FP64, FP32) and the inverse diagonal of A (FP64, FP32), the Chebyshev intervals,
+// the coarse-level inverse, and the finest level's M_{1/eta} quadrature weights and inverse
+// diagonal.
+struct mfs_mg_state {
+  mfs_problem* prob = nullptr;
+  int l_min = 0, l_max = 0;
+  std::vector<std::pair<void*, size_t>> blocks;   // device copies in a fixed order
+  std::vector<double> lo, hi;
+  std::vector<int> have_bounds;
+};
+
+namespace mfs {
+// the device arrays of the state, in the order of mfs_mg_state::blocks
+static std::vector<std::pair<void*, size_t>> mg_state_arrays(mfs_problem* Pb) {
+  MG* G = Pb->mg;
+  mfs_mesh* M = Pb->mesh;
+  std::vector<std::pair<void*, size_t>> a;
+  for (int l = 0; l <= M->l_max; ++l) {
+    const size_t n1 = (size_t)M->levels[l].nb1.total;
+    a.push_back({Pb->eta64[l], sizeof(double) * n1});
+    a.push_back({Pb->eta32[l], sizeof(float) * n1});
+  }
+  for (int l = G->l_min; l <= G->l_max; ++l) {
+    const size_t n3 = 3 * (size_t)M->levels[l].nb2.total;
+    a.push_back({G->w64[l].dinv, sizeof(double) * n3});
+    a.push_back({G->w32[l].dinv, sizeof(float) * n3});
+  }
+  a.push_back({G->Ainv, sizeof(double) * (size_t)G->ncoarse * G->ncoarse});
+  const size_t nw = (size_t)mass_weight_count(M->levels[M->l_max]);
+  const size_t n1 = (size_t)M->levels[M->l_max].nb1.total;
+  a.push_back({G->mw64, sizeof(double) * nw});
+  a.push_back({G->mw32, sizeof(float) * nw});
+  a.push_back({G->mdinv64, sizeof(double) * n1});
+  a.push_back({G->mdinv32, sizeof(float) * n1});
+  return a;
+}
+}  // namespace mfs
+
+mfs_status mfs_mg_state_destroy(mfs_mg_state* S) {
+  if (!S) return MFS_OK;
+  for (auto& b : S->blocks) cudaFree(b.first);
+  delete S;
+  return MFS_OK;
+}
+
+mfs_status mfs_mg_checkpoint(mfs_problem* Pb, mfs_mg_state** out) {
+  if (!out) {
+    set_error("null output");
+    return MFS_EINVAL;
+  }
+  *out = nullptr;
+  MFS_TRY(need_mg(Pb, Pb ? (Pb->mg ? Pb->mg->l_max : 0) : 0));
+  if (Pb->l_eta >= 0) {
+    set_error("checkpoint of a hierarchy with quadrature-point viscosity (l_eta >= 0) is not supported");
+    return MFS_EINVAL;
+  }
+  mfs_mg_state* S = new (std::nothrow) mfs_mg_state;
+  if (!S) {
+    set_error("host allocation failed");
+    return MFS_ENOMEM;
+  }
+  S->prob = Pb;
+  S->l_min = Pb->mg->l_min;
+  S->l_max = Pb->mg->l_max;
+  S->lo = Pb->mg->lo;
+  S->hi = Pb->mg->hi;
+  S->have_bounds = Pb->mg->have_bounds;
+  cudaStream_t s = Pb->mesh->ctx->stream;
+  for (auto& a : mg_state_arrays(Pb)) {
+    void* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, a.second ? a.second : 16);
+    if (e == cudaSuccess) {
+      S->blocks.push_back({d, a.second});
+      e = cudaMemcpyAsync(d, a.first, a.second, cudaMemcpyDeviceToDevice, s);
+    }
+    if (e != cudaSuccess) {
+      mfs_mg_state_destroy(S);
+      return cuda_fail(e, "mfs_mg_checkpoint");
+    }
+  }
+  const cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    mfs_mg_state_destroy(S);
+    return cuda_fail(e, "mfs_mg_checkpoint");
+  }
+  *out = S;
+  return MFS_OK;
+}
+
+mfs_status mfs_mg_restore(mfs_problem* Pb, const mfs_mg_state* S) {
+  if (!S || S->prob != Pb) {
+    set_error("null state or a state of another problem");
+    return MFS_EINVAL;
+  }
+  MFS_TRY(need_mg(Pb, S->l_max));
+  if (Pb->mg->l_min != S->l_min || Pb->mg->l_max != S->l_max || Pb->l_eta >= 0) {
+    set_error("the hierarchy's level range or viscosity mode changed since the checkpoint");
+    return MFS_EINVAL;
+  }
+  const auto arrays = mg_state_arrays(Pb);
+  if (arrays.size() != S->blocks.size()) {
+    set_error("internal: checkpoint layout mismatch");
+    return MFS_EINVAL;
+  }
+  cudaStream_t s = Pb->mesh->ctx->stream;
+  for (size_t k = 0; k < arrays.size(); ++k)
+    MFS_CUDA(cudaMemcpyAsync(arrays[k].first, S->blocks[k].first, S->blocks[k].second, cudaMemcpyDeviceToDevice, s));
+  Pb->mg->lo = S->lo;
+  Pb->mg->hi = S->hi;
+  Pb->mg->have_bounds = S->have_bounds;
+  Pb->has_eta = true;
+  Pb->version++;        // coefficient-keyed caches (ensembles, weighted-BFBT operators) rebuild
+  drop_vgraphs(Pb->mg);  // the intervals may differ
+  MFS_CUDA(cudaStreamSynchronize(s));
+  return MFS_OK;
+}
+
 mfs_status mfs_estimate_cheb_bounds(mfs_problem* Pb, int lvl, const double* x0, double* lam_max) {
   MFS_TRY(need_mg(Pb, lvl));
   if (!x0 || !lam_max) {

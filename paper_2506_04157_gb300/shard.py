@@ -147,7 +147,6 @@ class Reducer:
         import torch
         m = np.tile(part.owned, comps).astype(np.float64)
         self.mask64 = torch.as_tensor(m, device=device)
-        self.mask32 = self.mask64.float()
         self.n = part.n * comps
         self.group = group
 
@@ -156,9 +155,6 @@ class Reducer:
         if dist.is_initialized() and dist.get_world_size(self.group) > 1:
             dist.all_reduce(v, op=dist.ReduceOp.SUM, group=self.group)
         return v
-
-    def _mask(self, x):
-        return self.mask64 if x.dtype.itemsize == 8 else self.mask32
 
     def dot(self, x, y):
         """sum_i x_i y_i over all nodes (FP64 accumulation)."""
@@ -299,6 +295,12 @@ def library_level(prob, level, m0, m1, part, group=None, device=None, bounds=Non
             prob.prolongate(level, xc, xf)
             return xf
 
+    if bounds is None:
+        from . import MfsError
+        try:
+            bounds = prob.cheb_bounds(level)
+        except MfsError:            # the coarsest level has no smoother
+            bounds = None
     ex = Exchange(part, comps=3, exclude=exclude_dirichlet, group=group, device=device)
     owned = torch.as_tensor(np.tile(part.owned, 3).astype(np.float64), device=device)
-    return ShardedLevel(partial_A, dinv, project, ex, bounds or prob.cheb_bounds(level), restrict, prolong, owned)
+    return ShardedLevel(partial_A, dinv, project, ex, bounds, restrict, prolong, owned)

@@ -2,7 +2,8 @@
 a stand-in problem solves a small dense nonsymmetric system K(eta) u = f (p = g) exactly, with
 its adjoint K^T lam = du and the gradient -eta_k lam^T (dK/d eta_k) u, so that gradcheck tests
 the wrapper's plumbing: which solve runs in backward, the order of the returned gradients, and
-the restoration of the viscosity when another forward pass changed it in between."""
+the restoration of the forward pass's checkpointed state when another forward pass changed the
+viscosity in between."""
 import types
 
 import pytest
@@ -22,6 +23,7 @@ class DenseProblem:
         self.E = torch.einsum("ki,kj->kij", V, V)          # eta_k's rank-one parts
         self.log_eta = None
         self.setups = 0
+        self.restores = 0
         self.mesh = types.SimpleNamespace(l_max=1, info=lambda L: types.SimpleNamespace(n_p1=NP))
 
     def K(self):
@@ -33,6 +35,13 @@ class DenseProblem:
 
     def setup_multigrid(self, l_min):
         self.setups += 1
+
+    def mg_checkpoint(self):
+        return self.log_eta.clone()
+
+    def mg_restore(self, state):
+        self.restores += 1
+        self.log_eta = state.clone()
 
     def solve(self, f, g, u, p, **opts):
         u.copy_(torch.linalg.solve(self.K(), f))
@@ -67,10 +76,11 @@ def test_backward_restores_the_viscosity_of_its_forward():
     stokes_solve(le2, f, g, prob)                           # another viscosity in between
     setups = prob.setups
     (u1 ** 2).sum().backward()
-    assert prob.setups == setups + 1 and torch.equal(prob.log_eta, le1.detach())
+    # the checkpoint of the first forward pass is restored: no second hierarchy setup
+    assert prob.setups == setups and prob.restores == 1 and torch.equal(prob.log_eta, le1.detach())
     # against the same derivative with no forward pass in between
     prob2 = DenseProblem(2)
     le1b = le1.detach().clone().requires_grad_()
     u1b, _ = stokes_solve(le1b, f, g, prob2)
     (u1b ** 2).sum().backward()
-    assert prob2.setups == 1 and torch.allclose(le1.grad, le1b.grad, rtol=1e-12, atol=0)
+    assert prob2.setups == 1 and prob2.restores == 0 and torch.allclose(le1.grad, le1b.grad, rtol=1e-12, atol=0)

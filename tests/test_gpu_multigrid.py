@@ -136,3 +136,55 @@ def test_buoyancy_rhs(table):
     prob.rhs_buoyancy(torch.tensor(T, device="cuda"), f, scale=2.5)
     ref = buoyancy_rhs(L, T, np.array(table), scale=2.5)
     assert rel(f.cpu().numpy(), ref) <= 1e-10
+
+
+def test_checkpoint_restores_the_hierarchy():
+    """mfs_mg_checkpoint / mfs_mg_restore: after another viscosity and a new setup, restoring
+    the checkpoint brings back every level's viscosity, inverse diagonal, Chebyshev interval,
+    coarse inverse and mass weights: A applies, diagonals, bounds, V-cycles and solves equal
+    those before (FP64)."""
+    H, ctx, gm, _ = setup(3)
+    prob = mfs.Problem(gm)
+    L = H.levels[3]
+    prob.set_viscosity(torch.tensor(W.viscosity_plumes(L.p1_x, seed=11, contrast=1e4), device="cuda"))
+    prob.set_density(W.dlnrho_table_compressible())
+    prob.setup_multigrid(1)
+    state = prob.mg_checkpoint()
+    u = torch.tensor(W.random_field(3 * L.n_p2, 12), device="cuda")
+    f = torch.tensor(H.cons[3].P0(W.random_field(3 * L.n_p2, 13)), device="cuda")
+
+    def snapshot():
+        out = {}
+        for l in (2, 3):
+            n3 = 3 * H.levels[l].n_p2
+            y = torch.empty(n3, dtype=torch.float64, device="cuda")
+            prob.apply_A(l, u[:n3].contiguous(), y, constrained=True)
+            d = torch.empty_like(y)
+            prob.diag_A(l, d)
+            out[l] = (y, d, prob.cheb_bounds(l))
+        x = torch.zeros_like(f)
+        prob.vcycle(3, f, x, 3, 2)
+        out["v"] = x
+        g = torch.zeros(L.n_p1, dtype=torch.float64, device="cuda")
+        uu, pp = torch.zeros_like(f), torch.zeros_like(g)
+        st = prob.solve(f, g, uu, pp, mixed=0)
+        out["solve"] = (uu, st["fgmres_iters"])
+        return out
+
+    a = snapshot()
+    prob.set_viscosity(torch.tensor(W.viscosity_radial(L.p1_x), device="cuda"))
+    prob.setup_multigrid(1)
+    b = snapshot()
+    assert rel(b[3][0].cpu().numpy(), a[3][0].cpu().numpy()) > 1e-3     # the state did change
+    prob.mg_restore(state)
+    c = snapshot()
+    for l in (2, 3):
+        assert rel(c[l][0].cpu().numpy(), a[l][0].cpu().numpy()) <= 1e-13
+        assert rel(c[l][1].cpu().numpy(), a[l][1].cpu().numpy()) <= 1e-13 and c[l][2] == a[l][2]
+    assert rel(c["v"].cpu().numpy(), a["v"].cpu().numpy()) <= 1e-12
+    assert rel(c["solve"][0].cpu().numpy(), a["solve"][0].cpu().numpy()) <= 1e-8
+    other = mfs.Problem(gm)
+    other.set_viscosity(torch.tensor(W.viscosity_radial(L.p1_x), device="cuda"))
+    other.setup_multigrid(1)
+    with pytest.raises(mfs.MfsError):
+        other.mg_restore(state)
