@@ -610,6 +610,34 @@ def oracle_levels(budget_s=3.0):
     return out
 
 
+def compare_preconditioners(level, max_iters=200):
+    """The block preconditioners and Schur approximations of Sec. 5.2 on the same workload and
+    forcing as the bench's solves (FP64 outer FGMRES around the FP32 preconditioner, mixed = 2;
+    tol_A 1e-4 for the one-sided Uzawa steps): FGMRES iterations, time, reached residual."""
+    import torch
+    ctx, mesh, prob, inf = setup_problem(level, 0)
+    dev = "cuda:0"
+    f = buoyancy_forcing(mesh, prob, level, dev)
+    g = torch.zeros(inf.n_p1, dtype=torch.float64, device=dev)
+    out = {}
+    for sname, schur in (("vbfbt", 0), ("mass", 1), ("diagA_bfbt", 2), ("wbfbt_consistent", 3)):
+        for uname, uzawa in (("symmetric", 0), ("inexact", 1), ("adjoint_inexact", 2)):
+            opts = dict(mixed=2, schur=schur, uzawa=uzawa, max_iters=max_iters)
+            if uzawa:
+                opts["tol_A"] = 1e-4
+            prob.setup_multigrid(1)
+            u = torch.zeros(3 * inf.n_p2, dtype=torch.float64, device=dev)
+            p = torch.zeros(inf.n_p1, dtype=torch.float64, device=dev)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = prob.solve(f, g, u, p, raise_on_error=False, **opts)
+            torch.cuda.synchronize()
+            out[f"{sname}/{uname}"] = {"fgmres_iters": st["fgmres_iters"], "time_s": round(time.perf_counter() - t0, 2),
+                                       "rel_residual": st["rel_residual"], "status": st["status"]}
+            print(json.dumps({f"{sname}/{uname}": out[f"{sname}/{uname}"]}), flush=True)
+    print(json.dumps({"compare_preconditioners": out, "level": level}), flush=True)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -656,6 +684,8 @@ def main():
     ap.add_argument("--no-solve-fp64", dest="solve_fp64", action="store_false")
     ap.add_argument("--solve-fp64-l5", action="store_true", help="also the plain FP64 solve at level 5")
     ap.add_argument("--solve-reps", type=int, default=3, help="level-5 mixed-precision solves (median reported)")
+    ap.add_argument("--compare-preconditioners", action="store_true",
+                    help="only the Uzawa x Schur comparison of the solver on the --level workload")
     ap.add_argument("--profile-solve", action="store_true",
                     help="profiler window only (cudaProfilerStart/Stop): one V-cycle (3,2), one V-cycle "
                          "(1,1) and a solve capped at one FGMRES iteration, for ncu --profile-from-start off")
@@ -665,6 +695,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.profile_solve:
         profile_solve(args.level)
+        return
+    if args.compare_preconditioners:
+        compare_preconditioners(args.level)
         return
     if args.impl == "reference":
         line = run_reference(args, rank, world)

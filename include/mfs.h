@@ -225,6 +225,16 @@ mfs_status mfs_mg_checkpoint(mfs_problem* prob, mfs_mg_state** out);
 mfs_status mfs_mg_restore(mfs_problem* prob, const mfs_mg_state* state);
 mfs_status mfs_mg_state_destroy(mfs_mg_state* state);
 
+/* Form of the constraint (mass-conservation) row.  rho_weighted = 0 (default): the paper's
+ * B + C of Eq. SaddlePointStructure, -int q (div u + grad ln rho . u).  rho_weighted = 1: the
+ * density-weighted form -int q div(rho u) = -int q rho (div u + grad ln rho . u), rho(r) the
+ * profile of mfs_set_density normalised to rho(r_surf) = 1 — the same continuous constraint
+ * scaled by rho, a different discrete weighting.  It replaces B + C everywhere the library
+ * uses it (applies with with_C, the fused apply and its transpose, the Uzawa pressure update,
+ * residuals); the momentum rows keep B^T.  Batches refuse members with rho_weighted = 1.
+ * Errors: MFS_EINVAL. */
+mfs_status mfs_set_constraint_form(mfs_problem* prob, int rho_weighted);
+
 /* diag(A) on level lvl without the free-slip projection (paper Sec. 5.2.2), 1 on
  * Dirichlet rows; y: [3][n_p2]. */
 mfs_status mfs_diag_A(mfs_problem* prob, int lvl, mfs_prec prec, void* y);
@@ -311,8 +321,8 @@ typedef struct {
                          with a vertex on the outer surface (1, 1; Table parametertable) */
   double tol_wBFBT;   /* CG on K_{1/sqrt(eta)}, relative or absolute, whichever is met first
                          (1e-10; at least 1e-5 in FP32) */
-  int vmass;          /* weighted-BFBT vector mass M_{sqrt(eta)}: 0 the lumped mass (default),
-                         1 the consistent mass (mfs_apply_vmass) by Jacobi-preconditioned CG on
+  int vmass;          /* weighted-BFBT vector mass M_{sqrt(eta)}: 0 the lumped mass, 1 (default)
+                         the consistent mass (mfs_apply_vmass) by Jacobi-preconditioned CG on
                          the constrained velocity space to tol_VectorMass (Sec. 5.2.3); with
                          schur = 3 the cg_M_* statistics count these CGs.  The consistent mass
                          keeps the approximation's spectrum of order one under refinement and

@@ -120,6 +120,19 @@ def element_C(geo, mesh, dlnrho_table):
     return -np.einsum("eq,qk,eqi->eki", geo.W, geo.psi, val)
 
 
+def element_B_rho(geo, mesh, dlnrho_table):
+    """(E,4,30): the density-weighted constraint -int psi_k div(rho phi_i)
+    = -int rho psi_k (div phi_i + grad ln rho . phi_i): the integrand of B + C weighted by
+    rho(r) at the quadrature point (rho(r_surf) = 1; the form int q div(rho u) of the
+    compressible continuity equation, Sec. 2, with the sign of B)."""
+    r = np.linalg.norm(geo.x, axis=-1)                                                     # (E,Q)
+    rho = rho_profile(dlnrho_table, r, mesh.r_cmb, mesh.r_surf)
+    div = np.transpose(geo.grad, (0, 1, 3, 2)).reshape(geo.grad.shape[0], 4, 30)
+    g = interp_table(dlnrho_table, r, mesh.r_cmb, mesh.r_surf)[..., None] * geo.x / r[..., None]
+    val = div + np.einsum("eqc,qa->eqca", g, geo.phi).reshape(geo.x.shape[0], 4, 30)
+    return -np.einsum("eq,qk,eqi->eki", geo.W * rho, geo.psi, val)
+
+
 def element_mass_p1(geo, weight_q):
     """(E,4,4): int w psi_j psi_k with quadrature-point weight w (E,Q)."""
     return np.einsum("eq,qk,qj->ekj", geo.W * weight_q, geo.psi, geo.psi)
@@ -151,11 +164,14 @@ def viscosity_law(x, T, law):
 
 class Operators:
     """Assembled FP64 blocks on one level (matrix entries are the definition, the
-    matrix-vector product is the operator application).  With `law` and the level's P2
+    matrix-vector product is the operator application).  rho_weighted: the constraint is
+    -int q div(rho u) (element_B_rho) in place of B + C of Eq. SaddlePointStructure; C then
+    holds the difference, so that B + C is always the constraint and B stays the momentum
+    equation's (incompressible) block.  With `law` and the level's P2
     temperature T_p2, A takes the viscosity at the quadrature points, eta(x_q, T(x_q)) with
     T(x_q) the P2 interpolant (Sec. 5.2.2, levels up to l_eta); M_{1/eta} keeps eta_p1."""
 
-    def __init__(self, level, eta_p1, dlnrho_table=(0.0,), chunk=4096, law=None, T_p2=None):
+    def __init__(self, level, eta_p1, dlnrho_table=(0.0,), chunk=4096, law=None, T_p2=None, rho_weighted=False):
         mesh = level.mesh
         nu, npp = 3 * level.n_p2, level.n_p1
         E = level.tet_p2.shape[0]
@@ -173,7 +189,10 @@ class Operators:
             else:
                 As.append(assemble(vd, vd, element_A(geo, ev), (nu, nu)))
             Bs.append(assemble(pd, vd, element_B(geo), (npp, nu)))
-            Cs.append(assemble(pd, vd, element_C(geo, mesh, dlnrho_table), (npp, nu)))
+            if rho_weighted:   # C holds B_rho - B, so that B + C is the density-weighted constraint
+                Cs.append(assemble(pd, vd, element_B_rho(geo, mesh, dlnrho_table) - element_B(geo), (npp, nu)))
+            else:
+                Cs.append(assemble(pd, vd, element_C(geo, mesh, dlnrho_table), (npp, nu)))
             etaq = ev @ QUAD_BARY.T
             Ms.append(assemble(pd, pd, element_mass_p1(geo, 1.0 / etaq), (npp, npp)))
         self.A = sum(As[1:], As[0]).tocsr()

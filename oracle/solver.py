@@ -175,7 +175,7 @@ class Hierarchy:
     """Per-level constrained operators, diagonals, transfers and Chebyshev bounds."""
 
     def __init__(self, mesh, l_max, eta_fine, dlnrho_table=(0.0,), bc=(0, 1), l_min=1,
-                 bounds=None, with_C=True, law=None, T_fine=None, l_eta=-1):
+                 bounds=None, with_C=True, law=None, T_fine=None, l_eta=-1, rho_weighted=False):
         self.mesh, self.l_min, self.l_max = mesh, l_min, l_max
         self.levels, self.ops, self.cons, self.co, self.diag = {}, {}, {}, {}, {}
         Lf = Level(mesh, l_max)
@@ -199,9 +199,9 @@ class Hierarchy:
             L = self.levels[l]
             eta = self.etas[l]
             if law is not None and l <= l_eta:
-                ops = Operators(L, eta, dlnrho_table, law=law, T_p2=self.T[l])
+                ops = Operators(L, eta, dlnrho_table, law=law, T_p2=self.T[l], rho_weighted=rho_weighted)
             else:
-                ops = Operators(L, eta, dlnrho_table)
+                ops = Operators(L, eta, dlnrho_table, rho_weighted=rho_weighted)
             cons = Constraints(L, *bc)
             self.ops[l], self.cons[l] = ops, cons
             self.co[l] = ConstrainedOperators(ops, cons, with_C=with_C)

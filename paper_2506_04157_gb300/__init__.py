@@ -94,6 +94,7 @@ _SIGS = {
     "mfs_problem_destroy": ([_vp], _i),
     "mfs_set_viscosity": ([_vp, _vp, _i], _i),
     "mfs_set_density": ([_vp, _i, _vp], _i),
+    "mfs_set_constraint_form": ([_vp, _i], _i),
     "mfs_apply_A": ([_vp, _i, _i, _i, _vp, _vp], _i),
     "mfs_apply_B": ([_vp, _i, _i, _i, _i, _vp, _vp], _i),
     "mfs_apply_BT": ([_vp, _i, _i, _i, _i, _vp, _vp], _i),
@@ -336,6 +337,10 @@ class Problem:
     def set_density(self, dlnrho_dr):
         t = np.ascontiguousarray(np.atleast_1d(dlnrho_dr), dtype=np.float64)
         _check(lib().mfs_set_density(self.handle, t.size, t.ctypes.data_as(ctypes.c_void_p)))
+
+    def set_constraint_form(self, rho_weighted):
+        """The constraint row: the paper's B + C (False) or -int q div(rho u) (True)."""
+        _check(lib().mfs_set_constraint_form(self.handle, int(bool(rho_weighted))))
 
     def _sizes(self, level):
         inf = self.mesh.info(level)

@@ -54,6 +54,7 @@ struct ApplyParams {
   T* yp;             // [n_p1]    (OP_B), accumulated atomically: zeroed by the launcher
   const T* eta;      // [n_p1] nodal viscosity of this level
   const T* dlnrho;   // radial table of d ln rho / dr (n_dlnrho entries)
+  const T* dlnrho_int;   // OP_RHO: its integral from r_cmb to each table node (n_dlnrho entries)
   const T* psum;     // device scalar: sum of p; p - psum/n_p1 is used (P_p), or nullptr
   const MacroGeom<T>* geom;
   const Tile* tiles;
@@ -123,6 +124,24 @@ __device__ __forceinline__ T dlnrho_at(const ApplyParams<T>& P, T r) {
   i = i > P.n_dlnrho - 2 ? P.n_dlnrho - 2 : i;
   const T f = s - T(i);
   return (T(1) - f) * P.dlnrho[i] + f * P.dlnrho[i + 1];
+}
+
+// rho(r) = exp(int_{r_surf}^{r} d ln rho/dr), rho(r_surf) = 1, for the piecewise-linear table
+// (integrated exactly: the node integrals from the table plus one trapezoid inside the cell)
+template <typename T>
+__device__ __forceinline__ T rho_bar(const ApplyParams<T>& P, T rad) {
+  if (P.n_dlnrho <= 1) return exp(P.dlnrho[0] * (rad - P.r_surf));
+  const int nt = P.n_dlnrho;
+  const T top = T(nt - 1);
+  T s = (rad - P.r_cmb) * P.inv_dr * top;
+  s = s < T(0) ? T(0) : (s > top ? top : s);
+  int i = (int)s;
+  i = i > nt - 2 ? nt - 2 : i;
+  const T f = s - T(i);
+  const T hcell = T(1) / (P.inv_dr * top);
+  const T g = (T(1) - f) * P.dlnrho[i] + f * P.dlnrho[i + 1];
+  const T G = P.dlnrho_int[i] + T(0.5) * (P.dlnrho[i] + g) * f * hcell;
+  return exp(G - P.dlnrho_int[nt - 1]);
 }
 
 // outward radial unit vector at a lattice point (Kuhn coordinates A,B,C of N)
@@ -216,6 +235,7 @@ __device__ __forceinline__ void tet_element(const ApplyParams<T>& P, const Macro
   constexpr bool HAS_CT = (OP & OP_CT) != 0;
   constexpr bool HAS_BC = (OP & OP_BC) != 0;
   constexpr bool NEED_GR = (OUT_P && HAS_BC) || HAS_CT;
+  constexpr bool RHO = (OP & OP_RHO) != 0;
   const T QA = T(MFS_QA), QB = T(MFS_QB);
   const T dd = QA - QB;
   const T dq = T(4) * dd;                  // 4(alpha - beta)
@@ -371,6 +391,7 @@ __device__ __forceinline__ void tet_element(const ApplyParams<T>& P, const Macro
       }
     }
 
+    const T rq = RHO ? rho_bar<T>(P, BLEND ? h * dinv : r2 * rinv) : T(1);
     if (OUT_P) {
       T b = coefB * trace;
       if (HAS_BC) {
@@ -378,6 +399,7 @@ __device__ __forceinline__ void tet_element(const ApplyParams<T>& P, const Macro
 #pragma unroll
         for (int c = 0; c < 3; ++c) eu += (U0[c] + (fva - fvb) * wq[c] + (fei - feo) * wsum[c]) * x[c];
         b += Wq * gr * eu * rinv;
+        if (RHO) b *= rq;
       }
       bq[q] = b;
     }
@@ -404,6 +426,7 @@ __device__ __forceinline__ void tet_element(const ApplyParams<T>& P, const Macro
       T pq = T(0);
       if (HAS_P) {
         pq = QB * p_sum + dd * pv[q];
+        if (RHO && HAS_CT) pq *= rq;   // the transposed density-weighted constraint
         const T sp = coefB * pq;
         S[0][0] -= sp;
         S[1][1] -= sp;
@@ -528,6 +551,12 @@ __device__ __forceinline__ void tet_sweep_regs(const ApplyParams<T>& P, const Ma
 // the callers' NaN checks still see it.
 constexpr int kFixedMaxRounds = 3;
 __device__ __forceinline__ unsigned abs_bits(float x) { return __float_as_uint(x) & 0x7fffffffu; }
+// max(m, |x|), NaN if either is NaN
+__device__ __forceinline__ float max_nan_abs(float m, float x) {
+  float r;
+  asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(m), "f"(fabsf(x)));
+  return r;
+}
 // scale exponent k of a round from the largest |output| bits; 255 marks a bad round
 __device__ __forceinline__ int fixed_scale_exp(unsigned maxbits) {
   const int e = (int)(maxbits >> 23) - 127;   // floor(log2 max|out|); -127 for zero / denormals
@@ -568,18 +597,21 @@ __device__ __forceinline__ void tet_sweep_fixed(const ApplyParams<float>& P, con
 #pragma unroll
       for (int a = 0; a < 4; ++a) ypv[a] = 0.f;
     }
+    // largest |output| of the thread (a NaN propagates: max.NaN), then of the warp as float bits
     unsigned mu = 0u, mp = 0u;
     if (OUT_U) {
+      float m = 0.f;
 #pragma unroll
       for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int a = 0; a < 10; ++a) mu = max(mu, abs_bits(yv[c][a]));
-      mu = __reduce_max_sync(0xffffffffu, mu);
+        for (int a = 0; a < 10; ++a) m = max_nan_abs(m, yv[c][a]);
+      mu = __reduce_max_sync(0xffffffffu, abs_bits(m));
     }
     if (OUT_P) {
+      float m = 0.f;
 #pragma unroll
-      for (int a = 0; a < 4; ++a) mp = max(mp, abs_bits(ypv[a]));
-      mp = __reduce_max_sync(0xffffffffu, mp);
+      for (int a = 0; a < 4; ++a) m = max_nan_abs(m, ypv[a]);
+      mp = __reduce_max_sync(0xffffffffu, abs_bits(m));
     }
     if ((tid & 31) == 0) {
       if (OUT_U) atomicMax(&rmax[2 * r], mu);
@@ -936,7 +968,9 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
         }
       }
 
-      // B: weights of -(div u + grad ln rho . u)
+      // B: weights of -(div u + grad ln rho . u); OP_RHO: times rho at the point
+      constexpr bool RHO = (OP & OP_RHO) != 0;
+      const T rq = RHO ? rho_bar<T>(P, BLEND ? h * dinv : r2 * rinv) : T(1);
       if (OUT_P) {
         T b = coefB * trace;
         if (HAS_BC) {
@@ -944,6 +978,7 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
 #pragma unroll
           for (int c = 0; c < 3; ++c) eu += (U0[c] + (fva - fvb) * wq[c] + (fei - feo) * wsum[c]) * x[c];
           b += Wq * gr * eu * rinv;
+          if (RHO) b *= rq;
         }
         bq[q] = b;
       }
@@ -983,6 +1018,7 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
         T pq = T(0);
         if (HAS_P) {
           pq = QB * p_sum + (QA - QB) * p_v[q];
+          if (RHO && HAS_CT) pq *= rq;   // the transposed density-weighted constraint
           const T sp = coefB * pq;
           S[0][0] -= sp;
           S[1][1] -= sp;

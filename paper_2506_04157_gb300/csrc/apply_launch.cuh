@@ -19,6 +19,7 @@ struct PrecData<double> {
   static const double* lbase(mfs_problem* P) { return P->d_lbase64; }
   static const MacroGeom<double>* geom(mfs_mesh* M) { return M->d_geom64; }
   static const double* dlnrho(mfs_problem* P) { return P->d_dlnrho64; }
+  static const double* dlnrho_int(mfs_problem* P) { return P->d_dlnrho_int64; }
 };
 template <>
 struct PrecData<float> {
@@ -27,6 +28,7 @@ struct PrecData<float> {
   static const float* lbase(mfs_problem* P) { return P->d_lbase32; }
   static const MacroGeom<float>* geom(mfs_mesh* M) { return M->d_geom32; }
   static const float* dlnrho(mfs_problem* P) { return P->d_dlnrho32; }
+  static const float* dlnrho_int(mfs_problem* P) { return P->d_dlnrho_int32; }
 };
 
 // Opt a kernel in to its dynamic shared memory once per (kernel, device): the attribute is a
@@ -111,6 +113,7 @@ ApplyParams<T> fill_params(mfs_problem* P, int lvl, int constrained, const T* u,
   prm.yp = yp;
   prm.eta = PrecData<T>::eta(P, lvl);
   prm.dlnrho = PrecData<T>::dlnrho(P);
+  prm.dlnrho_int = PrecData<T>::dlnrho_int(P);
   prm.n_dlnrho = P->n_dlnrho;
   prm.psum = psum;
   prm.geom = PrecData<T>::geom(M);
@@ -123,6 +126,7 @@ ApplyParams<T> fill_params(mfs_problem* P, int lvl, int constrained, const T* u,
   prm.n_p1 = L.nb1.total;
   prm.n = L.n;
   prm.r_cmb = (T)M->host.r_cmb;
+  prm.r_surf = (T)M->host.r_surf;
   prm.inv_dr = (T)(1.0 / (M->host.r_surf - M->host.r_cmb));
   prm.constrained = constrained;
   prm.bc_surface = P->bc_surface;
@@ -186,6 +190,7 @@ mfs_status launch_apply(mfs_problem* P, int lvl, int op, int constrained, int wi
   prm.yp = yp;
   prm.eta = PrecData<T>::eta(P, lvl);
   prm.dlnrho = PrecData<T>::dlnrho(P);
+  prm.dlnrho_int = PrecData<T>::dlnrho_int(P);
   prm.n_dlnrho = P->n_dlnrho;
   prm.psum = psum;
   prm.geom = PrecData<T>::geom(M);
@@ -198,6 +203,7 @@ mfs_status launch_apply(mfs_problem* P, int lvl, int op, int constrained, int wi
   prm.n_p1 = L.nb1.total;
   prm.n = L.n;
   prm.r_cmb = (T)M->host.r_cmb;
+  prm.r_surf = (T)M->host.r_surf;
   prm.inv_dr = (T)(1.0 / (M->host.r_surf - M->host.r_cmb));
   prm.constrained = constrained;
   prm.bc_surface = P->bc_surface;
@@ -222,6 +228,7 @@ mfs_status launch_apply(mfs_problem* P, int lvl, int op, int constrained, int wi
   if (zero_out && (op & (OP_A | OP_BT))) MFS_CUDA(cudaMemsetAsync(yu, 0, sizeof(T) * 3 * (size_t)L.nb2.total, s));
   if (zero_out && (op & OP_B)) MFS_CUDA(cudaMemsetAsync(yp, 0, sizeof(T) * (size_t)L.nb1.total, s));
   if ((op & OP_B) && withc_b) op |= OP_BC;
+  if (P->rho_weighted && (op & (OP_BC | OP_CT))) op |= OP_RHO;
   const int bl = M->host.blending;
   switch (op) {
     case OP_A: MFS_TRY((run_sweep<T, OP_A>(prm, L.n_tiles, bl, M->ctx, L.variant, nm))); break;
@@ -232,6 +239,12 @@ mfs_status launch_apply(mfs_problem* P, int lvl, int op, int constrained, int wi
     case OP_B | OP_BC: MFS_TRY((run_sweep<T, OP_B | OP_BC>(prm, L.n_tiles, bl, M->ctx, L.variant, nm))); break;
     case OP_A | OP_BT | OP_B | OP_BC: MFS_TRY((run_sweep<T, OP_A | OP_BT | OP_B | OP_BC>(prm, L.n_tiles, bl, M->ctx, L.variant, nm))); break;
     case OP_A | OP_BT | OP_CT | OP_B: MFS_TRY((run_sweep<T, OP_A | OP_BT | OP_CT | OP_B>(prm, L.n_tiles, bl, M->ctx, L.variant, nm))); break;
+    case OP_B | OP_BC | OP_RHO: MFS_TRY((run_sweep<T, OP_B | OP_BC | OP_RHO>(prm, L.n_tiles, bl, M->ctx, 0, nm))); break;
+    case OP_BT | OP_CT | OP_RHO: MFS_TRY((run_sweep<T, OP_BT | OP_CT | OP_RHO>(prm, L.n_tiles, bl, M->ctx, 0, nm))); break;
+    case OP_A | OP_BT | OP_B | OP_BC | OP_RHO:
+      MFS_TRY((run_sweep<T, OP_A | OP_BT | OP_B | OP_BC | OP_RHO>(prm, L.n_tiles, bl, M->ctx, 0, nm))); break;
+    case OP_A | OP_BT | OP_CT | OP_B | OP_RHO:
+      MFS_TRY((run_sweep<T, OP_A | OP_BT | OP_CT | OP_B | OP_RHO>(prm, L.n_tiles, bl, M->ctx, 0, nm))); break;
     default: set_error("internal: unsupported operator combination %d", op); return MFS_EINVAL;
   }
   MFS_CUDA(cudaGetLastError());

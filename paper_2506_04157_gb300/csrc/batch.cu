@@ -223,6 +223,10 @@ mfs_status mfs_batch_create(mfs_ctx* ctx, int n, mfs_problem* const* probs, mfs_
       set_error("batch member %d: null, on another context, or without viscosity", b);
       return MFS_EINVAL;
     }
+    if (probs[b]->rho_weighted) {
+      set_error("batch member %d uses the density-weighted constraint, which the batched sweep does not have", b);
+      return MFS_EINVAL;
+    }
     if (probs[b]->mesh->host.blending != probs[0]->mesh->host.blending) {
       set_error("batch members must all be blended or all polyhedral");
       return MFS_EINVAL;
@@ -286,11 +290,17 @@ mfs_status mfs_batch_apply_stokes(mfs_batch* B, mfs_prec prec, int transpose, co
     set_error("null argument");
     return MFS_EINVAL;
   }
-  for (size_t b = 0; b < B->probs.size(); ++b)
+  for (size_t b = 0; b < B->probs.size(); ++b) {
     if (!u[b] || !p[b] || !yu[b] || !yp[b]) {
       set_error("null vector for batch member %d", (int)b);
       return MFS_EINVAL;
     }
+    if (B->probs[b]->rho_weighted) {
+      set_error("batch member %d uses the density-weighted constraint, which the batched sweep does not have",
+                (int)b);
+      return MFS_EINVAL;
+    }
+  }
   if (prec == MFS_F64) return batch_apply_typed<double>(B, transpose, 1, u, p, yu, yp);
   if (prec == MFS_F32) return batch_apply_typed<float>(B, transpose, 1, u, p, yu, yp);
   set_error("invalid precision");

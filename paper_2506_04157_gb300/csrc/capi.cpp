@@ -378,6 +378,8 @@ mfs_status mfs_problem_destroy(mfs_problem* P) {
   cudaFree(P->d_lbase32);
   cudaFree(P->d_dlnrho64);
   cudaFree(P->d_dlnrho32);
+  cudaFree(P->d_dlnrho_int64);
+  cudaFree(P->d_dlnrho_int32);
   cudaFree(P->d_red64);
   cudaFree(P->d_red32);
   delete P;
@@ -592,6 +594,17 @@ mfs_status mfs_set_density(mfs_problem* P, int n, const double* tab) {
   for (int k = 1; k < n; ++k) constant = constant && tab[k] == tab[0];
   if (constant) n = 1;
   std::vector<float> t32(tab, tab + n);
+  // integral of the piecewise-linear table from r_cmb to each node (trapezoids are exact)
+  std::vector<double> gi(n, 0.0);
+  const double hcell = n > 1 ? (P->mesh->host.r_surf - P->mesh->host.r_cmb) / (n - 1) : 0.0;
+  for (int k = 1; k < n; ++k) gi[k] = gi[k - 1] + 0.5 * (tab[k - 1] + tab[k]) * hcell;
+  std::vector<float> gi32(gi.begin(), gi.end());
+  cudaFree(P->d_dlnrho_int64);
+  cudaFree(P->d_dlnrho_int32);
+  P->d_dlnrho_int64 = nullptr;
+  P->d_dlnrho_int32 = nullptr;
+  MFS_TRY(upload(&P->d_dlnrho_int64, gi.data(), (size_t)n, s));
+  MFS_TRY(upload(&P->d_dlnrho_int32, gi32.data(), (size_t)n, s));
   MFS_TRY(upload(&P->d_dlnrho64, tab, (size_t)n, s));
   MFS_TRY(upload(&P->d_dlnrho32, t32.data(), (size_t)n, s));
   MFS_CUDA(cudaStreamSynchronize(s));
@@ -623,6 +636,16 @@ static mfs_status dispatch(mfs_problem* P, int lvl, mfs_prec prec, int op, int c
   }
   if (prec == MFS_F64) return apply_typed<double>(P, lvl, op, constrained, withc_b, u, p, yu, yp);
   return apply_typed<float>(P, lvl, op, constrained, withc_b, u, p, yu, yp);
+}
+
+mfs_status mfs_set_constraint_form(mfs_problem* P, int rho_weighted) {
+  if (!P || (rho_weighted != 0 && rho_weighted != 1)) {
+    set_error("null problem or rho_weighted outside {0, 1}");
+    return MFS_EINVAL;
+  }
+  P->rho_weighted = rho_weighted;
+  P->version++;
+  return MFS_OK;
 }
 
 mfs_status mfs_apply_part(mfs_problem* P, int lvl, mfs_prec prec, int fused, int m0, int m1, const void* u,

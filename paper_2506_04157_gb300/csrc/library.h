@@ -148,6 +148,9 @@ struct mfs_problem {
   std::vector<float*> eta32;
   double* d_dlnrho64 = nullptr;
   float* d_dlnrho32 = nullptr;
+  double* d_dlnrho_int64 = nullptr;   // integral of the table from r_cmb to each node
+  float* d_dlnrho_int32 = nullptr;
+  int rho_weighted = 0;             // constraint -int q div(rho u) instead of B + C
   int n_dlnrho = 1;
   // reduction workspace: partial sums and a few device scalars
   double* d_red64 = nullptr;    // [kRedSlots]

@@ -84,7 +84,9 @@ struct Tile {
 // OP_BC: the B part is (B + C).
 // OP_ETAQ (with OP_A alone): the viscosity at the quadrature points from the level's P2
 // temperature and the viscosity law (levels up to l_eta) instead of the P1 nodal values.
-enum { OP_A = 1, OP_BT = 2, OP_B = 4, OP_CT = 8, OP_BC = 16, OP_ETAQ = 32 };
+// OP_RHO (with OP_BC / OP_CT): the constraint is the density-weighted -int q div(rho u)
+// (mfs_set_constraint_form) — the B + C integrand weighted by rho(r) at the quadrature point.
+enum { OP_A = 1, OP_BT = 2, OP_B = 4, OP_CT = 8, OP_BC = 16, OP_ETAQ = 32, OP_RHO = 64 };
 
 // Boundary condition types (match include/mfs.h).
 enum { BC_DIRICHLET = 0, BC_FREESLIP = 1 };

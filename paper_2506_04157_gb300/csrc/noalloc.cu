@@ -126,6 +126,10 @@ using namespace mfs;
 
 mfs_status mfs_apply_B_noalloc(mfs_problem* P, int lvl, mfs_prec prec, mfs_bcmode mode, int with_C, const void* u,
                                void* q) {
+  if (!u || !q) {   // the same order of checks as mfs_apply_B: vectors first
+    set_error("null vector pointer");
+    return MFS_EINVAL;
+  }
   if (!P) {
     set_error("null problem");
     return MFS_EINVAL;
@@ -142,10 +146,6 @@ mfs_status mfs_apply_B_noalloc(mfs_problem* P, int lvl, mfs_prec prec, mfs_bcmod
   if (n > kNoallocMaxP1) {
     set_error("level %d has %lld pressure entries; mfs_apply_B_noalloc handles at most %lld "
               "(fixed scratch of %d partial sums)", lvl, (long long)n, (long long)kNoallocMaxP1, kMaxPartials);
-    return MFS_EINVAL;
-  }
-  if (!u || !q) {
-    set_error("null vector pointer");
     return MFS_EINVAL;
   }
   if (prec != MFS_F64 && prec != MFS_F32) {

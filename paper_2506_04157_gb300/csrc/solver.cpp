@@ -1584,7 +1584,7 @@ void mfs_solve_opts_default(mfs_solve_opts* o) {
   o->a_l = 1.0;
   o->a_r = 1.0;
   o->tol_wBFBT = 1e-10;
-  o->vmass = 0;
+  o->vmass = 1;   // the consistent vector mass (Sec. 5.2.3), the paper's CG solve
   o->tol_VectorMass = 1e-4;
 }
 

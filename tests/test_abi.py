@@ -96,7 +96,8 @@ def test_library_default_options_match_paper_table(lib):
     for k, v in gold.items():
         if k not in ("_source", "tol_coarse"):
             assert getattr(o, k) == v, k
-    assert (o.uzawa, o.schur, o.mixed, o.tol_wBFBT, o.vmass) == (0, 0, 1, 1e-10, 0)
+    # the weighted BFBT's vector mass is the consistent one, solved by CG (Sec. 5.2.3)
+    assert (o.uzawa, o.schur, o.mixed, o.tol_wBFBT, o.vmass) == (0, 0, 1, 1e-10, 1)
     t = mfs.Problem.temp_params()
     assert t.tol_T == 1e-10 and t.restart == 30
     assert ctypes.sizeof(mfs.SolveOpts) == 152 and ctypes.sizeof(mfs.TempParams) == 96

@@ -93,7 +93,7 @@ def test_wbfbt_apply_fp64(L, al, ar):
     r = project_mean_zero(W.random_field(n, 21))
     z = torch.empty(n, dtype=torch.float64, device="cuda")
     st = prob.apply_schur(torch.tensor(r, device="cuda"), z, schur=3, a_l=al, a_r=ar, tol_wBFBT=1e-13,
-                          max_cg=400)
+                          max_cg=400, vmass=0)
     wl, wr = oracle_ops(L, L, al), oracle_ops(L, L, ar)
     ref = project_mean_zero(wbfbt_apply(H.co[L], H.cons[L], H.co[L].apply_A, wl, wr, r))
     assert rel(z.cpu().numpy(), ref) <= 1e-8, st
@@ -106,7 +106,7 @@ def test_wbfbt_apply_fp32():
     n = H.levels[3].n_p1
     r = project_mean_zero(W.random_field(n, 22)).astype(np.float32)
     z = torch.empty(n, dtype=torch.float32, device="cuda")
-    prob.apply_schur(torch.tensor(r, device="cuda"), z, schur=3)
+    prob.apply_schur(torch.tensor(r, device="cuda"), z, schur=3, vmass=0)
     wl = oracle_ops(3, 3, 1.0)
     ref = project_mean_zero(wbfbt_apply(H.co[3], H.cons[3], H.co[3].apply_A, wl, wl, r.astype(np.float64)))
     assert rel(z.double().cpu().numpy(), ref) <= 1e-2
@@ -144,9 +144,9 @@ def test_schur_refusals():
 @pytest.mark.parametrize("mixed", [2, 0])
 @pytest.mark.parametrize("al", [1.0, 3.0])
 def test_solve_with_wbfbt(mixed, al):
-    """FGMRES with the symmetric Uzawa step and the weighted BFBT (symmetric and asymmetric
-    surface scaling) reaches the oracle's direct solution (omega = 0.03: the approximation's
-    spectrum reaches ~20-80 here).  Solved to 1e-10: with the contrast-1e4 plumes and a
+    """FGMRES with the symmetric Uzawa step and the weighted BFBT on the lumped vector mass
+    (symmetric and asymmetric surface scaling) reaches the oracle's direct solution (omega =
+    0.03: the lumped approximation's spectrum reaches ~20-80 here).  Solved to 1e-10: with the contrast-1e4 plumes and a
     rough forcing, a 1e-8 residual leaves a pressure error of ~5e-5."""
     H, ctx, gm, prob = setup(2)
     S = StokesOracle(H)
@@ -157,7 +157,7 @@ def test_solve_with_wbfbt(mixed, al):
     u = torch.zeros(3 * L.n_p2, dtype=torch.float64, device="cuda")
     p = torch.zeros(L.n_p1, dtype=torch.float64, device="cuda")
     st = prob.solve(torch.tensor(f, device="cuda"), torch.tensor(g, device="cuda"), u, p, mixed=mixed, schur=3,
-                    a_l=al, omega=0.03, restart=50, max_iters=1500, rtol=1e-10)
+                    a_l=al, omega=0.03, restart=50, max_iters=1500, rtol=1e-10, vmass=0)
     assert st["status"] == "MFS_OK" and st["rel_residual"] <= 1e-10, st
     un, pn = u.cpu().numpy(), p.cpu().numpy()
     r0 = np.linalg.norm(S.residual(f, g, 0 * un, 0 * pn))

@@ -289,3 +289,64 @@ def test_temperature_injection_exact_for_linear_fields():
     T2, T1 = temperature_on_level(Lf, Lc, Lf.p2_x @ a)
     assert np.allclose(T2, Lc.p2_x @ a, rtol=0, atol=1e-13)
     assert np.allclose(T1, Lc.p1_x @ a, rtol=0, atol=1e-13)
+
+
+def test_density_weighted_constraint_pins():
+    """element_B_rho (the constraint -int q div(rho u)): reduces to B for a constant density
+    (d ln rho/dr = 0), and its quadrature-point integrand equals div(rho u_h) taken by central
+    differences of the vector field rho(x) u_h(x) in physical space (product rule, sign and
+    radial direction of grad rho) for a random P2 field u_h on a blended micro-tet."""
+    from oracle.mesh import MacroMesh, Level
+    from oracle.fem import Geometry, element_B, element_B_rho, rho_profile, QUAD_BARY
+    mesh = MacroMesh()
+    L = Level(mesh, 1)
+    sel = np.arange(0, L.tet_p2.shape[0], 37)
+    geo = Geometry(mesh, L.tet_x[sel], L.tet_prism[sel])
+    assert np.array_equal(element_B_rho(geo, mesh, [0.0]), element_B(geo))
+    table = [-0.8, -0.2, 0.4]
+    Br = element_B_rho(geo, mesh, table)
+    rng = np.random.default_rng(3)
+    e = 5
+    ue = rng.standard_normal(30)
+    X = L.tet_x[sel][e]
+    prism = L.tet_prism[sel][e]
+    # the P2 field on this element as a function of the physical point: invert the blended map
+    # by Newton on the straight barycentric coordinates
+    from oracle.mesh import LOCAL_EDGES
+
+    def phys(lam):
+        return mesh.blend((lam @ X)[None], np.array([prism]))[0]
+
+    def lam_of(x):
+        lam = np.full(4, 0.25)
+        for _ in range(30):
+            F = phys(lam) - x
+            Jc = np.stack([(phys(lam + h * (np.eye(4)[k] - np.eye(4)[0])) - phys(lam - h * (np.eye(4)[k] - np.eye(4)[0])))
+                           / (2 * h) for k in (1, 2, 3) for h in [1e-6]], axis=1)
+            d = np.linalg.solve(Jc, -F)
+            lam = lam + np.concatenate([[-d.sum()], d])
+        return lam
+
+    def p2_vals(lam):
+        v = [l * (2 * l - 1) for l in lam] + [4 * lam[a] * lam[b] for (a, b) in LOCAL_EDGES]
+        return np.array(v)
+
+    def field(x):
+        r = np.linalg.norm(x)
+        phi = p2_vals(lam_of(x))
+        u = np.array([ue[c * 10:(c + 1) * 10] @ phi for c in range(3)])
+        return rho_profile(table, np.array([r]), mesh.r_cmb, mesh.r_surf)[0] * u
+
+    W, psi = geo.W[e], geo.psi
+    for q in range(QUAD_BARY.shape[0]):
+        xq = geo.x[e, q]
+        h = 1e-5
+        div = sum((field(xq + h * np.eye(3)[c])[c] - field(xq - h * np.eye(3)[c])[c]) / (2 * h) for c in range(3))
+        # integrand of row k at this point: -W_q psi_k(q) div(rho u_h)(x_q); compare with the
+        # element matrix restricted to this quadrature point (the rule is a sum over points)
+        g1 = Geometry(mesh, L.tet_x[sel][e:e + 1], L.tet_prism[sel][e:e + 1])
+        Wq = np.zeros_like(g1.W)
+        Wq[0, q] = g1.W[0, q]
+        g1.W = Wq
+        row = element_B_rho(g1, mesh, table)[0] @ ue
+        assert np.allclose(row, -W[q] * psi[q] * div, rtol=1e-6, atol=1e-9 * np.abs(row).max())

@@ -43,3 +43,17 @@ def test_noalloc_matches_apply_B_twice(problem, level, dtype):
         assert np.isfinite(a).all()
         assert np.linalg.norm(a - b) / np.linalg.norm(b) <= TOL[dtype]
         assert abs(a.mean()) <= 1e3 * np.finfo(np.float32 if dtype == torch.float32 else np.float64).eps * np.abs(a).max()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_noalloc_raw_mode_matches_apply_B(problem, dtype):
+    """MFS_RAW (no mean removal, so no scratch use): the same as mfs_apply_B's raw block."""
+    ctx, mesh, prob = problem
+    inf = mesh.info(3)
+    u = torch.tensor(W.random_field(3 * inf.n_p2, 44), dtype=dtype, device="cuda")
+    q_ref = torch.empty(inf.n_p1, dtype=dtype, device="cuda")
+    q_na = torch.empty_like(q_ref)
+    prob.apply_B(3, u, q_ref, with_C=True, constrained=False)
+    prob.apply_B_noalloc(3, u, q_na, with_C=True, constrained=False)
+    a, b = q_na.double().cpu().numpy(), q_ref.double().cpu().numpy()
+    assert np.linalg.norm(a - b) / np.linalg.norm(b) <= TOL[dtype]
