@@ -37,8 +37,9 @@ WORKLOADS = {
 # dram__bytes_read.sum + dram__bytes_write.sum of one fused FP32 launch of the default sweep
 # variant, per level, from ncu captures of _one launch_ (profiles/ names the command); None
 # where no capture of the current kernel exists
-MEASURED_DRAM_BYTES = {6: 765440768 + 242512640, 5: 100032000 + 9126144}
-DEFAULT_KERNEL = "stokes_tile_kernel_fixed<float, A|BT|B|C, blended, 192 threads, 3 CTAs/SM>"
+MEASURED_DRAM_BYTES = {6: 765305344 + 241406208, 5: 99991552 + 7762688}
+DRAM_PROFILE = "profiles/stokes_tile_kernel_fixed_x2_f32_fused_dram.md"
+DEFAULT_KERNEL = "stokes_tile_kernel_fixed_x2<float, A|BT|B|C, blended, 128 threads, 4 CTAs/SM>"
 
 
 def fused_stokes_flops_per_tet():
@@ -329,7 +330,7 @@ def roofline(level, inf, kern_ms, fp64_ms, peaks):
     return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
             "frac": round(achieved / peak, 4), "traffic": traffic,
             "traffic_source": f"ncu dram__bytes_read.sum + dram__bytes_write.sum of one level-{level} launch "
-                              f"(profiles/stokes_tile_kernel_fixed_f32_fused_dram.md)" if traffic is not None else None,
+                              f"({DRAM_PROFILE})" if traffic is not None else None,
             "kernel": DEFAULT_KERNEL, "kernel_ms": round(kern_ms, 5), "flops_per_launch": flops,
             "flops_per_tet": fused_stokes_flops_per_tet(),
             "algorithmic_bytes": bytes32, "algorithmic_GB_s": round(bytes32 / (kern_ms * 1e-3) / 1e9, 1),
@@ -360,7 +361,7 @@ def run_ours(args, rank, world, device):
                    "density": "compressible, d ln rho/dr = -0.3781",
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": f"{ab['nsets']} rotating input sets of {ab['bytes_per_set'] / 2**20:.1f} MiB (> L2)",
-                   "sweep_variant": 6},
+                   "sweep_variant": prob.get_tuning(level)},
         "roofline": roofline(level, inf, ab["kernel_ms"], ab["fp64_kernel_ms"], peaks),
         "e2e": e2e,
         "gpu_launches": int(args.steps * 6),   # per apply: 2 (p sum) + 1 sweep + 2 (q sum) + 1 (mean removal)

@@ -551,12 +551,14 @@ mfs_status mfs_apply_part(mfs_problem* prob, int lvl, mfs_prec prec, int fused, 
                           const void* p, void* yu, void* yp);
 
 /* ---------------------------------------------------------------- autotuning (not in the paper)
- * The FP32 hot sweeps (fused saddle-point apply and A alone) have 7 launch variants per mesh
+ * The FP32 hot sweeps (fused saddle-point apply and A alone) have 9 launch variants per mesh
  * level: 0 = shared-memory element body with float atomics, 192 threads, 4 resident CTAs
  * per SM; 1 = the same with 3 CTAs per SM; 2-6 = register-resident element body with
  * fixed-point (int32) accumulation of each tile in rounds with their own power-of-two
- * scales, with (threads, CTAs per SM) = (192, 2), (128, 3), (128, 4), (256, 2), (192, 3).
- * Variant 6 is the default of every level.  All compute the same operator (rounding order and the fixed-point rounding
+ * scales, with (threads, CTAs per SM) = (192, 2), (128, 3), (128, 4), (256, 2), (192, 3);
+ * 7-8 = the fixed-point body with the four quadrature points processed in two packed FP32
+ * pairs (fma/add/mul.f32x2), (192, 3) and (128, 4).  Variant 8 is the default of every
+ * level.  All compute the same operator (rounding order and the fixed-point rounding
  * aside).  mfs_autotune times every variant on every level of the problem's mesh with CUDA
  * events and keeps the fastest for all later applies on that mesh.  cache_path (may be
  * NULL): a text file read first (levels found there are not timed) and written with the
@@ -565,7 +567,7 @@ mfs_status mfs_apply_part(mfs_problem* prob, int lvl, mfs_prec prec, int fused, 
 mfs_status mfs_autotune(mfs_problem* prob, const char* cache_path);
 /* The variant in use on a level. */
 mfs_status mfs_get_tuning(const mfs_problem* prob, int lvl, int* variant);
-/* Select the variant of a level by hand (0 <= variant < 7); it applies to every problem on
+/* Select the variant of a level by hand (0 <= variant < 9); it applies to every problem on
  * the mesh.  Errors: MFS_EINVAL. */
 mfs_status mfs_set_tuning(mfs_problem* prob, int lvl, int variant);
 

@@ -497,8 +497,14 @@ class Problem:
 
     # ---- autotuning
     def set_tuning(self, level, variant):
-        """Select the sweep launch variant of a level by hand (0..4, see include/mfs.h)."""
+        """Select the sweep launch variant of a level by hand (0..8, see include/mfs.h)."""
         _check(lib().mfs_set_tuning(self.handle, level, variant))
+
+    def get_tuning(self, level):
+        """The sweep launch variant in use on a level."""
+        v = ctypes.c_int()
+        _check(lib().mfs_get_tuning(self.handle, level, ctypes.byref(v)))
+        return v.value
 
     def autotune(self, cache_path=None):
         """Pick the fastest sweep variant per level (cached in cache_path if given)."""

@@ -492,6 +492,308 @@ __device__ __forceinline__ void tet_element(const ApplyParams<T>& P, const Macro
   }
 }
 
+// ---- packed FP32 pairs (sm_100+ fma.rn.f32x2 / add / mul): two quadrature points per op ----
+__device__ __forceinline__ float2 bc2(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// One micro-tet of the FP32 register-resident sweep with the quadrature points processed in
+// pairs (0, 1) and (2, 3): every per-point quantity is a float2 holding the two points, and
+// the per-point algebra runs on packed FP32 instructions (one instruction, two points).  Same
+// arithmetic, outputs and node order as tet_element.
+template <int OP, bool BLEND>
+__device__ __forceinline__ void tet_element_x2(const ApplyParams<float>& P, const MacroGeom<float>& G, const int code,
+                                               const int a0, const int b0, const int c0, const float* us,
+                                               const float* eta_s, const float* p_s, const float* cM,
+                                               const float* cJn, const float (&v0)[3], const float (&Jn)[9],
+                                               const float (&csum)[3], const float (&nh)[3], const float* dtab,
+                                               float (&yv)[3][10], float (&ypv)[4]) {
+  using T = float;
+  constexpr bool HAS_U = (OP & (OP_A | OP_B)) != 0;
+  constexpr bool HAS_P = (OP & OP_BT) != 0;
+  constexpr bool OUT_U = (OP & (OP_A | OP_BT)) != 0;
+  constexpr bool OUT_P = (OP & OP_B) != 0;
+  constexpr bool HAS_CT = (OP & OP_CT) != 0;
+  constexpr bool HAS_BC = (OP & OP_BC) != 0;
+  constexpr bool NEED_GR = (OUT_P && HAS_BC) || HAS_CT;
+  constexpr bool RHO = (OP & OP_RHO) != 0;
+  const T QA = T(MFS_QA), QB = T(MFS_QB);
+  const T dd = QA - QB;
+  const T dq = T(4) * dd;
+  const T bq1 = T(4) * QB - T(1);
+  const T b4 = T(4) * QB;
+  const T fvb = QB * (T(2) * QB - T(1)), fva = QA * (T(2) * QA - T(1));
+  const T feo = T(4) * QB * QB, fei = T(4) * QA * QB;
+  const int n = P.n;
+  const T C0 = G.absdet / (T(24) * T(n) * T(n) * T(n));
+  const T dinv = T(1) / G.delta;
+  const int ci = code & 15, cj = (code >> 4) & 15, ck = (code >> 8) & 15, pmu = code >> 12;
+  const int p0 = perm_at(pmu, 0), p1 = perm_at(pmu, 1), p2 = perm_at(pmu, 2);
+  const int base = ci + 5 * cj + 25 * ck;
+
+  T u[3][10];
+  if (HAS_U) {
+#pragma unroll
+    for (int a = 0; a < 10; ++a) {
+      const int sa = base + slot_off(pmu, a);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) u[c][a] = us[c * NSLOT2 + sa];
+    }
+  }
+  T ev[4], pv[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    ev[a] = eta_s[base + slot_off(pmu, a)];
+    pv[a] = HAS_P ? p_s[base + slot_off(pmu, a)] : T(0);
+  }
+  const T eta_sum = ev[0] + ev[1] + ev[2] + ev[3];
+  const T p_sum = pv[0] + pv[1] + pv[2] + pv[3];
+
+  T Mp[3][3], cp[3][3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    Mp[0][d] = cM[3 * p0 + d];
+    Mp[1][d] = cM[3 * p1 + d];
+    Mp[2][d] = cM[3 * p2 + d];
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    cp[0][r] = cJn[3 * r + p0];
+    cp[1][r] = cJn[3 * r + p1];
+    cp[2][r] = csum[r] - cp[0][r] - cp[1][r];
+  }
+  // positions of the four quadrature points: cube corner + beta (3 e_p0 + 2 e_p1 + e_p2), then
+  // (alpha - beta) e_p0, e_p1, e_p2 added in turn
+  const T qx = T(a0 + ci), qy = T(b0 + cj), qz = T(c0 + ck);
+  T xs[4][3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    xs[0][r] = v0[r] + Jn[3 * r] * qx + Jn[3 * r + 1] * qy + Jn[3 * r + 2] * qz +
+               QB * (T(3) * cp[0][r] + T(2) * cp[1][r] + cp[2][r]);
+    xs[1][r] = xs[0][r] + dd * cp[0][r];
+    xs[2][r] = xs[1][r] + dd * cp[1][r];
+    xs[3][r] = xs[2][r] + dd * cp[2][r];
+  }
+
+  // qp-independent parts of the lattice gradient: dbase_j = base_{j+1} - base_j
+  T dbase[3][3], U0[3];
+  if (HAS_U) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T bs0 = bq1 * u[c][0] + b4 * (u[c][4] + u[c][5] + u[c][6]);
+      const T bs1 = bq1 * u[c][1] + b4 * (u[c][4] + u[c][7] + u[c][8]);
+      const T bs2 = bq1 * u[c][2] + b4 * (u[c][5] + u[c][7] + u[c][9]);
+      const T bs3 = bq1 * u[c][3] + b4 * (u[c][6] + u[c][8] + u[c][9]);
+      dbase[0][c] = bs1 - bs0;
+      dbase[1][c] = bs2 - bs1;
+      dbase[2][c] = bs3 - bs2;
+      if (HAS_BC)
+        U0[c] = fvb * (u[c][0] + u[c][1] + u[c][2] + u[c][3]) +
+                feo * (u[c][4] + u[c][5] + u[c][6] + u[c][7] + u[c][8] + u[c][9]);
+    }
+  }
+
+  float2 Rs[3][3], Zs[3];
+  T Vq[4][3], Ea[6][3], bq[4];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    Zs[c] = bc2(0.f);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Rs[c][j] = bc2(0.f);
+#pragma unroll
+    for (int e = 0; e < 6; ++e) Ea[e][c] = T(0);
+  }
+
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int qa = 2 * k, qb = 2 * k + 1;
+    float2 x[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) x[r] = make_float2(xs[qa][r], xs[qb][r]);
+    const float2 r2 = fma2(x[2], x[2], fma2(x[1], x[1], mul2(x[0], x[0])));
+    const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    float2 K[3][3];
+    float2 hr = bc2(1.f), h = bc2(0.f);
+    if (BLEND) {
+      h = fma2(x[2], bc2(nh[2]), fma2(x[1], bc2(nh[1]), mul2(x[0], bc2(nh[0]))));
+      const float2 hinv = make_float2(__frcp_rn(h.x), __frcp_rn(h.y));
+      hr = mul2(mul2(h, rinv), bc2(dinv));
+      const float2 nri2 = mul2(rinv, make_float2(-rinv.x, -rinv.y));   // -1/|x|^2
+      float2 v[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) v[d] = fma2(x[d], nri2, mul2(bc2(nh[d]), hinv));
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const float2 tj = fma2(bc2(Mp[j][2]), x[2], fma2(bc2(Mp[j][1]), x[1], mul2(bc2(Mp[j][0]), x[0])));
+        const float2 ntj = make_float2(-tj.x, -tj.y);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) K[j][d] = fma2(ntj, v[d], bc2(Mp[j][d]));
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) K[j][d] = bc2(Mp[j][d]);
+    }
+    const float2 coefB = mul2(mul2(bc2(C0), hr), hr);
+    const float2 Wq = mul2(coefB, hr);
+
+    float2 trace = bc2(0.f), Gp[3][3], wsum[3], wq[3];
+    if (HAS_U) {
+      float2 D[3][3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float2 w[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) w[a] = make_float2(u[c][wnode(a, qa)], u[c][wnode(a, qb)]);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) D[j][c] = fma2(bc2(dq), sub2(w[j + 1], w[j]), bc2(dbase[j][c]));
+        wq[c] = make_float2(u[c][qa], u[c][qb]);
+        wsum[c] = sub2(add2(add2(w[0], w[1]), add2(w[2], w[3])), wq[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) Gp[c][d] = fma2(D[2][c], K[2][d], fma2(D[1][c], K[1][d], mul2(D[0][c], K[0][d])));
+      trace = add2(add2(Gp[0][0], Gp[1][1]), Gp[2][2]);
+    }
+
+    float2 gr = bc2(0.f);
+    if (NEED_GR) {
+      if (P.n_dlnrho <= 1) {
+        gr = bc2(dtab[0]);
+      } else {
+        const T top = T(P.n_dlnrho - 1);
+        T gg[2];
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+          const T rad = BLEND ? (l ? h.y : h.x) * dinv : (l ? r2.y * rinv.y : r2.x * rinv.x);
+          T sg = (rad - P.r_cmb) * P.inv_dr * top;
+          sg = sg < T(0) ? T(0) : (sg > top ? top : sg);
+          int ig = (int)sg;
+          ig = ig > P.n_dlnrho - 2 ? P.n_dlnrho - 2 : ig;
+          const T fg = sg - T(ig);
+          gg[l] = (ig + 1 < 64) ? (T(1) - fg) * dtab[ig] + fg * dtab[ig + 1]
+                                : (T(1) - fg) * P.dlnrho[ig] + fg * P.dlnrho[ig + 1];
+        }
+        gr = make_float2(gg[0], gg[1]);
+      }
+    }
+    float2 rq = bc2(1.f);
+    if (RHO) {
+      rq = make_float2(rho_bar<T>(P, BLEND ? h.x * dinv : r2.x * rinv.x),
+                       rho_bar<T>(P, BLEND ? h.y * dinv : r2.y * rinv.y));
+    }
+
+    if (OUT_P) {
+      float2 b = mul2(coefB, trace);
+      if (HAS_BC) {
+        float2 eu = bc2(0.f);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          eu = fma2(fma2(bc2(fei - feo), wsum[c], fma2(bc2(fva - fvb), wq[c], bc2(U0[c]))), x[c], eu);
+        b = fma2(mul2(mul2(Wq, gr), rinv), eu, b);
+        if (RHO) b = mul2(b, rq);
+      }
+      bq[qa] = b.x;
+      bq[qb] = b.y;
+    }
+
+    if (OUT_U) {
+      float2 S[3][3];
+      if (OP & OP_A) {
+        const float2 etaq = fma2(bc2(dd), make_float2(ev[qa], ev[qb]), bc2(QB * eta_sum));
+        const float2 coefA = mul2(mul2(bc2(2.f * C0), etaq), hr);
+        const float2 hA = mul2(bc2(0.5f), coefA);
+        const float2 nt3 = mul2(trace, bc2(-1.0f / 3.0f));
+        S[0][0] = mul2(coefA, add2(Gp[0][0], nt3));
+        S[1][1] = mul2(coefA, add2(Gp[1][1], nt3));
+        S[2][2] = mul2(coefA, add2(Gp[2][2], nt3));
+        S[0][1] = S[1][0] = mul2(hA, add2(Gp[0][1], Gp[1][0]));
+        S[0][2] = S[2][0] = mul2(hA, add2(Gp[0][2], Gp[2][0]));
+        S[1][2] = S[2][1] = mul2(hA, add2(Gp[1][2], Gp[2][1]));
+      } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) S[c][d] = bc2(0.f);
+      }
+      float2 pq = bc2(0.f);
+      if (HAS_P) {
+        pq = fma2(bc2(dd), make_float2(pv[qa], pv[qb]), bc2(QB * p_sum));
+        if (RHO && HAS_CT) pq = mul2(pq, rq);   // the transposed density-weighted constraint
+        const float2 sp = mul2(coefB, pq);
+        S[0][0] = sub2(S[0][0], sp);
+        S[1][1] = sub2(S[1][1], sp);
+        S[2][2] = sub2(S[2][2], sp);
+      }
+      float2 zq[3] = {bc2(0.f), bc2(0.f), bc2(0.f)};
+      if (HAS_CT) {
+        const float2 zc = mul2(mul2(mul2(Wq, pq), gr), make_float2(-rinv.x, -rinv.y));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          zq[c] = mul2(zc, x[c]);
+          Zs[c] = add2(Zs[c], zq[c]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float2 r0 = fma2(S[c][2], K[0][2], fma2(S[c][1], K[0][1], mul2(S[c][0], K[0][0])));
+        const float2 r1 = fma2(S[c][2], K[1][2], fma2(S[c][1], K[1][1], mul2(S[c][0], K[1][0])));
+        const float2 r2c = fma2(S[c][2], K[2][2], fma2(S[c][1], K[2][1], mul2(S[c][0], K[2][0])));
+        Rs[c][0] = add2(Rs[c][0], r0);
+        Rs[c][1] = add2(Rs[c][1], r1);
+        Rs[c][2] = add2(Rs[c][2], r2c);
+        float2 sv[4];
+        sv[0] = make_float2(-r0.x, -r0.y);
+        sv[1] = sub2(r0, r1);
+        sv[2] = sub2(r1, r2c);
+        sv[3] = r2c;
+        Vq[qa][c] = dq * sv[qa].x + (HAS_CT ? (fva - fvb) * zq[c].x : T(0));
+        Vq[qb][c] = dq * sv[qb].y + (HAS_CT ? (fva - fvb) * zq[c].y : T(0));
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          if (a != qa) Ea[edge_of(a, qa)][c] += sv[a].x + (HAS_CT ? ((fei - feo) / dq) * zq[c].x : T(0));
+          if (a != qb) Ea[edge_of(a, qb)][c] += sv[a].y + (HAS_CT ? ((fei - feo) / dq) * zq[c].y : T(0));
+        }
+      }
+    }
+  }  // pairs
+
+  if (OUT_U) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T R0 = Rs[c][0].x + Rs[c][0].y, R1 = Rs[c][1].x + Rs[c][1].y, R2 = Rs[c][2].x + Rs[c][2].y;
+      const T Z = Zs[c].x + Zs[c].y;
+      T Tacc[4];
+      Tacc[0] = -R0;
+      Tacc[1] = R0 - R1;
+      Tacc[2] = R1 - R2;
+      Tacc[3] = R2;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        yv[c][a] = bq1 * Tacc[a] + Vq[a][c];
+        if (HAS_CT) yv[c][a] += fvb * Z;
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = a + 1; b < 4; ++b) {
+          T val = b4 * (Tacc[a] + Tacc[b]) + dq * Ea[edge_of(a, b)][c];
+          if (HAS_CT) val += feo * Z;
+          yv[c][4 + edge_of(a, b)] = val;
+        }
+    }
+  }
+  if (OUT_P) {
+    const T sb = bq[0] + bq[1] + bq[2] + bq[3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) ypv[a] = -(QB * sb + dd * bq[a]);
+  }
+}
+
 // CTA-uniform geometry of the register-resident sweep, held in registers
 template <typename T>
 __device__ __forceinline__ void tile_uniforms(const T* cJn, const T* cv0, const T* cnh, T (&v0)[3], T (&Jn)[9],
@@ -569,7 +871,7 @@ __device__ __forceinline__ void red_shared_s32(int* addr, int v) {
   asm volatile("red.shared.add.s32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(addr)), "r"(v) : "memory");
 }
 
-template <int OP, bool BLEND, int NT, int NR>
+template <int OP, bool BLEND, int NT, int NR, bool PAIR>
 __device__ __forceinline__ void tet_sweep_fixed(const ApplyParams<float>& P, const MacroGeom<float>& G, const Tile tile,
                                                 const float* us, int* ysi, const float* eta_s, const float* p_s,
                                                 int* ypi, const float* cM, const float* cJn, const float* cv0,
@@ -588,7 +890,10 @@ __device__ __forceinline__ void tet_sweep_fixed(const ApplyParams<float>& P, con
     int code = 0;
     if (active) {
       code = P.tets[cinfo.x + t];
-      tet_element<float, OP, BLEND>(P, G, code, a0, b0, c0, us, eta_s, p_s, cM, cJn, v0, Jn, csum, nh, dtab, yv, ypv);
+      if constexpr (PAIR)
+        tet_element_x2<OP, BLEND>(P, G, code, a0, b0, c0, us, eta_s, p_s, cM, cJn, v0, Jn, csum, nh, dtab, yv, ypv);
+      else
+        tet_element<float, OP, BLEND>(P, G, code, a0, b0, c0, us, eta_s, p_s, cM, cJn, v0, Jn, csum, nh, dtab, yv, ypv);
     } else {
 #pragma unroll
       for (int c = 0; c < 3; ++c)
@@ -648,7 +953,8 @@ __device__ __forceinline__ void tet_sweep_fixed(const ApplyParams<float>& P, con
 
 // BODY 0: shared-memory element body (float atomics, also inside the quadrature loop);
 // BODY 1: register-resident element body with float atomics; BODY 2: register-resident body
-// with fixed-point accumulation in NR rounds (FP32 only).
+// with fixed-point accumulation in NR rounds (FP32 only); BODY 3: BODY 2 with the quadrature
+// points processed in packed FP32 pairs (tet_element_x2).
 template <typename T, int OP, bool BLEND, int BODY = 0, int NT = kSweepThreads, int NR = 1>
 __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m, const int tidx, const int n_tiles) {
   constexpr bool HAS_U = (OP & (OP_A | OP_B)) != 0;
@@ -659,9 +965,9 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
   constexpr bool HAS_BC = (OP & OP_BC) != 0;
   constexpr bool ETAQ = (OP & OP_ETAQ) != 0;
   static_assert(!ETAQ || OP == (OP_A | OP_ETAQ), "the quadrature-point viscosity serves A alone");
-  static_assert(BODY != 2 || (sizeof(T) == 4 && !ETAQ && NR >= 1 && NR <= kFixedMaxRounds && NR * NT >= 384),
+  static_assert(BODY < 2 || (sizeof(T) == 4 && !ETAQ && NR >= 1 && NR <= kFixedMaxRounds && NR * NT >= 384),
                 "the fixed-point body is FP32, without quadrature-point viscosity, and covers a full tile");
-  constexpr int NCOPY = BODY == 2 ? NR : 1;
+  constexpr int NCOPY = BODY >= 2 ? NR : 1;
 
   // dynamic shared memory, layout of sweep_smem_bytes(): us, ys, eta_s, p_s, yp_s, ts, gid2, gid1
   // (BODY 2: ys and yp_s hold NR int32 copies)
@@ -686,7 +992,7 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
   const int n = P.n, N = 2 * n;
   const int tid = threadIdx.x;
 
-  if (BODY == 2 && tid < 2 * kFixedMaxRounds) rmax[tid] = 0u;
+  if (BODY >= 2 && tid < 2 * kFixedMaxRounds) rmax[tid] = 0u;
   if (tid < 9) {
     cM[tid] = T(n) * G.Jinv[tid];
     cJn[tid] = G.Jm[tid] / T(n);
@@ -695,7 +1001,7 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
     cv0[tid] = G.v0[tid];
     cnh[tid] = G.nh[tid];
   }
-  if (tid < 72) {
+  if (BODY == 0 && tid < 72) {
     // lattice offset of qp q of type pm: beta (3 e_p0 + 2 e_p1 + e_p2) + (alpha - beta) S_q
     const int pm = tid / 12, q = (tid / 3) % 4, r = tid % 3;
     const int p0 = perm_at(pm, 0), p1 = perm_at(pm, 1), p2 = perm_at(pm, 2);
@@ -713,16 +1019,26 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
   __shared__ T lbt[64];   // ETAQ: ln eta_base table (first 64 entries)
   if (ETAQ && tid < 64 && tid < P.n_lbase) lbt[tid] = T(2.302585092994045684) * P.lbase[tid];
 
-  // ---- stage the P2 node block (u, with the input-side projections) ----
-  // All table entries of this thread first, then all node values: independent loads in flight.
+  // ---- stage the P2 node block (u, with the input-side projections) and the P1 vertex
+  // block (eta, p) ----
+  // All table entries of this thread (both blocks) first, then all node values: the loads of
+  // each kind are independent and in flight together (two memory latencies per tile).
   constexpr int kG = (NSLOT2 + NT - 1) / NT;
+  constexpr int kG1 = (NSLOT1 + NT - 1) / NT;
   const int* tab2 = P.ids2 + tile_lin * NSLOT2;
-  int codes[kG];
+  const int* tab1 = P.ids1 + tile_lin * NSLOT1;
+  int codes[kG], ids1v[kG1];
 #pragma unroll
   for (int k = 0; k < kG; ++k) {
     const int s = tid + k * NT;
     codes[k] = s < NSLOT2 ? __ldg(tab2 + s) : -1;
   }
+#pragma unroll
+  for (int k = 0; k < kG1; ++k) {
+    const int s = tid + k * NT;
+    ids1v[k] = s < NSLOT1 ? __ldg(tab1 + s) : -1;
+  }
+  const T psum = (HAS_P && P.psum) ? *P.psum : T(0);
   T uv[kG][3];
 #pragma unroll
   for (int k = 0; k < kG; ++k) {
@@ -732,6 +1048,16 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
       uv[k][0] = __ldg(P.u + id);
       uv[k][1] = __ldg(P.u + P.n_p2 + id);
       uv[k][2] = __ldg(P.u + 2 * P.n_p2 + id);
+    }
+  }
+  T ev1[kG1], pv1[kG1];
+#pragma unroll
+  for (int k = 0; k < kG1; ++k) {
+    ev1[k] = T(1);
+    pv1[k] = T(0);
+    if (ids1v[k] >= 0) {
+      ev1[k] = __ldg(P.eta + ids1v[k]);
+      if (HAS_P) pv1[k] = __ldg(P.p + ids1v[k]);
     }
   }
   if (ETAQ) {
@@ -769,37 +1095,31 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
       us[NSLOT2 + s] = v1;
       us[2 * NSLOT2 + s] = v2;
     }
-    if (OUT_U) {
-#pragma unroll
-      for (int r = 0; r < NCOPY; ++r) {
-        ys[r * 3 * NSLOT2 + s] = T(0);
-        ys[r * 3 * NSLOT2 + NSLOT2 + s] = T(0);
-        ys[r * 3 * NSLOT2 + 2 * NSLOT2 + s] = T(0);
-      }
-    }
   }
-  // ---- stage the P1 vertex block (eta, p) ----
-  const int* tab1 = P.ids1 + tile_lin * NSLOT1;
-  const T pm = (HAS_P && P.psum) ? *P.psum / T(P.n_p1) : T(0);
-  for (int s = tid; s < NSLOT1; s += NT) {
-    const int id = tab1[s];
-    T e = T(1), pv = T(0);
-    if (id >= 0) {
-      e = P.eta[id];
-      if (HAS_P) pv = P.p[id] - pm;
-    }
-    eta_s[s] = e;
-    if (HAS_P) p_s[s] = pv;
+  if (OUT_U) {   // zero the output block(s), 16 bytes per store
+    static_assert((3 * NSLOT2 * sizeof(T)) % 16 == 0 && ((HAS_U ? 3 * NSLOT2 : 0) * sizeof(T)) % 16 == 0,
+                  "the output block is 16-byte aligned and sized");
+    constexpr int n4 = NCOPY * 3 * NSLOT2 * (int)sizeof(T) / 16;
+    int4* y4 = reinterpret_cast<int4*>(ys);
+    for (int i = tid; i < n4; i += NT) y4[i] = make_int4(0, 0, 0, 0);
+  }
+  const T pm = psum / T(P.n_p1);
+#pragma unroll
+  for (int k = 0; k < kG1; ++k) {
+    const int s = tid + k * NT;
+    if (s >= NSLOT1) break;
+    eta_s[s] = ev1[k];
+    if (HAS_P) p_s[s] = ids1v[k] >= 0 ? pv1[k] - pm : T(0);
     if (OUT_P) {
 #pragma unroll
       for (int r = 0; r < NCOPY; ++r) yp_s[r * NSLOT1 + s] = T(0);
-      gid1[s] = id;
+      gid1[s] = ids1v[k];
     }
   }
   __syncthreads();
 
-  if constexpr (BODY == 2) {
-    tet_sweep_fixed<OP, BLEND, NT, NR>(P, G, tile, us, reinterpret_cast<int*>(ys), eta_s, p_s,
+  if constexpr (BODY >= 2) {
+    tet_sweep_fixed<OP, BLEND, NT, NR, BODY == 3>(P, G, tile, us, reinterpret_cast<int*>(ys), eta_s, p_s,
                                        reinterpret_cast<int*>(yp_s), cM, cJn, cv0, cnh, dtab, rmax, tid);
   } else if constexpr (BODY == 1) {
     tet_sweep_regs<T, OP, BLEND, NT>(P, G, tile, us, ys, eta_s, p_s, yp_s, cM, cJn, cv0, cnh, dtab, tid);
@@ -1112,6 +1432,17 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
   __syncthreads();
 
   // ---- add the block to the global result (output-side projections) ----
+  // fixed-point bodies: 2^-k_r of each round (NaN for a marked round)
+  T inv_u[NR], inv_p[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    inv_u[r] = inv_p[r] = T(0);
+    if constexpr (BODY >= 2) {
+      const int ku = fixed_scale_exp(rmax[2 * r]), kp = fixed_scale_exp(rmax[2 * r + 1]);
+      inv_u[r] = ku == 255 ? T(__int_as_float(0x7fc00000)) : T(exp2_int(-ku));
+      inv_p[r] = kp == 255 ? T(__int_as_float(0x7fc00000)) : T(exp2_int(-kp));
+    }
+  }
   if (OUT_U) {
     const int nn = P.n_p2;
     for (int s = tid; s < NSLOT2; s += NT) {
@@ -1134,13 +1465,12 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
         continue;
       }
       T v0, v1, v2;
-      if constexpr (BODY == 2) {
+      if constexpr (BODY >= 2) {
         const int* yi = reinterpret_cast<const int*>(ys);
         v0 = v1 = v2 = T(0);
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
-          const int k = fixed_scale_exp(rmax[2 * r]);
-          const T inv = k == 255 ? T(__int_as_float(0x7fc00000)) : T(exp2_int(-k));
+          const T inv = inv_u[r];
           v0 += T(yi[r * 3 * NSLOT2 + s]) * inv;
           v1 += T(yi[r * 3 * NSLOT2 + NSLOT2 + s]) * inv;
           v2 += T(yi[r * 3 * NSLOT2 + 2 * NSLOT2 + s]) * inv;
@@ -1170,13 +1500,10 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
       const int id = gid1[s];
       if (id < 0) continue;
       T v = T(0);
-      if constexpr (BODY == 2) {
+      if constexpr (BODY >= 2) {
         const int* yi = reinterpret_cast<const int*>(yp_s);
 #pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          const int k = fixed_scale_exp(rmax[2 * r + 1]);
-          v += T(yi[r * NSLOT1 + s]) * (k == 255 ? T(__int_as_float(0x7fc00000)) : T(exp2_int(-k)));
-        }
+        for (int r = 0; r < NR; ++r) v += T(yi[r * NSLOT1 + s]) * inv_p[r];
       } else {
         v = yp_s[s];
       }
@@ -1200,6 +1527,11 @@ __global__ void __launch_bounds__(NT, MINB) stokes_tile_kernel_regs(const ApplyP
 template <typename T, int OP, bool BLEND, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) stokes_tile_kernel_fixed(const ApplyParams<T> P) {
   sweep_tile<T, OP, BLEND, 2, NT, (384 + NT - 1) / NT>(P, P.m0 + blockIdx.y, blockIdx.x, gridDim.x);
+}
+// the same with the packed-pair element body
+template <typename T, int OP, bool BLEND, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) stokes_tile_kernel_fixed_x2(const ApplyParams<T> P) {
+  sweep_tile<T, OP, BLEND, 3, NT, (384 + NT - 1) / NT>(P, P.m0 + blockIdx.y, blockIdx.x, gridDim.x);
 }
 // the same sweep compiled for one fewer resident CTA per SM (more registers per thread);
 // the autotuner picks between the two per level

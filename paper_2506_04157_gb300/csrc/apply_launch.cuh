@@ -55,15 +55,23 @@ inline cudaError_t smem_opt_in(const void* func, size_t smem) {
 //   4: the same, 128 threads, 4 CTAs per SM (128 registers)
 //   5: the same, 256 threads, 2 CTAs per SM (128 registers)
 //   6: the same, 192 threads, 3 CTAs per SM (96 registers)
+//   7: variant 6 with the packed-pair element body (two quadrature points per FP32x2 op)
+//   8: variant 4 with the packed-pair element body
+// the operator sets whose FP32 sweeps are tunable (run_sweep passes variant 0 for the rest)
+template <typename T, int OP>
+constexpr bool kTunable = sizeof(T) == 4 && (OP == OP_A || OP == (OP_A | OP_BT | OP_B | OP_BC));
+
 template <typename T, int OP, bool BLEND>
 static void (*sweep_kernel(int variant, int* nt, size_t* smem))(const ApplyParams<T>) {
-  if constexpr (sizeof(T) == 4 && (OP & OP_ETAQ) == 0) {
+  if constexpr (kTunable<T, OP>) {
     switch (variant) {
       case 2: *nt = 192; *smem = sweep_smem_bytes<T, OP, 2>(); return stokes_tile_kernel_fixed<T, OP, BLEND, 192, 2>;
       case 3: *nt = 128; *smem = sweep_smem_bytes<T, OP, 3>(); return stokes_tile_kernel_fixed<T, OP, BLEND, 128, 3>;
       case 4: *nt = 128; *smem = sweep_smem_bytes<T, OP, 3>(); return stokes_tile_kernel_fixed<T, OP, BLEND, 128, 4>;
       case 5: *nt = 256; *smem = sweep_smem_bytes<T, OP, 2>(); return stokes_tile_kernel_fixed<T, OP, BLEND, 256, 2>;
       case 6: *nt = 192; *smem = sweep_smem_bytes<T, OP, 2>(); return stokes_tile_kernel_fixed<T, OP, BLEND, 192, 3>;
+      case 7: *nt = 192; *smem = sweep_smem_bytes<T, OP, 2>(); return stokes_tile_kernel_fixed_x2<T, OP, BLEND, 192, 3>;
+      case 8: *nt = 128; *smem = sweep_smem_bytes<T, OP, 3>(); return stokes_tile_kernel_fixed_x2<T, OP, BLEND, 128, 4>;
       default: break;
     }
   }
@@ -91,8 +99,7 @@ static mfs_status run_sweep_v(const ApplyParams<T>& prm, int n_tiles, mfs_ctx* c
 template <typename T, int OP>
 static mfs_status run_sweep(const ApplyParams<T>& prm, int n_tiles, int blending, mfs_ctx* ctx, int variant,
                            int n_macros) {
-  constexpr bool tunable = sizeof(T) == 4 && (OP == OP_A || OP == (OP_A | OP_BT | OP_B | OP_BC));
-  if constexpr (tunable) {
+  if constexpr (kTunable<T, OP>) {
     if (variant > 0 && variant < kSweepVariants)
       return blending ? run_sweep_v<T, OP, true>(prm, n_tiles, ctx, variant, n_macros)
                       : run_sweep_v<T, OP, false>(prm, n_tiles, ctx, variant, n_macros);

@@ -57,10 +57,10 @@ HostTiles build_tiles(int n);
 
 // launch variants of the FP32 hot sweeps (element body, threads per CTA, resident CTAs per
 // SM), chosen per level by mfs_autotune; apply_launch.cuh lists them.  The default is the
-// fastest on the GB300 at levels 5 and 6: the register-resident body with fixed-point
-// accumulation, 192 threads, 3 CTAs per SM.
-constexpr int kSweepVariants = 7;
-constexpr int kDefaultSweepVariant = 6;
+// fastest on the GB300 at levels 5 and 6: the register-resident body with the quadrature
+// points in packed FP32 pairs and fixed-point accumulation, 128 threads, 4 CTAs per SM.
+constexpr int kSweepVariants = 9;
+constexpr int kDefaultSweepVariant = 8;
 
 struct LevelData {
   int l = 0, n = 1;

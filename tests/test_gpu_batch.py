@@ -89,7 +89,7 @@ def test_autotune_keeps_results(ensemble, tmp_path):
     P.apply_stokes(L, u, p, y0u, y0p)
     cache = str(tmp_path / "tune.json")
     choice = P.autotune(cache)
-    assert all(0 <= v < 7 for v in choice) and len(choice) == L + 1
+    assert all(0 <= v < 9 for v in choice) and len(choice) == L + 1
     rows = json.load(open(cache))
     assert [r["variant"] for r in rows] == choice
     assert P.autotune(cache) == choice          # read back from the cache
