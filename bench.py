@@ -406,7 +406,68 @@ def run_ours(args, rank, world, device):
     line["clocks"] = clk.summary()
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(level, budget_s=args.cpu_seconds)
+    if world == 1 and args.solve and not args.no_ensemble:
+        line["ensemble"] = ensemble_bench(device, sequential=args.ensemble)
     return line
+
+
+def ensemble_bench(device, n_members=64, n_streams=8, sequential=False):
+    """The ensemble workload: n_members shells with refinement levels drawn from {3, 4, 5},
+    log-uniform viscosity contrast in [1e4, 1e6] (plumes, seeds 100 + i), compressible
+    density, buoyancy forcing from a seeded temperature field per member; FP32 applies in FP64
+    refinement (mixed = 1) to 1e-8, at most 1000 FGMRES iterations.  Time to solve all members (wall clock, device synchronized
+    before and after): one member after another (one host thread) and concurrently
+    (mfs_solve_concurrent, one host thread per stream), from zero initial guesses each time.
+    The one-after-another run only when `sequential`."""
+    import numpy as np
+    import torch
+    import workloads as W
+    import paper_2506_04157_gb300 as mfs
+    dev = f"cuda:{device}"
+    rng = np.random.default_rng(3)
+    levels = rng.integers(3, 6, size=n_members)
+    contrasts = 10.0 ** rng.uniform(4.0, 6.0, size=n_members)
+    ens = mfs.Ensemble(levels, n_streams=n_streams, device=device)
+    fs, gs = [], []
+    t0 = time.perf_counter()
+    for i, (l, c) in enumerate(zip(levels, contrasts)):
+        l = int(l)
+        P = ens.problems[i]
+        x1 = P.mesh.coords(l, p2=False).T
+        P.set_viscosity(torch.tensor(W.viscosity_plumes(x1, 100 + i, float(c)), device=dev))
+        P.set_density(W.dlnrho_table_compressible())
+        P.setup_multigrid(1)
+        T = torch.tensor(W.temperature_blobs(P.mesh.coords(l).T, 500 + i), device=dev)
+        f = torch.empty(3 * T.numel(), dtype=torch.float64, device=dev)
+        P.rhs_buoyancy(T, f, scale=1.0)
+        fs.append(f)
+        gs.append(torch.zeros(P._sizes(l)[1], dtype=torch.float64, device=dev))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    out = {"members": n_members, "levels": {str(l): int((levels == l).sum()) for l in (3, 4, 5)},
+           "dofs": int(sum(sum(P._sizes(int(l))) for P, l in zip(ens.problems, levels))),
+           "streams": n_streams, "mixed": 1, "setup_s": round(setup_s, 3)}
+    runs = (("sequential", 1), ("concurrent", 0)) if sequential else (("concurrent", 0),)
+    for name, nt in runs:
+        us = [torch.zeros_like(f) for f in fs]
+        ps = [torch.zeros_like(g) for g in gs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        stats = ens.solve(fs, gs, us, ps, n_threads=nt, raise_on_error=False, mixed=1, max_iters=1000)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        its = [st["fgmres_iters"] for st in stats]
+        out[name] = {"time_to_solve_s": round(dt, 3), "threads": 1 if nt == 1 else min(n_streams, n_members),
+                     "fgmres_iters_min_max": [int(min(its)), int(max(its))],
+                     "converged": int(sum(st["rel_residual"] <= 1e-8 for st in stats)),
+                     "max_rel_residual_fp64": max(st["rel_residual"] for st in stats)}
+    if sequential:
+        out["speedup"] = round(out["sequential"]["time_to_solve_s"] / out["concurrent"]["time_to_solve_s"], 3)
+    out["note"] = ("each member's solve reaches 1e-8 measured in FP64; the concurrent run overlaps the "
+                   "members of different streams (mfs_solve_concurrent)")
+    del ens
+    torch.cuda.empty_cache()
+    return out
 
 
 def buoyancy_forcing(mesh, prob, level, dev):
@@ -687,6 +748,9 @@ def main():
     ap.add_argument("--solve-reps", type=int, default=3, help="level-5 mixed-precision solves (median reported)")
     ap.add_argument("--compare-preconditioners", action="store_true",
                     help="only the Uzawa x Schur comparison of the solver on the --level workload")
+    ap.add_argument("--ensemble", action="store_true",
+                    help="the 64-member ensemble (levels 3-5) also solved one member after another")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-member ensemble solve")
     ap.add_argument("--profile-solve", action="store_true",
                     help="profiler window only (cudaProfilerStart/Stop): one V-cycle (3,2), one V-cycle "
                          "(1,1) and a solve capped at one FGMRES iteration, for ncu --profile-from-start off")

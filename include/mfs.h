@@ -521,6 +521,23 @@ mfs_status mfs_batch_apply_stokes(mfs_batch* batch, mfs_prec prec, int transpose
 mfs_status mfs_batch_solve(mfs_batch* batch, const mfs_solve_opts* opts, const double* const* f,
                            const double* const* g, double* const* u, double* const* p, mfs_solve_stats* stats);
 
+/* Concurrent solve of n independent problems (not in the paper): mfs_stokes_solve for every
+ * member, with the members of DIFFERENT contexts running at the same time.  The members are
+ * grouped by the context of their mesh; one host thread works through a group member after
+ * member on that context's stream, and up to n_threads groups (0: one thread per group) run
+ * concurrently, so that the small kernels and host round trips of low-level members overlap
+ * on the device.  Members of one context never run concurrently; two contexts must not share
+ * a stream.  The call synchronizes each device it uses before the first solve (inputs written
+ * on other streams are complete) and returns after every solve has finished.  f, g, u, p:
+ * HOST arrays of n FP64 device pointers as in mfs_stokes_solve (each member needs
+ * mfs_setup_multigrid); stats: n entries or NULL.  Returns MFS_OK when every member
+ * converged, MFS_ENOTCONV when some did not (the other members' results are valid), else the
+ * first member's error; mfs_last_error names the member.  Errors: MFS_EINVAL (null arrays,
+ * negative n or n_threads, contexts sharing a stream), as mfs_stokes_solve. */
+mfs_status mfs_solve_concurrent(int n, mfs_problem* const* probs, const mfs_solve_opts* opts, const double* const* f,
+                                const double* const* g, double* const* u, double* const* p, mfs_solve_stats* stats,
+                                int n_threads);
+
 /* ---------------------------------------------------------------- sharding by macro-tets
  * The hybrid hierarchical grid of paper Sec. 4.1 splits naturally by macro-tets: every
  * micro-tet, and so every element contribution, belongs to exactly one macro; nodes on macro

@@ -129,6 +129,7 @@ _SIGS = {
     "mfs_batch_destroy": ([_vp], _i),
     "mfs_batch_apply_stokes": ([_vp, _i, _i, _vp, _vp, _vp, _vp], _i),
     "mfs_batch_solve": ([_vp, ctypes.POINTER(SolveOpts), _vp, _vp, _vp, _vp, _vp], _i),
+    "mfs_solve_concurrent": ([_i, _vp, ctypes.POINTER(SolveOpts), _vp, _vp, _vp, _vp, _vp, _i], _i),
     "mfs_stokes_solve": ([_vp, ctypes.POINTER(SolveOpts), _vp, _vp, _vp, _vp, ctypes.POINTER(SolveStats)], _i),
     "mfs_apply_schur": ([_vp, ctypes.POINTER(SolveOpts), _i, _vp, _vp, ctypes.POINTER(SolveStats)], _i),
     "mfs_apply_poisson": ([_vp, _i, _i, _d, _vp, _vp], _i),
@@ -705,3 +706,57 @@ class Batch:
         if getattr(self, "handle", None) and _lib is not None:
             _lib.mfs_batch_destroy(self.handle)
             self.handle = None
+
+
+def solve_concurrent(problems, fs, gs, us, ps, n_threads=0, raise_on_error=True, **opts):
+    """mfs_stokes_solve for every problem, the problems of different contexts (streams) at the
+    same time (mfs_solve_concurrent): one host thread per context works through its problems
+    in turn.  fs, gs, us, ps: FP64 device tensors per problem (us, ps: initial guesses, solved
+    in place).  Returns the statistics per problem (dicts with 'status')."""
+    import torch
+    probs = list(problems)
+    for P, f, g, u, p in zip(probs, fs, gs, us, ps):
+        nu, npp = P._sizes(P.mesh.l_max)
+        _need(f, nu, torch.float64, "f"); _need(g, npp, torch.float64, "g")
+        _need(u, nu, torch.float64, "u"); _need(p, npp, torch.float64, "p")
+    if not (len(probs) == len(fs) == len(gs) == len(us) == len(ps)):
+        raise MfsError(EINVAL, "one right-hand side and one solution per problem")
+    o = Problem.default_opts(**opts)
+    stats = (SolveStats * max(len(probs), 1))()
+    arr = (ctypes.c_void_p * max(len(probs), 1))(*[P.handle.value for P in probs])
+    rc = lib().mfs_solve_concurrent(len(probs), arr, ctypes.byref(o), _ptr_array(fs), _ptr_array(gs),
+                                    _ptr_array(us), _ptr_array(ps), stats, int(n_threads))
+    if rc not in (OK, ENOTCONV) or (rc != OK and raise_on_error):
+        raise MfsError(rc, lib().mfs_last_error().decode())
+    out = [stats[i].as_dict() for i in range(len(probs))]
+    return out
+
+
+class Ensemble:
+    """Independent Stokes problems (levels may differ) spread over n_streams CUDA streams of one
+    device, for mfs_solve_concurrent: one context and one mesh per (stream, level); members
+    are placed largest first on the stream with the least work so far (work ~ 8^level)."""
+
+    def __init__(self, levels, n_streams=8, device=0):
+        import torch
+        self.levels = [int(l) for l in levels]
+        n_streams = max(1, min(int(n_streams), len(self.levels)))
+        self.streams = [torch.cuda.Stream(device) for _ in range(n_streams)]
+        self.ctxs = [Context(device, s.cuda_stream) for s in self.streams]
+        load = [0] * n_streams
+        self.stream_of = [0] * len(self.levels)
+        for i in sorted(range(len(self.levels)), key=lambda i: -self.levels[i]):
+            k = min(range(n_streams), key=lambda k: load[k])
+            self.stream_of[i] = k
+            load[k] += 8 ** self.levels[i]
+        self.meshes = {}
+        self.problems = []
+        for i, l in enumerate(self.levels):
+            key = (self.stream_of[i], l)
+            if key not in self.meshes:
+                self.meshes[key] = Mesh(self.ctxs[key[0]], l)
+            self.problems.append(Problem(self.meshes[key]))
+
+    def solve(self, fs, gs, us, ps, n_threads=0, raise_on_error=True, **opts):
+        return solve_concurrent(self.problems, fs, gs, us, ps, n_threads=n_threads,
+                                raise_on_error=raise_on_error, **opts)

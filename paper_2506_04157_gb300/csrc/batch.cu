@@ -1,8 +1,13 @@
 // Ensembles of problems (possibly of different refinement levels): the constrained fused
 // saddle-point apply of every instance in one sweep launch, with batched zeroing and
-// pressure mean removal; and a batch solve over the instances.
+// pressure mean removal; a batch solve over the instances; and a concurrent solve of
+// problems on several contexts (streams), one host thread per context.
+#include <atomic>
 #include <cstring>
 #include <new>
+#include <string>
+#include <system_error>
+#include <thread>
 #include <vector>
 
 #include "apply.cuh"
@@ -321,6 +326,101 @@ mfs_status mfs_batch_solve(mfs_batch* B, const mfs_solve_opts* opts, const doubl
     if (stats) stats[b] = st;
     if (rc != MFS_OK && worst == MFS_OK) worst = rc;
     if (rc != MFS_OK && rc != MFS_ENOTCONV) return rc;
+  }
+  return worst;
+}
+
+// Concurrent solve: the problems are grouped by context; one host thread works through a
+// group, member after member, on that context's stream, and up to n_threads groups run at the
+// same time, so that the many small kernels and host round trips of low-level members of
+// different groups overlap on the device.  A worker's errors are recorded per member and the
+// first one is reported on the calling thread (the error text is per thread).
+mfs_status mfs_solve_concurrent(int n, mfs_problem* const* probs, const mfs_solve_opts* opts, const double* const* f,
+                                const double* const* g, double* const* u, double* const* p, mfs_solve_stats* stats,
+                                int n_threads) {
+  if (n < 0 || (n > 0 && (!probs || !opts || !f || !g || !u || !p)) || n_threads < 0) {
+    set_error("invalid arguments: n >= 0, n_threads >= 0 and non-null arrays");
+    return MFS_EINVAL;
+  }
+  std::vector<mfs_ctx*> ctxs;
+  std::vector<std::vector<int>> groups;
+  for (int b = 0; b < n; ++b) {
+    if (!probs[b] || !probs[b]->mesh || !probs[b]->mesh->ctx || !f[b] || !g[b] || !u[b] || !p[b]) {
+      set_error("null problem or vector for member %d", b);
+      return MFS_EINVAL;
+    }
+    mfs_ctx* c = probs[b]->mesh->ctx;
+    size_t k = 0;
+    while (k < ctxs.size() && ctxs[k] != c) ++k;
+    if (k == ctxs.size()) {
+      for (mfs_ctx* o : ctxs)
+        if (o->stream == c->stream && o->device == c->device) {
+          set_error("two contexts of the members share one stream: the members would not run concurrently");
+          return MFS_EINVAL;
+        }
+      ctxs.push_back(c);
+      groups.emplace_back();
+    }
+    groups[k].push_back(b);
+  }
+  if (n == 0) return MFS_OK;
+  // inputs written on other streams are complete before any member starts
+  {
+    int cur = 0;
+    MFS_CUDA(cudaGetDevice(&cur));
+    std::vector<int> devs;
+    for (mfs_ctx* c : ctxs) {
+      bool seen = false;
+      for (int d : devs) seen = seen || d == c->device;
+      if (seen) continue;
+      devs.push_back(c->device);
+      MFS_CUDA(cudaSetDevice(c->device));
+      MFS_CUDA(cudaDeviceSynchronize());
+    }
+    MFS_CUDA(cudaSetDevice(cur));
+  }
+  std::vector<mfs_status> rc(n, MFS_OK);
+  std::vector<std::string> msg(n);
+  std::vector<mfs_solve_stats> st(n);
+  std::atomic<int> next{0};
+  const int ngroups = (int)groups.size();
+  auto worker = [&]() {
+    for (int k = next++; k < ngroups; k = next++) {
+      const cudaError_t e = cudaSetDevice(ctxs[k]->device);
+      for (int b : groups[k]) {
+        std::memset(&st[b], 0, sizeof(mfs_solve_stats));
+        if (e != cudaSuccess) {
+          rc[b] = MFS_ECUDA;
+          msg[b] = cudaGetErrorString(e);
+          continue;
+        }
+        rc[b] = mfs_stokes_solve(probs[b], opts, f[b], g[b], u[b], p[b], &st[b]);
+        if (rc[b] != MFS_OK) msg[b] = mfs_last_error();
+      }
+    }
+  };
+  const int nt = n_threads > 0 && n_threads < ngroups ? n_threads : ngroups;
+  std::vector<std::thread> pool;
+  try {
+    for (int t = 1; t < nt; ++t) pool.emplace_back(worker);
+  } catch (const std::system_error&) {
+    // fewer threads than asked: the ones running (and this one) take the remaining groups
+  }
+  worker();
+  for (auto& t : pool) t.join();
+  if (stats)
+    for (int b = 0; b < n; ++b) stats[b] = st[b];
+  mfs_status worst = MFS_OK;
+  for (int b = 0; b < n; ++b) {
+    if (rc[b] == MFS_OK) continue;
+    if (rc[b] != MFS_ENOTCONV) {
+      set_error("member %d: %s", b, msg[b].c_str());
+      return rc[b];
+    }
+    if (worst == MFS_OK) {
+      worst = MFS_ENOTCONV;
+      set_error("member %d: %s", b, msg[b].c_str());
+    }
   }
   return worst;
 }

@@ -61,6 +61,18 @@ def test_errors_without_gpu_or_bad_args(lib):
                        ("mfs_temperature_step", (null, None, null, null, null, null, 0.1, 0.1, null, null, None))]:
         assert getattr(L, name)(*args) == 1, name
         assert L.mfs_last_error(), name
+    # the concurrent solve: an empty ensemble is a no-op; a negative count, a negative thread
+    # count or null arrays are refused before any device work
+    opts = mfs.SolveOpts()
+    L.mfs_solve_opts_default(ctypes.byref(opts))
+    assert L.mfs_solve_concurrent(0, null, ctypes.byref(opts), null, null, null, null, null, 0) == 0
+    assert L.mfs_solve_concurrent(-1, null, ctypes.byref(opts), null, null, null, null, null, 0) == 1
+    assert L.mfs_solve_concurrent(0, null, ctypes.byref(opts), null, null, null, null, null, -2) == 1
+    assert L.mfs_solve_concurrent(2, null, ctypes.byref(opts), null, null, null, null, null, 0) == 1
+    assert b"non-null" in L.mfs_last_error()
+    two = (ctypes.c_void_p * 2)(None, None)
+    assert L.mfs_solve_concurrent(2, two, ctypes.byref(opts), two, two, two, two, null, 0) == 1
+    assert b"member 0" in L.mfs_last_error()
 
 
 @pytest.mark.parametrize("blending", [True, False])
