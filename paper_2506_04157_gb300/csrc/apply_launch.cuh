@@ -57,9 +57,15 @@ inline cudaError_t smem_opt_in(const void* func, size_t smem) {
 //   6: the same, 192 threads, 3 CTAs per SM (96 registers)
 //   7: variant 6 with the packed-pair element body (two quadrature points per FP32x2 op)
 //   8: variant 4 with the packed-pair element body
-// the operator sets whose FP32 sweeps are tunable (run_sweep passes variant 0 for the rest)
+// The FP32 sweeps of A alone (smoothers) and of the forward fused operator (Krylov) are
+// tunable over all variants.  The other FP32 operator sets without quadrature-point viscosity
+// (B, B^T, their C and density-weighted forms, the transposed fused operator) run the
+// packed-pair fixed-point body with 128 threads and 4 CTAs per SM whenever the level's variant
+// is a fixed-point one (2-8), else the shared-memory body; FP64 always runs the latter.
 template <typename T, int OP>
 constexpr bool kTunable = sizeof(T) == 4 && (OP == OP_A || OP == (OP_A | OP_BT | OP_B | OP_BC));
+template <typename T, int OP>
+constexpr bool kFixedBody = sizeof(T) == 4 && (OP & OP_ETAQ) == 0;
 
 template <typename T, int OP, bool BLEND>
 static void (*sweep_kernel(int variant, int* nt, size_t* smem))(const ApplyParams<T>) {
@@ -73,6 +79,12 @@ static void (*sweep_kernel(int variant, int* nt, size_t* smem))(const ApplyParam
       case 7: *nt = 192; *smem = sweep_smem_bytes<T, OP, 2>(); return stokes_tile_kernel_fixed_x2<T, OP, BLEND, 192, 3>;
       case 8: *nt = 128; *smem = sweep_smem_bytes<T, OP, 3>(); return stokes_tile_kernel_fixed_x2<T, OP, BLEND, 128, 4>;
       default: break;
+    }
+  } else if constexpr (kFixedBody<T, OP>) {
+    if (variant >= 2) {
+      *nt = 128;
+      *smem = sweep_smem_bytes<T, OP, 3>();
+      return stokes_tile_kernel_fixed_x2<T, OP, BLEND, 128, 4>;
     }
   }
   *nt = kSweepThreads;
@@ -95,11 +107,11 @@ static mfs_status run_sweep_v(const ApplyParams<T>& prm, int n_tiles, mfs_ctx* c
   return MFS_OK;
 }
 
-// the hot FP32 sweeps (A alone: smoothers; fused forward: Krylov) have tunable variants
+// the level's variant selects the kernel of the FP32 sweeps (see kTunable / kFixedBody)
 template <typename T, int OP>
 static mfs_status run_sweep(const ApplyParams<T>& prm, int n_tiles, int blending, mfs_ctx* ctx, int variant,
                            int n_macros) {
-  if constexpr (kTunable<T, OP>) {
+  if constexpr (kTunable<T, OP> || kFixedBody<T, OP>) {
     if (variant > 0 && variant < kSweepVariants)
       return blending ? run_sweep_v<T, OP, true>(prm, n_tiles, ctx, variant, n_macros)
                       : run_sweep_v<T, OP, false>(prm, n_tiles, ctx, variant, n_macros);
