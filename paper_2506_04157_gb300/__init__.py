@@ -732,23 +732,33 @@ def solve_concurrent(problems, fs, gs, us, ps, n_threads=0, raise_on_error=True,
     return out
 
 
+def place_members(levels, n_streams):
+    """Stream of each ensemble member: members taken largest first (work ~ 8^level, the
+    micro-tet count), each onto the stream with the least work so far (ties: the lowest
+    stream).  Returns (stream index per member, work per stream)."""
+    levels = [int(l) for l in levels]
+    n_streams = max(1, min(int(n_streams), max(len(levels), 1)))
+    load = [0] * n_streams
+    stream_of = [0] * len(levels)
+    for i in sorted(range(len(levels)), key=lambda i: (-levels[i], i)):
+        k = min(range(n_streams), key=lambda k: (load[k], k))
+        stream_of[i] = k
+        load[k] += 8 ** levels[i]
+    return stream_of, load
+
+
 class Ensemble:
     """Independent Stokes problems (levels may differ) spread over n_streams CUDA streams of one
-    device, for mfs_solve_concurrent: one context and one mesh per (stream, level); members
-    are placed largest first on the stream with the least work so far (work ~ 8^level)."""
+    device, for mfs_solve_concurrent: one context and one mesh per (stream, level), members
+    placed by place_members."""
 
     def __init__(self, levels, n_streams=8, device=0):
         import torch
         self.levels = [int(l) for l in levels]
-        n_streams = max(1, min(int(n_streams), len(self.levels)))
+        self.stream_of, _ = place_members(self.levels, n_streams)
+        n_streams = max(self.stream_of) + 1 if self.levels else 1
         self.streams = [torch.cuda.Stream(device) for _ in range(n_streams)]
         self.ctxs = [Context(device, s.cuda_stream) for s in self.streams]
-        load = [0] * n_streams
-        self.stream_of = [0] * len(self.levels)
-        for i in sorted(range(len(self.levels)), key=lambda i: -self.levels[i]):
-            k = min(range(n_streams), key=lambda k: load[k])
-            self.stream_of[i] = k
-            load[k] += 8 ** self.levels[i]
         self.meshes = {}
         self.problems = []
         for i, l in enumerate(self.levels):
