@@ -533,7 +533,8 @@ mfs_status mfs_batch_solve(mfs_batch* batch, const mfs_solve_opts* opts, const d
  * mfs_setup_multigrid); stats: n entries or NULL.  Returns MFS_OK when every member
  * converged, MFS_ENOTCONV when some did not (the other members' results are valid), else the
  * first member's error; mfs_last_error names the member.  Errors: MFS_EINVAL (null arrays,
- * negative n or n_threads, contexts sharing a stream), as mfs_stokes_solve. */
+ * negative n or n_threads, contexts sharing a stream), MFS_ENOMEM (a host exception in a
+ * member's solve, caught in its thread), as mfs_stokes_solve. */
 mfs_status mfs_solve_concurrent(int n, mfs_problem* const* probs, const mfs_solve_opts* opts, const double* const* f,
                                 const double* const* g, double* const* u, double* const* p, mfs_solve_stats* stats,
                                 int n_threads);

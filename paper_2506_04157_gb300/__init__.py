@@ -715,12 +715,12 @@ def solve_concurrent(problems, fs, gs, us, ps, n_threads=0, raise_on_error=True,
     in place).  Returns the statistics per problem (dicts with 'status')."""
     import torch
     probs = list(problems)
+    if not (len(probs) == len(fs) == len(gs) == len(us) == len(ps)):
+        raise MfsError(EINVAL, "one right-hand side and one solution per problem")
     for P, f, g, u, p in zip(probs, fs, gs, us, ps):
         nu, npp = P._sizes(P.mesh.l_max)
         _need(f, nu, torch.float64, "f"); _need(g, npp, torch.float64, "g")
         _need(u, nu, torch.float64, "u"); _need(p, npp, torch.float64, "p")
-    if not (len(probs) == len(fs) == len(gs) == len(us) == len(ps)):
-        raise MfsError(EINVAL, "one right-hand side and one solution per problem")
     o = Problem.default_opts(**opts)
     stats = (SolveStats * max(len(probs), 1))()
     arr = (ctypes.c_void_p * max(len(probs), 1))(*[P.handle.value for P in probs])

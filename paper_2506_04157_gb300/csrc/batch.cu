@@ -4,6 +4,7 @@
 // problems on several contexts (streams), one host thread per context.
 #include <atomic>
 #include <cstring>
+#include <exception>
 #include <new>
 #include <string>
 #include <system_error>
@@ -394,8 +395,16 @@ mfs_status mfs_solve_concurrent(int n, mfs_problem* const* probs, const mfs_solv
           msg[b] = cudaGetErrorString(e);
           continue;
         }
-        rc[b] = mfs_stokes_solve(probs[b], opts, f[b], g[b], u[b], p[b], &st[b]);
-        if (rc[b] != MFS_OK) msg[b] = mfs_last_error();
+        try {   // nothing may escape a worker thread (it would end the process)
+          rc[b] = mfs_stokes_solve(probs[b], opts, f[b], g[b], u[b], p[b], &st[b]);
+          if (rc[b] != MFS_OK) msg[b] = mfs_last_error();
+        } catch (const std::exception& x) {
+          rc[b] = MFS_ENOMEM;
+          msg[b] = std::string("host exception: ") + x.what();
+        } catch (...) {
+          rc[b] = MFS_ENOMEM;
+          msg[b] = "host exception";
+        }
       }
     }
   };
