@@ -409,7 +409,8 @@ def run_ours(args, rank, world, device):
         "e2e": e2e,
         "gpu_launches": int(args.steps * 6),   # per apply: 2 (p sum) + 1 sweep + 2 (q sum) + 1 (mean removal)
         "a_block": {"kernel_ms": round(ab["a_ms"], 5), "gdofs": round(nu / (ab["a_ms"] * 1e-3) / 1e9, 3),
-                    "note": "constrained A sweep alone, N_u per kernel time"},
+                    "note": "constrained A sweep alone (sweep variant 7: packed pairs, 192 threads, "
+                            "3 CTAs/SM), N_u per kernel time"},
         "measured_peaks": peaks,
         "hbm_peak_measured_gbs": read_peaks().get("hbm_gbs"),
     }

@@ -575,15 +575,16 @@ mfs_status mfs_apply_part(mfs_problem* prob, int lvl, mfs_prec prec, int fused, 
  * fixed-point (int32) accumulation of each tile in rounds with their own power-of-two
  * scales, with (threads, CTAs per SM) = (192, 2), (128, 3), (128, 4), (256, 2), (192, 3);
  * 7-8 = the fixed-point body with the four quadrature points processed in two packed FP32
- * pairs (fma/add/mul.f32x2), (192, 3) and (128, 4).  Variant 8 is the default of every
- * level.  All compute the same operator (rounding order and the fixed-point rounding
+ * pairs (fma/add/mul.f32x2), (192, 3) and (128, 4).  By default every level runs variant 8
+ * for the fused apply (and the other operator sets) and variant 7 for A alone; mfs_set_tuning
+ * and mfs_autotune set one variant for both.  All compute the same operator (rounding order and the fixed-point rounding
  * aside).  mfs_autotune times every variant on every level of the problem's mesh with CUDA
  * events and keeps the fastest for all later applies on that mesh.  cache_path (may be
  * NULL): a text file read first (levels found there are not timed) and written with the
  * choices and timings.  Allocates and frees temporary device vectors.
  * Errors: MFS_EINVAL, MFS_ENOMEM, MFS_ECUDA. */
 mfs_status mfs_autotune(mfs_problem* prob, const char* cache_path);
-/* The variant in use on a level. */
+/* The variant in use on a level (of the fused apply; mfs_set_tuning sets both). */
 mfs_status mfs_get_tuning(const mfs_problem* prob, int lvl, int* variant);
 /* Select the variant of a level by hand (0 <= variant < 9); it applies to every problem on
  * the mesh.  Errors: MFS_EINVAL. */

@@ -250,7 +250,7 @@ mfs_status launch_apply(mfs_problem* P, int lvl, int op, int constrained, int wi
   if (P->rho_weighted && (op & (OP_BC | OP_CT))) op |= OP_RHO;
   const int bl = M->host.blending;
   switch (op) {
-    case OP_A: MFS_TRY((run_sweep<T, OP_A>(prm, L.n_tiles, bl, M->ctx, L.variant, nm))); break;
+    case OP_A: MFS_TRY((run_sweep<T, OP_A>(prm, L.n_tiles, bl, M->ctx, L.variant_a, nm))); break;
     case OP_A | OP_ETAQ: MFS_TRY((run_sweep<T, OP_A | OP_ETAQ>(prm, L.n_tiles, bl, M->ctx, 0, nm))); break;
     case OP_BT: MFS_TRY((run_sweep<T, OP_BT>(prm, L.n_tiles, bl, M->ctx, L.variant, nm))); break;
     case OP_BT | OP_CT: MFS_TRY((run_sweep<T, OP_BT | OP_CT>(prm, L.n_tiles, bl, M->ctx, L.variant, nm))); break;

@@ -21,7 +21,7 @@ static mfs_status time_variant(mfs_problem* P, int l, int variant, float* u, flo
                                double* ms_out) {
   mfs_mesh* M = P->mesh;
   cudaStream_t s = M->ctx->stream;
-  M->levels[l].variant = variant;
+  M->levels[l].variant = M->levels[l].variant_a = variant;
   for (int w = 0; w < 2; ++w)
     MFS_TRY(launch_apply<float>(P, l, OP_A | OP_BT | OP_B, 0, 1, u, p, yu, yp, nullptr));
   cudaEvent_t e0, e1;
@@ -90,6 +90,7 @@ mfs_status mfs_autotune(mfs_problem* P, const char* cache_path) {
     cudaFree(yp);
     if (st != MFS_OK) {
       M->levels[l].variant = kDefaultSweepVariant;
+      M->levels[l].variant_a = kDefaultSweepVariantA;
       return st;
     }
     int best = 0;
@@ -98,7 +99,7 @@ mfs_status mfs_autotune(mfs_problem* P, const char* cache_path) {
     chosen[l] = best;
     timed = true;
   }
-  for (int l = 0; l <= L; ++l) M->levels[l].variant = chosen[l];
+  for (int l = 0; l <= L; ++l) M->levels[l].variant = M->levels[l].variant_a = chosen[l];
   M->tuning_gen++;
   if (cache_path && timed) {
     if (FILE* f = std::fopen(cache_path, "w")) {
@@ -129,7 +130,7 @@ mfs_status mfs_set_tuning(mfs_problem* P, int lvl, int variant) {
     set_error("invalid arguments: level outside the mesh or variant outside 0..%d", kSweepVariants - 1);
     return MFS_EINVAL;
   }
-  P->mesh->levels[lvl].variant = variant;
+  P->mesh->levels[lvl].variant = P->mesh->levels[lvl].variant_a = variant;
   P->mesh->tuning_gen++;
   return MFS_OK;
 }

@@ -56,11 +56,15 @@ struct HostTiles {
 HostTiles build_tiles(int n);
 
 // launch variants of the FP32 hot sweeps (element body, threads per CTA, resident CTAs per
-// SM), chosen per level by mfs_autotune; apply_launch.cuh lists them.  The default is the
-// fastest on the GB300 at levels 5 and 6: the register-resident body with the quadrature
-// points in packed FP32 pairs and fixed-point accumulation, 128 threads, 4 CTAs per SM.
+// SM), chosen per level by mfs_autotune; apply_launch.cuh lists them.  The defaults are the
+// fastest on the GB300, both the register-resident body with the quadrature points in packed
+// FP32 pairs and fixed-point accumulation: 128 threads and 4 CTAs per SM for the fused
+// operator (and the other operator sets; fastest at levels 5 and 6), 192 threads and 3 CTAs
+// per SM for A alone (the smoother's operator, which needs fewer registers; fastest on every
+// level).
 constexpr int kSweepVariants = 9;
 constexpr int kDefaultSweepVariant = 8;
+constexpr int kDefaultSweepVariantA = 7;
 
 struct LevelData {
   int l = 0, n = 1;
@@ -78,6 +82,7 @@ struct LevelData {
   double* d_er_w = nullptr;
   int64_t n_tets = 0, n_surface = 0, n_cmb = 0;
   int variant = kDefaultSweepVariant;   // sweep launch variant (mfs_autotune / mfs_set_tuning)
+  int variant_a = kDefaultSweepVariantA;   // the same for the sweep of A alone
   // viscosity law (built on first use): per P1 vertex the finest-level P2 node at the same
   // point and the vertex's radius; per P2 node (levels below the finest) the finest node
   int* d_vfine = nullptr;
