@@ -19,7 +19,7 @@ nodes").  Identity rows of Dirichlet nodes need no exchange: every rank touching
 writes the same value.
 
 The module holds the partition, the exchange, the distributed reductions and the distributed
-operator / Chebyshev / V-cycle orchestration; the arithmetic of every step comes from the
+operator / Chebyshev / V-cycle / preconditioned CG orchestration; the arithmetic of every step comes from the
 callables it is given (the library's kernels on the GPU).  torch.distributed provides the
 all-reduce (NCCL between GPUs, gloo between CPU processes).
 """
@@ -263,6 +263,51 @@ class ShardedVCycle:
         ec = self(l - 1, rc, steps, degree)
         x = x + lv.prolong(ec)
         return self.chebyshev(lv, x, b, steps, degree)
+
+
+class ShardedPCG:
+    """Preconditioned conjugate gradients on the constrained A block of one level (the A-block
+    solve of the Uzawa preconditioner, Sec. 5.2, with the multigrid V-cycle as preconditioner)
+    over macro-sharded levels: A x by the sharded operator (partial sums and the interface
+    exchange), the preconditioner a callable on consistent vectors (by default the sharded
+    V-cycle of the level), and every inner product over the owned entries summed over the
+    ranks (reducer.dot), so that all ranks take the same step lengths and stop at the same
+    iteration.  b and the returned x are full-length and consistent on the touched nodes."""
+
+    def __init__(self, vcycle, level, reducer, steps=3, degree=2, precond=None):
+        self.level_op = vcycle.levels[level]
+        self.red = reducer
+        self.precond = precond if precond is not None else (lambda r: vcycle(level, r, steps, degree))
+
+    def solve(self, b, x=None, rtol=1e-8, max_iters=200, fixed_iters=None):
+        """(x, iterations, residual norms per iteration); stops at ||r|| <= rtol ||r0||, or
+        after exactly fixed_iters iterations when given."""
+        import math
+        import torch
+        A = self.level_op.A
+        x = torch.zeros_like(b) if x is None else x.clone()
+        r = b - A(x)
+        r0 = math.sqrt(self.red.dot(r, r))
+        hist = [r0]
+        if r0 == 0.0:
+            return x, 0, hist
+        z = self.precond(r)
+        p = z.clone()
+        rz = self.red.dot(r, z)
+        n = fixed_iters if fixed_iters is not None else max_iters
+        for it in range(1, n + 1):
+            q = A(p)
+            alpha = rz / self.red.dot(p, q)
+            x = x + alpha * p
+            r = r - alpha * q
+            hist.append(math.sqrt(self.red.dot(r, r)))
+            if fixed_iters is None and hist[-1] <= rtol * r0:
+                return x, it, hist
+            z = self.precond(r)
+            rz_new = self.red.dot(r, z)
+            p = z + (rz_new / rz) * p
+            rz = rz_new
+        return x, n, hist
 
 
 def library_level(prob, level, m0, m1, part, group=None, device=None, bounds=None, exclude_dirichlet=None):

@@ -4,7 +4,8 @@ Each rank owns half of the macro-tets (prism-aligned ranges); its partial operat
 oracle's element sum over the micro-tets of its macros with the constrained arithmetic of
 Sec. 5.1 (P0 on the inputs, P_v on the free-slip outputs, identity rows at the Dirichlet
 nodes it touches), standing in for mfs_apply_part.  The two-rank results of the fused apply,
-the dot products, the mean removal and one V-cycle are checked
+the dot products, the mean removal, one V-cycle and a preconditioned CG on the A block are
+checked
   * bit for bit against a one-process evaluation that groups the same partial sums the same
     way (rank 0's part + rank 1's part on shared nodes, owned fine rows restricted per rank),
   * and against the unsharded oracle (ConstrainedOperators, Hierarchy.vcycle) to 1e-12.
@@ -21,6 +22,7 @@ import torch.multiprocessing as mp
 
 LEVEL = 3
 STEPS, DEGREE = 2, 2
+CG_ITERS = 10
 
 
 def _free_port():
@@ -192,7 +194,10 @@ def _compute(rank, ranges, emulate):
     coarse = lambda bc: torch.from_numpy(H.vcycle(H.l_min, bc.numpy(), STEPS, DEGREE, coarse_exact=True))
     V = shard.ShardedVCycle(levels, H.l_min, coarse)
     x = V(H.l_max, b, STEPS, DEGREE)
-    return dict(yu=yu.numpy(), yp=yp.numpy(), x=x.numpy(), dots=dots,
+    lv = levels[H.l_max]
+    jacobi = lambda r: lv.project(lv.dinv * r)
+    xc, its, hist = shard.ShardedPCG(V, H.l_max, red_u, precond=jacobi).solve(b, fixed_iters=CG_ITERS)
+    return dict(yu=yu.numpy(), yp=yp.numpy(), x=x.numpy(), dots=dots, cg=(xc.numpy(), its, hist),
                 touched2=np.tile(part2.touched, 3), touched1=part1.touched)
 
 
@@ -282,3 +287,27 @@ def test_vcycle_two_ranks(results):
         t2 = got[r]["touched2"]
         assert np.array_equal(got[r]["x"][t2], emu["x"][t2])
         assert np.linalg.norm(got[r]["x"][t2] - ref[t2]) <= 1e-12 * np.linalg.norm(ref[t2])
+
+
+def test_pcg_two_ranks(results):
+    """Preconditioned CG on the constrained A block (Jacobi preconditioner, P0-projected; the
+    V-cycle preconditioner is checked on its own above), 10 iterations: the two ranks take the
+    same steps (residual histories equal, bit for bit against the same grouping in one process)
+    and their iterate equals the oracle's own PCG (Sec. 5.2) to 1e-9."""
+    got, emu, H, dl = results
+    import workloads as W
+    from oracle.solver import cg
+    L = H.levels[H.l_max]
+    cons = H.cons[H.l_max]
+    b = cons.P0(W.random_field(3 * L.n_p2, 5))
+    M = lambda r: cons.P0(r / H.diag[H.l_max])
+    ref, ref_it = cg(H.co[H.l_max].apply_A, b, M=M, fixed_iters=CG_ITERS)
+    assert ref_it == CG_ITERS
+    for r in (0, 1):
+        xc, its, hist = got[r]["cg"]
+        t2 = got[r]["touched2"]
+        assert its == CG_ITERS and hist == emu["cg"][2]
+        assert np.array_equal(xc[t2], emu["cg"][0][t2])
+        assert np.linalg.norm(xc[t2] - ref[t2]) <= 1e-9 * np.linalg.norm(ref[t2])
+        assert hist[-1] < hist[0]
+    assert got[0]["cg"][2] == got[1]["cg"][2]
