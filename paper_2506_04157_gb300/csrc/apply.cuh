@@ -808,38 +808,6 @@ __device__ __forceinline__ void tile_uniforms(const T* cJn, const T* cv0, const 
   }
 }
 
-// Register-resident element body, outputs added to the tile block with shared-memory float
-// atomics (one add per node and component of each micro-tet).
-template <typename T, int OP, bool BLEND, int NT>
-__device__ __forceinline__ void tet_sweep_regs(const ApplyParams<T>& P, const MacroGeom<T>& G, const Tile tile,
-                                               const T* us, T* ys, const T* eta_s, const T* p_s, T* yp_s,
-                                               const T* cM, const T* cJn, const T* cv0, const T* cnh,
-                                               const T* dtab, const int tid) {
-  constexpr bool OUT_U = (OP & (OP_A | OP_BT)) != 0;
-  constexpr bool OUT_P = (OP & OP_B) != 0;
-  T v0[3], Jn[9], csum[3], nh[3];
-  tile_uniforms<T>(cJn, cv0, cnh, v0, Jn, csum, nh);
-  const int a0 = tile.ta * TT, b0 = tile.tb * TT, c0 = tile.tc * TT;
-  const int2 cinfo = P.classes[tile.cls];
-  for (int t = tid; t < cinfo.y; t += NT) {
-    const int code = P.tets[cinfo.x + t];
-    T yv[3][10], ypv[4];
-    tet_element<T, OP, BLEND>(P, G, code, a0, b0, c0, us, eta_s, p_s, cM, cJn, v0, Jn, csum, nh, dtab, yv, ypv);
-    const int pmu = code >> 12;
-    const int base = (code & 15) + 5 * ((code >> 4) & 15) + 25 * ((code >> 8) & 15);
-    if (OUT_U) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int a = 0; a < 10; ++a) atomicAdd(&ys[c * NSLOT2 + base + slot_off(pmu, a)], yv[c][a]);
-    }
-    if (OUT_P) {
-#pragma unroll
-      for (int a = 0; a < 4; ++a) atomicAdd(&yp_s[base + slot_off(pmu, a)], ypv[a]);
-    }
-  }
-}
-
 // Fixed-point accumulation (FP32 sweeps): the micro-tets of a tile are processed in NR rounds
 // of NT; each round has its own int32 copy of the tile block and its own power-of-two scale
 // 2^k_r, chosen after the round's outputs are known so that |output| * 2^k_r < 2^25 for every
@@ -952,9 +920,10 @@ __device__ __forceinline__ void tet_sweep_fixed(const ApplyParams<float>& P, con
 }
 
 // BODY 0: shared-memory element body (float atomics, also inside the quadrature loop);
-// BODY 1: register-resident element body with float atomics; BODY 2: register-resident body
-// with fixed-point accumulation in NR rounds (FP32 only); BODY 3: BODY 2 with the quadrature
-// points processed in packed FP32 pairs (tet_element_x2).
+// BODY 2: register-resident element body (tet_element) with fixed-point accumulation in NR
+// rounds (FP32 only); BODY 3: BODY 2 with the quadrature points processed in packed FP32
+// pairs (tet_element_x2).  (A register-resident body with float atomics, once BODY 1, was
+// slower than BODY 0 and is gone.)
 template <typename T, int OP, bool BLEND, int BODY = 0, int NT = kSweepThreads, int NR = 1>
 __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m, const int tidx, const int n_tiles) {
   constexpr bool HAS_U = (OP & (OP_A | OP_B)) != 0;
@@ -1121,8 +1090,6 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
   if constexpr (BODY >= 2) {
     tet_sweep_fixed<OP, BLEND, NT, NR, BODY == 3>(P, G, tile, us, reinterpret_cast<int*>(ys), eta_s, p_s,
                                        reinterpret_cast<int*>(yp_s), cM, cJn, cv0, cnh, dtab, rmax, tid);
-  } else if constexpr (BODY == 1) {
-    tet_sweep_regs<T, OP, BLEND, NT>(P, G, tile, us, ys, eta_s, p_s, yp_s, cM, cJn, cv0, cnh, dtab, tid);
   } else {
   // ---- element sweep: one thread per micro-tet ----
   const T QA = T(MFS_QA), QB = T(MFS_QB);
@@ -1516,12 +1483,6 @@ __device__ __forceinline__ void sweep_tile(const ApplyParams<T>& P, const int m,
 template <typename T, int OP, bool BLEND>
 __global__ void __launch_bounds__(kSweepThreads, MFS_SWEEP_MINBLOCKS) stokes_tile_kernel(const ApplyParams<T> P) {
   sweep_tile<T, OP, BLEND>(P, P.m0 + blockIdx.y, blockIdx.x, gridDim.x);
-}
-// the register-resident element body (FP32 hot path) with NT threads per CTA and MINB
-// resident CTAs per SM; float atomics
-template <typename T, int OP, bool BLEND, int NT, int MINB>
-__global__ void __launch_bounds__(NT, MINB) stokes_tile_kernel_regs(const ApplyParams<T> P) {
-  sweep_tile<T, OP, BLEND, 1, NT>(P, P.m0 + blockIdx.y, blockIdx.x, gridDim.x);
 }
 // the register-resident element body with fixed-point accumulation in ceil(384 / NT) rounds
 template <typename T, int OP, bool BLEND, int NT, int MINB>
