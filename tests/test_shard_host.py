@@ -150,7 +150,7 @@ class _GroupedReducer:
         return x
 
 
-def _compute(rank, ranges, emulate):
+def _compute(rank, ranges, emulate, full=True):
     import workloads as W
     from paper_2506_04157_gb300 import shard
     H, dl, topo = _setup()
@@ -190,6 +190,9 @@ def _compute(rank, ranges, emulate):
     yu, yp = torch.empty_like(u), torch.empty_like(p)
     op.apply(u, p, yu, yp)
     dots = (red_u.dot(u, yu), red_u.dot(b, b))
+    if not full:
+        return dict(yu=yu.numpy(), yp=yp.numpy(), dots=dots, touched2=np.tile(part2.touched, 3),
+                    touched1=part1.touched)
     levels = _levels(H, dl, topo, ranges, rank, emulate)
     coarse = lambda bc: torch.from_numpy(H.vcycle(H.l_min, bc.numpy(), STEPS, DEGREE, coarse_exact=True))
     V = shard.ShardedVCycle(levels, H.l_min, coarse)
@@ -201,32 +204,36 @@ def _compute(rank, ranges, emulate):
                 touched2=np.tile(part2.touched, 3), touched1=part1.touched)
 
 
-def _worker(rank, world, port, q):
+def _worker(rank, world, port, q, full=True):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         from paper_2506_04157_gb300 import shard
-        out = _compute(rank, shard.macro_ranges(world), emulate=False)
+        out = _compute(rank, shard.macro_ranges(world), emulate=False, full=full)
         q.put((rank, out))
     finally:
         dist.destroy_process_group()
 
 
-@pytest.fixture(scope="module")
-def results():
+def _run_ranks(world, full):
     from paper_2506_04157_gb300 import shard
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q, full)) for r in range(world)]
     for p in procs:
         p.start()
     got = dict(q.get(timeout=600) for _ in procs)
     for p in procs:
         p.join(timeout=60)
-    emu = _compute(0, shard.macro_ranges(2), emulate=True)
+    emu = _compute(0, shard.macro_ranges(world), emulate=True, full=full)
     H, dl, topo = _setup()
     return got, emu, H, dl
+
+
+@pytest.fixture(scope="module")
+def results():
+    return _run_ranks(2, full=True)
 
 
 def test_partition_covers_every_node_once():
@@ -311,3 +318,35 @@ def test_pcg_two_ranks(results):
         assert np.linalg.norm(xc[t2] - ref[t2]) <= 1e-9 * np.linalg.norm(ref[t2])
         assert hist[-1] < hist[0]
     assert got[0]["cg"][2] == got[1]["cg"][2]
+
+
+def test_fused_apply_and_dots_three_ranks():
+    """Three gloo ranks (prism-aligned ranges of 21, 18 and 21 macros): an uneven split and
+    interface points shared by all three ranges.  With three ranks the all-reduce adds the
+    partial sums in an association of its own, so the comparison with the one-process grouping
+    is to rounding (1e-14) rather than bit for bit; every rank holds the same interface sums
+    and the same dot products (bit for bit), and the fused apply equals the unsharded oracle to
+    1e-12 on every rank's touched nodes."""
+    got, emu, H, dl = _run_ranks(3, full=False)
+    import workloads as W
+    co = H.co[H.l_max]
+    L = H.levels[H.l_max]
+    u = W.random_field(3 * L.n_p2, 3)
+    p = W.random_field(L.n_p1, 4)
+    ref_u = co.apply_A(u) + co.apply_BT(p)
+    ref_p = co.apply_Bbar(u)
+    for r in range(3):
+        t2, t1 = got[r]["touched2"], got[r]["touched1"]
+        assert np.linalg.norm(got[r]["yu"][t2] - emu["yu"][t2]) <= 1e-14 * np.linalg.norm(emu["yu"][t2])
+        assert np.linalg.norm(got[r]["yp"][t1] - emu["yp"][t1]) <= 1e-14 * np.linalg.norm(emu["yp"][t1])
+        assert np.linalg.norm(got[r]["yu"][t2] - ref_u[t2]) <= 1e-12 * np.linalg.norm(ref_u[t2])
+        assert np.linalg.norm(got[r]["yp"][t1] - ref_p[t1]) <= 1e-12 * np.linalg.norm(ref_p[t1])
+        for k in (0, 1):
+            assert got[r]["dots"][k] == got[0]["dots"][k]
+            assert abs(got[r]["dots"][k] - emu["dots"][k]) <= 1e-14 * abs(emu["dots"][k])
+        for q in range(3):          # the ranks agree on the points both touch
+            both2 = got[r]["touched2"] & got[q]["touched2"]
+            both1 = got[r]["touched1"] & got[q]["touched1"]
+            assert np.array_equal(got[r]["yu"][both2], got[q]["yu"][both2])
+            assert np.array_equal(got[r]["yp"][both1], got[q]["yp"][both1])
+    assert (got[0]["touched2"] | got[1]["touched2"] | got[2]["touched2"]).all()
