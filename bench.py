@@ -383,6 +383,18 @@ def roofline(level, inf, kern_ms, fp64_ms, peaks):
                      "kernel_ms": round(fp64_ms, 4), "peak_basis": "measured in this run: FP64 FMA-chain kernel"}}
 
 
+def _optional(fn):
+    """Runs an optional part of the bench line (solves, the level-5 lines, the ensemble, the CPU
+    baseline); a failure is reported in its place instead of ending the run before the headline
+    line is printed."""
+    try:
+        return fn()
+    except Exception as e:   # reported, not fatal: the headline stands
+        import traceback
+        traceback.print_exc(file=sys.stderr)
+        return {"error": f"{type(e).__name__}: {e}"}
+
+
 def run_ours(args, rank, world, device):
     import torch
     torch.cuda.set_device(device)
@@ -419,29 +431,34 @@ def run_ours(args, rank, world, device):
         modes = [("mixed_fp64_outer", dict(mixed=2), 2, 1), ("mixed", dict(mixed=1), 1, 0)]
         if args.solve_fp64 and world == 1:
             modes.append(("fp64", dict(mixed=0), 1, 0))
-        solve[f"L{level}"] = solve_bench(prob, mesh, level, dev, modes)
+        solve[f"L{level}"] = _optional(lambda: solve_bench(prob, mesh, level, dev, modes))
     del prob, mesh
     torch.cuda.empty_cache()
-    # the level-5 workload beside it: apply, roofline, solves, Schur applications
-    if level != 5 and world == 1 and not args.no_level5:
+
+    def level5():
+        # the level-5 workload beside it: apply, roofline, solves, Schur applications
         ctx5, mesh5, prob5, inf5 = setup_problem(5, device)
         ab5 = apply_bench(ctx5, prob5, inf5, 5, args.steps, args.warmup, 1, 0, dev)
         del ab5["sets"]
-        line["level5"] = {"workload": WORKLOADS[5], "value": round(ab5["value"], 3), "unit": "GDoF/s",
-                          "ms_per_step": round(ab5["ms_per_step"], 5),
-                          "roofline": roofline(5, inf5, ab5["kernel_ms"], ab5["fp64_kernel_ms"], peaks),
-                          "a_block": {"kernel_ms": round(ab5["a_ms"], 5),
-                                      "gdofs": round(3 * inf5.n_p2 / (ab5["a_ms"] * 1e-3) / 1e9, 3)}}
+        out = {"workload": WORKLOADS[5], "value": round(ab5["value"], 3), "unit": "GDoF/s",
+               "ms_per_step": round(ab5["ms_per_step"], 5),
+               "roofline": roofline(5, inf5, ab5["kernel_ms"], ab5["fp64_kernel_ms"], peaks),
+               "a_block": {"kernel_ms": round(ab5["a_ms"], 5),
+                           "gdofs": round(3 * inf5.n_p2 / (ab5["a_ms"] * 1e-3) / 1e9, 3)}}
         if args.solve:
             modes5 = [("mixed", dict(mixed=1), args.solve_reps, 1),
                       ("mixed_fp64_outer", dict(mixed=2), args.solve_reps, 1),
                       ("mixed_fp64_outer_adjoint_uzawa", dict(mixed=2, uzawa=2, tol_A=1e-4), args.solve_reps, 1)]
             if args.solve_fp64_l5:
                 modes5.append(("fp64", dict(mixed=0), 1, 0))
-            solve["L5"] = solve_bench(prob5, mesh5, 5, dev, modes5)
-            line["level5"]["schur_apply"] = schur_applies(prob5, 5, inf5, dev)
+            solve["L5"] = _optional(lambda: solve_bench(prob5, mesh5, 5, dev, modes5))
+            out["schur_apply"] = _optional(lambda: schur_applies(prob5, 5, inf5, dev))
         del prob5, mesh5
         torch.cuda.empty_cache()
+        return out
+
+    if level != 5 and world == 1 and not args.no_level5:
+        line["level5"] = _optional(level5)
     clk.stop()
     if rank != 0:
         return None
@@ -449,9 +466,9 @@ def run_ours(args, rank, world, device):
         line["time_to_solve"] = solve
     line["clocks"] = clk.summary()
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(level, budget_s=args.cpu_seconds)
+        line["cpu_baseline"] = _optional(lambda: cpu_baseline(level, budget_s=args.cpu_seconds))
     if world == 1 and args.solve and not args.no_ensemble:
-        line["ensemble"] = ensemble_bench(device, sequential=args.ensemble)
+        line["ensemble"] = _optional(lambda: ensemble_bench(device, sequential=args.ensemble))
     return line
 
 
